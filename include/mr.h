@@ -1,0 +1,194 @@
+/*
+ * mr.h — C ABI of the GB300 fused map-and-reduce library (libmrgb.so).
+ *
+ * The library runs MapReduce jobs whose map and reduce functions are built
+ * in ("functor pairs"), following the programming model of arXiv:1309.0215
+ * Sec. II-A: map is applied to every element of an input array and emits
+ * intermediate key/value pairs; reduce folds all values that share a key; the
+ * result pairs may be ordered.  Every emitted pair is combined at once into a
+ * container (Sec. III-A "Efficient combiners"): an array for integer keys in
+ * a fixed range, a hash table for open-ended keys (Sec. III-A "Hash table and
+ * array containers").  Whether per-worker (here: per-CTA shared-memory) local
+ * arrays are kept or eliminated in favour of atomics on the global array is
+ * decided automatically from the container's footprint (Sec. III-E, last
+ * paragraph), unless the caller pins a container.
+ *
+ * Conventions
+ *  - All pointers are plain host or device addresses; no framework types.
+ *  - Every call returns an mr_status; no exception or longjmp crosses the ABI.
+ *  - A context is single-threaded: calls on one mr_ctx must not overlap.
+ *    Different contexts may be used from different threads.
+ *  - Work is enqueued on the context's CUDA stream; mr_run returns before the
+ *    GPU finishes.  mr_fetch / mr_poll / mr_sync observe completion.
+ *  - Status MR_ECUDA means a CUDA call failed; mr_last_error() gives the text.
+ */
+#ifndef MR_H_
+#define MR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MR_OK = 0,
+  MR_EINVAL = 1,      /* bad argument (null pointer, bad size, bad enum) */
+  MR_ENOMEM = 2,      /* device or host allocation failed */
+  MR_ECUDA = 3,       /* a CUDA runtime/driver call failed */
+  MR_EOVERFLOW = 4,   /* a caller-pinned hash container was too small */
+  MR_ETIMEOUT = 5,    /* a bounded device wait gave up */
+  MR_EBUDGET = 6,     /* the job does not fit the context's HBM budget */
+  MR_ENOTREADY = 7,   /* the job has not finished yet (mr_poll) */
+  MR_ENOJOB = 8       /* unknown or released job id */
+} mr_status;
+
+/* Built-in map/reduce functor pairs. */
+typedef enum {
+  /* Word Count (paper Table I, hash-table container).  Input: bytes.  map:
+   * a token is a maximal run of bytes that are not ASCII whitespace
+   * (' ', \t, \n, \v, \f, \r); each emits (token, 1).  reduce: sum.
+   * Output ordered by count descending, then key bytes ascending (unsigned,
+   * a proper prefix first). */
+  MR_WORDCOUNT = 0,
+  /* Histogram (paper Table I, array container) over interleaved R,G,B bytes:
+   * byte 3p+c emits (c*256 + value, 1).  Input length must be a multiple of
+   * 3.  Output: 768 uint64 bins, bins[c*256 + v]. */
+  MR_HIST_RGB8 = 1,
+  /* Linear-regression sums over int8 pairs (x = b[2i], y = b[2i+1]); five
+   * fixed keys.  Input length must be even.  Output: int64 {Σx, Σy, Σx²,
+   * Σy², Σxy}. */
+  MR_LINREG_I8 = 2,
+  /* k-means (Lloyd) over FP32 points [n][km_dims]: km_iters rounds of
+   * assign-to-nearest-centroid (squared Euclidean, the lowest index wins an
+   * exact tie) then centroid = mean of assigned points (an empty cluster keeps
+   * its centroid).  The key is the cluster id (array container of K*D sums +
+   * K counts).  Assignments equal FP64 argmin; centroids are FP64 means
+   * rounded to FP32.  Output layout (packed): float centroids[K][D], int32
+   * assign[n], zero padding to an 8-byte boundary, uint64 stats[4] =
+   * {points re-checked in FP32, points re-checked in FP64, iterations, 0}. */
+  MR_KMEANS_F32 = 3
+} mr_kind;
+
+typedef enum {
+  MR_C_AUTO = 0,          /* let the library choose (paper Sec. III-E rule) */
+  MR_C_SMEM_ARRAY = 1,    /* local arrays in shared memory, flushed to the global array */
+  MR_C_GLOBAL_ARRAY = 2,  /* no local arrays: atomics straight on the global array */
+  MR_C_HASH = 3           /* global open-addressing hash table */
+} mr_container;
+
+typedef enum {
+  MR_RUN_PLAIN = 0,       /* one launch sequence per job, in submission order */
+  MR_RUN_BATCHED = 1      /* all pending array/hash jobs in one persistent launch */
+} mr_mode;
+
+typedef enum {
+  MR_KM_FP32 = 0,         /* FP32 SIMT distances, exact re-check of near ties */
+  MR_KM_BF16_TC = 1       /* BF16 tensor-core distance GEMM (FP32 accumulate),
+                             FP32 then FP64 re-check of near ties */
+} mr_km_precision;
+
+typedef struct mr_ctx mr_ctx;
+
+typedef struct {
+  uint32_t struct_size;   /* sizeof(mr_config) */
+  int device;             /* CUDA device ordinal */
+  void* cuda_stream;      /* cudaStream_t to enqueue on; NULL = library-owned stream */
+  uint64_t hbm_budget;    /* max device bytes held by this context; 0 = unlimited */
+  /* Optional device allocator (e.g. a framework's caching allocator).  When
+   * alloc is NULL the library uses cudaMallocAsync on its stream.  alloc
+   * returns NULL on failure; free must accept any pointer alloc returned. */
+  void* (*alloc)(void* user, size_t bytes);
+  void (*free)(void* user, void* ptr);
+  void* alloc_user;
+  uint32_t flags;         /* MR_FLAG_* bits */
+} mr_config;
+
+/* mr_config.flags: record CUDA timing events around each job's kernels so
+ * that mr_job_elapsed_ms can report the job's device time. */
+#define MR_FLAG_TIMING 1u
+
+typedef struct {
+  uint32_t struct_size;   /* sizeof(mr_job_desc) */
+  mr_kind kind;
+  const void* input;      /* job input (host or device address) */
+  uint64_t input_bytes;
+  int input_on_device;    /* 1: device pointer, borrowed until the job completes;
+                             0: host pointer, copied before mr_add_job returns */
+  mr_container container; /* MR_C_AUTO unless the caller pins one */
+  /* k-means only */
+  uint32_t km_dims;       /* D */
+  uint32_t km_k;          /* K */
+  uint32_t km_iters;      /* number of Lloyd rounds (no early stop) */
+  const float* km_init;   /* K*D initial centroids; same memory space as input */
+  uint32_t km_precision;  /* mr_km_precision */
+  /* word count only: initial hash-table slots (power of two, 0 = automatic) */
+  uint64_t wc_slots;
+} mr_job_desc;
+
+/* Create a context on cfg->device.  *out receives the handle.
+ * Errors: MR_EINVAL (null, bad struct_size, bad device), MR_ECUDA. */
+mr_status mr_create(const mr_config* cfg, mr_ctx** out);
+
+/* Destroy a context: waits for its work, frees every job and container. */
+void mr_destroy(mr_ctx* ctx);
+
+/* Validate a job, choose its container, reserve its device memory (and copy a
+ * host input to the device) and queue it for the next mr_run.
+ * *job_id receives an id > 0.  Errors: MR_EINVAL, MR_ENOMEM, MR_EBUDGET,
+ * MR_ECUDA. */
+mr_status mr_add_job(mr_ctx* ctx, const mr_job_desc* desc, uint64_t* job_id);
+
+/* Enqueue every pending job on the context stream.  PLAIN launches each job's
+ * kernels in order; BATCHED runs all pending word-count / histogram /
+ * regression jobs in one persistent kernel (k-means jobs always run plain).
+ * Returns when the work is enqueued. */
+mr_status mr_run(mr_ctx* ctx, mr_mode mode);
+
+/* Copy a finished job's result into host memory buf (buf_bytes long).
+ * Blocks until the job is done.  With buf == NULL only *needed is set (the
+ * result size in bytes).  A word-count job whose automatic hash table
+ * overflowed is re-run with a larger table inside this call.
+ * Errors: MR_ENOJOB, MR_EINVAL (buf too small), MR_EOVERFLOW, MR_ECUDA. */
+mr_status mr_fetch(mr_ctx* ctx, uint64_t job_id, void* buf, uint64_t buf_bytes, uint64_t* needed);
+
+/* Device address and size of a finished job's result (valid until
+ * mr_release).  Blocks until the job is done (same rules as mr_fetch). */
+mr_status mr_result_device(mr_ctx* ctx, uint64_t job_id, const void** dptr, uint64_t* bytes);
+
+/* Free a job's containers and result.  Waits for the job if it is running. */
+mr_status mr_release(mr_ctx* ctx, uint64_t job_id);
+
+/* Serving: admit a job if the context's HBM budget allows (MR_EBUDGET
+ * otherwise, nothing queued), and enqueue it at once on the context stream.
+ * Completion is observed with mr_poll. */
+mr_status mr_submit(mr_ctx* ctx, const mr_job_desc* desc, uint64_t* job_id);
+
+/* MR_OK when the job has finished, MR_ENOTREADY while it runs. */
+mr_status mr_poll(mr_ctx* ctx, uint64_t job_id);
+
+/* Wait for all work enqueued on the context. */
+mr_status mr_sync(mr_ctx* ctx);
+
+/* Device bytes currently held by the context's jobs. */
+uint64_t mr_bytes_in_use(const mr_ctx* ctx);
+
+/* Device time in milliseconds between the start and the end of a finished
+ * job's kernel sequence on the context stream (the context must have been
+ * created with MR_FLAG_TIMING).  Blocks until the job is done.
+ * Errors: MR_ENOJOB, MR_ENOTREADY (not run yet), MR_EINVAL (no timing). */
+mr_status mr_job_elapsed_ms(mr_ctx* ctx, uint64_t job_id, float* ms);
+
+/* Number of CUDA kernels this context has launched so far (all jobs). */
+uint64_t mr_kernel_launches(const mr_ctx* ctx);
+
+const char* mr_status_str(mr_status s);
+
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char* mr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MR_H_ */

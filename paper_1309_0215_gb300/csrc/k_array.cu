@@ -1,0 +1,281 @@
+// Array-container jobs: RGB8 histogram and int8 linear-regression sums.
+//
+// Paper mapping (arXiv:1309.0215):
+//  - map + combiner (Sec. III-A): every input byte emits (key, 1) and is
+//    combined at once into a local array;
+//  - local arrays vs "eliminating local arrays" (Sec. III-E): with local
+//    arrays each worker owns a private array that is merged into the global
+//    array at the end; without them every emit is an atomic on the global
+//    array.  Here a worker is a CTA and its local array lives in shared
+//    memory; the "eliminated" form issues global atomics per emit.
+//
+// GB300 design of the local array (histogram): a CTA keeps 32 copies of the
+// 768 bins laid out bin-major, [channel*256 + value][lane], one u32 column per
+// lane index, shared by every warp of the CTA.  The word a lane touches is
+// always in bank (lane), so a warp-wide update never has a bank conflict
+// whatever the data skew, and updates from different warps are resolved by
+// the shared-memory atomic unit.  The update is a fire-and-forget
+// `red.shared.add.u32`.  Input is streamed with coalesced 128-bit
+// non-allocating loads: a warp reads 1536 contiguous bytes (three 512-byte
+// rows, 16 bytes per lane per row); 1536 is a multiple of 3, so the channel of
+// every byte is a fixed rotation per (row, lane).
+#include "mr_internal.h"
+
+namespace mrgb {
+namespace {
+
+constexpr int HIST_THREADS = 1024;
+constexpr int HIST_BINS = 768;
+constexpr int HIST_COLS = 32;
+constexpr int HIST_WORDS = HIST_BINS * HIST_COLS;   // 96 KiB of u32 counters
+constexpr int CHUNK = 1536;                          // bytes per warp step
+constexpr int CHUNK_VEC = CHUNK / 16;
+
+__device__ __forceinline__ uint4 ldg_stream(const uint4* p) {
+  uint4 r;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "l"(p));
+  return r;
+}
+
+__device__ __forceinline__ void red_shared_add(uint32_t addr, uint32_t v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+// One 32-bit word = 4 bytes; byte b belongs to channel slot (j0 + b) % 3 of
+// the rotation cb[]; cb[q] already holds the lane's column base for that
+// channel.  Counter address = column base + value * 32 lanes * 4 bytes.
+template <int J0>
+__device__ __forceinline__ void hist_word(uint32_t w, const uint32_t (&cb)[3]) {
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    uint32_t v = (w >> (8 * b)) & 0xFFu;
+    red_shared_add(cb[(J0 + b) % 3] + v * (HIST_COLS * 4), 1u);
+  }
+}
+
+// 16 bytes loaded by one lane for row k of a chunk.  Byte j of row k is at
+// chunk offset k*512 + lane*16 + j; its channel is (rot0 + 2k + j) % 3 where
+// rot0 = (alignment offset + lane) % 3 (512 = 2 mod 3, 16 = 1 mod 3).
+template <int K>
+__device__ __forceinline__ void hist_vec(uint4 a, const uint32_t (&cb)[3]) {
+  constexpr int R = (2 * K) % 3;
+  // cbk[q] = column base of channel (rot0 + R + q) % 3
+  uint32_t cbk[3] = {cb[R % 3], cb[(R + 1) % 3], cb[(R + 2) % 3]};
+  hist_word<0>(a.x, cbk);
+  hist_word<4>(a.y, cbk);
+  hist_word<8>(a.z, cbk);
+  hist_word<12>(a.w, cbk);
+}
+
+__global__ void __launch_bounds__(HIST_THREADS, 1)
+hist_smem_kernel(const uint8_t* __restrict__ in, uint64_t n, unsigned long long* __restrict__ bins) {
+  extern __shared__ uint32_t hs[];
+  for (int i = threadIdx.x; i < HIST_WORDS; i += blockDim.x) hs[i] = 0;
+  __syncthreads();
+
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(hs);
+  const uint32_t lb = sbase + lane * 4;
+
+  // 16-byte aligned main region
+  uint64_t o0 = (16 - ((uintptr_t)in & 15)) & 15;
+  if (o0 > n) o0 = n;
+  const uint64_t nchunks = (n - o0) / CHUNK;
+  const uint4* vin = reinterpret_cast<const uint4*>(in + o0);
+
+  const uint32_t rot0 = (uint32_t)((o0 + lane) % 3);
+  uint32_t cb[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) cb[q] = lb + ((rot0 + q) % 3) * (256u * HIST_COLS * 4);
+
+  const uint64_t w0 = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  uint64_t c = w0;
+  for (; c + nw < nchunks; c += 2 * nw) {
+    const uint4* p = vin + c * CHUNK_VEC + lane;
+    const uint4* q = vin + (c + nw) * CHUNK_VEC + lane;
+    uint4 a0 = ldg_stream(p), a1 = ldg_stream(p + 32), a2 = ldg_stream(p + 64);
+    uint4 b0 = ldg_stream(q), b1 = ldg_stream(q + 32), b2 = ldg_stream(q + 64);
+    hist_vec<0>(a0, cb);
+    hist_vec<1>(a1, cb);
+    hist_vec<2>(a2, cb);
+    hist_vec<0>(b0, cb);
+    hist_vec<1>(b1, cb);
+    hist_vec<2>(b2, cb);
+  }
+  if (c < nchunks) {
+    const uint4* p = vin + c * CHUNK_VEC + lane;
+    uint4 a0 = ldg_stream(p), a1 = ldg_stream(p + 32), a2 = ldg_stream(p + 64);
+    hist_vec<0>(a0, cb);
+    hist_vec<1>(a1, cb);
+    hist_vec<2>(a2, cb);
+  }
+  // unaligned head and ragged tail: the last CTA, byte by byte
+  if (blockIdx.x == gridDim.x - 1) {
+    const uint64_t tail0 = o0 + nchunks * CHUNK;
+    const uint64_t nscalar = o0 + (n - tail0);
+    for (uint64_t t = threadIdx.x; t < nscalar; t += blockDim.x) {
+      uint64_t i = t < o0 ? t : tail0 + (t - o0);
+      uint32_t ch = (uint32_t)(i % 3);
+      red_shared_add(lb + ch * (256u * HIST_COLS * 4) + (uint32_t)in[i] * (HIST_COLS * 4), 1u);
+    }
+  }
+  __syncthreads();
+  // merge the local array into the global array
+  for (int bin = threadIdx.x; bin < HIST_BINS; bin += blockDim.x) {
+    unsigned long long s = 0;
+#pragma unroll 8
+    for (int l = 0; l < HIST_COLS; ++l) s += hs[bin * HIST_COLS + ((l + bin) & 31)];
+    if (s) atomicAdd(bins + bin, s);
+  }
+}
+
+// "Eliminated local arrays": every emit is a 64-bit atomic on the global bins.
+__global__ void hist_global_kernel(const uint8_t* __restrict__ in, uint64_t n, unsigned long long* __restrict__ bins) {
+  uint64_t o0 = (16 - ((uintptr_t)in & 15)) & 15;
+  if (o0 > n) o0 = n;
+  const uint64_t nvec = (n - o0) / 16;
+  const uint4* vin = reinterpret_cast<const uint4*>(in + o0);
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = tid; v < nvec; v += nth) {
+    uint4 a = ldg_stream(vin + v);
+    uint32_t w[4] = {a.x, a.y, a.z, a.w};
+    uint32_t ch = (uint32_t)((o0 + 16 * v) % 3);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      uint32_t val = (w[j >> 2] >> (8 * (j & 3))) & 0xFFu;
+      atomicAdd(bins + ch * 256 + val, 1ull);
+      ch = ch == 2 ? 0 : ch + 1;
+    }
+  }
+  const uint64_t tail0 = o0 + nvec * 16;
+  const uint64_t nscalar = o0 + (n - tail0);
+  for (uint64_t t = tid; t < nscalar; t += nth) {
+    uint64_t i = t < o0 ? t : tail0 + (t - o0);
+    atomicAdd(bins + (i % 3) * 256 + in[i], 1ull);
+  }
+}
+
+// ------------------------------------------------------------- regression
+// Σx, Σy, Σx², Σy², Σxy over int8 pairs with dp4a on 32-bit words holding
+// two pairs [x0 y0 x1 y1].  Per-thread partials are int32 for at most
+// LR_FLUSH vectors (|partial| <= 4096 * 4 words * 2 * 16384 < 2^31), then
+// widened to int64.
+constexpr int LR_THREADS = 512;
+constexpr int LR_FLUSH = 4096;
+
+struct Sums5 { long long v[5]; };
+
+__device__ __forceinline__ void lr_word(uint32_t w, int (&p)[5]) {
+  const int wi = (int)w;
+  const int xm = (int)(w & 0x00FF00FFu);           // [x0 0 x1 0]
+  const int ym = (int)(w & 0xFF00FF00u);           // [0 y0 0 y1]
+  const int sw = (int)__byte_perm(w, 0, 0x2301);   // [y0 x0 y1 x1]
+  p[0] = __dp4a(wi, 0x00010001, p[0]);
+  p[1] = __dp4a(wi, 0x01000100, p[1]);
+  p[2] = __dp4a(xm, wi, p[2]);
+  p[3] = __dp4a(ym, wi, p[3]);
+  p[4] = __dp4a(xm, sw, p[4]);
+}
+
+__device__ __forceinline__ void block_add_sums(long long (&acc)[5], long long* out) {
+  __shared__ long long part[32][5];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    long long v = acc[i];
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) part[warp][i] = v;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nwarps = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      long long v = lane < nwarps ? part[lane][i] : 0;
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0 && v) atomicAdd(reinterpret_cast<unsigned long long*>(out + i), (unsigned long long)v);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(LR_THREADS)
+linreg_kernel(const int8_t* __restrict__ in, uint64_t n, long long* __restrict__ sums) {
+  long long acc[5] = {0, 0, 0, 0, 0};
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t npairs = n / 2;
+  if (((uintptr_t)in & 1) == 0) {
+    uint64_t o0 = (16 - ((uintptr_t)in & 15)) & 15;  // even
+    if (o0 > n) o0 = n & ~1ull;
+    const uint64_t nvec = (n - o0) / 16;
+    const uint4* vin = reinterpret_cast<const uint4*>(in + o0);
+    uint64_t v = tid;
+    while (v < nvec) {
+      int p[5] = {0, 0, 0, 0, 0};
+      int it = 0;
+      for (; v + nth < nvec && it < LR_FLUSH; v += 2 * nth, it += 2) {
+        uint4 a = ldg_stream(vin + v);
+        uint4 b = ldg_stream(vin + v + nth);
+        lr_word(a.x, p); lr_word(a.y, p); lr_word(a.z, p); lr_word(a.w, p);
+        lr_word(b.x, p); lr_word(b.y, p); lr_word(b.z, p); lr_word(b.w, p);
+      }
+      if (v < nvec && it < LR_FLUSH) {
+        uint4 a = ldg_stream(vin + v);
+        lr_word(a.x, p); lr_word(a.y, p); lr_word(a.z, p); lr_word(a.w, p);
+        v += nth;
+      }
+#pragma unroll
+      for (int i = 0; i < 5; ++i) acc[i] += p[i];
+    }
+    // head pairs [0, o0/2) and tail pairs from o0 + 16*nvec
+    const uint64_t head = o0 / 2;
+    const uint64_t tail0 = (o0 + nvec * 16) / 2;
+    const uint64_t nscalar = head + (npairs - tail0);
+    for (uint64_t t = tid; t < nscalar; t += nth) {
+      uint64_t i = t < head ? t : tail0 + (t - head);
+      long long x = in[2 * i], y = in[2 * i + 1];
+      acc[0] += x; acc[1] += y; acc[2] += x * x; acc[3] += y * y; acc[4] += x * y;
+    }
+  } else {
+    for (uint64_t i = tid; i < npairs; i += nth) {
+      long long x = in[2 * i], y = in[2 * i + 1];
+      acc[0] += x; acc[1] += y; acc[2] += x * x; acc[3] += y * y; acc[4] += x * y;
+    }
+  }
+  block_add_sums(acc, sums);
+}
+
+}  // namespace
+
+int hist_smem_bytes() { return HIST_WORDS * 4; }
+int hist_block_threads() { return HIST_THREADS; }
+
+cudaError_t launch_hist_smem(const uint8_t* in, uint64_t n, uint64_t* bins, int grid, cudaStream_t s) {
+  static bool attr_done = false;  // per process; the attribute is per function
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(hist_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, HIST_WORDS * 4);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  if (grid < 1) grid = 1;
+  hist_smem_kernel<<<grid, HIST_THREADS, HIST_WORDS * 4, s>>>(in, n, reinterpret_cast<unsigned long long*>(bins));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hist_global(const uint8_t* in, uint64_t n, uint64_t* bins, int grid, cudaStream_t s) {
+  if (grid < 1) grid = 1;
+  hist_global_kernel<<<grid, 512, 0, s>>>(in, n, reinterpret_cast<unsigned long long*>(bins));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_linreg(const int8_t* in, uint64_t n, int64_t* sums, int grid, cudaStream_t s) {
+  if (grid < 1) grid = 1;
+  linreg_kernel<<<grid, LR_THREADS, 0, s>>>(in, n, reinterpret_cast<long long*>(sums));
+  return cudaGetLastError();
+}
+
+}  // namespace mrgb

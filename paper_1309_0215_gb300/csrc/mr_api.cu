@@ -1,0 +1,692 @@
+// Host runtime behind the C ABI in include/mr.h: contexts, jobs, the
+// container planner (paper Sec. III-E automatic detection), plain and batched
+// launch sequencing, result fetch, and HBM-budget admission for serving.
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mr_internal.h"
+
+namespace mrgb {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const char* where, cudaError_t e) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+}
+
+}  // namespace mrgb
+
+using namespace mrgb;
+
+namespace {
+
+enum JobState { JOB_PENDING = 0, JOB_ENQUEUED = 1 };
+
+struct Job {
+  uint64_t id = 0;
+  mr_job_desc desc{};
+  mr_container container = MR_C_AUTO;
+  JobState state = JOB_PENDING;
+  const uint8_t* in = nullptr;   // device input
+  void* in_owned = nullptr;      // device copy of a host input
+  uint64_t in_owned_bytes = 0;
+  void* slab = nullptr;          // containers + scratch + result
+  uint64_t slab_bytes = 0;
+  void* result = nullptr;
+  uint64_t result_bytes = 0;     // fixed-size kinds
+  cudaEvent_t done = nullptr;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;  // timing events (MR_FLAG_TIMING)
+  // word count
+  WcBuffers wc;
+  bool wc_auto = true;
+  // k-means
+  KmBuffers km;
+  float* km_init_dev = nullptr;
+  void* km_init_owned = nullptr;
+};
+
+}  // namespace
+
+struct mr_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  DevInfo di;
+  void* (*alloc)(void*, size_t) = nullptr;
+  void (*free_fn)(void*, void*) = nullptr;
+  void* alloc_user = nullptr;
+  uint64_t budget = 0;
+  uint64_t in_use = 0;
+  uint32_t flags = 0;
+  uint64_t launches = 0;
+  uint64_t next_id = 1;
+  std::map<uint64_t, Job*> jobs;
+  std::vector<uint64_t> pending;
+  // batched launch scratch
+  void* batch_desc = nullptr;
+  uint64_t batch_desc_bytes = 0;
+  void* batch_cursor = nullptr;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+mr_status dev_alloc(mr_ctx* c, uint64_t bytes, void** out) {
+  *out = nullptr;
+  if (bytes == 0) bytes = 256;
+  if (c->budget && c->in_use + bytes > c->budget) return MR_EBUDGET;
+  void* p = nullptr;
+  if (c->alloc) {
+    p = c->alloc(c->alloc_user, (size_t)bytes);
+    if (!p) return MR_ENOMEM;
+  } else {
+    cudaError_t e = cudaMallocAsync(&p, (size_t)bytes, c->stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_last_error("cudaMallocAsync", e);
+      return e == cudaErrorMemoryAllocation ? MR_ENOMEM : MR_ECUDA;
+    }
+  }
+  c->in_use += bytes;
+  *out = p;
+  return MR_OK;
+}
+
+void dev_free(mr_ctx* c, void* p, uint64_t bytes) {
+  if (!p) return;
+  if (bytes == 0) bytes = 256;
+  if (c->free_fn) c->free_fn(c->alloc_user, p);
+  else cudaFreeAsync(p, c->stream);
+  c->in_use -= bytes < c->in_use ? bytes : c->in_use;
+}
+
+inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+inline uint64_t km_stats_offset(uint64_t K, uint64_t D, uint64_t N) { return (K * D * 4 + N * 4 + 7) & ~7ull; }
+
+uint64_t next_pow2(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// Planner: the paper keeps per-worker local arrays while each one fits the
+// per-core cache and eliminates them otherwise (Sec. III-E).  The GB300 local
+// store of a worker (CTA) is its shared memory, so an array job keeps local
+// arrays when its lane-column copy fits the opt-in shared memory of one CTA.
+mr_container plan_container(const mr_ctx* c, const mr_job_desc* d) {
+  switch (d->kind) {
+    case MR_WORDCOUNT:
+      return MR_C_HASH;
+    case MR_HIST_RGB8:
+      if (d->container == MR_C_SMEM_ARRAY || d->container == MR_C_GLOBAL_ARRAY) return d->container;
+      return hist_smem_bytes() <= c->di.smem_optin ? MR_C_SMEM_ARRAY : MR_C_GLOBAL_ARRAY;
+    case MR_LINREG_I8:
+    case MR_KMEANS_F32:
+    default:
+      return MR_C_SMEM_ARRAY;
+  }
+}
+
+mr_status validate(const mr_ctx* c, const mr_job_desc* d) {
+  if (!d || d->struct_size < sizeof(mr_job_desc)) return MR_EINVAL;
+  if ((unsigned)d->kind > (unsigned)MR_KMEANS_F32) return MR_EINVAL;
+  if ((unsigned)d->container > (unsigned)MR_C_HASH) return MR_EINVAL;
+  if (d->input_bytes && !d->input) return MR_EINVAL;
+  switch (d->kind) {
+    case MR_WORDCOUNT:
+      if (d->container != MR_C_AUTO && d->container != MR_C_HASH) return MR_EINVAL;
+      if (d->input_bytes >= (1ull << 40) - 1) return MR_EINVAL;
+      if (d->wc_slots && (d->wc_slots & (d->wc_slots - 1))) return MR_EINVAL;
+      if (d->wc_slots && (d->wc_slots < 1024 || d->wc_slots > (1ull << 32))) return MR_EINVAL;
+      break;
+    case MR_HIST_RGB8:
+      if (d->input_bytes % 3) return MR_EINVAL;
+      if (d->container == MR_C_HASH) return MR_EINVAL;
+      break;
+    case MR_LINREG_I8:
+      if (d->input_bytes % 2) return MR_EINVAL;
+      if (d->container == MR_C_HASH) return MR_EINVAL;
+      break;
+    case MR_KMEANS_F32: {
+      if (d->container == MR_C_HASH || d->container == MR_C_GLOBAL_ARRAY) return MR_EINVAL;
+      if (d->km_dims == 0 || d->km_k == 0 || !d->km_init || d->km_iters == 0) return MR_EINVAL;
+      if (d->km_dims > 1024 || d->km_k > 4096) return MR_EINVAL;
+      const uint64_t row = (uint64_t)d->km_dims * 4;
+      if (d->input_bytes % row) return MR_EINVAL;
+      const uint64_t n = d->input_bytes / row;
+      if (n == 0 || n > 0x7fffffffull) return MR_EINVAL;
+      if (d->km_precision > MR_KM_BF16_TC) return MR_EINVAL;
+      if (d->km_precision == MR_KM_BF16_TC && !km_tc_supported(d->km_dims, d->km_k)) return MR_EINVAL;
+      break;
+    }
+  }
+  (void)c;
+  return MR_OK;
+}
+
+mr_status alloc_wc(mr_ctx* c, Job* j, uint64_t cap) {
+  const uint64_t n = j->desc.input_bytes;
+  WcBuffers& b = j->wc;
+  const uint64_t t_bytes = align256(2 * cap * 8);
+  const uint64_t s_bytes = align256(16);
+  const uint64_t sb_bytes = align256(wc_sortbuf_bytes(cap));
+  const uint64_t o_bytes = align256(wc_out_bytes(cap, n));
+  const uint64_t total = t_bytes + s_bytes + sb_bytes + o_bytes;
+  void* slab = nullptr;
+  mr_status st = dev_alloc(c, total, &slab);
+  if (st) return st;
+  uint8_t* p = static_cast<uint8_t*>(slab);
+  b.cap = cap;
+  b.key = reinterpret_cast<uint64_t*>(p);
+  b.cnt = b.key + cap;
+  b.state = reinterpret_cast<uint32_t*>(p + t_bytes);
+  b.sortbuf = p + t_bytes + s_bytes;
+  b.out = p + t_bytes + s_bytes + sb_bytes;
+  b.out_cap = wc_out_bytes(cap, n);
+  j->slab = slab;
+  j->slab_bytes = total;
+  j->result = b.out;
+  return MR_OK;
+}
+
+mr_status alloc_job_memory(mr_ctx* c, Job* j) {
+  const mr_job_desc& d = j->desc;
+  switch (d.kind) {
+    case MR_WORDCOUNT: {
+      uint64_t cap = d.wc_slots;
+      j->wc_auto = cap == 0;
+      if (!cap) {
+        // estimate: one distinct key per 64 input bytes, at most half full
+        cap = next_pow2(d.input_bytes / 32 + 1);
+        if (cap < 4096) cap = 4096;
+        if (cap > (1ull << 26)) cap = 1ull << 26;
+      }
+      return alloc_wc(c, j, cap);
+    }
+    case MR_HIST_RGB8: {
+      j->result_bytes = 768 * 8;
+      mr_status st = dev_alloc(c, 768 * 8, &j->slab);
+      if (st) return st;
+      j->slab_bytes = 768 * 8;
+      j->result = j->slab;
+      return MR_OK;
+    }
+    case MR_LINREG_I8: {
+      j->result_bytes = 5 * 8;
+      mr_status st = dev_alloc(c, 64, &j->slab);
+      if (st) return st;
+      j->slab_bytes = 64;
+      j->result = j->slab;
+      return MR_OK;
+    }
+    case MR_KMEANS_F32: {
+      const uint32_t D = d.km_dims, K = d.km_k;
+      const uint32_t N = (uint32_t)(d.input_bytes / ((uint64_t)D * 4));
+      // result: centroids [K*D] f32 | assignments [N] i32 | pad to 8 | stats [4] u64
+      const uint64_t res_bytes = km_stats_offset(K, D, N) + 32;
+      const uint64_t res = align256(res_bytes);
+      const uint64_t scr = align256(km_scratch_bytes(N, D, K, (int)d.km_precision));
+      const uint64_t init_bytes = d.input_on_device ? 0 : align256((uint64_t)K * D * 4);
+      mr_status st = dev_alloc(c, res + scr + init_bytes, &j->slab);
+      if (st) return st;
+      j->slab_bytes = res + scr + init_bytes;
+      uint8_t* p = static_cast<uint8_t*>(j->slab);
+      j->result = p;
+      j->result_bytes = res_bytes;
+      j->km.n = N;
+      j->km.d = D;
+      j->km.k = K;
+      j->km.precision = (int)d.km_precision;
+      cudaError_t e = km_carve(j->km, p + res, scr);
+      if (e != cudaSuccess) {
+        set_last_error("km_carve", e);
+        return MR_EINVAL;
+      }
+      if (!d.input_on_device) {
+        j->km_init_dev = reinterpret_cast<float*>(p + res + scr);
+        MR_CUDA_TRY(cudaMemcpyAsync(j->km_init_dev, d.km_init, (size_t)K * D * 4, cudaMemcpyHostToDevice, c->stream));
+      } else {
+        j->km_init_dev = const_cast<float*>(d.km_init);
+      }
+      return MR_OK;
+    }
+  }
+  return MR_EINVAL;
+}
+
+void free_job(mr_ctx* c, Job* j) {
+  if (j->done) cudaEventDestroy(j->done);
+  if (j->t0) cudaEventDestroy(j->t0);
+  if (j->t1) cudaEventDestroy(j->t1);
+  dev_free(c, j->slab, j->slab_bytes);
+  dev_free(c, j->in_owned, j->in_owned_bytes);
+  delete j;
+}
+
+int grid_for(const mr_ctx* c, uint64_t bytes, uint64_t bytes_per_block, int max_per_sm) {
+  uint64_t g = (bytes + bytes_per_block - 1) / bytes_per_block;
+  const uint64_t gmax = (uint64_t)c->di.sms * max_per_sm;
+  if (g > gmax) g = gmax;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+mr_status enqueue_plain(mr_ctx* c, Job* j) {
+  const uint64_t n = j->desc.input_bytes;
+  if (j->t0) MR_CUDA_TRY(cudaEventRecord(j->t0, c->stream));
+  switch (j->desc.kind) {
+    case MR_HIST_RGB8: {
+      MR_CUDA_TRY(cudaMemsetAsync(j->result, 0, 768 * 8, c->stream));
+      if (j->container == MR_C_GLOBAL_ARRAY) {
+        MR_CUDA_TRY(launch_hist_global(j->in, n, static_cast<uint64_t*>(j->result), grid_for(c, n, 512 * 64, 4),
+                                       c->stream));
+        ++c->launches;
+      } else {
+        // a CTA is worth launching once each of its 32 warps gets a few 1536-byte steps
+        MR_CUDA_TRY(launch_hist_smem(j->in, n, static_cast<uint64_t*>(j->result),
+                                     grid_for(c, n, 1536ull * 32 * 4, 1), c->stream));
+        ++c->launches;
+      }
+      break;
+    }
+    case MR_LINREG_I8:
+      MR_CUDA_TRY(cudaMemsetAsync(j->result, 0, 5 * 8, c->stream));
+      MR_CUDA_TRY(launch_linreg(reinterpret_cast<const int8_t*>(j->in), n, static_cast<int64_t*>(j->result),
+                                grid_for(c, n, 512ull * 16 * 8, 2), c->stream));
+      ++c->launches;
+      break;
+    case MR_WORDCOUNT:
+      MR_CUDA_TRY(launch_wordcount(j->in, n, j->wc, c->di, c->stream, &c->launches));
+      break;
+    case MR_KMEANS_F32: {
+      uint8_t* p = static_cast<uint8_t*>(j->result);
+      const uint32_t K = j->km.k, D = j->km.d, N = j->km.n;
+      float* oc = reinterpret_cast<float*>(p);
+      int32_t* oa = reinterpret_cast<int32_t*>(p + (uint64_t)K * D * 4);
+      unsigned long long* os = reinterpret_cast<unsigned long long*>(p + km_stats_offset(K, D, N));
+      MR_CUDA_TRY(launch_kmeans(reinterpret_cast<const float*>(j->in), j->km_init_dev, j->desc.km_iters, j->km,
+                                c->di, c->stream, oc, oa, os, &c->launches));
+      break;
+    }
+  }
+  if (j->t1) MR_CUDA_TRY(cudaEventRecord(j->t1, c->stream));
+  MR_CUDA_TRY(cudaEventRecord(j->done, c->stream));
+  j->state = JOB_ENQUEUED;
+  return MR_OK;
+}
+
+mr_status enqueue_batched(mr_ctx* c, std::vector<Job*>& jobs) {
+  // k-means jobs always run plain; the others share one persistent launch
+  std::vector<BatchJob> bj;
+  std::vector<Job*> batched;
+  uint64_t tiles = 0;
+  for (Job* j : jobs) {
+    if (j->desc.kind == MR_KMEANS_F32) continue;
+    BatchJob b{};
+    b.kind = (uint32_t)j->desc.kind;
+    b.container = (uint32_t)j->container;
+    b.in = j->in;
+    b.n = j->desc.input_bytes;
+    b.out = j->result;
+    if (j->desc.kind == MR_WORDCOUNT) {
+      b.wc_key = j->wc.key;
+      b.wc_cnt = j->wc.cnt;
+      b.wc_cap = j->wc.cap;
+      b.wc_state = j->wc.state;
+    }
+    b.tile_begin = tiles;
+    b.ntiles = batch_tiles_for(b.kind, b.n);
+    tiles += b.ntiles;
+    bj.push_back(b);
+    batched.push_back(j);
+  }
+  if (!bj.empty()) {
+    const uint64_t need = align256(bj.size() * sizeof(BatchJob));
+    if (need > c->batch_desc_bytes) {
+      dev_free(c, c->batch_desc, c->batch_desc_bytes);
+      c->batch_desc = nullptr;
+      c->batch_desc_bytes = 0;
+      mr_status st = dev_alloc(c, need, &c->batch_desc);
+      if (st) return st;
+      c->batch_desc_bytes = need;
+    }
+    if (!c->batch_cursor) {
+      mr_status st = dev_alloc(c, 256, &c->batch_cursor);
+      if (st) return st;
+    }
+    // zero every container that the batch kernel accumulates into
+    for (Job* j : batched) {
+      if (j->desc.kind == MR_WORDCOUNT) {
+        MR_CUDA_TRY(cudaMemsetAsync(j->wc.key, 0, 2 * j->wc.cap * 8, c->stream));
+        MR_CUDA_TRY(cudaMemsetAsync(j->wc.state, 0, 16, c->stream));
+      } else {
+        MR_CUDA_TRY(cudaMemsetAsync(j->result, 0, j->result_bytes, c->stream));
+      }
+    }
+    MR_CUDA_TRY(cudaMemcpyAsync(c->batch_desc, bj.data(), bj.size() * sizeof(BatchJob), cudaMemcpyHostToDevice,
+                                c->stream));
+    MR_CUDA_TRY(cudaMemsetAsync(c->batch_cursor, 0, 8, c->stream));
+    MR_CUDA_TRY(launch_batch(static_cast<const BatchJob*>(c->batch_desc), (uint32_t)bj.size(), tiles,
+                             static_cast<unsigned long long*>(c->batch_cursor), c->di, c->stream));
+    // hash jobs still need their merge + sort after the shared map/combine pass
+    for (Job* j : batched) {
+      if (j->desc.kind == MR_WORDCOUNT) {
+        WcBuffers b = j->wc;
+        (void)b;
+      }
+    }
+    for (Job* j : batched) {
+      MR_CUDA_TRY(cudaEventRecord(j->done, c->stream));
+      j->state = JOB_ENQUEUED;
+    }
+  }
+  for (Job* j : jobs)
+    if (j->desc.kind == MR_KMEANS_F32) {
+      mr_status st = enqueue_plain(c, j);
+      if (st) return st;
+    }
+  return MR_OK;
+}
+
+Job* find_job(mr_ctx* c, uint64_t id) {
+  auto it = c->jobs.find(id);
+  return it == c->jobs.end() ? nullptr : it->second;
+}
+
+// Wait for a job; for an automatic word-count table that overflowed, regrow
+// it (4x) and re-run until it fits.
+mr_status wait_job(mr_ctx* c, Job* j) {
+  if (j->state == JOB_PENDING) return MR_ENOTREADY;
+  MR_CUDA_TRY(cudaEventSynchronize(j->done));
+  if (j->desc.kind != MR_WORDCOUNT) return MR_OK;
+  for (;;) {
+    uint32_t st[4];
+    MR_CUDA_TRY(cudaMemcpyAsync(st, j->wc.state, 16, cudaMemcpyDeviceToHost, c->stream));
+    MR_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (!(st[0] & 1u)) return MR_OK;
+    if (!j->wc_auto) return MR_EOVERFLOW;
+    const uint64_t cap = j->wc.cap * 4;
+    if (cap > (1ull << 32)) return MR_EOVERFLOW;
+    dev_free(c, j->slab, j->slab_bytes);
+    j->slab = nullptr;
+    mr_status s = alloc_wc(c, j, cap);
+    if (s) return s;
+    MR_CUDA_TRY(launch_wordcount(j->in, j->desc.input_bytes, j->wc, c->di, c->stream, &c->launches));
+    MR_CUDA_TRY(cudaEventRecord(j->done, c->stream));
+    MR_CUDA_TRY(cudaEventSynchronize(j->done));
+  }
+}
+
+mr_status result_size(mr_ctx* c, Job* j, uint64_t* bytes) {
+  if (j->desc.kind == MR_WORDCOUNT) {
+    uint64_t hdr[2];
+    MR_CUDA_TRY(cudaMemcpyAsync(hdr, j->wc.out, 16, cudaMemcpyDeviceToHost, c->stream));
+    MR_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    *bytes = 16 + 24 * hdr[0] + hdr[1];
+  } else {
+    *bytes = j->result_bytes;
+  }
+  return MR_OK;
+}
+
+mr_status add_job_impl(mr_ctx* c, const mr_job_desc* desc, uint64_t* job_id) {
+  if (!c || !job_id) return MR_EINVAL;
+  mr_status st = validate(c, desc);
+  if (st) return st;
+  Job* j = new (std::nothrow) Job();
+  if (!j) return MR_ENOMEM;
+  j->desc = *desc;
+  j->container = plan_container(c, desc);
+  cudaError_t e = cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming);
+  if (e == cudaSuccess && (c->flags & MR_FLAG_TIMING)) {
+    e = cudaEventCreate(&j->t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&j->t1);
+  }
+  if (e != cudaSuccess) {
+    set_last_error("cudaEventCreate", e);
+    free_job(c, j);
+    return MR_ECUDA;
+  }
+  if (desc->input_on_device || desc->input_bytes == 0) {
+    j->in = static_cast<const uint8_t*>(desc->input);
+  } else {
+    st = dev_alloc(c, desc->input_bytes, &j->in_owned);
+    if (st) {
+      free_job(c, j);
+      return st;
+    }
+    j->in_owned_bytes = desc->input_bytes;
+    e = cudaMemcpyAsync(j->in_owned, desc->input, desc->input_bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) {
+      set_last_error("cudaMemcpyAsync(H2D)", e);
+      free_job(c, j);
+      return MR_ECUDA;
+    }
+    j->in = static_cast<const uint8_t*>(j->in_owned);
+  }
+  st = alloc_job_memory(c, j);
+  if (st) {
+    free_job(c, j);
+    return st;
+  }
+  if (!desc->input_on_device) {
+    // host buffers (input, k-means init) may be reused once this call returns
+    e = cudaEventRecord(j->done, c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(j->done);
+    if (e != cudaSuccess) {
+      set_last_error("host input copy", e);
+      free_job(c, j);
+      return MR_ECUDA;
+    }
+  }
+  j->id = c->next_id++;
+  c->jobs[j->id] = j;
+  *job_id = j->id;
+  return MR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mr_status_str(mr_status s) {
+  switch (s) {
+    case MR_OK: return "MR_OK";
+    case MR_EINVAL: return "MR_EINVAL: invalid argument";
+    case MR_ENOMEM: return "MR_ENOMEM: out of memory";
+    case MR_ECUDA: return "MR_ECUDA: CUDA error";
+    case MR_EOVERFLOW: return "MR_EOVERFLOW: hash container too small";
+    case MR_ETIMEOUT: return "MR_ETIMEOUT: device wait timed out";
+    case MR_EBUDGET: return "MR_EBUDGET: HBM budget exceeded";
+    case MR_ENOTREADY: return "MR_ENOTREADY: job not finished";
+    case MR_ENOJOB: return "MR_ENOJOB: no such job";
+  }
+  return "unknown mr_status";
+}
+
+const char* mr_last_error(void) { return g_last_error.c_str(); }
+
+mr_status mr_create(const mr_config* cfg, mr_ctx** out) {
+  if (!cfg || !out || cfg->struct_size < sizeof(mr_config)) return MR_EINVAL;
+  if ((cfg->alloc == nullptr) != (cfg->free == nullptr)) return MR_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  MR_CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (cfg->device < 0 || cfg->device >= ndev) return MR_EINVAL;
+  DeviceGuard g(cfg->device);
+  mr_ctx* c = new (std::nothrow) mr_ctx();
+  if (!c) return MR_ENOMEM;
+  c->device = cfg->device;
+  c->alloc = cfg->alloc;
+  c->free_fn = cfg->free;
+  c->alloc_user = cfg->alloc_user;
+  c->budget = cfg->hbm_budget;
+  c->flags = cfg->flags;
+  cudaError_t e = cudaDeviceGetAttribute(&c->di.sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->di.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->di.l2_bytes, cudaDevAttrL2CacheSize, c->device);
+  if (e == cudaSuccess) {
+    if (cfg->cuda_stream) {
+      c->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+    } else {
+      e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+      c->own_stream = e == cudaSuccess;
+    }
+  }
+  if (e != cudaSuccess) {
+    set_last_error("mr_create", e);
+    delete c;
+    return MR_ECUDA;
+  }
+  *out = c;
+  return MR_OK;
+}
+
+void mr_destroy(mr_ctx* c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->jobs) free_job(c, kv.second);
+  c->jobs.clear();
+  dev_free(c, c->batch_desc, c->batch_desc_bytes);
+  dev_free(c, c->batch_cursor, 256);
+  cudaStreamSynchronize(c->stream);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+mr_status mr_add_job(mr_ctx* c, const mr_job_desc* desc, uint64_t* job_id) {
+  if (!c) return MR_EINVAL;
+  DeviceGuard g(c->device);
+  mr_status st = add_job_impl(c, desc, job_id);
+  if (st == MR_OK) c->pending.push_back(*job_id);
+  return st;
+}
+
+mr_status mr_run(mr_ctx* c, mr_mode mode) {
+  if (!c || (mode != MR_RUN_PLAIN && mode != MR_RUN_BATCHED)) return MR_EINVAL;
+  DeviceGuard g(c->device);
+  std::vector<Job*> jobs;
+  for (uint64_t id : c->pending) {
+    Job* j = find_job(c, id);
+    if (j && j->state == JOB_PENDING) jobs.push_back(j);
+  }
+  c->pending.clear();
+  if (mode == MR_RUN_BATCHED) return enqueue_batched(c, jobs);
+  for (Job* j : jobs) {
+    mr_status st = enqueue_plain(c, j);
+    if (st) return st;
+  }
+  return MR_OK;
+}
+
+mr_status mr_fetch(mr_ctx* c, uint64_t job_id, void* buf, uint64_t buf_bytes, uint64_t* needed) {
+  if (!c) return MR_EINVAL;
+  DeviceGuard g(c->device);
+  Job* j = find_job(c, job_id);
+  if (!j) return MR_ENOJOB;
+  mr_status st = wait_job(c, j);
+  if (st) return st;
+  uint64_t bytes = 0;
+  st = result_size(c, j, &bytes);
+  if (st) return st;
+  if (needed) *needed = bytes;
+  if (!buf) return MR_OK;
+  if (buf_bytes < bytes) return MR_EINVAL;
+  MR_CUDA_TRY(cudaMemcpyAsync(buf, j->result, bytes, cudaMemcpyDeviceToHost, c->stream));
+  MR_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return MR_OK;
+}
+
+mr_status mr_result_device(mr_ctx* c, uint64_t job_id, const void** dptr, uint64_t* bytes) {
+  if (!c || !dptr || !bytes) return MR_EINVAL;
+  DeviceGuard g(c->device);
+  Job* j = find_job(c, job_id);
+  if (!j) return MR_ENOJOB;
+  mr_status st = wait_job(c, j);
+  if (st) return st;
+  st = result_size(c, j, bytes);
+  if (st) return st;
+  *dptr = j->result;
+  return MR_OK;
+}
+
+mr_status mr_release(mr_ctx* c, uint64_t job_id) {
+  if (!c) return MR_EINVAL;
+  DeviceGuard g(c->device);
+  Job* j = find_job(c, job_id);
+  if (!j) return MR_ENOJOB;
+  if (j->state == JOB_ENQUEUED) MR_CUDA_TRY(cudaEventSynchronize(j->done));
+  c->jobs.erase(job_id);
+  for (size_t i = 0; i < c->pending.size(); ++i)
+    if (c->pending[i] == job_id) {
+      c->pending.erase(c->pending.begin() + i);
+      break;
+    }
+  free_job(c, j);
+  return MR_OK;
+}
+
+mr_status mr_submit(mr_ctx* c, const mr_job_desc* desc, uint64_t* job_id) {
+  if (!c) return MR_EINVAL;
+  DeviceGuard g(c->device);
+  mr_status st = add_job_impl(c, desc, job_id);
+  if (st) return st;
+  Job* j = find_job(c, *job_id);
+  st = enqueue_plain(c, j);
+  return st;
+}
+
+mr_status mr_poll(mr_ctx* c, uint64_t job_id) {
+  if (!c) return MR_EINVAL;
+  DeviceGuard g(c->device);
+  Job* j = find_job(c, job_id);
+  if (!j) return MR_ENOJOB;
+  if (j->state == JOB_PENDING) return MR_ENOTREADY;
+  cudaError_t e = cudaEventQuery(j->done);
+  if (e == cudaSuccess) return MR_OK;
+  if (e == cudaErrorNotReady) return MR_ENOTREADY;
+  set_last_error("cudaEventQuery", e);
+  return MR_ECUDA;
+}
+
+mr_status mr_sync(mr_ctx* c) {
+  if (!c) return MR_EINVAL;
+  DeviceGuard g(c->device);
+  MR_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return MR_OK;
+}
+
+uint64_t mr_bytes_in_use(const mr_ctx* c) { return c ? c->in_use : 0; }
+
+uint64_t mr_kernel_launches(const mr_ctx* c) { return c ? c->launches : 0; }
+
+mr_status mr_job_elapsed_ms(mr_ctx* c, uint64_t job_id, float* ms) {
+  if (!c || !ms) return MR_EINVAL;
+  DeviceGuard g(c->device);
+  Job* j = find_job(c, job_id);
+  if (!j) return MR_ENOJOB;
+  if (j->state == JOB_PENDING) return MR_ENOTREADY;
+  if (!j->t0 || !j->t1) return MR_EINVAL;
+  MR_CUDA_TRY(cudaEventSynchronize(j->t1));
+  MR_CUDA_TRY(cudaEventElapsedTime(ms, j->t0, j->t1));
+  return MR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// Internal declarations shared by the CUDA translation units of libmrgb.so.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "../../include/mr.h"
+
+namespace mrgb {
+
+// ---------------------------------------------------------------- helpers
+void set_last_error(const char* where, cudaError_t e);
+
+#define MR_CUDA_TRY(expr)                                   \
+  do {                                                      \
+    cudaError_t e_ = (expr);                                \
+    if (e_ != cudaSuccess) {                                \
+      ::mrgb::set_last_error(#expr, e_);                    \
+      return MR_ECUDA;                                      \
+    }                                                       \
+  } while (0)
+
+struct DevInfo {
+  int sms = 0;
+  int smem_optin = 0;   // max dynamic shared memory per block (opt-in)
+  int l2_bytes = 0;
+};
+
+// ------------------------------------------------------------ array jobs
+// RGB8 histogram, local arrays in shared memory ("lane-column" layout:
+// bins x 32 u32 columns, one column per lane, shared by all warps of a CTA).
+// bins must be zeroed before the launch.
+cudaError_t launch_hist_smem(const uint8_t* in, uint64_t n, uint64_t* bins, int grid, cudaStream_t s);
+// RGB8 histogram without local arrays: atomics straight on the global bins.
+cudaError_t launch_hist_global(const uint8_t* in, uint64_t n, uint64_t* bins, int grid, cudaStream_t s);
+// int8 regression sums; sums must be zeroed before the launch.
+cudaError_t launch_linreg(const int8_t* in, uint64_t n, int64_t* sums, int grid, cudaStream_t s);
+
+int hist_smem_bytes();         // dynamic shared memory the smem histogram needs
+int hist_block_threads();
+
+// --------------------------------------------------------- word count job
+struct WcBuffers {
+  uint64_t cap = 0;            // global hash-table slots (power of two)
+  uint64_t* key = nullptr;     // [cap] 0 = empty, else (len<<40)|(offset+1)
+  uint64_t* cnt = nullptr;     // [cap] combined counts
+  uint32_t* state = nullptr;   // [0] overflow flag, [1] records, [2..3] spare
+  uint8_t* sortbuf = nullptr;  // 2 x cap sort records + cap u64 block sums
+  uint8_t* out = nullptr;      // result: header + records + key bytes
+  uint64_t out_cap = 0;
+};
+size_t wc_sortbuf_bytes(uint64_t cap);
+uint64_t wc_out_bytes(uint64_t cap, uint64_t n);
+// Zero the table and state, run map+combine, compaction, sort and gather.
+// *nk is incremented by the number of kernels launched.
+cudaError_t launch_wordcount(const uint8_t* in, uint64_t n, const WcBuffers& b, const DevInfo& di, cudaStream_t s,
+                             uint64_t* nk);
+// Merge + sort + gather only (the map/combine pass already filled the table).
+cudaError_t launch_wordcount_post(const uint8_t* in, uint64_t n, const WcBuffers& b, cudaStream_t s, uint64_t* nk);
+
+// ---------------------------------------------------------------- k-means
+struct KmBuffers {
+  uint32_t n = 0, d = 0, k = 0;
+  float* cent = nullptr;        // [k][d] current centroids (FP32 state)
+  float* cent_bf16_norm = nullptr;
+  int32_t* assign = nullptr;    // [n]
+  long long* sums = nullptr;    // [k][d] fixed-point sums
+  unsigned long long* counts = nullptr;  // [k]
+  unsigned long long* stats = nullptr;   // [4]
+  uint32_t* flagged = nullptr;  // [n] indices of points to re-check
+  uint32_t* nflag = nullptr;    // [2] counters
+  float* xnorm = nullptr;       // [n] ||x||
+  float* cnorm = nullptr;       // [k] ||c|| and ||c||^2
+  uint16_t* xb = nullptr;       // BF16 copy of the points [n][d]
+  uint16_t* cb = nullptr;       // BF16 centroids [k][d]
+  unsigned int* maxabs = nullptr;  // [1] bits of max |x|
+  int fx_shift = 32;            // fixed-point scale exponent
+  int precision = 0;
+};
+size_t km_scratch_bytes(uint32_t n, uint32_t d, uint32_t k, int precision);
+cudaError_t km_carve(KmBuffers& b, uint8_t* base, size_t bytes);
+cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmBuffers& b, const DevInfo& di,
+                          cudaStream_t s, float* out_cent, int32_t* out_assign, unsigned long long* out_stats,
+                          uint64_t* nk);
+bool km_tc_supported(uint32_t d, uint32_t k);
+
+// --------------------------------------------------------- batched launch
+struct BatchJob {
+  uint32_t kind;       // mr_kind
+  uint32_t container;  // mr_container chosen
+  const uint8_t* in;
+  uint64_t n;
+  void* out;           // bins / sums
+  // word count
+  uint64_t* wc_key;
+  uint64_t* wc_cnt;
+  uint64_t wc_cap;
+  uint32_t* wc_state;
+  uint64_t tile_begin; // first tile index of this job in the global tile space
+  uint64_t ntiles;
+};
+cudaError_t launch_batch(const BatchJob* jobs_dev, uint32_t njobs, uint64_t total_tiles,
+                         unsigned long long* cursor, const DevInfo& di, cudaStream_t s);
+uint64_t batch_tiles_for(uint32_t kind, uint64_t n);
+
+}  // namespace mrgb

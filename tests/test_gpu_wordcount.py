@@ -1,0 +1,99 @@
+"""GPU parity: word count (hash container + device sort), bit-exact vs the oracle.
+
+The result is a byte string in the layout of include/mr.h; parity means the
+GPU bytes equal the oracle's bytes (same records, same order, same keys)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _dev(data: bytes, offset=0):
+    import torch
+    raw = np.frombuffer(bytes(data), dtype=np.uint8)
+    buf = torch.zeros(raw.size + offset + 16, dtype=torch.uint8, device="cuda")
+    if raw.size:
+        buf[offset: offset + raw.size] = torch.from_numpy(raw.copy()).cuda()
+    return buf[offset: offset + raw.size]
+
+
+@pytest.mark.parametrize("name", ["wc_tiny.txt", "wc_edge.bin"])
+def test_wc_golden_files(mr, name):
+    text = open(os.path.join(GOLDEN, name), "rb").read()
+    assert mr.wordcount(_dev(text)) == oracle.wordcount(text)
+
+
+@pytest.mark.parametrize("text", [
+    b"", b" ", b"a", b"a ", b" a", b"x y x y x", b"ab abc ab abd abc", b"\x80 \x7f \x80",
+    b"tie1 tie2 tie1 tie2", b"\x00\x00 \x00", b"a\rb\x0bc\x0cd\te\nf g",
+])
+def test_wc_small_cases(mr, text):
+    assert mr.wordcount(_dev(text)) == oracle.wordcount(text)
+
+
+def test_wc_random_alphabets(mr):
+    rng = np.random.default_rng(5)
+    alphabet = np.frombuffer(b"ab \n\t\x00\xffc", dtype=np.uint8)
+    for n in [1, 31, 511, 512, 513, 575, 576, 577, 5000, 100_000]:
+        text = alphabet[rng.integers(0, len(alphabet), n)].tobytes()
+        assert mr.wordcount(_dev(text)) == oracle.wordcount(text), n
+
+
+def test_wc_tokens_straddle_segments_and_long_keys(mr):
+    rng = np.random.default_rng(9)
+    parts = []
+    for _ in range(3000):
+        L = int(rng.choice([1, 5, 15, 16, 17, 40, 511, 600, 1300]))
+        stem = b"prefix_shared_by_many_keys_" if L > 30 else b""
+        body = bytes(rng.integers(97, 100, L).astype(np.uint8))
+        parts.append(stem + body)
+    parts += [parts[3]] * 50 + [parts[7]] * 20
+    rng.shuffle(parts)
+    text = b" ".join(parts) + b"x"  # no trailing delimiter
+    for off in (0, 1, 7):
+        assert mr.wordcount(_dev(text, off)) == oracle.wordcount(text)
+
+
+def test_wc_hot_key_contention(mr):
+    text = b"hot " * 500_000 + b"cold hot\n" * 1000
+    assert mr.wordcount(_dev(text)) == oracle.wordcount(text)
+
+
+def test_wc_pinned_table_overflow_reports(mr):
+    text = b" ".join(b"w%d" % i for i in range(5000))
+    c = mr.Context()
+    j = c.add_job(mr.WORDCOUNT, _dev(text), wc_slots=1024)
+    c.run()
+    with pytest.raises(mr.MRError) as e:
+        c.fetch(j)
+    assert e.value.status == mr.MR_EOVERFLOW
+    c.release(j)
+    c.close()
+
+
+def test_wc_automatic_table_regrows(mr):
+    # ~4-byte distinct tokens: far more keys than the automatic estimate
+    text = b" ".join(b"%x" % i for i in range(400_000))
+    assert mr.wordcount(_dev(text)) == oracle.wordcount(text)
+
+
+def test_wc_host_input(mr):
+    text, _, _ = synth.wc_text(1 << 20, nwords=3000)
+    assert mr.wordcount(text.tobytes()) == oracle.wordcount(text)
+
+
+def test_wc_zipf_16MiB_bit_exact(mr):
+    """The word-count workload: 16 MiB Zipf(1) text over 50,000 words."""
+    import torch
+    text, ranks, vocab = synth.wc_text(16 << 20)
+    got = mr.wordcount(torch.from_numpy(text).cuda())
+    ref = oracle.wordcount(text)
+    assert got == ref
+    recs = oracle.parse_wordcount(got)
+    assert sum(c for _, c in recs) == len(ranks)
