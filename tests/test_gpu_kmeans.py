@@ -1,0 +1,123 @@
+"""GPU parity: k-means (array container keyed by cluster id).
+
+Assignments must equal the FP64 oracle's exactly; centroids must be within
+1e-5 relative (per centroid, ||c - c64|| / max(||c64||, 1)) of the oracle's.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def _rel_err(c, ref):
+    num = np.linalg.norm(c.astype(np.float64) - ref.astype(np.float64), axis=1)
+    den = np.maximum(np.linalg.norm(ref.astype(np.float64), axis=1), 1.0)
+    return float((num / den).max())
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _run(mr, x, init, iters, precision=0, on_device=True):
+    if on_device:
+        return mr.kmeans(_dev(x), _dev(init), iters, precision)
+    return mr.kmeans(x, init, iters, precision)
+
+
+@pytest.mark.parametrize("n,d,k,iters", [
+    (20_000, 64, 256, 3),   # the workload's shape, reduced N
+    (5_001, 37, 50, 2),     # ragged dims / tiles
+    (3_000, 100, 20, 2),    # D > 64: chunked dimensions
+    (4_000, 16, 300, 2),    # K > 256: chunked centroids
+    (777, 3, 1, 2),         # K = 1: the global mean
+    (64, 8, 64, 1),         # every point its own centroid
+])
+def test_kmeans_fp32_vs_oracle(mr, n, d, k, iters):
+    x, _, _ = synth.kmeans_points(n, d, max(1, min(k, 256)), seed=n + d + k)
+    init = synth.kmeans_init(x, k, seed=n)
+    c_ref, a_ref = oracle.kmeans(x, init, iters)
+    c, a, stats = _run(mr, x, init, iters)
+    assert np.array_equal(a, a_ref)
+    assert _rel_err(c, c_ref) <= TOL
+    assert int(stats[2]) == iters
+
+
+def test_kmeans_host_inputs(mr):
+    x, _, _ = synth.kmeans_points(4096, 32, 64, seed=5)
+    init = synth.kmeans_init(x, 64, seed=6)
+    c_ref, a_ref = oracle.kmeans(x, init, 2)
+    c, a, _ = _run(mr, x, init, 2, on_device=False)
+    assert np.array_equal(a, a_ref) and _rel_err(c, c_ref) <= TOL
+
+
+def test_kmeans_exact_ties_take_lowest_index(mr):
+    x, _, _ = synth.kmeans_points(6000, 8, 16, seed=21)
+    init = synth.kmeans_init(x, 16, seed=22)
+    init[9] = init[4]     # duplicate centroid: index 4 must win every tie
+    init[15] = init[0]
+    c_ref, a_ref = oracle.kmeans(x, init, 1)
+    c, a, stats = _run(mr, x, init, 1)
+    assert np.array_equal(a, a_ref)
+    assert not np.any(a == 9) and not np.any(a == 15)
+    assert int(stats[1]) > 0  # the tied points were re-checked in FP64
+    assert _rel_err(c, c_ref) <= TOL
+
+
+def test_kmeans_empty_cluster_keeps_centroid(mr):
+    x, _, _ = synth.kmeans_points(3000, 4, 3, seed=31)
+    init = np.concatenate([x[:3], np.full((1, 4), 1e4, dtype=np.float32)])
+    c_ref, a_ref = oracle.kmeans(x, init, 3)
+    c, a, _ = _run(mr, x, init, 3)
+    assert np.array_equal(a, a_ref)
+    assert np.array_equal(c[3], init[3])
+    assert _rel_err(c, c_ref) <= TOL
+
+
+def test_kmeans_teacher_forced_iterations(mr):
+    """Each GPU iteration, started from the oracle's centroids, reproduces the
+    oracle's assignment exactly and its update within tolerance."""
+    x, _, _ = synth.kmeans_points(30_000, 64, 256, seed=41)
+    cur = synth.kmeans_init(x, 256, seed=42)
+    for _ in range(4):
+        a_ref = oracle.kmeans_assign(x, cur)
+        c_ref, _ = oracle.kmeans_update(x, a_ref, cur)
+        c, a, _ = _run(mr, x, cur, 1)
+        assert np.array_equal(a, a_ref)
+        assert _rel_err(c, c_ref) <= TOL
+        cur = c_ref
+
+
+def test_kmeans_rejects_bad_args(mr):
+    x = np.zeros((10, 4), dtype=np.float32)
+    with pytest.raises(mr.MRError):
+        mr.kmeans(x, np.zeros((2, 4), dtype=np.float32), 0)
+    c = mr.Context()
+    with pytest.raises(mr.MRError):
+        c.add_job(mr.KMEANS_F32, x, km_dims=3, km_k=2, km_iters=1, km_init=np.zeros((2, 3), dtype=np.float32))
+    c.close()
+
+
+@pytest.mark.slow
+def test_kmeans_full_size_fp32(mr):
+    """4M x 64 points, K = 256, 10 iterations: determinism across a split run,
+    sampled exact assignment check against FP64 and a full FP64 update check."""
+    import torch
+    x, _, _ = synth.kmeans_points(4 << 20, 64, 256)
+    init = synth.kmeans_init(x, 256)
+    dx = torch.from_numpy(x).cuda()
+    c10, a10, _ = mr.kmeans(dx, _dev(init), 10)
+    c9, _, _ = mr.kmeans(dx, _dev(init), 9)
+    c10b, a10b, _ = mr.kmeans(dx, _dev(c9), 1)
+    assert np.array_equal(c10, c10b) and np.array_equal(a10, a10b)
+    rng = np.random.default_rng(0)
+    sample = rng.choice(x.shape[0], 3000, replace=False)
+    assert np.array_equal(a10[sample], oracle.kmeans_assign(x[sample], c9))
+    c_upd, _ = oracle.kmeans_update(x, a10, c9)
+    assert _rel_err(c10, c_upd) <= TOL
