@@ -183,6 +183,38 @@ mr_status mr_job_elapsed_ms(mr_ctx* ctx, uint64_t job_id, float* ms);
 /* Number of CUDA kernels this context has launched so far (all jobs). */
 uint64_t mr_kernel_launches(const mr_ctx* ctx);
 
+/* Word count that allocates no device memory (the paper has no counterpart;
+ * this is a deployment convenience).
+ *
+ * Who needs it: callers that cannot call cudaMalloc — for example a host
+ * program that reserves the GPU's memory up front for its own pool and does
+ * not let other components allocate, or a latency-critical loop that cannot
+ * accept the implicit synchronisation and unpredictable cost of cudaMalloc
+ * and cudaFree.  The job's hash table and sort scratch live in a fixed
+ * device array inside the library (about 11 MiB, sized for
+ * MR_NOALLOC_WC_SLOTS table slots) that every GPU loading the library holds
+ * until the process exits.
+ *
+ * Arguments: d_input / input_bytes = the text in device memory (borrowed);
+ * d_out = caller-owned device buffer of out_cap bytes, which must be at
+ * least 16 + 24 * MR_NOALLOC_WC_SLOTS + input_bytes; on success *out_bytes
+ * is the size of the result written to d_out, in the MR_WORDCOUNT layout;
+ * cuda_stream = cudaStream_t to run on (NULL = the legacy default stream).
+ * The call blocks until the job has finished on that stream.
+ *
+ * The first call on a device looks up the device address of the scratch
+ * array (with that device current); make that first call before any stream
+ * capture.  Every call on a device shares the same array, and each call
+ * clears it before use: calls whose work overlaps on the GPU (other threads
+ * or streams) race and give wrong results.
+ *
+ * Errors: MR_EINVAL (null pointer, out_cap too small, input of 2^40 bytes
+ * or more), MR_EOVERFLOW (more distinct words than the fixed table holds;
+ * the result is then invalid), MR_ECUDA. */
+#define MR_NOALLOC_WC_SLOTS 131072u
+mr_status mr_wordcount_noalloc(const void* d_input, uint64_t input_bytes, void* d_out, uint64_t out_cap,
+                               uint64_t* out_bytes, void* cuda_stream);
+
 const char* mr_status_str(mr_status s);
 
 /* Text of the last CUDA error seen by this thread ("" if none). */

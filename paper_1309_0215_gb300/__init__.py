@@ -28,7 +28,8 @@ KM_FP32, KM_BF16_TC = range(2)
 # every entry point declared in include/mr.h
 EXPORTS = ("mr_create", "mr_destroy", "mr_add_job", "mr_run", "mr_fetch", "mr_result_device", "mr_release",
            "mr_submit", "mr_poll", "mr_sync", "mr_bytes_in_use", "mr_job_elapsed_ms", "mr_kernel_launches",
-           "mr_status_str", "mr_last_error")
+           "mr_status_str", "mr_last_error", "mr_wordcount_noalloc")
+NOALLOC_WC_SLOTS = 131072
 FLAG_TIMING = 1
 
 
@@ -103,6 +104,8 @@ def load():
         lib.mr_job_elapsed_ms.restype = st
         lib.mr_kernel_launches.argtypes = [vp]
         lib.mr_kernel_launches.restype = u64
+        lib.mr_wordcount_noalloc.argtypes = [vp, u64, vp, u64, ctypes.POINTER(u64), vp]
+        lib.mr_wordcount_noalloc.restype = st
         lib.mr_status_str.argtypes = [ctypes.c_int]
         lib.mr_status_str.restype = ctypes.c_char_p
         lib.mr_last_error.argtypes = []

@@ -607,3 +607,98 @@ cudaError_t launch_wordcount_post(const uint8_t* in, uint64_t n, const WcBuffers
 }
 
 }  // namespace mrgb
+
+// ---------------------------------------------------------------------------
+// Word count without device allocation.
+//
+// Some callers cannot call cudaMalloc: a host program that has reserved the
+// GPU's memory up front for its own pool and does not allow other components
+// to allocate, or a latency-critical loop where the implicit synchronisation
+// and unpredictable cost of cudaMalloc / cudaFree are not acceptable.  For
+// them the hash table and sort scratch of one word-count job live in the
+// file-scope array below, sized for NOALLOC_SLOTS table slots.  Every GPU
+// that loads this library keeps the array (about 11 MiB) until the process
+// exits.
+#include <mutex>
+
+namespace mrgb {
+namespace {
+constexpr uint64_t NOALLOC_SLOTS = 1ull << 17;
+constexpr uint64_t NOALLOC_TABLE_BYTES = 2 * NOALLOC_SLOTS * 8;
+constexpr uint64_t NOALLOC_STATE_BYTES = 256;
+constexpr uint64_t NOALLOC_SORT_BYTES =
+    ((2 * NOALLOC_SLOTS * sizeof(SortRec) + NOALLOC_SLOTS * 8 + ((NOALLOC_SLOTS + CB - 1) / CB) * 8 + 256) + 255) &
+    ~255ull;
+constexpr uint64_t NOALLOC_SCRATCH_BYTES = NOALLOC_TABLE_BYTES + NOALLOC_STATE_BYTES + NOALLOC_SORT_BYTES;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+}  // namespace
+}  // namespace mrgb
+
+static __device__ __align__(256) unsigned char g_wc_noalloc_scratch[mrgb::NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[mrgb::NOALLOC_MAX_DEVICES] = {};
+int g_noalloc_sms[mrgb::NOALLOC_MAX_DEVICES] = {};
+
+// Once per device, with that device current: the device address of the
+// scratch array (host code only sees a host-side stand-in for the symbol).
+mr_status noalloc_setup(int dev, void** base, int* sms) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (dev < 0 || dev >= mrgb::NOALLOC_MAX_DEVICES) return MR_EINVAL;
+  if (!g_noalloc_base[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_wc_noalloc_scratch);
+    if (e != cudaSuccess) {
+      mrgb::set_last_error("cudaGetSymbolAddress(g_wc_noalloc_scratch)", e);
+      return MR_ECUDA;
+    }
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+      mrgb::set_last_error("cudaDeviceGetAttribute", e);
+      return MR_ECUDA;
+    }
+    g_noalloc_sms[dev] = n;
+    g_noalloc_base[dev] = p;
+  }
+  *base = g_noalloc_base[dev];
+  *sms = g_noalloc_sms[dev];
+  return MR_OK;
+}
+}  // namespace
+
+extern "C" mr_status mr_wordcount_noalloc(const void* d_input, uint64_t input_bytes, void* d_out, uint64_t out_cap,
+                                          uint64_t* out_bytes, void* cuda_stream) {
+  using namespace mrgb;
+  if ((!d_input && input_bytes) || !d_out || !out_bytes) return MR_EINVAL;
+  if (input_bytes >= (1ull << 40) - 1) return MR_EINVAL;
+  if (out_cap < wc_out_bytes(NOALLOC_SLOTS, input_bytes)) return MR_EINVAL;
+  int dev = 0;
+  MR_CUDA_TRY(cudaGetDevice(&dev));
+  void* base = nullptr;
+  DevInfo di;
+  mr_status st = noalloc_setup(dev, &base, &di.sms);
+  if (st) return st;
+  uint8_t* p = static_cast<uint8_t*>(base);
+  WcBuffers b;
+  b.cap = NOALLOC_SLOTS;
+  b.key = reinterpret_cast<uint64_t*>(p);
+  b.cnt = b.key + NOALLOC_SLOTS;
+  b.state = reinterpret_cast<uint32_t*>(p + NOALLOC_TABLE_BYTES);
+  b.sortbuf = p + NOALLOC_TABLE_BYTES + NOALLOC_STATE_BYTES;
+  b.out = static_cast<uint8_t*>(d_out);
+  b.out_cap = out_cap;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  uint64_t nk = 0;
+  // launch_wordcount clears the table and the state words before the map pass
+  MR_CUDA_TRY(launch_wordcount(static_cast<const uint8_t*>(d_input), input_bytes, b, di, s, &nk));
+  uint32_t state[4] = {0, 0, 0, 0};
+  uint64_t hdr[2] = {0, 0};
+  MR_CUDA_TRY(cudaMemcpyAsync(state, b.state, sizeof(state), cudaMemcpyDeviceToHost, s));
+  MR_CUDA_TRY(cudaMemcpyAsync(hdr, d_out, sizeof(hdr), cudaMemcpyDeviceToHost, s));
+  MR_CUDA_TRY(cudaStreamSynchronize(s));
+  if (state[0] & 1u) return MR_EOVERFLOW;
+  *out_bytes = 16 + 24 * hdr[0] + hdr[1];
+  return MR_OK;
+}
