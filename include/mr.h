@@ -67,7 +67,8 @@ typedef enum {
    * K counts).  Assignments equal FP64 argmin; centroids are FP64 means
    * rounded to FP32.  Output layout (packed): float centroids[K][D], int32
    * assign[n], zero padding to an 8-byte boundary, uint64 stats[4] =
-   * {points re-checked in FP32, points re-checked in FP64, iterations, 0}. */
+   * {points re-checked in FP32, points re-checked in FP64, iterations,
+   * device waits that timed out (0 unless mr_fetch returned MR_ETIMEOUT)}. */
   MR_KMEANS_F32 = 3
 } mr_kind;
 
@@ -85,8 +86,12 @@ typedef enum {
 
 typedef enum {
   MR_KM_FP32 = 0,         /* FP32 SIMT distances, exact re-check of near ties */
-  MR_KM_BF16_TC = 1       /* BF16 tensor-core distance GEMM (FP32 accumulate),
-                             FP32 then FP64 re-check of near ties */
+  MR_KM_BF16_TC = 1,      /* BF16 tensor-core distance GEMM (tcgen05, FP32
+                             accumulate) on split operands x = hi + lo (three
+                             BF16 products), FP32 then FP64 re-check of near
+                             ties; D <= 64, K <= 256 */
+  MR_KM_BF16X1_TC = 2     /* as MR_KM_BF16_TC with a single BF16 product (more
+                             points fall back to the FP32 re-check) */
 } mr_km_precision;
 
 typedef struct mr_ctx mr_ctx;

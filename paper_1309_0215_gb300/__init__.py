@@ -23,7 +23,7 @@ MR_OK, MR_EINVAL, MR_ENOMEM, MR_ECUDA, MR_EOVERFLOW, MR_ETIMEOUT, MR_EBUDGET, MR
 WORDCOUNT, HIST_RGB8, LINREG_I8, KMEANS_F32 = range(4)
 C_AUTO, C_SMEM_ARRAY, C_GLOBAL_ARRAY, C_HASH = range(4)
 RUN_PLAIN, RUN_BATCHED = range(2)
-KM_FP32, KM_BF16_TC = range(2)
+KM_FP32, KM_BF16_TC, KM_BF16X1_TC = range(3)
 
 # every entry point declared in include/mr.h
 EXPORTS = ("mr_create", "mr_destroy", "mr_add_job", "mr_run", "mr_fetch", "mr_result_device", "mr_release",

@@ -340,7 +340,7 @@ __global__ void km_finish_kernel(const float* c, uint64_t kd, float* out_c, cons
     out_s[0] = stats[0];
     out_s[1] = stats[1];
     out_s[2] = iters;
-    out_s[3] = 0;
+    out_s[3] = stats[3];
   }
 }
 
@@ -359,7 +359,7 @@ size_t km_scratch_bytes(uint32_t n, uint32_t d, uint32_t k, int precision) {
   b += a256(4 * 4);                    // nflag[2], maxabs, cmax
   b += a256((uint64_t)k * 4 * 2);      // cnorm (||c||^2) + spare
   b += a256(16);                       // shift
-  if (precision == MR_KM_BF16_TC) {
+  if (precision != MR_KM_FP32) {
     b += a256((uint64_t)n * 4);        // second flag list
     b += a256((uint64_t)k * d * 2 * 2);  // bf16 centroids (hi, lo)
   }
@@ -383,7 +383,7 @@ cudaError_t km_carve(KmBuffers& b, uint8_t* p, size_t bytes) {
   int* shift = reinterpret_cast<int*>(take(16));
   b.fx_shift = 0;
   b.xnorm = reinterpret_cast<float*>(shift);  // holds the device-side shift
-  if (b.precision == MR_KM_BF16_TC) {
+  if (b.precision != MR_KM_FP32) {
     b.cent_bf16_norm = reinterpret_cast<float*>(take(n * 4));  // second flag list
     b.cb = reinterpret_cast<uint16_t*>(take(k * d * 4));
   }
@@ -423,7 +423,7 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
   const uint32_t agrid = ntiles < (uint32_t)di.sms * 2 ? ntiles : (uint32_t)di.sms * 2;
   for (uint32_t it = 0; it < iters; ++it) {
     km_prep_kernel<<<64, 256, 0, s>>>(b.cent, k, d, b.cnorm, cmax_bits, b.sums, b.counts, b.nflag);
-    if (b.precision == MR_KM_BF16_TC) {
+    if (b.precision != MR_KM_FP32) {
       if ((e = launch_kmeans_tc_assign(x, n, d, b.cent, k, b, di, s, nk)) != cudaSuccess) return e;
     } else {
       km_assign_fp32_kernel<<<agrid, KM_THREADS, asm_bytes, s>>>(x, n, d, b.cent, k, b.cnorm, cmax_bits, nullptr,

@@ -171,8 +171,8 @@ mr_status validate(const mr_ctx* c, const mr_job_desc* d) {
       if (d->input_bytes % row) return MR_EINVAL;
       const uint64_t n = d->input_bytes / row;
       if (n == 0 || n > 0x7fffffffull) return MR_EINVAL;
-      if (d->km_precision > MR_KM_BF16_TC) return MR_EINVAL;
-      if (d->km_precision == MR_KM_BF16_TC && !km_tc_supported(d->km_dims, d->km_k)) return MR_EINVAL;
+      if (d->km_precision > MR_KM_BF16X1_TC) return MR_EINVAL;
+      if (d->km_precision != MR_KM_FP32 && !km_tc_supported(d->km_dims, d->km_k)) return MR_EINVAL;
       break;
     }
   }
@@ -414,6 +414,14 @@ Job* find_job(mr_ctx* c, uint64_t id) {
 mr_status wait_job(mr_ctx* c, Job* j) {
   if (j->state == JOB_PENDING) return MR_ENOTREADY;
   MR_CUDA_TRY(cudaEventSynchronize(j->done));
+  if (j->desc.kind == MR_KMEANS_F32) {
+    // stats[3] counts device waits that gave up (bounded mbarrier waits)
+    unsigned long long to = 0;
+    const uint64_t so = km_stats_offset(j->km.k, j->km.d, j->km.n) + 24;
+    MR_CUDA_TRY(cudaMemcpyAsync(&to, static_cast<uint8_t*>(j->result) + so, 8, cudaMemcpyDeviceToHost, c->stream));
+    MR_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return to ? MR_ETIMEOUT : MR_OK;
+  }
   if (j->desc.kind != MR_WORDCOUNT) return MR_OK;
   for (;;) {
     uint32_t st[4];

@@ -121,3 +121,48 @@ def test_kmeans_full_size_fp32(mr):
     assert np.array_equal(a10[sample], oracle.kmeans_assign(x[sample], c9))
     c_upd, _ = oracle.kmeans_update(x, a10, c9)
     assert _rel_err(c10, c_upd) <= TOL
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("n,d,k,iters", [
+    (20_000, 64, 256, 3),   # the workload's shape, reduced N
+    (5_001, 37, 50, 2),     # D < 64 (zero-padded), K not a multiple of 16
+    (777, 3, 1, 2),         # K = 1
+    (300, 64, 16, 1),       # fewer points than one CTA per SM
+])
+def test_kmeans_bf16_tensor_core_vs_oracle(mr, precision, n, d, k, iters):
+    x, _, _ = synth.kmeans_points(n, d, max(1, min(k, 256)), seed=n + d + k + 7)
+    init = synth.kmeans_init(x, k, seed=n + 1)
+    c_ref, a_ref = oracle.kmeans(x, init, iters)
+    c, a, stats = _run(mr, x, init, iters, precision=precision)
+    assert np.array_equal(a, a_ref)
+    assert _rel_err(c, c_ref) <= TOL
+    assert int(stats[3]) == 0
+
+
+def test_kmeans_bf16_teacher_forced(mr):
+    x, _, _ = synth.kmeans_points(30_000, 64, 256, seed=43)
+    cur = synth.kmeans_init(x, 256, seed=44)
+    for _ in range(3):
+        a_ref = oracle.kmeans_assign(x, cur)
+        c_ref, _ = oracle.kmeans_update(x, a_ref, cur)
+        c, a, stats = _run(mr, x, cur, 1, precision=1)
+        assert np.array_equal(a, a_ref)
+        assert _rel_err(c, c_ref) <= TOL
+        cur = c_ref
+
+
+@pytest.mark.slow
+def test_kmeans_full_size_bf16_matches_fp32_path(mr):
+    """4M x 64, K = 256, 10 iterations: the tensor-core path gives the same
+    assignments and centroids as the FP32 path (both equal the FP64 argmin
+    each iteration, and the integer sums make the update deterministic)."""
+    import torch
+    x, _, _ = synth.kmeans_points(4 << 20, 64, 256)
+    init = synth.kmeans_init(x, 256)
+    dx = torch.from_numpy(x).cuda()
+    c32, a32, _ = mr.kmeans(dx, _dev(init), 10, 0)
+    c16, a16, st = mr.kmeans(dx, _dev(init), 10, 1)
+    assert np.array_equal(a16, a32)
+    assert np.array_equal(c16, c32)
+    assert int(st[3]) == 0
