@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "input GB/s per job (% of HBM peak); batched jobs/s and p99 latency vs plain"
 HIST_PIXELS = 512 << 20      # 1,610,612,736 bytes
+KM_ITERS = 10
 LR_PAIRS = 256 << 20         # 536,870,912 bytes
 
 
@@ -142,6 +143,11 @@ def make_inputs(workload: str, scale: float, rank: int):
         n = max(1024, int((16 << 20) * scale))
         text, _, _ = synth.wc_text(n, seed=synth.SEED_BASE + 1000 * rank)
         return {"text": text}
+    if workload == "kmeans":
+        n = max(1024, int((4 << 20) * scale))
+        x, _, _ = synth.kmeans_points(n, 64, 256, seed=synth.SEED_BASE + 3 + 1000 * rank)
+        init = synth.kmeans_init(x, 256, seed=synth.SEED_BASE + 4 + 1000 * rank)
+        return {"x": x, "init": init}
     raise ValueError(workload)
 
 
@@ -151,6 +157,11 @@ def workload_config(workload: str, inp) -> dict:
             inp["px"].nbytes, inp["px"].nbytes // 3, inp["xy"].nbytes, inp["xy"].nbytes // 2),
             "inputs": "synthetic, resident in HBM, larger than L2 (no flush needed)",
             "containers": "histogram: shared-memory local arrays; regression: register accumulators"}
+    if workload == "kmeans":
+        n, d = inp["x"].shape
+        return {"workload": "k-means %d x %d FP32 points (%d B), K=%d, %d iterations" % (
+            n, d, inp["x"].nbytes, inp["init"].shape[0], KM_ITERS),
+            "inputs": "synthetic 256-component Gaussian mixture, resident in HBM, larger than L2"}
     return {"workload": "word count %d B Zipf(1) text, 50,000-word vocabulary" % inp["text"].nbytes,
             "inputs": "synthetic, resident in HBM; 16 MiB fits in L2 (warm)"}
 
@@ -188,6 +199,19 @@ def run_ours(args):
             ctx.run()
             return [a, b]
         dominant = ("hist_smem_kernel", "paper_1309_0215_gb300/csrc/k_array.cu", d_px.numel())
+    elif args.workload == "kmeans":
+        d_x, d_i = dinp["x"], dinp["init"]
+        total_bytes = d_x.numel() * 4
+        nn, dd = d_x.shape
+        kk = d_i.shape[0]
+
+        def step():
+            a = ctx.add_job(mr.KMEANS_F32, d_x, km_dims=dd, km_k=kk, km_iters=KM_ITERS, km_init=d_i,
+                            km_precision=args.precision)
+            ctx.run()
+            return [a]
+        kname = "km_tc_assign_kernel" if args.precision else "km_assign_fp32_kernel"
+        dominant = (kname, "paper_1309_0215_gb300/csrc/k_kmeans_tc.cu", d_x.numel() * 4)
     else:
         d_t = dinp["text"]
         total_bytes = d_t.numel()
@@ -234,8 +258,18 @@ def run_ours(args):
     value = total_bytes * ws * args.steps / (ms_max / 1e3) / 1e9
 
     # end to end through the public API: pinned host inputs, H2D + run + D2H every step
+    km_stats = None
+    if args.workload == "kmeans":
+        js = step()
+        ctx.sync()
+        raw = ctx.fetch(js[0])
+        _, _, st = mr.split_kmeans_result(raw, nn, dd, kk)
+        km_stats = {"fp32_rechecks": int(st[0]), "fp64_rechecks": int(st[1]), "iterations": int(st[2]),
+                    "timeouts": int(st[3]), "ms_per_iteration": round(dom_ms / KM_ITERS, 4),
+                    "distance_tflops": round(2.0 * nn * kk * dd * KM_ITERS / (dom_ms / 1e3) / 1e12, 2)}
+        ctx.release(js[0])
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and args.workload != "kmeans":
         pinned = {k: torch.from_numpy(v).pin_memory() for k, v in inp.items()}
         kinds = {"px": mr.HIST_RGB8, "xy": mr.LINREG_I8, "text": mr.WORDCOUNT}
         out_bytes = {}
@@ -260,7 +294,7 @@ def run_ours(args):
                "steps": n_e2e}
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and args.workload != "kmeans":
         cpu = cpu_baseline(args.workload, inp)
 
     ctx.close()
@@ -280,10 +314,231 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": int(kbytes)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
         }
+        if km_stats:
+            line["kmeans"] = km_stats
+            line["roofline"]["note"] = "achieved = one read of the points per job time (10 iterations)"
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def batched_specs(njobs: int, seed: int):
+    """4,096-job mix: 50% word count, 30% RGB histogram, 20% regression; sizes
+    log-uniform on [4 KiB, 64 MiB], rounded down to the kind's record size."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(4096), np.log(64 << 20), njobs)).astype(np.int64)
+    kinds = rng.choice(3, size=njobs, p=[0.5, 0.3, 0.2])
+    offs = rng.random(njobs)
+    out = []
+    for k, n, o in zip(kinds, sizes, offs):
+        n = int(n) - (int(n) % (1, 3, 2)[k])
+        out.append((int(k), n, float(o)))
+    return out
+
+
+def run_batched(args):
+    """Batched jobs/s: one persistent launch (graph replay) vs the plain path."""
+    import numpy as np
+    import torch
+    import oracle
+    import synth
+    import paper_1309_0215_gb300 as mr
+    torch.cuda.set_device(0)
+    mr.load()
+    njobs = max(8, int(4096 * args.scale))
+    specs = batched_specs(njobs, synth.SEED_BASE + 7)
+    pool_text, _, _ = synth.wc_text(256 << 20, seed=synth.SEED_BASE)
+    pool_px = synth.hist_rgb8(64 << 20, seed=synth.SEED_BASE + 1)
+    pool_xy = synth.linreg_i8(64 << 20, seed=synth.SEED_BASE + 2)
+    pools_h = [pool_text, pool_px, pool_xy]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        pools = [torch.from_numpy(p).cuda() for p in pools_h]
+    stream.synchronize()
+    kinds = [mr.WORDCOUNT, mr.HIST_RGB8, mr.LINREG_I8]
+    rec = (1, 3, 2)
+
+    def slice_of(k, n, o):
+        cap = pools[k].numel() - n
+        off = int(o * cap) // rec[k] * rec[k]
+        return off, pools[k][off: off + n]
+    total_bytes = sum(n for _, n, _ in specs)
+    ctx = mr.Context(0, stream=stream, autotune=True)
+    ids = [ctx.add_job(kinds[k], slice_of(k, n, o)[1]) for k, n, o in specs]
+    t0 = time.perf_counter()
+    ctx.run(mr.RUN_BATCHED)
+    ctx.sync()
+    t_first = time.perf_counter() - t0
+    # spot-check 24 small jobs against the oracle
+    small = [i for i, (k, n, o) in enumerate(specs) if n < (1 << 20)][:24]
+    for i in small:
+        k, n, o = specs[i]
+        off, _ = slice_of(k, n, o)
+        data = pools_h[k][off: off + n]
+        exp = (oracle.wordcount(data) if k == 0 else
+               oracle.hist_rgb8(data).tobytes() if k == 1 else oracle.linreg_i8(data).tobytes())
+        assert ctx.fetch(ids[i]) == exp, "batched job %d differs from the oracle" % i
+    for _ in range(args.warmup):
+        ctx.rerun()
+    ctx.sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = ctx.kernel_launches
+    ev0.record(stream)
+    for _ in range(args.steps):
+        ctx.rerun()
+    ev1.record(stream)
+    ev1.synchronize()
+    launches = ctx.kernel_launches - l0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    # plain path: one launch sequence per job, same jobs
+    ids2 = [ctx.add_job(kinds[k], slice_of(k, n, o)[1]) for k, n, o in specs]
+    ctx.sync()
+    ev0.record(stream)
+    w0 = time.perf_counter()
+    ctx.run(mr.RUN_PLAIN)
+    ev1.record(stream)
+    ev1.synchronize()
+    plain_wall = time.perf_counter() - w0
+    plain_ms = ev0.elapsed_time(ev1)
+    for i in small[:8]:
+        assert ctx.fetch(ids2[i]) == ctx.fetch(ids[i])
+    tune = ctx.tuning()
+    ctx.close()
+    hbm_peak, _, _, peak_src = _peaks()
+    print(json.dumps({
+        "metric": METRIC, "value": round(njobs / (ms / 1e3), 1), "unit": "jobs/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8/i8 in, u64/i64 exact counts",
+        "data": "synthetic (seeded generators); job inputs are slices of device-resident pools",
+        "config": {"workload": "%d jobs (50%% word count, 30%% RGB histogram, 20%% int8 regression), sizes "
+                               "log-uniform 4 KiB-64 MiB, %d bytes in total" % (njobs, total_bytes),
+                   "mode": "one persistent launch + one word-count merge/sort, replayed from a CUDA graph"},
+        "aggregate_gbs": round(total_bytes / (ms / 1e3) / 1e9, 2),
+        "pct_of_hbm_peak": round(100 * total_bytes / (ms / 1e3) / 1e9 / hbm_peak, 2),
+        "plain": {"ms_device": round(plain_ms, 3), "ms_wall": round(1e3 * plain_wall, 3),
+                  "jobs_per_s": round(njobs / (max(plain_ms, 1e3 * plain_wall) / 1e3), 1)},
+        "speedup_vs_plain": round(max(plain_ms, 1e3 * plain_wall) / ms, 2),
+        "first_run_s_incl_autotune": round(t_first, 3), "tuning": tune, "gpu_launches": int(launches),
+    }), flush=True)
+
+
+def serving_specs(rate: float, duration: float, seed: int):
+    """Poisson arrivals; 25% each of word count, RGB histogram, int8 regression
+    and k-means; sizes log-uniform on [1 KiB, 256 MiB] (k-means: D in [8, 64],
+    K in [16, 256], N in [64K, 2M] clamped to 256 MiB of points, 10 iterations)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    n = int(rate * duration * 1.2) + 16
+    t = np.cumsum(rng.exponential(1.0 / rate, n))
+    t = t[t < duration]
+    out = []
+    for a in t:
+        kind = int(rng.integers(0, 4))
+        if kind < 3:
+            size = int(np.exp(rng.uniform(np.log(1024), np.log(256 << 20))))
+            size -= size % (1, 3, 2)[kind]
+            out.append((float(a), kind, (size, float(rng.random()))))
+        else:
+            d = int(rng.integers(8, 65))
+            k = int(rng.integers(16, 257))
+            npts = int(np.exp(rng.uniform(np.log(64 << 10), np.log(2 << 20))))
+            npts = min(npts, (256 << 20) // (4 * d))
+            out.append((float(a), 3, (npts, d, k, int(rng.integers(0, 2)))))
+    return out
+
+
+def run_serving(args):
+    """Poisson request stream served with continuous batching (mr_submit /
+    mr_poll) against an HBM budget, vs a plain server that launches each
+    request on arrival; latency = arrival to result in host memory."""
+    import collections
+    import numpy as np
+    import torch
+    import synth
+    import paper_1309_0215_gb300 as mr
+    torch.cuda.set_device(0)
+    mr.load()
+    specs = serving_specs(args.rate, args.duration, synth.SEED_BASE + 9)
+    pool_text, _, _ = synth.wc_text(256 << 20, seed=synth.SEED_BASE)
+    pools_h = [pool_text, synth.hist_rgb8((256 << 20) // 3, seed=synth.SEED_BASE + 1),
+               synth.linreg_i8(128 << 20, seed=synth.SEED_BASE + 2)]
+    kx, _, _ = synth.kmeans_points(2 << 20, 64, 256, seed=synth.SEED_BASE + 3)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        pools = [torch.from_numpy(p).cuda() for p in pools_h]
+        kpool = torch.from_numpy(kx.reshape(-1)).cuda()
+    stream.synchronize()
+    kinds = [mr.WORDCOUNT, mr.HIST_RGB8, mr.LINREG_I8]
+
+    def submit(ctx, spec, plain):
+        kind, p = spec[1], spec[2]
+        if kind < 3:
+            size, o = p
+            pool = pools[kind]
+            size = min(size, pool.numel())
+            rec = (1, 3, 2)[kind]
+            off = int(o * (pool.numel() - size)) // rec * rec
+            t, args_ = pool[off: off + size], {}
+            mk = kinds[kind]
+        else:
+            npts, d, k, prec = p
+            t = kpool[: npts * d].view(npts, d)
+            args_ = dict(km_dims=d, km_k=k, km_iters=10, km_init=t[:k].contiguous(), km_precision=prec)
+            mk = mr.KMEANS_F32
+        if plain:
+            j = ctx.add_job(mk, t, **args_)
+            ctx.run(mr.RUN_PLAIN)
+            return j, t.numel() * t.element_size()
+        return ctx.submit(mk, t, **args_), t.numel() * t.element_size()
+
+    def serve(plain):
+        ctx = mr.Context(0, stream=stream, hbm_budget=120 << 30)
+        waiting = collections.deque()
+        inflight = {}
+        lat, nbytes = [], 0
+        nxt = 0
+        t0 = time.perf_counter()
+        while nxt < len(specs) or waiting or inflight:
+            now = time.perf_counter() - t0
+            while nxt < len(specs) and specs[nxt][0] <= now:
+                waiting.append(specs[nxt])
+                nxt += 1
+            while waiting:
+                try:
+                    j, b = submit(ctx, waiting[0], plain)
+                except mr.MRError as e:
+                    if e.status != mr.MR_EBUDGET:
+                        raise
+                    break
+                inflight[j] = (waiting.popleft()[0], b)
+            for j in list(inflight):
+                if ctx.poll(j):
+                    ctx.fetch(j)
+                    arr, b = inflight.pop(j)
+                    lat.append(time.perf_counter() - t0 - arr)
+                    nbytes += b
+                    ctx.release(j)
+        wall = time.perf_counter() - t0
+        ctx.close()
+        lat = np.array(lat) * 1e3
+        return {"requests": len(lat), "wall_s": round(wall, 3), "req_per_s": round(len(lat) / wall, 1),
+                "gbs": round(nbytes / wall / 1e9, 3), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                "p99_ms": round(float(np.percentile(lat, 99)), 3), "max_ms": round(float(lat.max()), 3)}
+
+    served = serve(False)
+    plain = serve(True)
+    print(json.dumps({
+        "metric": METRIC, "value": served["p99_ms"], "unit": "ms (p99 latency)", "n_gpus": 1,
+        "steps": 1, "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u8/i8/f32 in, exact counts; k-means FP32/BF16 paths",
+        "data": "synthetic; request inputs are slices of device-resident pools",
+        "config": {"workload": "Poisson %.0f req/s for %.1f s, 25%% each word count / histogram / regression / "
+                               "k-means, sizes log-uniform 1 KiB-256 MiB, 120 GiB HBM budget" % (args.rate, args.duration)},
+        "served_continuous_batching": served, "plain_one_launch_per_request": plain,
+        "p99_speedup_vs_plain": round(plain["p99_ms"] / served["p99_ms"], 2) if served["p99_ms"] else None,
+    }), flush=True)
 
 
 def cpu_baseline(workload, inp, max_seconds=30.0):
@@ -369,7 +624,10 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["arrays", "wordcount"], default="arrays")
+    ap.add_argument("--workload", choices=["arrays", "wordcount", "kmeans", "batched", "serving"], default="arrays")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean requests per second")
+    ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
+    ap.add_argument("--precision", type=int, default=1, help="k-means: 0 FP32, 1 BF16 split, 2 BF16 single")
     ap.add_argument("--scale", type=float, default=1.0, help="input size relative to the full workload")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -378,6 +636,10 @@ def main():
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -113,6 +113,19 @@ typedef struct {
 /* mr_config.flags: record CUDA timing events around each job's kernels so
  * that mr_job_elapsed_ms can report the job's device time. */
 #define MR_FLAG_TIMING 1u
+/* mr_config.flags: on the first batched mr_run of a context, time candidate
+ * tile sizes and histogram container thresholds on the pending batch itself
+ * and keep the fastest (see mr_get_tuning). */
+#define MR_FLAG_AUTOTUNE 2u
+
+/* Batched-launch parameters chosen by the autotuner (or the defaults). */
+typedef struct {
+  uint64_t arr_tile;           /* bytes per tile of histogram / regression jobs (multiple of 1536) */
+  uint64_t wc_tile;            /* bytes per tile of word-count jobs (multiple of 512) */
+  uint64_t hist_global_below;  /* histogram jobs smaller than this use global atomics (no local arrays) */
+  float best_ms;               /* device time of the batch with these values (0 if not tuned) */
+  uint32_t tuned;              /* 1 once the autotuner has run */
+} mr_tuning;
 
 typedef struct {
   uint32_t struct_size;   /* sizeof(mr_job_desc) */
@@ -147,8 +160,9 @@ mr_status mr_add_job(mr_ctx* ctx, const mr_job_desc* desc, uint64_t* job_id);
 
 /* Enqueue every pending job on the context stream.  PLAIN launches each job's
  * kernels in order; BATCHED runs all pending word-count / histogram /
- * regression jobs in one persistent kernel (k-means jobs always run plain).
- * Returns when the work is enqueued. */
+ * regression jobs in one persistent kernel, followed by one merge + sort for
+ * all word-count jobs, captured as one CUDA graph (k-means jobs always run
+ * plain).  Returns when the work is enqueued (an autotuning run waits). */
 mr_status mr_run(mr_ctx* ctx, mr_mode mode);
 
 /* Copy a finished job's result into host memory buf (buf_bytes long).
@@ -162,12 +176,29 @@ mr_status mr_fetch(mr_ctx* ctx, uint64_t job_id, void* buf, uint64_t buf_bytes, 
  * mr_release).  Blocks until the job is done (same rules as mr_fetch). */
 mr_status mr_result_device(mr_ctx* ctx, uint64_t job_id, const void** dptr, uint64_t* bytes);
 
+/* Re-run, in place, the jobs of the last batched mr_run (same inputs;
+ * results are recomputed and overwritten) by relaunching the CUDA graph
+ * captured for that batch (captured again first if a job's hash table was
+ * regrown since).  Errors: MR_ENOJOB if one of those jobs was released,
+ * MR_EINVAL if there was no batched run. */
+mr_status mr_rerun(mr_ctx* ctx);
+
+/* Current batched-launch parameters of the context. */
+mr_status mr_get_tuning(const mr_ctx* ctx, mr_tuning* out);
+
 /* Free a job's containers and result.  Waits for the job if it is running. */
 mr_status mr_release(mr_ctx* ctx, uint64_t job_id);
 
-/* Serving: admit a job if the context's HBM budget allows (MR_EBUDGET
- * otherwise, nothing queued), and enqueue it at once on the context stream.
- * Completion is observed with mr_poll. */
+/* Serving: admit a request if the context's HBM budget allows (MR_EBUDGET
+ * otherwise; nothing is queued and the caller retries once results have been
+ * released).  Admitted requests are batched continuously: whenever one of the
+ * context's internal streams has finished its previous micro-batch, every
+ * admitted request that is not running yet is launched on it as one
+ * persistent batch (plus one merge + sort for its word-count requests;
+ * k-means requests follow on the same stream).  Requests that arrive while
+ * others run are therefore picked up as soon as a stream frees, and
+ * micro-batches overlap on the device.  mr_poll and mr_fetch also drive this
+ * launching.  Containers stay resident until mr_release. */
 mr_status mr_submit(mr_ctx* ctx, const mr_job_desc* desc, uint64_t* job_id);
 
 /* MR_OK when the job has finished, MR_ENOTREADY while it runs. */

@@ -28,9 +28,10 @@ KM_FP32, KM_BF16_TC, KM_BF16X1_TC = range(3)
 # every entry point declared in include/mr.h
 EXPORTS = ("mr_create", "mr_destroy", "mr_add_job", "mr_run", "mr_fetch", "mr_result_device", "mr_release",
            "mr_submit", "mr_poll", "mr_sync", "mr_bytes_in_use", "mr_job_elapsed_ms", "mr_kernel_launches",
-           "mr_status_str", "mr_last_error", "mr_wordcount_noalloc")
+           "mr_status_str", "mr_last_error", "mr_wordcount_noalloc", "mr_rerun", "mr_get_tuning")
 NOALLOC_WC_SLOTS = 131072
 FLAG_TIMING = 1
+FLAG_AUTOTUNE = 2
 
 
 class MRError(RuntimeError):
@@ -47,6 +48,11 @@ class _Config(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
                 ("hbm_budget", ctypes.c_uint64), ("alloc", _ALLOC_FN), ("free", _FREE_FN),
                 ("alloc_user", ctypes.c_void_p), ("flags", ctypes.c_uint32)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("arr_tile", ctypes.c_uint64), ("wc_tile", ctypes.c_uint64), ("hist_global_below", ctypes.c_uint64),
+                ("best_ms", ctypes.c_float), ("tuned", ctypes.c_uint32)]
 
 
 class _JobDesc(ctypes.Structure):
@@ -104,6 +110,10 @@ def load():
         lib.mr_job_elapsed_ms.restype = st
         lib.mr_kernel_launches.argtypes = [vp]
         lib.mr_kernel_launches.restype = u64
+        lib.mr_rerun.argtypes = [vp]
+        lib.mr_rerun.restype = st
+        lib.mr_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+        lib.mr_get_tuning.restype = st
         lib.mr_wordcount_noalloc.argtypes = [vp, u64, vp, u64, ctypes.POINTER(u64), vp]
         lib.mr_wordcount_noalloc.restype = st
         lib.mr_status_str.argtypes = [ctypes.c_int]
@@ -150,7 +160,7 @@ class Context:
     """One library context: a device, a stream and the jobs queued on it."""
 
     def __init__(self, device: Optional[int] = None, stream=None, hbm_budget: int = 0,
-                 use_torch_allocator: bool = True, timing: bool = False):
+                 use_torch_allocator: bool = True, timing: bool = False, autotune: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the map/reduce library runs only on the GPU")
@@ -164,7 +174,7 @@ class Context:
         cfg.device = self.device
         cfg.cuda_stream = ctypes.c_void_p(stream.cuda_stream)
         cfg.hbm_budget = int(hbm_budget)
-        cfg.flags = FLAG_TIMING if timing else 0
+        cfg.flags = (FLAG_TIMING if timing else 0) | (FLAG_AUTOTUNE if autotune else 0)
         self._cb = None
         if use_torch_allocator:
             dev, sptr = self.device, stream.cuda_stream
@@ -256,6 +266,16 @@ class Context:
 
     def sync(self):
         _check(self._lib.mr_sync(self._h), "mr_sync")
+
+    def rerun(self):
+        """Re-run the last batched mr_run in place (relaunches its CUDA graph)."""
+        _check(self._lib.mr_rerun(self._h), "mr_rerun")
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        _check(self._lib.mr_get_tuning(self._h, ctypes.byref(t)), "mr_get_tuning")
+        return {"arr_tile": t.arr_tile, "wc_tile": t.wc_tile, "hist_global_below": t.hist_global_below,
+                "best_ms": t.best_ms, "tuned": bool(t.tuned)}
 
     def elapsed_ms(self, job: int) -> float:
         ms = ctypes.c_float()

@@ -1,0 +1,306 @@
+// Device code of the word-count map + combine pass, shared by the plain
+// kernel (k_wordcount.cu) and the persistent batched kernel (k_batch.cu).
+//
+// Map (arXiv:1309.0215 Sec. II-A): a token is a maximal run of bytes that are
+// not ASCII whitespace; each emits (token, 1); reduce is a sum.
+//
+// Key encoding (128 bits, the container's key):
+//   short token, 1..15 bytes:  w0 = bytes 0..7 (little-endian, zero padded)
+//                              w1 = bytes 8..14 | length << 56
+//   long token, >= 16 bytes:   w0 = offset of an occurrence in the input + 1
+//                              w1 = 0xFF << 56 | length
+// A short key is its own identity (no memory read to compare); a long key
+// is compared byte for byte against the resident, immutable input.  w1 is
+// never zero, so {0, 0} marks an empty slot.
+//
+// Global container: open addressing, linear probing, a slot = 16-byte key
+// claimed with one 128-bit atomic CAS (written once, never changed) plus a
+// 64-bit count updated with atomicAdd.  Running out of probes raises the
+// job's overflow flag (the host then re-runs with a larger table).
+//
+// Local container (the paper's combiner, Sec. III-A, with the bounded local
+// table of Sec. III-D): every warp owns a 256-slot table in shared memory;
+// tokens are combined into it warp-synchronously, and it is flushed into the
+// global container when half full and at the end.
+#pragma once
+#include <cstdint>
+
+namespace mrgb {
+namespace wc {
+
+constexpr int SEG = 512;                // bytes per warp step (16 per lane)
+constexpr int HALO = 64;                // staged bytes after the segment
+constexpr int BUF = SEG + HALO;
+constexpr int LT = 256;                 // local slots per warp
+constexpr int LT_FLUSH_AT = LT / 2;
+constexpr int MAX_PROBES = 4096;
+constexpr uint64_t LONG_TAG = 0xFFull << 56;
+constexpr uint64_t LEN_MASK = (1ull << 56) - 1;
+
+struct WarpLocal {
+  unsigned long long w0[LT];
+  unsigned long long w1[LT];
+  uint32_t h[LT];
+  uint32_t cnt[LT];
+  uint8_t buf[BUF];
+  uint16_t starts[SEG / 2];
+};
+static_assert(sizeof(WarpLocal) % 16 == 0, "WarpLocal must keep 16-byte alignment");
+
+// One word-count job as the kernels see it.
+struct JobDev {
+  const uint8_t* in;
+  uint64_t n;
+  unsigned long long* key;   // [cap][2]
+  unsigned long long* cnt;   // [cap]
+  uint64_t cap;              // power of two
+  uint32_t log2cap;
+  uint32_t* state;           // [0] overflow flag; [2..7] filled by the post phase
+  uint8_t* out;
+  uint64_t blk0;             // first compaction block of this job
+};
+
+__device__ __forceinline__ bool is_ws(uint32_t c) { return c == 32u || (c - 9u) < 5u; }
+
+// 0xFF in every byte of u that is ASCII whitespace
+__device__ __forceinline__ uint32_t ws_bytes(uint32_t u) {
+  return __vcmpeq4(u, 0x20202020u) | __vcmpltu4(__vsub4(u, 0x09090909u), 0x05050505u);
+}
+// compress a 0xFF-per-byte mask to 4 bits (byte i -> bit i)
+__device__ __forceinline__ uint32_t byte_bits(uint32_t m) { return ((m & 0x80808080u) * 0x00204081u) >> 28; }
+
+__device__ __forceinline__ uint64_t fmix64(uint64_t k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+__device__ __forceinline__ uint32_t hash_short(uint64_t w0, uint64_t w1) {
+  uint64_t h = w0 * 0x9E3779B97F4A7C15ull ^ ((w1 * 0xC2B2AE3D27D4EB4Full) >> 7) ^ w1;
+  h ^= h >> 29;
+  h *= 0xBF58476D1CE4E5B9ull;
+  h ^= h >> 32;
+  return (uint32_t)h;
+}
+
+struct Tok {
+  uint64_t w0, w1;
+  uint32_t h;
+};
+
+// Bytes of two long tokens of equal length len, at offsets a and b.
+__device__ inline bool long_equal(const uint8_t* __restrict__ in, uint64_t a, uint64_t b, uint64_t len) {
+  if (a == b) return true;
+  for (uint64_t i = 0; i < len; ++i)
+    if (in[a + i] != in[b + i]) return false;
+  return true;
+}
+
+// The token starting at segment-relative byte r (its first 16 bytes are
+// always inside the staged buffer; bytes past the input end were staged as
+// spaces).
+__device__ __forceinline__ Tok read_token(const uint8_t* __restrict__ in, uint64_t n, uint64_t base,
+                                          const uint8_t* buf, uint32_t r) {
+  const uint32_t* wb = reinterpret_cast<const uint32_t*>(buf);
+  const uint32_t a = r >> 2, sh = (r & 3) * 8;
+  const uint32_t x0 = wb[a], x1 = wb[a + 1], x2 = wb[a + 2], x3 = wb[a + 3], x4 = wb[a + 4];
+  const uint32_t u0 = __funnelshift_r(x0, x1, sh), u1 = __funnelshift_r(x1, x2, sh);
+  const uint32_t u2 = __funnelshift_r(x2, x3, sh), u3 = __funnelshift_r(x3, x4, sh);
+  const uint32_t m = byte_bits(ws_bytes(u0)) | (byte_bits(ws_bytes(u1)) << 4) | (byte_bits(ws_bytes(u2)) << 8) |
+                     (byte_bits(ws_bytes(u3)) << 12);
+  Tok t;
+  if (m) {
+    const uint32_t L = __ffs(m) - 1;  // 1..15 (byte 0 is a token byte)
+    uint64_t k0 = (uint64_t)u0 | ((uint64_t)u1 << 32);
+    uint64_t k1 = (uint64_t)u2 | ((uint64_t)u3 << 32);
+    if (L < 8) {
+      k0 &= (1ull << (8 * L)) - 1;
+      k1 = 0;
+    } else {
+      k1 &= (1ull << (8 * (L - 8))) - 1;
+    }
+    t.w0 = k0;
+    t.w1 = k1 | ((uint64_t)L << 56);
+    t.h = hash_short(t.w0, t.w1);
+    return t;
+  }
+  // long token: FNV-1a 64 over its bytes, then the length is mixed in
+  const uint64_t off = base + r;
+  uint64_t h = 0xcbf29ce484222325ull, len = 0;
+  for (uint64_t i = off; i < n; ++i) {
+    const uint32_t rel = (uint32_t)(i - base);
+    const uint32_t c = (i - base) < (uint64_t)BUF ? buf[rel] : in[i];
+    if (is_ws(c)) break;
+    h = (h ^ c) * 0x100000001b3ull;
+    ++len;
+  }
+  t.w0 = off + 1;
+  t.w1 = LONG_TAG | (len & LEN_MASK);
+  t.h = (uint32_t)fmix64(h ^ len);
+  return t;
+}
+
+__device__ __forceinline__ void ld_slot(const unsigned long long* p, uint64_t& a, uint64_t& b) {
+  asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
+
+__device__ __forceinline__ void cas_slot(unsigned long long* p, uint64_t n0, uint64_t n1, uint64_t& o0, uint64_t& o1) {
+  asm volatile(
+      "{\n\t.reg .b128 d, c, v;\n\t"
+      "mov.b128 c, {%2, %2};\n\t"
+      "mov.b128 v, {%3, %4};\n\t"
+      "atom.relaxed.gpu.global.cas.b128 d, [%5], c, v;\n\t"
+      "mov.b128 {%0, %1}, d;\n\t}\n"
+      : "=l"(o0), "=l"(o1)
+      : "l"(0ull), "l"(n0), "l"(n1), "l"(p)
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_slot(uint32_t h, uint32_t log2cap) {
+  return log2cap ? (uint64_t)((h * 0x9E3779B1u) >> (32 - log2cap)) : 0;
+}
+
+// Combine (key, c) into the job's global container.
+__device__ inline void global_insert(const JobDev& J, uint64_t w0, uint64_t w1, uint32_t h, uint64_t c) {
+  uint64_t slot = global_slot(h, J.log2cap);
+  const bool is_long = (w1 >> 56) == 0xFF;
+  for (int p = 0; p < MAX_PROBES; ++p) {
+    unsigned long long* sp = J.key + 2 * slot;
+    uint64_t r0, r1;
+    ld_slot(sp, r0, r1);
+    if (r0 == 0 || r1 == 0) {  // empty, or a read that raced the CAS: ask the CAS
+      cas_slot(sp, w0, w1, r0, r1);
+      if (r0 == 0 && r1 == 0) {
+        atomicAdd(J.cnt + slot, (unsigned long long)c);
+        return;
+      }
+    }
+    if (r1 == w1 && (r0 == w0 || (is_long && long_equal(J.in, r0 - 1, w0 - 1, w1 & LEN_MASK)))) {
+      atomicAdd(J.cnt + slot, (unsigned long long)c);
+      return;
+    }
+    slot = (slot + 1) & (J.cap - 1);
+  }
+  atomicOr(J.state, 1u);
+}
+
+__device__ __forceinline__ bool local_equal(const WarpLocal& L, int s, const Tok& t, const uint8_t* __restrict__ in) {
+  if (L.w1[s] != t.w1) return false;
+  if (L.w0[s] == t.w0) return true;
+  return (t.w1 >> 56) == 0xFF && L.h[s] == t.h && long_equal(in, L.w0[s] - 1, t.w0 - 1, t.w1 & LEN_MASK);
+}
+
+// Warp-synchronous combine of one token per active lane into the warp's
+// local table; occ (warp-uniform) counts occupied slots.
+__device__ __forceinline__ void local_insert(WarpLocal& L, bool active, const Tok& t, int& occ,
+                                             const uint8_t* __restrict__ in) {
+  const int lane = threadIdx.x & 31;
+  int s = (int)(t.h & (LT - 1));
+  bool pending = active;
+  while (__any_sync(0xffffffffu, pending)) {
+    bool empty = false, match = false;
+    if (pending) {
+      if (L.w1[s] == 0) empty = true;
+      else match = local_equal(L, s, t, in);
+    }
+    if (match) {
+      atomicAdd(&L.cnt[s], 1u);
+      pending = false;
+    }
+    const unsigned em = __ballot_sync(0xffffffffu, empty);
+    bool claimed = false;
+    if (empty) {
+      const unsigned grp = __match_any_sync(em, s);  // lanes that found the same empty slot
+      claimed = lane == __ffs(grp) - 1;
+      if (claimed) {
+        L.w0[s] = t.w0;
+        L.w1[s] = t.w1;
+        L.h[s] = t.h;
+        L.cnt[s] = 0;
+      }
+    }
+    occ += __popc(__ballot_sync(0xffffffffu, claimed));
+    __syncwarp();
+    if (pending && !empty && !match) s = (s + 1) & (LT - 1);
+  }
+}
+
+__device__ inline void local_clear(WarpLocal& L) {
+  for (int s = threadIdx.x & 31; s < LT; s += 32) L.w1[s] = 0;
+  __syncwarp();
+}
+
+__device__ inline void local_flush(WarpLocal& L, int& occ, const JobDev& J) {
+  for (int s = threadIdx.x & 31; s < LT; s += 32) {
+    if (L.w1[s] != 0) {
+      global_insert(J, L.w0[s], L.w1[s], L.h[s], L.cnt[s]);
+      L.w1[s] = 0;
+    }
+  }
+  __syncwarp();
+  occ = 0;
+}
+
+// One warp maps and combines the tokens whose first byte lies in segment seg.
+__device__ inline void warp_segment(const JobDev& J, uint64_t seg, WarpLocal& L, int& occ) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t base = seg * SEG;
+  const uint8_t* __restrict__ in = J.in;
+  const uint64_t n = J.n;
+  const uint64_t rem = n - base;
+  // stage the segment and its halo; bytes past the input end read as spaces
+  const bool vec = ((reinterpret_cast<uintptr_t>(in) & 15) == 0) && rem >= (uint64_t)BUF;
+  uint4 mine;
+  if (vec) {
+    const uint4* src = reinterpret_cast<const uint4*>(in + base);
+    mine = __ldg(src + lane);
+    reinterpret_cast<uint4*>(L.buf)[lane] = mine;
+    if (lane < HALO / 16) reinterpret_cast<uint4*>(L.buf)[32 + lane] = __ldg(src + 32 + lane);
+  } else {
+    for (uint32_t r = lane; r < (uint32_t)BUF; r += 32) L.buf[r] = r < rem ? in[base + r] : (uint8_t)' ';
+    __syncwarp();
+    mine = reinterpret_cast<const uint4*>(L.buf)[lane];
+  }
+  // token starts among this lane's 16 bytes
+  uint32_t wsm = byte_bits(ws_bytes(mine.x)) | (byte_bits(ws_bytes(mine.y)) << 4) |
+                 (byte_bits(ws_bytes(mine.z)) << 8) | (byte_bits(ws_bytes(mine.w)) << 12);
+  const uint64_t lb = base + 16 * (uint64_t)lane;
+  if (lb + 16 > n) wsm |= lb >= n ? 0xFFFFu : (0xFFFFu & ~((1u << (uint32_t)(n - lb)) - 1u));
+  uint32_t prev = __shfl_up_sync(0xffffffffu, wsm >> 15, 1) & 1u;
+  if (lane == 0) prev = (base == 0) ? 1u : (uint32_t)is_ws(in[base - 1]);
+  const uint32_t start = ~wsm & ((wsm << 1) | prev) & 0xFFFFu;
+  const int c = __popc(start);
+  int incl = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  {
+    int o = incl - c;
+    uint32_t m = start;
+    while (m) {
+      const int j = __ffs(m) - 1;
+      L.starts[o++] = (uint16_t)(lane * 16 + j);
+      m &= m - 1;
+    }
+  }
+  __syncwarp();
+  for (int r0 = 0; r0 < total; r0 += 32) {
+    if (occ >= LT_FLUSH_AT) local_flush(L, occ, J);
+    const int i = r0 + lane;
+    const bool active = i < total;
+    Tok t;
+    if (active) t = read_token(in, n, base, L.buf, L.starts[i]);
+    else t.w0 = 0, t.w1 = 0, t.h = 0;
+    local_insert(L, active, t, occ, in);
+  }
+  __syncwarp();
+}
+
+}  // namespace wc
+}  // namespace mrgb

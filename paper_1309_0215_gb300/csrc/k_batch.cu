@@ -1,8 +1,264 @@
-// Persistent batched launch (placeholder).
+// Batched execution: many independent jobs of uneven sizes in ONE persistent
+// launch.
+//
+// Every pending histogram / regression / word-count job is cut into fixed
+// tiles (array jobs: a multiple of 1536 bytes; word count: a multiple of the
+// 512-byte segment), and the tiles of all jobs are laid end to end in one
+// tile space.  Persistent CTAs (two per SM) pull tile indices from a global
+// atomic cursor, so large and small jobs share the GPU without per-job launch
+// or tail costs.  A CTA keeps the local container of the job it is working on
+// (the paper's combiner, Sec. III-A) across consecutive tiles of that job —
+// lane-column shared-memory arrays for a histogram, registers for the
+// regression sums, per-warp shared-memory hash tables for word count — and
+// merges it into the job's global container when it moves to a tile of
+// another job and at the end.  The word-count jobs' merge and sort then run
+// once for all of them (k_wordcount.cu, sort keyed by job).
+//
+// Per-job choices (tile sizes, histogram local arrays vs global atomics) come
+// from the planner / autotuner in mr_api.cu.
 #include "mr_internal.h"
+#include "dev_array.cuh"
+#include "dev_wordcount.cuh"
+
 namespace mrgb {
-uint64_t batch_tiles_for(uint32_t, uint64_t) { return 1; }
-cudaError_t launch_batch(const BatchJob*, uint32_t, uint64_t, unsigned long long*, const DevInfo&, cudaStream_t) {
-  return cudaErrorNotSupported;
+namespace {
+
+constexpr int BT = 256;
+constexpr int BWARPS = BT / 32;
+constexpr int B_SMEM_HIST = arr::HIST_WORDS * 4;
+constexpr int B_SMEM_WC = BWARPS * (int)sizeof(wc::WarpLocal);
+constexpr int B_SMEM = B_SMEM_HIST > B_SMEM_WC ? B_SMEM_HIST : B_SMEM_WC;
+
+__device__ __forceinline__ uint32_t find_job(const BatchJob* jobs, uint32_t njobs, uint64_t t) {
+  uint32_t lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].tile_begin <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
 }
+
+__device__ __forceinline__ void block_reduce_add5(long long (&acc)[5], long long* out, long long (*part)[5]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    long long v = acc[i];
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) part[warp][i] = v;
+    acc[i] = 0;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      long long v = lane < BWARPS ? part[lane][i] : 0;
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0 && v) atomicAdd(reinterpret_cast<unsigned long long*>(out + i), (unsigned long long)v);
+    }
+  }
+  __syncthreads();
+}
+
+// histogram tile [t0, t1) of a job (t0 a multiple of 1536), local arrays
+__device__ void hist_tile_smem(const BatchJob& J, uint64_t t0, uint64_t t1, uint32_t sbase) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lb = sbase + lane * 4;
+  const uint8_t* in = J.in;
+  uint64_t scalar0 = t0;
+  if (((uintptr_t)in & 15) == 0) {
+    const uint32_t rot0 = lane % 3;  // tiles and chunks start at multiples of 3
+    uint32_t cb[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) cb[q] = lb + ((rot0 + q) % 3) * (256u * arr::HIST_COLS * 4);
+    const uint64_t c0 = t0 / arr::CHUNK, c1 = c0 + (t1 - t0) / arr::CHUNK;
+    const uint4* vin = reinterpret_cast<const uint4*>(in);
+    uint64_t c = c0 + warp;
+    for (; c + BWARPS < c1; c += 2 * BWARPS) {
+      const uint4* p = vin + c * arr::CHUNK_VEC + lane;
+      const uint4* q = vin + (c + BWARPS) * arr::CHUNK_VEC + lane;
+      uint4 a0 = arr::ldg_stream(p), a1 = arr::ldg_stream(p + 32), a2 = arr::ldg_stream(p + 64);
+      uint4 b0 = arr::ldg_stream(q), b1 = arr::ldg_stream(q + 32), b2 = arr::ldg_stream(q + 64);
+      arr::hist_vec<0>(a0, cb);
+      arr::hist_vec<1>(a1, cb);
+      arr::hist_vec<2>(a2, cb);
+      arr::hist_vec<0>(b0, cb);
+      arr::hist_vec<1>(b1, cb);
+      arr::hist_vec<2>(b2, cb);
+    }
+    if (c < c1) {
+      const uint4* p = vin + c * arr::CHUNK_VEC + lane;
+      uint4 a0 = arr::ldg_stream(p), a1 = arr::ldg_stream(p + 32), a2 = arr::ldg_stream(p + 64);
+      arr::hist_vec<0>(a0, cb);
+      arr::hist_vec<1>(a1, cb);
+      arr::hist_vec<2>(a2, cb);
+    }
+    scalar0 = c1 * arr::CHUNK;
+  }
+  for (uint64_t i = scalar0 + threadIdx.x; i < t1; i += BT)
+    arr::red_shared_add(lb + (uint32_t)(i % 3) * (256u * arr::HIST_COLS * 4) + (uint32_t)in[i] * (arr::HIST_COLS * 4),
+                        1u);
+}
+
+// histogram tile without local arrays: 64-bit atomics on the global bins
+__device__ void hist_tile_global(const BatchJob& J, uint64_t t0, uint64_t t1) {
+  unsigned long long* bins = static_cast<unsigned long long*>(J.out);
+  for (uint64_t i = t0 + threadIdx.x; i < t1; i += BT) atomicAdd(bins + (i % 3) * 256 + J.in[i], 1ull);
+}
+
+__device__ void linreg_tile(const BatchJob& J, uint64_t t0, uint64_t t1, long long (&acc)[5]) {
+  const int8_t* in = reinterpret_cast<const int8_t*>(J.in);
+  uint64_t scalar0 = t0;
+  if (((uintptr_t)in & 15) == 0) {
+    const uint64_t v0 = t0 / 16, v1 = t1 / 16;  // t0 is a multiple of 16
+    const uint4* vin = reinterpret_cast<const uint4*>(in);
+    int p[5] = {0, 0, 0, 0, 0};  // at most a tile per flush: far below the int32 limit
+    uint64_t v = v0 + threadIdx.x;
+    for (; v + BT < v1; v += 2 * BT) {
+      uint4 a = arr::ldg_stream(vin + v);
+      uint4 b = arr::ldg_stream(vin + v + BT);
+      arr::lr_word(a.x, p); arr::lr_word(a.y, p); arr::lr_word(a.z, p); arr::lr_word(a.w, p);
+      arr::lr_word(b.x, p); arr::lr_word(b.y, p); arr::lr_word(b.z, p); arr::lr_word(b.w, p);
+    }
+    if (v < v1) {
+      uint4 a = arr::ldg_stream(vin + v);
+      arr::lr_word(a.x, p); arr::lr_word(a.y, p); arr::lr_word(a.z, p); arr::lr_word(a.w, p);
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) acc[i] += p[i];
+    scalar0 = v1 * 16;
+  }
+  for (uint64_t i = scalar0 / 2 + threadIdx.x; 2 * i + 1 < t1 + 1 && 2 * i < t1; i += BT) {
+    const long long x = in[2 * i], y = in[2 * i + 1];
+    acc[0] += x; acc[1] += y; acc[2] += x * x; acc[3] += y * y; acc[4] += x * y;
+  }
+}
+
+__global__ void __launch_bounds__(BT, 2)
+batch_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs, uint64_t total_tiles, unsigned long long* cursor,
+             uint64_t arr_tile, uint64_t wc_tile) {
+  extern __shared__ __align__(16) unsigned char bsm[];
+  __shared__ unsigned long long s_tile[2];
+  __shared__ uint32_t s_job[2];
+  __shared__ long long part[BWARPS][5];
+  uint32_t* hs = reinterpret_cast<uint32_t*>(bsm);
+  wc::WarpLocal& L = reinterpret_cast<wc::WarpLocal*>(bsm)[threadIdx.x >> 5];
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(hs);
+  int64_t cur = -1;
+  uint32_t kind = 0, cont = 0;
+  long long acc[5] = {0, 0, 0, 0, 0};
+  int occ = 0;
+
+  auto flush = [&](const BatchJob& J) {
+    if (kind == MR_HIST_RGB8 && cont != MR_C_GLOBAL_ARRAY) {
+      __syncthreads();
+      unsigned long long* bins = static_cast<unsigned long long*>(J.out);
+      for (int bin = threadIdx.x; bin < arr::HIST_BINS; bin += BT) {
+        unsigned long long s = 0;
+#pragma unroll 8
+        for (int l = 0; l < arr::HIST_COLS; ++l) s += hs[bin * arr::HIST_COLS + ((l + bin) & 31)];
+        if (s) atomicAdd(bins + bin, s);
+      }
+      __syncthreads();
+    } else if (kind == MR_LINREG_I8) {
+      block_reduce_add5(acc, static_cast<long long*>(J.out), part);
+    } else if (kind == MR_WORDCOUNT) {
+      wc::local_flush(L, occ, J.wc);
+      __syncthreads();
+    }
+  };
+  auto init = [&](const BatchJob& J) {
+    kind = J.kind;
+    cont = J.container;
+    if (kind == MR_HIST_RGB8 && cont != MR_C_GLOBAL_ARRAY) {
+      for (int i = threadIdx.x; i < arr::HIST_WORDS; i += BT) hs[i] = 0;
+      __syncthreads();
+    } else if (kind == MR_WORDCOUNT) {
+      wc::local_clear(L);
+      occ = 0;
+    }
+  };
+
+  for (int it = 0;; ++it) {
+    const int b = it & 1;  // double-buffered broadcast: one barrier per tile
+    if (threadIdx.x == 0) {
+      const unsigned long long t = atomicAdd(cursor, 1ull);
+      s_tile[b] = t;
+      s_job[b] = t < total_tiles ? find_job(jobs, njobs, t) : 0xffffffffu;
+    }
+    __syncthreads();
+    const uint64_t t = s_tile[b];
+    if (t >= total_tiles) break;
+    const uint32_t j = s_job[b];
+    const BatchJob& J = jobs[j];
+    if ((int64_t)j != cur) {
+      if (cur >= 0) flush(jobs[cur]);
+      init(J);
+      cur = j;
+    }
+    const uint64_t local = t - J.tile_begin;
+    if (J.kind == MR_WORDCOUNT) {
+      const uint64_t s0 = local * (wc_tile / wc::SEG);
+      uint64_t s1 = s0 + wc_tile / wc::SEG;
+      const uint64_t nseg = (J.n + wc::SEG - 1) / wc::SEG;
+      if (s1 > nseg) s1 = nseg;
+      for (uint64_t sg = s0 + (threadIdx.x >> 5); sg < s1; sg += BWARPS) wc::warp_segment(J.wc, sg, L, occ);
+    } else {
+      const uint64_t t0 = local * arr_tile;
+      const uint64_t t1 = (t0 + arr_tile) < J.n ? t0 + arr_tile : J.n;
+      if (J.kind == MR_HIST_RGB8) {
+        if (cont == MR_C_GLOBAL_ARRAY) hist_tile_global(J, t0, t1);
+        else hist_tile_smem(J, t0, t1, sbase);
+      } else {
+        linreg_tile(J, t0, t1, acc);
+      }
+    }
+  }
+  if (cur >= 0) flush(jobs[cur]);
+}
+
+// Zero every container the batch accumulates into: histogram bins,
+// regression sums, word-count tables and state words.  One CTA per job.
+__global__ void batch_init_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs) {
+  for (uint32_t j = blockIdx.x; j < njobs; j += gridDim.x) {
+    const BatchJob& J = jobs[j];
+    uint4* p;
+    uint64_t n16;
+    if (J.kind == MR_WORDCOUNT) {
+      p = reinterpret_cast<uint4*>(J.wc.key);
+      n16 = J.wc.cap * 24 / 16;
+      for (uint32_t i = threadIdx.x; i < 64 / 4; i += blockDim.x) J.wc.state[i] = 0;
+    } else {
+      p = static_cast<uint4*>(J.out);
+      n16 = J.kind == MR_HIST_RGB8 ? 768 * 8 / 16 : 48 / 16;
+    }
+    for (uint64_t i = threadIdx.x; i < n16; i += blockDim.x) p[i] = make_uint4(0, 0, 0, 0);
+  }
+}
+
+}  // namespace
+
+uint64_t batch_tiles_for(uint32_t kind, uint64_t n, uint64_t arr_tile, uint64_t wc_tile) {
+  const uint64_t t = kind == MR_WORDCOUNT ? wc_tile : arr_tile;
+  return (n + t - 1) / t;
+}
+
+cudaError_t batch_prepare() {
+  return cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SMEM);
+}
+
+cudaError_t launch_batch(const BatchJob* jobs_dev, uint32_t njobs, uint64_t total_tiles, unsigned long long* cursor,
+                         uint64_t arr_tile, uint64_t wc_tile, const DevInfo& di, cudaStream_t s, uint64_t* nk) {
+  cudaError_t e;
+  batch_init_kernel<<<di.sms * 4, 256, 0, s>>>(jobs_dev, njobs);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(cursor, 0, 8, s)) != cudaSuccess) return e;
+  uint64_t grid = 2ull * di.sms;
+  if (grid > total_tiles) grid = total_tiles ? total_tiles : 1;
+  batch_kernel<<<(unsigned)grid, BT, B_SMEM, s>>>(jobs_dev, njobs, total_tiles, cursor, arr_tile, wc_tile);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  *nk += 2;
+  return cudaSuccess;
+}
+
 }  // namespace mrgb

@@ -14,11 +14,17 @@
 //    of Numerical Algorithms, eq. 3.4 / 3.5 for dot products); we use
 //    E = 1.01 (D + 8) 2^-24 (||x|| + max_k ||c_k||)^2.  If the two smallest
 //    d~ differ by more than 2E the FP32 winner is the FP64 winner.
-//  * Every other point is re-checked exactly in FP64 over all K centroids
-//    with the same operation order as the definition above.
+//  * Every other point is re-checked exactly in FP64 with the same operation
+//    order as the definition above, over the centroids that can still win:
+//    FP32 direct-difference distances have relative error at most
+//    g = gamma_{D+3} (Higham, eq. 3.5 on a sum of squares), so centroid k can
+//    be the minimum only if d~_k <= d~_min (1 + g) / (1 - g).
 //  * Sums are accumulated as int64 fixed point q = rint(x * 2^s), with s chosen
 //    from max|x| and N so no sum can overflow; integer addition is exact and
-//    order-independent, so results do not depend on scheduling.
+//    order-independent, so results do not depend on scheduling.  The update
+//    first groups points by cluster (counting sort), so each warp adds runs
+//    of points of one cluster in registers and issues a handful of atomics
+//    per run instead of one per coordinate.
 #include <cmath>
 
 #include "mr_internal.h"
@@ -203,9 +209,24 @@ km_assign_fp32_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const
   }
 }
 
-// Exact FP64 argmin for the listed points: one warp per point, lane l takes
-// centroids l, l+32, ...; the distance is the definition's sum in order with
-// separately rounded subtract, multiply and add.
+// Exact FP64 argmin for the listed points, one warp per point.  Pass 1:
+// FP32 distance to every centroid with the lanes spread over the dimensions
+// (coalesced centroid rows, warp-sum; the bound below holds for any order),
+// keeping the smallest.  Pass 2: in FP64, separately rounded subtract,
+// multiply and add with the dimensions in order, only for the centroids whose
+// FP32 distance is within the relative error bound of that minimum (one lane
+// per such centroid).
+__device__ __forceinline__ float warp_dist32(const float* __restrict__ xp, const float* __restrict__ cp, uint32_t d,
+                                             int lane) {
+  float s = 0.f;
+  for (uint32_t j = lane; j < d; j += 32) {
+    const float t = xp[j] - cp[j];
+    s = fmaf(t, t, s);
+  }
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
 __global__ void km_recheck_fp64_kernel(const float* __restrict__ x, uint32_t d, const float* __restrict__ c, uint32_t k,
                                        const uint32_t* flagged, const uint32_t* nflag, int32_t* assign,
                                        unsigned long long* stat) {
@@ -214,19 +235,33 @@ __global__ void km_recheck_fp64_kernel(const float* __restrict__ x, uint32_t d, 
   const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   if (w0 == 0 && lane == 0 && stat) atomicAdd(stat, (unsigned long long)nf);
+  const float g = 1.01f * (float)(d + 8) * 5.9604644775390625e-08f;
+  const float widen = (1.f + g) / (1.f - g) * (1.f + 4.f * 5.9604644775390625e-08f);
   for (uint64_t f = w0; f < nf; f += nw) {
     const uint32_t p = flagged[f];
     const float* xp = x + (uint64_t)p * d;
+    float m32 = INFINITY;
+    for (uint32_t kk = 0; kk < k; ++kk) m32 = fminf(m32, warp_dist32(xp, c + (uint64_t)kk * d, d, lane));
+    const float lim = m32 * widen;
     double best = INFINITY;
     int bk = 0x7fffffff;
-    for (uint32_t kk = lane; kk < k; kk += 32) {
-      const float* cp = c + (uint64_t)kk * d;
-      double s = 0.0;
-      for (uint32_t j = 0; j < d; ++j) {
-        const double t = __dsub_rn((double)xp[j], (double)cp[j]);
-        s = __dadd_rn(s, __dmul_rn(t, t));
+    for (uint32_t k0 = 0; k0 < k; k0 += 32) {
+      // candidates of this group of 32 centroids, then one lane per candidate
+      uint32_t cand = 0;
+      for (uint32_t t = 0; t < 32 && k0 + t < k; ++t) {
+        const float s32 = warp_dist32(xp, c + (uint64_t)(k0 + t) * d, d, lane);
+        if (s32 <= lim || m32 != m32) cand |= 1u << t;
       }
-      if (s < best) best = s, bk = (int)kk;  // kk increases: the lowest index keeps a tie
+      if ((cand >> lane) & 1u) {
+        const uint32_t kk = k0 + lane;
+        const float* cp = c + (uint64_t)kk * d;
+        double s64 = 0.0;
+        for (uint32_t j = 0; j < d; ++j) {
+          const double t = __dsub_rn((double)xp[j], (double)cp[j]);
+          s64 = __dadd_rn(s64, __dmul_rn(t, t));
+        }
+        if (s64 < best) best = s64, bk = (int)kk;  // kk increases per lane: the lowest index keeps a tie
+      }
     }
     for (int o = 16; o; o >>= 1) {
       const double ob = __shfl_xor_sync(0xffffffffu, best, o);
@@ -240,8 +275,20 @@ __global__ void km_recheck_fp64_kernel(const float* __restrict__ x, uint32_t d, 
 // max |x| over all coordinates (as float bits; non-negative floats order like ints)
 __global__ void km_maxabs_kernel(const float* __restrict__ x, uint64_t cnt, unsigned int* out) {
   unsigned int m = 0;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (uint64_t)gridDim.x * blockDim.x)
-    m = max(m, __float_as_uint(fabsf(x[i])));
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t done = 0;
+  if (((uintptr_t)x & 15) == 0) {
+    const uint64_t n4 = cnt / 4;
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    for (uint64_t i = tid; i < n4; i += nth) {
+      const float4 v = __ldg(x4 + i);
+      m = max(m, max(max(__float_as_uint(fabsf(v.x)), __float_as_uint(fabsf(v.y))),
+                     max(__float_as_uint(fabsf(v.z)), __float_as_uint(fabsf(v.w)))));
+    }
+    done = n4 * 4;
+  }
+  for (uint64_t i = done + tid; i < cnt; i += nth) m = max(m, __float_as_uint(fabsf(x[i])));
   for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
@@ -257,63 +304,146 @@ __global__ void km_scale_kernel(const unsigned int* maxabs, uint32_t n, int* shi
   *shift = s;
 }
 
-// Per-cluster int64 fixed-point sums and counts.  A CTA keeps a local copy in
-// shared memory when K*D*8 + K*8 fits, else it adds straight into the global
-// arrays (the paper's "eliminated local arrays").  A warp takes 8 points per
-// step and issues all their loads before the atomics, to keep enough bytes in
-// flight; lane l covers dimensions l and l + 32 of each 64-dimension slice.
-__global__ void __launch_bounds__(512)
-km_update_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, uint32_t k,
-                 const int32_t* __restrict__ assign, const int* shift, long long* sums,
-                 unsigned long long* counts, int use_smem) {
-  extern __shared__ long long up_sm[];
-  long long* ls = up_sm;                                         // [k*d]
-  unsigned long long* lc = reinterpret_cast<unsigned long long*>(up_sm + (uint64_t)k * d);  // [k]
-  long long* ts = use_smem ? ls : sums;
-  unsigned long long* tc = use_smem ? lc : counts;
-  if (use_smem) {
-    for (uint64_t i = threadIdx.x; i < (uint64_t)k * d; i += blockDim.x) ls[i] = 0;
-    for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) lc[i] = 0;
+__device__ __forceinline__ uint32_t cluster_of(const int32_t* assign, uint64_t i, uint32_t k) {
+  const int a = assign[i];
+  return (a < 0 || (uint32_t)a >= k) ? 0u : (uint32_t)a;
+}
+
+// Cluster sizes (a CTA counts in shared memory, then adds to the global counts).
+__global__ void km_count_kernel(const int32_t* __restrict__ assign, uint32_t n, uint32_t k,
+                                unsigned long long* counts) {
+  extern __shared__ uint32_t hc[];
+  for (uint32_t t = threadIdx.x; t < k; t += blockDim.x) hc[t] = 0;
+  __syncthreads();
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    atomicAdd(&hc[cluster_of(assign, i, k)], 1u);
+  __syncthreads();
+  for (uint32_t t = threadIdx.x; t < k; t += blockDim.x)
+    if (hc[t]) atomicAdd(counts + t, (unsigned long long)hc[t]);
+}
+
+// Exclusive scan of the counts into each cluster's write cursor (one CTA).
+__global__ void km_offsets_kernel(const unsigned long long* counts, uint32_t k, uint32_t* cursor) {
+  __shared__ uint32_t carry;
+  __shared__ uint32_t wsum[32];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t b = 0; b < k; b += blockDim.x) {
+    const uint32_t i = b + threadIdx.x;
+    const uint32_t v = i < k ? (uint32_t)counts[i] : 0;
+    uint32_t incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+      uint32_t wi = w;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += t;
+      }
+      wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    const uint32_t ex = carry + wsum[warp] + incl - v;
+    if (i < k) cursor[i] = ex;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = ex + v;
     __syncthreads();
   }
-  const double scale = ldexp(1.0, *shift);
+}
+
+// Counting-sort scatter: perm lists the points grouped by cluster (order
+// inside a cluster does not matter: the sums are exact integers).  A CTA takes
+// a chunk of points, counts them per cluster in shared memory, reserves each
+// cluster's range with one global atomic, then places its points with
+// shared-memory cursors.
+constexpr int SCAT_THREADS = 256;
+constexpr int SCAT_PER_THREAD = 16;
+__global__ void __launch_bounds__(SCAT_THREADS) km_scatter_kernel(const int32_t* __restrict__ assign, uint32_t n,
+                                                                  uint32_t k, uint32_t* cursor,
+                                                                  uint32_t* __restrict__ perm) {
+  extern __shared__ uint32_t sc[];  // [k] local counts, then local cursors
+  const uint64_t chunk = (uint64_t)SCAT_THREADS * SCAT_PER_THREAD;
+  const uint64_t b0 = (uint64_t)blockIdx.x * chunk;
+  for (uint32_t t = threadIdx.x; t < k; t += SCAT_THREADS) sc[t] = 0;
+  __syncthreads();
+  uint32_t a[SCAT_PER_THREAD];
+#pragma unroll
+  for (int r = 0; r < SCAT_PER_THREAD; ++r) {
+    const uint64_t i = b0 + (uint64_t)r * SCAT_THREADS + threadIdx.x;
+    a[r] = i < n ? cluster_of(assign, i, k) : 0xffffffffu;
+    if (a[r] != 0xffffffffu) atomicAdd(&sc[a[r]], 1u);
+  }
+  __syncthreads();
+  for (uint32_t t = threadIdx.x; t < k; t += SCAT_THREADS)
+    if (sc[t]) sc[t] = atomicAdd(cursor + t, sc[t]);
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < SCAT_PER_THREAD; ++r) {
+    const uint64_t i = b0 + (uint64_t)r * SCAT_THREADS + threadIdx.x;
+    if (a[r] != 0xffffffffu) perm[atomicAdd(&sc[a[r]], 1u)] = (uint32_t)i;
+  }
+}
+
+// Per-cluster int64 fixed-point sums.  Warp w adds points perm[64w ..
+// 64w+63]; they come in runs of one cluster, summed in registers (lane l holds
+// dimensions l and l+32 of the current 64-dimension slice) and added to the
+// global sums once per run.
+constexpr int SUM_RUN = 64;
+__global__ void __launch_bounds__(256) km_sum_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, uint32_t k,
+                                                     const int32_t* __restrict__ assign, const uint32_t* __restrict__ perm,
+                                                     const int* shift, long long* sums) {
   const int lane = threadIdx.x & 31;
-  const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t p0 = w0 * 8; p0 < n; p0 += nw * 8) {
-    const int al = (lane < 8 && p0 + lane < n) ? assign[p0 + lane] : -1;
-    for (uint32_t j0 = 0; j0 < d; j0 += 64) {
-      float v[8][2];
+  const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t p0 = w * SUM_RUN;
+  if (p0 >= n) return;
+  const uint64_t p1 = (p0 + SUM_RUN) < n ? p0 + SUM_RUN : n;
+  // x * 2^s is exact in FP32 (a power-of-two scale far from overflow), so
+  // rounding it to int64 gives the same q as in double precision
+  const float scale = ldexpf(1.f, *shift);
+  uint32_t idx[2];
+  idx[0] = perm[p0 + lane < p1 ? p0 + lane : p0];
+  idx[1] = perm[p0 + 32 + lane < p1 ? p0 + 32 + lane : p0];
+  for (uint32_t j0 = 0; j0 < d; j0 += 64) {
+    const uint32_t dj0 = j0 + lane, dj1 = j0 + 32 + lane;
+    long long a0 = 0, a1 = 0;
+    int cur = -1;
+    for (uint64_t p = p0; p < p1; p += 4) {
+      float v[4][2];
+      int cl[4];
 #pragma unroll
-      for (int r = 0; r < 8; ++r)
+      for (int u = 0; u < 4; ++u) {
+        const uint64_t pp = p + u;
+        const uint32_t i = __shfl_sync(0xffffffffu, idx[(pp - p0) >> 5], (int)((pp - p0) & 31));
+        const bool ok = pp < p1;
+        cl[u] = ok ? (int)cluster_of(assign, i, k) : -1;
+        v[u][0] = (ok && dj0 < d) ? x[(uint64_t)i * d + dj0] : 0.f;
+        v[u][1] = (ok && dj1 < d) ? x[(uint64_t)i * d + dj1] : 0.f;
+      }
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint32_t dj = j0 + lane + 32 * h;
-          v[r][h] = (p0 + r < n && dj < d) ? x[(p0 + r) * d + dj] : 0.f;
-        }
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int a = __shfl_sync(0xffffffffu, al, r);
-        if (a < 0 || (uint32_t)a >= k) continue;
-        long long* sp = ts + (uint64_t)a * d;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint32_t dj = j0 + lane + 32 * h;
-          if (dj < d) {
-            const long long q = __double2ll_rn((double)v[r][h] * scale);
-            atomicAdd(reinterpret_cast<unsigned long long*>(sp + dj), (unsigned long long)q);
+      for (int u = 0; u < 4; ++u) {
+        if (cl[u] < 0) break;
+        if (cl[u] != cur) {
+          if (cur >= 0) {
+            if (dj0 < d && a0) atomicAdd(reinterpret_cast<unsigned long long*>(sums + (uint64_t)cur * d + dj0), (unsigned long long)a0);
+            if (dj1 < d && a1) atomicAdd(reinterpret_cast<unsigned long long*>(sums + (uint64_t)cur * d + dj1), (unsigned long long)a1);
           }
+          cur = cl[u];
+          a0 = a1 = 0;
         }
+        a0 += __float2ll_rn(v[u][0] * scale);
+        a1 += __float2ll_rn(v[u][1] * scale);
       }
     }
-    if (al >= 0 && (uint32_t)al < k) atomicAdd(tc + al, 1ull);
-  }
-  if (use_smem) {
-    __syncthreads();
-    for (uint64_t i = threadIdx.x; i < (uint64_t)k * d; i += blockDim.x)
-      if (ls[i]) atomicAdd(reinterpret_cast<unsigned long long*>(sums + i), (unsigned long long)ls[i]);
-    for (uint32_t i = threadIdx.x; i < k; i += blockDim.x)
-      if (lc[i]) atomicAdd(counts + i, lc[i]);
+    if (cur >= 0) {
+      if (dj0 < d && a0) atomicAdd(reinterpret_cast<unsigned long long*>(sums + (uint64_t)cur * d + dj0), (unsigned long long)a0);
+      if (dj1 < d && a1) atomicAdd(reinterpret_cast<unsigned long long*>(sums + (uint64_t)cur * d + dj1), (unsigned long long)a1);
+    }
   }
 }
 
@@ -359,6 +489,7 @@ size_t km_scratch_bytes(uint32_t n, uint32_t d, uint32_t k, int precision) {
   b += a256(4 * 4);                    // nflag[2], maxabs, cmax
   b += a256((uint64_t)k * 4 * 2);      // cnorm (||c||^2) + spare
   b += a256(16);                       // shift
+  b += a256((uint64_t)k * 4);          // per-cluster write cursor
   if (precision != MR_KM_FP32) {
     b += a256((uint64_t)n * 4);        // second flag list
     b += a256((uint64_t)k * d * 2 * 2);  // bf16 centroids (hi, lo)
@@ -381,6 +512,7 @@ cudaError_t km_carve(KmBuffers& b, uint8_t* p, size_t bytes) {
   b.cnorm = reinterpret_cast<float*>(take(k * 8));
   b.cent_bf16_norm = nullptr;
   int* shift = reinterpret_cast<int*>(take(16));
+  b.kcursor = reinterpret_cast<uint32_t*>(take(k * 4));
   b.fx_shift = 0;
   b.xnorm = reinterpret_cast<float*>(shift);  // holds the device-side shift
   if (b.precision != MR_KM_FP32) {
@@ -412,13 +544,12 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
   if ((e = cudaFuncSetAttribute(km_assign_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, asm_bytes)) !=
       cudaSuccess)
     return e;
-  const uint64_t up_bytes = (uint64_t)k * d * 8 + (uint64_t)k * 8;
-  const int use_smem = up_bytes <= (uint64_t)di.smem_optin ? 1 : 0;
-  if (use_smem) {
-    if ((e = cudaFuncSetAttribute(km_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)up_bytes)) !=
-        cudaSuccess)
-      return e;
-  }
+  if ((e = cudaFuncSetAttribute(km_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(k * 4))) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(km_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(k * 4))) !=
+      cudaSuccess)
+    return e;
   const uint32_t ntiles = (n + TP - 1) / TP;
   const uint32_t agrid = ntiles < (uint32_t)di.sms * 2 ? ntiles : (uint32_t)di.sms * 2;
   for (uint32_t it = 0; it < iters; ++it) {
@@ -431,10 +562,16 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
       ++*nk;
     }
     km_recheck_fp64_kernel<<<di.sms * 4, 256, 0, s>>>(x, d, b.cent, k, b.flagged, b.nflag, b.assign, b.stats + 1);
-    km_update_kernel<<<di.sms, 512, use_smem ? up_bytes : 0, s>>>(x, n, d, k, b.assign, shift, b.sums, b.counts,
-                                                                  use_smem);
+    // update: counting sort of the points by cluster, then run-wise sums
+    km_count_kernel<<<di.sms * 2, 512, k * 4, s>>>(b.assign, n, k, b.counts);
+    km_offsets_kernel<<<1, 1024, 0, s>>>(b.counts, k, b.kcursor);
+    const uint64_t sc_blocks = (n + (uint64_t)SCAT_THREADS * SCAT_PER_THREAD - 1) / ((uint64_t)SCAT_THREADS * SCAT_PER_THREAD);
+    km_scatter_kernel<<<(unsigned)sc_blocks, SCAT_THREADS, k * 4, s>>>(b.assign, n, k, b.kcursor, b.flagged);
+    const uint64_t sum_warps = (n + SUM_RUN - 1) / SUM_RUN;
+    km_sum_kernel<<<(unsigned)((sum_warps * 32 + 255) / 256), 256, 0, s>>>(x, n, d, k, b.assign, b.flagged, shift,
+                                                                           b.sums);
     km_finalize_kernel<<<64, 256, 0, s>>>(b.cent, k, d, b.sums, b.counts, shift, cmax_bits);
-    *nk += 4;
+    *nk += 7;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   km_finish_kernel<<<di.sms, 256, 0, s>>>(b.cent, (uint64_t)k * d, out_c, b.assign, n, out_a, b.stats, out_s, iters);

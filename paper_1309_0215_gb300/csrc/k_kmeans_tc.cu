@@ -14,11 +14,14 @@
 //   * one thread issues tcgen05.mma (M = 128, N = K rounded up to 16, K = 16
 //     per instruction, 4 steps over D = 64) into one of two 256-column TMEM
 //     accumulators, and commits completion to mbarriers;
-//   * 4 epilogue warps read the 128 x N FP32 tile with tcgen05.ld (one TMEM
-//     lane per point), form d~ = fma(-2, acc, ||x||^2) + ||c||^2, keep the
-//     two smallest, and apply the margin test below.
-// Converters, MMA issue and epilogue overlap through double-buffered operand
-// stages and accumulators.  Every mbarrier wait is bounded; on timeout the
+//   * 8 epilogue warps read the 128 x N FP32 tile with tcgen05.ld (one TMEM
+//     lane per point; two warps per lane quadrant, each on half of the
+//     columns), form d~ = fma(-2, acc, ||x||^2) + ||c||^2 and keep the two
+//     smallest with four independent branch-free running minima per thread;
+//     the upper half hands its pair to the lower half, which applies the
+//     margin test below.
+// Converters, MMA issue and epilogue overlap through three operand stages
+// and two TMEM accumulators.  Every mbarrier wait is bounded; on timeout the
 // CTA stops, drains its MMAs, frees TMEM and reports through stats[3].
 //
 // Margin test (rigorous, per point).  With u_b = 2^-8 (BF16 rounding) the
@@ -41,12 +44,13 @@ namespace {
 constexpr int TM = 128;          // points per tile = MMA M = TMEM lanes
 constexpr int KD = 64;           // padded dimension: one 128-byte row of BF16
 constexpr int NMAX = 256;        // centroids: MMA N
-constexpr int EPI_WARPS = 4;
-constexpr int MMA_WARP = 4;
-constexpr int CVT_WARP0 = 5;
+constexpr int EPI_WARPS = 8;      // two per TMEM lane quadrant, each on half the columns
+constexpr int MMA_WARP = 8;
+constexpr int CVT_WARP0 = 9;
 constexpr int CVT_WARPS = 8;
-constexpr int TC_THREADS = (EPI_WARPS + 1 + CVT_WARPS) * 32;  // 416
-constexpr int STAGES = 2;
+constexpr int TC_THREADS = (EPI_WARPS + 1 + CVT_WARPS) * 32;  // 544
+constexpr int STAGES = 3;         // operand stages
+constexpr int ACCS = 2;           // TMEM accumulators
 constexpr uint32_t TMEM_COLS = 512;  // two 256-column FP32 accumulators
 constexpr long long SPIN_LIMIT = 1ll << 24;
 
@@ -57,8 +61,11 @@ struct __align__(1024) TcSmem {
   uint8_t a_lo[STAGES][TM * 128];
   float nx[STAGES][TM];
   float cn[NMAX];
+  float xd1[ACCS][TM], xd2[ACCS][TM];  // top-2 of the upper column half, per row
+  int xk1[ACCS][TM];
   unsigned long long full_a[STAGES], empty_a[STAGES], nx_free[STAGES];
-  unsigned long long full_acc[STAGES], empty_acc[STAGES], drained;
+  unsigned long long full_acc[ACCS], empty_acc[ACCS], drained;
+  unsigned long long xfull[ACCS], xfree[ACCS];  // upper-half top-2 handed to the lower half
   uint32_t tmem_base;
   int err;
 };
@@ -130,16 +137,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void best2_push(float d, int k, float& d1, int& k1, float& d2) {
-  if (d < d1 || (d == d1 && k < k1)) {
-    d2 = d1;
-    d1 = d;
-    k1 = k;
-  } else if (d < d2) {
-    d2 = d;
-  }
-}
-
 // BF16 hi/lo split of two values, packed little-endian (element 0 low half).
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
   const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
@@ -171,8 +168,12 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
       mbar_init(&S.full_a[s], CVT_WARPS);
       mbar_init(&S.empty_a[s], 1);
       mbar_init(&S.nx_free[s], EPI_WARPS);
-      mbar_init(&S.full_acc[s], 1);
-      mbar_init(&S.empty_acc[s], EPI_WARPS);
+    }
+    for (int b = 0; b < ACCS; ++b) {
+      mbar_init(&S.full_acc[b], 1);
+      mbar_init(&S.empty_acc[b], EPI_WARPS);
+      mbar_init(&S.xfull[b], EPI_WARPS / 2);
+      mbar_init(&S.xfree[b], EPI_WARPS / 2);
     }
     mbar_init(&S.drained, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -198,7 +199,8 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
     *reinterpret_cast<uint32_t*>(S.b_hi + off) = hi;
     *reinterpret_cast<uint32_t*>(S.b_lo + off) = lo;
   }
-  for (uint32_t t = threadIdx.x; t < NMAX; t += blockDim.x) S.cn[t] = t < k ? cnorm[t] : 0.f;
+  // padded centroid columns get an infinite norm, so they never win
+  for (uint32_t t = threadIdx.x; t < NMAX; t += blockDim.x) S.cn[t] = t < k ? cnorm[t] : INFINITY;
   fence_proxy_async();
   tc_fence_before();
   __syncthreads();
@@ -214,8 +216,8 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
     for (uint32_t i = 0;; ++i) {
       const uint32_t tile = blockIdx.x + i * gridDim.x;
       if (tile >= ntiles) break;
-      const int s = i & 1;
-      const uint32_t u = i >> 1;
+      const int s = (int)(i % STAGES);
+      const uint32_t u = i / STAGES;
       const uint32_t p = tile * TM + r;
       float v[32];
       if (p < n && vec) {
@@ -235,7 +237,7 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
           v[j] = (p < n && dj < d) ? x[(uint64_t)p * d + dj] : 0.f;
         }
       }
-      if (i >= 2) {
+      if (i >= STAGES) {
         bool ok = mbar_wait(&S.empty_a[s], (u + 1) & 1, err);
         ok = ok && mbar_wait(&S.nx_free[s], (u + 1) & 1, err);
         if (!__all_sync(0xffffffffu, ok)) break;
@@ -267,12 +269,14 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
       for (uint32_t i = 0;; ++i) {
         const uint32_t tile = blockIdx.x + i * gridDim.x;
         if (tile >= ntiles) break;
-        const int s = i & 1;
-        const uint32_t u = i >> 1;
+        const int s = (int)(i % STAGES);
+        const uint32_t u = i / STAGES;
+        const int b = (int)(i & 1);
+        const uint32_t v = i >> 1;
         if (!mbar_wait(&S.full_a[s], u & 1, err)) break;
-        if (i >= 2 && !mbar_wait(&S.empty_acc[s], (u + 1) & 1, err)) break;
+        if (i >= ACCS && !mbar_wait(&S.empty_acc[b], (v + 1) & 1, err)) break;
         tc_fence_after();
-        const uint32_t dt = tmem + (uint32_t)s * 256u;
+        const uint32_t dt = tmem + (uint32_t)b * 256u;
         const uint32_t ah = su32(S.a_hi[s]), al = su32(S.a_lo[s]);
 #pragma unroll
         for (int kk = 0; kk < KD / 16; ++kk) {
@@ -284,7 +288,7 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
           }
         }
         mma_commit(&S.empty_a[s]);
-        mma_commit(&S.full_acc[s]);
+        mma_commit(&S.full_acc[b]);
         ++issued;
       }
       // no MMA may still be running when TMEM is released
@@ -295,47 +299,96 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
     __syncwarp();
   } else {
     // ------------------------------------------------------------- epilogue
-    const int r = warp * 32 + lane;
+    // warp e reads TMEM lane quadrant e % 4 (rows 32*(e%4) ..), columns of
+    // half e / 4; four independent running top-2s per thread (columns j mod
+    // 4) keep the compare chains short.
+    const int q = warp & 3, half = warp >> 2;
+    const int r = q * 32 + lane;
     const float eps_sum = TERMS == 3 ? (3.05f * 1.52587890625e-05f + (float)(3 * KD + 8) * 4.76837158203125e-07f)
                                      : (2.f * 3.90625e-03f + 1.52587890625e-05f + (float)(KD + 8) * 4.76837158203125e-07f);
     const float eps32 = 1.01f * (float)(d + 8) * 5.9604644775390625e-08f;
+    const uint32_t c_lo = (uint32_t)half * 128u;
+    const uint32_t c_hi = min(npad, c_lo + 128u);
     for (uint32_t i = 0;; ++i) {
       const uint32_t tile = blockIdx.x + i * gridDim.x;
       if (tile >= ntiles) break;
-      const int s = i & 1;
-      const uint32_t u = i >> 1;
-      const bool ok = mbar_wait(&S.full_acc[s], u & 1, err);
+      const int s = (int)(i % STAGES);
+      const int b = (int)(i & 1);
+      const uint32_t v = i >> 1;
+      const bool ok = mbar_wait(&S.full_acc[b], v & 1, err);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
       const float nxv = S.nx[s][r];
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.nx_free[s]);
-      float d1 = INFINITY, d2 = INFINITY;
-      int k1 = 0x7fffffff;
-      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)s * 256u;
+      float d1[4], d2[4];
+      int k1[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) d1[a] = d2[a] = INFINITY, k1[a] = 0x7fffffff;
+      const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * 256u;
       const uint32_t p = tile * TM + r;
-      for (uint32_t ch = 0; ch < npad; ch += 32) {
+      for (uint32_t ch = c_lo; ch < c_hi; ch += 32) {
         uint32_t acc[32];
         tmem_ld32(ta + ch, acc);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
+          const int a = j & 3;
           const uint32_t kk = ch + j;
-          if (kk < k) {
-            const float dist = fmaf(-2.f, __uint_as_float(acc[j]), nxv) + S.cn[kk];
-            if (dbg && tile == 0) dbg[(uint64_t)r * NMAX + kk] = dist;
-            best2_push(dist, (int)kk, d1, k1, d2);
-          }
+          const float dist = fmaf(-2.f, __uint_as_float(acc[j]), nxv) + S.cn[kk];
+          if (dbg && tile == 0 && kk < k) dbg[(uint64_t)r * NMAX + kk] = dist;
+          const bool lt = dist < d1[a];  // columns increase: the first minimum keeps a tie
+          d2[a] = fminf(d2[a], fmaxf(d1[a], dist));
+          k1[a] = lt ? (int)kk : k1[a];
+          d1[a] = fminf(d1[a], dist);
         }
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&S.empty_acc[s]);
+      if (lane == 0) mbar_arrive(&S.empty_acc[b]);
+#pragma unroll
+      for (int a = 1; a < 4; ++a) {
+        if (d1[a] < d1[0] || (d1[a] == d1[0] && k1[a] < k1[0])) {
+          d2[0] = fminf(d1[0], d2[a]);
+          d1[0] = d1[a];
+          k1[0] = k1[a];
+        } else {
+          d2[0] = fminf(d2[0], d1[a]);
+        }
+      }
+      if (half == 1) {
+        // hand this half's top-2 to the warp of the other half on the same rows
+        if (i >= ACCS) {
+          const bool okf = mbar_wait(&S.xfree[b], (v + 1) & 1, err);
+          if (!__all_sync(0xffffffffu, okf)) break;
+        }
+        S.xd1[b][r] = d1[0];
+        S.xd2[b][r] = d2[0];
+        S.xk1[b][r] = k1[0];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.xfull[b]);
+        continue;
+      }
+      {
+        const bool okx = mbar_wait(&S.xfull[b], v & 1, err);
+        if (!__all_sync(0xffffffffu, okx)) break;
+        const float e1 = S.xd1[b][r], e2 = S.xd2[b][r];
+        const int f1 = S.xk1[b][r];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.xfree[b]);
+        if (e1 < d1[0] || (e1 == d1[0] && f1 < k1[0])) {
+          d2[0] = fminf(d1[0], e2);
+          d1[0] = e1;
+          k1[0] = f1;
+        } else {
+          d2[0] = fminf(d2[0], e1);
+        }
+      }
       bool flag = false;
       if (p < n) {
         const float xn = sqrtf(nxv);
         const float e = 2.f * eps_sum * xn * cmax + eps32 * (xn + cmax) * (xn + cmax);
-        const float thr = fmaxf(1e-3f * fabsf(d1), 2.f * e);
-        if (d2 - d1 > thr) assign[p] = k1;
+        const float thr = fmaxf(1e-3f * fabsf(d1[0]), 2.f * e);
+        if (d2[0] - d1[0] > thr) assign[p] = k1[0];
         else flag = true;
       }
       const unsigned fm = __ballot_sync(0xffffffffu, flag);

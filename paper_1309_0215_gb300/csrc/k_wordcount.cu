@@ -2,298 +2,98 @@
 //
 // Map (Sec. II-A): a token is a maximal run of bytes that are not ASCII
 // whitespace; each emits (token, 1).  Reduce: sum.  Output ordered by count
-// descending, then key bytes ascending.
+// descending, then key bytes ascending (Sec. II-A "ordered (optional)").
 //
 // GB300 design
-//  * Split (Sec. II-A, Fig. 1): the input is cut into 512-byte segments; a warp
-//    owns the tokens whose FIRST byte lies in its segment and reads past the
-//    segment end to finish them.  A warp stages its segment (+64-byte halo)
-//    in shared memory with coalesced 128-bit loads.
-//  * Token boundaries: each lane classifies its 16 bytes and builds a 16-bit
-//    token-start mask; a warp prefix sum of the mask popcounts compacts all
-//    starts of the segment into a list, and lanes then take tokens from the
-//    list 32 at a time.  This is the GPU form of the paper's SIMD hashing
-//    (Sec. III-C): lanes are SIMD units, and a lane that finishes a token takes
-//    the next one from the list instead of idling, as in SIMDH-Stream; the
-//    prefix sum plays the role of the paper's prefix-sum lookup table.
-//  * Hash: FNV-1a 64 (the paper's Listing 2 shape: a byte-at-a-time update
-//    loop, with FNV as one of its two example functions), followed by a 64-bit
-//    finaliser so low and high bits are both usable.
-//  * Combiner / local container (Sec. III-A; bounded local table of Sec.
-//    III-D): each warp owns a 256-slot hash table in shared memory; every
-//    token is combined into it at once.  Keys of <= 16 bytes are held in the
-//    slot as two packed words, so equality needs no memory reads.  When the
-//    table is half full it is flushed (partitioned by the global table's hash)
-//    into the global container, as the paper's map workers hand full local
-//    tables to the reduce side.
-//  * Global container: open addressing with linear probing.  A slot's key word
-//    (length << 40 | offset + 1) is claimed with one 64-bit CAS and never
-//    changes afterwards; the key bytes are the token's bytes in the resident,
-//    immutable input, so a reader that sees a non-zero word can compare keys
-//    at once (no BUSY state, no publish race).  Counts combine in place with
-//    64-bit atomicAdd.  Probing is bounded; running out of probes raises an
-//    overflow flag and the host re-runs the job with a larger table.
-//  * Merge + sort (Sec. II-A "ordered (optional)"): occupied slots are
-//    compacted, sorted by (count desc, key asc) with a shared-memory bitonic
-//    block sort plus merge-path passes, and gathered into the result layout
-//    {u64 n, u64 key bytes; n x {u64 count, u64 key_off, u64 key_len}; keys}.
+//  * Split (Sec. II-A, Fig. 1): 512-byte segments; a warp owns the tokens
+//    whose FIRST byte lies in its segment and reads past the segment end to
+//    finish them.  The segment (+64-byte halo) is staged in shared memory
+//    with coalesced 128-bit loads.
+//  * Token boundaries: each lane classifies its 16 bytes with SIMD-within-a-
+//    register byte compares; a warp prefix sum over the per-lane start masks
+//    lists every token start of the segment, and lanes take tokens from the
+//    list 32 at a time — the GPU form of the paper's SIMD hashing (Sec.
+//    III-C): lanes are the SIMD units and a lane that finishes a token takes
+//    the next one from the list (as SIMDH-Stream refills a lane), the warp
+//    prefix sum replacing the paper's prefix-sum lookup table.  A short token
+//    is read as 16 bytes at once and becomes its own 128-bit key.
+//  * Combiner / local container (Sec. III-A, Sec. III-D): a 256-slot table per
+//    warp in shared memory, flushed into the global container when half full
+//    (the paper's bounded local table handed to the reduce side).
+//  * Global container: open addressing with a 128-bit CAS per new key and an
+//    atomicAdd per combine (see dev_wordcount.cuh).
+//  * Merge + sort: occupied slots of every job are compacted into one record
+//    array and sorted once by (job, count desc, key asc) — a shared-memory
+//    bitonic sort of 2048-record blocks, then merge passes whose split points
+//    come from a warp-cooperative 33-way search and whose inputs are staged in
+//    shared memory — so a batch
+//    of jobs is ordered by a single launch sequence; per-job boundaries and a
+//    scan of key lengths place each job's records and key bytes in its
+//    result: {u64 n, u64 key bytes; n x {u64 count, u64 key_off, u64 key_len};
+//    key bytes}.
 #include "mr_internal.h"
+#include "dev_wordcount.cuh"
 
 namespace mrgb {
 namespace {
 
-constexpr int WC_WARPS = 8;
-constexpr int WC_THREADS = WC_WARPS * 32;
-constexpr int SEG = 512;
-constexpr int HALO = 64;
-constexpr int LT = 256;                 // local slots per warp
-constexpr int LT_FLUSH_AT = LT / 2;     // flush before a round when occupancy >= this
-constexpr uint64_t OFF_MASK = (1ull << 40) - 1;
-constexpr uint32_t LEN_SAT = (1u << 24) - 1;
-constexpr int MAX_PROBES = 4096;
-constexpr uint64_t FNV_OFFSET = 0xcbf29ce484222325ull;
-constexpr uint64_t FNV_PRIME = 0x100000001b3ull;
+using wc::JobDev;
+using wc::WarpLocal;
 
-struct WarpSmem {
-  unsigned long long h[LT];
-  unsigned long long off[LT];
-  unsigned long long k0[LT];
-  unsigned long long k1[LT];
-  uint32_t len[LT];
-  uint32_t cnt[LT];
-  uint8_t buf[SEG + HALO];
-  uint16_t starts[SEG / 2];
-};
+constexpr int MAP_WARPS = 8;
+constexpr int MAP_THREADS = MAP_WARPS * 32;
+constexpr int CB = 1024;            // records per compaction / sort / scan block
+constexpr uint64_t CNT_MAX = (1ull << 40) - 1;
 
-__device__ __forceinline__ bool is_ws(uint32_t c) { return c == 32u || (c - 9u) < 5u; }
-
-__device__ __forceinline__ uint64_t fmix64(uint64_t k) {
-  k ^= k >> 33; k *= 0xff51afd7ed558ccdull;
-  k ^= k >> 33; k *= 0xc4ceb9fe1a85ec53ull;
-  k ^= k >> 33;
-  return k;
+__device__ __forceinline__ JobDev job_at(const JobDev* jobs, const JobDev& single, uint32_t j) {
+  return jobs ? jobs[j] : single;
 }
 
-struct Tok {
-  uint64_t h, off, k0, k1;
-  uint32_t len;
-};
-
-// Read the token that starts at segment-relative byte r.
-__device__ __forceinline__ Tok read_token(const uint8_t* __restrict__ in, uint64_t n, uint64_t base,
-                                          const uint8_t* buf, uint32_t bufn, uint32_t r) {
-  Tok t;
-  t.off = base + r;
-  uint64_t h = FNV_OFFSET, k0 = 0, k1 = 0;
-  uint32_t len = 0;
-  for (;;) {
-    uint32_t c;
-    if (r < bufn) {
-      c = buf[r];
-    } else {
-      uint64_t gi = base + r;
-      if (gi >= n) break;
-      c = in[gi];
-    }
-    if (is_ws(c)) break;
-    h = (h ^ c) * FNV_PRIME;
-    if (len < 8) k0 |= (uint64_t)c << (8 * len);
-    else if (len < 16) k1 |= (uint64_t)c << (8 * (len - 8));
-    ++len;
-    ++r;
-  }
-  h = fmix64(h);
-  t.h = h ? h : 1;
-  t.k0 = k0;
-  t.k1 = k1;
-  t.len = len;
-  return t;
-}
-
-// Do the tokens at offsets a and b (b's length len) have equal bytes?
-__device__ bool tok_equal_global(const uint8_t* __restrict__ in, uint64_t n, uint64_t a, uint64_t b, uint32_t len) {
-  if (a == b) return true;
-  if (a + len > n) return false;
-  for (uint32_t i = 0; i < len; ++i)
-    if (in[a + i] != in[b + i]) return false;
-  return a + len == n || is_ws(in[a + len]);
-}
-
-__device__ void global_insert(const uint8_t* __restrict__ in, uint64_t n, unsigned long long* gkey,
-                              unsigned long long* gcnt, uint64_t cap, uint32_t* state, uint64_t h, uint64_t off,
-                              uint32_t len, uint64_t cnt) {
-  const uint32_t lsat = len < LEN_SAT ? len : LEN_SAT;
-  const unsigned long long mine = ((unsigned long long)lsat << 40) | (off + 1);
-  uint64_t slot = (h >> 20) & (cap - 1);
-  for (int p = 0; p < MAX_PROBES; ++p) {
-    unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(gkey + slot);
-    if (w == 0) {
-      unsigned long long prev = atomicCAS(gkey + slot, 0ull, mine);
-      if (prev == 0) {
-        atomicAdd(gcnt + slot, (unsigned long long)cnt);
-        return;
-      }
-      w = prev;
-    }
-    if ((uint32_t)(w >> 40) == lsat && tok_equal_global(in, n, (w & OFF_MASK) - 1, off, len)) {
-      atomicAdd(gcnt + slot, (unsigned long long)cnt);
-      return;
-    }
-    slot = (slot + 1) & (cap - 1);
-  }
-  atomicOr(state, 1u);  // overflow: the host re-runs with a larger table
-}
-
-__device__ __forceinline__ bool local_equal(const WarpSmem& S, int slot, const Tok& t, const uint8_t* __restrict__ in,
-                                            uint64_t n) {
-  if (S.h[slot] != t.h || S.len[slot] != t.len) return false;
-  if (t.len <= 16) return S.k0[slot] == t.k0 && S.k1[slot] == t.k1;
-  return tok_equal_global(in, n, S.off[slot], t.off, t.len);
-}
-
-// Warp-synchronous combine of one token per active lane into the warp's
-// local table.  occ (warp-uniform) counts occupied slots.
-__device__ __forceinline__ void local_insert(WarpSmem& S, bool active, const Tok& t, int& occ,
-                                             const uint8_t* __restrict__ in, uint64_t n) {
-  const int lane = threadIdx.x & 31;
-  int slot = (int)(t.h & (LT - 1));
-  bool pending = active;
-  while (__any_sync(0xffffffffu, pending)) {
-    bool empty = false, match = false;
-    if (pending) {
-      if (S.h[slot] == 0) empty = true;
-      else match = local_equal(S, slot, t, in, n);
-    }
-    if (match) {
-      atomicAdd(&S.cnt[slot], 1u);
-      pending = false;
-    }
-    const unsigned em = __ballot_sync(0xffffffffu, empty);
-    bool claimed = false;
-    if (empty) {
-      // lanes that found the same empty slot: the lowest one claims it
-      const unsigned grp = __match_any_sync(em, slot);
-      claimed = lane == __ffs(grp) - 1;
-      if (claimed) {
-        S.h[slot] = t.h;
-        S.off[slot] = t.off;
-        S.k0[slot] = t.k0;
-        S.k1[slot] = t.k1;
-        S.len[slot] = t.len;
-        S.cnt[slot] = 0;
-      }
-    }
-    occ += __popc(__ballot_sync(0xffffffffu, claimed));
-    __syncwarp();
-    if (pending && !empty && !match) slot = (slot + 1) & (LT - 1);
-  }
-}
-
-__device__ void local_flush(WarpSmem& S, int& occ, const uint8_t* __restrict__ in, uint64_t n,
-                            unsigned long long* gkey, unsigned long long* gcnt, uint64_t cap, uint32_t* state) {
-  const int lane = threadIdx.x & 31;
-  for (int s = lane; s < LT; s += 32) {
-    if (S.h[s] != 0) {
-      global_insert(in, n, gkey, gcnt, cap, state, S.h[s], S.off[s], S.len[s], S.cnt[s]);
-      S.h[s] = 0;
-    }
-  }
-  __syncwarp();
-  occ = 0;
-}
-
-__global__ void __launch_bounds__(WC_THREADS, 2)
-wc_map_kernel(const uint8_t* __restrict__ in, uint64_t n, unsigned long long* gkey, unsigned long long* gcnt,
-              uint64_t cap, uint32_t* state) {
+__global__ void __launch_bounds__(MAP_THREADS, 3) wc_map_kernel(JobDev J) {
   extern __shared__ __align__(16) unsigned char wc_smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  WarpSmem& S = reinterpret_cast<WarpSmem*>(wc_smem)[warp];
-  for (int i = lane; i < LT; i += 32) S.h[i] = 0;
-  __syncwarp();
+  WarpLocal& L = reinterpret_cast<WarpLocal*>(wc_smem)[threadIdx.x >> 5];
+  wc::local_clear(L);
   int occ = 0;
-  const uint64_t nseg = (n + SEG - 1) / SEG;
-  const uint64_t gw = (uint64_t)blockIdx.x * WC_WARPS + warp;
-  const uint64_t nw = (uint64_t)gridDim.x * WC_WARPS;
-  const bool aligned = ((uintptr_t)in & 15) == 0;
-  for (uint64_t seg = gw; seg < nseg; seg += nw) {
-    const uint64_t base = seg * SEG;
-    const uint64_t rem = n - base;
-    const uint32_t bufn = rem < (uint64_t)(SEG + HALO) ? (uint32_t)rem : (uint32_t)(SEG + HALO);
-    if (aligned && bufn == SEG + HALO) {
-      const uint4* src = reinterpret_cast<const uint4*>(in + base);
-      reinterpret_cast<uint4*>(S.buf)[lane] = src[lane];
-      if (lane < HALO / 16) reinterpret_cast<uint4*>(S.buf)[32 + lane] = src[32 + lane];
-    } else {
-      for (uint32_t r = lane; r < bufn; r += 32) S.buf[r] = in[base + r];
-    }
-    __syncwarp();
-    // token-start mask of this lane's 16 bytes
-    uint32_t mask = 0;
-    {
-      const uint32_t r0 = lane * 16;
-      bool pws;
-      if (r0 == 0) pws = (base == 0) ? true : is_ws(in[base - 1]);
-      else pws = (r0 - 1 < bufn) ? is_ws(S.buf[r0 - 1]) : true;
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const uint32_t r = r0 + j;
-        if (r < bufn) {
-          const bool w = is_ws(S.buf[r]);
-          if (!w && pws) mask |= 1u << j;
-          pws = w;
-        }
-      }
-    }
-    const int c = __popc(mask);
-    int incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    {
-      int o = incl - c;
-      uint32_t m = mask;
-      while (m) {
-        const int j = __ffs(m) - 1;
-        S.starts[o++] = (uint16_t)(lane * 16 + j);
-        m &= m - 1;
-      }
-    }
-    __syncwarp();
-    for (int r0 = 0; r0 < total; r0 += 32) {
-      if (occ >= LT_FLUSH_AT) local_flush(S, occ, in, n, gkey, gcnt, cap, state);
-      const int i = r0 + lane;
-      const bool active = i < total;
-      Tok t;
-      if (active) t = read_token(in, n, base, S.buf, bufn, S.starts[i]);
-      else t.h = 0, t.off = 0, t.k0 = 0, t.k1 = 0, t.len = 0;
-      local_insert(S, active, t, occ, in, n);
-    }
-    __syncwarp();
-  }
-  local_flush(S, occ, in, n, gkey, gcnt, cap, state);
+  const uint64_t nseg = (J.n + wc::SEG - 1) / wc::SEG;
+  const uint64_t gw = (uint64_t)blockIdx.x * MAP_WARPS + (threadIdx.x >> 5);
+  const uint64_t nw = (uint64_t)gridDim.x * MAP_WARPS;
+  for (uint64_t seg = gw; seg < nseg; seg += nw) wc::warp_segment(J, seg, L, occ);
+  wc::local_flush(L, occ, J);
 }
 
 // ------------------------------------------------------------------ sort
 struct SortRec {
-  unsigned long long nc;   // ~count  (ascending nc = descending count)
-  unsigned long long s0;   // key bytes 0..7, big-endian, zero padded
-  unsigned long long s1;   // key bytes 8..15
-  uint32_t len;
-  uint32_t idx;            // index into the offsets array
+  unsigned long long key1;  // job << 40 | (2^40 - 1 - count): ascending = job, then count descending
+  unsigned long long s0;    // key bytes 0..7, big-endian, zero padded
+  unsigned long long s1;    // key bytes 8..15
+  uint32_t len;             // key length (saturated at 2^32 - 1)
+  uint32_t idx;             // index of the record's source offset (long keys)
 };
 static_assert(sizeof(SortRec) == 32, "SortRec layout");
 
-__device__ __forceinline__ bool rec_less(const SortRec& a, const SortRec& b, const uint8_t* __restrict__ in,
-                                         const unsigned long long* offs) {
-  if (a.nc != b.nc) return a.nc < b.nc;
+struct Post {
+  SortRec* r0;
+  SortRec* r1;
+  unsigned long long* src;   // [R] input offset of a long key
+  unsigned long long* excl;  // [R] exclusive scan of key lengths in sorted order
+  unsigned long long* bsum;  // [ceil(R / CB)]
+  unsigned long long* glob;  // [0] number of records
+};
+
+__device__ __forceinline__ uint64_t bswap64(uint64_t v) {
+  const uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+  return ((uint64_t)__byte_perm(lo, 0, 0x0123) << 32) | __byte_perm(hi, 0, 0x0123);
+}
+
+__device__ bool rec_less(const SortRec& a, const SortRec& b, const JobDev* jobs, const JobDev& single,
+                         const unsigned long long* src) {
+  if (a.key1 != b.key1) return a.key1 < b.key1;
   if (a.s0 != b.s0) return a.s0 < b.s0;
   if (a.s1 != b.s1) return a.s1 < b.s1;
   if (a.len <= 16 || b.len <= 16) return a.len < b.len;
-  // both longer than 16 bytes with the same first 16: compare the rest
-  const uint64_t oa = offs[a.idx], ob = offs[b.idx];
+  // both longer than 16 bytes with the same first 16 (same job): compare on
+  const uint8_t* in = job_at(jobs, single, (uint32_t)(a.key1 >> 40)).in;
+  const uint64_t oa = src[a.idx], ob = src[b.idx];
   const uint32_t m = a.len < b.len ? a.len : b.len;
   for (uint32_t i = 16; i < m; ++i) {
     const uint8_t ca = in[oa + i], cb = in[ob + i];
@@ -302,10 +102,17 @@ __device__ __forceinline__ bool rec_less(const SortRec& a, const SortRec& b, con
   return a.len < b.len;
 }
 
-constexpr int CB = 1024;  // compaction / block-sort / scan block size (records)
+__device__ __forceinline__ uint32_t find_job_by_block(const JobDev* jobs, uint32_t njobs, uint64_t b) {
+  uint32_t lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].blk0 <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
 
 __device__ __forceinline__ int block_excl_scan(int v, int* tmp, int& total) {
-  // blockDim.x == 1024 assumed by callers
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int incl = v;
 #pragma unroll
@@ -316,7 +123,7 @@ __device__ __forceinline__ int block_excl_scan(int v, int* tmp, int& total) {
   if (lane == 31) tmp[warp] = incl;
   __syncthreads();
   if (warp == 0) {
-    int w = tmp[lane];
+    const int w = tmp[lane];
     int wi = w;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -333,131 +140,196 @@ __device__ __forceinline__ int block_excl_scan(int v, int* tmp, int& total) {
   return r;
 }
 
-__global__ void __launch_bounds__(CB)
-wc_compact_kernel(const uint8_t* __restrict__ in, uint64_t n, const unsigned long long* gkey,
-                  const unsigned long long* gcnt, uint64_t cap, uint32_t* state, SortRec* recs,
-                  unsigned long long* offs) {
+// Occupied slots of every job -> records.  Block b belongs to the job whose
+// block range contains b.  The first block of a job also zeroes the job's
+// result header (a job with no records keeps {0, 0}).
+__global__ void __launch_bounds__(CB) wc_compact_kernel(const JobDev* jobs, JobDev single, uint32_t njobs, Post P) {
   __shared__ int tmp[33];
-  __shared__ uint32_t blk_base;
-  const uint64_t s = (uint64_t)blockIdx.x * CB + threadIdx.x;
-  const unsigned long long w = s < cap ? gkey[s] : 0ull;
+  __shared__ unsigned long long blk_base;
+  const uint32_t j = jobs ? find_job_by_block(jobs, njobs, blockIdx.x) : 0;
+  const JobDev J = job_at(jobs, single, j);
+  const uint64_t slot = ((uint64_t)blockIdx.x - J.blk0) * CB + threadIdx.x;
+  if (blockIdx.x == J.blk0 && threadIdx.x < 2) reinterpret_cast<unsigned long long*>(J.out)[threadIdx.x] = 0;
+  uint64_t w0 = 0, w1 = 0;
+  if (slot < J.cap) {
+    w0 = J.key[2 * slot];
+    w1 = J.key[2 * slot + 1];
+  }
+  const bool occ = w1 != 0;
   int total;
-  const int r = block_excl_scan(w != 0, tmp, total);
-  if (threadIdx.x == 0) blk_base = total ? atomicAdd(state + 1, (uint32_t)total) : 0u;
+  const int r = block_excl_scan(occ ? 1 : 0, tmp, total);
+  if (threadIdx.x == 0) blk_base = total ? atomicAdd(P.glob, (unsigned long long)total) : 0ull;
   __syncthreads();
-  if (w == 0) return;
-  const uint32_t i = blk_base + (uint32_t)r;
-  const uint64_t off = (w & OFF_MASK) - 1;
-  uint32_t len = (uint32_t)(w >> 40);
-  if (len == LEN_SAT) {
-    uint64_t e = off + len;
-    while (e < n && !is_ws(in[e])) ++e;
-    len = (uint32_t)(e - off);
-  }
-  unsigned long long s0 = 0, s1 = 0;
-  const uint32_t l16 = len < 16 ? len : 16;
-  for (uint32_t j = 0; j < l16; ++j) {
-    const unsigned long long b = in[off + j];
-    if (j < 8) s0 |= b << (56 - 8 * j);
-    else s1 |= b << (56 - 8 * (j - 8));
-  }
+  if (!occ) return;
+  const uint64_t i = blk_base + (uint64_t)r;
+  const uint64_t cnt = J.cnt[slot];
   SortRec rec;
-  rec.nc = ~gcnt[s];
-  rec.s0 = s0;
-  rec.s1 = s1;
-  rec.len = len;
-  rec.idx = i;
-  recs[i] = rec;
-  offs[i] = off;
+  rec.key1 = ((uint64_t)j << 40) | (CNT_MAX - (cnt < CNT_MAX ? cnt : CNT_MAX));
+  rec.idx = (uint32_t)i;
+  if ((w1 >> 56) != 0xFF) {
+    rec.len = (uint32_t)(w1 >> 56);
+    rec.s0 = bswap64(w0);
+    rec.s1 = bswap64(w1 & wc::LEN_MASK);
+    P.src[i] = 0;
+  } else {
+    const uint64_t len = w1 & wc::LEN_MASK;
+    const uint64_t off = w0 - 1;
+    rec.len = len < 0xffffffffull ? (uint32_t)len : 0xffffffffu;
+    uint64_t s0 = 0, s1 = 0;
+    for (int q = 0; q < 16; ++q) {
+      const uint64_t b = J.in[off + q];
+      if (q < 8) s0 |= b << (56 - 8 * q);
+      else s1 |= b << (56 - 8 * (q - 8));
+    }
+    rec.s0 = s0;
+    rec.s1 = s1;
+    P.src[i] = off;
+  }
+  P.r0[i] = rec;
 }
 
-__global__ void __launch_bounds__(512)
-wc_blocksort_kernel(SortRec* recs, const uint32_t* state, const uint8_t* __restrict__ in,
-                    const unsigned long long* offs) {
-  __shared__ SortRec sh[CB];
-  const uint32_t m = state[1];
-  const uint64_t b0 = (uint64_t)blockIdx.x * CB;
+// Block sort: SB records per CTA, bitonic network in shared memory.
+constexpr int SB = 2048;
+constexpr int SB_THREADS = 1024;
+
+__global__ void __launch_bounds__(SB_THREADS) wc_blocksort_kernel(const JobDev* jobs, JobDev single, Post P) {
+  extern __shared__ __align__(16) unsigned char bs_raw[];
+  SortRec* sh = reinterpret_cast<SortRec*>(bs_raw);
+  const uint64_t m = *P.glob;
+  const uint64_t b0 = (uint64_t)blockIdx.x * SB;
   if (b0 >= m) return;
-  for (int i = threadIdx.x; i < CB; i += blockDim.x) {
-    if (b0 + i < m) sh[i] = recs[b0 + i];
+  for (int i = threadIdx.x; i < SB; i += blockDim.x) {
+    if (b0 + i < m) sh[i] = P.r0[b0 + i];
     else sh[i] = SortRec{~0ull, ~0ull, ~0ull, 0xffffffffu, 0xffffffffu};
   }
   __syncthreads();
-  for (int k = 2; k <= CB; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      const int t = threadIdx.x;  // 512 threads, one pair each
-      const int lo = 2 * j * (t / j) + (t % j);
-      const int hi = lo + j;
-      const bool up = (lo & k) == 0;
-      SortRec a = sh[lo], b = sh[hi];
-      const bool a_pad = a.idx == 0xffffffffu, b_pad = b.idx == 0xffffffffu;
-      bool b_lt_a;
-      if (a_pad || b_pad) b_lt_a = a_pad && !b_pad;
-      else b_lt_a = rec_less(b, a, in, offs);
-      if (b_lt_a == up) {
-        sh[lo] = b;
-        sh[hi] = a;
+  for (int k = 2; k <= SB; k <<= 1) {
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int t = threadIdx.x; t < SB / 2; t += blockDim.x) {
+        const int lo = 2 * jj * (t / jj) + (t % jj);
+        const int hi = lo + jj;
+        const bool up = (lo & k) == 0;
+        const SortRec a = sh[lo], b = sh[hi];
+        const bool a_pad = a.idx == 0xffffffffu, b_pad = b.idx == 0xffffffffu;
+        bool b_lt_a;
+        if (a_pad || b_pad) b_lt_a = a_pad && !b_pad;
+        else b_lt_a = rec_less(b, a, jobs, single, P.src);
+        if (b_lt_a == up) {
+          sh[lo] = b;
+          sh[hi] = a;
+        }
       }
       __syncthreads();
     }
   }
-  for (int i = threadIdx.x; i < CB; i += blockDim.x)
-    if (b0 + i < m) recs[b0 + i] = sh[i];
+  for (int i = threadIdx.x; i < SB; i += blockDim.x)
+    if (b0 + i < m) P.r0[b0 + i] = sh[i];
 }
 
-constexpr int MERGE_ITEMS = 8;
+// Number of A records among the first kk outputs of merge(A[0..la), B[0..lb)),
+// found by the whole warp: each step probes 32 evenly spaced positions at once
+// (the "A[i] < B[kk-1-i]" predicate is true on a prefix), shrinking the range
+// about 33-fold, so a search over L records costs ~log_33(L) dependent loads.
+__device__ uint64_t corank_warp(const SortRec* A, uint64_t la, const SortRec* B, uint64_t lb, uint64_t kk,
+                                const JobDev* jobs, const JobDev& single, const unsigned long long* src) {
+  const int lane = threadIdx.x & 31;
+  uint64_t lo = kk > lb ? kk - lb : 0;
+  uint64_t hi = kk < la ? kk : la;
+  while (lo < hi) {
+    const uint64_t span = hi - lo;
+    const uint64_t m = lo + (span * (uint64_t)(lane + 1)) / 33;
+    const bool pr = rec_less(A[m], B[kk - 1 - m], jobs, single, src);
+    const unsigned bal = __ballot_sync(0xffffffffu, pr);
+    const int nt = __popc(bal);
+    const uint64_t mt = __shfl_sync(0xffffffffu, m, nt > 0 ? nt - 1 : 0);
+    const uint64_t mf = __shfl_sync(0xffffffffu, m, nt < 32 ? nt : 31);
+    const uint64_t nlo = nt > 0 ? mt + 1 : lo;
+    const uint64_t nhi = nt < 32 ? mf : hi;
+    lo = nlo;
+    hi = nhi;
+  }
+  return lo;
+}
 
-__global__ void __launch_bounds__(256)
-wc_merge_kernel(const SortRec* __restrict__ src, SortRec* __restrict__ dst, const uint32_t* state, uint64_t L,
-                const uint8_t* __restrict__ in, const unsigned long long* offs) {
-  const uint64_t m = state[1];
-  const uint64_t k0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * MERGE_ITEMS;
-  if (k0 >= m) return;
-  const uint64_t a0 = (k0 / (2 * L)) * (2 * L);
+// One merge pass: runs of L sorted records are merged pairwise.  A CTA owns
+// MTILE consecutive outputs: two warps find where its range starts and ends
+// in the two runs, the CTA stages both input windows in shared memory, and
+// each thread merges MI outputs from there.
+constexpr int MT = 256;
+constexpr int MI = 8;
+constexpr int MTILE = MT * MI;
+
+__global__ void __launch_bounds__(MT) wc_merge_kernel(const SortRec* __restrict__ src, SortRec* __restrict__ dst,
+                                                      uint64_t L, const JobDev* jobs, JobDev single, Post P) {
+  extern __shared__ __align__(16) unsigned char mg_raw[];
+  SortRec* ms = reinterpret_cast<SortRec*>(mg_raw);
+  __shared__ uint64_t cr[2];
+  const uint64_t m = *P.glob;
+  const uint64_t o0 = (uint64_t)blockIdx.x * MTILE;
+  if (o0 >= m) return;
+  const uint64_t a0 = (o0 / (2 * L)) * (2 * L);  // MTILE divides 2L: a tile never spans two pairs
   const uint64_t la = (m - a0) < L ? (m - a0) : L;
   const uint64_t b0 = a0 + L;
   const uint64_t lb = b0 < m ? ((m - b0) < L ? (m - b0) : L) : 0;
   const SortRec* A = src + a0;
   const SortRec* B = src + b0;
-  const uint64_t kk = k0 - a0;
-  uint64_t lo = kk > lb ? kk - lb : 0;
-  uint64_t hi = kk < la ? kk : la;
+  const uint64_t kk0 = o0 - a0;
+  const uint64_t kk1 = (kk0 + MTILE) < la + lb ? kk0 + MTILE : la + lb;
+  if (lb == 0) {  // a lone run: copy
+    for (uint64_t t = kk0 + threadIdx.x; t < kk1; t += MT) dst[a0 + t] = A[t];
+    return;
+  }
+  const int warp = threadIdx.x >> 5;
+  if (warp < 2) {
+    const uint64_t kk = warp == 0 ? kk0 : kk1;
+    const uint64_t c = corank_warp(A, la, B, lb, kk, jobs, single, P.src);
+    if ((threadIdx.x & 31) == 0) cr[warp] = c;
+  }
+  __syncthreads();
+  const uint64_t i0 = cr[0], i1 = cr[1];
+  const uint32_t na = (uint32_t)(i1 - i0);
+  const uint32_t nb = (uint32_t)((kk1 - i1) - (kk0 - i0));
+  for (uint32_t t = threadIdx.x; t < na; t += MT) ms[t] = A[i0 + t];
+  for (uint32_t t = threadIdx.x; t < nb; t += MT) ms[na + t] = B[kk0 - i0 + t];
+  __syncthreads();
+  const SortRec* sa = ms;
+  const SortRec* sb = ms + na;
+  const uint32_t r0 = threadIdx.x * MI;
+  const uint32_t tot = na + nb;
+  if (r0 >= tot) return;
+  uint32_t lo = r0 > nb ? r0 - nb : 0, hi = r0 < na ? r0 : na;
   while (lo < hi) {
-    const uint64_t mid = (lo + hi) >> 1;
-    if (rec_less(A[mid], B[kk - 1 - mid], in, offs)) lo = mid + 1;
+    const uint32_t mid = (lo + hi) >> 1;
+    if (rec_less(sa[mid], sb[r0 - 1 - mid], jobs, single, P.src)) lo = mid + 1;
     else hi = mid;
   }
-  uint64_t i = lo, j = kk - lo;
-  const uint64_t end = a0 + la + lb;
-  for (int t = 0; t < MERGE_ITEMS && k0 + t < end; ++t) {
+  uint32_t i = lo, j = r0 - lo;
+  for (int t = 0; t < MI && r0 + t < tot; ++t) {
     bool takeA;
-    if (j >= lb) takeA = true;
-    else if (i >= la) takeA = false;
-    else takeA = rec_less(A[i], B[j], in, offs);
-    dst[k0 + t] = takeA ? A[i++] : B[j++];
+    if (j >= nb) takeA = true;
+    else if (i >= na) takeA = false;
+    else takeA = rec_less(sa[i], sb[j], jobs, single, P.src);
+    dst[o0 + r0 + t] = takeA ? sa[i++] : sb[j++];
   }
 }
 
-// Sum of key lengths per block of CB sorted records.
-__global__ void __launch_bounds__(CB)
-wc_lensum_kernel(const SortRec* recs, const uint32_t* state, unsigned long long* bsum) {
-  const uint32_t m = state[1];
+__global__ void __launch_bounds__(CB) wc_lensum_kernel(const SortRec* recs, Post P) {
+  __shared__ unsigned long long ws[32];
+  const uint64_t m = *P.glob;
   const uint64_t i = (uint64_t)blockIdx.x * CB + threadIdx.x;
   unsigned long long v = i < m ? recs[i].len : 0;
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __shared__ unsigned long long ws[32];
   if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long s = 0;
     for (int w = 0; w < 32; ++w) s += ws[w];
-    bsum[blockIdx.x] = s;
+    P.bsum[blockIdx.x] = s;
   }
 }
 
-// Exclusive scan of the block sums (one CTA) and the result header.
-__global__ void __launch_bounds__(CB)
-wc_bscan_kernel(unsigned long long* bsum, uint64_t nb, const uint32_t* state, unsigned long long* out_hdr) {
+// exclusive scan of the block sums (one CTA)
+__global__ void __launch_bounds__(CB) wc_bscan_kernel(Post P, uint64_t nb) {
   __shared__ unsigned long long carry;
   __shared__ unsigned long long wsum[32];
   if (threadIdx.x == 0) carry = 0;
@@ -465,7 +337,7 @@ wc_bscan_kernel(unsigned long long* bsum, uint64_t nb, const uint32_t* state, un
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint64_t b = 0; b < nb; b += CB) {
     const uint64_t i = b + threadIdx.x;
-    const unsigned long long v = i < nb ? bsum[i] : 0;
+    const unsigned long long v = i < nb ? P.bsum[i] : 0;
     unsigned long long incl = v;
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
@@ -483,28 +355,22 @@ wc_bscan_kernel(unsigned long long* bsum, uint64_t nb, const uint32_t* state, un
       wsum[lane] = wi - w;
     }
     __syncthreads();
-    const unsigned long long excl = carry + wsum[warp] + incl - v;
-    if (i < nb) bsum[i] = excl;
+    const unsigned long long ex = carry + wsum[warp] + incl - v;
+    if (i < nb) P.bsum[i] = ex;
     __syncthreads();
-    if (threadIdx.x == CB - 1) carry = excl + v;
+    if (threadIdx.x == CB - 1) carry = ex + v;
     __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    out_hdr[0] = state[1];
-    out_hdr[1] = carry;
   }
 }
 
-// Write the records and copy the key bytes.
-__global__ void __launch_bounds__(CB)
-wc_gather_kernel(const SortRec* recs, const uint32_t* state, const unsigned long long* bsum,
-                 const uint8_t* __restrict__ in, const unsigned long long* offs, uint8_t* out) {
-  const uint32_t m = state[1];
+// Exclusive length scan per record; each job's first / end record and the
+// scan at both are stored in the job's state as 64-bit fields 1..4.
+__global__ void __launch_bounds__(CB) wc_bounds_kernel(const SortRec* recs, const JobDev* jobs, JobDev single, Post P) {
+  __shared__ unsigned long long wsum[32];
+  const uint64_t m = *P.glob;
   const uint64_t i = (uint64_t)blockIdx.x * CB + threadIdx.x;
   if ((uint64_t)blockIdx.x * CB >= m) return;
   const uint32_t len = i < m ? recs[i].len : 0;
-  // block-exclusive scan of lengths in 64-bit
-  __shared__ unsigned long long wsum[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned long long incl = len;
   for (int o = 1; o < 32; o <<= 1) {
@@ -524,86 +390,172 @@ wc_gather_kernel(const SortRec* recs, const uint32_t* state, const unsigned long
   }
   __syncthreads();
   if (i >= m) return;
+  const unsigned long long ex = P.bsum[blockIdx.x] + wsum[warp] + incl - len;
+  P.excl[i] = ex;
+  const uint32_t j = (uint32_t)(recs[i].key1 >> 40);
+  const bool first = i == 0 || (uint32_t)(recs[i - 1].key1 >> 40) != j;
+  const bool last = i + 1 == m || (uint32_t)(recs[i + 1].key1 >> 40) != j;
+  unsigned long long* st = reinterpret_cast<unsigned long long*>(job_at(jobs, single, j).state);
+  if (first) {
+    st[1] = i;
+    st[2] = ex;
+  }
+  if (last) {
+    st[3] = i + 1;
+    st[4] = ex + len;
+  }
+}
+
+// Records and key bytes into each job's result.
+__global__ void __launch_bounds__(256) wc_gather_kernel(const SortRec* recs, const JobDev* jobs, JobDev single, Post P) {
+  const uint64_t m = *P.glob;
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
   const SortRec r = recs[i];
-  const unsigned long long koff = bsum[blockIdx.x] + wsum[warp] + incl - len;
-  unsigned long long* rec = reinterpret_cast<unsigned long long*>(out + 16 + 24 * i);
-  rec[0] = ~r.nc;
+  const uint32_t j = (uint32_t)(r.key1 >> 40);
+  const JobDev J = job_at(jobs, single, j);
+  const unsigned long long* st = reinterpret_cast<const unsigned long long*>(J.state);
+  const uint64_t first = st[1], scan0 = st[2], end = st[3], scan1 = st[4];
+  const uint64_t nrec = end - first, li = i - first;
+  unsigned long long* out = reinterpret_cast<unsigned long long*>(J.out);
+  if (li == 0) {
+    out[0] = nrec;
+    out[1] = scan1 - scan0;
+  }
+  const uint64_t koff = P.excl[i] - scan0;
+  unsigned long long* rec = out + 2 + 3 * li;
+  rec[0] = CNT_MAX - (r.key1 & CNT_MAX);
   rec[1] = koff;
-  rec[2] = len;
-  uint8_t* keys = out + 16 + 24 * (uint64_t)m + koff;
-  const uint64_t src = offs[r.idx];
-  for (uint32_t j = 0; j < len; ++j) keys[j] = in[src + j];
+  rec[2] = r.len;
+  uint8_t* keys = J.out + 16 + 24 * nrec + koff;
+  if (r.len <= 15) {
+    for (uint32_t q = 0; q < r.len; ++q)
+      keys[q] = (uint8_t)(q < 8 ? r.s0 >> (56 - 8 * q) : r.s1 >> (56 - 8 * (q - 8)));
+  } else {
+    const uint8_t* s = J.in + P.src[r.idx];
+    for (uint32_t q = 0; q < r.len; ++q) keys[q] = s[q];
+  }
+}
+
+inline uint64_t a256(uint64_t x) { return (x + 255) & ~255ull; }
+
+Post carve_post(uint8_t* p, uint64_t R) {
+  Post P;
+  P.glob = reinterpret_cast<unsigned long long*>(p);
+  p += 256;
+  P.r0 = reinterpret_cast<SortRec*>(p);
+  p += a256(R * sizeof(SortRec));
+  P.r1 = reinterpret_cast<SortRec*>(p);
+  p += a256(R * sizeof(SortRec));
+  P.src = reinterpret_cast<unsigned long long*>(p);
+  p += a256(R * 8);
+  P.excl = reinterpret_cast<unsigned long long*>(p);
+  p += a256(R * 8);
+  P.bsum = reinterpret_cast<unsigned long long*>(p);
+  return P;
+}
+
+uint32_t ilog2(uint64_t x) {
+  uint32_t l = 0;
+  while ((1ull << l) < x) ++l;
+  return l;
 }
 
 }  // namespace
 
-size_t wc_sortbuf_bytes(uint64_t cap) {
-  const uint64_t nb = (cap + CB - 1) / CB;
-  return 2 * cap * sizeof(SortRec) + cap * sizeof(unsigned long long) + nb * sizeof(unsigned long long) + 256;
+uint64_t wc_table_bytes(uint64_t cap) { return cap * 24; }
+uint64_t wc_state_bytes() { return 64; }
+
+size_t wc_sortbuf_bytes(uint64_t R) {
+  const uint64_t nb = (R + CB - 1) / CB;
+  return 256 + 2 * a256(R * sizeof(SortRec)) + 2 * a256(R * 8) + a256(nb * 8);
 }
 
 uint64_t wc_out_bytes(uint64_t cap, uint64_t n) {
-  // at most min(cap, n/1 tokens) records; key bytes never exceed n
+  // at most cap records; key bytes never exceed the input
   return 16 + 24 * cap + n;
 }
 
-cudaError_t launch_wordcount(const uint8_t* in, uint64_t n, const WcBuffers& b, const DevInfo& di, cudaStream_t s,
-                             uint64_t* nk) {
-  cudaError_t e;
-  // table: key and count arrays are contiguous (key then cnt)
-  if ((e = cudaMemsetAsync(b.key, 0, 2 * b.cap * sizeof(uint64_t), s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(b.state, 0, 4 * sizeof(uint32_t), s)) != cudaSuccess) return e;
-  unsigned long long* gkey = reinterpret_cast<unsigned long long*>(b.key);
-  unsigned long long* gcnt = reinterpret_cast<unsigned long long*>(b.cnt);
-  if (n > 0) {
-    const int smem = WC_WARPS * (int)sizeof(WarpSmem);
-    if ((e = cudaFuncSetAttribute(wc_map_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
-      return e;
-    const uint64_t nseg = (n + SEG - 1) / SEG;
-    uint64_t grid = (nseg + WC_WARPS - 1) / WC_WARPS;
-    const uint64_t gmax = 2ull * di.sms;
-    if (grid > gmax) grid = gmax;
-    wc_map_kernel<<<(unsigned)grid, WC_THREADS, smem, s>>>(in, n, gkey, gcnt, b.cap, b.state);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    ++*nk;
-  }
-  return launch_wordcount_post(in, n, b, s, nk);
+int wc_map_smem_bytes() { return MAP_WARPS * (int)sizeof(WarpLocal); }
+
+wc::JobDev wc_job_dev(const uint8_t* in, uint64_t n, const WcBuffers& b, uint64_t blk0) {
+  JobDev J;
+  J.in = in;
+  J.n = n;
+  J.key = reinterpret_cast<unsigned long long*>(b.key);
+  J.cnt = reinterpret_cast<unsigned long long*>(b.cnt);
+  J.cap = b.cap;
+  J.log2cap = ilog2(b.cap);
+  J.state = b.state;
+  J.out = b.out;
+  J.blk0 = blk0;
+  return J;
 }
 
-cudaError_t launch_wordcount_post(const uint8_t* in, uint64_t n, const WcBuffers& b, cudaStream_t s, uint64_t* nk) {
+uint64_t wc_compact_blocks(uint64_t cap) { return (cap + CB - 1) / CB; }
+
+cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev& single, uint32_t njobs,
+                                        uint64_t nblocks, uint64_t R, uint8_t* sortbuf, cudaStream_t s,
+                                        uint64_t* nk) {
   cudaError_t e;
-  (void)n;
-  unsigned long long* gkey = reinterpret_cast<unsigned long long*>(b.key);
-  unsigned long long* gcnt = reinterpret_cast<unsigned long long*>(b.cnt);
-  SortRec* r0 = reinterpret_cast<SortRec*>(b.sortbuf);
-  SortRec* r1 = r0 + b.cap;
-  unsigned long long* offs = reinterpret_cast<unsigned long long*>(r1 + b.cap);
-  unsigned long long* bsum = offs + b.cap;
-  const uint64_t nb = (b.cap + CB - 1) / CB;
-  wc_compact_kernel<<<(unsigned)nb, CB, 0, s>>>(in, n, gkey, gcnt, b.cap, b.state, r0, offs);
+  Post P = carve_post(sortbuf, R);
+  if ((e = cudaMemsetAsync(P.glob, 0, 8, s)) != cudaSuccess) return e;
+  wc_compact_kernel<<<(unsigned)nblocks, CB, 0, s>>>(jobs, single, njobs, P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  wc_blocksort_kernel<<<(unsigned)nb, 512, 0, s>>>(r0, b.state, in, offs);
+  const uint64_t nb = (R + CB - 1) / CB;
+  const int bs_smem = SB * (int)sizeof(SortRec);
+  const int mg_smem = MTILE * (int)sizeof(SortRec);
+  if ((e = cudaFuncSetAttribute(wc_blocksort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bs_smem)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(wc_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mg_smem)) !=
+      cudaSuccess)
+    return e;
+  wc_blocksort_kernel<<<(unsigned)((R + SB - 1) / SB), SB_THREADS, bs_smem, s>>>(jobs, single, P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   *nk += 2;
-  SortRec* src = r0;
-  SortRec* dst = r1;
-  for (uint64_t L = CB; L < b.cap; L *= 2) {
-    const uint64_t threads = (b.cap + MERGE_ITEMS - 1) / MERGE_ITEMS;
-    wc_merge_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(src, dst, b.state, L, in, offs);
+  SortRec* src = P.r0;
+  SortRec* dst = P.r1;
+  for (uint64_t L = SB; L < R; L *= 2) {
+    wc_merge_kernel<<<(unsigned)((R + MTILE - 1) / MTILE), MT, mg_smem, s>>>(src, dst, L, jobs, single, P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ++*nk;
     SortRec* t = src;
     src = dst;
     dst = t;
   }
-  wc_lensum_kernel<<<(unsigned)nb, CB, 0, s>>>(src, b.state, bsum);
+  wc_lensum_kernel<<<(unsigned)nb, CB, 0, s>>>(src, P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  wc_bscan_kernel<<<1, CB, 0, s>>>(bsum, nb, b.state, reinterpret_cast<unsigned long long*>(b.out));
+  wc_bscan_kernel<<<1, CB, 0, s>>>(P, nb);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  wc_gather_kernel<<<(unsigned)nb, CB, 0, s>>>(src, b.state, bsum, in, offs, b.out);
+  wc_bounds_kernel<<<(unsigned)nb, CB, 0, s>>>(src, jobs, single, P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  *nk += 3;
+  wc_gather_kernel<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(src, jobs, single, P);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  *nk += 4;
   return cudaSuccess;
+}
+
+cudaError_t launch_wordcount(const uint8_t* in, uint64_t n, const WcBuffers& b, const DevInfo& di, cudaStream_t s,
+                             uint64_t* nk) {
+  cudaError_t e;
+  // table (keys then counts) and state words start at zero
+  if ((e = cudaMemsetAsync(b.key, 0, wc_table_bytes(b.cap), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(b.state, 0, wc_state_bytes(), s)) != cudaSuccess) return e;
+  const JobDev J = wc_job_dev(in, n, b, 0);
+  if (n > 0) {
+    const int smem = wc_map_smem_bytes();
+    if ((e = cudaFuncSetAttribute(wc_map_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+      return e;
+    const uint64_t nseg = (n + wc::SEG - 1) / wc::SEG;
+    uint64_t grid = (nseg + MAP_WARPS - 1) / MAP_WARPS;
+    const uint64_t gmax = 3ull * di.sms;
+    if (grid > gmax) grid = gmax;
+    wc_map_kernel<<<(unsigned)grid, MAP_THREADS, smem, s>>>(J);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ++*nk;
+  }
+  return launch_wordcount_post_multi(nullptr, J, 1, wc_compact_blocks(b.cap), b.cap, b.sortbuf, s, nk);
 }
 
 }  // namespace mrgb
@@ -617,18 +569,18 @@ cudaError_t launch_wordcount_post(const uint8_t* in, uint64_t n, const WcBuffers
 // and unpredictable cost of cudaMalloc / cudaFree are not acceptable.  For
 // them the hash table and sort scratch of one word-count job live in the
 // file-scope array below, sized for NOALLOC_SLOTS table slots.  Every GPU
-// that loads this library keeps the array (about 11 MiB) until the process
+// that loads this library keeps the array (about 14 MiB) until the process
 // exits.
 #include <mutex>
 
 namespace mrgb {
 namespace {
 constexpr uint64_t NOALLOC_SLOTS = 1ull << 17;
-constexpr uint64_t NOALLOC_TABLE_BYTES = 2 * NOALLOC_SLOTS * 8;
+constexpr uint64_t NOALLOC_TABLE_BYTES = NOALLOC_SLOTS * 24;
 constexpr uint64_t NOALLOC_STATE_BYTES = 256;
-constexpr uint64_t NOALLOC_SORT_BYTES =
-    ((2 * NOALLOC_SLOTS * sizeof(SortRec) + NOALLOC_SLOTS * 8 + ((NOALLOC_SLOTS + CB - 1) / CB) * 8 + 256) + 255) &
-    ~255ull;
+constexpr uint64_t NOALLOC_SORT_BYTES = 256 + 2 * ((NOALLOC_SLOTS * sizeof(SortRec) + 255) & ~255ull) +
+                                        2 * ((NOALLOC_SLOTS * 8 + 255) & ~255ull) +
+                                        ((((NOALLOC_SLOTS + CB - 1) / CB) * 8 + 255) & ~255ull);
 constexpr uint64_t NOALLOC_SCRATCH_BYTES = NOALLOC_TABLE_BYTES + NOALLOC_STATE_BYTES + NOALLOC_SORT_BYTES;
 constexpr int NOALLOC_MAX_DEVICES = 64;
 }  // namespace
@@ -684,7 +636,7 @@ extern "C" mr_status mr_wordcount_noalloc(const void* d_input, uint64_t input_by
   WcBuffers b;
   b.cap = NOALLOC_SLOTS;
   b.key = reinterpret_cast<uint64_t*>(p);
-  b.cnt = b.key + NOALLOC_SLOTS;
+  b.cnt = b.key + 2 * NOALLOC_SLOTS;
   b.state = reinterpret_cast<uint32_t*>(p + NOALLOC_TABLE_BYTES);
   b.sortbuf = p + NOALLOC_TABLE_BYTES + NOALLOC_STATE_BYTES;
   b.out = static_cast<uint8_t*>(d_out);

@@ -2,6 +2,7 @@
 // container planner (paper Sec. III-E automatic detection), plain and batched
 // launch sequencing, result fetch, and HBM-budget admission for serving.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -24,7 +25,7 @@ using namespace mrgb;
 
 namespace {
 
-enum JobState { JOB_PENDING = 0, JOB_ENQUEUED = 1 };
+enum JobState { JOB_PENDING = 0, JOB_ENQUEUED = 1, JOB_SERVE_QUEUED = 2 };
 
 struct Job {
   uint64_t id = 0;
@@ -66,10 +67,35 @@ struct mr_ctx {
   uint64_t next_id = 1;
   std::map<uint64_t, Job*> jobs;
   std::vector<uint64_t> pending;
-  // batched launch scratch
+  // batched launch scratch and the last batch's graph
   void* batch_desc = nullptr;
   uint64_t batch_desc_bytes = 0;
+  void* batch_wc = nullptr;
+  uint64_t batch_wc_bytes = 0;
+  void* batch_sort = nullptr;
+  uint64_t batch_sort_bytes = 0;
   void* batch_cursor = nullptr;
+  cudaGraphExec_t batch_exec = nullptr;
+  std::vector<uint64_t> batch_ids;
+  uint64_t batch_launches = 0;  // kernels per replay of the graph
+  mr_tuning tune{3ull * 1536 * 128, 512ull * 128, 0, 0.f, 0};
+  // serving: continuous batching over a few internal streams ("slots")
+  struct Slot {
+    cudaStream_t s = nullptr;
+    cudaEvent_t busy = nullptr;
+    bool used = false;
+    void* desc = nullptr;
+    uint64_t desc_bytes = 0;
+    void* wcd = nullptr;
+    uint64_t wcd_bytes = 0;
+    void* sort = nullptr;
+    uint64_t sort_bytes = 0;
+    void* cursor = nullptr;
+  };
+  static constexpr int SERVE_SLOTS = 3;
+  Slot slots[SERVE_SLOTS];
+  std::vector<Job*> serve_pending;  // admitted, waiting for a free slot
+  cudaEvent_t serve_ready = nullptr;
 };
 
 namespace {
@@ -135,6 +161,8 @@ mr_container plan_container(const mr_ctx* c, const mr_job_desc* d) {
       return MR_C_HASH;
     case MR_HIST_RGB8:
       if (d->container == MR_C_SMEM_ARRAY || d->container == MR_C_GLOBAL_ARRAY) return d->container;
+      // small jobs cannot amortise zeroing and merging a CTA's local arrays
+      if (d->input_bytes < c->tune.hist_global_below) return MR_C_GLOBAL_ARRAY;
       return hist_smem_bytes() <= c->di.smem_optin ? MR_C_SMEM_ARRAY : MR_C_GLOBAL_ARRAY;
     case MR_LINREG_I8:
     case MR_KMEANS_F32:
@@ -183,8 +211,8 @@ mr_status validate(const mr_ctx* c, const mr_job_desc* d) {
 mr_status alloc_wc(mr_ctx* c, Job* j, uint64_t cap) {
   const uint64_t n = j->desc.input_bytes;
   WcBuffers& b = j->wc;
-  const uint64_t t_bytes = align256(2 * cap * 8);
-  const uint64_t s_bytes = align256(16);
+  const uint64_t t_bytes = align256(wc_table_bytes(cap));
+  const uint64_t s_bytes = align256(wc_state_bytes());
   const uint64_t sb_bytes = align256(wc_sortbuf_bytes(cap));
   const uint64_t o_bytes = align256(wc_out_bytes(cap, n));
   const uint64_t total = t_bytes + s_bytes + sb_bytes + o_bytes;
@@ -194,7 +222,7 @@ mr_status alloc_wc(mr_ctx* c, Job* j, uint64_t cap) {
   uint8_t* p = static_cast<uint8_t*>(slab);
   b.cap = cap;
   b.key = reinterpret_cast<uint64_t*>(p);
-  b.cnt = b.key + cap;
+  b.cnt = b.key + 2 * cap;
   b.state = reinterpret_cast<uint32_t*>(p + t_bytes);
   b.sortbuf = p + t_bytes + s_bytes;
   b.out = p + t_bytes + s_bytes + sb_bytes;
@@ -212,10 +240,11 @@ mr_status alloc_job_memory(mr_ctx* c, Job* j) {
       uint64_t cap = d.wc_slots;
       j->wc_auto = cap == 0;
       if (!cap) {
-        // estimate: one distinct key per 64 input bytes, at most half full
-        cap = next_pow2(d.input_bytes / 32 + 1);
+        // estimate: at most one distinct key per 16 input bytes, capped at
+        // 2^17 slots; a table that overflows is regrown 4x and the job re-run
+        cap = next_pow2(d.input_bytes / 16 + 1);
         if (cap < 4096) cap = 4096;
-        if (cap > (1ull << 26)) cap = 1ull << 26;
+        if (cap > (1ull << 17)) cap = 1ull << 17;
       }
       return alloc_wc(c, j, cap);
     }
@@ -279,6 +308,13 @@ void free_job(mr_ctx* c, Job* j) {
   delete j;
 }
 
+// The captured graph names the jobs' containers; it is dropped (and captured
+// again by mr_rerun) when one of them moves.
+void drop_batch_graph(mr_ctx* c) {
+  if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
+  c->batch_exec = nullptr;
+}
+
 int grid_for(const mr_ctx* c, uint64_t bytes, uint64_t bytes_per_block, int max_per_sm) {
   uint64_t g = (bytes + bytes_per_block - 1) / bytes_per_block;
   const uint64_t gmax = (uint64_t)c->di.sms * max_per_sm;
@@ -287,32 +323,32 @@ int grid_for(const mr_ctx* c, uint64_t bytes, uint64_t bytes_per_block, int max_
   return (int)g;
 }
 
-mr_status enqueue_plain(mr_ctx* c, Job* j) {
+mr_status enqueue_plain_on(mr_ctx* c, Job* j, cudaStream_t st) {
   const uint64_t n = j->desc.input_bytes;
-  if (j->t0) MR_CUDA_TRY(cudaEventRecord(j->t0, c->stream));
+  if (j->t0) MR_CUDA_TRY(cudaEventRecord(j->t0, st));
   switch (j->desc.kind) {
     case MR_HIST_RGB8: {
-      MR_CUDA_TRY(cudaMemsetAsync(j->result, 0, 768 * 8, c->stream));
+      MR_CUDA_TRY(cudaMemsetAsync(j->result, 0, 768 * 8, st));
       if (j->container == MR_C_GLOBAL_ARRAY) {
         MR_CUDA_TRY(launch_hist_global(j->in, n, static_cast<uint64_t*>(j->result), grid_for(c, n, 512 * 64, 4),
-                                       c->stream));
+                                       st));
         ++c->launches;
       } else {
         // a CTA is worth launching once each of its 32 warps gets a few 1536-byte steps
         MR_CUDA_TRY(launch_hist_smem(j->in, n, static_cast<uint64_t*>(j->result),
-                                     grid_for(c, n, 1536ull * 32 * 4, 1), c->stream));
+                                     grid_for(c, n, 1536ull * 32 * 4, 1), st));
         ++c->launches;
       }
       break;
     }
     case MR_LINREG_I8:
-      MR_CUDA_TRY(cudaMemsetAsync(j->result, 0, 5 * 8, c->stream));
+      MR_CUDA_TRY(cudaMemsetAsync(j->result, 0, 5 * 8, st));
       MR_CUDA_TRY(launch_linreg(reinterpret_cast<const int8_t*>(j->in), n, static_cast<int64_t*>(j->result),
-                                grid_for(c, n, 512ull * 16 * 8, 2), c->stream));
+                                grid_for(c, n, 512ull * 16 * 8, 2), st));
       ++c->launches;
       break;
     case MR_WORDCOUNT:
-      MR_CUDA_TRY(launch_wordcount(j->in, n, j->wc, c->di, c->stream, &c->launches));
+      MR_CUDA_TRY(launch_wordcount(j->in, n, j->wc, c->di, st, &c->launches));
       break;
     case MR_KMEANS_F32: {
       uint8_t* p = static_cast<uint8_t*>(j->result);
@@ -321,77 +357,188 @@ mr_status enqueue_plain(mr_ctx* c, Job* j) {
       int32_t* oa = reinterpret_cast<int32_t*>(p + (uint64_t)K * D * 4);
       unsigned long long* os = reinterpret_cast<unsigned long long*>(p + km_stats_offset(K, D, N));
       MR_CUDA_TRY(launch_kmeans(reinterpret_cast<const float*>(j->in), j->km_init_dev, j->desc.km_iters, j->km,
-                                c->di, c->stream, oc, oa, os, &c->launches));
+                                c->di, st, oc, oa, os, &c->launches));
       break;
     }
   }
-  if (j->t1) MR_CUDA_TRY(cudaEventRecord(j->t1, c->stream));
-  MR_CUDA_TRY(cudaEventRecord(j->done, c->stream));
+  if (j->t1) MR_CUDA_TRY(cudaEventRecord(j->t1, st));
+  MR_CUDA_TRY(cudaEventRecord(j->done, st));
   j->state = JOB_ENQUEUED;
   return MR_OK;
 }
 
-mr_status enqueue_batched(mr_ctx* c, std::vector<Job*>& jobs) {
-  // k-means jobs always run plain; the others share one persistent launch
+mr_status enqueue_plain(mr_ctx* c, Job* j) { return enqueue_plain_on(c, j, c->stream); }
+
+mr_status ensure_scratch(mr_ctx* c, void** p, uint64_t* have, uint64_t need) {
+  need = align256(need ? need : 256);
+  if (need <= *have) return MR_OK;
+  dev_free(c, *p, *have);
+  *p = nullptr;
+  *have = 0;
+  mr_status st = dev_alloc(c, need, p);
+  if (st) return st;
+  *have = need;
+  return MR_OK;
+}
+
+struct BatchPlan {
   std::vector<BatchJob> bj;
-  std::vector<Job*> batched;
-  uint64_t tiles = 0;
+  std::vector<wc::JobDev> wj;
+  uint64_t tiles = 0, wc_blocks = 0, wc_records = 0;
+};
+
+void plan_batch(const std::vector<Job*>& jobs, const mr_tuning& tp, BatchPlan& P) {
   for (Job* j : jobs) {
-    if (j->desc.kind == MR_KMEANS_F32) continue;
     BatchJob b{};
     b.kind = (uint32_t)j->desc.kind;
     b.container = (uint32_t)j->container;
+    if (j->desc.kind == MR_HIST_RGB8 && j->desc.container == MR_C_AUTO)
+      b.container = j->desc.input_bytes < tp.hist_global_below ? MR_C_GLOBAL_ARRAY : MR_C_SMEM_ARRAY;
     b.in = j->in;
     b.n = j->desc.input_bytes;
     b.out = j->result;
     if (j->desc.kind == MR_WORDCOUNT) {
-      b.wc_key = j->wc.key;
-      b.wc_cnt = j->wc.cnt;
-      b.wc_cap = j->wc.cap;
-      b.wc_state = j->wc.state;
+      b.wc = wc_job_dev(j->in, b.n, j->wc, P.wc_blocks);
+      P.wc_blocks += wc_compact_blocks(j->wc.cap);
+      P.wc_records += j->wc.cap;
+      P.wj.push_back(b.wc);
     }
-    b.tile_begin = tiles;
-    b.ntiles = batch_tiles_for(b.kind, b.n);
-    tiles += b.ntiles;
-    bj.push_back(b);
-    batched.push_back(j);
+    b.tile_begin = P.tiles;
+    b.ntiles = batch_tiles_for(b.kind, b.n, tp.arr_tile, tp.wc_tile);
+    P.tiles += b.ntiles;
+    P.bj.push_back(b);
   }
-  if (!bj.empty()) {
-    const uint64_t need = align256(bj.size() * sizeof(BatchJob));
-    if (need > c->batch_desc_bytes) {
-      dev_free(c, c->batch_desc, c->batch_desc_bytes);
-      c->batch_desc = nullptr;
-      c->batch_desc_bytes = 0;
-      mr_status st = dev_alloc(c, need, &c->batch_desc);
-      if (st) return st;
-      c->batch_desc_bytes = need;
-    }
-    if (!c->batch_cursor) {
-      mr_status st = dev_alloc(c, 256, &c->batch_cursor);
-      if (st) return st;
-    }
-    // zero every container that the batch kernel accumulates into
-    for (Job* j : batched) {
-      if (j->desc.kind == MR_WORDCOUNT) {
-        MR_CUDA_TRY(cudaMemsetAsync(j->wc.key, 0, 2 * j->wc.cap * 8, c->stream));
-        MR_CUDA_TRY(cudaMemsetAsync(j->wc.state, 0, 16, c->stream));
-      } else {
-        MR_CUDA_TRY(cudaMemsetAsync(j->result, 0, j->result_bytes, c->stream));
-      }
-    }
-    MR_CUDA_TRY(cudaMemcpyAsync(c->batch_desc, bj.data(), bj.size() * sizeof(BatchJob), cudaMemcpyHostToDevice,
+}
+
+// Build the batch's descriptors for the given parameters, capture the launch
+// sequence into a CUDA graph and instantiate it (not launched).
+mr_status build_batch_graph(mr_ctx* c, const std::vector<Job*>& jobs, const mr_tuning& tp, cudaGraphExec_t* out) {
+  *out = nullptr;
+  BatchPlan P;
+  plan_batch(jobs, tp, P);
+  std::vector<BatchJob>& bj = P.bj;
+  std::vector<wc::JobDev>& wj = P.wj;
+  const uint64_t tiles = P.tiles, wc_blocks = P.wc_blocks, wc_records = P.wc_records;
+  mr_status st = ensure_scratch(c, &c->batch_desc, &c->batch_desc_bytes, bj.size() * sizeof(BatchJob));
+  if (!st) st = ensure_scratch(c, &c->batch_wc, &c->batch_wc_bytes, wj.size() * sizeof(wc::JobDev));
+  if (!st && !wj.empty()) st = ensure_scratch(c, &c->batch_sort, &c->batch_sort_bytes, wc_sortbuf_bytes(wc_records));
+  if (!st && !c->batch_cursor) st = dev_alloc(c, 256, &c->batch_cursor);
+  if (st) return st;
+  MR_CUDA_TRY(cudaMemcpyAsync(c->batch_desc, bj.data(), bj.size() * sizeof(BatchJob), cudaMemcpyHostToDevice,
+                              c->stream));
+  if (!wj.empty())
+    MR_CUDA_TRY(cudaMemcpyAsync(c->batch_wc, wj.data(), wj.size() * sizeof(wc::JobDev), cudaMemcpyHostToDevice,
                                 c->stream));
-    MR_CUDA_TRY(cudaMemsetAsync(c->batch_cursor, 0, 8, c->stream));
-    MR_CUDA_TRY(launch_batch(static_cast<const BatchJob*>(c->batch_desc), (uint32_t)bj.size(), tiles,
-                             static_cast<unsigned long long*>(c->batch_cursor), c->di, c->stream));
-    // hash jobs still need their merge + sort after the shared map/combine pass
-    for (Job* j : batched) {
-      if (j->desc.kind == MR_WORDCOUNT) {
-        WcBuffers b = j->wc;
-        (void)b;
+  MR_CUDA_TRY(batch_prepare());
+  uint64_t nk = 0;
+  cudaGraph_t g = nullptr;
+  MR_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = launch_batch(static_cast<const BatchJob*>(c->batch_desc), (uint32_t)bj.size(), tiles,
+                               static_cast<unsigned long long*>(c->batch_cursor), tp.arr_tile, tp.wc_tile, c->di,
+                               c->stream, &nk);
+  if (e == cudaSuccess && !wj.empty())
+    e = launch_wordcount_post_multi(static_cast<const wc::JobDev*>(c->batch_wc), wj[0], (uint32_t)wj.size(),
+                                    wc_blocks, wc_records, static_cast<uint8_t*>(c->batch_sort), c->stream, &nk);
+  cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    set_last_error("batch graph capture", e != cudaSuccess ? e : e2);
+    return MR_ECUDA;
+  }
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    set_last_error("cudaGraphInstantiate", e);
+    return MR_ECUDA;
+  }
+  c->batch_launches = nk;
+  return MR_OK;
+}
+
+// Time one candidate parameter set on the batch (device time of one run).
+mr_status time_candidate(mr_ctx* c, const std::vector<Job*>& jobs, const mr_tuning& tp, float* ms) {
+  cudaGraphExec_t ex = nullptr;
+  mr_status st = build_batch_graph(c, jobs, tp, &ex);
+  if (st) return st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ex, c->stream);  // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(a, c->stream);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ex, c->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(b, c->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaGraphExecDestroy(ex);
+  if (e != cudaSuccess) {
+    set_last_error("autotune timing", e);
+    return MR_ECUDA;
+  }
+  return MR_OK;
+}
+
+// Coordinate search over the batch parameters on the pending batch itself.
+mr_status autotune_batch(mr_ctx* c, const std::vector<Job*>& jobs) {
+  mr_tuning best = c->tune;
+  float best_ms = 0.f;
+  mr_status st = time_candidate(c, jobs, best, &best_ms);
+  if (st) return st;
+  const uint64_t arr_c[] = {1536ull * 32, 1536ull * 128, 1536ull * 512};
+  const uint64_t wc_c[] = {512ull * 32, 512ull * 128, 512ull * 512};
+  const uint64_t hg_c[] = {0, 1ull << 14, 1ull << 17};
+  for (int dim = 0; dim < 3; ++dim) {
+    for (int k = 0; k < 3; ++k) {
+      mr_tuning t = best;
+      if (dim == 0) t.arr_tile = arr_c[k];
+      else if (dim == 1) t.wc_tile = wc_c[k];
+      else t.hist_global_below = hg_c[k];
+      if (t.arr_tile == best.arr_tile && t.wc_tile == best.wc_tile && t.hist_global_below == best.hist_global_below)
+        continue;
+      float ms = 0.f;
+      st = time_candidate(c, jobs, t, &ms);
+      if (st) return st;
+      if (ms < best_ms) {
+        best = t;
+        best_ms = ms;
       }
     }
+  }
+  best.best_ms = best_ms;
+  best.tuned = 1;
+  c->tune = best;
+  if (const char* path = getenv("MR_TUNE_CACHE")) {
+    if (FILE* f = fopen(path, "a")) {
+      fprintf(f, "sms=%d jobs=%zu arr_tile=%llu wc_tile=%llu hist_global_below=%llu ms=%.4f\n", c->di.sms, jobs.size(),
+              (unsigned long long)best.arr_tile, (unsigned long long)best.wc_tile,
+              (unsigned long long)best.hist_global_below, best.best_ms);
+      fclose(f);
+    }
+  }
+  return MR_OK;
+}
+
+mr_status enqueue_batched(mr_ctx* c, std::vector<Job*>& jobs) {
+  std::vector<Job*> batched;
+  for (Job* j : jobs)
+    if (j->desc.kind != MR_KMEANS_F32) batched.push_back(j);
+  if (!batched.empty()) {
+    drop_batch_graph(c);
+    c->batch_ids.clear();
+    if ((c->flags & MR_FLAG_AUTOTUNE) && !c->tune.tuned) {
+      mr_status st = autotune_batch(c, batched);
+      if (st) return st;
+    }
+    for (Job* j : batched)
+      if (j->t0) MR_CUDA_TRY(cudaEventRecord(j->t0, c->stream));
+    mr_status st = build_batch_graph(c, batched, c->tune, &c->batch_exec);
+    if (st) return st;
+    MR_CUDA_TRY(cudaGraphLaunch(c->batch_exec, c->stream));
+    c->launches += c->batch_launches;
     for (Job* j : batched) {
+      c->batch_ids.push_back(j->id);
+      if (j->t1) MR_CUDA_TRY(cudaEventRecord(j->t1, c->stream));
       MR_CUDA_TRY(cudaEventRecord(j->done, c->stream));
       j->state = JOB_ENQUEUED;
     }
@@ -404,6 +551,101 @@ mr_status enqueue_batched(mr_ctx* c, std::vector<Job*>& jobs) {
   return MR_OK;
 }
 
+// Serving: launch every admitted request that is not running yet as one
+// micro-batch on a slot whose previous micro-batch has finished.  Requests
+// that arrive while the GPU is busy are picked up as soon as a slot frees, so
+// successive micro-batches overlap on the device.  Returns MR_OK also when no
+// slot is free (the requests stay queued).
+mr_status serve_pump(mr_ctx* c) {
+  if (c->serve_pending.empty()) return MR_OK;
+  mr_ctx::Slot* slot = nullptr;
+  for (auto& sl : c->slots) {
+    if (!sl.s) {
+      MR_CUDA_TRY(cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking));
+      MR_CUDA_TRY(cudaEventCreateWithFlags(&sl.busy, cudaEventDisableTiming));
+    }
+    if (!sl.used) {
+      slot = &sl;
+      break;
+    }
+    const cudaError_t q = cudaEventQuery(sl.busy);
+    if (q == cudaSuccess) {
+      slot = &sl;
+      break;
+    }
+    if (q != cudaErrorNotReady) {
+      set_last_error("cudaEventQuery(slot)", q);
+      return MR_ECUDA;
+    }
+  }
+  if (!slot) return MR_OK;
+  std::vector<Job*> jobs;
+  jobs.swap(c->serve_pending);
+  std::vector<Job*> arr;
+  for (Job* j : jobs)
+    if (j->desc.kind != MR_KMEANS_F32) arr.push_back(j);
+  // the slot stream must see the submit-time copies and clears on the context stream
+  if (!c->serve_ready) MR_CUDA_TRY(cudaEventCreateWithFlags(&c->serve_ready, cudaEventDisableTiming));
+  MR_CUDA_TRY(cudaEventRecord(c->serve_ready, c->stream));
+  MR_CUDA_TRY(cudaStreamWaitEvent(slot->s, c->serve_ready, 0));
+  for (Job* j : jobs)
+    if (j->t0) MR_CUDA_TRY(cudaEventRecord(j->t0, slot->s));
+  if (!arr.empty()) {
+    BatchPlan P;
+    plan_batch(arr, c->tune, P);
+    mr_status st = ensure_scratch(c, &slot->desc, &slot->desc_bytes, P.bj.size() * sizeof(BatchJob));
+    if (!st) st = ensure_scratch(c, &slot->wcd, &slot->wcd_bytes, P.wj.size() * sizeof(wc::JobDev));
+    if (!st && !P.wj.empty()) st = ensure_scratch(c, &slot->sort, &slot->sort_bytes, wc_sortbuf_bytes(P.wc_records));
+    if (!st && !slot->cursor) st = dev_alloc(c, 256, &slot->cursor);
+    if (st) {
+      c->serve_pending.insert(c->serve_pending.begin(), jobs.begin(), jobs.end());
+      return st;
+    }
+    MR_CUDA_TRY(cudaMemcpyAsync(slot->desc, P.bj.data(), P.bj.size() * sizeof(BatchJob), cudaMemcpyHostToDevice,
+                                slot->s));
+    if (!P.wj.empty())
+      MR_CUDA_TRY(cudaMemcpyAsync(slot->wcd, P.wj.data(), P.wj.size() * sizeof(wc::JobDev), cudaMemcpyHostToDevice,
+                                  slot->s));
+    MR_CUDA_TRY(batch_prepare());
+    MR_CUDA_TRY(launch_batch(static_cast<const BatchJob*>(slot->desc), (uint32_t)P.bj.size(), P.tiles,
+                             static_cast<unsigned long long*>(slot->cursor), c->tune.arr_tile, c->tune.wc_tile, c->di,
+                             slot->s, &c->launches));
+    if (!P.wj.empty())
+      MR_CUDA_TRY(launch_wordcount_post_multi(static_cast<const wc::JobDev*>(slot->wcd), P.wj[0],
+                                              (uint32_t)P.wj.size(), P.wc_blocks, P.wc_records,
+                                              static_cast<uint8_t*>(slot->sort), slot->s, &c->launches));
+    for (Job* j : arr) {
+      if (j->t1) MR_CUDA_TRY(cudaEventRecord(j->t1, slot->s));
+      MR_CUDA_TRY(cudaEventRecord(j->done, slot->s));
+      j->state = JOB_ENQUEUED;
+    }
+  }
+  for (Job* j : jobs)
+    if (j->desc.kind == MR_KMEANS_F32) {
+      mr_status st = enqueue_plain_on(c, j, slot->s);
+      if (st) return st;
+    }
+  MR_CUDA_TRY(cudaEventRecord(slot->busy, slot->s));
+  slot->used = true;
+  return MR_OK;
+}
+
+// Block until the queued request j has been launched.
+mr_status serve_launch_now(mr_ctx* c, Job* j) {
+  while (j->state == JOB_SERVE_QUEUED) {
+    mr_status st = serve_pump(c);
+    if (st) return st;
+    if (j->state != JOB_SERVE_QUEUED) break;
+    // every slot is busy: wait for the one that was launched first to drain
+    for (auto& sl : c->slots)
+      if (sl.used) {
+        MR_CUDA_TRY(cudaEventSynchronize(sl.busy));
+        break;
+      }
+  }
+  return MR_OK;
+}
+
 Job* find_job(mr_ctx* c, uint64_t id) {
   auto it = c->jobs.find(id);
   return it == c->jobs.end() ? nullptr : it->second;
@@ -411,7 +653,13 @@ Job* find_job(mr_ctx* c, uint64_t id) {
 
 // Wait for a job; for an automatic word-count table that overflowed, regrow
 // it (4x) and re-run until it fits.
+mr_status serve_launch_now(mr_ctx* c, Job* j);
+
 mr_status wait_job(mr_ctx* c, Job* j) {
+  if (j->state == JOB_SERVE_QUEUED) {
+    mr_status st = serve_launch_now(c, j);
+    if (st) return st;
+  }
   if (j->state == JOB_PENDING) return MR_ENOTREADY;
   MR_CUDA_TRY(cudaEventSynchronize(j->done));
   if (j->desc.kind == MR_KMEANS_F32) {
@@ -429,6 +677,12 @@ mr_status wait_job(mr_ctx* c, Job* j) {
     MR_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (!(st[0] & 1u)) return MR_OK;
     if (!j->wc_auto) return MR_EOVERFLOW;
+    // the job's containers move: a captured batch graph that names them is stale
+    for (uint64_t id : c->batch_ids)
+      if (id == j->id) {
+        drop_batch_graph(c);
+        break;
+      }
     const uint64_t cap = j->wc.cap * 4;
     if (cap > (1ull << 32)) return MR_EOVERFLOW;
     dev_free(c, j->slab, j->slab_bytes);
@@ -572,9 +826,25 @@ void mr_destroy(mr_ctx* c) {
   cudaStreamSynchronize(c->stream);
   for (auto& kv : c->jobs) free_job(c, kv.second);
   c->jobs.clear();
+  for (auto& sl : c->slots)
+    if (sl.s) cudaStreamSynchronize(sl.s);
+  drop_batch_graph(c);
+  for (auto& sl : c->slots) {
+    dev_free(c, sl.desc, sl.desc_bytes);
+    dev_free(c, sl.wcd, sl.wcd_bytes);
+    dev_free(c, sl.sort, sl.sort_bytes);
+    dev_free(c, sl.cursor, 256);
+  }
   dev_free(c, c->batch_desc, c->batch_desc_bytes);
+  dev_free(c, c->batch_wc, c->batch_wc_bytes);
+  dev_free(c, c->batch_sort, c->batch_sort_bytes);
   dev_free(c, c->batch_cursor, 256);
   cudaStreamSynchronize(c->stream);
+  for (auto& sl : c->slots) {
+    if (sl.busy) cudaEventDestroy(sl.busy);
+    if (sl.s) cudaStreamDestroy(sl.s);
+  }
+  if (c->serve_ready) cudaEventDestroy(c->serve_ready);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -641,6 +911,17 @@ mr_status mr_release(mr_ctx* c, uint64_t job_id) {
   Job* j = find_job(c, job_id);
   if (!j) return MR_ENOJOB;
   if (j->state == JOB_ENQUEUED) MR_CUDA_TRY(cudaEventSynchronize(j->done));
+  for (size_t i = 0; i < c->serve_pending.size(); ++i)
+    if (c->serve_pending[i] == j) {
+      c->serve_pending.erase(c->serve_pending.begin() + i);
+      break;
+    }
+  for (uint64_t id : c->batch_ids)
+    if (id == job_id) {
+      drop_batch_graph(c);
+      c->batch_ids.clear();
+      break;
+    }
   c->jobs.erase(job_id);
   for (size_t i = 0; i < c->pending.size(); ++i)
     if (c->pending[i] == job_id) {
@@ -657,16 +938,19 @@ mr_status mr_submit(mr_ctx* c, const mr_job_desc* desc, uint64_t* job_id) {
   mr_status st = add_job_impl(c, desc, job_id);
   if (st) return st;
   Job* j = find_job(c, *job_id);
-  st = enqueue_plain(c, j);
-  return st;
+  j->state = JOB_SERVE_QUEUED;
+  c->serve_pending.push_back(j);
+  return serve_pump(c);
 }
 
 mr_status mr_poll(mr_ctx* c, uint64_t job_id) {
   if (!c) return MR_EINVAL;
   DeviceGuard g(c->device);
+  mr_status ps = serve_pump(c);
+  if (ps) return ps;
   Job* j = find_job(c, job_id);
   if (!j) return MR_ENOJOB;
-  if (j->state == JOB_PENDING) return MR_ENOTREADY;
+  if (j->state == JOB_PENDING || j->state == JOB_SERVE_QUEUED) return MR_ENOTREADY;
   cudaError_t e = cudaEventQuery(j->done);
   if (e == cudaSuccess) return MR_OK;
   if (e == cudaErrorNotReady) return MR_ENOTREADY;
@@ -677,6 +961,13 @@ mr_status mr_poll(mr_ctx* c, uint64_t job_id) {
 mr_status mr_sync(mr_ctx* c) {
   if (!c) return MR_EINVAL;
   DeviceGuard g(c->device);
+  while (!c->serve_pending.empty()) {
+    Job* j = c->serve_pending.front();
+    mr_status st = serve_launch_now(c, j);
+    if (st) return st;
+  }
+  for (auto& sl : c->slots)
+    if (sl.s) MR_CUDA_TRY(cudaStreamSynchronize(sl.s));
   MR_CUDA_TRY(cudaStreamSynchronize(c->stream));
   return MR_OK;
 }
@@ -684,6 +975,38 @@ mr_status mr_sync(mr_ctx* c) {
 uint64_t mr_bytes_in_use(const mr_ctx* c) { return c ? c->in_use : 0; }
 
 uint64_t mr_kernel_launches(const mr_ctx* c) { return c ? c->launches : 0; }
+
+mr_status mr_rerun(mr_ctx* c) {
+  if (!c) return MR_EINVAL;
+  DeviceGuard g(c->device);
+  if (c->batch_ids.empty()) return MR_EINVAL;
+  std::vector<Job*> jobs;
+  for (uint64_t id : c->batch_ids) {
+    Job* j = find_job(c, id);
+    if (!j) return MR_ENOJOB;
+    jobs.push_back(j);
+  }
+  if (!c->batch_exec) {  // a job's containers moved since the capture
+    mr_status st = build_batch_graph(c, jobs, c->tune, &c->batch_exec);
+    if (st) return st;
+  }
+  for (Job* j : jobs)
+    if (j->t0) MR_CUDA_TRY(cudaEventRecord(j->t0, c->stream));
+  MR_CUDA_TRY(cudaGraphLaunch(c->batch_exec, c->stream));
+  c->launches += c->batch_launches;
+  for (Job* j : jobs) {
+    if (j->t1) MR_CUDA_TRY(cudaEventRecord(j->t1, c->stream));
+    MR_CUDA_TRY(cudaEventRecord(j->done, c->stream));
+    j->state = JOB_ENQUEUED;
+  }
+  return MR_OK;
+}
+
+mr_status mr_get_tuning(const mr_ctx* c, mr_tuning* out) {
+  if (!c || !out) return MR_EINVAL;
+  *out = c->tune;
+  return MR_OK;
+}
 
 mr_status mr_job_elapsed_ms(mr_ctx* c, uint64_t job_id, float* ms) {
   if (!c || !ms) return MR_EINVAL;

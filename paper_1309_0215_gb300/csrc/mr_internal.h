@@ -5,6 +5,7 @@
 #include <cstddef>
 
 #include "../../include/mr.h"
+#include "dev_wordcount.cuh"
 
 namespace mrgb {
 
@@ -42,21 +43,29 @@ int hist_block_threads();
 // --------------------------------------------------------- word count job
 struct WcBuffers {
   uint64_t cap = 0;            // global hash-table slots (power of two)
-  uint64_t* key = nullptr;     // [cap] 0 = empty, else (len<<40)|(offset+1)
-  uint64_t* cnt = nullptr;     // [cap] combined counts
-  uint32_t* state = nullptr;   // [0] overflow flag, [1] records, [2..3] spare
-  uint8_t* sortbuf = nullptr;  // 2 x cap sort records + cap u64 block sums
+  uint64_t* key = nullptr;     // [cap][2] 128-bit keys, {0, 0} = empty
+  uint64_t* cnt = nullptr;     // [cap] combined counts (contiguous after key)
+  uint32_t* state = nullptr;   // 64 bytes: word 0 overflow flag, 64-bit fields 1..4 post-phase bounds
+  uint8_t* sortbuf = nullptr;  // post-phase scratch for cap records
   uint8_t* out = nullptr;      // result: header + records + key bytes
   uint64_t out_cap = 0;
 };
-size_t wc_sortbuf_bytes(uint64_t cap);
+uint64_t wc_table_bytes(uint64_t cap);
+uint64_t wc_state_bytes();
+size_t wc_sortbuf_bytes(uint64_t records);
 uint64_t wc_out_bytes(uint64_t cap, uint64_t n);
+int wc_map_smem_bytes();
+uint64_t wc_compact_blocks(uint64_t cap);
+wc::JobDev wc_job_dev(const uint8_t* in, uint64_t n, const WcBuffers& b, uint64_t blk0);
+// Compaction, sort (by job, count desc, key asc), bounds and gather for
+// njobs jobs (jobs: device array, or nullptr with `single` for one job).
+cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev& single, uint32_t njobs,
+                                        uint64_t nblocks, uint64_t records, uint8_t* sortbuf, cudaStream_t s,
+                                        uint64_t* nk);
 // Zero the table and state, run map+combine, compaction, sort and gather.
 // *nk is incremented by the number of kernels launched.
 cudaError_t launch_wordcount(const uint8_t* in, uint64_t n, const WcBuffers& b, const DevInfo& di, cudaStream_t s,
                              uint64_t* nk);
-// Merge + sort + gather only (the map/combine pass already filled the table).
-cudaError_t launch_wordcount_post(const uint8_t* in, uint64_t n, const WcBuffers& b, cudaStream_t s, uint64_t* nk);
 
 // ---------------------------------------------------------------- k-means
 struct KmBuffers {
@@ -74,6 +83,7 @@ struct KmBuffers {
   uint16_t* xb = nullptr;       // BF16 copy of the points [n][d]
   uint16_t* cb = nullptr;       // BF16 centroids [k][d]
   unsigned int* maxabs = nullptr;  // [1] bits of max |x|
+  uint32_t* kcursor = nullptr;  // [k] counting-sort write cursors
   int fx_shift = 32;            // fixed-point scale exponent
   int precision = 0;
 };
@@ -90,17 +100,15 @@ struct BatchJob {
   uint32_t container;  // mr_container chosen
   const uint8_t* in;
   uint64_t n;
-  void* out;           // bins / sums
-  // word count
-  uint64_t* wc_key;
-  uint64_t* wc_cnt;
-  uint64_t wc_cap;
-  uint32_t* wc_state;
-  uint64_t tile_begin; // first tile index of this job in the global tile space
+  void* out;           // histogram bins / regression sums
+  wc::JobDev wc;       // word count
+  uint64_t tile_begin; // first tile index of this job in the batch's tile space
   uint64_t ntiles;
 };
-cudaError_t launch_batch(const BatchJob* jobs_dev, uint32_t njobs, uint64_t total_tiles,
-                         unsigned long long* cursor, const DevInfo& di, cudaStream_t s);
-uint64_t batch_tiles_for(uint32_t kind, uint64_t n);
+cudaError_t batch_prepare();
+// Zero the jobs' containers, then run every tile in one persistent launch.
+cudaError_t launch_batch(const BatchJob* jobs_dev, uint32_t njobs, uint64_t total_tiles, unsigned long long* cursor,
+                         uint64_t arr_tile, uint64_t wc_tile, const DevInfo& di, cudaStream_t s, uint64_t* nk);
+uint64_t batch_tiles_for(uint32_t kind, uint64_t n, uint64_t arr_tile, uint64_t wc_tile);
 
 }  // namespace mrgb
