@@ -42,6 +42,11 @@ def _L():
             lib.oracle_kmeans_assign.argtypes = [vp, u64, u32, vp, u32, vp, vp]
             lib.oracle_kmeans_update.argtypes = [vp, u64, u32, vp, u32, vp, vp, vp]
             lib.oracle_kmeans.argtypes = [vp, u64, u32, vp, u32, u32, vp, vp]
+            lib.oracle_hist_u32.argtypes = [vp, u64, u32, vp]
+            lib.oracle_mix64.argtypes = [u64]
+            lib.oracle_mix64.restype = u64
+            lib.oracle_bloom_dna.argtypes = [vp, u64, u32, u64, u32, vp]
+            lib.oracle_bloom_codes.argtypes = [vp, u64, u64, u32, vp]
             _lib = lib
     return _lib
 
@@ -80,6 +85,37 @@ def linreg_i8(xy) -> np.ndarray:
     if _L().oracle_linreg_i8(p, xy.size, sums.ctypes.data):
         raise ValueError("input length must be even")
     return sums
+
+
+def hist_u32(keys, nbins: int) -> np.ndarray:
+    """u64[nbins + 1]: counts of each key < nbins, then the out-of-range count."""
+    k, p = _buf(np.asarray(keys, dtype=np.uint32))
+    out = np.zeros(nbins + 1, dtype=np.uint64)
+    if _L().oracle_hist_u32(p, k.size, nbins, out.ctypes.data):
+        raise ValueError("oracle_hist_u32")
+    return out
+
+
+def mix64(z: int) -> int:
+    return int(_L().oracle_mix64(ctypes.c_uint64(z & (2 ** 64 - 1))))
+
+
+def bloom_dna(seq, L: int, m: int, h: int) -> np.ndarray:
+    """Bloom filter bits (ceil(m/8) bytes) of every all-ACGT window of length L."""
+    s, p = _buf(np.frombuffer(seq, dtype=np.uint8) if isinstance(seq, (bytes, bytearray))
+                else np.asarray(seq, dtype=np.uint8))
+    out = np.zeros((m + 7) // 8, dtype=np.uint8)
+    if _L().oracle_bloom_dna(p, s.size, L, m, h, out.ctypes.data):
+        raise ValueError("oracle_bloom_dna")
+    return out
+
+
+def bloom_codes(codes, m: int, h: int) -> np.ndarray:
+    c, p = _buf(np.asarray(codes, dtype=np.uint64))
+    out = np.zeros((m + 7) // 8, dtype=np.uint8)
+    if _L().oracle_bloom_codes(p, c.size, m, h, out.ctypes.data):
+        raise ValueError("oracle_bloom_codes")
+    return out
 
 
 def kmeans_assign(x, c, want_dmin: bool = False):

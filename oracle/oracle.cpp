@@ -114,6 +114,88 @@ int oracle_linreg_i8(const int8_t* xy, uint64_t n, int64_t* sums) {
   return 0;
 }
 
+/* Large-key histogram (the Histogram application of Sec. IV: 16M unique
+ * keys, 256M elements; array container of Sec. III-A, held as one global
+ * array per Sec. III-E "eliminating local arrays").
+ * map: element i is a u32 key and emits (key, 1); reduce: sum.
+ * Output u64[nbins + 1]: out[k] = number of elements equal to k (k < nbins),
+ * out[nbins] = number of elements >= nbins. */
+int oracle_hist_u32(const uint32_t* keys, uint64_t n, uint32_t nbins, uint64_t* out) {
+  if ((!keys && n) || !out || nbins == 0) return 1;
+  std::vector<uint64_t> bins((size_t)nbins + 1, 0);
+  for (uint64_t i = 0; i < n; ++i) {
+    const uint32_t key = keys[i];
+    bins[key < nbins ? key : nbins] += 1;
+  }
+  std::memcpy(out, bins.data(), bins.size() * sizeof(uint64_t));
+  return 0;
+}
+
+/* The SplitMix64 output function (Steele, Lea & Flood, "Fast splittable
+ * pseudorandom number generators", OOPSLA 2014), used as the Bloom filter's
+ * base hash: applied to a state value it gives that state's output. */
+uint64_t oracle_mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+/* Bloom-filter build (the Bloom Filter application of Sec. IV: 30M elements
+ * into 300M entries, k-mers of a chromosome; array container, Sec. III-E).
+ * Elements: every window of L consecutive bytes that are all in {A,C,G,T};
+ * its code is the base-4 number of the window (A=0, C=1, G=2, T=3, first
+ * base most significant), L <= 32.  Hashes (double hashing, Kirsch and
+ * Mitzenmacher, ESA 2006): a = mix(code) mod m, b = 1 + mix(code ^
+ * 0x9E3779B97F4A7C15) mod (m - 1); the element sets bits (a + i*b) mod m for
+ * i = 0..h-1.  Output: ceil(m/8) bytes, bit j = bit (j mod 8) of byte j/8.
+ * A window containing any other byte (N, lower case, newline) is skipped. */
+static int base_code(uint8_t c) {
+  switch (c) {
+    case 'A': return 0;
+    case 'C': return 1;
+    case 'G': return 2;
+    case 'T': return 3;
+    default: return -1;
+  }
+}
+
+static void bloom_insert(uint64_t code, uint64_t m, uint32_t h, uint8_t* bits) {
+  const uint64_t a = oracle_mix64(code) % m;
+  const uint64_t b = 1 + oracle_mix64(code ^ 0x9E3779B97F4A7C15ull) % (m - 1);
+  for (uint32_t i = 0; i < h; ++i) {
+    const uint64_t j = (a + (uint64_t)i * b) % m;
+    bits[j / 8] |= (uint8_t)(1u << (j % 8));
+  }
+}
+
+int oracle_bloom_dna(const uint8_t* seq, uint64_t n, uint32_t L, uint64_t m, uint32_t h, uint8_t* bits) {
+  if ((!seq && n) || !bits || L == 0 || L > 32 || m < 2 || m > (1ull << 32) || h == 0 || h > 32) return 1;
+  std::memset(bits, 0, (size_t)((m + 7) / 8));
+  for (uint64_t p = 0; p + L <= n; ++p) {
+    uint64_t code = 0;
+    bool ok = true;
+    for (uint32_t j = 0; j < L; ++j) {
+      const int v = base_code(seq[p + j]);
+      if (v < 0) {
+        ok = false;
+        break;
+      }
+      code = code * 4 + (uint64_t)v;
+    }
+    if (ok) bloom_insert(code, m, h, bits);
+  }
+  return 0;
+}
+
+/* The same insertion for explicit element codes (used to pin the window
+ * encoding from outside). */
+int oracle_bloom_codes(const uint64_t* codes, uint64_t n, uint64_t m, uint32_t h, uint8_t* bits) {
+  if ((!codes && n) || !bits || m < 2 || m > (1ull << 32) || h == 0 || h > 32) return 1;
+  std::memset(bits, 0, (size_t)((m + 7) / 8));
+  for (uint64_t i = 0; i < n; ++i) bloom_insert(codes[i], m, h, bits);
+  return 0;
+}
+
 /* Squared Euclidean distance in FP64: Σ_j (x_j - c_j)², j in order, no FMA. */
 static double dist2_f64(const float* x, const float* c, uint32_t d) {
   double s = 0.0;

@@ -17,6 +17,8 @@ Recipes (the readings of the workload descriptions are listed in the design doc):
   y = clamp(3x + round(4 N(0,1)), -128, 127), stored x0 y0 x1 y1 ...
 * k-means: 256-component Gaussian mixture, means uniform in [-10, 10]^d,
   unit variance, FP32; K initial centroids are K distinct sampled points.
+* large-key histogram: u32 keys uniform on [0, 2^24) (or a skewed variant).
+* Bloom filter: uniform A/C/G/T bases, optionally with runs of N.
 """
 from __future__ import annotations
 
@@ -60,6 +62,8 @@ def _L():
             lib.synth_wc_candidates.argtypes = [u64, u64, u32, u32, u32, vp, vp]
             lib.synth_wc_text.argtypes = [u64, vp, vp, vp, u32, vp, u64, u32, u32, vp, vp, u64]
             lib.synth_wc_text.restype = ctypes.c_int64
+            lib.synth_keys_u32.argtypes = [u64, u64, u32, i32, vp, i32]
+            lib.synth_dna.argtypes = [u64, u64, u32, u32, vp, i32]
             _lib = lib
     return _lib
 
@@ -106,6 +110,29 @@ def kmeans_points(n: int, d: int = 64, ncomp: int = 256, seed: int = SEED_BASE +
     if rc:
         raise ValueError("synth_kmeans_f32 failed")
     return x, comp, means
+
+
+def keys_u32(n: int, nbins: int = 1 << 24, seed: int = SEED_BASE + 5, skewed: bool = False,
+             out: np.ndarray | None = None) -> np.ndarray:
+    """u32 keys in [0, nbins): uniform, or skewed (rank density ~ 1/(rank + 1),
+    ranks spread over the key range by a fixed bijection)."""
+    if out is None:
+        out = np.empty(n, dtype=np.uint32)
+    assert out.dtype == np.uint32 and out.size >= n and out.flags.c_contiguous
+    if _L().synth_keys_u32(seed, n, nbins, 1 if skewed else 0, _p(out), _threads()):
+        raise ValueError("synth_keys_u32 failed")
+    return out[:n]
+
+
+def dna(n: int, seed: int = SEED_BASE + 6, n_runs: int = 0, max_run: int = 1000,
+        out: np.ndarray | None = None) -> np.ndarray:
+    """ASCII DNA bases (uniform A/C/G/T), with n_runs runs of 'N' written over it."""
+    if out is None:
+        out = np.empty(n, dtype=np.uint8)
+    assert out.dtype == np.uint8 and out.size >= n and out.flags.c_contiguous
+    if _L().synth_dna(seed, n, n_runs, max_run, _p(out), _threads()):
+        raise ValueError("synth_dna failed")
+    return out[:n]
 
 
 def sample_distinct(n: int, k: int, seed: int) -> np.ndarray:

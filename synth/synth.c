@@ -215,6 +215,71 @@ int synth_kmeans_f32(uint64_t seed, uint64_t n, uint32_t d, uint32_t ncomp, doub
   return 0;
 }
 
+/* ------------------------------------------------------------------ */
+/* u32 keys for the large-key histogram.                                */
+/* dist 0: uniform on [0, nbins).                                       */
+/* dist 1: skewed: rank j = min(floor((nbins + 1)^u) - 1, nbins - 1)     */
+/* with u uniform on [0, 1), so P(j) falls off roughly like 1/(j + 1)   */
+/* (a continuous stand-in for Zipf, s = 1); ranks are spread over the   */
+/* key range by j -> (j * 2654435761) mod nbins, a bijection because    */
+/* 2654435761 is prime and larger than any u32 nbins it could divide.   */
+/* ------------------------------------------------------------------ */
+typedef struct { uint64_t seed; uint32_t nbins; int dist; double lg; uint32_t* out; } keys_ctx;
+
+static void keys_chunk(void* p, uint64_t chunk, uint64_t b, uint64_t e) {
+  keys_ctx* c = (keys_ctx*)p;
+  rng_t r; rng_seed(&r, c->seed, chunk + 1);
+  for (uint64_t i = b; i < e; ++i) {
+    if (c->dist == 0) {
+      c->out[i] = rng_below(&r, c->nbins);
+    } else {
+      double v = floor(exp(rng_u01(&r) * c->lg)) - 1.0;
+      uint64_t j = v < 0.0 ? 0 : (uint64_t)v;
+      if (j > c->nbins - 1) j = c->nbins - 1;
+      c->out[i] = (uint32_t)((j * 2654435761ull) % c->nbins);
+    }
+  }
+}
+
+int synth_keys_u32(uint64_t seed, uint64_t n, uint32_t nbins, int dist, uint32_t* out, int nthreads) {
+  if ((!out && n) || nbins == 0 || dist < 0 || dist > 1) return 1;
+  keys_ctx c = {seed, nbins, dist, log((double)nbins + 1.0), out};
+  run_chunks(keys_chunk, &c, n, CHUNK, nthreads);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* DNA sequence for the Bloom-filter build: bases 'A','C','G','T'       */
+/* uniform and independent; optionally n_runs runs of 'N' (length      */
+/* uniform on [1, max_run]) written over uniformly drawn positions, as  */
+/* assemblies carry gaps.                                               */
+/* ------------------------------------------------------------------ */
+typedef struct { uint64_t seed; uint8_t* out; } dna_ctx;
+
+static void dna_chunk(void* p, uint64_t chunk, uint64_t b, uint64_t e) {
+  dna_ctx* c = (dna_ctx*)p;
+  static const uint8_t base[4] = {'A', 'C', 'G', 'T'};
+  rng_t r; rng_seed(&r, c->seed, chunk + 1);
+  uint64_t i = b;
+  while (i < e) {
+    uint64_t w = rng_next(&r);
+    for (int q = 0; q < 32 && i < e; ++q, ++i) c->out[i] = base[(w >> (2 * q)) & 3];
+  }
+}
+
+int synth_dna(uint64_t seed, uint64_t n, uint32_t n_runs, uint32_t max_run, uint8_t* out, int nthreads) {
+  if ((!out && n) || (n_runs && (max_run == 0 || n == 0))) return 1;
+  dna_ctx c = {seed, out};
+  run_chunks(dna_chunk, &c, n, CHUNK, nthreads);
+  rng_t r; rng_seed(&r, seed, 0xDA7Aull);
+  for (uint32_t k = 0; k < n_runs; ++k) {
+    uint64_t at = rng_next(&r) % n;
+    uint32_t len = 1 + rng_below(&r, max_run);
+    for (uint32_t j = 0; j < len && at + j < n; ++j) out[at + j] = 'N';
+  }
+  return 0;
+}
+
 /* k distinct indices in [0, n) by a partial Fisher-Yates shuffle; scratch holds n u32 */
 int synth_sample_distinct(uint64_t seed, uint32_t n, uint32_t k, uint32_t* scratch, uint32_t* out) {
   if (k > n || !scratch || !out) return 1;

@@ -244,3 +244,104 @@ def test_kmeans_loop_is_assign_then_update():
         assert int(counts.sum()) == x.shape[0]
     c3, a3 = oracle.kmeans(x, init, 3)
     assert np.array_equal(c3, cur) and np.array_equal(a3, a)
+
+
+# ----------------------------------------------------------- large-key histogram
+
+def test_hist_u32_brute_force_tiny():
+    rng = np.random.default_rng(7)
+    for nbins in (1, 5, 64):
+        keys = rng.integers(0, nbins + 3, size=500).astype(np.uint32)  # some keys out of range
+        got = oracle.hist_u32(keys, nbins)
+        exp = [0] * (nbins + 1)
+        for k in keys.tolist():
+            exp[k if k < nbins else nbins] += 1
+        assert got.tolist() == exp
+
+
+def test_hist_u32_equals_bincount_and_conserves():
+    keys = synth.keys_u32(1 << 20, 1 << 16)
+    got = oracle.hist_u32(keys, 1 << 16)
+    assert np.array_equal(got[:-1], np.bincount(keys, minlength=1 << 16).astype(np.uint64))
+    assert got[-1] == 0 and int(got.sum()) == keys.size
+    sk = synth.keys_u32(1 << 20, 1 << 16, skewed=True)
+    g2 = oracle.hist_u32(sk, 1 << 16)
+    assert np.array_equal(g2[:-1], np.bincount(sk, minlength=1 << 16).astype(np.uint64))
+
+
+def test_hist_u32_constant_and_extreme_keys():
+    keys = np.full(1000, 123, dtype=np.uint32)
+    got = oracle.hist_u32(keys, 200)
+    assert got[123] == 1000 and int(got.sum()) == 1000
+    ext = np.array([0, 2 ** 32 - 1, 9, 10, 2 ** 31], dtype=np.uint32)
+    got = oracle.hist_u32(ext, 10)
+    assert got.tolist() == [1] + [0] * 8 + [1] + [3]
+    assert oracle.hist_u32(np.zeros(0, dtype=np.uint32), 4).tolist() == [0] * 5
+
+
+# ----------------------------------------------------------------- Bloom filter
+
+def test_mix64_is_splitmix64_output_function():
+    # SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) seeded with 1234567: its
+    # first five outputs, as published with the generator's reference
+    # implementations; next() adds the golden gamma and then mixes.
+    gamma = 0x9E3779B97F4A7C15
+    st, outs = 1234567, []
+    for _ in range(5):
+        st = (st + gamma) % 2 ** 64
+        outs.append(oracle.mix64(st))
+    assert outs == [6457827717110365317, 3203168211198807973, 9817491932198370423,
+                    4593380528125082431, 16408922859458223821]
+    assert oracle.mix64(gamma) == 0xE220A8397B1DCDAF  # seed 0, first output
+
+
+def _windows(seq: bytes, L: int):
+    return [seq[i:i + L] for i in range(len(seq) - L + 1)]
+
+
+def test_bloom_window_codes_are_base4_numbers():
+    seq = bytes(synth.dna(300, seed=11))
+    for L in (1, 7, 31, 32):
+        codes = [int(w.translate(bytes.maketrans(b"ACGT", b"0123")), 4) for w in _windows(seq, L)]
+        assert np.array_equal(oracle.bloom_dna(seq, L, 1000, 3), oracle.bloom_codes(codes, 1000, 3))
+
+
+def test_bloom_skips_windows_with_other_bytes():
+    a, b = bytes(synth.dna(200, seed=1)), bytes(synth.dna(150, seed=2))
+    L, m, h = 16, 4099, 5
+    for sep in (b"N", b"\n", b"a", b"NNNN"):
+        got = oracle.bloom_dna(a + sep + b, L, m, h)
+        assert np.array_equal(got, oracle.bloom_dna(a, L, m, h) | oracle.bloom_dna(b, L, m, h))
+    assert not oracle.bloom_dna(b"ACGTNACGTN", 5, m, h).any()  # no complete window
+    assert not oracle.bloom_dna(b"ACG", 4, m, h).any()         # shorter than one window
+
+
+def test_bloom_is_union_of_single_windows():
+    seq = bytes(synth.dna(120, seed=3))
+    L, m, h = 9, 977, 4
+    acc = np.zeros((m + 7) // 8, dtype=np.uint8)
+    for w in _windows(seq, L):
+        acc |= oracle.bloom_dna(w, L, m, h)
+    assert np.array_equal(oracle.bloom_dna(seq, L, m, h), acc)
+
+
+def test_bloom_bit_positions_of_one_element():
+    m, h = 1_000_003, 7
+    for code in (0, 1, 12345, 2 ** 64 - 1):
+        a = oracle.mix64(code) % m
+        b = 1 + oracle.mix64(code ^ 0x9E3779B97F4A7C15) % (m - 1)
+        pos = {(a + i * b) % m for i in range(h)}
+        bits = np.unpackbits(oracle.bloom_codes([code], m, h), bitorder="little")[:m]
+        assert set(np.flatnonzero(bits).tolist()) == pos
+
+
+def test_bloom_fill_matches_expectation_and_no_false_negatives():
+    m, h, n = 1 << 20, 7, 100_000
+    codes = np.unique(synth.keys_u32(n + 5000, 2 ** 32 - 1, seed=9).astype(np.uint64) * 7919)[:n]
+    bits = np.unpackbits(oracle.bloom_codes(codes, m, h), bitorder="little")[:m]
+    # fill of an ideal filter: m (1 - (1 - 1/m)^(h n)), binomial-like spread
+    p = 1 - (1 - 1 / m) ** (h * codes.size)
+    assert abs(bits.sum() - m * p) < 6 * math.sqrt(m * p * (1 - p))
+    for c in codes[:200].tolist():
+        one = np.unpackbits(oracle.bloom_codes([c], m, h), bitorder="little")[:m]
+        assert np.all(bits[one == 1] == 1)
