@@ -8,7 +8,7 @@ mr_run) on inputs already resident in HBM.  Inputs are larger than L2, so no
 flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload arrays|wordcount|kmeans|batched|serving] [--scale S]
+                  [--workload arrays|wordcount|kmeans|histkeys|bloom|batched|serving] [--scale S]
 
 Other workloads are for manual measurement; the default line is the contract.
 Multi-GPU (torchrun): each rank runs its own replica of the workload on its own
@@ -34,6 +34,11 @@ METRIC = "input GB/s per job (% of HBM peak); batched jobs/s and p99 latency vs 
 HIST_PIXELS = 512 << 20      # 1,610,612,736 bytes
 KM_ITERS = 10
 LR_PAIRS = 256 << 20         # 536,870,912 bytes
+HK_KEYS = 256 << 20          # large-key histogram: 256M u32 keys (1 GiB) ...
+HK_BINS = 1 << 24            # ... over 16M bins
+BF_ELEMS = 30_000_000        # Bloom filter: 30M k-mers ...
+BF_BITS = 300_000_000        # ... into 300M bits ...
+BF_KMER, BF_HASHES = 32, 7   # ... 32-base windows, 7 bit positions each
 
 
 def _peaks():
@@ -45,14 +50,21 @@ def _peaks():
         return 6800.0, 1900.0, 1700.0, "fallback"
 
 
-def _traffic(kernel: str, source: str):
-    """Per-launch DRAM bytes from the committed ncu summary, if the kernel's
-    source is unchanged since the capture (else None)."""
+def source_sha(sources) -> str:
+    h = hashlib.sha256()
+    for src in sources:
+        h.update(open(os.path.join(ROOT, src), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel: str, sources):
+    """Per-launch DRAM bytes (at this workload's size) from the committed ncu
+    summary, if the kernel's sources are unchanged since the capture (else
+    None)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f)[kernel]
-        h = hashlib.sha256(open(os.path.join(ROOT, source), "rb").read()).hexdigest()[:16]
-        return rec["bytes_per_launch"] if rec.get("source_sha") == h else None
+        return rec["bytes_per_launch"] if rec.get("source_sha") == source_sha(sources) else None
     except Exception:
         return None
 
@@ -119,9 +131,18 @@ def _max_over_ranks(x: float, ws: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def combine_ranks(ms: float, nbytes: int, steps: int, ws: int):
+    """Whole-job throughput of weak-scaled replicas: every rank processed
+    nbytes per step; the job took the slowest rank's time.  Returns
+    (ms_max, value in GB/s)."""
+    ms_max = _max_over_ranks(ms, ws)
+    return ms_max, nbytes * ws * steps / (ms_max / 1e3) / 1e9
 
 
 def _barrier(ws):
@@ -148,6 +169,12 @@ def make_inputs(workload: str, scale: float, rank: int):
         x, _, _ = synth.kmeans_points(n, 64, 256, seed=synth.SEED_BASE + 3 + 1000 * rank)
         init = synth.kmeans_init(x, 256, seed=synth.SEED_BASE + 4 + 1000 * rank)
         return {"x": x, "init": init}
+    if workload == "histkeys":
+        n = max(1024, int(HK_KEYS * scale))
+        return {"keys": synth.keys_u32(n, HK_BINS, seed=synth.SEED_BASE + 5 + 1000 * rank)}
+    if workload == "bloom":
+        n = max(1024, int(BF_ELEMS * scale)) + BF_KMER - 1
+        return {"seq": synth.dna(n, seed=synth.SEED_BASE + 6 + 1000 * rank)}
     raise ValueError(workload)
 
 
@@ -162,6 +189,15 @@ def workload_config(workload: str, inp) -> dict:
         return {"workload": "k-means %d x %d FP32 points (%d B), K=%d, %d iterations" % (
             n, d, inp["x"].nbytes, inp["init"].shape[0], KM_ITERS),
             "inputs": "synthetic 256-component Gaussian mixture, resident in HBM, larger than L2"}
+    if workload == "histkeys":
+        return {"workload": "large-key histogram: %d u32 keys (%d B) uniform over %d bins" % (
+            inp["keys"].size, inp["keys"].nbytes, HK_BINS),
+            "inputs": "synthetic, resident in HBM, larger than L2 (no flush needed)",
+            "containers": "global array (u32 counters, 64 MiB, L2-resident), no local arrays"}
+    if workload == "bloom":
+        return {"workload": "Bloom-filter build: %d-base windows of %d uniform ACGT bases (%d elements) into %d bits, "
+                            "%d hashes" % (BF_KMER, inp["seq"].size, inp["seq"].size - BF_KMER + 1, BF_BITS, BF_HASHES),
+                "inputs": "synthetic, resident in HBM; the 37.5 MB filter is L2-resident"}
     return {"workload": "word count %d B Zipf(1) text, 50,000-word vocabulary" % inp["text"].nbytes,
             "inputs": "synthetic, resident in HBM; 16 MiB fits in L2 (warm)"}
 
@@ -198,7 +234,8 @@ def run_ours(args):
             b = ctx.add_job(mr.LINREG_I8, d_xy)
             ctx.run()
             return [a, b]
-        dominant = ("hist_smem_kernel", "paper_1309_0215_gb300/csrc/k_array.cu", d_px.numel())
+        dominant = ("hist_smem_kernel", ["paper_1309_0215_gb300/csrc/k_array.cu",
+                                         "paper_1309_0215_gb300/csrc/dev_array.cuh"], d_px.numel())
     elif args.workload == "kmeans":
         d_x, d_i = dinp["x"], dinp["init"]
         total_bytes = d_x.numel() * 4
@@ -211,7 +248,26 @@ def run_ours(args):
             ctx.run()
             return [a]
         kname = "km_tc_assign_kernel" if args.precision else "km_assign_fp32_kernel"
-        dominant = (kname, "paper_1309_0215_gb300/csrc/k_kmeans_tc.cu", d_x.numel() * 4)
+        dominant = (kname, ["paper_1309_0215_gb300/csrc/k_kmeans_tc.cu" if args.precision else
+                            "paper_1309_0215_gb300/csrc/k_kmeans.cu"], d_x.numel() * 4)
+    elif args.workload == "histkeys":
+        d_k = dinp["keys"]
+        total_bytes = d_k.numel() * 4
+
+        def step():
+            a = ctx.add_job(mr.HIST_U32, d_k, hist_bins=HK_BINS)
+            ctx.run()
+            return [a]
+        dominant = ("hk_global_kernel", ["paper_1309_0215_gb300/csrc/k_keys.cu"], d_k.numel() * 4)
+    elif args.workload == "bloom":
+        d_s = dinp["seq"]
+        total_bytes = d_s.numel()
+
+        def step():
+            a = ctx.add_job(mr.BLOOM_DNA, d_s, bloom_kmer=BF_KMER, bloom_bits=BF_BITS, bloom_hashes=BF_HASHES)
+            ctx.run()
+            return [a]
+        dominant = ("bloom_kernel", ["paper_1309_0215_gb300/csrc/k_keys.cu"], d_s.numel())
     else:
         d_t = dinp["text"]
         total_bytes = d_t.numel()
@@ -220,7 +276,8 @@ def run_ours(args):
             a = ctx.add_job(mr.WORDCOUNT, d_t)
             ctx.run()
             return [a]
-        dominant = ("wc_map_kernel", "paper_1309_0215_gb300/csrc/k_wordcount.cu", d_t.numel())
+        dominant = ("wc_map_kernel", ["paper_1309_0215_gb300/csrc/k_wordcount.cu",
+                                      "paper_1309_0215_gb300/csrc/dev_wordcount.cuh"], d_t.numel())
 
     # warm-up, plus a parity spot check of the last warm-up step
     jobs = []
@@ -230,6 +287,9 @@ def run_ours(args):
     if args.workload == "arrays":
         bins = np.frombuffer(ctx.fetch(jobs[-1][0]), dtype=np.uint64)
         assert int(bins.sum()) == 3 * (d_px.numel() // 3), "histogram invariant failed"
+    if args.workload == "histkeys":
+        bins = np.frombuffer(ctx.fetch(jobs[-1][0]), dtype=np.uint64)
+        assert int(bins.sum()) == d_k.numel() and int(bins[-1]) == 0, "histogram invariant failed"
     for js in jobs:
         for j in js:
             ctx.release(j)
@@ -253,9 +313,8 @@ def run_ours(args):
     for js in timed:
         for j in js:
             ctx.release(j)
-    ms_max = _max_over_ranks(ms, ws)
+    ms_max, value = combine_ranks(ms, total_bytes, args.steps, ws)
     ms_per_step = ms_max / args.steps
-    value = total_bytes * ws * args.steps / (ms_max / 1e3) / 1e9
 
     # end to end through the public API: pinned host inputs, H2D + run + D2H every step
     km_stats = None
@@ -271,11 +330,15 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e and args.workload != "kmeans":
         pinned = {k: torch.from_numpy(v).pin_memory() for k, v in inp.items()}
-        kinds = {"px": mr.HIST_RGB8, "xy": mr.LINREG_I8, "text": mr.WORDCOUNT}
+        adders = {"px": lambda t: ctx.add_job(mr.HIST_RGB8, t), "xy": lambda t: ctx.add_job(mr.LINREG_I8, t),
+                  "text": lambda t: ctx.add_job(mr.WORDCOUNT, t),
+                  "keys": lambda t: ctx.add_job(mr.HIST_U32, t, hist_bins=HK_BINS),
+                  "seq": lambda t: ctx.add_job(mr.BLOOM_DNA, t, bloom_kmer=BF_KMER, bloom_bits=BF_BITS,
+                                               bloom_hashes=BF_HASHES)}
         out_bytes = {}
 
         def e2e_step():
-            ids = [(k, ctx.add_job(kinds[k], t)) for k, t in pinned.items()]
+            ids = [(k, adders[k](t)) for k, t in pinned.items()]
             ctx.run()
             for k, j in ids:
                 out_bytes[k] = len(ctx.fetch(j))
@@ -314,6 +377,13 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": int(kbytes)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
         }
+        if args.workload == "histkeys":
+            line["updates"] = {"keys_per_s": round(d_k.numel() / (dom_ms / 1e3), 1),
+                               "note": "one counter increment per key (atomics after warp combining)"}
+        if args.workload == "bloom":
+            ne = d_s.numel() - BF_KMER + 1
+            line["updates"] = {"elements_per_s": round(ne / (dom_ms / 1e3), 1),
+                               "bit_sets_per_s": round(ne * BF_HASHES / (dom_ms / 1e3), 1)}
         if km_stats:
             line["kmeans"] = km_stats
             line["roofline"]["note"] = "achieved = one read of the points per job time (10 iterations)"
@@ -365,7 +435,7 @@ def run_batched(args):
         off = int(o * cap) // rec[k] * rec[k]
         return off, pools[k][off: off + n]
     total_bytes = sum(n for _, n, _ in specs)
-    ctx = mr.Context(0, stream=stream, autotune=True)
+    ctx = mr.Context(0, stream=stream, autotune=not args.no_autotune)
     ids = [ctx.add_job(kinds[k], slice_of(k, n, o)[1]) for k, n, o in specs]
     t0 = time.perf_counter()
     ctx.run(mr.RUN_BATCHED)
@@ -427,7 +497,8 @@ def run_batched(args):
 def serving_specs(rate: float, duration: float, seed: int):
     """Poisson arrivals; 25% each of word count, RGB histogram, int8 regression
     and k-means; sizes log-uniform on [1 KiB, 256 MiB] (k-means: D in [8, 64],
-    K in [16, 256], N in [64K, 2M] clamped to 256 MiB of points, 10 iterations)."""
+    K in [16, 256], N in [64K, 2M] clamped to 256 MiB of points, 10 iterations,
+    BF16 tensor-core path)."""
     import numpy as np
     rng = np.random.default_rng(seed)
     n = int(rate * duration * 1.2) + 16
@@ -485,7 +556,7 @@ def run_serving(args):
         else:
             npts, d, k, prec = p
             t = kpool[: npts * d].view(npts, d)
-            args_ = dict(km_dims=d, km_k=k, km_iters=10, km_init=t[:k].contiguous(), km_precision=prec)
+            args_ = dict(km_dims=d, km_k=k, km_iters=10, km_init=t[:k].contiguous(), km_precision=1)
             mk = mr.KMEANS_F32
         if plain:
             j = ctx.add_job(mk, t, **args_)
@@ -553,6 +624,20 @@ def cpu_baseline(workload, inp, max_seconds=30.0):
         el = time.perf_counter() - t0
         return {"value": round((px.nbytes + xy.nbytes) / el / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                 "sample": "one full step: histogram %d B + regression %d B, serial C++ oracle" % (px.nbytes, xy.nbytes)}
+    if workload == "histkeys":
+        k = inp["keys"][: 64 << 20]
+        t0 = time.perf_counter()
+        oracle.hist_u32(k, HK_BINS)
+        el = time.perf_counter() - t0
+        return {"value": round(k.nbytes / el / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                "sample": "first %d keys of the step's input, serial C++ oracle" % k.size}
+    if workload == "bloom":
+        sq = inp["seq"][: 10_000_000]
+        t0 = time.perf_counter()
+        oracle.bloom_dna(sq, BF_KMER, BF_BITS, BF_HASHES)
+        el = time.perf_counter() - t0
+        return {"value": round(sq.nbytes / el / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                "sample": "first %d bases of the step's input, serial C++ oracle" % sq.size}
     t = inp["text"]
     t0 = time.perf_counter()
     oracle.wordcount(t)
@@ -588,6 +673,24 @@ def run_reference(args):
             oracle.linreg_i8(sx)
         nbytes = sp.nbytes + sx.nbytes
         sample = "first %d B of the histogram input + first %d B of the regression input per step" % (sp.nbytes, sx.nbytes)
+    elif args.workload in ("histkeys", "bloom"):
+        a = inp["keys"] if args.workload == "histkeys" else inp["seq"]
+        if args.workload == "histkeys":
+            def run_on(x):
+                oracle.hist_u32(x, HK_BINS)
+        else:
+            def run_on(x):
+                oracle.bloom_dna(x, BF_KMER, BF_BITS, BF_HASHES)
+        t0 = time.perf_counter()
+        run_on(a[: 1 << 20])
+        rate = (1 << 20) / (time.perf_counter() - t0)  # elements per second
+        cnt = int(min(budget / nsteps * rate, a.size))
+        sa = a[: max(cnt, 64)]
+
+        def step():
+            run_on(sa)
+        nbytes = sa.nbytes
+        sample = "first %d %s of the input per step" % (sa.size, "keys" if args.workload == "histkeys" else "bases")
     else:
         t = inp["text"]
         t0 = time.perf_counter()
@@ -624,13 +727,15 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["arrays", "wordcount", "kmeans", "batched", "serving"], default="arrays")
+    ap.add_argument("--workload", choices=["arrays", "wordcount", "kmeans", "histkeys", "bloom", "batched", "serving"],
+                    default="arrays")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean requests per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
     ap.add_argument("--precision", type=int, default=1, help="k-means: 0 FP32, 1 BF16 split, 2 BF16 single")
     ap.add_argument("--scale", type=float, default=1.0, help="input size relative to the full workload")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="batched: keep the default tile sizes")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -69,7 +69,23 @@ typedef enum {
    * assign[n], zero padding to an 8-byte boundary, uint64 stats[4] =
    * {points re-checked in FP32, points re-checked in FP64, iterations,
    * device waits that timed out (0 unless mr_fetch returned MR_ETIMEOUT)}. */
-  MR_KMEANS_F32 = 3
+  MR_KMEANS_F32 = 3,
+  /* Large-key histogram (the paper's Histogram application with 16M unique
+   * keys, Sec. IV data sets; array container without local arrays,
+   * Sec. III-E).  Input: uint32 keys (input_bytes a multiple of 4, a device
+   * input 4-byte aligned); key k < hist_bins emits (k, 1), any other key
+   * (hist_bins, 1).  Output: uint64 bins[hist_bins + 1]. */
+  MR_HIST_U32 = 4,
+  /* Bloom-filter build (the paper's Bloom Filter application: k-mers of a
+   * chromosome, 30M elements into 300M entries, Sec. IV data sets; array
+   * container without local arrays, Sec. III-E).  Input: ASCII bases.  Each
+   * window of bloom_kmer bytes that are all 'A','C','G','T' is one element
+   * with code = base-4 number of the window (A=0 .. T=3, first base most
+   * significant).  With mix = the SplitMix64 output function, a = mix(code)
+   * mod m and b = 1 + mix(code ^ 0x9E3779B97F4A7C15) mod (m - 1), the element
+   * sets bits (a + i*b) mod m for i < bloom_hashes (m = bloom_bits).  Output:
+   * ceil(m / 8) bytes, bit j = bit (j mod 8) of byte j / 8. */
+  MR_BLOOM_DNA = 5
 } mr_kind;
 
 typedef enum {
@@ -143,6 +159,13 @@ typedef struct {
   uint32_t km_precision;  /* mr_km_precision */
   /* word count only: initial hash-table slots (power of two, 0 = automatic) */
   uint64_t wc_slots;
+  /* large-key histogram only: number of bins, >= 1 */
+  uint32_t hist_bins;
+  /* Bloom filter only: bases per element (1..32), bits set per element
+   * (1..32) and filter size in bits (2..2^32) */
+  uint32_t bloom_kmer;
+  uint32_t bloom_hashes;
+  uint64_t bloom_bits;
 } mr_job_desc;
 
 /* Create a context on cfg->device.  *out receives the handle.
@@ -159,10 +182,11 @@ void mr_destroy(mr_ctx* ctx);
 mr_status mr_add_job(mr_ctx* ctx, const mr_job_desc* desc, uint64_t* job_id);
 
 /* Enqueue every pending job on the context stream.  PLAIN launches each job's
- * kernels in order; BATCHED runs all pending word-count / histogram /
+ * kernels in order; BATCHED runs all pending word-count / RGB-histogram /
  * regression jobs in one persistent kernel, followed by one merge + sort for
- * all word-count jobs, captured as one CUDA graph (k-means jobs always run
- * plain).  Returns when the work is enqueued (an autotuning run waits). */
+ * all word-count jobs, captured as one CUDA graph (k-means, large-key
+ * histogram and Bloom-filter jobs always run plain, after the batch).
+ * Returns when the work is enqueued (an autotuning run waits). */
 mr_status mr_run(mr_ctx* ctx, mr_mode mode);
 
 /* Copy a finished job's result into host memory buf (buf_bytes long).

@@ -20,7 +20,7 @@ from ._build import LIB as _LIB_PATH, build as _build_lib, up_to_date as _up_to_
 
 # ---------------------------------------------------------------- constants
 MR_OK, MR_EINVAL, MR_ENOMEM, MR_ECUDA, MR_EOVERFLOW, MR_ETIMEOUT, MR_EBUDGET, MR_ENOTREADY, MR_ENOJOB = range(9)
-WORDCOUNT, HIST_RGB8, LINREG_I8, KMEANS_F32 = range(4)
+WORDCOUNT, HIST_RGB8, LINREG_I8, KMEANS_F32, HIST_U32, BLOOM_DNA = range(6)
 C_AUTO, C_SMEM_ARRAY, C_GLOBAL_ARRAY, C_HASH = range(4)
 RUN_PLAIN, RUN_BATCHED = range(2)
 KM_FP32, KM_BF16_TC, KM_BF16X1_TC = range(3)
@@ -59,7 +59,9 @@ class _JobDesc(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("kind", ctypes.c_int), ("input", ctypes.c_void_p),
                 ("input_bytes", ctypes.c_uint64), ("input_on_device", ctypes.c_int), ("container", ctypes.c_int),
                 ("km_dims", ctypes.c_uint32), ("km_k", ctypes.c_uint32), ("km_iters", ctypes.c_uint32),
-                ("km_init", ctypes.c_void_p), ("km_precision", ctypes.c_uint32), ("wc_slots", ctypes.c_uint64)]
+                ("km_init", ctypes.c_void_p), ("km_precision", ctypes.c_uint32), ("wc_slots", ctypes.c_uint64),
+                ("hist_bins", ctypes.c_uint32), ("bloom_kmer", ctypes.c_uint32), ("bloom_hashes", ctypes.c_uint32),
+                ("bloom_bits", ctypes.c_uint64)]
 
 
 _lib = None
@@ -195,7 +197,8 @@ class Context:
         self._keep = {}
 
     # ------------------------------------------------------------------ jobs
-    def _desc(self, kind, data, container, km_dims, km_k, km_iters, km_init, km_precision, wc_slots):
+    def _desc(self, kind, data, container, km_dims, km_k, km_iters, km_init, km_precision, wc_slots,
+              hist_bins=0, bloom_kmer=0, bloom_hashes=0, bloom_bits=0):
         addr, nbytes, on_dev, keep = _as_input(data)
         d = _JobDesc()
         d.struct_size = ctypes.sizeof(_JobDesc)
@@ -213,11 +216,16 @@ class Context:
             d.km_init = iaddr
         d.km_precision = int(km_precision)
         d.wc_slots = int(wc_slots)
+        d.hist_bins = int(hist_bins)
+        d.bloom_kmer, d.bloom_hashes, d.bloom_bits = int(bloom_kmer), int(bloom_hashes), int(bloom_bits)
         return d, (keep, keep_init) if on_dev else None
 
     def add_job(self, kind, data, container=C_AUTO, km_dims=0, km_k=0, km_iters=0, km_init=None,
-                km_precision=KM_FP32, wc_slots=0) -> int:
-        d, keep = self._desc(kind, data, container, km_dims, km_k, km_iters, km_init, km_precision, wc_slots)
+            km_precision=KM_FP32, wc_slots=0, **params) -> int:
+        """params: hist_bins (large-key histogram); bloom_kmer, bloom_hashes,
+        bloom_bits (Bloom filter)."""
+        d, keep = self._desc(kind, data, container, km_dims, km_k, km_iters, km_init, km_precision, wc_slots,
+                             **params)
         jid = ctypes.c_uint64()
         _check(self._lib.mr_add_job(self._h, ctypes.byref(d), ctypes.byref(jid)), "mr_add_job")
         if keep is not None:
@@ -225,8 +233,11 @@ class Context:
         return jid.value
 
     def submit(self, kind, data, container=C_AUTO, km_dims=0, km_k=0, km_iters=0, km_init=None,
-               km_precision=KM_FP32, wc_slots=0) -> int:
-        d, keep = self._desc(kind, data, container, km_dims, km_k, km_iters, km_init, km_precision, wc_slots)
+            km_precision=KM_FP32, wc_slots=0, **params) -> int:
+        """params: hist_bins (large-key histogram); bloom_kmer, bloom_hashes,
+        bloom_bits (Bloom filter)."""
+        d, keep = self._desc(kind, data, container, km_dims, km_k, km_iters, km_init, km_precision, wc_slots,
+                             **params)
         jid = ctypes.c_uint64()
         _check(self._lib.mr_submit(self._h, ctypes.byref(d), ctypes.byref(jid)), "mr_submit")
         if keep is not None:
@@ -343,6 +354,17 @@ def hist_rgb8(px, container=C_AUTO) -> np.ndarray:
 
 def linreg_i8(xy) -> np.ndarray:
     return np.frombuffer(_one(LINREG_I8, xy), dtype=np.int64).copy()
+
+
+def hist_u32(keys, nbins: int, container=C_AUTO) -> np.ndarray:
+    """uint64 [nbins + 1]: count of each key < nbins, then the out-of-range count."""
+    return np.frombuffer(_one(HIST_U32, keys, container=container, hist_bins=nbins), dtype=np.uint64).copy()
+
+
+def bloom_dna(seq, kmer: int, bits: int, hashes: int) -> np.ndarray:
+    """Bloom-filter bytes (ceil(bits / 8)) of every all-ACGT window of kmer bases."""
+    raw = _one(BLOOM_DNA, seq, bloom_kmer=kmer, bloom_bits=bits, bloom_hashes=hashes)
+    return np.frombuffer(raw, dtype=np.uint8).copy()
 
 
 def kmeans(x, init, iters: int, precision: int = KM_FP32):

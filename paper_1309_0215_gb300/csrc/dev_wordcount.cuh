@@ -19,9 +19,13 @@
 // job's overflow flag (the host then re-runs with a larger table).
 //
 // Local container (the paper's combiner, Sec. III-A, with the bounded local
-// table of Sec. III-D): every warp owns a 256-slot table in shared memory;
-// tokens are combined into it warp-synchronously, and it is flushed into the
-// global container when half full and at the end.
+// table of Sec. III-D), shaped for Zipf-like key streams: tokens of a warp
+// round that carry the same key are merged first (one match_any); then a
+// direct-mapped cache of hot keys per warp in shared memory (one compare, no
+// probing) absorbs the frequent keys, and the rest go straight to the global
+// container, where such rarer keys do not contend.  The cache is merged into
+// the global container every CACHE_EPOCH segments (so it can re-learn which
+// keys are hot) and at the end.
 #pragma once
 #include <cstdint>
 
@@ -31,8 +35,8 @@ namespace wc {
 constexpr int SEG = 512;                // bytes per warp step (16 per lane)
 constexpr int HALO = 64;                // staged bytes after the segment
 constexpr int BUF = SEG + HALO;
-constexpr int LT = 256;                 // local slots per warp
-constexpr int LT_FLUSH_AT = LT / 2;
+constexpr int LT = 128;                 // hot-key cache entries per warp
+constexpr int CACHE_EPOCH = 64;         // segments between cache merges
 constexpr int MAX_PROBES = 4096;
 constexpr uint64_t LONG_TAG = 0xFFull << 56;
 constexpr uint64_t LEN_MASK = (1ull << 56) - 1;
@@ -187,45 +191,44 @@ __device__ inline void global_insert(const JobDev& J, uint64_t w0, uint64_t w1, 
   atomicOr(J.state, 1u);
 }
 
-__device__ __forceinline__ bool local_equal(const WarpLocal& L, int s, const Tok& t, const uint8_t* __restrict__ in) {
-  if (L.w1[s] != t.w1) return false;
-  if (L.w0[s] == t.w0) return true;
-  return (t.w1 >> 56) == 0xFF && L.h[s] == t.h && long_equal(in, L.w0[s] - 1, t.w0 - 1, t.w1 & LEN_MASK);
-}
-
-// Warp-synchronous combine of one token per active lane into the warp's
-// local table; occ (warp-uniform) counts occupied slots.
-__device__ __forceinline__ void local_insert(WarpLocal& L, bool active, const Tok& t, int& occ,
-                                             const uint8_t* __restrict__ in) {
+// Combine one token per active lane; all 32 lanes call this together and
+// every collective is full-warp.  Lanes holding the same short key merge into
+// their lowest lane; each remaining (key, count) goes to the warp's hot-key
+// cache if its slot holds that key, or claims the slot if it is empty (the
+// lowest of the lanes that want the same empty slot wins), else goes to the
+// global container.  Long keys (>= 16 bytes) bypass the cache.
+__device__ __forceinline__ void combine_round(WarpLocal& L, bool active, const Tok& t, const JobDev& J) {
+  const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  int s = (int)(t.h & (LT - 1));
-  bool pending = active;
-  while (__any_sync(0xffffffffu, pending)) {
-    bool empty = false, match = false;
-    if (pending) {
-      if (L.w1[s] == 0) empty = true;
-      else match = local_equal(L, s, t, in);
-    }
-    if (match) {
-      atomicAdd(&L.cnt[s], 1u);
-      pending = false;
-    }
-    const unsigned em = __ballot_sync(0xffffffffu, empty);
-    bool claimed = false;
-    if (empty) {
-      const unsigned grp = __match_any_sync(em, s);  // lanes that found the same empty slot
-      claimed = lane == __ffs(grp) - 1;
-      if (claimed) {
-        L.w0[s] = t.w0;
-        L.w1[s] = t.w1;
-        L.h[s] = t.h;
-        L.cnt[s] = 0;
-      }
-    }
-    occ += __popc(__ballot_sync(0xffffffffu, claimed));
-    __syncwarp();
-    if (pending && !empty && !match) s = (s + 1) & (LT - 1);
+  const bool is_long = (t.w1 >> 56) == 0xFF;
+  // inactive lanes get a value no hash can take, so they group alone
+  const unsigned long long hkey = active ? (unsigned long long)t.h : ((1ull << 32) | (unsigned)lane);
+  const unsigned grp = __match_any_sync(FULL, hkey);
+  const int leader = __ffs(grp) - 1;
+  const uint64_t l0 = __shfl_sync(FULL, t.w0, leader), l1 = __shfl_sync(FULL, t.w1, leader);
+  const bool same = t.w0 == l0 && t.w1 == l1;
+  const bool merged = (__ballot_sync(FULL, same) & grp) == grp;
+  const bool handle = active && (!merged || lane == leader);
+  const uint32_t c = merged ? (uint32_t)__popc(grp) : 1u;
+  const int s = (int)(t.h & (LT - 1));
+  bool hit = false, empty = false;
+  if (handle && !is_long) {
+    const uint64_t r1 = L.w1[s];
+    hit = r1 == t.w1 && L.w0[s] == t.w0;
+    empty = r1 == 0;
   }
+  if (hit) atomicAdd(&L.cnt[s], c);
+  const bool want = handle && empty;
+  const unsigned long long skey = want ? (unsigned long long)s : ((1ull << 32) | (unsigned)lane);
+  const unsigned sg = __match_any_sync(FULL, skey);
+  const bool claim = want && lane == __ffs(sg) - 1;
+  if (claim) {
+    L.w0[s] = t.w0;
+    L.w1[s] = t.w1;
+    L.h[s] = t.h;
+    L.cnt[s] = c;
+  }
+  if (handle && !hit && !claim) global_insert(J, t.w0, t.w1, t.h, c);
 }
 
 __device__ inline void local_clear(WarpLocal& L) {
@@ -233,7 +236,9 @@ __device__ inline void local_clear(WarpLocal& L) {
   __syncwarp();
 }
 
+// Merge the warp's cache into the global container and empty it.
 __device__ inline void local_flush(WarpLocal& L, int& occ, const JobDev& J) {
+  __syncwarp();
   for (int s = threadIdx.x & 31; s < LT; s += 32) {
     if (L.w1[s] != 0) {
       global_insert(J, L.w0[s], L.w1[s], L.h[s], L.cnt[s]);
@@ -291,15 +296,16 @@ __device__ inline void warp_segment(const JobDev& J, uint64_t seg, WarpLocal& L,
   }
   __syncwarp();
   for (int r0 = 0; r0 < total; r0 += 32) {
-    if (occ >= LT_FLUSH_AT) local_flush(L, occ, J);
     const int i = r0 + lane;
     const bool active = i < total;
     Tok t;
     if (active) t = read_token(in, n, base, L.buf, L.starts[i]);
     else t.w0 = 0, t.w1 = 0, t.h = 0;
-    local_insert(L, active, t, occ, in);
+    combine_round(L, active, t, J);
+    __syncwarp();
   }
-  __syncwarp();
+  // occ counts segments since the last cache merge
+  if (++occ >= CACHE_EPOCH) local_flush(L, occ, J);
 }
 
 }  // namespace wc

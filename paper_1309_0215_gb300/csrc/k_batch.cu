@@ -23,11 +23,15 @@
 namespace mrgb {
 namespace {
 
-constexpr int BT = 256;
+// 16 warps per CTA, two CTAs per SM: 32 warps per SM keep the word-count
+// tiles' latency-bound loops fed; the histogram tiles share one 96 KiB
+// lane-column table per CTA (64 registers per thread at this shape).
+constexpr int BT = 512;
 constexpr int BWARPS = BT / 32;
 constexpr int B_SMEM_HIST = arr::HIST_WORDS * 4;
 constexpr int B_SMEM_WC = BWARPS * (int)sizeof(wc::WarpLocal);
 constexpr int B_SMEM = B_SMEM_HIST > B_SMEM_WC ? B_SMEM_HIST : B_SMEM_WC;
+static_assert(2 * B_SMEM + 4096 <= 232448, "two batch CTAs must fit one SM's shared memory");
 
 __device__ __forceinline__ uint32_t find_job(const BatchJob* jobs, uint32_t njobs, uint64_t t) {
   uint32_t lo = 0, hi = njobs - 1;

@@ -37,24 +37,37 @@ constexpr int TP = 64;            // points per tile (8 per warp)
 constexpr int KC_MAX = 256;       // centroids per chunk (8 per lane)
 constexpr int DC_MAX = 64;        // dims per chunk
 
-__device__ __forceinline__ void best2_push(float d, int k, float& d1, int& k1, float& d2) {
-  if (d < d1 || (d == d1 && k < k1)) {
-    d2 = d1;
-    d1 = d;
-    k1 = k;
-  } else if (d < d2) {
-    d2 = d;
+// Running top three distances (the two smallest with their indices);
+// between equal distances the lower index ranks first.
+struct Top3 {
+  float d1, d2, d3;
+  int k1, k2;
+};
+__device__ __forceinline__ void top3_init(Top3& t) {
+  t.d1 = t.d2 = t.d3 = INFINITY;
+  t.k1 = t.k2 = 0x7fffffff;
+}
+__device__ __forceinline__ void top3_push(Top3& t, float d, int k) {
+  if (d < t.d1 || (d == t.d1 && k < t.k1)) {
+    t.d3 = t.d2;
+    t.d2 = t.d1;
+    t.k2 = t.k1;
+    t.d1 = d;
+    t.k1 = k;
+  } else if (d < t.d2 || (d == t.d2 && k < t.k2)) {
+    t.d3 = t.d2;
+    t.d2 = d;
+    t.k2 = k;
+  } else if (d < t.d3) {
+    t.d3 = d;
   }
 }
-
-__device__ __forceinline__ void best2_merge(float& d1, int& k1, float& d2, float e1, int f1, float e2) {
-  if (e1 < d1 || (e1 == d1 && f1 < k1)) {
-    d2 = fminf(d1, e2);
-    d1 = e1;
-    k1 = f1;
-  } else {
-    d2 = fminf(d2, e1);
-  }
+// merge another triple in (its third index is never needed: a third value
+// can only rank third)
+__device__ __forceinline__ void top3_merge(Top3& t, const Top3& o) {
+  top3_push(t, o.d1, o.k1);
+  top3_push(t, o.d2, o.k2);
+  top3_push(t, o.d3, 0x7fffffff);
 }
 
 // Centroid norms: cn[k] = ||c_k||^2 (FP32, sequential FMA); cmax[0] = max ||c_k||.
@@ -71,6 +84,7 @@ __global__ void km_prep_kernel(const float* __restrict__ c, uint32_t k, uint32_t
   for (uint64_t i = tid; i < (uint64_t)k * d; i += nth) sums[i] = 0;
   for (uint64_t i = tid; i < (uint64_t)k; i += nth) counts[i] = 0;
   if (tid < 2) nflag[tid] = 0;
+  if (tid == 2) nflag[4] = 0;  // pair list
 }
 
 // FP32 assignment.  A CTA processes tiles of 64 points; warp w owns points
@@ -83,7 +97,7 @@ __global__ void __launch_bounds__(KM_THREADS, 2)
 km_assign_fp32_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const float* __restrict__ c, uint32_t k,
                       const float* __restrict__ cn, const unsigned int* cmax_bits, const uint32_t* idx,
                       const uint32_t* nidx, int32_t* __restrict__ assign, uint32_t* flagged, uint32_t* nflag,
-                      unsigned long long* stat) {
+                      uint2* __restrict__ pairs, uint32_t* npairs, unsigned long long* stat) {
   extern __shared__ float km_sm[];
   const int dc = d < DC_MAX ? (int)d : DC_MAX;
   const int kc = k < KC_MAX ? (int)k : KC_MAX;
@@ -111,10 +125,9 @@ km_assign_fp32_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const
   const uint32_t ntiles = (npts + TP - 1) / TP;
   for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const uint32_t p0 = tile * TP;
-    float d1[8], d2[8];
-    int k1[8];
+    Top3 tp[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) d1[i] = d2[i] = INFINITY, k1[i] = 0x7fffffff;
+    for (int i = 0; i < 8; ++i) top3_init(tp[i]);
     float nxacc = 0.f;  // ||x||^2 of point threadIdx.x (threads < TP), FMA over dims in order
     for (uint32_t k0 = 0; k0 < k; k0 += KC_MAX) {
       float acc[8][8];
@@ -166,7 +179,7 @@ km_assign_fp32_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const float dist = fmaf(-2.f, acc[i][j], nx_s[warp * 8 + i]) + ncv;
-            best2_push(dist, (int)kk, d1[i], k1[i], d2[i]);
+            top3_push(tp[i], dist, (int)kk);
           }
         }
       }
@@ -175,26 +188,41 @@ km_assign_fp32_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       for (int o = 16; o; o >>= 1) {
-        const float e1 = __shfl_xor_sync(0xffffffffu, d1[i], o);
-        const int f1 = __shfl_xor_sync(0xffffffffu, k1[i], o);
-        const float e2 = __shfl_xor_sync(0xffffffffu, d2[i], o);
-        best2_merge(d1[i], k1[i], d2[i], e1, f1, e2);
+        Top3 ot;
+        ot.d1 = __shfl_xor_sync(0xffffffffu, tp[i].d1, o);
+        ot.d2 = __shfl_xor_sync(0xffffffffu, tp[i].d2, o);
+        ot.d3 = __shfl_xor_sync(0xffffffffu, tp[i].d3, o);
+        ot.k1 = __shfl_xor_sync(0xffffffffu, tp[i].k1, o);
+        ot.k2 = __shfl_xor_sync(0xffffffffu, tp[i].k2, o);
+        top3_merge(tp[i], ot);
       }
     }
     // lane i decides point i of the warp
-    float md1 = 0.f, md2 = 0.f;
-    int mk1 = 0;
+    Top3 mt;
+    top3_init(mt);
 #pragma unroll
     for (int i = 0; i < 8; ++i)
-      if (lane == i) md1 = d1[i], md2 = d2[i], mk1 = k1[i];
+      if (lane == i) mt = tp[i];
     const uint32_t pi = p0 + warp * 8 + lane;
-    bool flag = false;
+    bool flag = false, pair = false;
     if (lane < 8 && pi < npts) {
       const uint32_t p = idx ? idx[pi] : pi;
       const float nxv = sqrtf(nx_s[warp * 8 + lane]);
       const float e = eps * (nxv + cmax) * (nxv + cmax);
-      if (md2 - md1 > 2.f * e) assign[p] = mk1;
+      // only the top two can be the exact minimum when the third is 2E away
+      if (mt.d2 - mt.d1 > 2.f * e) assign[p] = mt.k1;
+      else if (mt.d3 - mt.d1 > 2.f * e) pair = true;
       else flag = true;
+    }
+    const unsigned pm = __ballot_sync(0xffffffffu, pair);
+    if (pm) {
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(npairs, (uint32_t)__popc(pm));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (pair) {
+        const uint32_t p = idx ? idx[pi] : pi;
+        pairs[base + __popc(pm & ((1u << lane) - 1))] = make_uint2(p, (uint32_t)mt.k1 | ((uint32_t)mt.k2 << 16));
+      }
     }
     const unsigned fm = __ballot_sync(0xffffffffu, flag);
     if (fm) {
@@ -206,6 +234,34 @@ km_assign_fp32_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const
         flagged[base + __popc(fm & ((1u << lane) - 1))] = p;
       }
     }
+  }
+}
+
+// Exact FP64 choice between the two candidates of each listed point (the
+// definition's operation order: dimensions in order, separately rounded
+// subtract, multiply and add); the lower index wins an exact tie.
+__device__ __forceinline__ double dist64(const float* __restrict__ xp, const float* __restrict__ cp, uint32_t d) {
+  double s = 0.0;
+  for (uint32_t j = 0; j < d; ++j) {
+    const double t = __dsub_rn((double)xp[j], (double)cp[j]);
+    s = __dadd_rn(s, __dmul_rn(t, t));
+  }
+  return s;
+}
+
+__global__ void km_pair_kernel(const float* __restrict__ x, uint32_t d, const float* __restrict__ c,
+                               const uint2* __restrict__ pairs, const uint32_t* npairs, int32_t* assign,
+                               unsigned long long* stat) {
+  const uint32_t np = *npairs;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid == 0 && stat) atomicAdd(stat, (unsigned long long)np);
+  for (uint64_t i = tid; i < np; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint2 e = pairs[i];
+    const uint32_t k1 = e.y & 0xffffu, k2 = e.y >> 16;
+    const float* xp = x + (uint64_t)e.x * d;
+    const double s1 = dist64(xp, c + (uint64_t)k1 * d, d);
+    const double s2 = dist64(xp, c + (uint64_t)k2 * d, d);
+    assign[e.x] = (s2 < s1 || (s2 == s1 && k2 < k1)) ? (int32_t)k2 : (int32_t)k1;
   }
 }
 
@@ -269,6 +325,72 @@ __global__ void km_recheck_fp64_kernel(const float* __restrict__ x, uint32_t d, 
       if (ob < best || (ob == best && ok < bk)) best = ob, bk = ok;
     }
     if (lane == 0) assign[p] = bk == 0x7fffffff ? 0 : bk;  // all-NaN distances: index 0, as the definition
+  }
+}
+
+// The same re-check with the centroids staged in shared memory (row stride
+// D + 1 floats: lanes reading different rows at one column hit different
+// banks).  Lane l owns centroids l, l+32, ... (at most KLANE of them): one
+// pass computes their FP32 distances into registers, the warp takes the
+// minimum, and each lane evaluates in FP64 only its own candidates.
+constexpr int KLANE = 8;  // K <= 256
+__global__ void km_recheck_fp64_smem_kernel(const float* __restrict__ x, uint32_t d, const float* __restrict__ c,
+                                            uint32_t k, const uint32_t* flagged, const uint32_t* nflag,
+                                            int32_t* assign, unsigned long long* stat) {
+  extern __shared__ float cs[];  // [k][d + 1]
+  const uint32_t ld = d + 1;
+  for (uint32_t t = threadIdx.x; t < k * d; t += blockDim.x) cs[(t / d) * ld + (t % d)] = c[t];
+  __syncthreads();
+  const uint32_t nf = *nflag;
+  const int lane = threadIdx.x & 31;
+  const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  if (w0 == 0 && lane == 0 && stat) atomicAdd(stat, (unsigned long long)nf);
+  const float g = 1.01f * (float)(d + 8) * 5.9604644775390625e-08f;
+  const float widen = (1.f + g) / (1.f - g) * (1.f + 4.f * 5.9604644775390625e-08f);
+  for (uint64_t f = w0; f < nf; f += nw) {
+    const uint32_t p = flagged[f];
+    const float* xp = x + (uint64_t)p * d;
+    float dist[KLANE];
+#pragma unroll
+    for (int q = 0; q < KLANE; ++q) dist[q] = 0.f;
+    for (uint32_t j = 0; j < d; ++j) {
+      const float xv = __ldg(xp + j);
+#pragma unroll
+      for (int q = 0; q < KLANE; ++q) {
+        const uint32_t kk = lane + 32 * q;
+        if (kk < k) {
+          const float t = xv - cs[kk * ld + j];
+          dist[q] = fmaf(t, t, dist[q]);
+        }
+      }
+    }
+    float m32 = INFINITY;
+#pragma unroll
+    for (int q = 0; q < KLANE; ++q)
+      if (lane + 32 * q < k) m32 = fminf(m32, dist[q]);
+    for (int o = 16; o; o >>= 1) m32 = fminf(m32, __shfl_xor_sync(0xffffffffu, m32, o));
+    const float lim = m32 * widen;
+    double best = INFINITY;
+    int bk = 0x7fffffff;
+#pragma unroll
+    for (int q = 0; q < KLANE; ++q) {
+      const uint32_t kk = lane + 32 * q;
+      if (kk < k && (dist[q] <= lim || m32 != m32)) {
+        double s64 = 0.0;
+        for (uint32_t j = 0; j < d; ++j) {
+          const double t = __dsub_rn((double)__ldg(xp + j), (double)cs[kk * ld + j]);
+          s64 = __dadd_rn(s64, __dmul_rn(t, t));
+        }
+        if (s64 < best) best = s64, bk = (int)kk;  // kk increases per lane: the lowest index keeps a tie
+      }
+    }
+    for (int o = 16; o; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+      if (ob < best || (ob == best && ok < bk)) best = ob, bk = ok;
+    }
+    if (lane == 0) assign[p] = bk == 0x7fffffff ? 0 : bk;
   }
 }
 
@@ -467,6 +589,7 @@ __global__ void km_finish_kernel(const float* c, uint64_t kd, float* out_c, cons
   for (uint64_t i = tid; i < kd; i += nth) out_c[i] = c[i];
   for (uint64_t i = tid; i < n; i += nth) out_a[i] = assign[i];
   if (tid == 0) {
+    if ((kd + n) & 1) out_a[n] = 0;  // the zero padding before the 8-byte aligned stats
     out_s[0] = stats[0];
     out_s[1] = stats[1];
     out_s[2] = iters;
@@ -486,7 +609,8 @@ size_t km_scratch_bytes(uint32_t n, uint32_t d, uint32_t k, int precision) {
   b += a256((uint64_t)k * 8);          // counts
   b += a256(4 * 8);                    // stats
   b += a256((uint64_t)n * 4);          // flagged
-  b += a256(4 * 4);                    // nflag[2], maxabs, cmax
+  b += a256(8 * 4);                    // counters: nflag[2], maxabs, cmax, pairs
+  b += a256((uint64_t)n * 8);          // pair list
   b += a256((uint64_t)k * 4 * 2);      // cnorm (||c||^2) + spare
   b += a256(16);                       // shift
   b += a256((uint64_t)k * 4);          // per-cluster write cursor
@@ -507,7 +631,8 @@ cudaError_t km_carve(KmBuffers& b, uint8_t* p, size_t bytes) {
   b.counts = reinterpret_cast<unsigned long long*>(take(k * 8));
   b.stats = reinterpret_cast<unsigned long long*>(take(32));
   b.flagged = reinterpret_cast<uint32_t*>(take(n * 4));
-  b.nflag = reinterpret_cast<uint32_t*>(take(16));
+  b.nflag = reinterpret_cast<uint32_t*>(take(32));
+  b.pairs = reinterpret_cast<uint2*>(take(n * 8));
   b.maxabs = reinterpret_cast<unsigned int*>(b.nflag + 2);
   b.cnorm = reinterpret_cast<float*>(take(k * 8));
   b.cent_bf16_norm = nullptr;
@@ -536,7 +661,7 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
   unsigned int* cmax_bits = b.nflag + 3;
   if ((e = cudaMemcpyAsync(b.cent, init, (size_t)k * d * 4, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(b.stats, 0, 32, s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(b.nflag, 0, 16, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(b.nflag, 0, 32, s)) != cudaSuccess) return e;
   km_maxabs_kernel<<<di.sms * 4, 256, 0, s>>>(x, (uint64_t)n * d, b.maxabs);
   km_scale_kernel<<<1, 1, 0, s>>>(b.maxabs, n, shift);
   *nk += 2;
@@ -550,6 +675,12 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
   if ((e = cudaFuncSetAttribute(km_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(k * 4))) !=
       cudaSuccess)
     return e;
+  const int rc_bytes = (int)((uint64_t)k * (d + 1) * 4);
+  const bool rc_smem = k <= 32 * KLANE && rc_bytes <= di.smem_optin;
+  if (rc_smem &&
+      (e = cudaFuncSetAttribute(km_recheck_fp64_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, rc_bytes)) !=
+          cudaSuccess)
+    return e;
   const uint32_t ntiles = (n + TP - 1) / TP;
   const uint32_t agrid = ntiles < (uint32_t)di.sms * 2 ? ntiles : (uint32_t)di.sms * 2;
   for (uint32_t it = 0; it < iters; ++it) {
@@ -558,10 +689,17 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
       if ((e = launch_kmeans_tc_assign(x, n, d, b.cent, k, b, di, s, nk)) != cudaSuccess) return e;
     } else {
       km_assign_fp32_kernel<<<agrid, KM_THREADS, asm_bytes, s>>>(x, n, d, b.cent, k, b.cnorm, cmax_bits, nullptr,
-                                                                 nullptr, b.assign, b.flagged, b.nflag, nullptr);
+                                                                 nullptr, b.assign, b.flagged, b.nflag, b.pairs,
+                                                                 b.nflag + 4, nullptr);
       ++*nk;
     }
-    km_recheck_fp64_kernel<<<di.sms * 4, 256, 0, s>>>(x, d, b.cent, k, b.flagged, b.nflag, b.assign, b.stats + 1);
+    km_pair_kernel<<<di.sms * 2, 256, 0, s>>>(x, d, b.cent, b.pairs, b.nflag + 4, b.assign, b.stats + 1);
+    ++*nk;
+    if (rc_smem)
+      km_recheck_fp64_smem_kernel<<<di.sms, 512, rc_bytes, s>>>(x, d, b.cent, k, b.flagged, b.nflag, b.assign,
+                                                                b.stats + 1);
+    else
+      km_recheck_fp64_kernel<<<di.sms * 4, 256, 0, s>>>(x, d, b.cent, k, b.flagged, b.nflag, b.assign, b.stats + 1);
     // update: counting sort of the points by cluster, then run-wise sums
     km_count_kernel<<<di.sms * 2, 512, k * 4, s>>>(b.assign, n, k, b.counts);
     km_offsets_kernel<<<1, 1024, 0, s>>>(b.counts, k, b.kcursor);
@@ -587,7 +725,8 @@ cudaError_t launch_kmeans_fp32_list(const float* x, uint32_t n, uint32_t d, cons
   const uint32_t ntiles = (n + TP - 1) / TP;
   const uint32_t agrid = ntiles < (uint32_t)di.sms * 2 ? ntiles : (uint32_t)di.sms * 2;
   km_assign_fp32_kernel<<<agrid, KM_THREADS, asm_bytes, s>>>(x, n, d, c, k, b.cnorm, b.nflag + 3, list, nlist,
-                                                             b.assign, b.flagged, b.nflag, b.stats);
+                                                             b.assign, b.flagged, b.nflag, b.pairs, b.nflag + 4,
+                                                             b.stats);
   ++*nk;
   return cudaGetLastError();
 }

@@ -5,9 +5,12 @@
 // The distance d(x, c) = ||x||^2 - 2 x.c + ||c||^2 needs the cross term x.c,
 // a dense (points x D) . (D x K) contraction — the one step of the hot path
 // that is a real GEMM.  Per tile of 128 points:
-//   * 8 converter warps load the FP32 rows (coalesced 128-bit loads), compute
-//     ||x||^2 in FP32, and write BF16 operands in the 128-byte-swizzled
-//     K-major layout the MMA reads.  With TERMS = 3 each value is split as
+//   * for D = 64 one producer thread moves each FP32 tile (128 rows, 32 KB,
+//     contiguous) into a two-deep shared-memory ring with one bulk copy
+//     (cp.async.bulk, completion counted on an mbarrier), so loads stay in
+//     flight without registers; 8 converter warps read the tile (or load it
+//     themselves for other D), compute ||x||^2 in FP32, and write BF16
+//     operands in the 128-byte-swizzled K-major layout the MMA reads.  With TERMS = 3 each value is split as
 //     x = hi + lo (hi = bf16(x), lo = bf16(x - hi)) and the MMA accumulates
 //     hi.hi + hi.lo + lo.hi, so the cross term is good to about 2^-15
 //     relative; TERMS = 1 is the plain single BF16 product.
@@ -16,12 +19,13 @@
 //     accumulators, and commits completion to mbarriers;
 //   * 8 epilogue warps read the 128 x N FP32 tile with tcgen05.ld (one TMEM
 //     lane per point; two warps per lane quadrant, each on half of the
-//     columns), form d~ = fma(-2, acc, ||x||^2) + ||c||^2 and keep the two
-//     smallest with four independent branch-free running minima per thread;
-//     the upper half hands its pair to the lower half, which applies the
-//     margin test below.
-// Converters, MMA issue and epilogue overlap through three operand stages
-// and two TMEM accumulators.  Every mbarrier wait is bounded; on timeout the
+//     columns), form d~ = fma(-2, acc, ||x||^2) + ||c||^2, pack it with its
+//     column into one sortable 32-bit key and keep the three smallest keys
+//     with unsigned min/max (eight independent top-3s per thread); the upper
+//     half hands its top-3 to the lower half, which applies the margin tests
+//     below.
+// Copies, converters, MMA issue and epilogue overlap through the staging
+// ring, two operand stages and two TMEM accumulators.  Every mbarrier wait is bounded; on timeout the
 // CTA stops, drains its MMAs, frees TMEM and reports through stats[3].
 //
 // Margin test (rigorous, per point).  With u_b = 2^-8 (BF16 rounding) the
@@ -31,9 +35,13 @@
 // exact BF16 products is charged (products + 8) * 2^-21 ||x|| ||c|| (four
 // times the round-to-nearest bound, allowing truncating adders), and the FP32
 // norms and the final fma/add (D + 8) * 2^-24 (||x|| + ||c||)^2 (Higham,
-// eq. 3.5).  If d~_2 - d~_1 > max(1e-3 d~_1, 2E) the tensor-core winner is
-// the exact winner; every other point goes to the FP32 pass (and from there,
-// if still close, to the FP64 pass), so assignments equal the FP64 argmin.
+// eq. 3.5).  The keys hold d~ truncated to 16 mantissa bits (t <= d~ <
+// t (1 + 2^-15)), so with G = 2E + 2^-14 t_1: if t_2 - t_1 > max(1e-3 t_1, G)
+// the tensor-core winner is the exact winner.  Otherwise, if t_3 - t_1 > G,
+// every centroid but the top two has exact distance above t_1 (1 + 2^-15) + E
+// >= d(k_1), so the point only needs an exact FP64 choice between those two
+// (pair list); every other point goes to the FP32 pass (and from there, if
+// still close, to FP64), so assignments equal the FP64 argmin.
 #include <cuda_bf16.h>
 
 #include "mr_internal.h"
@@ -48,24 +56,29 @@ constexpr int EPI_WARPS = 8;      // two per TMEM lane quadrant, each on half th
 constexpr int MMA_WARP = 8;
 constexpr int CVT_WARP0 = 9;
 constexpr int CVT_WARPS = 8;
-constexpr int TC_THREADS = (EPI_WARPS + 1 + CVT_WARPS) * 32;  // 544
-constexpr int STAGES = 3;         // operand stages
+constexpr int TMA_WARP = CVT_WARP0 + CVT_WARPS;  // 17
+constexpr int TC_THREADS = (EPI_WARPS + 1 + CVT_WARPS + 1) * 32;  // 576
+constexpr int STAGES = 2;         // operand stages
+constexpr int XST = 2;            // FP32 staging buffers filled by the bulk copy engine
 constexpr int ACCS = 2;           // TMEM accumulators
 constexpr uint32_t TMEM_COLS = 512;  // two 256-column FP32 accumulators
 constexpr long long SPIN_LIMIT = 1ll << 24;
+constexpr int NSET = 8;           // independent running top-3s per epilogue thread
+constexpr int CHUNK = 32;         // TMEM columns per tcgen05.ld in the epilogue
 
 struct __align__(1024) TcSmem {
   uint8_t b_hi[NMAX * 128];
   uint8_t b_lo[NMAX * 128];
   uint8_t a_hi[STAGES][TM * 128];
   uint8_t a_lo[STAGES][TM * 128];
+  float xs[XST][TM * KD];             // FP32 point tiles (D == 64 path)
   float nx[STAGES][TM];
   float cn[NMAX];
-  float xd1[ACCS][TM], xd2[ACCS][TM];  // top-2 of the upper column half, per row
-  int xk1[ACCS][TM];
+  uint32_t xt1[ACCS][TM], xt2[ACCS][TM], xt3[ACCS][TM];  // top-3 keys of the upper column half, per row
   unsigned long long full_a[STAGES], empty_a[STAGES], nx_free[STAGES];
   unsigned long long full_acc[ACCS], empty_acc[ACCS], drained;
   unsigned long long xfull[ACCS], xfree[ACCS];  // upper-half top-2 handed to the lower half
+  unsigned long long tfull[XST], tempty[XST];   // FP32 staging ring
   uint32_t tmem_base;
   int err;
 };
@@ -95,6 +108,18 @@ __device__ bool mbar_wait(unsigned long long* b, uint32_t parity, volatile int* 
   }
   *err = 1;
   return false;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+// One contiguous global -> shared copy by the bulk copy engine; completion is
+// signalled as transaction bytes on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(dst)),
+      "l"(src), "r"(bytes), "r"(su32(b))
+      : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -137,6 +162,84 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 64 consecutive TMEM columns of this warp's 32 lanes (one FP32 each).
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+      "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+      "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]),
+        "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]),
+        "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]),
+        "=r"(v[48]), "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]),
+        "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[32]) { tmem_ld32(taddr, v); }
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[64]) { tmem_ld64(taddr, v); }
+
+// Sortable key of a distance: its FP32 bit pattern (a negative value, which
+// only rounding can produce, counts as 0) with the low 8 mantissa bits
+// replaced by the centroid column.  For non-negative floats the bit pattern
+// is monotonic, so keys order by distance truncated to 16 mantissa bits
+// (an under-statement of less than 2^-15 of the distance), then by column.
+__device__ __forceinline__ uint32_t dist_key(float dist, uint32_t col) {
+  return ((uint32_t)max((int)__float_as_uint(dist), 0) & 0xFFFFFF00u) | col;
+}
+__device__ __forceinline__ float key_dist(uint32_t key) { return __uint_as_float(key & 0xFFFFFF00u); }
+
+// Insert key into the sorted triple (t1 <= t2 <= t3): five min/max.
+__device__ __forceinline__ void top3_insert(uint32_t& t1, uint32_t& t2, uint32_t& t3, uint32_t key) {
+  const uint32_t h1 = max(t1, key);
+  t1 = min(t1, key);
+  const uint32_t h2 = max(t2, h1);
+  t2 = min(t2, h1);
+  t3 = min(t3, h2);
+}
+
+// Smallest three of two sorted triples: the j-th smallest of the union is
+// the minimum over i of max(a_i, b_{j-i}).
+__device__ __forceinline__ void top3_merge_keys(uint32_t& a1, uint32_t& a2, uint32_t& a3, uint32_t b1, uint32_t b2,
+                                                uint32_t b3) {
+  const uint32_t c3 = min(min(a3, b3), min(max(a2, b1), max(a1, b2)));
+  const uint32_t c2 = min(min(a2, b2), max(a1, b1));
+  a1 = min(a1, b1);
+  a2 = c2;
+  a3 = c3;
+}
+
+// Distances of CHUNK columns (ch .. ch + CHUNK - 1) of one point into its eight running
+// top-3s.  MASK: some columns are >= k (their TMEM words are not written by
+// the MMA and may hold anything), so those keys are forced to the maximum.
+template <bool MASK>
+__device__ __forceinline__ void top3_keys(const uint32_t (&acc)[CHUNK], uint32_t ch, float nxv, const float* cn,
+                                          uint32_t k, uint32_t (&t1)[NSET], uint32_t (&t2)[NSET], uint32_t (&t3)[NSET],
+                                          float* dbg_row) {
+#pragma unroll
+  for (int j = 0; j < CHUNK; j += 4) {
+    const float4 c4 = *reinterpret_cast<const float4*>(cn + ch + j);
+    const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const uint32_t kk = ch + (uint32_t)(j + e);
+      const float dist = fmaf(-2.f, __uint_as_float(acc[j + e]), nxv) + cv[e];
+      uint32_t key = dist_key(dist, kk);
+      if (MASK) {
+        if (kk >= k) key = 0xFFFFFFFFu;
+        else if (dbg_row) dbg_row[kk] = dist;
+      }
+      const int a = (j + e) % NSET;
+      top3_insert(t1[a], t2[a], t3[a], key);
+    }
+  }
+}
+
 // BF16 hi/lo split of two values, packed little-endian (element 0 low half).
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
   const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
@@ -154,7 +257,8 @@ template <int TERMS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const float* __restrict__ c, uint32_t k,
                     const float* __restrict__ cnorm, const unsigned int* cmax_bits, int32_t* __restrict__ assign,
-                    uint32_t* __restrict__ list, uint32_t* nlist, unsigned long long* timeouts, float* dbg) {
+                    uint32_t* __restrict__ list, uint32_t* nlist, uint2* __restrict__ pairs, uint32_t* npairs,
+                    unsigned long long* timeouts, float* dbg) {
   extern __shared__ uint8_t tc_raw[];
   TcSmem& S = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -174,6 +278,10 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
       mbar_init(&S.empty_acc[b], EPI_WARPS);
       mbar_init(&S.xfull[b], EPI_WARPS / 2);
       mbar_init(&S.xfree[b], EPI_WARPS / 2);
+    }
+    for (int q = 0; q < XST; ++q) {
+      mbar_init(&S.tfull[q], 1);
+      mbar_init(&S.tempty[q], CVT_WARPS);
     }
     mbar_init(&S.drained, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -208,33 +316,42 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
   const uint32_t tmem = S.tmem_base;
   const float cmax = __uint_as_float(*cmax_bits);
 
-  if (warp >= CVT_WARP0) {
+  if (warp >= CVT_WARP0 && warp < CVT_WARP0 + CVT_WARPS) {
     // ---------------------------------------------------------- converters
-    const int ct = threadIdx.x - CVT_WARP0 * 32;  // 0..255
-    const int r = ct >> 1, h = ct & 1;
+    // Warp cw owns tile rows 16 cw .. 16 cw + 15.  Step q gives lane l row
+    // 16 cw + 2q + l / 16 and dims 4 (l % 16) .. + 3, so one warp load reads
+    // two whole FP32 rows (512 contiguous bytes) and one warp store writes
+    // two whole 128-byte swizzled BF16 rows: no shared-memory bank conflicts.
+    const int cw = warp - CVT_WARP0;
+    const int col = lane & 15, rsub = lane >> 4;
     const bool vec = d == KD && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
     for (uint32_t i = 0;; ++i) {
       const uint32_t tile = blockIdx.x + i * gridDim.x;
       if (tile >= ntiles) break;
       const int s = (int)(i % STAGES);
       const uint32_t u = i / STAGES;
-      const uint32_t p = tile * TM + r;
-      float v[32];
-      if (p < n && vec) {
-        const float4* src = reinterpret_cast<const float4*>(x + (uint64_t)p * KD + h * 32);
+      const int q2 = (int)(i % XST);
+      float4 v[8];
+      if (vec) {
+        // the tile was staged by the bulk copy engine
+        const bool okt = mbar_wait(&S.tfull[q2], (i / XST) & 1, err);
+        if (!__all_sync(0xffffffffu, okt)) break;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const float4 f = __ldg(src + q);
-          v[4 * q] = f.x;
-          v[4 * q + 1] = f.y;
-          v[4 * q + 2] = f.z;
-          v[4 * q + 3] = f.w;
+          const int rr = 16 * cw + 2 * q + rsub;
+          v[q] = tile * TM + rr < n ? *reinterpret_cast<const float4*>(&S.xs[q2][rr * KD + 4 * col])
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
         }
       } else {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const uint32_t dj = h * 32 + j;
-          v[j] = (p < n && dj < d) ? x[(uint64_t)p * d + dj] : 0.f;
+        for (int q = 0; q < 8; ++q) {
+          const uint32_t p = tile * TM + 16 * cw + 2 * q + rsub;
+          const uint32_t d0 = 4 * col;
+          const float* row = x + (uint64_t)p * d;
+          v[q].x = (p < n && d0 < d) ? row[d0] : 0.f;
+          v[q].y = (p < n && d0 + 1 < d) ? row[d0 + 1] : 0.f;
+          v[q].z = (p < n && d0 + 2 < d) ? row[d0 + 2] : 0.f;
+          v[q].w = (p < n && d0 + 3 < d) ? row[d0 + 3] : 0.f;
         }
       }
       if (i >= STAGES) {
@@ -242,24 +359,53 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
         ok = ok && mbar_wait(&S.nx_free[s], (u + 1) & 1, err);
         if (!__all_sync(0xffffffffu, ok)) break;
       }
-      float ss = 0.f;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) ss = fmaf(v[j], v[j], ss);
-      ss += __shfl_xor_sync(0xffffffffu, ss, 1);
-      if (h == 0) S.nx[s][r] = ss;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        uint32_t hi[4], lo[4];
-#pragma unroll
-        for (int w = 0; w < 4; ++w) split2(v[8 * q + 2 * w], v[8 * q + 2 * w + 1], hi[w], lo[w]);
-        const uint32_t off = swz(r, h * 4 + q);
-        *reinterpret_cast<uint4*>(S.a_hi[s] + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        if (TERMS == 3) *reinterpret_cast<uint4*>(S.a_lo[s] + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      for (int q = 0; q < 8; ++q) {
+        const int rr = 16 * cw + 2 * q + rsub;
+        float ss = fmaf(v[q].w, v[q].w, fmaf(v[q].z, v[q].z, fmaf(v[q].y, v[q].y, v[q].x * v[q].x)));
+        ss += __shfl_xor_sync(0xffffffffu, ss, 8);
+        ss += __shfl_xor_sync(0xffffffffu, ss, 4);
+        ss += __shfl_xor_sync(0xffffffffu, ss, 2);
+        ss += __shfl_xor_sync(0xffffffffu, ss, 1);
+        if (col == 0) S.nx[s][rr] = ss;
+        uint32_t hi0, lo0, hi1, lo1;
+        split2(v[q].x, v[q].y, hi0, lo0);
+        split2(v[q].z, v[q].w, hi1, lo1);
+        const uint32_t off = swz(rr, col >> 1) + (uint32_t)(col & 1) * 8u;
+        *reinterpret_cast<uint2*>(S.a_hi[s] + off) = make_uint2(hi0, hi1);
+        if (TERMS == 3) *reinterpret_cast<uint2*>(S.a_lo[s] + off) = make_uint2(lo0, lo1);
       }
+      // The staging buffer is released only here: the bulk copy engine writes
+      // through the async proxy, so the shared loads above must be ordered
+      // before its next fill by this proxy fence (the stores that consumed
+      // them precede it), not just by the mbarrier arrive.
       fence_proxy_async();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&S.full_a[s]);
+      if (lane == 0) {
+        mbar_arrive(&S.full_a[s]);
+        if (vec) mbar_arrive(&S.tempty[q2]);
+      }
     }
+  } else if (warp == TMA_WARP) {
+    // ------------------------------------------------- bulk-copy producer
+    if (lane == 0 && d == KD && ((reinterpret_cast<uintptr_t>(x) & 15) == 0)) {
+      uint32_t issued = 0;
+      for (uint32_t i = 0;; ++i) {
+        const uint32_t tile = blockIdx.x + i * gridDim.x;
+        if (tile >= ntiles) break;
+        const int q2 = (int)(i % XST);
+        if (i >= XST && !mbar_wait(&S.tempty[q2], ((i / XST) + 1) & 1, err)) break;
+        const uint32_t rows = (n - tile * TM) < (uint32_t)TM ? (n - tile * TM) : (uint32_t)TM;
+        const uint32_t bytes = rows * KD * 4;
+        mbar_expect_tx(&S.tfull[q2], bytes);
+        bulk_g2s(S.xs[q2], x + (uint64_t)tile * TM * KD, bytes, &S.tfull[q2]);
+        ++issued;
+      }
+      // no copy may still be landing in shared memory when the CTA exits
+      for (uint32_t i = issued > (uint32_t)XST ? issued - XST : 0; i < issued; ++i)
+        mbar_wait(&S.tfull[i % XST], (i / XST) & 1, err);
+    }
+    __syncwarp();
   } else if (warp == MMA_WARP) {
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
@@ -299,9 +445,11 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
     __syncwarp();
   } else {
     // ------------------------------------------------------------- epilogue
-    // warp e reads TMEM lane quadrant e % 4 (rows 32*(e%4) ..), columns of
-    // half e / 4; four independent running top-2s per thread (columns j mod
-    // 4) keep the compare chains short.
+    // Warp e reads TMEM lane quadrant e % 4 (rows 32 (e % 4) ..), columns of
+    // half e / 4, CHUNK columns per tcgen05.ld.  Each distance becomes one
+    // sortable 32-bit key (see dist_key), so a running top-3 costs five
+    // unsigned min/max; eight independent top-3s per thread (columns j mod 8)
+    // keep the dependency chains short, and are merged at the end of the tile.
     const int q = warp & 3, half = warp >> 2;
     const int r = q * 32 + lane;
     const float eps_sum = TERMS == 3 ? (3.05f * 1.52587890625e-05f + (float)(3 * KD + 8) * 4.76837158203125e-07f)
@@ -321,49 +469,33 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
       const float nxv = S.nx[s][r];
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.nx_free[s]);
-      float d1[4], d2[4];
-      int k1[4];
+      uint32_t t1[NSET], t2[NSET], t3[NSET];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) d1[a] = d2[a] = INFINITY, k1[a] = 0x7fffffff;
+      for (int a = 0; a < NSET; ++a) t1[a] = t2[a] = t3[a] = 0xFFFFFFFFu;
       const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * 256u;
-      const uint32_t p = tile * TM + r;
-      for (uint32_t ch = c_lo; ch < c_hi; ch += 32) {
-        uint32_t acc[32];
-        tmem_ld32(ta + ch, acc);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int a = j & 3;
-          const uint32_t kk = ch + j;
-          const float dist = fmaf(-2.f, __uint_as_float(acc[j]), nxv) + S.cn[kk];
-          if (dbg && tile == 0 && kk < k) dbg[(uint64_t)r * NMAX + kk] = dist;
-          const bool lt = dist < d1[a];  // columns increase: the first minimum keeps a tie
-          d2[a] = fminf(d2[a], fmaxf(d1[a], dist));
-          k1[a] = lt ? (int)kk : k1[a];
-          d1[a] = fminf(d1[a], dist);
-        }
+      float* dbg_row = (dbg && tile == 0) ? dbg + (uint64_t)r * NMAX : nullptr;
+      for (uint32_t ch = c_lo; ch < c_hi; ch += CHUNK) {
+        uint32_t acc[CHUNK];
+        tmem_ld(ta + ch, acc);
+        if (ch + CHUNK <= k && !dbg_row)
+          top3_keys<false>(acc, ch, nxv, S.cn, k, t1, t2, t3, nullptr);
+        else
+          top3_keys<true>(acc, ch, nxv, S.cn, k, t1, t2, t3, dbg_row);
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.empty_acc[b]);
 #pragma unroll
-      for (int a = 1; a < 4; ++a) {
-        if (d1[a] < d1[0] || (d1[a] == d1[0] && k1[a] < k1[0])) {
-          d2[0] = fminf(d1[0], d2[a]);
-          d1[0] = d1[a];
-          k1[0] = k1[a];
-        } else {
-          d2[0] = fminf(d2[0], d1[a]);
-        }
-      }
+      for (int a = 1; a < NSET; ++a) top3_merge_keys(t1[0], t2[0], t3[0], t1[a], t2[a], t3[a]);
       if (half == 1) {
-        // hand this half's top-2 to the warp of the other half on the same rows
+        // hand this half's top-3 to the warp of the other half on the same rows
         if (i >= ACCS) {
           const bool okf = mbar_wait(&S.xfree[b], (v + 1) & 1, err);
           if (!__all_sync(0xffffffffu, okf)) break;
         }
-        S.xd1[b][r] = d1[0];
-        S.xd2[b][r] = d2[0];
-        S.xk1[b][r] = k1[0];
+        S.xt1[b][r] = t1[0];
+        S.xt2[b][r] = t2[0];
+        S.xt3[b][r] = t3[0];
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.xfull[b]);
         continue;
@@ -371,25 +503,31 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
       {
         const bool okx = mbar_wait(&S.xfull[b], v & 1, err);
         if (!__all_sync(0xffffffffu, okx)) break;
-        const float e1 = S.xd1[b][r], e2 = S.xd2[b][r];
-        const int f1 = S.xk1[b][r];
+        const uint32_t o1 = S.xt1[b][r], o2 = S.xt2[b][r], o3 = S.xt3[b][r];
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.xfree[b]);
-        if (e1 < d1[0] || (e1 == d1[0] && f1 < k1[0])) {
-          d2[0] = fminf(d1[0], e2);
-          d1[0] = e1;
-          k1[0] = f1;
-        } else {
-          d2[0] = fminf(d2[0], e1);
-        }
+        top3_merge_keys(t1[0], t2[0], t3[0], o1, o2, o3);
       }
-      bool flag = false;
+      const uint32_t p = tile * TM + r;
+      bool flag = false, pair = false;
       if (p < n) {
+        const float d1 = key_dist(t1[0]), d2 = key_dist(t2[0]), d3 = key_dist(t3[0]);
+        const int k1 = (int)(t1[0] & 0xFFu);
         const float xn = sqrtf(nxv);
         const float e = 2.f * eps_sum * xn * cmax + eps32 * (xn + cmax) * (xn + cmax);
-        const float thr = fmaxf(1e-3f * fabsf(d1[0]), 2.f * e);
-        if (d2[0] - d1[0] > thr) assign[p] = k1[0];
+        // keys under-state a distance by less than 2^-15 of it (2^-14 allowed)
+        const float gap = 2.f * e + 6.103515625e-05f * d1;
+        if (d2 - d1 > fmaxf(1e-3f * d1, gap)) assign[p] = k1;
+        else if (d3 - d1 > gap) pair = true;  // only the top two can be the exact minimum
         else flag = true;
+      }
+      const unsigned pm = __ballot_sync(0xffffffffu, pair);
+      if (pm) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(npairs, (uint32_t)__popc(pm));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (pair)
+          pairs[base + __popc(pm & ((1u << lane) - 1))] = make_uint2(p, (t1[0] & 0xFFu) | ((t2[0] & 0xFFu) << 16));
       }
       const unsigned fm = __ballot_sync(0xffffffffu, flag);
       if (fm) {
@@ -423,7 +561,8 @@ size_t km_tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
 // points that need the FP32 pass.
 cudaError_t launch_km_tc_kernel(int terms, const float* x, uint32_t n, uint32_t d, const float* c, uint32_t k,
                                 const float* cnorm, const unsigned int* cmax_bits, int32_t* assign, uint32_t* list,
-                                uint32_t* nlist, unsigned long long* timeouts, float* dbg, int grid, cudaStream_t s) {
+                                uint32_t* nlist, uint2* pairs, uint32_t* npairs, unsigned long long* timeouts,
+                                float* dbg, int grid, cudaStream_t s) {
   const int smem = (int)km_tc_smem_bytes();
   cudaError_t e;
   if (terms == 3) {
@@ -431,13 +570,13 @@ cudaError_t launch_km_tc_kernel(int terms, const float* x, uint32_t n, uint32_t 
         cudaSuccess)
       return e;
     km_tc_assign_kernel<3><<<grid, TC_THREADS, smem, s>>>(x, n, d, c, k, cnorm, cmax_bits, assign, list, nlist,
-                                                           timeouts, dbg);
+                                                           pairs, npairs, timeouts, dbg);
   } else {
     if ((e = cudaFuncSetAttribute(km_tc_assign_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
         cudaSuccess)
       return e;
     km_tc_assign_kernel<1><<<grid, TC_THREADS, smem, s>>>(x, n, d, c, k, cnorm, cmax_bits, assign, list, nlist,
-                                                           timeouts, dbg);
+                                                           pairs, npairs, timeouts, dbg);
   }
   return cudaGetLastError();
 }
@@ -449,7 +588,7 @@ cudaError_t launch_kmeans_tc_assign(const float* x, uint32_t n, uint32_t d, cons
   uint32_t* list = reinterpret_cast<uint32_t*>(b.cent_bf16_norm);
   const int terms = b.precision == MR_KM_BF16X1_TC ? 1 : 3;
   cudaError_t e = launch_km_tc_kernel(terms, x, n, d, c, k, b.cnorm, b.nflag + 3, b.assign, list, b.nflag + 1,
-                                      b.stats + 3, nullptr, grid, s);
+                                      b.pairs, b.nflag + 4, b.stats + 3, nullptr, grid, s);
   if (e != cudaSuccess) return e;
   ++*nk;
   // near ties of the tensor-core pass: FP32 pass over the list (its own near

@@ -49,7 +49,7 @@ __device__ __forceinline__ JobDev job_at(const JobDev* jobs, const JobDev& singl
   return jobs ? jobs[j] : single;
 }
 
-__global__ void __launch_bounds__(MAP_THREADS, 3) wc_map_kernel(JobDev J) {
+__global__ void __launch_bounds__(MAP_THREADS, 5) wc_map_kernel(JobDev J) {
   extern __shared__ __align__(16) unsigned char wc_smem[];
   WarpLocal& L = reinterpret_cast<WarpLocal*>(wc_smem)[threadIdx.x >> 5];
   wc::local_clear(L);
@@ -549,7 +549,7 @@ cudaError_t launch_wordcount(const uint8_t* in, uint64_t n, const WcBuffers& b, 
       return e;
     const uint64_t nseg = (n + wc::SEG - 1) / wc::SEG;
     uint64_t grid = (nseg + MAP_WARPS - 1) / MAP_WARPS;
-    const uint64_t gmax = 3ull * di.sms;
+    const uint64_t gmax = 5ull * di.sms;
     if (grid > gmax) grid = gmax;
     wc_map_kernel<<<(unsigned)grid, MAP_THREADS, smem, s>>>(J);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

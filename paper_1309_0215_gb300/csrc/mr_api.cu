@@ -44,6 +44,8 @@ struct Job {
   // word count
   WcBuffers wc;
   bool wc_auto = true;
+  // large-key histogram: u32 counters (null: count straight into the u64 result)
+  void* hk_counters = nullptr;
   // k-means
   KmBuffers km;
   float* km_init_dev = nullptr;
@@ -164,6 +166,14 @@ mr_container plan_container(const mr_ctx* c, const mr_job_desc* d) {
       // small jobs cannot amortise zeroing and merging a CTA's local arrays
       if (d->input_bytes < c->tune.hist_global_below) return MR_C_GLOBAL_ARRAY;
       return hist_smem_bytes() <= c->di.smem_optin ? MR_C_SMEM_ARRAY : MR_C_GLOBAL_ARRAY;
+    case MR_HIST_U32:
+      // local arrays only while every bin of the job fits one CTA's shared
+      // memory; beyond that the global array (L2-resident up to ~100 MB of
+      // counters) replaces them, as the paper does for large arrays
+      if (d->container == MR_C_SMEM_ARRAY || d->container == MR_C_GLOBAL_ARRAY) return d->container;
+      return d->hist_bins <= (uint32_t)hk_smem_max_bins(c->di) ? MR_C_SMEM_ARRAY : MR_C_GLOBAL_ARRAY;
+    case MR_BLOOM_DNA:
+      return MR_C_GLOBAL_ARRAY;
     case MR_LINREG_I8:
     case MR_KMEANS_F32:
     default:
@@ -171,9 +181,12 @@ mr_container plan_container(const mr_ctx* c, const mr_job_desc* d) {
   }
 }
 
+// Kinds that the batched kernel does not cover: they run plain, after the batch.
+bool plain_only(mr_kind k) { return k == MR_KMEANS_F32 || k == MR_HIST_U32 || k == MR_BLOOM_DNA; }
+
 mr_status validate(const mr_ctx* c, const mr_job_desc* d) {
   if (!d || d->struct_size < sizeof(mr_job_desc)) return MR_EINVAL;
-  if ((unsigned)d->kind > (unsigned)MR_KMEANS_F32) return MR_EINVAL;
+  if ((unsigned)d->kind > (unsigned)MR_BLOOM_DNA) return MR_EINVAL;
   if ((unsigned)d->container > (unsigned)MR_C_HASH) return MR_EINVAL;
   if (d->input_bytes && !d->input) return MR_EINVAL;
   switch (d->kind) {
@@ -203,6 +216,17 @@ mr_status validate(const mr_ctx* c, const mr_job_desc* d) {
       if (d->km_precision != MR_KM_FP32 && !km_tc_supported(d->km_dims, d->km_k)) return MR_EINVAL;
       break;
     }
+    case MR_HIST_U32:
+      if (d->input_bytes % 4 || d->hist_bins == 0 || d->hist_bins == 0xFFFFFFFFu) return MR_EINVAL;
+      if (d->container == MR_C_HASH) return MR_EINVAL;
+      if (d->container == MR_C_SMEM_ARRAY && d->hist_bins > (uint32_t)hk_smem_max_bins(c->di)) return MR_EINVAL;
+      if (d->input_on_device && (reinterpret_cast<uintptr_t>(d->input) & 3)) return MR_EINVAL;
+      break;
+    case MR_BLOOM_DNA:
+      if (d->container != MR_C_AUTO && d->container != MR_C_GLOBAL_ARRAY) return MR_EINVAL;
+      if (d->bloom_kmer == 0 || d->bloom_kmer > 32 || d->bloom_hashes == 0 || d->bloom_hashes > 32) return MR_EINVAL;
+      if (d->bloom_bits < 2 || d->bloom_bits > (1ull << 32)) return MR_EINVAL;
+      break;
   }
   (void)c;
   return MR_OK;
@@ -262,6 +286,29 @@ mr_status alloc_job_memory(mr_ctx* c, Job* j) {
       if (st) return st;
       j->slab_bytes = 64;
       j->result = j->slab;
+      return MR_OK;
+    }
+    case MR_HIST_U32: {
+      const uint64_t nb = (uint64_t)d.hist_bins + 1;
+      const uint64_t res = align256(nb * 8);
+      // u32 counters while no bin can reach 2^32
+      const bool wide = d.input_bytes / 4 >= (1ull << 32);
+      const uint64_t cnt = wide ? 0 : align256(nb * 4);
+      mr_status st = dev_alloc(c, res + cnt, &j->slab);
+      if (st) return st;
+      j->slab_bytes = res + cnt;
+      j->result = j->slab;
+      j->result_bytes = nb * 8;
+      j->hk_counters = wide ? nullptr : static_cast<uint8_t*>(j->slab) + res;
+      return MR_OK;
+    }
+    case MR_BLOOM_DNA: {
+      const uint64_t bytes = align256((d.bloom_bits + 31) / 32 * 4);
+      mr_status st = dev_alloc(c, bytes, &j->slab);
+      if (st) return st;
+      j->slab_bytes = bytes;
+      j->result = j->slab;
+      j->result_bytes = (d.bloom_bits + 7) / 8;
       return MR_OK;
     }
     case MR_KMEANS_F32: {
@@ -349,6 +396,15 @@ mr_status enqueue_plain_on(mr_ctx* c, Job* j, cudaStream_t st) {
       break;
     case MR_WORDCOUNT:
       MR_CUDA_TRY(launch_wordcount(j->in, n, j->wc, c->di, st, &c->launches));
+      break;
+    case MR_HIST_U32:
+      MR_CUDA_TRY(launch_hist_keys(reinterpret_cast<const uint32_t*>(j->in), n / 4, j->desc.hist_bins,
+                                   j->container == MR_C_SMEM_ARRAY, j->hk_counters, j->hk_counters == nullptr,
+                                   static_cast<unsigned long long*>(j->result), c->di, st, &c->launches));
+      break;
+    case MR_BLOOM_DNA:
+      MR_CUDA_TRY(launch_bloom(j->in, n, j->desc.bloom_kmer, j->desc.bloom_bits, j->desc.bloom_hashes,
+                               static_cast<uint32_t*>(j->result), c->di, st, &c->launches));
       break;
     case MR_KMEANS_F32: {
       uint8_t* p = static_cast<uint8_t*>(j->result);
@@ -522,7 +578,7 @@ mr_status autotune_batch(mr_ctx* c, const std::vector<Job*>& jobs) {
 mr_status enqueue_batched(mr_ctx* c, std::vector<Job*>& jobs) {
   std::vector<Job*> batched;
   for (Job* j : jobs)
-    if (j->desc.kind != MR_KMEANS_F32) batched.push_back(j);
+    if (!plain_only(j->desc.kind)) batched.push_back(j);
   if (!batched.empty()) {
     drop_batch_graph(c);
     c->batch_ids.clear();
@@ -544,7 +600,7 @@ mr_status enqueue_batched(mr_ctx* c, std::vector<Job*>& jobs) {
     }
   }
   for (Job* j : jobs)
-    if (j->desc.kind == MR_KMEANS_F32) {
+    if (plain_only(j->desc.kind)) {
       mr_status st = enqueue_plain(c, j);
       if (st) return st;
     }
@@ -583,7 +639,7 @@ mr_status serve_pump(mr_ctx* c) {
   jobs.swap(c->serve_pending);
   std::vector<Job*> arr;
   for (Job* j : jobs)
-    if (j->desc.kind != MR_KMEANS_F32) arr.push_back(j);
+    if (!plain_only(j->desc.kind)) arr.push_back(j);
   // the slot stream must see the submit-time copies and clears on the context stream
   if (!c->serve_ready) MR_CUDA_TRY(cudaEventCreateWithFlags(&c->serve_ready, cudaEventDisableTiming));
   MR_CUDA_TRY(cudaEventRecord(c->serve_ready, c->stream));
@@ -621,7 +677,7 @@ mr_status serve_pump(mr_ctx* c) {
     }
   }
   for (Job* j : jobs)
-    if (j->desc.kind == MR_KMEANS_F32) {
+    if (plain_only(j->desc.kind)) {
       mr_status st = enqueue_plain_on(c, j, slot->s);
       if (st) return st;
     }

@@ -40,6 +40,19 @@ cudaError_t launch_linreg(const int8_t* in, uint64_t n, int64_t* sums, int grid,
 int hist_smem_bytes();         // dynamic shared memory the smem histogram needs
 int hist_block_threads();
 
+// ------------------------------------------- large-key histogram, Bloom
+// Largest bin count whose local arrays (nbins + 1 u32) fit one CTA.
+int hk_smem_max_bins(const DevInfo& di);
+// Histogram of n u32 keys into out[nbins + 1] (zeroed here).  smem: local
+// arrays per CTA; else atomics on the global array.  wide: count straight into
+// the u64 output (needed from 2^32 keys on); else into the u32 counters
+// (nbins + 1 words) and widen at the end.
+cudaError_t launch_hist_keys(const uint32_t* keys, uint64_t n, uint32_t nbins, bool smem, void* counters,
+                             bool wide, unsigned long long* out, const DevInfo& di, cudaStream_t s, uint64_t* nk);
+// Bloom-filter build over n bases into ceil(m / 32) u32 words (zeroed here).
+cudaError_t launch_bloom(const uint8_t* seq, uint64_t n, uint32_t L, uint64_t m, uint32_t h, uint32_t* bits,
+                         const DevInfo& di, cudaStream_t s, uint64_t* nk);
+
 // --------------------------------------------------------- word count job
 struct WcBuffers {
   uint64_t cap = 0;            // global hash-table slots (power of two)
@@ -77,7 +90,8 @@ struct KmBuffers {
   unsigned long long* counts = nullptr;  // [k]
   unsigned long long* stats = nullptr;   // [4]
   uint32_t* flagged = nullptr;  // [n] indices of points to re-check
-  uint32_t* nflag = nullptr;    // [2] counters
+  uint32_t* nflag = nullptr;    // [8] counters: [0] FP64 list, [1] FP32 list, [2] max|x| bits, [3] max||c|| bits, [4] pairs
+  uint2* pairs = nullptr;       // [n] {point, k1 | k2 << 16}: exact choice between two centroids
   float* xnorm = nullptr;       // [n] ||x||
   float* cnorm = nullptr;       // [k] ||c|| and ||c||^2
   uint16_t* xb = nullptr;       // BF16 copy of the points [n][d]
