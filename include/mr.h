@@ -243,6 +243,22 @@ mr_status mr_job_elapsed_ms(mr_ctx* ctx, uint64_t job_id, float* ms);
 /* Number of CUDA kernels this context has launched so far (all jobs). */
 uint64_t mr_kernel_launches(const mr_ctx* ctx);
 
+/* SIMD hashing of variable-length strings (the paper's SIMDH-Padding and
+ * SIMDH-Stream, Sec. III-C, with warp lanes as the SIMD lanes): the 64-bit
+ * FNV-1a hash (offset basis 0xcbf29ce484222325, prime 0x100000001b3, one
+ * byte at a time) of each of ntok tokens.  Token i is the tok_len[i] bytes
+ * at text + tok_off[i]; every token must lie inside the text, and
+ * text_bytes < 2^32.  All pointers are device addresses (text needs no
+ * alignment); hashes[i] receives token i's hash.  method: */
+#define MR_SIMDH_PADDING 0  /* 32 consecutive tokens per warp round, one per lane; rounds = longest, shorter lanes masked */
+#define MR_SIMDH_STREAM 1   /* a lane that finishes takes the next token at once (ballot + prefix count refill) */
+#define MR_SIMDH_WIDE 2     /* Padding's grouping, four bytes per load through a funnel shift */
+/* Enqueued on cuda_stream (NULL = the legacy default stream); returns once
+ * launched.  Errors: MR_EINVAL (bad method or size, null pointer),
+ * MR_ECUDA. */
+mr_status mr_simdh_hash(const uint8_t* text, uint64_t text_bytes, const uint32_t* tok_off, const uint32_t* tok_len,
+                        uint64_t ntok, int method, uint64_t* hashes, void* cuda_stream);
+
 /* Word count that allocates no device memory (the paper has no counterpart;
  * this is a deployment convenience).
  *

@@ -47,6 +47,9 @@ def _L():
             lib.oracle_mix64.restype = u64
             lib.oracle_bloom_dna.argtypes = [vp, u64, u32, u64, u32, vp]
             lib.oracle_bloom_codes.argtypes = [vp, u64, u64, u32, vp]
+            lib.oracle_fnv1a64.argtypes = [vp, u64]
+            lib.oracle_fnv1a64.restype = u64
+            lib.oracle_token_hashes.argtypes = [vp, u64, vp, vp, vp, u64, ctypes.POINTER(ctypes.c_uint64)]
             _lib = lib
     return _lib
 
@@ -116,6 +119,25 @@ def bloom_codes(codes, m: int, h: int) -> np.ndarray:
     if _L().oracle_bloom_codes(p, c.size, m, h, out.ctypes.data):
         raise ValueError("oracle_bloom_codes")
     return out
+
+
+def fnv1a64(data: bytes) -> int:
+    buf = np.frombuffer(bytes(data), dtype=np.uint8)
+    return int(_L().oracle_fnv1a64(buf.ctypes.data if buf.size else None, buf.size))
+
+
+def token_hashes(text):
+    """(offsets u64, lengths u64, FNV-1a 64 hashes u64) of the word-count tokens, in order."""
+    t, p = _buf(np.frombuffer(text, dtype=np.uint8) if isinstance(text, (bytes, bytearray))
+                else np.asarray(text, dtype=np.uint8))
+    cnt = ctypes.c_uint64()
+    if _L().oracle_token_hashes(p, t.size, None, None, None, 0, ctypes.byref(cnt)):
+        raise ValueError("oracle_token_hashes")
+    n = cnt.value
+    off, ln, h = (np.zeros(n, dtype=np.uint64) for _ in range(3))
+    if _L().oracle_token_hashes(p, t.size, off.ctypes.data, ln.ctypes.data, h.ctypes.data, n, ctypes.byref(cnt)):
+        raise ValueError("oracle_token_hashes")
+    return off, ln, h
 
 
 def kmeans_assign(x, c, want_dmin: bool = False):

@@ -196,6 +196,39 @@ int oracle_bloom_codes(const uint64_t* codes, uint64_t n, uint64_t m, uint32_t h
   return 0;
 }
 
+/* Hash computation for strings (Sec. III-C, Listing 1): a string is hashed
+ * character by character, v = func(v, c).  The paper names FNV; this is
+ * 64-bit FNV-1a (Fowler, Noll, Vo): v = 0xcbf29ce484222325, then for each
+ * byte v = (v xor byte) * 0x100000001b3 mod 2^64.  Tokens are the word-count
+ * tokens (maximal runs of non-whitespace bytes), in input order.  With
+ * out_* null only *ntok is set. */
+uint64_t oracle_fnv1a64(const uint8_t* s, uint64_t len) {
+  uint64_t v = 0xcbf29ce484222325ull;
+  for (uint64_t i = 0; i < len; ++i) v = (v ^ s[i]) * 0x100000001b3ull;
+  return v;
+}
+
+int oracle_token_hashes(const uint8_t* text, uint64_t n, uint64_t* out_off, uint64_t* out_len, uint64_t* out_hash,
+                        uint64_t cap, uint64_t* ntok) {
+  if ((!text && n) || !ntok) return 1;
+  uint64_t t = 0, i = 0;
+  while (i < n) {
+    while (i < n && is_ws(text[i])) ++i;
+    if (i >= n) break;
+    const uint64_t b = i;
+    while (i < n && !is_ws(text[i])) ++i;
+    if (out_off) {
+      if (t >= cap) return 2;
+      out_off[t] = b;
+      out_len[t] = i - b;
+      out_hash[t] = oracle_fnv1a64(text + b, i - b);
+    }
+    ++t;
+  }
+  *ntok = t;
+  return 0;
+}
+
 /* Squared Euclidean distance in FP64: Σ_j (x_j - c_j)², j in order, no FMA. */
 static double dist2_f64(const float* x, const float* c, uint32_t d) {
   double s = 0.0;

@@ -28,7 +28,8 @@ KM_FP32, KM_BF16_TC, KM_BF16X1_TC = range(3)
 # every entry point declared in include/mr.h
 EXPORTS = ("mr_create", "mr_destroy", "mr_add_job", "mr_run", "mr_fetch", "mr_result_device", "mr_release",
            "mr_submit", "mr_poll", "mr_sync", "mr_bytes_in_use", "mr_job_elapsed_ms", "mr_kernel_launches",
-           "mr_status_str", "mr_last_error", "mr_wordcount_noalloc", "mr_rerun", "mr_get_tuning")
+           "mr_status_str", "mr_last_error", "mr_wordcount_noalloc", "mr_rerun", "mr_get_tuning", "mr_simdh_hash")
+SIMDH_PADDING, SIMDH_STREAM, SIMDH_WIDE = range(3)
 NOALLOC_WC_SLOTS = 131072
 FLAG_TIMING = 1
 FLAG_AUTOTUNE = 2
@@ -118,6 +119,8 @@ def load():
         lib.mr_get_tuning.restype = st
         lib.mr_wordcount_noalloc.argtypes = [vp, u64, vp, u64, ctypes.POINTER(u64), vp]
         lib.mr_wordcount_noalloc.restype = st
+        lib.mr_simdh_hash.argtypes = [vp, u64, vp, vp, u64, ctypes.c_int, vp, vp]
+        lib.mr_simdh_hash.restype = st
         lib.mr_status_str.argtypes = [ctypes.c_int]
         lib.mr_status_str.restype = ctypes.c_char_p
         lib.mr_last_error.argtypes = []
@@ -354,6 +357,23 @@ def hist_rgb8(px, container=C_AUTO) -> np.ndarray:
 
 def linreg_i8(xy) -> np.ndarray:
     return np.frombuffer(_one(LINREG_I8, xy), dtype=np.int64).copy()
+
+
+def simdh_hash(text, tok_off, tok_len, method: int = SIMDH_STREAM, out=None, stream=None):
+    """FNV-1a 64 of each token (device tensors: text uint8, tok_off / tok_len
+    int32 or uint32 views); returns the uint64 hashes as an int64 device
+    tensor (launched on `stream`, default: torch's current stream)."""
+    import torch
+    lib = load()
+    ntok = int(tok_off.numel())
+    if out is None:
+        out = torch.empty(ntok, dtype=torch.int64, device=text.device)
+    s = stream if stream is not None else torch.cuda.current_stream(text.device)
+    st = lib.mr_simdh_hash(text.data_ptr() if text.numel() else None, int(text.numel()),
+                           tok_off.data_ptr() if ntok else None, tok_len.data_ptr() if ntok else None, ntok,
+                           int(method), out.data_ptr() if ntok else None, ctypes.c_void_p(s.cuda_stream))
+    _check(st, "mr_simdh_hash")
+    return out
 
 
 def hist_u32(keys, nbins: int, container=C_AUTO) -> np.ndarray:

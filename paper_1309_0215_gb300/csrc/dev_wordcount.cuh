@@ -19,11 +19,13 @@
 // job's overflow flag (the host then re-runs with a larger table).
 //
 // Local container (the paper's combiner, Sec. III-A, with the bounded local
-// table of Sec. III-D), shaped for Zipf-like key streams: tokens of a warp
-// round that carry the same key are merged first (one match_any); then a
-// direct-mapped cache of hot keys per warp in shared memory (one compare, no
-// probing) absorbs the frequent keys, and the rest go straight to the global
-// container, where such rarer keys do not contend.  The cache is merged into
+// table of Sec. III-D), shaped for Zipf-like key streams: a 2-way cache of
+// hot keys per warp in shared memory (two candidate slots per key, one
+// compare each, no probing) absorbs the frequent keys, and the rest go
+// straight to the global container, where such rarer keys do not contend.
+// No warp collective is used: lanes of one round that carry the same key
+// simply add to the same slot count (shared-memory atomics), and an empty
+// slot is claimed with a 64-bit shared-memory CAS.  The cache is merged into
 // the global container every CACHE_EPOCH segments (so it can re-learn which
 // keys are hot) and at the end.
 #pragma once
@@ -191,44 +193,48 @@ __device__ inline void global_insert(const JobDev& J, uint64_t w0, uint64_t w1, 
   atomicOr(J.state, 1u);
 }
 
-// Combine one token per active lane; all 32 lanes call this together and
-// every collective is full-warp.  Lanes holding the same short key merge into
-// their lowest lane; each remaining (key, count) goes to the warp's hot-key
-// cache if its slot holds that key, or claims the slot if it is empty (the
-// lowest of the lanes that want the same empty slot wins), else goes to the
-// global container.  Long keys (>= 16 bytes) bypass the cache.
+// Combine one token per active lane; all 32 lanes call this together (the
+// warp syncs inside).  A short key that sits in one of its two cache slots
+// adds 1 there.  Otherwise the first of its slots that is empty is claimed by
+// a CAS on the slot's w1: the winner fills the slot with count 1; a loser
+// whose key turns out to be the winner's (read after a warp sync) adds 1 to
+// it.  Everything else — long keys (>= 16 bytes), keys whose slots are held
+// by other keys, lost claims for other keys — goes to the global container.
 __device__ __forceinline__ void combine_round(WarpLocal& L, bool active, const Tok& t, const JobDev& J) {
-  const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
   const bool is_long = (t.w1 >> 56) == 0xFF;
-  // inactive lanes get a value no hash can take, so they group alone
-  const unsigned long long hkey = active ? (unsigned long long)t.h : ((1ull << 32) | (unsigned)lane);
-  const unsigned grp = __match_any_sync(FULL, hkey);
-  const int leader = __ffs(grp) - 1;
-  const uint64_t l0 = __shfl_sync(FULL, t.w0, leader), l1 = __shfl_sync(FULL, t.w1, leader);
-  const bool same = t.w0 == l0 && t.w1 == l1;
-  const bool merged = (__ballot_sync(FULL, same) & grp) == grp;
-  const bool handle = active && (!merged || lane == leader);
-  const uint32_t c = merged ? (uint32_t)__popc(grp) : 1u;
-  const int s = (int)(t.h & (LT - 1));
-  bool hit = false, empty = false;
-  if (handle && !is_long) {
-    const uint64_t r1 = L.w1[s];
-    hit = r1 == t.w1 && L.w0[s] == t.w0;
-    empty = r1 == 0;
+  const int s0 = (int)(t.h & (LT - 1)), s1 = (int)((t.h >> 16) & (LT - 1));
+  bool done = !active;
+  int want = -1;
+  if (active && !is_long) {
+    const uint64_t a1 = L.w1[s0], b1 = L.w1[s1];
+    if (a1 == t.w1 && L.w0[s0] == t.w0) {
+      atomicAdd(&L.cnt[s0], 1u);
+      done = true;
+    } else if (b1 == t.w1 && L.w0[s1] == t.w0) {
+      atomicAdd(&L.cnt[s1], 1u);
+      done = true;
+    } else if (a1 == 0) {
+      want = s0;
+    } else if (b1 == 0) {
+      want = s1;
+    }
   }
-  if (hit) atomicAdd(&L.cnt[s], c);
-  const bool want = handle && empty;
-  const unsigned long long skey = want ? (unsigned long long)s : ((1ull << 32) | (unsigned)lane);
-  const unsigned sg = __match_any_sync(FULL, skey);
-  const bool claim = want && lane == __ffs(sg) - 1;
-  if (claim) {
-    L.w0[s] = t.w0;
-    L.w1[s] = t.w1;
-    L.h[s] = t.h;
-    L.cnt[s] = c;
+  __syncwarp();
+  unsigned long long old = ~0ull;
+  if (want >= 0) old = atomicCAS(&L.w1[want], 0ull, (unsigned long long)t.w1);
+  const bool won = want >= 0 && old == 0;
+  if (won) {
+    L.w0[want] = t.w0;
+    L.h[want] = t.h;
+    L.cnt[want] = 1u;
+    done = true;
   }
-  if (handle && !hit && !claim) global_insert(J, t.w0, t.w1, t.h, c);
+  __syncwarp();
+  if (want >= 0 && !won && old == t.w1 && L.w0[want] == t.w0) {
+    atomicAdd(&L.cnt[want], 1u);
+    done = true;
+  }
+  if (!done) global_insert(J, t.w0, t.w1, t.h, 1);
 }
 
 __device__ inline void local_clear(WarpLocal& L) {

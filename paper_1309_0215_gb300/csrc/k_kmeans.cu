@@ -36,6 +36,7 @@ constexpr int KM_THREADS = 256;   // 8 warps
 constexpr int TP = 64;            // points per tile (8 per warp)
 constexpr int KC_MAX = 256;       // centroids per chunk (8 per lane)
 constexpr int DC_MAX = 64;        // dims per chunk
+constexpr int CS_LD = KC_MAX + 1;  // staged centroid row stride: the transposing stores hit distinct banks
 
 // Running top three distances (the two smallest with their indices);
 // between equal distances the lower index ranks first.
@@ -70,6 +71,38 @@ __device__ __forceinline__ void top3_merge(Top3& t, const Top3& o) {
   top3_push(t, o.d3, 0x7fffffff);
 }
 
+// Sortable keys (K <= 256): the FP32 bits of a distance (negatives, which
+// only rounding produces, clamped to 0) with the low 8 mantissa bits replaced
+// by the centroid index.  Non-negative floats order like their bits, so keys
+// order by the distance truncated to 16 mantissa bits (an under-statement of
+// less than 2^-15 of it), then by index; a running top-2 is three unsigned
+// min/max.  KEY_NONE (no centroid) decodes to +inf.
+constexpr uint32_t KEY_NONE = 0x7F8000FFu;
+__device__ __forceinline__ uint32_t dist_key(float dist, uint32_t kk) {
+  return ((uint32_t)max((int)__float_as_uint(dist), 0) & 0xFFFFFF00u) | kk;
+}
+__device__ __forceinline__ float key_dist(uint32_t key) { return __uint_as_float(key & 0xFFFFFF00u); }
+__device__ __forceinline__ void top2_insert(uint32_t& t1, uint32_t& t2, uint32_t key) {
+  const uint32_t h = max(t1, key);
+  t1 = min(t1, key);
+  t2 = min(t2, h);
+}
+// (a1 <= a2, every other key of set a >= la) merged with the same of set b:
+// the union's top-2 and a lower bound of its other keys.
+__device__ __forceinline__ void top2lb_merge(uint32_t& a1, uint32_t& a2, uint32_t& la, uint32_t b1, uint32_t b2,
+                                             uint32_t lb) {
+  const uint32_t g1 = min(a1, b1);
+  const uint32_t g2 = min(max(a1, b1), min(a2, b2));
+  uint32_t g3 = min(la, lb);
+  g3 = (a1 != g1 && a1 != g2) ? min(g3, a1) : g3;
+  g3 = (a2 != g1 && a2 != g2) ? min(g3, a2) : g3;
+  g3 = (b1 != g1 && b1 != g2) ? min(g3, b1) : g3;
+  g3 = (b2 != g1 && b2 != g2) ? min(g3, b2) : g3;
+  a1 = g1;
+  a2 = g2;
+  la = g3;
+}
+
 // Centroid norms: cn[k] = ||c_k||^2 (FP32, sequential FMA); cmax[0] = max ||c_k||.
 __global__ void km_prep_kernel(const float* __restrict__ c, uint32_t k, uint32_t d, float* __restrict__ cn,
                                unsigned int* cmax_bits, long long* sums, unsigned long long* counts, uint32_t* nflag) {
@@ -93,6 +126,9 @@ __global__ void km_prep_kernel(const float* __restrict__ c, uint32_t k, uint32_t
 // staged in shared memory (points transposed [dim][point], centroids
 // [dim][centroid]).  When K <= 256 and D <= 64 the centroids are loaded once
 // per CTA.  idx != nullptr restricts the pass to the listed points.
+// KEYS (K <= 256): selection by packed keys (top-2 plus a lower bound of
+// the other keys); else a float top-3 with indices.
+template <bool KEYS>
 __global__ void __launch_bounds__(KM_THREADS, 2)
 km_assign_fp32_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const float* __restrict__ c, uint32_t k,
                       const float* __restrict__ cn, const unsigned int* cmax_bits, const uint32_t* idx,
@@ -101,8 +137,8 @@ km_assign_fp32_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const
   extern __shared__ float km_sm[];
   const int dc = d < DC_MAX ? (int)d : DC_MAX;
   const int kc = k < KC_MAX ? (int)k : KC_MAX;
-  float* cs = km_sm;              // [dc][KC_MAX]
-  float* xs = km_sm + DC_MAX * KC_MAX;  // [dc][TP]
+  float* cs = km_sm;              // [dc][CS_LD]
+  float* xs = km_sm + DC_MAX * CS_LD;  // [dc][TP]
   __shared__ float nx_s[TP];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t npts = idx ? *nidx : n;
@@ -110,12 +146,13 @@ km_assign_fp32_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const
   const float cmax = __uint_as_float(*cmax_bits);
   const float eps = 1.01f * (float)(d + 8) * 5.9604645e-8f;  // 2^-24
   if (idx && blockIdx.x == 0 && threadIdx.x == 0 && stat) atomicAdd(stat, (unsigned long long)npts);
+  if ((uint64_t)blockIdx.x * TP >= npts) return;  // no tile for this CTA (a short list)
 
   auto load_c = [&](uint32_t k0, uint32_t d0) {
     for (int t = threadIdx.x; t < kc * dc; t += KM_THREADS) {
       const int kk = t / dc, dd = t % dc;
       const uint32_t kg = k0 + kk, dg = d0 + dd;
-      cs[dd * KC_MAX + kk] = (kg < k && dg < d) ? c[(uint64_t)kg * d + dg] : 0.f;
+      cs[dd * CS_LD + kk] = (kg < k && dg < d) ? c[(uint64_t)kg * d + dg] : 0.f;
     }
   };
   if (resident) {
@@ -125,9 +162,15 @@ km_assign_fp32_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const
   const uint32_t ntiles = (npts + TP - 1) / TP;
   for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const uint32_t p0 = tile * TP;
-    Top3 tp[8];
+    Top3 tp[KEYS ? 1 : 8];
+    uint32_t t1[KEYS ? 8 : 1], t2[KEYS ? 8 : 1];
+    if (KEYS) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) top3_init(tp[i]);
+      for (int i = 0; i < 8; ++i) t1[i] = t2[i] = KEY_NONE;
+    } else {
+#pragma unroll
+      for (int i = 0; i < (KEYS ? 1 : 8); ++i) top3_init(tp[i]);
+    }
     float nxacc = 0.f;  // ||x||^2 of point threadIdx.x (threads < TP), FMA over dims in order
     for (uint32_t k0 = 0; k0 < k; k0 += KC_MAX) {
       float acc[8][8];
@@ -158,7 +201,7 @@ km_assign_fp32_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const
           const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
           float cv[8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) cv[j] = cs[dd * KC_MAX + lane + 32 * j];
+          for (int j = 0; j < 8; ++j) cv[j] = cs[dd * CS_LD + lane + 32 * j];
 #pragma unroll
           for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -174,44 +217,76 @@ km_assign_fp32_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const uint32_t kk = k0 + lane + 32 * j;
-        if (kk < k && lane + 32 * j < kc) {
-          const float ncv = cn[kk];
+        if (KEYS) {
+          const bool valid = kk < k && lane + 32 * j < kc;
+          const float ncv = valid ? cn[kk] : 0.f;
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
+            const float dist = fmaf(-2.f, acc[i][j], nx_s[warp * 8 + i]) + ncv;
+            top2_insert(t1[i], t2[i], valid ? dist_key(dist, kk) : KEY_NONE);
+          }
+        } else if (kk < k && lane + 32 * j < kc) {
+          const float ncv = cn[kk];
+#pragma unroll
+          for (int i = 0; i < (KEYS ? 1 : 8); ++i) {
             const float dist = fmaf(-2.f, acc[i][j], nx_s[warp * 8 + i]) + ncv;
             top3_push(tp[i], dist, (int)kk);
           }
         }
       }
     }
-    // combine the lanes' candidates for each of the warp's 8 points
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      for (int o = 16; o; o >>= 1) {
-        Top3 ot;
-        ot.d1 = __shfl_xor_sync(0xffffffffu, tp[i].d1, o);
-        ot.d2 = __shfl_xor_sync(0xffffffffu, tp[i].d2, o);
-        ot.d3 = __shfl_xor_sync(0xffffffffu, tp[i].d3, o);
-        ot.k1 = __shfl_xor_sync(0xffffffffu, tp[i].k1, o);
-        ot.k2 = __shfl_xor_sync(0xffffffffu, tp[i].k2, o);
-        top3_merge(tp[i], ot);
-      }
-    }
-    // lane i decides point i of the warp
+    // combine the lanes' candidates for each of the warp's 8 points; lane i
+    // then decides point i of the warp
     Top3 mt;
     top3_init(mt);
+    if (KEYS) {
+      uint32_t m1 = KEY_NONE, m2 = KEY_NONE, m3 = KEY_NONE;
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
-      if (lane == i) mt = tp[i];
+      for (int i = 0; i < 8; ++i) {
+        // a lane's keys other than its top-2 are all >= its second key
+        uint32_t a1 = t1[i], a2 = t2[i], la = t2[i];
+        for (int o = 16; o; o >>= 1) {
+          const uint32_t b1 = __shfl_xor_sync(0xffffffffu, a1, o);
+          const uint32_t b2 = __shfl_xor_sync(0xffffffffu, a2, o);
+          const uint32_t lb = __shfl_xor_sync(0xffffffffu, la, o);
+          top2lb_merge(a1, a2, la, b1, b2, lb);
+        }
+        if (lane == i) m1 = a1, m2 = a2, m3 = la;
+      }
+      // keys under-state a distance by less than 2^-15 of it: the margin
+      // tests below get 2^-14 d1 more
+      mt.d1 = key_dist(m1);
+      mt.d2 = key_dist(m2);
+      mt.d3 = key_dist(m3);
+      mt.k1 = (int)(m1 & 0xFFu);
+      mt.k2 = (int)(m2 & 0xFFu);
+    } else {
+#pragma unroll
+      for (int i = 0; i < (KEYS ? 1 : 8); ++i) {
+        for (int o = 16; o; o >>= 1) {
+          Top3 ot;
+          ot.d1 = __shfl_xor_sync(0xffffffffu, tp[i].d1, o);
+          ot.d2 = __shfl_xor_sync(0xffffffffu, tp[i].d2, o);
+          ot.d3 = __shfl_xor_sync(0xffffffffu, tp[i].d3, o);
+          ot.k1 = __shfl_xor_sync(0xffffffffu, tp[i].k1, o);
+          ot.k2 = __shfl_xor_sync(0xffffffffu, tp[i].k2, o);
+          top3_merge(tp[i], ot);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < (KEYS ? 1 : 8); ++i)
+        if (lane == i) mt = tp[i];
+    }
     const uint32_t pi = p0 + warp * 8 + lane;
     bool flag = false, pair = false;
     if (lane < 8 && pi < npts) {
       const uint32_t p = idx ? idx[pi] : pi;
       const float nxv = sqrtf(nx_s[warp * 8 + lane]);
       const float e = eps * (nxv + cmax) * (nxv + cmax);
+      const float gap = 2.f * e + (KEYS ? 6.103515625e-05f * fmaxf(mt.d1, 0.f) : 0.f);
       // only the top two can be the exact minimum when the third is 2E away
-      if (mt.d2 - mt.d1 > 2.f * e) assign[p] = mt.k1;
-      else if (mt.d3 - mt.d1 > 2.f * e) pair = true;
+      if (mt.d2 - mt.d1 > gap) assign[p] = mt.k1;
+      else if (mt.d3 - mt.d1 > gap) pair = true;
       else flag = true;
     }
     const unsigned pm = __ballot_sync(0xffffffffu, pair);
@@ -249,29 +324,6 @@ __device__ __forceinline__ double dist64(const float* __restrict__ xp, const flo
   return s;
 }
 
-__global__ void km_pair_kernel(const float* __restrict__ x, uint32_t d, const float* __restrict__ c,
-                               const uint2* __restrict__ pairs, const uint32_t* npairs, int32_t* assign,
-                               unsigned long long* stat) {
-  const uint32_t np = *npairs;
-  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid == 0 && stat) atomicAdd(stat, (unsigned long long)np);
-  for (uint64_t i = tid; i < np; i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint2 e = pairs[i];
-    const uint32_t k1 = e.y & 0xffffu, k2 = e.y >> 16;
-    const float* xp = x + (uint64_t)e.x * d;
-    const double s1 = dist64(xp, c + (uint64_t)k1 * d, d);
-    const double s2 = dist64(xp, c + (uint64_t)k2 * d, d);
-    assign[e.x] = (s2 < s1 || (s2 == s1 && k2 < k1)) ? (int32_t)k2 : (int32_t)k1;
-  }
-}
-
-// Exact FP64 argmin for the listed points, one warp per point.  Pass 1:
-// FP32 distance to every centroid with the lanes spread over the dimensions
-// (coalesced centroid rows, warp-sum; the bound below holds for any order),
-// keeping the smallest.  Pass 2: in FP64, separately rounded subtract,
-// multiply and add with the dimensions in order, only for the centroids whose
-// FP32 distance is within the relative error bound of that minimum (one lane
-// per such centroid).
 __device__ __forceinline__ float warp_dist32(const float* __restrict__ xp, const float* __restrict__ cp, uint32_t d,
                                              int lane) {
   float s = 0.f;
@@ -283,6 +335,52 @@ __device__ __forceinline__ float warp_dist32(const float* __restrict__ xp, const
   return s;
 }
 
+__global__ void km_pair_kernel(const float* __restrict__ x, uint32_t d, const float* __restrict__ c,
+                               const uint2* __restrict__ pairs, const uint32_t* npairs, int32_t* assign,
+                               unsigned long long* stat) {
+  const uint32_t np = *npairs;
+  const int lane = threadIdx.x & 31;
+  const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  if (w0 == 0 && lane == 0 && stat) atomicAdd(stat, (unsigned long long)np);
+  // One warp per pair.  FP32 direct differences first (lanes over the
+  // dimensions, coalesced rows): their relative error is at most g for any
+  // summation order (as in the re-check below), so a ratio beyond widen
+  // decides the exact order; only closer pairs (and NaNs) take the FP64
+  // definition, evaluated by one lane.
+  const float g = 1.01f * (float)(d + 8) * 5.9604644775390625e-08f;
+  const float widen = (1.f + g) / (1.f - g) * (1.f + 4.f * 5.9604644775390625e-08f);
+  for (uint64_t f = w0; f < np; f += nw) {
+    const uint2 e = pairs[f];
+    const uint32_t k1 = e.y & 0xffffu, k2 = e.y >> 16;
+    const float* xp = x + (uint64_t)e.x * d;
+    const float* c1 = c + (uint64_t)k1 * d;
+    const float* c2 = c + (uint64_t)k2 * d;
+    const float f1 = warp_dist32(xp, c1, d, lane);
+    const float f2 = warp_dist32(xp, c2, d, lane);
+    if (lane == 0) {
+      int32_t w;
+      if (f2 > f1 * widen) {
+        w = (int32_t)k1;
+      } else if (f1 > f2 * widen) {
+        w = (int32_t)k2;
+      } else {
+        const double s1 = dist64(xp, c1, d);
+        const double s2 = dist64(xp, c2, d);
+        w = (s2 < s1 || (s2 == s1 && k2 < k1)) ? (int32_t)k2 : (int32_t)k1;
+      }
+      assign[e.x] = w;
+    }
+  }
+}
+
+// Exact FP64 argmin for the listed points, one warp per point.  Pass 1:
+// FP32 distance to every centroid with the lanes spread over the dimensions
+// (coalesced centroid rows, warp-sum; the bound below holds for any order),
+// keeping the smallest.  Pass 2: in FP64, separately rounded subtract,
+// multiply and add with the dimensions in order, only for the centroids whose
+// FP32 distance is within the relative error bound of that minimum (one lane
+// per such centroid).
 __global__ void km_recheck_fp64_kernel(const float* __restrict__ x, uint32_t d, const float* __restrict__ c, uint32_t k,
                                        const uint32_t* flagged, const uint32_t* nflag, int32_t* assign,
                                        unsigned long long* stat) {
@@ -513,13 +611,22 @@ __global__ void __launch_bounds__(SCAT_THREADS) km_scatter_kernel(const int32_t*
 }
 
 // Per-cluster int64 fixed-point sums.  Warp w adds points perm[64w ..
-// 64w+63]; they come in runs of one cluster, summed in registers (lane l holds
-// dimensions l and l+32 of the current 64-dimension slice) and added to the
-// global sums once per run.
+// 64w+63]; they come in runs of one cluster (ends[c] = one past the last
+// position of cluster c in perm, so a run's cluster needs no lookup of the
+// point's assignment), summed in registers (lane l holds dimensions l and
+// l+32 of the current 64-dimension slice) and added to the global sums once
+// per run.  Eight rows are in flight per warp.
 constexpr int SUM_RUN = 64;
+constexpr int SUM_UNROLL = 8;
+__device__ __forceinline__ void sum_flush(long long* sums, uint32_t cur, uint32_t d, uint32_t dj0, uint32_t dj1,
+                                          long long a0, long long a1) {
+  if (dj0 < d && a0) atomicAdd(reinterpret_cast<unsigned long long*>(sums + (uint64_t)cur * d + dj0), (unsigned long long)a0);
+  if (dj1 < d && a1) atomicAdd(reinterpret_cast<unsigned long long*>(sums + (uint64_t)cur * d + dj1), (unsigned long long)a1);
+}
 __global__ void __launch_bounds__(256) km_sum_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, uint32_t k,
-                                                     const int32_t* __restrict__ assign, const uint32_t* __restrict__ perm,
-                                                     const int* shift, long long* sums) {
+                                                     const uint32_t* __restrict__ ends,
+                                                     const uint32_t* __restrict__ perm, const int* shift,
+                                                     long long* sums) {
   const int lane = threadIdx.x & 31;
   const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t p0 = w * SUM_RUN;
@@ -531,41 +638,43 @@ __global__ void __launch_bounds__(256) km_sum_kernel(const float* __restrict__ x
   uint32_t idx[2];
   idx[0] = perm[p0 + lane < p1 ? p0 + lane : p0];
   idx[1] = perm[p0 + 32 + lane < p1 ? p0 + 32 + lane : p0];
+  // cluster of position p0: the first c with ends[c] > p0
+  uint32_t c0 = 0, hi = k - 1;
+  while (c0 < hi) {
+    const uint32_t mid = (c0 + hi) >> 1;
+    if (ends[mid] > p0) hi = mid;
+    else c0 = mid + 1;
+  }
   for (uint32_t j0 = 0; j0 < d; j0 += 64) {
     const uint32_t dj0 = j0 + lane, dj1 = j0 + 32 + lane;
     long long a0 = 0, a1 = 0;
-    int cur = -1;
-    for (uint64_t p = p0; p < p1; p += 4) {
-      float v[4][2];
-      int cl[4];
+    uint32_t cur = c0, cend = ends[c0];
+    for (uint64_t p = p0; p < p1; p += SUM_UNROLL) {
+      float v[SUM_UNROLL][2];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < SUM_UNROLL; ++u) {
         const uint64_t pp = p + u;
-        const uint32_t i = __shfl_sync(0xffffffffu, idx[(pp - p0) >> 5], (int)((pp - p0) & 31));
+        const uint32_t sel = (uint32_t)(pp - p0);
+        const uint32_t i = __shfl_sync(0xffffffffu, sel < 32 ? idx[0] : idx[1], (int)(sel & 31));
         const bool ok = pp < p1;
-        cl[u] = ok ? (int)cluster_of(assign, i, k) : -1;
         v[u][0] = (ok && dj0 < d) ? x[(uint64_t)i * d + dj0] : 0.f;
         v[u][1] = (ok && dj1 < d) ? x[(uint64_t)i * d + dj1] : 0.f;
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (cl[u] < 0) break;
-        if (cl[u] != cur) {
-          if (cur >= 0) {
-            if (dj0 < d && a0) atomicAdd(reinterpret_cast<unsigned long long*>(sums + (uint64_t)cur * d + dj0), (unsigned long long)a0);
-            if (dj1 < d && a1) atomicAdd(reinterpret_cast<unsigned long long*>(sums + (uint64_t)cur * d + dj1), (unsigned long long)a1);
-          }
-          cur = cl[u];
+      for (int u = 0; u < SUM_UNROLL; ++u) {
+        const uint64_t pp = p + u;
+        if (pp >= p1) break;
+        while (pp >= cend) {  // warp-uniform: the run of cluster cur ended (empty clusters skipped)
+          sum_flush(sums, cur, d, dj0, dj1, a0, a1);
           a0 = a1 = 0;
+          ++cur;
+          cend = ends[cur];
         }
         a0 += __float2ll_rn(v[u][0] * scale);
         a1 += __float2ll_rn(v[u][1] * scale);
       }
     }
-    if (cur >= 0) {
-      if (dj0 < d && a0) atomicAdd(reinterpret_cast<unsigned long long*>(sums + (uint64_t)cur * d + dj0), (unsigned long long)a0);
-      if (dj1 < d && a1) atomicAdd(reinterpret_cast<unsigned long long*>(sums + (uint64_t)cur * d + dj1), (unsigned long long)a1);
-    }
+    sum_flush(sums, cur, d, dj0, dj1, a0, a1);
   }
 }
 
@@ -665,9 +774,11 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
   km_maxabs_kernel<<<di.sms * 4, 256, 0, s>>>(x, (uint64_t)n * d, b.maxabs);
   km_scale_kernel<<<1, 1, 0, s>>>(b.maxabs, n, shift);
   *nk += 2;
-  const int asm_bytes = (DC_MAX * KC_MAX + DC_MAX * TP) * 4;
-  if ((e = cudaFuncSetAttribute(km_assign_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, asm_bytes)) !=
-      cudaSuccess)
+  const int asm_bytes = (DC_MAX * CS_LD + DC_MAX * TP) * 4;
+  if ((e = cudaFuncSetAttribute(km_assign_fp32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                asm_bytes)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(km_assign_fp32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                asm_bytes)) != cudaSuccess)
     return e;
   if ((e = cudaFuncSetAttribute(km_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(k * 4))) !=
       cudaSuccess)
@@ -688,12 +799,12 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
     if (b.precision != MR_KM_FP32) {
       if ((e = launch_kmeans_tc_assign(x, n, d, b.cent, k, b, di, s, nk)) != cudaSuccess) return e;
     } else {
-      km_assign_fp32_kernel<<<agrid, KM_THREADS, asm_bytes, s>>>(x, n, d, b.cent, k, b.cnorm, cmax_bits, nullptr,
-                                                                 nullptr, b.assign, b.flagged, b.nflag, b.pairs,
-                                                                 b.nflag + 4, nullptr);
+      (k <= 256 ? km_assign_fp32_kernel<true> : km_assign_fp32_kernel<false>)<<<agrid, KM_THREADS, asm_bytes, s>>>(
+          x, n, d, b.cent, k, b.cnorm, cmax_bits, nullptr, nullptr, b.assign, b.flagged, b.nflag, b.pairs,
+          b.nflag + 4, nullptr);
       ++*nk;
     }
-    km_pair_kernel<<<di.sms * 2, 256, 0, s>>>(x, d, b.cent, b.pairs, b.nflag + 4, b.assign, b.stats + 1);
+    km_pair_kernel<<<di.sms * 4, 256, 0, s>>>(x, d, b.cent, b.pairs, b.nflag + 4, b.assign, b.stats + 1);
     ++*nk;
     if (rc_smem)
       km_recheck_fp64_smem_kernel<<<di.sms, 512, rc_bytes, s>>>(x, d, b.cent, k, b.flagged, b.nflag, b.assign,
@@ -706,7 +817,8 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
     const uint64_t sc_blocks = (n + (uint64_t)SCAT_THREADS * SCAT_PER_THREAD - 1) / ((uint64_t)SCAT_THREADS * SCAT_PER_THREAD);
     km_scatter_kernel<<<(unsigned)sc_blocks, SCAT_THREADS, k * 4, s>>>(b.assign, n, k, b.kcursor, b.flagged);
     const uint64_t sum_warps = (n + SUM_RUN - 1) / SUM_RUN;
-    km_sum_kernel<<<(unsigned)((sum_warps * 32 + 255) / 256), 256, 0, s>>>(x, n, d, k, b.assign, b.flagged, shift,
+    // after the scatter, kcursor[c] is one past the last position of cluster c
+    km_sum_kernel<<<(unsigned)((sum_warps * 32 + 255) / 256), 256, 0, s>>>(x, n, d, k, b.kcursor, b.flagged, shift,
                                                                            b.sums);
     km_finalize_kernel<<<64, 256, 0, s>>>(b.cent, k, d, b.sums, b.counts, shift, cmax_bits);
     *nk += 7;
@@ -721,12 +833,11 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
 cudaError_t launch_kmeans_fp32_list(const float* x, uint32_t n, uint32_t d, const float* c, uint32_t k, KmBuffers& b,
                                     const uint32_t* list, const uint32_t* nlist, const DevInfo& di, cudaStream_t s,
                                     uint64_t* nk) {
-  const int asm_bytes = (DC_MAX * KC_MAX + DC_MAX * TP) * 4;
+  const int asm_bytes = (DC_MAX * CS_LD + DC_MAX * TP) * 4;
   const uint32_t ntiles = (n + TP - 1) / TP;
   const uint32_t agrid = ntiles < (uint32_t)di.sms * 2 ? ntiles : (uint32_t)di.sms * 2;
-  km_assign_fp32_kernel<<<agrid, KM_THREADS, asm_bytes, s>>>(x, n, d, c, k, b.cnorm, b.nflag + 3, list, nlist,
-                                                             b.assign, b.flagged, b.nflag, b.pairs, b.nflag + 4,
-                                                             b.stats);
+  (k <= 256 ? km_assign_fp32_kernel<true> : km_assign_fp32_kernel<false>)<<<agrid, KM_THREADS, asm_bytes, s>>>(
+      x, n, d, c, k, b.cnorm, b.nflag + 3, list, nlist, b.assign, b.flagged, b.nflag, b.pairs, b.nflag + 4, b.stats);
   ++*nk;
   return cudaGetLastError();
 }

@@ -17,13 +17,13 @@
 //   * one thread issues tcgen05.mma (M = 128, N = K rounded up to 16, K = 16
 //     per instruction, 4 steps over D = 64) into one of two 256-column TMEM
 //     accumulators, and commits completion to mbarriers;
-//   * 8 epilogue warps read the 128 x N FP32 tile with tcgen05.ld (one TMEM
-//     lane per point; two warps per lane quadrant, each on half of the
-//     columns), form d~ = fma(-2, acc, ||x||^2) + ||c||^2, pack it with its
-//     column into one sortable 32-bit key and keep the three smallest keys
-//     with unsigned min/max (eight independent top-3s per thread); the upper
-//     half hands its top-3 to the lower half, which applies the margin tests
-//     below.
+//   * 16 epilogue warps read the 128 x N FP32 tile with tcgen05.ld (one
+//     TMEM lane per point; four warps per lane quadrant, each on a quarter
+//     of the columns), form d~ = fma(-2, acc, ||x||^2) + ||c||^2, pack it
+//     with its column into one sortable 32-bit key and keep the two smallest
+//     keys with unsigned min/max (eight independent top-2s per thread) plus
+//     a lower bound of all other keys; quarters 1..3 hand theirs to quarter
+//     0, which applies the margin tests below.
 // Copies, converters, MMA issue and epilogue overlap through the staging
 // ring, two operand stages and two TMEM accumulators.  Every mbarrier wait is bounded; on timeout the
 // CTA stops, drains its MMAs, frees TMEM and reports through stats[3].
@@ -37,11 +37,12 @@
 // norms and the final fma/add (D + 8) * 2^-24 (||x|| + ||c||)^2 (Higham,
 // eq. 3.5).  The keys hold d~ truncated to 16 mantissa bits (t <= d~ <
 // t (1 + 2^-15)), so with G = 2E + 2^-14 t_1: if t_2 - t_1 > max(1e-3 t_1, G)
-// the tensor-core winner is the exact winner.  Otherwise, if t_3 - t_1 > G,
-// every centroid but the top two has exact distance above t_1 (1 + 2^-15) + E
-// >= d(k_1), so the point only needs an exact FP64 choice between those two
-// (pair list); every other point goes to the FP32 pass (and from there, if
-// still close, to FP64), so assignments equal the FP64 argmin.
+// the tensor-core winner is the exact winner.  Otherwise, if b_3 - t_1 > G,
+// where b_3 is a lower bound of every key but the top two, every other
+// centroid has exact distance above t_1 (1 + 2^-15) + E >= d(k_1), so the
+// point only needs an exact FP64 choice between those two (pair list); every
+// other point goes to the FP32 pass (and from there, if still close, to
+// FP64), so assignments equal the FP64 argmin.
 #include <cuda_bf16.h>
 
 #include "mr_internal.h"
@@ -52,18 +53,20 @@ namespace {
 constexpr int TM = 128;          // points per tile = MMA M = TMEM lanes
 constexpr int KD = 64;           // padded dimension: one 128-byte row of BF16
 constexpr int NMAX = 256;        // centroids: MMA N
-constexpr int EPI_WARPS = 8;      // two per TMEM lane quadrant, each on half the columns
-constexpr int MMA_WARP = 8;
-constexpr int CVT_WARP0 = 9;
+constexpr int EPI_WARPS = 16;     // four per TMEM lane quadrant, each on a quarter of the columns
+constexpr int EPI_COLS = NMAX / (EPI_WARPS / 4);  // 64 columns per epilogue warp
+constexpr int MMA_WARP = EPI_WARPS;
+constexpr int CVT_WARP0 = MMA_WARP + 1;
 constexpr int CVT_WARPS = 8;
-constexpr int TMA_WARP = CVT_WARP0 + CVT_WARPS;  // 17
-constexpr int TC_THREADS = (EPI_WARPS + 1 + CVT_WARPS + 1) * 32;  // 576
+constexpr int TMA_WARP = CVT_WARP0 + CVT_WARPS;  // 25
+constexpr int TC_THREADS = (EPI_WARPS + 1 + CVT_WARPS + 1) * 32;  // 832
 constexpr int STAGES = 2;         // operand stages
 constexpr int XST = 2;            // FP32 staging buffers filled by the bulk copy engine
 constexpr int ACCS = 2;           // TMEM accumulators
 constexpr uint32_t TMEM_COLS = 512;  // two 256-column FP32 accumulators
-constexpr long long SPIN_LIMIT = 1ll << 24;
-constexpr int NSET = 8;           // independent running top-3s per epilogue thread
+constexpr long long SPIN_LIMIT = 1ll << 20;
+constexpr uint32_t SUSPEND_NS = 1000;  // a waiting thread sleeps up to this long per poll
+constexpr int NSET = 8;           // independent running top-2s per epilogue thread
 constexpr int CHUNK = 32;         // TMEM columns per tcgen05.ld in the epilogue
 
 struct __align__(1024) TcSmem {
@@ -74,14 +77,17 @@ struct __align__(1024) TcSmem {
   float xs[XST][TM * KD];             // FP32 point tiles (D == 64 path)
   float nx[STAGES][TM];
   float cn[NMAX];
-  uint32_t xt1[ACCS][TM], xt2[ACCS][TM], xt3[ACCS][TM];  // top-3 keys of the upper column half, per row
+  // top-2 keys and the lower bound of the other keys of column quarters 1..3, per row
+  uint32_t xw1[ACCS][EPI_WARPS / 4 - 1][TM], xw2[ACCS][EPI_WARPS / 4 - 1][TM], xlb[ACCS][EPI_WARPS / 4 - 1][TM];
   unsigned long long full_a[STAGES], empty_a[STAGES], nx_free[STAGES];
   unsigned long long full_acc[ACCS], empty_acc[ACCS], drained;
-  unsigned long long xfull[ACCS], xfree[ACCS];  // upper-half top-2 handed to the lower half
+  unsigned long long xfull[ACCS], xfree[ACCS];  // quarters 1..3 hand their keys to quarter 0
   unsigned long long tfull[XST], tempty[XST];   // FP32 staging ring
   uint32_t tmem_base;
   int err;
 };
+
+static_assert(sizeof(TcSmem) + 1024 <= 232448, "shared memory of one CTA");
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -91,20 +97,24 @@ __device__ __forceinline__ void mbar_init(unsigned long long* b, uint32_t count)
 __device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
+// Poll for the completion of the phase with the given parity; the thread is
+// suspended until the phase completes or SUSPEND_NS elapse, so waiting warps
+// do not take issue slots from the working ones.
 __device__ __forceinline__ bool mbar_try(unsigned long long* b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
       : "=r"(ok)
-      : "r"(su32(b)), "r"(parity)
+      : "r"(su32(b)), "r"(parity), "r"(SUSPEND_NS)
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the completion of the phase with the given parity.
+// Bounded wait (at most SPIN_LIMIT polls of at most SUSPEND_NS each, about a
+// second) for the completion of the phase with the given parity.
 __device__ bool mbar_wait(unsigned long long* b, uint32_t parity, volatile int* err) {
   for (long long i = 0; i < SPIN_LIMIT; ++i) {
     if (mbar_try(b, parity)) return true;
-    if ((i & 255) == 255 && *err) return false;
+    if ((i & 15) == 15 && *err) return false;
   }
   *err = 1;
   return false;
@@ -194,33 +204,31 @@ __device__ __forceinline__ uint32_t dist_key(float dist, uint32_t col) {
 }
 __device__ __forceinline__ float key_dist(uint32_t key) { return __uint_as_float(key & 0xFFFFFF00u); }
 
-// Insert key into the sorted triple (t1 <= t2 <= t3): five min/max.
-__device__ __forceinline__ void top3_insert(uint32_t& t1, uint32_t& t2, uint32_t& t3, uint32_t key) {
-  const uint32_t h1 = max(t1, key);
+// Key of a column that holds no centroid: above every finite distance's key,
+// and it decodes to +inf.
+constexpr uint32_t KEY_NONE = 0x7F8000FFu;
+
+// Insert key into the sorted pair (t1 <= t2): three min/max.
+__device__ __forceinline__ void top2_insert(uint32_t& t1, uint32_t& t2, uint32_t key) {
+  const uint32_t h = max(t1, key);
   t1 = min(t1, key);
-  const uint32_t h2 = max(t2, h1);
-  t2 = min(t2, h1);
-  t3 = min(t3, h2);
+  t2 = min(t2, h);
 }
 
-// Smallest three of two sorted triples: the j-th smallest of the union is
-// the minimum over i of max(a_i, b_{j-i}).
-__device__ __forceinline__ void top3_merge_keys(uint32_t& a1, uint32_t& a2, uint32_t& a3, uint32_t b1, uint32_t b2,
-                                                uint32_t b3) {
-  const uint32_t c3 = min(min(a3, b3), min(max(a2, b1), max(a1, b2)));
-  const uint32_t c2 = min(min(a2, b2), max(a1, b1));
+// Smallest two of two sorted pairs.
+__device__ __forceinline__ void top2_merge(uint32_t& a1, uint32_t& a2, uint32_t b1, uint32_t b2) {
+  const uint32_t c2 = min(max(a1, b1), min(a2, b2));
   a1 = min(a1, b1);
   a2 = c2;
-  a3 = c3;
 }
 
-// Distances of CHUNK columns (ch .. ch + CHUNK - 1) of one point into its eight running
-// top-3s.  MASK: some columns are >= k (their TMEM words are not written by
-// the MMA and may hold anything), so those keys are forced to the maximum.
+// Distances of CHUNK columns (ch .. ch + CHUNK - 1) of one point into its
+// NSET running top-2s (column j goes to set j mod NSET).  MASK: some columns
+// are >= k (their TMEM words are not written by the MMA and may hold
+// anything), so those keys are forced to KEY_NONE.
 template <bool MASK>
-__device__ __forceinline__ void top3_keys(const uint32_t (&acc)[CHUNK], uint32_t ch, float nxv, const float* cn,
-                                          uint32_t k, uint32_t (&t1)[NSET], uint32_t (&t2)[NSET], uint32_t (&t3)[NSET],
-                                          float* dbg_row) {
+__device__ __forceinline__ void top2_keys(const uint32_t (&acc)[CHUNK], uint32_t ch, float nxv, const float* cn,
+                                          uint32_t k, uint32_t (&t1)[NSET], uint32_t (&t2)[NSET], float* dbg_row) {
 #pragma unroll
   for (int j = 0; j < CHUNK; j += 4) {
     const float4 c4 = *reinterpret_cast<const float4*>(cn + ch + j);
@@ -231,11 +239,10 @@ __device__ __forceinline__ void top3_keys(const uint32_t (&acc)[CHUNK], uint32_t
       const float dist = fmaf(-2.f, __uint_as_float(acc[j + e]), nxv) + cv[e];
       uint32_t key = dist_key(dist, kk);
       if (MASK) {
-        if (kk >= k) key = 0xFFFFFFFFu;
+        if (kk >= k) key = KEY_NONE;
         else if (dbg_row) dbg_row[kk] = dist;
       }
-      const int a = (j + e) % NSET;
-      top3_insert(t1[a], t2[a], t3[a], key);
+      top2_insert(t1[(j + e) % NSET], t2[(j + e) % NSET], key);
     }
   }
 }
@@ -276,8 +283,8 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
     for (int b = 0; b < ACCS; ++b) {
       mbar_init(&S.full_acc[b], 1);
       mbar_init(&S.empty_acc[b], EPI_WARPS);
-      mbar_init(&S.xfull[b], EPI_WARPS / 2);
-      mbar_init(&S.xfree[b], EPI_WARPS / 2);
+      mbar_init(&S.xfull[b], EPI_WARPS - 4);
+      mbar_init(&S.xfree[b], 4);
     }
     for (int q = 0; q < XST; ++q) {
       mbar_init(&S.tfull[q], 1);
@@ -445,18 +452,23 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
     __syncwarp();
   } else {
     // ------------------------------------------------------------- epilogue
-    // Warp e reads TMEM lane quadrant e % 4 (rows 32 (e % 4) ..), columns of
-    // half e / 4, CHUNK columns per tcgen05.ld.  Each distance becomes one
-    // sortable 32-bit key (see dist_key), so a running top-3 costs five
-    // unsigned min/max; eight independent top-3s per thread (columns j mod 8)
-    // keep the dependency chains short, and are merged at the end of the tile.
-    const int q = warp & 3, half = warp >> 2;
+    // Warp e reads TMEM lane quadrant e % 4 (rows 32 (e % 4) ..) and column
+    // quarter e / 4 (EPI_COLS columns), CHUNK columns per tcgen05.ld.  Each
+    // distance becomes one sortable 32-bit key (see dist_key), so a running
+    // top-2 costs three unsigned min/max; NSET independent top-2s per thread
+    // (columns j mod NSET) keep the dependency chains short.  A warp then
+    // reduces its sets to its top-2 (w1, w2) and a lower bound lb of all its
+    // other keys (per set: the set's smallest key that is not w1 or w2, or
+    // its second key when both are, which bounds the rest of that set).
+    // Quarters 1..3 hand (w1, w2, lb) to quarter 0, which forms the row's
+    // exact top-2 (g1, g2) and a lower bound g3 of every other key.
+    const int q = warp & 3, quarter = warp >> 2;
     const int r = q * 32 + lane;
     const float eps_sum = TERMS == 3 ? (3.05f * 1.52587890625e-05f + (float)(3 * KD + 8) * 4.76837158203125e-07f)
                                      : (2.f * 3.90625e-03f + 1.52587890625e-05f + (float)(KD + 8) * 4.76837158203125e-07f);
     const float eps32 = 1.01f * (float)(d + 8) * 5.9604644775390625e-08f;
-    const uint32_t c_lo = (uint32_t)half * 128u;
-    const uint32_t c_hi = min(npad, c_lo + 128u);
+    const uint32_t c_lo = (uint32_t)quarter * EPI_COLS;
+    const uint32_t c_hi = min(npad, c_lo + (uint32_t)EPI_COLS);
     for (uint32_t i = 0;; ++i) {
       const uint32_t tile = blockIdx.x + i * gridDim.x;
       if (tile >= ntiles) break;
@@ -469,55 +481,75 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
       const float nxv = S.nx[s][r];
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.nx_free[s]);
-      uint32_t t1[NSET], t2[NSET], t3[NSET];
+      uint32_t t1[NSET], t2[NSET];
 #pragma unroll
-      for (int a = 0; a < NSET; ++a) t1[a] = t2[a] = t3[a] = 0xFFFFFFFFu;
+      for (int a = 0; a < NSET; ++a) t1[a] = t2[a] = KEY_NONE;
       const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * 256u;
       float* dbg_row = (dbg && tile == 0) ? dbg + (uint64_t)r * NMAX : nullptr;
       for (uint32_t ch = c_lo; ch < c_hi; ch += CHUNK) {
         uint32_t acc[CHUNK];
         tmem_ld(ta + ch, acc);
         if (ch + CHUNK <= k && !dbg_row)
-          top3_keys<false>(acc, ch, nxv, S.cn, k, t1, t2, t3, nullptr);
+          top2_keys<false>(acc, ch, nxv, S.cn, k, t1, t2, nullptr);
         else
-          top3_keys<true>(acc, ch, nxv, S.cn, k, t1, t2, t3, dbg_row);
+          top2_keys<true>(acc, ch, nxv, S.cn, k, t1, t2, dbg_row);
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.empty_acc[b]);
+      uint32_t w1 = t1[0], w2 = t2[0];
 #pragma unroll
-      for (int a = 1; a < NSET; ++a) top3_merge_keys(t1[0], t2[0], t3[0], t1[a], t2[a], t3[a]);
-      if (half == 1) {
-        // hand this half's top-3 to the warp of the other half on the same rows
+      for (int a = 1; a < NSET; ++a) top2_merge(w1, w2, t1[a], t2[a]);
+      uint32_t lb = KEY_NONE;
+#pragma unroll
+      for (int a = 0; a < NSET; ++a) lb = min(lb, (t1[a] == w1 || t1[a] == w2) ? t2[a] : t1[a]);
+      if (quarter != 0) {
         if (i >= ACCS) {
           const bool okf = mbar_wait(&S.xfree[b], (v + 1) & 1, err);
           if (!__all_sync(0xffffffffu, okf)) break;
         }
-        S.xt1[b][r] = t1[0];
-        S.xt2[b][r] = t2[0];
-        S.xt3[b][r] = t3[0];
+        S.xw1[b][quarter - 1][r] = w1;
+        S.xw2[b][quarter - 1][r] = w2;
+        S.xlb[b][quarter - 1][r] = lb;
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.xfull[b]);
         continue;
       }
+      uint32_t o1[EPI_WARPS / 4 - 1], o2[EPI_WARPS / 4 - 1], ol[EPI_WARPS / 4 - 1];
       {
         const bool okx = mbar_wait(&S.xfull[b], v & 1, err);
         if (!__all_sync(0xffffffffu, okx)) break;
-        const uint32_t o1 = S.xt1[b][r], o2 = S.xt2[b][r], o3 = S.xt3[b][r];
+#pragma unroll
+        for (int u = 0; u < EPI_WARPS / 4 - 1; ++u) {
+          o1[u] = S.xw1[b][u][r];
+          o2[u] = S.xw2[b][u][r];
+          ol[u] = S.xlb[b][u][r];
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.xfree[b]);
-        top3_merge_keys(t1[0], t2[0], t3[0], o1, o2, o3);
+      }
+      uint32_t g1 = w1, g2 = w2, g3 = lb;
+#pragma unroll
+      for (int u = 0; u < EPI_WARPS / 4 - 1; ++u) top2_merge(g1, g2, o1[u], o2[u]);
+      // every key other than g1, g2 is >= g3: the warps' bounds, and the
+      // warps' top-2 keys that did not make the row's top-2
+      g3 = (w1 != g1 && w1 != g2) ? min(g3, w1) : g3;
+      g3 = (w2 != g1 && w2 != g2) ? min(g3, w2) : g3;
+#pragma unroll
+      for (int u = 0; u < EPI_WARPS / 4 - 1; ++u) {
+        g3 = min(g3, ol[u]);
+        g3 = (o1[u] != g1 && o1[u] != g2) ? min(g3, o1[u]) : g3;
+        g3 = (o2[u] != g1 && o2[u] != g2) ? min(g3, o2[u]) : g3;
       }
       const uint32_t p = tile * TM + r;
       bool flag = false, pair = false;
       if (p < n) {
-        const float d1 = key_dist(t1[0]), d2 = key_dist(t2[0]), d3 = key_dist(t3[0]);
-        const int k1 = (int)(t1[0] & 0xFFu);
+        const float d1 = key_dist(g1), d2 = key_dist(g2), d3 = key_dist(g3);
         const float xn = sqrtf(nxv);
         const float e = 2.f * eps_sum * xn * cmax + eps32 * (xn + cmax) * (xn + cmax);
         // keys under-state a distance by less than 2^-15 of it (2^-14 allowed)
         const float gap = 2.f * e + 6.103515625e-05f * d1;
-        if (d2 - d1 > fmaxf(1e-3f * d1, gap)) assign[p] = k1;
+        if (d2 - d1 > fmaxf(1e-3f * d1, gap)) assign[p] = (int)(g1 & 0xFFu);
         else if (d3 - d1 > gap) pair = true;  // only the top two can be the exact minimum
         else flag = true;
       }
@@ -526,8 +558,7 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(npairs, (uint32_t)__popc(pm));
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (pair)
-          pairs[base + __popc(pm & ((1u << lane) - 1))] = make_uint2(p, (t1[0] & 0xFFu) | ((t2[0] & 0xFFu) << 16));
+        if (pair) pairs[base + __popc(pm & ((1u << lane) - 1))] = make_uint2(p, (g1 & 0xFFu) | ((g2 & 0xFFu) << 16));
       }
       const unsigned fm = __ballot_sync(0xffffffffu, flag);
       if (fm) {

@@ -345,3 +345,24 @@ def test_bloom_fill_matches_expectation_and_no_false_negatives():
     for c in codes[:200].tolist():
         one = np.unpackbits(oracle.bloom_codes([c], m, h), bitorder="little")[:m]
         assert np.all(bits[one == 1] == 1)
+
+
+# ------------------------------------------------------------- string hashing
+
+def test_fnv1a64_published_vectors():
+    # FNV-1a 64 test vectors published with the FNV reference code
+    assert oracle.fnv1a64(b"") == 0xCBF29CE484222325
+    assert oracle.fnv1a64(b"a") == 0xAF63DC4C8601EC8C
+    assert oracle.fnv1a64(b"foobar") == 0x85944171F73967E8
+
+
+def test_token_hashes_follow_the_tokens():
+    import re
+    text = bytes(synth.wc_text(200_000, nwords=3000)[0]) + b"\x00\xff x\ty\v\fz\r\n" + b"q" * 40
+    off, ln, h = oracle.token_hashes(text)
+    spans = [(m.start(), m.end()) for m in re.finditer(rb"[^ \t\n\v\f\r]+", text)]
+    assert [(int(a), int(a + b)) for a, b in zip(off, ln)] == spans
+    for i in (0, 1, len(spans) // 2, len(spans) - 1):
+        a, b = spans[i]
+        assert int(h[i]) == oracle.fnv1a64(text[a:b])
+    assert oracle.token_hashes(b"")[0].size == 0 and oracle.token_hashes(b" \n ")[0].size == 0
