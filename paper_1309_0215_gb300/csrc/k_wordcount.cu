@@ -17,20 +17,27 @@
 //    the next one from the list (as SIMDH-Stream refills a lane), the warp
 //    prefix sum replacing the paper's prefix-sum lookup table.  A short token
 //    is read as 16 bytes at once and becomes its own 128-bit key.
-//  * Combiner / local container (Sec. III-A, Sec. III-D): a 256-slot table per
-//    warp in shared memory, flushed into the global container when half full
-//    (the paper's bounded local table handed to the reduce side).
+//  * Combiner / local container (Sec. III-A, Sec. III-D): a 2-way cache of
+//    hot keys per warp in shared memory, merged into the global container
+//    every few dozen segments (the paper's bounded local table handed to the
+//    reduce side; see dev_wordcount.cuh).
 //  * Global container: open addressing with a 128-bit CAS per new key and an
 //    atomicAdd per combine (see dev_wordcount.cuh).
 //  * Merge + sort: occupied slots of every job are compacted into one record
-//    array and sorted once by (job, count desc, key asc) — a shared-memory
-//    bitonic sort of 2048-record blocks, then merge passes whose split points
-//    come from a warp-cooperative 33-way search and whose inputs are staged in
-//    shared memory — so a batch
-//    of jobs is ordered by a single launch sequence; per-job boundaries and a
-//    scan of key lengths place each job's records and key bytes in its
-//    result: {u64 n, u64 key bytes; n x {u64 count, u64 key_off, u64 key_len};
-//    key bytes}.
+//    array and sorted once by (job, count desc, key asc), so a batch of jobs
+//    is ordered by a single launch sequence.  The sort is a stable LSD radix
+//    sort (8-bit digits) on (job/count word, first 8 key bytes); digit
+//    positions that are equal in every key are skipped, decided on the
+//    device so the sequence can be captured in a CUDA graph.  Records that
+//    tie on both words (keys sharing their first 8 bytes and their count)
+//    are then ordered by the full comparison (one thread per short run, one
+//    CTA per run of up to 2048).  A longer tie run switches the whole batch
+//    to the comparison sort kept as a fallback: a shared-memory bitonic sort
+//    of 2048-record blocks, then merge passes whose split points come from a
+//    warp-cooperative 33-way search.  Per-job boundaries and a scan of key
+//    lengths then place each job's records and key bytes in its result:
+//    {u64 n, u64 key bytes; n x {u64 count, u64 key_off, u64 key_len}; key
+//    bytes}.
 #include "mr_internal.h"
 #include "dev_wordcount.cuh"
 
@@ -71,13 +78,34 @@ struct SortRec {
 };
 static_assert(sizeof(SortRec) == 32, "SortRec layout");
 
+// Radix sort geometry: one 256-thread CTA per tile of 2048 records, 8 items
+// per thread; tile histograms are scanned in chunks of 32 tiles.
+constexpr int RT = 256;
+constexpr int RIPT = 8;
+constexpr int RTILE = RT * RIPT;
+constexpr int RCHUNK = 32;
+constexpr int NPASS = 16;       // 8 digits of s0, then 8 digits of key1
+constexpr int FIX_THREAD = 32;  // tie runs up to this long: one thread's insertion sort
+// The radix sort runs ~70 short launches whatever the record count; below
+// this capacity the comparison sort (fewer, fuller launches) is faster.
+constexpr uint64_t RADIX_MIN_RECORDS = 1ull << 20;
+
 struct Post {
   SortRec* r0;
   SortRec* r1;
   unsigned long long* src;   // [R] input offset of a long key
   unsigned long long* excl;  // [R] exclusive scan of key lengths in sorted order
   unsigned long long* bsum;  // [ceil(R / CB)]
-  unsigned long long* glob;  // [0] number of records
+  // [0] number of records; [1] 1 = comparison-sort fallback; [2] long tie
+  // runs listed; [4..7] OR of ~key1, key1, ~s0, s0 (digits equal in every key)
+  unsigned long long* glob;
+  unsigned long long* kh[2];  // radix ping-pong: key1
+  unsigned long long* kl[2];  // s0
+  uint32_t* kv[2];            // record index
+  uint32_t* hist;             // [tiles][256] digit counts, per pass
+  uint32_t* csum;             // [chunks][256] chunk sums, then chunk offsets
+  uint32_t* plan;             // [NPASS] bit 0 active, bit 1 source buffer; [NPASS] final buffer
+  uint2* runs;                // tie runs longer than FIX_THREAD: {first, length}
 };
 
 __device__ __forceinline__ uint64_t bswap64(uint64_t v) {
@@ -195,6 +223,7 @@ constexpr int SB_THREADS = 1024;
 __global__ void __launch_bounds__(SB_THREADS) wc_blocksort_kernel(const JobDev* jobs, JobDev single, Post P) {
   extern __shared__ __align__(16) unsigned char bs_raw[];
   SortRec* sh = reinterpret_cast<SortRec*>(bs_raw);
+  if (!P.glob[1]) return;  // the radix sort succeeded
   const uint64_t m = *P.glob;
   const uint64_t b0 = (uint64_t)blockIdx.x * SB;
   if (b0 >= m) return;
@@ -264,6 +293,7 @@ __global__ void __launch_bounds__(MT) wc_merge_kernel(const SortRec* __restrict_
   extern __shared__ __align__(16) unsigned char mg_raw[];
   SortRec* ms = reinterpret_cast<SortRec*>(mg_raw);
   __shared__ uint64_t cr[2];
+  if (!P.glob[1]) return;  // the radix sort succeeded
   const uint64_t m = *P.glob;
   const uint64_t o0 = (uint64_t)blockIdx.x * MTILE;
   if (o0 >= m) return;
@@ -313,8 +343,14 @@ __global__ void __launch_bounds__(MT) wc_merge_kernel(const SortRec* __restrict_
   }
 }
 
-__global__ void __launch_bounds__(CB) wc_lensum_kernel(const SortRec* recs, Post P) {
+// The sorted records: the radix sort's output, or the fallback's.
+__device__ __forceinline__ const SortRec* final_recs(const Post& P, const SortRec* fallback) {
+  return P.glob[1] ? fallback : P.r1;
+}
+
+__global__ void __launch_bounds__(CB) wc_lensum_kernel(const SortRec* fb, Post P) {
   __shared__ unsigned long long ws[32];
+  const SortRec* recs = final_recs(P, fb);
   const uint64_t m = *P.glob;
   const uint64_t i = (uint64_t)blockIdx.x * CB + threadIdx.x;
   unsigned long long v = i < m ? recs[i].len : 0;
@@ -365,8 +401,9 @@ __global__ void __launch_bounds__(CB) wc_bscan_kernel(Post P, uint64_t nb) {
 
 // Exclusive length scan per record; each job's first / end record and the
 // scan at both are stored in the job's state as 64-bit fields 1..4.
-__global__ void __launch_bounds__(CB) wc_bounds_kernel(const SortRec* recs, const JobDev* jobs, JobDev single, Post P) {
+__global__ void __launch_bounds__(CB) wc_bounds_kernel(const SortRec* fb, const JobDev* jobs, JobDev single, Post P) {
   __shared__ unsigned long long wsum[32];
+  const SortRec* recs = final_recs(P, fb);
   const uint64_t m = *P.glob;
   const uint64_t i = (uint64_t)blockIdx.x * CB + threadIdx.x;
   if ((uint64_t)blockIdx.x * CB >= m) return;
@@ -407,7 +444,8 @@ __global__ void __launch_bounds__(CB) wc_bounds_kernel(const SortRec* recs, cons
 }
 
 // Records and key bytes into each job's result.
-__global__ void __launch_bounds__(256) wc_gather_kernel(const SortRec* recs, const JobDev* jobs, JobDev single, Post P) {
+__global__ void __launch_bounds__(256) wc_gather_kernel(const SortRec* fb, const JobDev* jobs, JobDev single, Post P) {
+  const SortRec* recs = final_recs(P, fb);
   const uint64_t m = *P.glob;
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
@@ -437,7 +475,289 @@ __global__ void __launch_bounds__(256) wc_gather_kernel(const SortRec* recs, con
   }
 }
 
+
+// ------------------------------------------------------------ radix sort
+// Keys and record indices of the compacted records, and which of the 16
+// digit positions differ between keys (bitwise OR of ~key and of key: a
+// digit position is constant iff both ORs agree there as complements).
+__global__ void __launch_bounds__(CB) wc_rkeys_kernel(Post P) {
+  __shared__ unsigned long long red[4][32];
+  const uint64_t m = *P.glob;
+  const uint64_t i = (uint64_t)blockIdx.x * CB + threadIdx.x;
+  if ((uint64_t)blockIdx.x * CB >= m) return;
+  unsigned long long v[4] = {0, 0, 0, 0};
+  if (i < m) {
+    const SortRec r = P.r0[i];
+    P.kh[0][i] = r.key1;
+    P.kl[0][i] = r.s0;
+    P.kv[0][i] = (uint32_t)i;
+    v[0] = ~r.key1;
+    v[1] = r.key1;
+    v[2] = ~r.s0;
+    v[3] = r.s0;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    for (int o = 16; o; o >>= 1) v[q] |= __shfl_xor_sync(0xffffffffu, v[q], o);
+    if (lane == 0) red[q][warp] = v[q];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      unsigned long long w = red[q][lane];
+      for (int o = 16; o; o >>= 1) w |= __shfl_xor_sync(0xffffffffu, w, o);
+      if (lane == 0 && w) atomicOr(P.glob + 4 + q, w);
+    }
+  }
+}
+
+// Pass plan: a pass is run only if its digit differs between keys; its
+// source is the buffer the previous run pass wrote.
+__global__ void wc_rplan_kernel(Post P) {
+  const uint64_t m = P.glob[0];
+  const unsigned long long and_hi = ~P.glob[4], or_hi = P.glob[5];
+  const unsigned long long and_lo = ~P.glob[6], or_lo = P.glob[7];
+  uint32_t cur = 0;
+  for (int p = 0; p < NPASS; ++p) {
+    const unsigned long long diff = p < 8 ? (and_lo ^ or_lo) : (and_hi ^ or_hi);
+    const bool active = m > 1 && ((diff >> (8 * (p & 7))) & 0xFFull) != 0;
+    P.plan[p] = active ? (1u | (cur << 1)) : 0u;
+    if (active) cur ^= 1u;
+  }
+  P.plan[NPASS] = cur;
+}
+
+__device__ __forceinline__ uint32_t rdigit(const Post& P, int p, uint32_t buf, uint64_t i) {
+  const unsigned long long w = p < 8 ? P.kl[buf][i] : P.kh[buf][i];
+  return (uint32_t)(w >> (8 * (p & 7))) & 0xFFu;
+}
+
+// Digit counts of each tile.
+__global__ void __launch_bounds__(RT) wc_rhist_kernel(Post P, int p) {
+  __shared__ uint32_t h[256];
+  const uint32_t plan = P.plan[p];
+  if (!(plan & 1u)) return;
+  const uint64_t m = *P.glob;
+  const uint64_t t0 = (uint64_t)blockIdx.x * RTILE;
+  if (t0 >= m) return;
+  const uint32_t src = (plan >> 1) & 1u;
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  for (int k = 0; k < RIPT; ++k) {
+    const uint64_t i = t0 + (uint64_t)k * RT + threadIdx.x;
+    if (i < m) atomicAdd(&h[rdigit(P, p, src, i)], 1u);
+  }
+  __syncthreads();
+  P.hist[(uint64_t)blockIdx.x * 256 + threadIdx.x] = h[threadIdx.x];
+}
+
+// Per digit: sum of each chunk of RCHUNK tiles.
+__global__ void __launch_bounds__(RT) wc_rscan1_kernel(Post P, int p) {
+  if (!(P.plan[p] & 1u)) return;
+  const uint64_t m = *P.glob;
+  const uint64_t ntiles = (m + RTILE - 1) / RTILE;
+  const uint64_t b0 = (uint64_t)blockIdx.x * RCHUNK;
+  if (b0 >= ntiles) return;
+  const uint64_t b1 = (b0 + RCHUNK) < ntiles ? b0 + RCHUNK : ntiles;
+  uint32_t sum = 0;
+  for (uint64_t b = b0; b < b1; ++b) sum += P.hist[b * 256 + threadIdx.x];
+  P.csum[(uint64_t)blockIdx.x * 256 + threadIdx.x] = sum;
+}
+
+// One CTA: chunk offsets = digit base (exclusive scan of the digit totals)
+// + exclusive scan over the chunks of that digit.
+__global__ void __launch_bounds__(RT) wc_rscan2_kernel(Post P, int p) {
+  __shared__ uint32_t tot[RT];
+  if (!(P.plan[p] & 1u)) return;
+  const uint64_t m = *P.glob;
+  const uint64_t nchunks = ((m + RTILE - 1) / RTILE + RCHUNK - 1) / RCHUNK;
+  const int d = threadIdx.x;
+  uint32_t run = 0;
+  for (uint64_t c = 0; c < nchunks; ++c) {
+    const uint32_t t = P.csum[c * 256 + d];
+    P.csum[c * 256 + d] = run;
+    run += t;
+  }
+  tot[d] = run;
+  __syncthreads();
+  if (d == 0) {
+    uint32_t acc = 0;
+    for (int q = 0; q < RT; ++q) {
+      const uint32_t t = tot[q];
+      tot[q] = acc;
+      acc += t;
+    }
+  }
+  __syncthreads();
+  const uint32_t base = tot[d];
+  for (uint64_t c = 0; c < nchunks; ++c) P.csum[c * 256 + d] += base;
+}
+
+// Stable scatter of one tile.  Items are taken in 8 rounds of 256 (round k,
+// warp w, lane l = tile position 256k + 32w + l), so tile order is (round,
+// warp, lane).  Per round: lanes with the same digit are found with 8
+// ballots (one per digit bit); each warp's digit counts are prefix-summed
+// over the warps in order, on top of the counts of earlier rounds and of
+// earlier tiles (chunk offset + tiles of the chunk before this one).
+__global__ void __launch_bounds__(RT) wc_rscatter_kernel(Post P, int p) {
+  __shared__ uint32_t run[256];
+  __shared__ uint32_t wh[RT / 32][256];
+  const uint32_t plan = P.plan[p];
+  if (!(plan & 1u)) return;
+  const uint64_t m = *P.glob;
+  const uint64_t b = blockIdx.x;
+  const uint64_t t0 = b * RTILE;
+  if (t0 >= m) return;
+  const uint32_t src = (plan >> 1) & 1u, dst = src ^ 1u;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  {
+    const uint64_t c = b / RCHUNK;
+    uint32_t off = P.csum[c * 256 + threadIdx.x];
+    for (uint64_t q = c * RCHUNK; q < b; ++q) off += P.hist[q * 256 + threadIdx.x];
+    run[threadIdx.x] = off;
+  }
+  const unsigned below = (1u << lane) - 1u;
+  for (int k = 0; k < RIPT; ++k) {
+    const uint64_t i = t0 + (uint64_t)k * RT + threadIdx.x;
+    const bool valid = i < m;
+    unsigned long long hi = 0, lo = 0;
+    uint32_t val = 0, d = 0;
+    if (valid) {
+      hi = P.kh[src][i];
+      lo = P.kl[src][i];
+      val = P.kv[src][i];
+      d = (uint32_t)((p < 8 ? lo : hi) >> (8 * (p & 7))) & 0xFFu;
+    }
+    unsigned peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (int bit = 0; bit < 8; ++bit) {
+      const unsigned bb = __ballot_sync(0xffffffffu, valid && ((d >> bit) & 1u));
+      peers &= ((d >> bit) & 1u) ? bb : ~bb;
+    }
+#pragma unroll
+    for (int q = 0; q < RT / 32; ++q) wh[q][threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t wrank = (uint32_t)__popc(peers & below);
+    if (valid && wrank == 0) wh[warp][d] = (uint32_t)__popc(peers);
+    __syncthreads();
+    {
+      uint32_t r = run[threadIdx.x];
+#pragma unroll
+      for (int q = 0; q < RT / 32; ++q) {
+        const uint32_t x = wh[q][threadIdx.x];
+        wh[q][threadIdx.x] = r;
+        r += x;
+      }
+      run[threadIdx.x] = r;
+    }
+    __syncthreads();
+    if (valid) {
+      const uint32_t pos = wh[warp][d] + wrank;
+      P.kh[dst][pos] = hi;
+      P.kl[dst][pos] = lo;
+      P.kv[dst][pos] = val;
+    }
+    __syncthreads();
+  }
+}
+
+// Records in radix order.
+__global__ void __launch_bounds__(256) wc_rgather_kernel(Post P) {
+  const uint64_t m = *P.glob;
+  const uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
+  if (i >= m) return;
+  const uint32_t fin = m > 1 ? P.plan[NPASS] : 0u;
+  P.r1[i] = P.r0[m > 1 ? P.kv[fin][i] : i];
+}
+
+__device__ __forceinline__ bool rtie(const SortRec& a, const SortRec& b) { return a.key1 == b.key1 && a.s0 == b.s0; }
+
+// Records that tie on (key1, s0) are ordered by the full comparison: a run
+// of up to FIX_THREAD by its first thread, longer ones are listed for
+// wc_rfix_long_kernel (up to SB records) or switch to the fallback sort.
+__global__ void __launch_bounds__(256) wc_rfix_kernel(Post P, const JobDev* jobs, JobDev single, uint64_t max_runs) {
+  const uint64_t m = *P.glob;
+  const uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
+  if (i + 1 >= m) return;
+  SortRec* r = P.r1;
+  if (!rtie(r[i], r[i + 1])) return;
+  if (i > 0 && rtie(r[i - 1], r[i])) return;  // not the first of its run
+  uint64_t L = 2;
+  while (i + L < m && L <= (uint64_t)SB && rtie(r[i], r[i + L])) ++L;
+  if (L <= (uint64_t)FIX_THREAD) {
+    for (uint64_t a = i + 1; a < i + L; ++a) {
+      const SortRec x = r[a];
+      uint64_t q = a;
+      while (q > i && rec_less(x, r[q - 1], jobs, single, P.src)) {
+        r[q] = r[q - 1];
+        --q;
+      }
+      r[q] = x;
+    }
+  } else if (L <= (uint64_t)SB) {
+    const unsigned long long k = atomicAdd(P.glob + 2, 1ull);
+    if (k < max_runs) P.runs[k] = make_uint2((uint32_t)i, (uint32_t)L);
+    else P.glob[1] = 1;
+  } else {
+    P.glob[1] = 1;
+  }
+}
+
+// One CTA per listed tie run: bitonic sort in shared memory.
+__global__ void __launch_bounds__(SB_THREADS) wc_rfix_long_kernel(Post P, const JobDev* jobs, JobDev single,
+                                                                  uint64_t max_runs) {
+  extern __shared__ __align__(16) unsigned char rf_raw[];
+  SortRec* sh = reinterpret_cast<SortRec*>(rf_raw);
+  if (P.glob[1]) return;
+  uint64_t nr = P.glob[2];
+  if (nr > max_runs) nr = max_runs;
+  for (uint64_t k = blockIdx.x; k < nr; k += gridDim.x) {
+    const uint2 run = P.runs[k];
+    SortRec* r = P.r1 + run.x;
+    const int L = (int)run.y;
+    int n2 = 1;
+    while (n2 < L) n2 <<= 1;
+    for (int i = threadIdx.x; i < n2; i += blockDim.x)
+      sh[i] = i < L ? r[i] : SortRec{~0ull, ~0ull, ~0ull, 0xffffffffu, 0xffffffffu};
+    __syncthreads();
+    for (int kk = 2; kk <= n2; kk <<= 1) {
+      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+        for (int t = threadIdx.x; t < n2 / 2; t += blockDim.x) {
+          const int lo = 2 * jj * (t / jj) + (t % jj);
+          const int hi = lo + jj;
+          const bool up = (lo & kk) == 0;
+          const SortRec a = sh[lo], bb = sh[hi];
+          const bool a_pad = a.idx == 0xffffffffu, b_pad = bb.idx == 0xffffffffu;
+          bool b_lt_a;
+          if (a_pad || b_pad) b_lt_a = a_pad && !b_pad;
+          else b_lt_a = rec_less(bb, a, jobs, single, P.src);
+          if (b_lt_a == up) {
+            sh[lo] = bb;
+            sh[hi] = a;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int i = threadIdx.x; i < L; i += blockDim.x) r[i] = sh[i];
+    __syncthreads();
+  }
+}
+
 inline uint64_t a256(uint64_t x) { return (x + 255) & ~255ull; }
+
+constexpr uint64_t ca256(uint64_t x) { return (x + 255) & ~255ull; }
+constexpr uint64_t rtiles(uint64_t R) { return (R + RTILE - 1) / RTILE; }
+constexpr uint64_t rchunks(uint64_t R) { return (rtiles(R) + RCHUNK - 1) / RCHUNK; }
+constexpr uint64_t max_runs(uint64_t R) { return R / (FIX_THREAD + 1) + 1; }
+constexpr uint64_t sortbuf_bytes(uint64_t R) {
+  return 256 + 2 * ca256(R * sizeof(SortRec)) + 2 * ca256(R * 8) + ca256(((R + CB - 1) / CB) * 8) +
+         (R >= RADIX_MIN_RECORDS ? 4 * ca256(R * 8) + 2 * ca256(R * 4) + ca256(rtiles(R) * 256 * 4) +
+                                       ca256(rchunks(R) * 256 * 4) + 256 + ca256(max_runs(R) * 8)
+                                 : 0);
+}
 
 Post carve_post(uint8_t* p, uint64_t R) {
   Post P;
@@ -452,6 +772,25 @@ Post carve_post(uint8_t* p, uint64_t R) {
   P.excl = reinterpret_cast<unsigned long long*>(p);
   p += a256(R * 8);
   P.bsum = reinterpret_cast<unsigned long long*>(p);
+  p += a256(((R + CB - 1) / CB) * 8);
+  if (R < RADIX_MIN_RECORDS) return P;  // comparison sort only: no radix buffers
+  for (int q = 0; q < 2; ++q) {
+    P.kh[q] = reinterpret_cast<unsigned long long*>(p);
+    p += a256(R * 8);
+    P.kl[q] = reinterpret_cast<unsigned long long*>(p);
+    p += a256(R * 8);
+  }
+  for (int q = 0; q < 2; ++q) {
+    P.kv[q] = reinterpret_cast<uint32_t*>(p);
+    p += a256(R * 4);
+  }
+  P.hist = reinterpret_cast<uint32_t*>(p);
+  p += a256(rtiles(R) * 256 * 4);
+  P.csum = reinterpret_cast<uint32_t*>(p);
+  p += a256(rchunks(R) * 256 * 4);
+  P.plan = reinterpret_cast<uint32_t*>(p);
+  p += 256;
+  P.runs = reinterpret_cast<uint2*>(p);
   return P;
 }
 
@@ -466,10 +805,7 @@ uint32_t ilog2(uint64_t x) {
 uint64_t wc_table_bytes(uint64_t cap) { return cap * 24; }
 uint64_t wc_state_bytes() { return 64; }
 
-size_t wc_sortbuf_bytes(uint64_t R) {
-  const uint64_t nb = (R + CB - 1) / CB;
-  return 256 + 2 * a256(R * sizeof(SortRec)) + 2 * a256(R * 8) + a256(nb * 8);
-}
+size_t wc_sortbuf_bytes(uint64_t R) { return sortbuf_bytes(R); }
 
 uint64_t wc_out_bytes(uint64_t cap, uint64_t n) {
   // at most cap records; key bytes never exceed the input
@@ -499,10 +835,41 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
                                         uint64_t* nk) {
   cudaError_t e;
   Post P = carve_post(sortbuf, R);
-  if ((e = cudaMemsetAsync(P.glob, 0, 8, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(P.glob, 0, 64, s)) != cudaSuccess) return e;
   wc_compact_kernel<<<(unsigned)nblocks, CB, 0, s>>>(jobs, single, njobs, P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const uint64_t nb = (R + CB - 1) / CB;
+  if (R < RADIX_MIN_RECORDS) {
+    // small record sets: the comparison sort below does all the work
+    if ((e = cudaMemsetAsync(P.glob + 1, 1, 1, s)) != cudaSuccess) return e;
+  } else {
+  // radix sort by (key1, s0), then the tie runs
+  wc_rkeys_kernel<<<(unsigned)nb, CB, 0, s>>>(P);
+  wc_rplan_kernel<<<1, 1, 0, s>>>(P);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  *nk += 3;
+  for (int p = 0; p < NPASS; ++p) {
+    wc_rhist_kernel<<<(unsigned)rtiles(R), RT, 0, s>>>(P, p);
+    wc_rscan1_kernel<<<(unsigned)rchunks(R), RT, 0, s>>>(P, p);
+    wc_rscan2_kernel<<<1, RT, 0, s>>>(P, p);
+    wc_rscatter_kernel<<<(unsigned)rtiles(R), RT, 0, s>>>(P, p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    *nk += 4;
+  }
+  wc_rgather_kernel<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(P);
+  wc_rfix_kernel<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(P, jobs, single, max_runs(R));
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  {
+    const int fx_smem = SB * (int)sizeof(SortRec);
+    if ((e = cudaFuncSetAttribute(wc_rfix_long_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem)) !=
+        cudaSuccess)
+      return e;
+    wc_rfix_long_kernel<<<64, SB_THREADS, fx_smem, s>>>(P, jobs, single, max_runs(R));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  *nk += 3;
+  }
+  // fallback (only if a tie run was too long): comparison sort of P.r0
   const int bs_smem = SB * (int)sizeof(SortRec);
   const int mg_smem = MTILE * (int)sizeof(SortRec);
   if ((e = cudaFuncSetAttribute(wc_blocksort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bs_smem)) !=
@@ -524,7 +891,7 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
     src = dst;
     dst = t;
   }
-  wc_lensum_kernel<<<(unsigned)nb, CB, 0, s>>>(src, P);
+  wc_lensum_kernel<<<(unsigned)nb, CB, 0, s>>>(src, P);  // src: the fallback's result
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   wc_bscan_kernel<<<1, CB, 0, s>>>(P, nb);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -569,7 +936,7 @@ cudaError_t launch_wordcount(const uint8_t* in, uint64_t n, const WcBuffers& b, 
 // and unpredictable cost of cudaMalloc / cudaFree are not acceptable.  For
 // them the hash table and sort scratch of one word-count job live in the
 // file-scope array below, sized for NOALLOC_SLOTS table slots.  Every GPU
-// that loads this library keeps the array (about 14 MiB) until the process
+// that loads this library keeps the array (about 13 MiB) until the process
 // exits.
 #include <mutex>
 
@@ -578,9 +945,7 @@ namespace {
 constexpr uint64_t NOALLOC_SLOTS = 1ull << 17;
 constexpr uint64_t NOALLOC_TABLE_BYTES = NOALLOC_SLOTS * 24;
 constexpr uint64_t NOALLOC_STATE_BYTES = 256;
-constexpr uint64_t NOALLOC_SORT_BYTES = 256 + 2 * ((NOALLOC_SLOTS * sizeof(SortRec) + 255) & ~255ull) +
-                                        2 * ((NOALLOC_SLOTS * 8 + 255) & ~255ull) +
-                                        ((((NOALLOC_SLOTS + CB - 1) / CB) * 8 + 255) & ~255ull);
+constexpr uint64_t NOALLOC_SORT_BYTES = sortbuf_bytes(NOALLOC_SLOTS);
 constexpr uint64_t NOALLOC_SCRATCH_BYTES = NOALLOC_TABLE_BYTES + NOALLOC_STATE_BYTES + NOALLOC_SORT_BYTES;
 constexpr int NOALLOC_MAX_DEVICES = 64;
 }  // namespace

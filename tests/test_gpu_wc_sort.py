@@ -1,0 +1,57 @@
+"""GPU parity: the word-count output sort when keys tie on the radix sort's
+words (job/count and the first 8 key bytes).
+
+Distinct words that share their first 8 bytes and their count form one tie
+run after the radix passes.  Runs of up to 32 are ordered by one thread,
+runs of up to 2048 by one CTA's bitonic sort, and a longer run switches the
+batch to the comparison sort; each path must give the oracle's bytes, also
+with long keys (> 15 bytes) whose first 16 bytes agree, and inside a batch.
+The radix sort runs for record capacities of 2^20 and up (a pinned table of
+2^20 slots here); smaller ones use the comparison sort alone (slots=0)."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _text(nwords: int, prefix: bytes, reps: int, seed: int) -> bytes:
+    rng = np.random.default_rng(seed)
+    words = [prefix + b"%05d" % i for i in range(nwords)]
+    toks = [w for w in words for _ in range(reps)]
+    rng.shuffle(toks)
+    return b" ".join(toks) + b"\n"
+
+
+@pytest.mark.parametrize("slots", [0, 1 << 20])
+@pytest.mark.parametrize("nwords", [2, 5, 32, 33, 700, 2048, 2049, 5000])
+def test_tie_runs_short_prefix(mr, nwords, slots):
+    raw = _text(nwords, b"abcdefgh", 3, nwords) + b" zz yy zz"
+    assert mr.wordcount(raw, wc_slots=slots) == oracle.wordcount(raw)
+
+
+@pytest.mark.parametrize("slots", [0, 1 << 20])
+@pytest.mark.parametrize("nwords", [7, 300, 3000])
+def test_tie_runs_long_keys(mr, nwords, slots):
+    raw = _text(nwords, b"prefix_shared_by_long_keys_", 2, nwords)
+    assert mr.wordcount(raw, wc_slots=slots) == oracle.wordcount(raw)
+
+
+def test_radix_path_on_wordcount_text(mr):
+    import synth
+    text, _, _ = synth.wc_text(4 << 20, nwords=30000, seed=9)
+    assert mr.wordcount(text, wc_slots=1 << 20) == oracle.wordcount(text)
+
+
+@pytest.mark.parametrize("slots", [0, 1 << 18])
+def test_tie_runs_in_a_batch(mr, slots):
+    import torch
+    raws = [_text(40, b"qqqqqqqq", 2, 1), _text(2500, b"rrrrrrrr", 1, 2), b"a b a", _text(900, b"ssssssss_", 4, 3)]
+    c = mr.Context()
+    ids = [c.add_job(mr.WORDCOUNT, torch.frombuffer(bytearray(r), dtype=torch.uint8).cuda(), wc_slots=slots)
+           for r in raws]
+    c.run(mr.RUN_BATCHED)
+    for j, r in zip(ids, raws):
+        assert c.fetch(j) == oracle.wordcount(r)
+    c.close()
