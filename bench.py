@@ -178,7 +178,7 @@ def make_inputs(workload: str, scale: float, rank: int):
     raise ValueError(workload)
 
 
-def workload_config(workload: str, inp) -> dict:
+def workload_config(workload: str, inp, pipelined: bool = False) -> dict:
     if workload == "arrays":
         return {"workload": "rgb8 histogram %d B (%d px) + int8 linreg %d B (%d pairs)" % (
             inp["px"].nbytes, inp["px"].nbytes // 3, inp["xy"].nbytes, inp["xy"].nbytes // 2),
@@ -198,7 +198,8 @@ def workload_config(workload: str, inp) -> dict:
         return {"workload": "Bloom-filter build: %d-base windows of %d uniform ACGT bases (%d elements) into %d bits, "
                             "%d hashes" % (BF_KMER, inp["seq"].size, inp["seq"].size - BF_KMER + 1, BF_BITS, BF_HASHES),
                 "inputs": "synthetic, resident in HBM; the 37.5 MB filter is L2-resident"}
-    return {"workload": "word count %d B Zipf(1) text, 50,000-word vocabulary" % inp["text"].nbytes,
+    return {"workload": "word count %d B Zipf(1) text, 50,000-word vocabulary%s" % (
+                inp["text"].nbytes, ", pipelined map/reduce warps" if pipelined else ""),
             "inputs": "synthetic, resident in HBM; 16 MiB fits in L2 (warm)"}
 
 
@@ -273,11 +274,12 @@ def run_ours(args):
         total_bytes = d_t.numel()
 
         def step():
-            a = ctx.add_job(mr.WORDCOUNT, d_t)
+            a = ctx.add_job(mr.WORDCOUNT, d_t, wc_pipelined=int(args.pipelined))
             ctx.run()
             return [a]
-        dominant = ("wc_map_kernel", ["paper_1309_0215_gb300/csrc/k_wordcount.cu",
-                                      "paper_1309_0215_gb300/csrc/dev_wordcount.cuh"], d_t.numel())
+        dominant = ("wc_pipe_kernel" if args.pipelined else "wc_map_kernel",
+                    ["paper_1309_0215_gb300/csrc/k_wordcount.cu", "paper_1309_0215_gb300/csrc/dev_wordcount.cuh"],
+                    d_t.numel())
 
     # warm-up, plus a parity spot check of the last warm-up step
     jobs = []
@@ -369,7 +371,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8/i8 in, u64/i64 exact counts",
             "data": "synthetic (seeded generators shaped like the paper's workloads)",
-            "config": workload_config(args.workload, inp),
+            "config": workload_config(args.workload, inp, args.pipelined),
             "pct_of_hbm_peak": round(100 * value / ws / hbm_peak, 2),
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": hbm_peak,
                          "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
@@ -794,6 +796,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="batched: keep the default tile sizes")
+    ap.add_argument("--pipelined", action="store_true", help="word count: pipelined map/reduce warps")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

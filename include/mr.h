@@ -166,6 +166,11 @@ typedef struct {
   uint32_t bloom_kmer;
   uint32_t bloom_hashes;
   uint64_t bloom_bits;
+  /* word count only, plain runs: 1 = pipelined map and reduce (mapper warps
+   * hand the keys their local cache cannot hold to reducer warps through
+   * shared-memory rings, paper Sec. III-D); 0 = each warp inserts its own
+   * misses.  Results are identical. */
+  uint32_t wc_pipelined;
 } mr_job_desc;
 
 /* Create a context on cfg->device.  *out receives the handle.
@@ -218,8 +223,9 @@ mr_status mr_release(mr_ctx* ctx, uint64_t job_id);
  * released).  Admitted requests are batched continuously: whenever one of the
  * context's internal streams has finished its previous micro-batch, every
  * admitted request that is not running yet is launched on it as one
- * persistent batch (plus one merge + sort for its word-count requests;
- * k-means requests follow on the same stream).  Requests that arrive while
+ * persistent batch (plus one merge + sort for its word-count requests), and
+ * its k-means, large-key histogram and Bloom requests are spread over four
+ * more streams of that slot so they run concurrently.  Requests that arrive while
  * others run are therefore picked up as soon as a stream frees, and
  * micro-batches overlap on the device.  mr_poll and mr_fetch also drive this
  * launching.  Containers stay resident until mr_release. */

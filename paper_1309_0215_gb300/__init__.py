@@ -62,7 +62,7 @@ class _JobDesc(ctypes.Structure):
                 ("km_dims", ctypes.c_uint32), ("km_k", ctypes.c_uint32), ("km_iters", ctypes.c_uint32),
                 ("km_init", ctypes.c_void_p), ("km_precision", ctypes.c_uint32), ("wc_slots", ctypes.c_uint64),
                 ("hist_bins", ctypes.c_uint32), ("bloom_kmer", ctypes.c_uint32), ("bloom_hashes", ctypes.c_uint32),
-                ("bloom_bits", ctypes.c_uint64)]
+                ("bloom_bits", ctypes.c_uint64), ("wc_pipelined", ctypes.c_uint32)]
 
 
 _lib = None
@@ -201,7 +201,7 @@ class Context:
 
     # ------------------------------------------------------------------ jobs
     def _desc(self, kind, data, container, km_dims, km_k, km_iters, km_init, km_precision, wc_slots,
-              hist_bins=0, bloom_kmer=0, bloom_hashes=0, bloom_bits=0):
+              hist_bins=0, bloom_kmer=0, bloom_hashes=0, bloom_bits=0, wc_pipelined=0):
         addr, nbytes, on_dev, keep = _as_input(data)
         d = _JobDesc()
         d.struct_size = ctypes.sizeof(_JobDesc)
@@ -221,12 +221,13 @@ class Context:
         d.wc_slots = int(wc_slots)
         d.hist_bins = int(hist_bins)
         d.bloom_kmer, d.bloom_hashes, d.bloom_bits = int(bloom_kmer), int(bloom_hashes), int(bloom_bits)
+        d.wc_pipelined = int(wc_pipelined)
         return d, (keep, keep_init) if on_dev else None
 
     def add_job(self, kind, data, container=C_AUTO, km_dims=0, km_k=0, km_iters=0, km_init=None,
             km_precision=KM_FP32, wc_slots=0, **params) -> int:
         """params: hist_bins (large-key histogram); bloom_kmer, bloom_hashes,
-        bloom_bits (Bloom filter)."""
+        bloom_bits (Bloom filter); wc_pipelined (word count)."""
         d, keep = self._desc(kind, data, container, km_dims, km_k, km_iters, km_init, km_precision, wc_slots,
                              **params)
         jid = ctypes.c_uint64()
@@ -238,7 +239,7 @@ class Context:
     def submit(self, kind, data, container=C_AUTO, km_dims=0, km_k=0, km_iters=0, km_init=None,
             km_precision=KM_FP32, wc_slots=0, **params) -> int:
         """params: hist_bins (large-key histogram); bloom_kmer, bloom_hashes,
-        bloom_bits (Bloom filter)."""
+        bloom_bits (Bloom filter); wc_pipelined (word count)."""
         d, keep = self._desc(kind, data, container, km_dims, km_k, km_iters, km_init, km_precision, wc_slots,
                              **params)
         jid = ctypes.c_uint64()
@@ -346,9 +347,9 @@ def _one(kind, data, **kw) -> bytes:
         c.release(j)
 
 
-def wordcount(text, wc_slots: int = 0) -> bytes:
+def wordcount(text, wc_slots: int = 0, pipelined: bool = False) -> bytes:
     """Word count; returns the serialized result (see include/mr.h)."""
-    return _one(WORDCOUNT, text, wc_slots=wc_slots)
+    return _one(WORDCOUNT, text, wc_slots=wc_slots, wc_pipelined=int(pipelined))
 
 
 def hist_rgb8(px, container=C_AUTO) -> np.ndarray:

@@ -193,14 +193,15 @@ __device__ inline void global_insert(const JobDev& J, uint64_t w0, uint64_t w1, 
   atomicOr(J.state, 1u);
 }
 
-// Combine one token per active lane; all 32 lanes call this together (the
-// warp syncs inside).  A short key that sits in one of its two cache slots
-// adds 1 there.  Otherwise the first of its slots that is empty is claimed by
-// a CAS on the slot's w1: the winner fills the slot with count 1; a loser
-// whose key turns out to be the winner's (read after a warp sync) adds 1 to
-// it.  Everything else — long keys (>= 16 bytes), keys whose slots are held
-// by other keys, lost claims for other keys — goes to the global container.
-__device__ __forceinline__ void combine_round(WarpLocal& L, bool active, const Tok& t, const JobDev& J) {
+// Combine one token per active lane into the warp's cache; all 32 lanes call
+// this together (the warp syncs inside).  A short key that sits in one of its
+// two cache slots adds 1 there.  Otherwise the first of its slots that is
+// empty is claimed by a CAS on the slot's w1: the winner fills the slot with
+// count 1; a loser whose key turns out to be the winner's (read after a warp
+// sync) adds 1 to it.  Returns true for a token the cache did not take —
+// long keys (>= 16 bytes), keys whose slots are held by other keys, lost
+// claims for other keys — which the caller sends to the global container.
+__device__ __forceinline__ bool combine_local(WarpLocal& L, bool active, const Tok& t) {
   const bool is_long = (t.w1 >> 56) == 0xFF;
   const int s0 = (int)(t.h & (LT - 1)), s1 = (int)((t.h >> 16) & (LT - 1));
   bool done = !active;
@@ -234,7 +235,7 @@ __device__ __forceinline__ void combine_round(WarpLocal& L, bool active, const T
     atomicAdd(&L.cnt[want], 1u);
     done = true;
   }
-  if (!done) global_insert(J, t.w0, t.w1, t.h, 1);
+  return !done;
 }
 
 __device__ inline void local_clear(WarpLocal& L) {
@@ -256,7 +257,10 @@ __device__ inline void local_flush(WarpLocal& L, int& occ, const JobDev& J) {
 }
 
 // One warp maps and combines the tokens whose first byte lies in segment seg.
-__device__ inline void warp_segment(const JobDev& J, uint64_t seg, WarpLocal& L, int& occ) {
+// miss(lane_has_miss, token) is called by all 32 lanes after each round of
+// up to 32 tokens and disposes of the tokens the cache did not take.
+template <class Miss>
+__device__ inline void warp_segment_t(const JobDev& J, uint64_t seg, WarpLocal& L, int& occ, Miss&& miss) {
   const int lane = threadIdx.x & 31;
   const uint64_t base = seg * SEG;
   const uint8_t* __restrict__ in = J.in;
@@ -307,11 +311,20 @@ __device__ inline void warp_segment(const JobDev& J, uint64_t seg, WarpLocal& L,
     Tok t;
     if (active) t = read_token(in, n, base, L.buf, L.starts[i]);
     else t.w0 = 0, t.w1 = 0, t.h = 0;
-    combine_round(L, active, t, J);
+    const bool m = combine_local(L, active, t);
+    miss(m, t);
     __syncwarp();
   }
   // occ counts segments since the last cache merge
   if (++occ >= CACHE_EPOCH) local_flush(L, occ, J);
+}
+
+// The direct form: a token the cache did not take goes straight to the
+// global container.
+__device__ inline void warp_segment(const JobDev& J, uint64_t seg, WarpLocal& L, int& occ) {
+  warp_segment_t(J, seg, L, occ, [&](bool m, const Tok& t) {
+    if (m) global_insert(J, t.w0, t.w1, t.h, 1);
+  });
 }
 
 }  // namespace wc

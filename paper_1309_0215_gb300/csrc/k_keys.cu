@@ -43,8 +43,37 @@ __device__ __forceinline__ uint4 ldg_nc(const uint4* p) {
   return r;
 }
 
+// L2 policies: the streamed keys are marked evict-first and the counters
+// evict-last, so the counter array (64 MiB at 16M bins) stays resident in L2
+// instead of being written back and re-read as the input streams through.
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint4 ldg_stream_hint(const uint4* p, uint64_t pol) {
+  uint4 r;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "l"(p), "l"(pol));
+  return r;
+}
+
 __device__ __forceinline__ void red_add(uint32_t* p, uint32_t v) { atomicAdd(p, v); }
 __device__ __forceinline__ void red_add(unsigned long long* p, uint32_t v) { atomicAdd(p, (unsigned long long)v); }
+__device__ __forceinline__ void red_add_hint(uint32_t* p, uint32_t v, uint64_t pol) {
+  asm volatile("red.relaxed.gpu.global.add.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void red_add_hint(unsigned long long* p, uint32_t v, uint64_t pol) {
+  asm volatile("red.relaxed.gpu.global.add.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(p), "l"((unsigned long long)v),
+               "l"(pol)
+               : "memory");
+}
 
 __device__ __forceinline__ uint32_t key_at(const uint4& w, int e) {
   return e == 0 ? w.x : e == 1 ? w.y : e == 2 ? w.z : w.w;
@@ -65,10 +94,11 @@ hk_global_kernel(const uint4* __restrict__ base, uint32_t off, uint64_t n, uint3
   const uint64_t nwarps = ((uint64_t)gridDim.x * HK_THREADS) >> 5;
   bool agg = true;
   uint32_t saved = 0, win = 0, off_windows = 0;
+  const uint64_t pol_in = l2_policy_evict_first(), pol_cnt = l2_policy_evict_last();
   for (uint64_t t = warp; t < tiles; t += nwarps) {
     const uint64_t g = t * 32 + lane;
     uint4 w = make_uint4(0, 0, 0, 0);
-    if (g < groups) w = ldg_nc(base + g);
+    if (g < groups) w = ldg_stream_hint(base + g, pol_in);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int64_t idx = (int64_t)(4 * g + e) - (int64_t)off;
@@ -79,11 +109,11 @@ hk_global_kernel(const uint4* __restrict__ base, uint32_t off, uint64_t n, uint3
         const uint32_t vm = __ballot_sync(0xffffffffu, valid);
         const uint32_t m = __match_any_sync(0xffffffffu, k) & vm;
         if (valid && (__ffs(m) - 1) == lane) {
-          red_add(cnt + k, (uint32_t)__popc(m));
+          red_add_hint(cnt + k, (uint32_t)__popc(m), pol_cnt);
           saved += (uint32_t)__popc(m) - 1;
         }
       } else if (valid) {
-        red_add(cnt + k, 1u);
+        red_add_hint(cnt + k, 1u, pol_cnt);
       }
     }
     if (++win == HK_WINDOW) {

@@ -194,30 +194,32 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[32]) { tmem_ld32(taddr, v); }
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[64]) { tmem_ld64(taddr, v); }
 
-// Sortable key of a distance: its FP32 bit pattern (a negative value, which
-// only rounding can produce, counts as 0) with the low 8 mantissa bits
-// replaced by the centroid column.  For non-negative floats the bit pattern
-// is monotonic, so keys order by distance truncated to 16 mantissa bits
-// (an under-statement of less than 2^-15 of the distance), then by column.
-__device__ __forceinline__ uint32_t dist_key(float dist, uint32_t col) {
-  return ((uint32_t)max((int)__float_as_uint(dist), 0) & 0xFFFFFF00u) | col;
+// Sortable key of a distance: its FP32 bit pattern with the low 8 mantissa
+// bits replaced by the centroid column, compared as a signed integer.  For
+// non-negative floats the pattern is monotonic, so keys order by distance
+// truncated to 16 mantissa bits (an under-statement of less than 2^-15 of
+// it), then by column; a negative distance (only rounding of a point lying on
+// a centroid produces one) orders below every non-negative one, and a point
+// whose smallest key is negative is always re-checked.
+__device__ __forceinline__ int dist_key(float dist, uint32_t col) {
+  return (int)((__float_as_uint(dist) & 0xFFFFFF00u) | col);
 }
-__device__ __forceinline__ float key_dist(uint32_t key) { return __uint_as_float(key & 0xFFFFFF00u); }
+__device__ __forceinline__ float key_dist(int key) { return __uint_as_float((uint32_t)key & 0xFFFFFF00u); }
 
 // Key of a column that holds no centroid: above every finite distance's key,
 // and it decodes to +inf.
-constexpr uint32_t KEY_NONE = 0x7F8000FFu;
+constexpr int KEY_NONE = 0x7F8000FF;
 
 // Insert key into the sorted pair (t1 <= t2): three min/max.
-__device__ __forceinline__ void top2_insert(uint32_t& t1, uint32_t& t2, uint32_t key) {
-  const uint32_t h = max(t1, key);
+__device__ __forceinline__ void top2_insert(int& t1, int& t2, int key) {
+  const int h = max(t1, key);
   t1 = min(t1, key);
   t2 = min(t2, h);
 }
 
 // Smallest two of two sorted pairs.
-__device__ __forceinline__ void top2_merge(uint32_t& a1, uint32_t& a2, uint32_t b1, uint32_t b2) {
-  const uint32_t c2 = min(max(a1, b1), min(a2, b2));
+__device__ __forceinline__ void top2_merge(int& a1, int& a2, int b1, int b2) {
+  const int c2 = min(max(a1, b1), min(a2, b2));
   a1 = min(a1, b1);
   a2 = c2;
 }
@@ -228,7 +230,7 @@ __device__ __forceinline__ void top2_merge(uint32_t& a1, uint32_t& a2, uint32_t 
 // anything), so those keys are forced to KEY_NONE.
 template <bool MASK>
 __device__ __forceinline__ void top2_keys(const uint32_t (&acc)[CHUNK], uint32_t ch, float nxv, const float* cn,
-                                          uint32_t k, uint32_t (&t1)[NSET], uint32_t (&t2)[NSET], float* dbg_row) {
+                                          uint32_t k, int (&t1)[NSET], int (&t2)[NSET], float* dbg_row) {
 #pragma unroll
   for (int j = 0; j < CHUNK; j += 4) {
     const float4 c4 = *reinterpret_cast<const float4*>(cn + ch + j);
@@ -237,7 +239,7 @@ __device__ __forceinline__ void top2_keys(const uint32_t (&acc)[CHUNK], uint32_t
     for (int e = 0; e < 4; ++e) {
       const uint32_t kk = ch + (uint32_t)(j + e);
       const float dist = fmaf(-2.f, __uint_as_float(acc[j + e]), nxv) + cv[e];
-      uint32_t key = dist_key(dist, kk);
+      int key = dist_key(dist, kk);
       if (MASK) {
         if (kk >= k) key = KEY_NONE;
         else if (dbg_row) dbg_row[kk] = dist;
@@ -481,7 +483,7 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
       const float nxv = S.nx[s][r];
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.nx_free[s]);
-      uint32_t t1[NSET], t2[NSET];
+      int t1[NSET], t2[NSET];
 #pragma unroll
       for (int a = 0; a < NSET; ++a) t1[a] = t2[a] = KEY_NONE;
       const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * 256u;
@@ -497,10 +499,10 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.empty_acc[b]);
-      uint32_t w1 = t1[0], w2 = t2[0];
+      int w1 = t1[0], w2 = t2[0];
 #pragma unroll
       for (int a = 1; a < NSET; ++a) top2_merge(w1, w2, t1[a], t2[a]);
-      uint32_t lb = KEY_NONE;
+      int lb = KEY_NONE;
 #pragma unroll
       for (int a = 0; a < NSET; ++a) lb = min(lb, (t1[a] == w1 || t1[a] == w2) ? t2[a] : t1[a]);
       if (quarter != 0) {
@@ -508,27 +510,27 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
           const bool okf = mbar_wait(&S.xfree[b], (v + 1) & 1, err);
           if (!__all_sync(0xffffffffu, okf)) break;
         }
-        S.xw1[b][quarter - 1][r] = w1;
-        S.xw2[b][quarter - 1][r] = w2;
-        S.xlb[b][quarter - 1][r] = lb;
+        S.xw1[b][quarter - 1][r] = (uint32_t)w1;
+        S.xw2[b][quarter - 1][r] = (uint32_t)w2;
+        S.xlb[b][quarter - 1][r] = (uint32_t)lb;
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.xfull[b]);
         continue;
       }
-      uint32_t o1[EPI_WARPS / 4 - 1], o2[EPI_WARPS / 4 - 1], ol[EPI_WARPS / 4 - 1];
+      int o1[EPI_WARPS / 4 - 1], o2[EPI_WARPS / 4 - 1], ol[EPI_WARPS / 4 - 1];
       {
         const bool okx = mbar_wait(&S.xfull[b], v & 1, err);
         if (!__all_sync(0xffffffffu, okx)) break;
 #pragma unroll
         for (int u = 0; u < EPI_WARPS / 4 - 1; ++u) {
-          o1[u] = S.xw1[b][u][r];
-          o2[u] = S.xw2[b][u][r];
-          ol[u] = S.xlb[b][u][r];
+          o1[u] = (int)S.xw1[b][u][r];
+          o2[u] = (int)S.xw2[b][u][r];
+          ol[u] = (int)S.xlb[b][u][r];
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.xfree[b]);
       }
-      uint32_t g1 = w1, g2 = w2, g3 = lb;
+      int g1 = w1, g2 = w2, g3 = lb;
 #pragma unroll
       for (int u = 0; u < EPI_WARPS / 4 - 1; ++u) top2_merge(g1, g2, o1[u], o2[u]);
       // every key other than g1, g2 is >= g3: the warps' bounds, and the
@@ -549,7 +551,8 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
         const float e = 2.f * eps_sum * xn * cmax + eps32 * (xn + cmax) * (xn + cmax);
         // keys under-state a distance by less than 2^-15 of it (2^-14 allowed)
         const float gap = 2.f * e + 6.103515625e-05f * d1;
-        if (d2 - d1 > fmaxf(1e-3f * d1, gap)) assign[p] = (int)(g1 & 0xFFu);
+        if (g1 < 0) flag = true;  // a negative smallest distance: re-check
+        else if (d2 - d1 > fmaxf(1e-3f * d1, gap)) assign[p] = g1 & 0xFF;
         else if (d3 - d1 > gap) pair = true;  // only the top two can be the exact minimum
         else flag = true;
       }
@@ -558,7 +561,9 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(npairs, (uint32_t)__popc(pm));
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (pair) pairs[base + __popc(pm & ((1u << lane) - 1))] = make_uint2(p, (g1 & 0xFFu) | ((g2 & 0xFFu) << 16));
+        if (pair)
+          pairs[base + __popc(pm & ((1u << lane) - 1))] =
+              make_uint2(p, ((uint32_t)g1 & 0xFFu) | (((uint32_t)g2 & 0xFFu) << 16));
       }
       const unsigned fm = __ballot_sync(0xffffffffu, flag);
       if (fm) {

@@ -68,6 +68,154 @@ __global__ void __launch_bounds__(MAP_THREADS, 5) wc_map_kernel(JobDev J) {
   wc::local_flush(L, occ, J);
 }
 
+
+// ------------------------------------------------- pipelined map / reduce
+// Sec. III-D pipelines the map and reduce phases on the hyper-threads of a
+// core: map threads combine into a bounded local table and hand what it
+// cannot hold to reduce threads, which insert into the global container.
+// Here a CTA pairs PIPE_PAIRS mapper warps with as many reducer warps.  A
+// mapper tokenizes, hashes and combines into its hot-key cache, and pushes
+// the tokens the cache did not take into its own ring in shared memory
+// (single producer, single consumer); its reducer warp inserts them into the
+// global container, so the global-memory latency is spent by the reducers
+// while the mappers go on tokenizing.  A mapper never waits for room: a
+// round whose misses do not fit the ring sends them straight to the global
+// container.  A reducer polls with __nanosleep and a bounded count; one that
+// gives up marks its ring dead and its mapper drains the rest itself.
+constexpr int PIPE_PAIRS = 4;
+constexpr int PIPE_THREADS = 2 * PIPE_PAIRS * 32;
+constexpr int RING = 256;
+constexpr long long PIPE_SPIN_LIMIT = 1ll << 22;  // polls of ~128 ns: about half a second
+
+struct RingRec {
+  unsigned long long w0, w1;
+  uint32_t h, pad;
+};
+struct Ring {
+  RingRec rec[RING];
+  unsigned int head;  // records consumed (written by the reducer)
+  unsigned int tail;  // records published (written by the mapper)
+  unsigned int done;  // the mapper has published its last record
+  unsigned int dead;  // the reducer gave up and no longer touches the ring
+};
+struct PipeSmem {
+  WarpLocal local[PIPE_PAIRS];
+  Ring ring[PIPE_PAIRS];
+};
+
+__device__ __forceinline__ unsigned vload(const unsigned int* p) { return *reinterpret_cast<const volatile unsigned int*>(p); }
+__device__ __forceinline__ void vstore(unsigned int* p, unsigned v) { *reinterpret_cast<volatile unsigned int*>(p) = v; }
+
+__global__ void __launch_bounds__(PIPE_THREADS, 4) wc_pipe_kernel(JobDev J) {
+  extern __shared__ __align__(16) unsigned char pipe_smem[];
+  PipeSmem& S = *reinterpret_cast<PipeSmem*>(pipe_smem);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x < PIPE_PAIRS) {
+    Ring& R = S.ring[threadIdx.x];
+    R.head = R.tail = R.done = R.dead = 0;
+  }
+  __syncthreads();
+  if (warp < PIPE_PAIRS) {
+    // ------------------------------------------------------------ mapper
+    WarpLocal& L = S.local[warp];
+    Ring& R = S.ring[warp];
+    wc::local_clear(L);
+    int occ = 0;
+    const unsigned below = (1u << lane) - 1u;
+    auto push = [&](bool m, const wc::Tok& t) {
+      const unsigned mm = __ballot_sync(0xffffffffu, m);
+      if (!mm) return;
+      const unsigned cnt = (unsigned)__popc(mm);
+      const unsigned tail = vload(&R.tail);  // this warp is the only writer
+      const unsigned head = vload(&R.head);
+      if (!vload(&R.dead) && tail - head + cnt <= (unsigned)RING) {
+        if (m) {
+          RingRec& rr = R.rec[(tail + (unsigned)__popc(mm & below)) % RING];
+          rr.w0 = t.w0;
+          rr.w1 = t.w1;
+          rr.h = t.h;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          __threadfence_block();
+          vstore(&R.tail, tail + cnt);
+        }
+      } else if (m) {
+        wc::global_insert(J, t.w0, t.w1, t.h, 1);
+      }
+    };
+    const uint64_t nseg = (J.n + wc::SEG - 1) / wc::SEG;
+    const uint64_t stride = (uint64_t)gridDim.x * PIPE_PAIRS;
+    for (uint64_t seg = (uint64_t)blockIdx.x * PIPE_PAIRS + warp; seg < nseg; seg += stride)
+      wc::warp_segment_t(J, seg, L, occ, push);
+    wc::local_flush(L, occ, J);
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      vstore(&R.done, 1u);
+    }
+    // wait for the reducer to drain the ring (or to give up)
+    bool drained = false, dead = false;
+    for (long long it = 0; it < PIPE_SPIN_LIMIT; ++it) {
+      dead = vload(&R.dead) != 0;
+      drained = vload(&R.head) == vload(&R.tail);
+      if (dead || drained) break;
+      __nanosleep(128);
+    }
+    dead = __shfl_sync(0xffffffffu, dead, 0);
+    drained = __shfl_sync(0xffffffffu, drained, 0);
+    if (dead && !drained) {
+      __threadfence_block();
+      for (unsigned q = vload(&R.head) + lane; q < vload(&R.tail); q += 32) {
+        const RingRec r = R.rec[q % RING];
+        wc::global_insert(J, r.w0, r.w1, r.h, 1);
+      }
+    } else if (!dead && !drained && lane == 0) {
+      atomicOr(J.state, 2u);  // the reducer neither finished nor gave up in time
+    }
+  } else {
+    // ----------------------------------------------------------- reducer
+    Ring& R = S.ring[warp - PIPE_PAIRS];
+    unsigned head = 0;
+    long long idle = 0;
+    for (;;) {
+      unsigned tail = 0, dn = 0;
+      if (lane == 0) {
+        dn = vload(&R.done);  // read before tail: with done set, the tail read is final
+        __threadfence_block();
+        tail = vload(&R.tail);
+      }
+      tail = __shfl_sync(0xffffffffu, tail, 0);
+      dn = __shfl_sync(0xffffffffu, dn, 0);
+      if (tail != head) {
+        __threadfence_block();
+        const unsigned n = (tail - head) < 32u ? (tail - head) : 32u;
+        if ((unsigned)lane < n) {
+          const RingRec r = R.rec[(head + (unsigned)lane) % RING];
+          wc::global_insert(J, r.w0, r.w1, r.h, 1);
+        }
+        __syncwarp();
+        head += n;
+        if (lane == 0) {
+          __threadfence_block();
+          vstore(&R.head, head);
+        }
+        idle = 0;
+        continue;
+      }
+      if (dn) break;
+      if (++idle > PIPE_SPIN_LIMIT) {
+        if (lane == 0) {
+          __threadfence_block();
+          vstore(&R.dead, 1u);
+        }
+        break;
+      }
+      __nanosleep(128);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ sort
 struct SortRec {
   unsigned long long key1;  // job << 40 | (2^40 - 1 - count): ascending = job, then count descending
@@ -904,13 +1052,24 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
 }
 
 cudaError_t launch_wordcount(const uint8_t* in, uint64_t n, const WcBuffers& b, const DevInfo& di, cudaStream_t s,
-                             uint64_t* nk) {
+                             uint64_t* nk, bool pipelined) {
   cudaError_t e;
   // table (keys then counts) and state words start at zero
   if ((e = cudaMemsetAsync(b.key, 0, wc_table_bytes(b.cap), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(b.state, 0, wc_state_bytes(), s)) != cudaSuccess) return e;
   const JobDev J = wc_job_dev(in, n, b, 0);
-  if (n > 0) {
+  if (n > 0 && pipelined) {
+    const int smem = (int)sizeof(PipeSmem);
+    if ((e = cudaFuncSetAttribute(wc_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+      return e;
+    const uint64_t nseg = (n + wc::SEG - 1) / wc::SEG;
+    uint64_t grid = (nseg + PIPE_PAIRS - 1) / PIPE_PAIRS;
+    const uint64_t gmax = 4ull * di.sms;
+    if (grid > gmax) grid = gmax;
+    wc_pipe_kernel<<<(unsigned)grid, PIPE_THREADS, smem, s>>>(J);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ++*nk;
+  } else if (n > 0) {
     const int smem = wc_map_smem_bytes();
     if ((e = cudaFuncSetAttribute(wc_map_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
       return e;

@@ -93,8 +93,13 @@ struct mr_ctx {
     void* sort = nullptr;
     uint64_t sort_bytes = 0;
     void* cursor = nullptr;
+    // plain-only requests (k-means, large-key histogram, Bloom) of a
+    // micro-batch run on these streams, round robin, so they overlap
+    static constexpr int AUX = 4;
+    cudaStream_t aux[AUX] = {};
+    cudaEvent_t aux_done[AUX] = {};
   };
-  static constexpr int SERVE_SLOTS = 3;
+  static constexpr int SERVE_SLOTS = 4;
   Slot slots[SERVE_SLOTS];
   std::vector<Job*> serve_pending;  // admitted, waiting for a free slot
   cudaEvent_t serve_ready = nullptr;
@@ -195,6 +200,7 @@ mr_status validate(const mr_ctx* c, const mr_job_desc* d) {
       if (d->input_bytes >= (1ull << 40) - 1) return MR_EINVAL;
       if (d->wc_slots && (d->wc_slots & (d->wc_slots - 1))) return MR_EINVAL;
       if (d->wc_slots && (d->wc_slots < 1024 || d->wc_slots > (1ull << 32))) return MR_EINVAL;
+      if (d->wc_pipelined > 1) return MR_EINVAL;
       break;
     case MR_HIST_RGB8:
       if (d->input_bytes % 3) return MR_EINVAL;
@@ -395,7 +401,7 @@ mr_status enqueue_plain_on(mr_ctx* c, Job* j, cudaStream_t st) {
       ++c->launches;
       break;
     case MR_WORDCOUNT:
-      MR_CUDA_TRY(launch_wordcount(j->in, n, j->wc, c->di, st, &c->launches));
+      MR_CUDA_TRY(launch_wordcount(j->in, n, j->wc, c->di, st, &c->launches, j->desc.wc_pipelined != 0));
       break;
     case MR_HIST_U32:
       MR_CUDA_TRY(launch_hist_keys(reinterpret_cast<const uint32_t*>(j->in), n / 4, j->desc.hist_bins,
@@ -619,6 +625,10 @@ mr_status serve_pump(mr_ctx* c) {
     if (!sl.s) {
       MR_CUDA_TRY(cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking));
       MR_CUDA_TRY(cudaEventCreateWithFlags(&sl.busy, cudaEventDisableTiming));
+      for (int a = 0; a < mr_ctx::Slot::AUX; ++a) {
+        MR_CUDA_TRY(cudaStreamCreateWithFlags(&sl.aux[a], cudaStreamNonBlocking));
+        MR_CUDA_TRY(cudaEventCreateWithFlags(&sl.aux_done[a], cudaEventDisableTiming));
+      }
     }
     if (!sl.used) {
       slot = &sl;
@@ -676,11 +686,20 @@ mr_status serve_pump(mr_ctx* c) {
       j->state = JOB_ENQUEUED;
     }
   }
+  int na = 0;
   for (Job* j : jobs)
     if (plain_only(j->desc.kind)) {
-      mr_status st = enqueue_plain_on(c, j, slot->s);
+      cudaStream_t as = slot->aux[na % mr_ctx::Slot::AUX];
+      if (na < mr_ctx::Slot::AUX) MR_CUDA_TRY(cudaStreamWaitEvent(as, c->serve_ready, 0));
+      mr_status st = enqueue_plain_on(c, j, as);
       if (st) return st;
+      ++na;
     }
+  // the slot is free again once its batch and its other requests are done
+  for (int a = 0; a < na && a < mr_ctx::Slot::AUX; ++a) {
+    MR_CUDA_TRY(cudaEventRecord(slot->aux_done[a], slot->aux[a]));
+    MR_CUDA_TRY(cudaStreamWaitEvent(slot->s, slot->aux_done[a], 0));
+  }
   MR_CUDA_TRY(cudaEventRecord(slot->busy, slot->s));
   slot->used = true;
   return MR_OK;
@@ -731,6 +750,7 @@ mr_status wait_job(mr_ctx* c, Job* j) {
     uint32_t st[4];
     MR_CUDA_TRY(cudaMemcpyAsync(st, j->wc.state, 16, cudaMemcpyDeviceToHost, c->stream));
     MR_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (st[0] & 2u) return MR_ETIMEOUT;  // a pipelined map pass whose reducer stalled
     if (!(st[0] & 1u)) return MR_OK;
     if (!j->wc_auto) return MR_EOVERFLOW;
     // the job's containers move: a captured batch graph that names them is stale
@@ -745,7 +765,8 @@ mr_status wait_job(mr_ctx* c, Job* j) {
     j->slab = nullptr;
     mr_status s = alloc_wc(c, j, cap);
     if (s) return s;
-    MR_CUDA_TRY(launch_wordcount(j->in, j->desc.input_bytes, j->wc, c->di, c->stream, &c->launches));
+    MR_CUDA_TRY(launch_wordcount(j->in, j->desc.input_bytes, j->wc, c->di, c->stream, &c->launches,
+                                 j->desc.wc_pipelined != 0));
     MR_CUDA_TRY(cudaEventRecord(j->done, c->stream));
     MR_CUDA_TRY(cudaEventSynchronize(j->done));
   }
@@ -882,8 +903,11 @@ void mr_destroy(mr_ctx* c) {
   cudaStreamSynchronize(c->stream);
   for (auto& kv : c->jobs) free_job(c, kv.second);
   c->jobs.clear();
-  for (auto& sl : c->slots)
+  for (auto& sl : c->slots) {
     if (sl.s) cudaStreamSynchronize(sl.s);
+    for (auto a : sl.aux)
+      if (a) cudaStreamSynchronize(a);
+  }
   drop_batch_graph(c);
   for (auto& sl : c->slots) {
     dev_free(c, sl.desc, sl.desc_bytes);
@@ -899,6 +923,10 @@ void mr_destroy(mr_ctx* c) {
   for (auto& sl : c->slots) {
     if (sl.busy) cudaEventDestroy(sl.busy);
     if (sl.s) cudaStreamDestroy(sl.s);
+    for (int a = 0; a < mr_ctx::Slot::AUX; ++a) {
+      if (sl.aux_done[a]) cudaEventDestroy(sl.aux_done[a]);
+      if (sl.aux[a]) cudaStreamDestroy(sl.aux[a]);
+    }
   }
   if (c->serve_ready) cudaEventDestroy(c->serve_ready);
   if (c->own_stream) cudaStreamDestroy(c->stream);

@@ -77,8 +77,10 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
                                         uint64_t* nk);
 // Zero the table and state, run map+combine, compaction, sort and gather.
 // *nk is incremented by the number of kernels launched.
+// pipelined: the map pass runs as mapper warps handing cache misses to
+// reducer warps through shared-memory rings (wc_pipe_kernel).
 cudaError_t launch_wordcount(const uint8_t* in, uint64_t n, const WcBuffers& b, const DevInfo& di, cudaStream_t s,
-                             uint64_t* nk);
+                             uint64_t* nk, bool pipelined = false);
 
 // ---------------------------------------------------------------- k-means
 struct KmBuffers {
