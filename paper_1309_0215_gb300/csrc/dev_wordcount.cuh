@@ -49,6 +49,7 @@ struct WarpLocal {
   uint32_t h[LT];
   uint32_t cnt[LT];
   uint8_t buf[BUF];
+  uint32_t wsb[BUF / 32 + 2];  // whitespace bitmap of buf: bit j of word q = byte 32q + j
   uint16_t starts[SEG / 2];
 };
 static_assert(sizeof(WarpLocal) % 16 == 0, "WarpLocal must keep 16-byte alignment");
@@ -68,9 +69,17 @@ struct JobDev {
 
 __device__ __forceinline__ bool is_ws(uint32_t c) { return c == 32u || (c - 9u) < 5u; }
 
-// 0xFF in every byte of u that is ASCII whitespace
+// 0x80 in every byte of u that is ASCII whitespace (0x20, or 0x09..0x0D),
+// else 0: exact per byte, with no carry between bytes.  Space: the byte of
+// u ^ 0x20202020 is zero iff ((b & 0x7F) + 0x7F) | b has its top bit clear.
+// 9..13: with h = b & 0x7F, h + 0x77 reaches 0x80 iff h >= 9 and h + 0x72
+// iff h >= 14; bytes >= 0x80 are excluded by their own top bit.
 __device__ __forceinline__ uint32_t ws_bytes(uint32_t u) {
-  return __vcmpeq4(u, 0x20202020u) | __vcmpltu4(__vsub4(u, 0x09090909u), 0x05050505u);
+  const uint32_t x = u ^ 0x20202020u;
+  const uint32_t sp = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x);
+  const uint32_t h = u & 0x7F7F7F7Fu;
+  const uint32_t rg = (h + 0x77777777u) & ~(h + 0x72727272u) & ~u;
+  return (sp | rg) & 0x80808080u;
 }
 // compress a 0xFF-per-byte mask to 4 bits (byte i -> bit i)
 __device__ __forceinline__ uint32_t byte_bits(uint32_t m) { return ((m & 0x80808080u) * 0x00204081u) >> 28; }
@@ -84,12 +93,17 @@ __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
   return k;
 }
 
+// 32-bit multiply-xorshift mix of the four 32-bit words of a short key
+// (the key is compared exactly; the hash only spreads slots).
 __device__ __forceinline__ uint32_t hash_short(uint64_t w0, uint64_t w1) {
-  uint64_t h = w0 * 0x9E3779B97F4A7C15ull ^ ((w1 * 0xC2B2AE3D27D4EB4Full) >> 7) ^ w1;
-  h ^= h >> 29;
-  h *= 0xBF58476D1CE4E5B9ull;
-  h ^= h >> 32;
-  return (uint32_t)h;
+  uint32_t h = (uint32_t)w0 * 0x9E3779B1u;
+  h ^= __funnelshift_l((uint32_t)(w0 >> 32) * 0x85EBCA77u, (uint32_t)(w0 >> 32) * 0x85EBCA77u, 13);
+  h ^= __funnelshift_l((uint32_t)w1 * 0xC2B2AE3Du, (uint32_t)w1 * 0xC2B2AE3Du, 7);
+  h ^= (uint32_t)(w1 >> 32) * 0x27D4EB2Fu;
+  h ^= h >> 15;
+  h *= 0x2C1B3C6Du;
+  h ^= h >> 12;
+  return h;
 }
 
 struct Tok {
@@ -107,19 +121,20 @@ __device__ inline bool long_equal(const uint8_t* __restrict__ in, uint64_t a, ui
 
 // The token starting at segment-relative byte r (its first 16 bytes are
 // always inside the staged buffer; bytes past the input end were staged as
-// spaces).
+// spaces).  Its length comes from the segment's whitespace bitmap.
 __device__ __forceinline__ Tok read_token(const uint8_t* __restrict__ in, uint64_t n, uint64_t base,
-                                          const uint8_t* buf, uint32_t r) {
-  const uint32_t* wb = reinterpret_cast<const uint32_t*>(buf);
-  const uint32_t a = r >> 2, sh = (r & 3) * 8;
-  const uint32_t x0 = wb[a], x1 = wb[a + 1], x2 = wb[a + 2], x3 = wb[a + 3], x4 = wb[a + 4];
-  const uint32_t u0 = __funnelshift_r(x0, x1, sh), u1 = __funnelshift_r(x1, x2, sh);
-  const uint32_t u2 = __funnelshift_r(x2, x3, sh), u3 = __funnelshift_r(x3, x4, sh);
-  const uint32_t m = byte_bits(ws_bytes(u0)) | (byte_bits(ws_bytes(u1)) << 4) | (byte_bits(ws_bytes(u2)) << 8) |
-                     (byte_bits(ws_bytes(u3)) << 12);
+                                          const WarpLocal& W, uint32_t r) {
+  const uint32_t* wb = reinterpret_cast<const uint32_t*>(W.buf);
+  // m bit i: byte r + 1 + i is whitespace
+  const uint32_t p = r + 1, wi = p >> 5, bs = p & 31;
+  const uint32_t m = __funnelshift_r(W.wsb[wi], W.wsb[wi + 1], bs);
   Tok t;
-  if (m) {
-    const uint32_t L = __ffs(m) - 1;  // 1..15 (byte 0 is a token byte)
+  if (m & 0x7FFFu) {
+    const uint32_t a = r >> 2, sh = (r & 3) * 8;
+    const uint32_t x0 = wb[a], x1 = wb[a + 1], x2 = wb[a + 2], x3 = wb[a + 3], x4 = wb[a + 4];
+    const uint32_t u0 = __funnelshift_r(x0, x1, sh), u1 = __funnelshift_r(x1, x2, sh);
+    const uint32_t u2 = __funnelshift_r(x2, x3, sh), u3 = __funnelshift_r(x3, x4, sh);
+    const uint32_t L = __ffs(m);  // 1..15 (byte 0 is a token byte)
     uint64_t k0 = (uint64_t)u0 | ((uint64_t)u1 << 32);
     uint64_t k1 = (uint64_t)u2 | ((uint64_t)u3 << 32);
     if (L < 8) {
@@ -138,7 +153,7 @@ __device__ __forceinline__ Tok read_token(const uint8_t* __restrict__ in, uint64
   uint64_t h = 0xcbf29ce484222325ull, len = 0;
   for (uint64_t i = off; i < n; ++i) {
     const uint32_t rel = (uint32_t)(i - base);
-    const uint32_t c = (i - base) < (uint64_t)BUF ? buf[rel] : in[i];
+    const uint32_t c = (i - base) < (uint64_t)BUF ? W.buf[rel] : in[i];
     if (is_ws(c)) break;
     h = (h ^ c) * 0x100000001b3ull;
     ++len;
@@ -284,6 +299,23 @@ __device__ inline void warp_segment_t(const JobDev& J, uint64_t seg, WarpLocal& 
                  (byte_bits(ws_bytes(mine.z)) << 8) | (byte_bits(ws_bytes(mine.w)) << 12);
   const uint64_t lb = base + 16 * (uint64_t)lane;
   if (lb + 16 > n) wsm |= lb >= n ? 0xFFFFu : (0xFFFFu & ~((1u << (uint32_t)(n - lb)) - 1u));
+  {
+    // whitespace bitmap of the staged bytes (segment, then the halo, which
+    // lanes 0..3 classify; staged bytes past the input end are spaces)
+    uint32_t wsh = 0;
+    if (lane < HALO / 16) {
+      const uint4 hv = reinterpret_cast<const uint4*>(L.buf)[32 + lane];
+      wsh = byte_bits(ws_bytes(hv.x)) | (byte_bits(ws_bytes(hv.y)) << 4) | (byte_bits(ws_bytes(hv.z)) << 8) |
+            (byte_bits(ws_bytes(hv.w)) << 12);
+      const uint64_t hb = base + SEG + 16 * (uint64_t)lane;
+      if (hb + 16 > n) wsh |= hb >= n ? 0xFFFFu : (0xFFFFu & ~((1u << (uint32_t)(n - hb)) - 1u));
+    }
+    const uint32_t up = __shfl_down_sync(0xffffffffu, wsm, 1);
+    const uint32_t uh = __shfl_down_sync(0xffffffffu, wsh, 1);
+    if ((lane & 1) == 0) L.wsb[lane >> 1] = (wsm & 0xFFFFu) | (up << 16);
+    if (lane < HALO / 16 && (lane & 1) == 0) L.wsb[SEG / 32 + (lane >> 1)] = (wsh & 0xFFFFu) | (uh << 16);
+    if (lane == 0) L.wsb[BUF / 32] = 0xFFFFFFFFu;  // past the halo
+  }
   uint32_t prev = __shfl_up_sync(0xffffffffu, wsm >> 15, 1) & 1u;
   if (lane == 0) prev = (base == 0) ? 1u : (uint32_t)is_ws(in[base - 1]);
   const uint32_t start = ~wsm & ((wsm << 1) | prev) & 0xFFFFu;
@@ -309,7 +341,7 @@ __device__ inline void warp_segment_t(const JobDev& J, uint64_t seg, WarpLocal& 
     const int i = r0 + lane;
     const bool active = i < total;
     Tok t;
-    if (active) t = read_token(in, n, base, L.buf, L.starts[i]);
+    if (active) t = read_token(in, n, base, L, L.starts[i]);
     else t.w0 = 0, t.w1 = 0, t.h = 0;
     const bool m = combine_local(L, active, t);
     miss(m, t);
