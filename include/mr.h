@@ -273,7 +273,7 @@ mr_status mr_simdh_hash(const uint8_t* text, uint64_t text_bytes, const uint32_t
  * not let other components allocate, or a latency-critical loop that cannot
  * accept the implicit synchronisation and unpredictable cost of cudaMalloc
  * and cudaFree.  The job's hash table and sort scratch live in a fixed
- * device array inside the library (about 13 MiB, sized for
+ * device array inside the library (about 19 MiB, sized for
  * MR_NOALLOC_WC_SLOTS table slots) that every GPU loading the library holds
  * until the process exits.
  *

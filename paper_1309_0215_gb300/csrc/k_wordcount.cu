@@ -254,6 +254,7 @@ struct Post {
   uint32_t* csum;             // [chunks][256] chunk sums, then chunk offsets
   uint32_t* plan;             // [NPASS] bit 0 active, bit 1 source buffer; [NPASS] final buffer
   uint2* runs;                // tie runs longer than FIX_THREAD: {first, length}
+  struct KeyRec* kr[2];       // compact keys for the comparison sort of small record sets
 };
 
 __device__ __forceinline__ uint64_t bswap64(uint64_t v) {
@@ -368,17 +369,46 @@ __global__ void __launch_bounds__(CB) wc_compact_kernel(const JobDev* jobs, JobD
 constexpr int SB = 2048;
 constexpr int SB_THREADS = 1024;
 
-__global__ void __launch_bounds__(SB_THREADS) wc_blocksort_kernel(const JobDev* jobs, JobDev single, Post P) {
+// Orders for the comparison sort.  FullCmp: the output order on whole
+// records (a pad sorts last).  KeyCmp: (key1, s0, index) on compact keys; the
+// index only makes the order total, records that tie on (key1, s0) are put in
+// the output order afterwards by the tie fix-up.
+struct KeyRec {
+  unsigned long long k1, k0;  // key1, s0 of the record
+  uint32_t idx, pad;          // record index
+};
+struct FullCmp {
+  const JobDev* jobs;
+  JobDev single;
+  const unsigned long long* src;
+  __device__ bool less(const SortRec& a, const SortRec& b) const {
+    const bool a_pad = a.idx == 0xffffffffu, b_pad = b.idx == 0xffffffffu;
+    if (a_pad || b_pad) return b_pad && !a_pad;
+    return rec_less(a, b, jobs, single, src);
+  }
+  __device__ static SortRec pad() { return SortRec{~0ull, ~0ull, ~0ull, 0xffffffffu, 0xffffffffu}; }
+};
+struct KeyCmp {
+  __device__ bool less(const KeyRec& a, const KeyRec& b) const {
+    if (a.k1 != b.k1) return a.k1 < b.k1;
+    if (a.k0 != b.k0) return a.k0 < b.k0;
+    return a.idx < b.idx;
+  }
+  __device__ static KeyRec pad() { return KeyRec{~0ull, ~0ull, 0xffffffffu, 0u}; }
+};
+
+// Block sort: SB items per CTA, bitonic network in shared memory.  Runs when
+// the fallback flag P.glob[1] equals `when`.
+template <class R, class C>
+__global__ void __launch_bounds__(SB_THREADS) blocksort_kernel(R* data, const unsigned long long* glob, C cmp,
+                                                               unsigned long long when) {
   extern __shared__ __align__(16) unsigned char bs_raw[];
-  SortRec* sh = reinterpret_cast<SortRec*>(bs_raw);
-  if (!P.glob[1]) return;  // the radix sort succeeded
-  const uint64_t m = *P.glob;
+  R* sh = reinterpret_cast<R*>(bs_raw);
+  if (glob[1] != when) return;
+  const uint64_t m = glob[0];
   const uint64_t b0 = (uint64_t)blockIdx.x * SB;
   if (b0 >= m) return;
-  for (int i = threadIdx.x; i < SB; i += blockDim.x) {
-    if (b0 + i < m) sh[i] = P.r0[b0 + i];
-    else sh[i] = SortRec{~0ull, ~0ull, ~0ull, 0xffffffffu, 0xffffffffu};
-  }
+  for (int i = threadIdx.x; i < SB; i += blockDim.x) sh[i] = b0 + i < m ? data[b0 + i] : C::pad();
   __syncthreads();
   for (int k = 2; k <= SB; k <<= 1) {
     for (int jj = k >> 1; jj > 0; jj >>= 1) {
@@ -386,12 +416,8 @@ __global__ void __launch_bounds__(SB_THREADS) wc_blocksort_kernel(const JobDev* 
         const int lo = 2 * jj * (t / jj) + (t % jj);
         const int hi = lo + jj;
         const bool up = (lo & k) == 0;
-        const SortRec a = sh[lo], b = sh[hi];
-        const bool a_pad = a.idx == 0xffffffffu, b_pad = b.idx == 0xffffffffu;
-        bool b_lt_a;
-        if (a_pad || b_pad) b_lt_a = a_pad && !b_pad;
-        else b_lt_a = rec_less(b, a, jobs, single, P.src);
-        if (b_lt_a == up) {
+        const R a = sh[lo], b = sh[hi];
+        if (cmp.less(b, a) == up) {
           sh[lo] = b;
           sh[hi] = a;
         }
@@ -400,22 +426,22 @@ __global__ void __launch_bounds__(SB_THREADS) wc_blocksort_kernel(const JobDev* 
     }
   }
   for (int i = threadIdx.x; i < SB; i += blockDim.x)
-    if (b0 + i < m) P.r0[b0 + i] = sh[i];
+    if (b0 + i < m) data[b0 + i] = sh[i];
 }
 
 // Number of A records among the first kk outputs of merge(A[0..la), B[0..lb)),
 // found by the whole warp: each step probes 32 evenly spaced positions at once
 // (the "A[i] < B[kk-1-i]" predicate is true on a prefix), shrinking the range
 // about 33-fold, so a search over L records costs ~log_33(L) dependent loads.
-__device__ uint64_t corank_warp(const SortRec* A, uint64_t la, const SortRec* B, uint64_t lb, uint64_t kk,
-                                const JobDev* jobs, const JobDev& single, const unsigned long long* src) {
+template <class R, class C>
+__device__ uint64_t corank_warp(const R* A, uint64_t la, const R* B, uint64_t lb, uint64_t kk, const C& cmp) {
   const int lane = threadIdx.x & 31;
   uint64_t lo = kk > lb ? kk - lb : 0;
   uint64_t hi = kk < la ? kk : la;
   while (lo < hi) {
     const uint64_t span = hi - lo;
     const uint64_t m = lo + (span * (uint64_t)(lane + 1)) / 33;
-    const bool pr = rec_less(A[m], B[kk - 1 - m], jobs, single, src);
+    const bool pr = cmp.less(A[m], B[kk - 1 - m]);
     const unsigned bal = __ballot_sync(0xffffffffu, pr);
     const int nt = __popc(bal);
     const uint64_t mt = __shfl_sync(0xffffffffu, m, nt > 0 ? nt - 1 : 0);
@@ -428,29 +454,30 @@ __device__ uint64_t corank_warp(const SortRec* A, uint64_t la, const SortRec* B,
   return lo;
 }
 
-// One merge pass: runs of L sorted records are merged pairwise.  A CTA owns
+// One merge pass: runs of L sorted items are merged pairwise.  A CTA owns
 // MTILE consecutive outputs: two warps find where its range starts and ends
 // in the two runs, the CTA stages both input windows in shared memory, and
-// each thread merges MI outputs from there.
+// each thread merges MI outputs from there.  Runs when P.glob[1] == when.
 constexpr int MT = 256;
 constexpr int MI = 8;
 constexpr int MTILE = MT * MI;
 
-__global__ void __launch_bounds__(MT) wc_merge_kernel(const SortRec* __restrict__ src, SortRec* __restrict__ dst,
-                                                      uint64_t L, const JobDev* jobs, JobDev single, Post P) {
+template <class R, class C>
+__global__ void __launch_bounds__(MT) merge_kernel(const R* __restrict__ src, R* __restrict__ dst, uint64_t L,
+                                                   const unsigned long long* glob, C cmp, unsigned long long when) {
   extern __shared__ __align__(16) unsigned char mg_raw[];
-  SortRec* ms = reinterpret_cast<SortRec*>(mg_raw);
+  R* ms = reinterpret_cast<R*>(mg_raw);
   __shared__ uint64_t cr[2];
-  if (!P.glob[1]) return;  // the radix sort succeeded
-  const uint64_t m = *P.glob;
+  if (glob[1] != when) return;
+  const uint64_t m = glob[0];
   const uint64_t o0 = (uint64_t)blockIdx.x * MTILE;
   if (o0 >= m) return;
   const uint64_t a0 = (o0 / (2 * L)) * (2 * L);  // MTILE divides 2L: a tile never spans two pairs
   const uint64_t la = (m - a0) < L ? (m - a0) : L;
   const uint64_t b0 = a0 + L;
   const uint64_t lb = b0 < m ? ((m - b0) < L ? (m - b0) : L) : 0;
-  const SortRec* A = src + a0;
-  const SortRec* B = src + b0;
+  const R* A = src + a0;
+  const R* B = src + b0;
   const uint64_t kk0 = o0 - a0;
   const uint64_t kk1 = (kk0 + MTILE) < la + lb ? kk0 + MTILE : la + lb;
   if (lb == 0) {  // a lone run: copy
@@ -460,7 +487,7 @@ __global__ void __launch_bounds__(MT) wc_merge_kernel(const SortRec* __restrict_
   const int warp = threadIdx.x >> 5;
   if (warp < 2) {
     const uint64_t kk = warp == 0 ? kk0 : kk1;
-    const uint64_t c = corank_warp(A, la, B, lb, kk, jobs, single, P.src);
+    const uint64_t c = corank_warp(A, la, B, lb, kk, cmp);
     if ((threadIdx.x & 31) == 0) cr[warp] = c;
   }
   __syncthreads();
@@ -470,15 +497,15 @@ __global__ void __launch_bounds__(MT) wc_merge_kernel(const SortRec* __restrict_
   for (uint32_t t = threadIdx.x; t < na; t += MT) ms[t] = A[i0 + t];
   for (uint32_t t = threadIdx.x; t < nb; t += MT) ms[na + t] = B[kk0 - i0 + t];
   __syncthreads();
-  const SortRec* sa = ms;
-  const SortRec* sb = ms + na;
+  const R* sa = ms;
+  const R* sb = ms + na;
   const uint32_t r0 = threadIdx.x * MI;
   const uint32_t tot = na + nb;
   if (r0 >= tot) return;
   uint32_t lo = r0 > nb ? r0 - nb : 0, hi = r0 < na ? r0 : na;
   while (lo < hi) {
     const uint32_t mid = (lo + hi) >> 1;
-    if (rec_less(sa[mid], sb[r0 - 1 - mid], jobs, single, P.src)) lo = mid + 1;
+    if (cmp.less(sa[mid], sb[r0 - 1 - mid])) lo = mid + 1;
     else hi = mid;
   }
   uint32_t i = lo, j = r0 - lo;
@@ -486,7 +513,7 @@ __global__ void __launch_bounds__(MT) wc_merge_kernel(const SortRec* __restrict_
     bool takeA;
     if (j >= nb) takeA = true;
     else if (i >= na) takeA = false;
-    else takeA = rec_less(sa[i], sb[j], jobs, single, P.src);
+    else takeA = cmp.less(sa[i], sb[j]);
     dst[o0 + r0 + t] = takeA ? sa[i++] : sb[j++];
   }
 }
@@ -811,6 +838,23 @@ __global__ void __launch_bounds__(RT) wc_rscatter_kernel(Post P, int p) {
   }
 }
 
+// Compact keys of the compacted records (small record sets).
+__global__ void __launch_bounds__(256) wc_kkeys_kernel(Post P) {
+  const uint64_t m = *P.glob;
+  const uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
+  if (i >= m) return;
+  const SortRec r = P.r0[i];
+  P.kr[0][i] = KeyRec{r.key1, r.s0, (uint32_t)i, 0u};
+}
+
+// Records in key order.
+__global__ void __launch_bounds__(256) wc_kgather_kernel(Post P, const KeyRec* sorted) {
+  const uint64_t m = *P.glob;
+  const uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
+  if (i >= m) return;
+  P.r1[i] = P.r0[sorted[i].idx];
+}
+
 // Records in radix order.
 __global__ void __launch_bounds__(256) wc_rgather_kernel(Post P) {
   const uint64_t m = *P.glob;
@@ -902,9 +946,10 @@ constexpr uint64_t rchunks(uint64_t R) { return (rtiles(R) + RCHUNK - 1) / RCHUN
 constexpr uint64_t max_runs(uint64_t R) { return R / (FIX_THREAD + 1) + 1; }
 constexpr uint64_t sortbuf_bytes(uint64_t R) {
   return 256 + 2 * ca256(R * sizeof(SortRec)) + 2 * ca256(R * 8) + ca256(((R + CB - 1) / CB) * 8) +
+         ca256(max_runs(R) * 8) +
          (R >= RADIX_MIN_RECORDS ? 4 * ca256(R * 8) + 2 * ca256(R * 4) + ca256(rtiles(R) * 256 * 4) +
-                                       ca256(rchunks(R) * 256 * 4) + 256 + ca256(max_runs(R) * 8)
-                                 : 0);
+                                       ca256(rchunks(R) * 256 * 4) + 256
+                                 : 2 * ca256(R * sizeof(KeyRec)));
 }
 
 Post carve_post(uint8_t* p, uint64_t R) {
@@ -921,7 +966,15 @@ Post carve_post(uint8_t* p, uint64_t R) {
   p += a256(R * 8);
   P.bsum = reinterpret_cast<unsigned long long*>(p);
   p += a256(((R + CB - 1) / CB) * 8);
-  if (R < RADIX_MIN_RECORDS) return P;  // comparison sort only: no radix buffers
+  P.runs = reinterpret_cast<uint2*>(p);
+  p += a256(max_runs(R) * 8);
+  if (R < RADIX_MIN_RECORDS) {  // comparison sort of compact keys
+    for (int q = 0; q < 2; ++q) {
+      P.kr[q] = reinterpret_cast<KeyRec*>(p);
+      p += a256(R * sizeof(KeyRec));
+    }
+    return P;
+  }
   for (int q = 0; q < 2; ++q) {
     P.kh[q] = reinterpret_cast<unsigned long long*>(p);
     p += a256(R * 8);
@@ -937,8 +990,6 @@ Post carve_post(uint8_t* p, uint64_t R) {
   P.csum = reinterpret_cast<uint32_t*>(p);
   p += a256(rchunks(R) * 256 * 4);
   P.plan = reinterpret_cast<uint32_t*>(p);
-  p += 256;
-  P.runs = reinterpret_cast<uint2*>(p);
   return P;
 }
 
@@ -986,53 +1037,80 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
   if ((e = cudaMemsetAsync(P.glob, 0, 64, s)) != cudaSuccess) return e;
   wc_compact_kernel<<<(unsigned)nblocks, CB, 0, s>>>(jobs, single, njobs, P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  ++*nk;
   const uint64_t nb = (R + CB - 1) / CB;
+  const unsigned g256 = (unsigned)((R + 255) / 256);
   if (R < RADIX_MIN_RECORDS) {
-    // small record sets: the comparison sort below does all the work
-    if ((e = cudaMemsetAsync(P.glob + 1, 1, 1, s)) != cudaSuccess) return e;
-  } else {
-  // radix sort by (key1, s0), then the tie runs
-  wc_rkeys_kernel<<<(unsigned)nb, CB, 0, s>>>(P);
-  wc_rplan_kernel<<<1, 1, 0, s>>>(P);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  *nk += 3;
-  for (int p = 0; p < NPASS; ++p) {
-    wc_rhist_kernel<<<(unsigned)rtiles(R), RT, 0, s>>>(P, p);
-    wc_rscan1_kernel<<<(unsigned)rchunks(R), RT, 0, s>>>(P, p);
-    wc_rscan2_kernel<<<1, RT, 0, s>>>(P, p);
-    wc_rscatter_kernel<<<(unsigned)rtiles(R), RT, 0, s>>>(P, p);
+    // small record sets: comparison sort of (key1, s0, index) keys
+    const int kbs = SB * (int)sizeof(KeyRec), kmg = MTILE * (int)sizeof(KeyRec);
+    if ((e = cudaFuncSetAttribute(blocksort_kernel<KeyRec, KeyCmp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kbs)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(merge_kernel<KeyRec, KeyCmp>, cudaFuncAttributeMaxDynamicSharedMemorySize, kmg)) !=
+            cudaSuccess)
+      return e;
+    wc_kkeys_kernel<<<g256, 256, 0, s>>>(P);
+    blocksort_kernel<KeyRec, KeyCmp><<<(unsigned)((R + SB - 1) / SB), SB_THREADS, kbs, s>>>(P.kr[0], P.glob,
+                                                                                          KeyCmp{}, 0ull);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    *nk += 4;
+    *nk += 2;
+    KeyRec* ks = P.kr[0];
+    KeyRec* kd = P.kr[1];
+    for (uint64_t L = SB; L < R; L *= 2) {
+      merge_kernel<KeyRec, KeyCmp><<<(unsigned)((R + MTILE - 1) / MTILE), MT, kmg, s>>>(ks, kd, L, P.glob,
+                                                                                       KeyCmp{}, 0ull);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      ++*nk;
+      KeyRec* t = ks;
+      ks = kd;
+      kd = t;
+    }
+    wc_kgather_kernel<<<g256, 256, 0, s>>>(P, ks);
+  } else {
+    // large record sets: radix sort by (key1, s0)
+    wc_rkeys_kernel<<<(unsigned)nb, CB, 0, s>>>(P);
+    wc_rplan_kernel<<<1, 1, 0, s>>>(P);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    *nk += 2;
+    for (int p = 0; p < NPASS; ++p) {
+      wc_rhist_kernel<<<(unsigned)rtiles(R), RT, 0, s>>>(P, p);
+      wc_rscan1_kernel<<<(unsigned)rchunks(R), RT, 0, s>>>(P, p);
+      wc_rscan2_kernel<<<1, RT, 0, s>>>(P, p);
+      wc_rscatter_kernel<<<(unsigned)rtiles(R), RT, 0, s>>>(P, p);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      *nk += 4;
+    }
+    wc_rgather_kernel<<<g256, 256, 0, s>>>(P);
   }
-  wc_rgather_kernel<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(P);
-  wc_rfix_kernel<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(P, jobs, single, max_runs(R));
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // ties on (key1, s0): the full order
+  wc_rfix_kernel<<<g256, 256, 0, s>>>(P, jobs, single, max_runs(R));
   {
     const int fx_smem = SB * (int)sizeof(SortRec);
     if ((e = cudaFuncSetAttribute(wc_rfix_long_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem)) !=
         cudaSuccess)
       return e;
     wc_rfix_long_kernel<<<64, SB_THREADS, fx_smem, s>>>(P, jobs, single, max_runs(R));
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   *nk += 3;
-  }
-  // fallback (only if a tie run was too long): comparison sort of P.r0
+  // fallback (only if a tie run was too long): comparison sort of whole records
+  const FullCmp fc{jobs, single, P.src};
   const int bs_smem = SB * (int)sizeof(SortRec);
   const int mg_smem = MTILE * (int)sizeof(SortRec);
-  if ((e = cudaFuncSetAttribute(wc_blocksort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bs_smem)) !=
-      cudaSuccess)
+  if ((e = cudaFuncSetAttribute(blocksort_kernel<SortRec, FullCmp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                bs_smem)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(merge_kernel<SortRec, FullCmp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                mg_smem)) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(wc_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mg_smem)) !=
-      cudaSuccess)
-    return e;
-  wc_blocksort_kernel<<<(unsigned)((R + SB - 1) / SB), SB_THREADS, bs_smem, s>>>(jobs, single, P);
+  blocksort_kernel<SortRec, FullCmp><<<(unsigned)((R + SB - 1) / SB), SB_THREADS, bs_smem, s>>>(P.r0, P.glob, fc,
+                                                                                                1ull);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  *nk += 2;
+  ++*nk;
   SortRec* src = P.r0;
   SortRec* dst = P.r1;
   for (uint64_t L = SB; L < R; L *= 2) {
-    wc_merge_kernel<<<(unsigned)((R + MTILE - 1) / MTILE), MT, mg_smem, s>>>(src, dst, L, jobs, single, P);
+    merge_kernel<SortRec, FullCmp><<<(unsigned)((R + MTILE - 1) / MTILE), MT, mg_smem, s>>>(src, dst, L, P.glob, fc,
+                                                                                           1ull);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ++*nk;
     SortRec* t = src;
@@ -1045,7 +1123,7 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   wc_bounds_kernel<<<(unsigned)nb, CB, 0, s>>>(src, jobs, single, P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  wc_gather_kernel<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(src, jobs, single, P);
+  wc_gather_kernel<<<g256, 256, 0, s>>>(src, jobs, single, P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   *nk += 4;
   return cudaSuccess;
@@ -1095,7 +1173,7 @@ cudaError_t launch_wordcount(const uint8_t* in, uint64_t n, const WcBuffers& b, 
 // and unpredictable cost of cudaMalloc / cudaFree are not acceptable.  For
 // them the hash table and sort scratch of one word-count job live in the
 // file-scope array below, sized for NOALLOC_SLOTS table slots.  Every GPU
-// that loads this library keeps the array (about 13 MiB) until the process
+// that loads this library keeps the array (about 19 MiB) until the process
 // exits.
 #include <mutex>
 
