@@ -27,28 +27,28 @@ __device__ __forceinline__ void red_shared_add(uint32_t addr, uint32_t v) {
 
 // One 32-bit word = 4 bytes; byte b belongs to channel slot (j0 + b) % 3 of
 // the rotation cb[]; cb[q] already holds the lane's column base for that
-// channel.  Counter address = column base + value * 32 lanes * 4 bytes.
-template <int J0>
+// channel.  Counter address = column base + value * COLS columns * 4 bytes.
+template <int J0, int COLS = HIST_COLS>
 __device__ __forceinline__ void hist_word(uint32_t w, const uint32_t (&cb)[3]) {
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
     uint32_t v = (w >> (8 * b)) & 0xFFu;
-    red_shared_add(cb[(J0 + b) % 3] + v * (HIST_COLS * 4), 1u);
+    red_shared_add(cb[(J0 + b) % 3] + v * (COLS * 4), 1u);
   }
 }
 
 // 16 bytes loaded by one lane for row k of a chunk.  Byte j of row k is at
 // chunk offset k*512 + lane*16 + j; its channel is (rot0 + 2k + j) % 3 where
 // rot0 = (alignment offset + lane) % 3 (512 = 2 mod 3, 16 = 1 mod 3).
-template <int K>
+template <int K, int COLS = HIST_COLS>
 __device__ __forceinline__ void hist_vec(uint4 a, const uint32_t (&cb)[3]) {
   constexpr int R = (2 * K) % 3;
   // cbk[q] = column base of channel (rot0 + R + q) % 3
   uint32_t cbk[3] = {cb[R % 3], cb[(R + 1) % 3], cb[(R + 2) % 3]};
-  hist_word<0>(a.x, cbk);
-  hist_word<4>(a.y, cbk);
-  hist_word<8>(a.z, cbk);
-  hist_word<12>(a.w, cbk);
+  hist_word<0, COLS>(a.x, cbk);
+  hist_word<4, COLS>(a.y, cbk);
+  hist_word<8, COLS>(a.z, cbk);
+  hist_word<12, COLS>(a.w, cbk);
 }
 
 struct Sums5 { long long v[5]; };

@@ -23,15 +23,20 @@
 namespace mrgb {
 namespace {
 
-// 16 warps per CTA, two CTAs per SM: 32 warps per SM keep the word-count
-// tiles' latency-bound loops fed; the histogram tiles share one 96 KiB
-// lane-column table per CTA (64 registers per thread at this shape).
-constexpr int BT = 512;
+// 8 warps per CTA, five CTAs per SM: 40 warps per SM keep the word-count
+// tiles' latency-bound loops fed (the plain map kernel's shape).  For that
+// the histogram tiles use a narrower local table than the plain kernel:
+// 8 lane columns (lane % 8) per bin, 24 KiB, so lanes 8 apart share a
+// column (a few more shared-memory atomic collisions on equal bins).
+constexpr int BT = 256;
 constexpr int BWARPS = BT / 32;
-constexpr int B_SMEM_HIST = arr::HIST_WORDS * 4;
+constexpr int BCTAS = 5;                 // CTAs per SM
+constexpr int BH_COLS = 8;               // histogram lane columns per bin
+constexpr int BH_WORDS = arr::HIST_BINS * BH_COLS;
+constexpr int B_SMEM_HIST = BH_WORDS * 4;
 constexpr int B_SMEM_WC = BWARPS * (int)sizeof(wc::WarpLocal);
 constexpr int B_SMEM = B_SMEM_HIST > B_SMEM_WC ? B_SMEM_HIST : B_SMEM_WC;
-static_assert(2 * B_SMEM + 4096 <= 232448, "two batch CTAs must fit one SM's shared memory");
+static_assert(BCTAS * (B_SMEM + 1024) + 4096 <= 232448, "BCTAS batch CTAs must fit one SM's shared memory");
 
 __device__ __forceinline__ uint32_t find_job(const BatchJob* jobs, uint32_t njobs, uint64_t t) {
   uint32_t lo = 0, hi = njobs - 1;
@@ -67,40 +72,35 @@ __device__ __forceinline__ void block_reduce_add5(long long (&acc)[5], long long
 // histogram tile [t0, t1) of a job (t0 a multiple of 1536), local arrays
 __device__ void hist_tile_smem(const BatchJob& J, uint64_t t0, uint64_t t1, uint32_t sbase) {
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t lb = sbase + lane * 4;
+  const uint32_t lb = sbase + (lane % BH_COLS) * 4;
   const uint8_t* in = J.in;
   uint64_t scalar0 = t0;
   if (((uintptr_t)in & 15) == 0) {
     const uint32_t rot0 = lane % 3;  // tiles and chunks start at multiples of 3
     uint32_t cb[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) cb[q] = lb + ((rot0 + q) % 3) * (256u * arr::HIST_COLS * 4);
+    for (int q = 0; q < 3; ++q) cb[q] = lb + ((rot0 + q) % 3) * (256u * BH_COLS * 4);
     const uint64_t c0 = t0 / arr::CHUNK, c1 = c0 + (t1 - t0) / arr::CHUNK;
     const uint4* vin = reinterpret_cast<const uint4*>(in);
     uint64_t c = c0 + warp;
-    for (; c + BWARPS < c1; c += 2 * BWARPS) {
+    for (; c + BWARPS < c1; c += BWARPS) {
       const uint4* p = vin + c * arr::CHUNK_VEC + lane;
-      const uint4* q = vin + (c + BWARPS) * arr::CHUNK_VEC + lane;
       uint4 a0 = arr::ldg_stream(p), a1 = arr::ldg_stream(p + 32), a2 = arr::ldg_stream(p + 64);
-      uint4 b0 = arr::ldg_stream(q), b1 = arr::ldg_stream(q + 32), b2 = arr::ldg_stream(q + 64);
-      arr::hist_vec<0>(a0, cb);
-      arr::hist_vec<1>(a1, cb);
-      arr::hist_vec<2>(a2, cb);
-      arr::hist_vec<0>(b0, cb);
-      arr::hist_vec<1>(b1, cb);
-      arr::hist_vec<2>(b2, cb);
+      arr::hist_vec<0, BH_COLS>(a0, cb);
+      arr::hist_vec<1, BH_COLS>(a1, cb);
+      arr::hist_vec<2, BH_COLS>(a2, cb);
     }
     if (c < c1) {
       const uint4* p = vin + c * arr::CHUNK_VEC + lane;
       uint4 a0 = arr::ldg_stream(p), a1 = arr::ldg_stream(p + 32), a2 = arr::ldg_stream(p + 64);
-      arr::hist_vec<0>(a0, cb);
-      arr::hist_vec<1>(a1, cb);
-      arr::hist_vec<2>(a2, cb);
+      arr::hist_vec<0, BH_COLS>(a0, cb);
+      arr::hist_vec<1, BH_COLS>(a1, cb);
+      arr::hist_vec<2, BH_COLS>(a2, cb);
     }
     scalar0 = c1 * arr::CHUNK;
   }
   for (uint64_t i = scalar0 + threadIdx.x; i < t1; i += BT)
-    arr::red_shared_add(lb + (uint32_t)(i % 3) * (256u * arr::HIST_COLS * 4) + (uint32_t)in[i] * (arr::HIST_COLS * 4),
+    arr::red_shared_add(lb + (uint32_t)(i % 3) * (256u * BH_COLS * 4) + (uint32_t)in[i] * (BH_COLS * 4),
                         1u);
 }
 
@@ -138,19 +138,19 @@ __device__ void linreg_tile(const BatchJob& J, uint64_t t0, uint64_t t1, long lo
   }
 }
 
-__global__ void __launch_bounds__(BT, 2)
+__global__ void __launch_bounds__(BT, BCTAS)
 batch_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs, uint64_t total_tiles, unsigned long long* cursor,
              uint64_t arr_tile, uint64_t wc_tile) {
   extern __shared__ __align__(16) unsigned char bsm[];
   __shared__ unsigned long long s_tile[2];
   __shared__ uint32_t s_job[2];
   __shared__ long long part[BWARPS][5];
+  __shared__ wc::JobDev s_jd;  // the current word-count job
   uint32_t* hs = reinterpret_cast<uint32_t*>(bsm);
   wc::WarpLocal& L = reinterpret_cast<wc::WarpLocal*>(bsm)[threadIdx.x >> 5];
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(hs);
   int64_t cur = -1;
   uint32_t kind = 0, cont = 0;
-  long long acc[5] = {0, 0, 0, 0, 0};
   int occ = 0;
 
   auto flush = [&](const BatchJob& J) {
@@ -160,12 +160,10 @@ batch_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs, uint64_t total_t
       for (int bin = threadIdx.x; bin < arr::HIST_BINS; bin += BT) {
         unsigned long long s = 0;
 #pragma unroll 8
-        for (int l = 0; l < arr::HIST_COLS; ++l) s += hs[bin * arr::HIST_COLS + ((l + bin) & 31)];
+        for (int l = 0; l < BH_COLS; ++l) s += hs[bin * BH_COLS + ((l + bin) & (BH_COLS - 1))];
         if (s) atomicAdd(bins + bin, s);
       }
       __syncthreads();
-    } else if (kind == MR_LINREG_I8) {
-      block_reduce_add5(acc, static_cast<long long*>(J.out), part);
     } else if (kind == MR_WORDCOUNT) {
       wc::local_flush(L, occ, J.wc);
       __syncthreads();
@@ -175,11 +173,13 @@ batch_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs, uint64_t total_t
     kind = J.kind;
     cont = J.container;
     if (kind == MR_HIST_RGB8 && cont != MR_C_GLOBAL_ARRAY) {
-      for (int i = threadIdx.x; i < arr::HIST_WORDS; i += BT) hs[i] = 0;
+      for (int i = threadIdx.x; i < BH_WORDS; i += BT) hs[i] = 0;
       __syncthreads();
     } else if (kind == MR_WORDCOUNT) {
+      if (threadIdx.x == 0) s_jd = J.wc;
       wc::local_clear(L);
       occ = 0;
+      __syncthreads();
     }
   };
 
@@ -206,7 +206,10 @@ batch_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs, uint64_t total_t
       uint64_t s1 = s0 + wc_tile / wc::SEG;
       const uint64_t nseg = (J.n + wc::SEG - 1) / wc::SEG;
       if (s1 > nseg) s1 = nseg;
-      for (uint64_t sg = s0 + (threadIdx.x >> 5); sg < s1; sg += BWARPS) wc::warp_segment(J.wc, sg, L, occ);
+      // the job's descriptor from shared memory (copied at the job switch):
+      // through a reference to global memory every use in the hot loop would
+      // be a global reload, and a register copy would not fit
+      for (uint64_t sg = s0 + (threadIdx.x >> 5); sg < s1; sg += BWARPS) wc::warp_segment(s_jd, sg, L, occ);
     } else {
       const uint64_t t0 = local * arr_tile;
       const uint64_t t1 = (t0 + arr_tile) < J.n ? t0 + arr_tile : J.n;
@@ -214,7 +217,10 @@ batch_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs, uint64_t total_t
         if (cont == MR_C_GLOBAL_ARRAY) hist_tile_global(J, t0, t1);
         else hist_tile_smem(J, t0, t1, sbase);
       } else {
+        // sums reduced per tile: no registers stay reserved across tiles
+        long long acc[5] = {0, 0, 0, 0, 0};
         linreg_tile(J, t0, t1, acc);
+        block_reduce_add5(acc, static_cast<long long*>(J.out), part);
       }
     }
   }
@@ -257,7 +263,7 @@ cudaError_t launch_batch(const BatchJob* jobs_dev, uint32_t njobs, uint64_t tota
   batch_init_kernel<<<di.sms * 4, 256, 0, s>>>(jobs_dev, njobs);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(cursor, 0, 8, s)) != cudaSuccess) return e;
-  uint64_t grid = 2ull * di.sms;
+  uint64_t grid = (uint64_t)BCTAS * di.sms;
   if (grid > total_tiles) grid = total_tiles ? total_tiles : 1;
   batch_kernel<<<(unsigned)grid, BT, B_SMEM, s>>>(jobs_dev, njobs, total_tiles, cursor, arr_tile, wc_tile);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
