@@ -65,7 +65,8 @@ typedef enum {
    * exact tie) then centroid = mean of assigned points (an empty cluster keeps
    * its centroid).  The key is the cluster id (array container of K*D sums +
    * K counts).  Assignments equal FP64 argmin; centroids are FP64 means
-   * rounded to FP32.  Output layout (packed): float centroids[K][D], int32
+   * rounded to FP32; points must be finite (other values give unspecified
+   * results).  Output layout (packed): float centroids[K][D], int32
    * assign[n], zero padding to an 8-byte boundary, uint64 stats[4] =
    * {points re-checked in FP32, points re-checked in FP64, iterations,
    * device waits that timed out (0 unless mr_fetch returned MR_ETIMEOUT)}. */
@@ -245,6 +246,16 @@ uint64_t mr_bytes_in_use(const mr_ctx* ctx);
  * created with MR_FLAG_TIMING).  Blocks until the job is done.
  * Errors: MR_ENOJOB, MR_ENOTREADY (not run yet), MR_EINVAL (no timing). */
 mr_status mr_job_elapsed_ms(mr_ctx* ctx, uint64_t job_id, float* ms);
+
+/* Device time of a finished job's main kernel: *ms = the summed duration of
+ * its launches, *launches = how many were timed.  The main kernel is the
+ * distance (assignment) pass of each k-means iteration, the map pass of a
+ * word count, and the one counting kernel of the other kinds; each launch is
+ * bracketed by CUDA events on the stream it runs on (up to 64 launches per
+ * job are timed).  Needs MR_FLAG_TIMING; blocks until the job is done.
+ * Errors: MR_ENOJOB, MR_ENOTREADY (not run yet), MR_EINVAL (no timing, or a
+ * job of the batched launch, whose kernels are shared by all its jobs). */
+mr_status mr_job_kernel_ms(mr_ctx* ctx, uint64_t job_id, float* ms, uint32_t* launches);
 
 /* Number of CUDA kernels this context has launched so far (all jobs). */
 uint64_t mr_kernel_launches(const mr_ctx* ctx);

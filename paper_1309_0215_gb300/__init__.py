@@ -27,7 +27,8 @@ KM_FP32, KM_BF16_TC, KM_BF16X1_TC = range(3)
 
 # every entry point declared in include/mr.h
 EXPORTS = ("mr_create", "mr_destroy", "mr_add_job", "mr_run", "mr_fetch", "mr_result_device", "mr_release",
-           "mr_submit", "mr_poll", "mr_sync", "mr_bytes_in_use", "mr_job_elapsed_ms", "mr_kernel_launches",
+           "mr_submit", "mr_poll", "mr_sync", "mr_bytes_in_use", "mr_job_elapsed_ms", "mr_job_kernel_ms",
+           "mr_kernel_launches",
            "mr_status_str", "mr_last_error", "mr_wordcount_noalloc", "mr_rerun", "mr_get_tuning", "mr_simdh_hash")
 SIMDH_PADDING, SIMDH_STREAM, SIMDH_WIDE = range(3)
 NOALLOC_WC_SLOTS = 131072
@@ -111,6 +112,8 @@ def load():
         lib.mr_bytes_in_use.restype = u64
         lib.mr_job_elapsed_ms.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_float)]
         lib.mr_job_elapsed_ms.restype = st
+        lib.mr_job_kernel_ms.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint32)]
+        lib.mr_job_kernel_ms.restype = st
         lib.mr_kernel_launches.argtypes = [vp]
         lib.mr_kernel_launches.restype = u64
         lib.mr_rerun.argtypes = [vp]
@@ -296,6 +299,12 @@ class Context:
         ms = ctypes.c_float()
         _check(self._lib.mr_job_elapsed_ms(self._h, job, ctypes.byref(ms)), "mr_job_elapsed_ms")
         return float(ms.value)
+
+    def kernel_ms(self, job: int):
+        """(summed ms, launches) of the job's main-kernel launches (timing contexts, plain jobs)."""
+        ms, n = ctypes.c_float(), ctypes.c_uint32()
+        _check(self._lib.mr_job_kernel_ms(self._h, job, ctypes.byref(ms), ctypes.byref(n)), "mr_job_kernel_ms")
+        return float(ms.value), int(n.value)
 
     @property
     def kernel_launches(self) -> int:

@@ -255,7 +255,8 @@ bloom_kernel(const uint8_t* __restrict__ seq, uint64_t n, uint32_t L, uint64_t m
 int hk_smem_max_bins(const DevInfo& di) { return di.smem_optin / 4 - 1; }
 
 cudaError_t launch_hist_keys(const uint32_t* keys, uint64_t n, uint32_t nbins, bool smem, void* counters,
-                             bool wide, unsigned long long* out, const DevInfo& di, cudaStream_t s, uint64_t* nk) {
+                             bool wide, unsigned long long* out, const DevInfo& di, cudaStream_t s, uint64_t* nk,
+                             KTimer* kt) {
   const uint64_t nb = (uint64_t)nbins + 1;
   cudaError_t e = cudaMemsetAsync(wide ? (void*)out : counters, 0, nb * (wide ? 8 : 4), s);
   if (e != cudaSuccess) return e;
@@ -264,6 +265,7 @@ cudaError_t launch_hist_keys(const uint32_t* keys, uint64_t n, uint32_t nbins, b
   const uint32_t off = (uint32_t)((addr & 15) / 4);
   const uint64_t groups = (n + off + 3) / 4;
   if (n) {
+    if ((e = kt_begin(kt, s)) != cudaSuccess) return e;
     if (smem) {
       const int bytes = (int)(nb * 4);
       const int per_sm = bytes <= 48 * 1024 ? 2 : 1;
@@ -291,7 +293,7 @@ cudaError_t launch_hist_keys(const uint32_t* keys, uint64_t n, uint32_t nbins, b
       else
         hk_global_kernel<uint32_t><<<(int)g, HK_THREADS, 0, s>>>(base, off, n, nbins, static_cast<uint32_t*>(counters));
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = kt_end(kt, s)) != cudaSuccess) return e;
     ++*nk;
   }
   if (!wide) {
@@ -305,15 +307,16 @@ cudaError_t launch_hist_keys(const uint32_t* keys, uint64_t n, uint32_t nbins, b
 }
 
 cudaError_t launch_bloom(const uint8_t* seq, uint64_t n, uint32_t L, uint64_t m, uint32_t h, uint32_t* bits,
-                         const DevInfo& di, cudaStream_t s, uint64_t* nk) {
+                         const DevInfo& di, cudaStream_t s, uint64_t* nk, KTimer* kt) {
   const uint64_t words = (m + 31) / 32;
   cudaError_t e = cudaMemsetAsync(bits, 0, words * 4, s);
   if (e != cudaSuccess || n < L) return e;
   const uint64_t rm = ~0ull / m, rm1 = ~0ull / (m - 1);
   const uint64_t tiles = (n - L + 1 + BF_TILE - 1) / BF_TILE;
   uint64_t g = tiles < (uint64_t)di.sms * 8 ? tiles : (uint64_t)di.sms * 8;
+  if ((e = kt_begin(kt, s)) != cudaSuccess) return e;
   bloom_kernel<<<(int)g, BF_THREADS, 0, s>>>(seq, n, L, m, rm, rm1, h, bits);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaGetLastError()) != cudaSuccess || (e = kt_end(kt, s)) != cudaSuccess) return e;
   ++*nk;
   return cudaSuccess;
 }

@@ -618,6 +618,21 @@ __global__ void __launch_bounds__(SCAT_THREADS) km_scatter_kernel(const int32_t*
 // per run.  Eight rows are in flight per warp.
 constexpr int SUM_RUN = 64;
 constexpr int SUM_UNROLL = 8;
+// Round-half-even of a finite FP32 value to int64 with FP32 adds and integer
+// operations only: the FP32 -> int64 conversion instruction issues on the FP64
+// pipe, which is narrow on this GPU and became the sum kernel's limit.
+//   |v| < 2^22:  v + 1.5*2^23 rounds (ties to even) to an integer whose value
+//                minus 1.5*2^23 sits in the low bits of the sum's encoding;
+//   |v| >= 2^23: v is an integer, its significand shifted by e - 150;
+//   in between:  one fraction bit, rounded to even by hand.
+__device__ __forceinline__ long long rint_i64(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const uint32_t e = (b >> 23) & 0xFFu;
+  if (e < 149u) return (long long)(int32_t)(__float_as_uint(__fadd_rn(v, 12582912.f)) - 0x4B400000u);
+  const uint64_t m = (b & 0x7FFFFFu) | 0x800000u;
+  const uint64_t q = e == 149u ? (m >> 1) + (m & (m >> 1) & 1u) : m << ((e - 150u) & 63u);
+  return (b >> 31) ? -(long long)q : (long long)q;
+}
 __device__ __forceinline__ void sum_flush(long long* sums, uint32_t cur, uint32_t d, uint32_t dj0, uint32_t dj1,
                                           long long a0, long long a1) {
   if (dj0 < d && a0) atomicAdd(reinterpret_cast<unsigned long long*>(sums + (uint64_t)cur * d + dj0), (unsigned long long)a0);
@@ -670,12 +685,107 @@ __global__ void __launch_bounds__(256) km_sum_kernel(const float* __restrict__ x
           ++cur;
           cend = ends[cur];
         }
-        a0 += __float2ll_rn(v[u][0] * scale);
-        a1 += __float2ll_rn(v[u][1] * scale);
+        a0 += rint_i64(v[u][0] * scale);
+        a1 += rint_i64(v[u][1] * scale);
       }
     }
     sum_flush(sums, cur, d, dj0, dj1, a0, a1);
   }
+}
+
+// Update step with local arrays (Sec. III-E: the array container, privatised
+// per thread block).  A CTA's [k][d] fixed-point sums and [k] counts live in
+// shared memory; one CTA per SM streams a contiguous range of points in input
+// order (coalesced rows: no sort and no gather) and adds each coordinate with a
+// shared-memory atomic.  It then stores its sums as one partial (plain stores)
+// and adds its counts to the global counts; km_reduce_finalize_kernel adds the
+// partials.  Integer sums make the result independent of the order.
+constexpr int LS_THREADS = 1024;
+constexpr int LS_ROWS = 4;  // rows in flight per warp
+constexpr uint32_t LS_MAX_CTAS = 160;  // partials held in scratch
+constexpr uint64_t LS_SMEM_MAX = 200 * 1024;
+inline bool local_sums_fit(uint64_t d, uint64_t k) { return k * d * 8 + k * 4 <= LS_SMEM_MAX; }
+__global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_kernel(const float* __restrict__ x, uint32_t n,
+                                                                     uint32_t d, uint32_t k,
+                                                                     const int32_t* __restrict__ assign,
+                                                                     const int* shift, long long* __restrict__ part,
+                                                                     unsigned long long* counts) {
+  extern __shared__ __align__(16) unsigned char ls_sm[];
+  const uint64_t kd = (uint64_t)k * d;
+  unsigned long long* S = reinterpret_cast<unsigned long long*>(ls_sm);
+  unsigned int* C = reinterpret_cast<unsigned int*>(S + kd);
+  for (uint64_t i = threadIdx.x; i < kd; i += LS_THREADS) S[i] = 0;
+  for (uint32_t i = threadIdx.x; i < k; i += LS_THREADS) C[i] = 0;
+  __syncthreads();
+  const float scale = ldexpf(1.f, *shift);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t per = (((uint64_t)n + gridDim.x - 1) / gridDim.x + 31) & ~31ull;
+  const uint64_t p0 = (uint64_t)blockIdx.x * per;
+  const uint64_t p1 = p0 + per < (uint64_t)n ? p0 + per : (uint64_t)n;
+  for (uint64_t r0 = p0 + 32 * (uint64_t)warp; r0 < p1; r0 += 32 * (LS_THREADS / 32)) {
+    // 32 consecutive rows per warp step; lane j holds row r0 + j's cluster
+    const uint32_t nr = (uint32_t)(p1 - r0 < 32 ? p1 - r0 : 32);
+    const uint32_t cl = (uint32_t)lane < nr ? cluster_of(assign, r0 + lane, k) : 0u;
+    if ((uint32_t)lane < nr) atomicAdd(&C[cl], 1u);
+    for (uint32_t j0 = 0; j0 < d; j0 += 64) {
+      const uint32_t dj0 = j0 + lane, dj1 = j0 + 32 + lane;
+      for (uint32_t rr = 0; rr < nr; rr += LS_ROWS) {
+        float v[LS_ROWS][2];
+        uint32_t c[LS_ROWS];
+#pragma unroll
+        for (int u = 0; u < LS_ROWS; ++u) {
+          const uint32_t j = rr + u;
+          c[u] = __shfl_sync(0xffffffffu, cl, (int)(j & 31));
+          const bool ok = j < nr;
+          const float* row = x + (r0 + j) * d;
+          v[u][0] = (ok && dj0 < d) ? row[dj0] : 0.f;
+          v[u][1] = (ok && dj1 < d) ? row[dj1] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < LS_ROWS; ++u) {
+          if (rr + u >= nr) break;  // warp-uniform
+          const uint64_t b = (uint64_t)c[u] * d;
+          if (dj0 < d) atomicAdd(&S[b + dj0], (unsigned long long)rint_i64(v[u][0] * scale));
+          if (dj1 < d) atomicAdd(&S[b + dj1], (unsigned long long)rint_i64(v[u][1] * scale));
+        }
+      }
+    }
+  }
+  __syncthreads();
+  long long* P = part + (uint64_t)blockIdx.x * kd;
+  for (uint64_t i = threadIdx.x; i < kd; i += LS_THREADS) P[i] = (long long)S[i];
+  for (uint32_t i = threadIdx.x; i < k; i += LS_THREADS)
+    if (C[i]) atomicAdd(counts + i, (unsigned long long)C[i]);
+}
+
+// Sum of the g partials of each element (warp w of a CTA adds partials w,
+// w + 8, ... of 32 consecutive elements), then the centroid as in
+// km_finalize_kernel.
+constexpr int RF_THREADS = 256;
+__global__ void __launch_bounds__(RF_THREADS) km_reduce_finalize_kernel(const long long* __restrict__ part,
+                                                                        uint32_t g, float* c, uint32_t k, uint32_t d,
+                                                                        const unsigned long long* counts,
+                                                                        const int* shift, unsigned int* cmax_bits) {
+  __shared__ long long red[RF_THREADS / 32][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint64_t kd = (uint64_t)k * d;
+  const uint64_t e = (uint64_t)blockIdx.x * 32 + lane;
+  long long a = 0;
+  if (e < kd) {
+#pragma unroll 4
+    for (uint32_t j = w; j < g; j += RF_THREADS / 32) a += part[(uint64_t)j * kd + e];
+  }
+  red[w][lane] = a;
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int i = 1; i < RF_THREADS / 32; ++i) a += red[i][lane];
+    if (e < kd) {
+      const unsigned long long cnt = counts[e / d];
+      if (cnt) c[e] = (float)(((double)a * ldexp(1.0, -*shift)) / (double)cnt);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *cmax_bits = 0;
 }
 
 // c_k = (sum_k * 2^-s) / count_k in FP64, rounded to FP32; empty clusters keep c_k.
@@ -727,6 +837,7 @@ size_t km_scratch_bytes(uint32_t n, uint32_t d, uint32_t k, int precision) {
     b += a256((uint64_t)n * 4);        // second flag list
     b += a256((uint64_t)k * d * 2 * 2);  // bf16 centroids (hi, lo)
   }
+  if (local_sums_fit(d, k)) b += a256((uint64_t)LS_MAX_CTAS * k * d * 8);  // per-CTA partial sums
   return (size_t)b;
 }
 
@@ -753,6 +864,7 @@ cudaError_t km_carve(KmBuffers& b, uint8_t* p, size_t bytes) {
     b.cent_bf16_norm = reinterpret_cast<float*>(take(n * 4));  // second flag list
     b.cb = reinterpret_cast<uint16_t*>(take(k * d * 4));
   }
+  b.part = local_sums_fit(d, k) ? reinterpret_cast<long long*>(take((uint64_t)LS_MAX_CTAS * k * d * 8)) : nullptr;
   if ((uint64_t)(q - p) > bytes) return cudaErrorInvalidValue;
   return cudaSuccess;
 }
@@ -786,6 +898,14 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
   if ((e = cudaFuncSetAttribute(km_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(k * 4))) !=
       cudaSuccess)
     return e;
+  const int ls_bytes = (int)((uint64_t)k * d * 8 + (uint64_t)k * 4);
+  const bool local = b.part != nullptr && ls_bytes <= di.smem_optin;
+  if (local && (e = cudaFuncSetAttribute(km_local_sum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         ls_bytes)) != cudaSuccess)
+    return e;
+  uint32_t ls_grid = (uint32_t)di.sms < LS_MAX_CTAS ? (uint32_t)di.sms : LS_MAX_CTAS;
+  if ((uint64_t)ls_grid * 1024 > n) ls_grid = (uint32_t)((n + 1023) / 1024);
+  if (ls_grid < 1) ls_grid = 1;
   const int rc_bytes = (int)((uint64_t)k * (d + 1) * 4);
   const bool rc_smem = k <= 32 * KLANE && rc_bytes <= di.smem_optin;
   if (rc_smem &&
@@ -799,9 +919,11 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
     if (b.precision != MR_KM_FP32) {
       if ((e = launch_kmeans_tc_assign(x, n, d, b.cent, k, b, di, s, nk)) != cudaSuccess) return e;
     } else {
+      if ((e = kt_begin(b.kt, s)) != cudaSuccess) return e;
       (k <= 256 ? km_assign_fp32_kernel<true> : km_assign_fp32_kernel<false>)<<<agrid, KM_THREADS, asm_bytes, s>>>(
           x, n, d, b.cent, k, b.cnorm, cmax_bits, nullptr, nullptr, b.assign, b.flagged, b.nflag, b.pairs,
           b.nflag + 4, nullptr);
+      if ((e = cudaGetLastError()) != cudaSuccess || (e = kt_end(b.kt, s)) != cudaSuccess) return e;
       ++*nk;
     }
     km_pair_kernel<<<di.sms * 4, 256, 0, s>>>(x, d, b.cent, b.pairs, b.nflag + 4, b.assign, b.stats + 1);
@@ -811,6 +933,14 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
                                                                 b.stats + 1);
     else
       km_recheck_fp64_kernel<<<di.sms * 4, 256, 0, s>>>(x, d, b.cent, k, b.flagged, b.nflag, b.assign, b.stats + 1);
+    if (local) {  // update with local arrays
+      km_local_sum_kernel<<<ls_grid, LS_THREADS, ls_bytes, s>>>(x, n, d, k, b.assign, shift, b.part, b.counts);
+      km_reduce_finalize_kernel<<<(unsigned)(((uint64_t)k * d + 31) / 32), RF_THREADS, 0, s>>>(
+          b.part, ls_grid, b.cent, k, d, b.counts, shift, cmax_bits);
+      *nk += 4;
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      continue;
+    }
     // update: counting sort of the points by cluster, then run-wise sums
     km_count_kernel<<<di.sms * 2, 512, k * 4, s>>>(b.assign, n, k, b.counts);
     km_offsets_kernel<<<1, 1024, 0, s>>>(b.counts, k, b.kcursor);

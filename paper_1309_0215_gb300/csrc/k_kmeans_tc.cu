@@ -172,27 +172,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// 64 consecutive TMEM columns of this warp's 32 lanes (one FP32 each).
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
-      "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
-      "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]),
-        "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]),
-        "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]),
-        "=r"(v[48]), "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]),
-        "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[32]) { tmem_ld32(taddr, v); }
-__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[64]) { tmem_ld64(taddr, v); }
 
 // Sortable key of a distance: its FP32 bit pattern with the low 8 mantissa
 // bits replaced by the centroid column, compared as a signed integer.  For
@@ -623,9 +603,11 @@ cudaError_t launch_kmeans_tc_assign(const float* x, uint32_t n, uint32_t d, cons
   const int grid = (int)(ntiles < (uint32_t)di.sms ? ntiles : (uint32_t)di.sms);
   uint32_t* list = reinterpret_cast<uint32_t*>(b.cent_bf16_norm);
   const int terms = b.precision == MR_KM_BF16X1_TC ? 1 : 3;
-  cudaError_t e = launch_km_tc_kernel(terms, x, n, d, c, k, b.cnorm, b.nflag + 3, b.assign, list, b.nflag + 1,
-                                      b.pairs, b.nflag + 4, b.stats + 3, nullptr, grid, s);
+  cudaError_t e = kt_begin(b.kt, s);
   if (e != cudaSuccess) return e;
+  e = launch_km_tc_kernel(terms, x, n, d, c, k, b.cnorm, b.nflag + 3, b.assign, list, b.nflag + 1, b.pairs,
+                          b.nflag + 4, b.stats + 3, nullptr, grid, s);
+  if (e != cudaSuccess || (e = kt_end(b.kt, s)) != cudaSuccess) return e;
   ++*nk;
   // near ties of the tensor-core pass: FP32 pass over the list (its own near
   // ties go on to the FP64 pass launched by the caller)

@@ -1130,7 +1130,7 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
 }
 
 cudaError_t launch_wordcount(const uint8_t* in, uint64_t n, const WcBuffers& b, const DevInfo& di, cudaStream_t s,
-                             uint64_t* nk, bool pipelined) {
+                             uint64_t* nk, bool pipelined, KTimer* kt) {
   cudaError_t e;
   // table (keys then counts) and state words start at zero
   if ((e = cudaMemsetAsync(b.key, 0, wc_table_bytes(b.cap), s)) != cudaSuccess) return e;
@@ -1144,8 +1144,9 @@ cudaError_t launch_wordcount(const uint8_t* in, uint64_t n, const WcBuffers& b, 
     uint64_t grid = (nseg + PIPE_PAIRS - 1) / PIPE_PAIRS;
     const uint64_t gmax = 4ull * di.sms;
     if (grid > gmax) grid = gmax;
+    if ((e = kt_begin(kt, s)) != cudaSuccess) return e;
     wc_pipe_kernel<<<(unsigned)grid, PIPE_THREADS, smem, s>>>(J);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = kt_end(kt, s)) != cudaSuccess) return e;
     ++*nk;
   } else if (n > 0) {
     const int smem = wc_map_smem_bytes();
@@ -1155,8 +1156,9 @@ cudaError_t launch_wordcount(const uint8_t* in, uint64_t n, const WcBuffers& b, 
     uint64_t grid = (nseg + MAP_WARPS - 1) / MAP_WARPS;
     const uint64_t gmax = 5ull * di.sms;
     if (grid > gmax) grid = gmax;
+    if ((e = kt_begin(kt, s)) != cudaSuccess) return e;
     wc_map_kernel<<<(unsigned)grid, MAP_THREADS, smem, s>>>(J);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = kt_end(kt, s)) != cudaSuccess) return e;
     ++*nk;
   }
   return launch_wordcount_post_multi(nullptr, J, 1, wc_compact_blocks(b.cap), b.cap, b.sortbuf, s, nk);

@@ -19,6 +19,30 @@ void set_last_error(const char* where, cudaError_t e) {
   g_last_error = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
 }
 
+cudaError_t kt_begin(KTimer* t, cudaStream_t s) {
+  if (!t || t->n >= KTimer::MAX) return cudaSuccess;
+  cudaEvent_t* ev = t->ev + 2 * t->n;
+  cudaError_t e = cudaSuccess;
+  if (!ev[0]) e = cudaEventCreate(&ev[0]);
+  if (e == cudaSuccess && !ev[1]) e = cudaEventCreate(&ev[1]);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+  return e;
+}
+
+cudaError_t kt_end(KTimer* t, cudaStream_t s) {
+  if (!t || t->n >= KTimer::MAX) return cudaSuccess;
+  const cudaError_t e = cudaEventRecord(t->ev[2 * t->n + 1], s);
+  if (e == cudaSuccess) ++t->n;
+  return e;
+}
+
+void kt_destroy(KTimer* t) {
+  if (!t) return;
+  for (cudaEvent_t& e : t->ev)
+    if (e) cudaEventDestroy(e);
+  delete t;
+}
+
 }  // namespace mrgb
 
 using namespace mrgb;
@@ -41,6 +65,7 @@ struct Job {
   uint64_t result_bytes = 0;     // fixed-size kinds
   cudaEvent_t done = nullptr;
   cudaEvent_t t0 = nullptr, t1 = nullptr;  // timing events (MR_FLAG_TIMING)
+  KTimer* kt = nullptr;                     // main-kernel launches (MR_FLAG_TIMING)
   // word count
   WcBuffers wc;
   bool wc_auto = true;
@@ -356,6 +381,7 @@ void free_job(mr_ctx* c, Job* j) {
   if (j->done) cudaEventDestroy(j->done);
   if (j->t0) cudaEventDestroy(j->t0);
   if (j->t1) cudaEventDestroy(j->t1);
+  kt_destroy(j->kt);
   dev_free(c, j->slab, j->slab_bytes);
   dev_free(c, j->in_owned, j->in_owned_bytes);
   delete j;
@@ -379,9 +405,11 @@ int grid_for(const mr_ctx* c, uint64_t bytes, uint64_t bytes_per_block, int max_
 mr_status enqueue_plain_on(mr_ctx* c, Job* j, cudaStream_t st) {
   const uint64_t n = j->desc.input_bytes;
   if (j->t0) MR_CUDA_TRY(cudaEventRecord(j->t0, st));
+  if (j->kt) j->kt->n = 0;
   switch (j->desc.kind) {
     case MR_HIST_RGB8: {
       MR_CUDA_TRY(cudaMemsetAsync(j->result, 0, 768 * 8, st));
+      MR_CUDA_TRY(kt_begin(j->kt, st));
       if (j->container == MR_C_GLOBAL_ARRAY) {
         MR_CUDA_TRY(launch_hist_global(j->in, n, static_cast<uint64_t*>(j->result), grid_for(c, n, 512 * 64, 4),
                                        st));
@@ -392,25 +420,28 @@ mr_status enqueue_plain_on(mr_ctx* c, Job* j, cudaStream_t st) {
                                      grid_for(c, n, 1536ull * 32 * 4, 1), st));
         ++c->launches;
       }
+      MR_CUDA_TRY(kt_end(j->kt, st));
       break;
     }
     case MR_LINREG_I8:
       MR_CUDA_TRY(cudaMemsetAsync(j->result, 0, 5 * 8, st));
+      MR_CUDA_TRY(kt_begin(j->kt, st));
       MR_CUDA_TRY(launch_linreg(reinterpret_cast<const int8_t*>(j->in), n, static_cast<int64_t*>(j->result),
                                 grid_for(c, n, 512ull * 16 * 8, 2), st));
+      MR_CUDA_TRY(kt_end(j->kt, st));
       ++c->launches;
       break;
     case MR_WORDCOUNT:
-      MR_CUDA_TRY(launch_wordcount(j->in, n, j->wc, c->di, st, &c->launches, j->desc.wc_pipelined != 0));
+      MR_CUDA_TRY(launch_wordcount(j->in, n, j->wc, c->di, st, &c->launches, j->desc.wc_pipelined != 0, j->kt));
       break;
     case MR_HIST_U32:
       MR_CUDA_TRY(launch_hist_keys(reinterpret_cast<const uint32_t*>(j->in), n / 4, j->desc.hist_bins,
                                    j->container == MR_C_SMEM_ARRAY, j->hk_counters, j->hk_counters == nullptr,
-                                   static_cast<unsigned long long*>(j->result), c->di, st, &c->launches));
+                                   static_cast<unsigned long long*>(j->result), c->di, st, &c->launches, j->kt));
       break;
     case MR_BLOOM_DNA:
       MR_CUDA_TRY(launch_bloom(j->in, n, j->desc.bloom_kmer, j->desc.bloom_bits, j->desc.bloom_hashes,
-                               static_cast<uint32_t*>(j->result), c->di, st, &c->launches));
+                               static_cast<uint32_t*>(j->result), c->di, st, &c->launches, j->kt));
       break;
     case MR_KMEANS_F32: {
       uint8_t* p = static_cast<uint8_t*>(j->result);
@@ -418,6 +449,7 @@ mr_status enqueue_plain_on(mr_ctx* c, Job* j, cudaStream_t st) {
       float* oc = reinterpret_cast<float*>(p);
       int32_t* oa = reinterpret_cast<int32_t*>(p + (uint64_t)K * D * 4);
       unsigned long long* os = reinterpret_cast<unsigned long long*>(p + km_stats_offset(K, D, N));
+      j->km.kt = j->kt;
       MR_CUDA_TRY(launch_kmeans(reinterpret_cast<const float*>(j->in), j->km_init_dev, j->desc.km_iters, j->km,
                                 c->di, st, oc, oa, os, &c->launches));
       break;
@@ -796,6 +828,7 @@ mr_status add_job_impl(mr_ctx* c, const mr_job_desc* desc, uint64_t* job_id) {
   if (e == cudaSuccess && (c->flags & MR_FLAG_TIMING)) {
     e = cudaEventCreate(&j->t0);
     if (e == cudaSuccess) e = cudaEventCreate(&j->t1);
+    if (e == cudaSuccess && !(j->kt = new (std::nothrow) KTimer())) e = cudaErrorMemoryAllocation;
   }
   if (e != cudaSuccess) {
     set_last_error("cudaEventCreate", e);
@@ -1089,6 +1122,25 @@ mr_status mr_rerun(mr_ctx* c) {
 mr_status mr_get_tuning(const mr_ctx* c, mr_tuning* out) {
   if (!c || !out) return MR_EINVAL;
   *out = c->tune;
+  return MR_OK;
+}
+
+mr_status mr_job_kernel_ms(mr_ctx* c, uint64_t job_id, float* ms, uint32_t* launches) {
+  if (!c || !ms || !launches) return MR_EINVAL;
+  DeviceGuard g(c->device);
+  Job* j = find_job(c, job_id);
+  if (!j) return MR_ENOJOB;
+  if (j->state == JOB_PENDING) return MR_ENOTREADY;
+  if (!j->kt || j->kt->n == 0) return MR_EINVAL;
+  MR_CUDA_TRY(cudaEventSynchronize(j->kt->ev[2 * j->kt->n - 1]));
+  float sum = 0.f;
+  for (uint32_t i = 0; i < j->kt->n; ++i) {
+    float t = 0.f;
+    MR_CUDA_TRY(cudaEventElapsedTime(&t, j->kt->ev[2 * i], j->kt->ev[2 * i + 1]));
+    sum += t;
+  }
+  *ms = sum;
+  *launches = j->kt->n;
   return MR_OK;
 }
 

@@ -40,6 +40,20 @@ cudaError_t launch_linreg(const int8_t* in, uint64_t n, int64_t* sums, int grid,
 int hist_smem_bytes();         // dynamic shared memory the smem histogram needs
 int hist_block_threads();
 
+// ------------------------------------------------------ kernel timing
+// Event pairs around each launch of a job's main kernel (the distance pass of
+// every k-means iteration, the word-count map pass, the one counting kernel of
+// the other kinds), recorded when the context times its jobs.  Events are
+// created on first use; launches past MAX are not timed.
+struct KTimer {
+  static constexpr uint32_t MAX = 64;
+  cudaEvent_t ev[2 * MAX] = {};
+  uint32_t n = 0;  // launches timed in the current run
+};
+cudaError_t kt_begin(KTimer* t, cudaStream_t s);  // no-op for t == nullptr
+cudaError_t kt_end(KTimer* t, cudaStream_t s);
+void kt_destroy(KTimer* t);
+
 // ------------------------------------------- large-key histogram, Bloom
 // Largest bin count whose local arrays (nbins + 1 u32) fit one CTA.
 int hk_smem_max_bins(const DevInfo& di);
@@ -48,10 +62,11 @@ int hk_smem_max_bins(const DevInfo& di);
 // the u64 output (needed from 2^32 keys on); else into the u32 counters
 // (nbins + 1 words) and widen at the end.
 cudaError_t launch_hist_keys(const uint32_t* keys, uint64_t n, uint32_t nbins, bool smem, void* counters,
-                             bool wide, unsigned long long* out, const DevInfo& di, cudaStream_t s, uint64_t* nk);
+                             bool wide, unsigned long long* out, const DevInfo& di, cudaStream_t s, uint64_t* nk,
+                             KTimer* kt = nullptr);
 // Bloom-filter build over n bases into ceil(m / 32) u32 words (zeroed here).
 cudaError_t launch_bloom(const uint8_t* seq, uint64_t n, uint32_t L, uint64_t m, uint32_t h, uint32_t* bits,
-                         const DevInfo& di, cudaStream_t s, uint64_t* nk);
+                         const DevInfo& di, cudaStream_t s, uint64_t* nk, KTimer* kt = nullptr);
 
 // --------------------------------------------------------- word count job
 struct WcBuffers {
@@ -80,7 +95,7 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
 // pipelined: the map pass runs as mapper warps handing cache misses to
 // reducer warps through shared-memory rings (wc_pipe_kernel).
 cudaError_t launch_wordcount(const uint8_t* in, uint64_t n, const WcBuffers& b, const DevInfo& di, cudaStream_t s,
-                             uint64_t* nk, bool pipelined = false);
+                             uint64_t* nk, bool pipelined = false, KTimer* kt = nullptr);
 
 // ---------------------------------------------------------------- k-means
 struct KmBuffers {
@@ -100,6 +115,8 @@ struct KmBuffers {
   uint16_t* cb = nullptr;       // BF16 centroids [k][d]
   unsigned int* maxabs = nullptr;  // [1] bits of max |x|
   uint32_t* kcursor = nullptr;  // [k] counting-sort write cursors
+  long long* part = nullptr;    // [CTAs][k][d] partial sums of the local-array update (nullptr: sort path)
+  KTimer* kt = nullptr;         // times the distance pass of each iteration
   int fx_shift = 32;            // fixed-point scale exponent
   int precision = 0;
 };

@@ -111,3 +111,36 @@ def test_context_jobs_plain_sequence(mr):
     with pytest.raises(mr.MRError):
         c.fetch(j1)
     c.close()
+
+
+def test_main_kernel_timing(mr):
+    """mr_job_kernel_ms: one timed launch per counting job, one per k-means
+    iteration, and the summed launch time within the job's own time."""
+    c = mr.Context(timing=True)
+    px = synth.hist_rgb8(3_000_000, seed=13)
+    x, _, _ = synth.kmeans_points(20_000, 64, 16, seed=14)
+    init = synth.kmeans_init(x, 16, seed=15)
+    text, _, _ = synth.wc_text(1 << 20, seed=16, want_ranks=False)
+    jh = c.add_job(mr.HIST_RGB8, _dev(px))
+    jl = c.add_job(mr.LINREG_I8, synth.linreg_i8(100_000, seed=17))
+    jk = c.add_job(mr.KMEANS_F32, x, km_dims=64, km_k=16, km_iters=3, km_init=init, km_precision=mr.KM_BF16_TC)
+    jw = c.add_job(mr.WORDCOUNT, text)
+    c.run()
+    for j, launches in ((jh, 1), (jl, 1), (jk, 3), (jw, 1)):
+        ms, n = c.kernel_ms(j)
+        assert n == launches
+        assert 0.0 < ms <= c.elapsed_ms(j) * 1.01
+    assert np.array_equal(np.frombuffer(c.fetch(jh), dtype=np.uint64), oracle.hist_rgb8(px))
+    c.close()
+    plain = mr.Context()  # no timing: refused
+    j = plain.add_job(mr.HIST_RGB8, px)
+    plain.run()
+    with pytest.raises(mr.MRError):
+        plain.kernel_ms(j)
+    plain.close()
+    batched = mr.Context(timing=True)  # the batched launch is shared by its jobs: refused
+    j = batched.add_job(mr.HIST_RGB8, px)
+    batched.run(mr.RUN_BATCHED)
+    with pytest.raises(mr.MRError):
+        batched.kernel_ms(j)
+    batched.close()

@@ -36,6 +36,7 @@ def _run(mr, x, init, iters, precision=0, on_device=True):
     (5_001, 37, 50, 2),     # ragged dims / tiles
     (3_000, 100, 20, 2),    # D > 64: chunked dimensions
     (4_000, 16, 300, 2),    # K > 256: chunked centroids
+    (6_000, 128, 260, 2),   # K*D sums too large for shared memory: the sorted update
     (777, 3, 1, 2),         # K = 1: the global mean
     (64, 8, 64, 1),         # every point its own centroid
 ])
