@@ -244,8 +244,9 @@ struct Post {
   unsigned long long* src;   // [R] input offset of a long key
   unsigned long long* excl;  // [R] exclusive scan of key lengths in sorted order
   unsigned long long* bsum;  // [ceil(R / CB)]
-  // [0] number of records; [1] 1 = comparison-sort fallback; [2] long tie
-  // runs listed; [4..7] OR of ~key1, key1, ~s0, s0 (digits equal in every key)
+  // [0] number of records; [2] tie runs of up to SB records listed; [3] tie
+  // runs longer than SB listed; [4..7] OR of ~key1, key1, ~s0, s0 (digits
+  // equal in every key)
   unsigned long long* glob;
   unsigned long long* kh[2];  // radix ping-pong: key1
   unsigned long long* kl[2];  // s0
@@ -365,28 +366,26 @@ __global__ void __launch_bounds__(CB) wc_compact_kernel(const JobDev* jobs, JobD
   P.r0[i] = rec;
 }
 
-// Block sort: SB records per CTA, bitonic network in shared memory.
+// Tie runs of up to SB records are ordered by one CTA's bitonic sort in
+// shared memory (SB_THREADS threads); longer ones by one CTA's merge sort.
 constexpr int SB = 2048;
 constexpr int SB_THREADS = 1024;
 
-// Orders for the comparison sort.  FullCmp: the output order on whole
-// records (a pad sorts last).  KeyCmp: (key1, s0, index) on compact keys; the
-// index only makes the order total, records that tie on (key1, s0) are put in
-// the output order afterwards by the tie fix-up.
+// Compact-key sort of small record sets: KSB records per CTA in the block
+// sort, then merge passes of KMT threads x KMI outputs per CTA (KMT * KMI
+// divides 2 * KSB, so a merge tile never spans two pairs of runs).
+constexpr int KSB = 512;
+constexpr int KSB_THREADS = 256;
+constexpr int KMT = 128;
+constexpr int KMI = 4;
+static_assert((2 * KSB) % (KMT * KMI) == 0, "merge tile must divide a pair of block-sorted runs");
+
+// Compact key: (key1, s0, index).  The index only makes the order total;
+// records that tie on (key1, s0) are put in the output order afterwards by
+// the tie fix-up.
 struct KeyRec {
   unsigned long long k1, k0;  // key1, s0 of the record
   uint32_t idx, pad;          // record index
-};
-struct FullCmp {
-  const JobDev* jobs;
-  JobDev single;
-  const unsigned long long* src;
-  __device__ bool less(const SortRec& a, const SortRec& b) const {
-    const bool a_pad = a.idx == 0xffffffffu, b_pad = b.idx == 0xffffffffu;
-    if (a_pad || b_pad) return b_pad && !a_pad;
-    return rec_less(a, b, jobs, single, src);
-  }
-  __device__ static SortRec pad() { return SortRec{~0ull, ~0ull, ~0ull, 0xffffffffu, 0xffffffffu}; }
 };
 struct KeyCmp {
   __device__ bool less(const KeyRec& a, const KeyRec& b) const {
@@ -397,22 +396,19 @@ struct KeyCmp {
   __device__ static KeyRec pad() { return KeyRec{~0ull, ~0ull, 0xffffffffu, 0u}; }
 };
 
-// Block sort: SB items per CTA, bitonic network in shared memory.  Runs when
-// the fallback flag P.glob[1] equals `when`.
-template <class R, class C>
-__global__ void __launch_bounds__(SB_THREADS) blocksort_kernel(R* data, const unsigned long long* glob, C cmp,
-                                                               unsigned long long when) {
+// Block sort: NB items per CTA (NT threads), bitonic network in shared memory.
+template <class R, class C, int NB, int NT>
+__global__ void __launch_bounds__(NT) blocksort_kernel(R* data, const unsigned long long* glob, C cmp) {
   extern __shared__ __align__(16) unsigned char bs_raw[];
   R* sh = reinterpret_cast<R*>(bs_raw);
-  if (glob[1] != when) return;
   const uint64_t m = glob[0];
-  const uint64_t b0 = (uint64_t)blockIdx.x * SB;
+  const uint64_t b0 = (uint64_t)blockIdx.x * NB;
   if (b0 >= m) return;
-  for (int i = threadIdx.x; i < SB; i += blockDim.x) sh[i] = b0 + i < m ? data[b0 + i] : C::pad();
+  for (int i = threadIdx.x; i < NB; i += NT) sh[i] = b0 + i < m ? data[b0 + i] : C::pad();
   __syncthreads();
-  for (int k = 2; k <= SB; k <<= 1) {
+  for (int k = 2; k <= NB; k <<= 1) {
     for (int jj = k >> 1; jj > 0; jj >>= 1) {
-      for (int t = threadIdx.x; t < SB / 2; t += blockDim.x) {
+      for (int t = threadIdx.x; t < NB / 2; t += NT) {
         const int lo = 2 * jj * (t / jj) + (t % jj);
         const int hi = lo + jj;
         const bool up = (lo & k) == 0;
@@ -425,7 +421,7 @@ __global__ void __launch_bounds__(SB_THREADS) blocksort_kernel(R* data, const un
       __syncthreads();
     }
   }
-  for (int i = threadIdx.x; i < SB; i += blockDim.x)
+  for (int i = threadIdx.x; i < NB; i += NT)
     if (b0 + i < m) data[b0 + i] = sh[i];
 }
 
@@ -455,33 +451,29 @@ __device__ uint64_t corank_warp(const R* A, uint64_t la, const R* B, uint64_t lb
 }
 
 // One merge pass: runs of L sorted items are merged pairwise.  A CTA owns
-// MTILE consecutive outputs: two warps find where its range starts and ends
+// T * I consecutive outputs: two warps find where its range starts and ends
 // in the two runs, the CTA stages both input windows in shared memory, and
-// each thread merges MI outputs from there.  Runs when P.glob[1] == when.
-constexpr int MT = 256;
-constexpr int MI = 8;
-constexpr int MTILE = MT * MI;
-
-template <class R, class C>
-__global__ void __launch_bounds__(MT) merge_kernel(const R* __restrict__ src, R* __restrict__ dst, uint64_t L,
-                                                   const unsigned long long* glob, C cmp, unsigned long long when) {
+// each thread merges I outputs from there.
+template <class R, class C, int T, int I>
+__global__ void __launch_bounds__(T) merge_kernel(const R* __restrict__ src, R* __restrict__ dst, uint64_t L,
+                                                  const unsigned long long* glob, C cmp) {
+  constexpr int TILE = T * I;
   extern __shared__ __align__(16) unsigned char mg_raw[];
   R* ms = reinterpret_cast<R*>(mg_raw);
   __shared__ uint64_t cr[2];
-  if (glob[1] != when) return;
   const uint64_t m = glob[0];
-  const uint64_t o0 = (uint64_t)blockIdx.x * MTILE;
+  const uint64_t o0 = (uint64_t)blockIdx.x * TILE;
   if (o0 >= m) return;
-  const uint64_t a0 = (o0 / (2 * L)) * (2 * L);  // MTILE divides 2L: a tile never spans two pairs
+  const uint64_t a0 = (o0 / (2 * L)) * (2 * L);  // TILE divides 2L: a tile never spans two pairs
   const uint64_t la = (m - a0) < L ? (m - a0) : L;
   const uint64_t b0 = a0 + L;
   const uint64_t lb = b0 < m ? ((m - b0) < L ? (m - b0) : L) : 0;
   const R* A = src + a0;
   const R* B = src + b0;
   const uint64_t kk0 = o0 - a0;
-  const uint64_t kk1 = (kk0 + MTILE) < la + lb ? kk0 + MTILE : la + lb;
+  const uint64_t kk1 = (kk0 + TILE) < la + lb ? kk0 + TILE : la + lb;
   if (lb == 0) {  // a lone run: copy
-    for (uint64_t t = kk0 + threadIdx.x; t < kk1; t += MT) dst[a0 + t] = A[t];
+    for (uint64_t t = kk0 + threadIdx.x; t < kk1; t += T) dst[a0 + t] = A[t];
     return;
   }
   const int warp = threadIdx.x >> 5;
@@ -494,12 +486,12 @@ __global__ void __launch_bounds__(MT) merge_kernel(const R* __restrict__ src, R*
   const uint64_t i0 = cr[0], i1 = cr[1];
   const uint32_t na = (uint32_t)(i1 - i0);
   const uint32_t nb = (uint32_t)((kk1 - i1) - (kk0 - i0));
-  for (uint32_t t = threadIdx.x; t < na; t += MT) ms[t] = A[i0 + t];
-  for (uint32_t t = threadIdx.x; t < nb; t += MT) ms[na + t] = B[kk0 - i0 + t];
+  for (uint32_t t = threadIdx.x; t < na; t += T) ms[t] = A[i0 + t];
+  for (uint32_t t = threadIdx.x; t < nb; t += T) ms[na + t] = B[kk0 - i0 + t];
   __syncthreads();
   const R* sa = ms;
   const R* sb = ms + na;
-  const uint32_t r0 = threadIdx.x * MI;
+  const uint32_t r0 = threadIdx.x * I;
   const uint32_t tot = na + nb;
   if (r0 >= tot) return;
   uint32_t lo = r0 > nb ? r0 - nb : 0, hi = r0 < na ? r0 : na;
@@ -509,7 +501,7 @@ __global__ void __launch_bounds__(MT) merge_kernel(const R* __restrict__ src, R*
     else hi = mid;
   }
   uint32_t i = lo, j = r0 - lo;
-  for (int t = 0; t < MI && r0 + t < tot; ++t) {
+  for (int t = 0; t < I && r0 + t < tot; ++t) {
     bool takeA;
     if (j >= nb) takeA = true;
     else if (i >= na) takeA = false;
@@ -518,14 +510,9 @@ __global__ void __launch_bounds__(MT) merge_kernel(const R* __restrict__ src, R*
   }
 }
 
-// The sorted records: the radix sort's output, or the fallback's.
-__device__ __forceinline__ const SortRec* final_recs(const Post& P, const SortRec* fallback) {
-  return P.glob[1] ? fallback : P.r1;
-}
-
-__global__ void __launch_bounds__(CB) wc_lensum_kernel(const SortRec* fb, Post P) {
+__global__ void __launch_bounds__(CB) wc_lensum_kernel(Post P) {
   __shared__ unsigned long long ws[32];
-  const SortRec* recs = final_recs(P, fb);
+  const SortRec* recs = P.r1;
   const uint64_t m = *P.glob;
   const uint64_t i = (uint64_t)blockIdx.x * CB + threadIdx.x;
   unsigned long long v = i < m ? recs[i].len : 0;
@@ -576,9 +563,9 @@ __global__ void __launch_bounds__(CB) wc_bscan_kernel(Post P, uint64_t nb) {
 
 // Exclusive length scan per record; each job's first / end record and the
 // scan at both are stored in the job's state as 64-bit fields 1..4.
-__global__ void __launch_bounds__(CB) wc_bounds_kernel(const SortRec* fb, const JobDev* jobs, JobDev single, Post P) {
+__global__ void __launch_bounds__(CB) wc_bounds_kernel(const JobDev* jobs, JobDev single, Post P) {
   __shared__ unsigned long long wsum[32];
-  const SortRec* recs = final_recs(P, fb);
+  const SortRec* recs = P.r1;
   const uint64_t m = *P.glob;
   const uint64_t i = (uint64_t)blockIdx.x * CB + threadIdx.x;
   if ((uint64_t)blockIdx.x * CB >= m) return;
@@ -619,8 +606,8 @@ __global__ void __launch_bounds__(CB) wc_bounds_kernel(const SortRec* fb, const 
 }
 
 // Records and key bytes into each job's result.
-__global__ void __launch_bounds__(256) wc_gather_kernel(const SortRec* fb, const JobDev* jobs, JobDev single, Post P) {
-  const SortRec* recs = final_recs(P, fb);
+__global__ void __launch_bounds__(256) wc_gather_kernel(const JobDev* jobs, JobDev single, Post P) {
+  const SortRec* recs = P.r1;
   const uint64_t m = *P.glob;
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
@@ -867,8 +854,11 @@ __global__ void __launch_bounds__(256) wc_rgather_kernel(Post P) {
 __device__ __forceinline__ bool rtie(const SortRec& a, const SortRec& b) { return a.key1 == b.key1 && a.s0 == b.s0; }
 
 // Records that tie on (key1, s0) are ordered by the full comparison: a run
-// of up to FIX_THREAD by its first thread, longer ones are listed for
-// wc_rfix_long_kernel (up to SB records) or switch to the fallback sort.
+// of up to FIX_THREAD by its first thread; longer ones are listed for
+// wc_rfix_long_kernel (up to SB records: P.runs from the front, count in
+// P.glob[2]) or wc_rfix_huge_kernel (P.runs from the back, count in
+// P.glob[3]).  Every listed run is longer than FIX_THREAD, so both lists
+// together hold fewer than max_runs entries.
 __global__ void __launch_bounds__(256) wc_rfix_kernel(Post P, const JobDev* jobs, JobDev single, uint64_t max_runs) {
   const uint64_t m = *P.glob;
   const uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
@@ -878,6 +868,26 @@ __global__ void __launch_bounds__(256) wc_rfix_kernel(Post P, const JobDev* jobs
   if (i > 0 && rtie(r[i - 1], r[i])) return;  // not the first of its run
   uint64_t L = 2;
   while (i + L < m && L <= (uint64_t)SB && rtie(r[i], r[i + L])) ++L;
+  if (L > (uint64_t)SB) {
+    // longer than SB: the run is contiguous, so gallop then bisect for its end
+    uint64_t lo = i + SB, hi = m, step = SB;
+    for (;;) {
+      const uint64_t q = lo + step;
+      if (q >= m) break;
+      if (!rtie(r[i], r[q])) {
+        hi = q;
+        break;
+      }
+      lo = q;
+      step *= 2;
+    }
+    while (hi - lo > 1) {
+      const uint64_t mid = lo + (hi - lo) / 2;
+      if (rtie(r[i], r[mid])) lo = mid;
+      else hi = mid;
+    }
+    L = hi - i;
+  }
   if (L <= (uint64_t)FIX_THREAD) {
     for (uint64_t a = i + 1; a < i + L; ++a) {
       const SortRec x = r[a];
@@ -891,49 +901,108 @@ __global__ void __launch_bounds__(256) wc_rfix_kernel(Post P, const JobDev* jobs
   } else if (L <= (uint64_t)SB) {
     const unsigned long long k = atomicAdd(P.glob + 2, 1ull);
     if (k < max_runs) P.runs[k] = make_uint2((uint32_t)i, (uint32_t)L);
-    else P.glob[1] = 1;
   } else {
-    P.glob[1] = 1;
+    const unsigned long long k = atomicAdd(P.glob + 3, 1ull);
+    if (k < max_runs) P.runs[max_runs - 1 - k] = make_uint2((uint32_t)i, (uint32_t)L);
   }
 }
 
-// One CTA per listed tie run: bitonic sort in shared memory.
+__device__ __forceinline__ bool rec_less_pad(const SortRec& a, const SortRec& b, const JobDev* jobs,
+                                             const JobDev& single, const unsigned long long* src) {
+  const bool a_pad = a.idx == 0xffffffffu, b_pad = b.idx == 0xffffffffu;
+  if (a_pad || b_pad) return b_pad && !a_pad;
+  return rec_less(a, b, jobs, single, src);
+}
+
+// Full-order bitonic sort of r[0..L) (L <= SB) by the CTA in shared memory.
+__device__ void cta_sort_run(SortRec* r, int L, SortRec* sh, const JobDev* jobs, const JobDev& single,
+                             const unsigned long long* src) {
+  int n2 = 1;
+  while (n2 < L) n2 <<= 1;
+  for (int i = threadIdx.x; i < n2; i += blockDim.x)
+    sh[i] = i < L ? r[i] : SortRec{~0ull, ~0ull, ~0ull, 0xffffffffu, 0xffffffffu};
+  __syncthreads();
+  for (int kk = 2; kk <= n2; kk <<= 1) {
+    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+      for (int t = threadIdx.x; t < n2 / 2; t += blockDim.x) {
+        const int lo = 2 * jj * (t / jj) + (t % jj);
+        const int hi = lo + jj;
+        const bool up = (lo & kk) == 0;
+        const SortRec a = sh[lo], bb = sh[hi];
+        if (rec_less_pad(bb, a, jobs, single, src) == up) {
+          sh[lo] = bb;
+          sh[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < L; i += blockDim.x) r[i] = sh[i];
+  __syncthreads();
+}
+
+// One CTA per listed tie run of up to SB records.
 __global__ void __launch_bounds__(SB_THREADS) wc_rfix_long_kernel(Post P, const JobDev* jobs, JobDev single,
                                                                   uint64_t max_runs) {
   extern __shared__ __align__(16) unsigned char rf_raw[];
   SortRec* sh = reinterpret_cast<SortRec*>(rf_raw);
-  if (P.glob[1]) return;
   uint64_t nr = P.glob[2];
   if (nr > max_runs) nr = max_runs;
   for (uint64_t k = blockIdx.x; k < nr; k += gridDim.x) {
     const uint2 run = P.runs[k];
-    SortRec* r = P.r1 + run.x;
-    const int L = (int)run.y;
-    int n2 = 1;
-    while (n2 < L) n2 <<= 1;
-    for (int i = threadIdx.x; i < n2; i += blockDim.x)
-      sh[i] = i < L ? r[i] : SortRec{~0ull, ~0ull, ~0ull, 0xffffffffu, 0xffffffffu};
-    __syncthreads();
-    for (int kk = 2; kk <= n2; kk <<= 1) {
-      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-        for (int t = threadIdx.x; t < n2 / 2; t += blockDim.x) {
-          const int lo = 2 * jj * (t / jj) + (t % jj);
-          const int hi = lo + jj;
-          const bool up = (lo & kk) == 0;
-          const SortRec a = sh[lo], bb = sh[hi];
-          const bool a_pad = a.idx == 0xffffffffu, b_pad = bb.idx == 0xffffffffu;
-          bool b_lt_a;
-          if (a_pad || b_pad) b_lt_a = a_pad && !b_pad;
-          else b_lt_a = rec_less(bb, a, jobs, single, P.src);
-          if (b_lt_a == up) {
-            sh[lo] = bb;
-            sh[hi] = a;
-          }
+    cta_sort_run(P.r1 + run.x, (int)run.y, sh, jobs, single, P.src);
+  }
+}
+
+// One CTA per listed tie run longer than SB: bitonic sort of each SB-record
+// tile, then merge passes of doubling width between the run's place in P.r1
+// and the same place in P.r0 (free once the records are in key order).  In a
+// pass each thread finds where its share of a pair's outputs starts in the
+// two inputs (binary search on the merge path), then merges sequentially.
+__global__ void __launch_bounds__(SB_THREADS) wc_rfix_huge_kernel(Post P, const JobDev* jobs, JobDev single,
+                                                                  uint64_t max_runs) {
+  extern __shared__ __align__(16) unsigned char rh_raw[];
+  SortRec* sh = reinterpret_cast<SortRec*>(rh_raw);
+  uint64_t nr = P.glob[3];
+  if (nr > max_runs) nr = max_runs;
+  for (uint64_t k = blockIdx.x; k < nr; k += gridDim.x) {
+    const uint2 run = P.runs[max_runs - 1 - k];
+    const uint64_t L = run.y;
+    SortRec* const home = P.r1 + run.x;
+    for (uint64_t t0 = 0; t0 < L; t0 += SB)
+      cta_sort_run(home + t0, (int)(L - t0 < (uint64_t)SB ? L - t0 : SB), sh, jobs, single, P.src);
+    SortRec* in = home;
+    SortRec* out = P.r0 + run.x;
+    for (uint64_t W = SB; W < L; W *= 2) {
+      for (uint64_t a0 = 0; a0 < L; a0 += 2 * W) {
+        const uint64_t la = L - a0 < W ? L - a0 : W;
+        const uint64_t lb = L - a0 > W ? (L - a0 - W < W ? L - a0 - W : W) : 0;
+        const SortRec* A = in + a0;
+        const SortRec* B = A + la;
+        const uint64_t tot = la + lb;
+        const uint64_t per = (tot + blockDim.x - 1) / blockDim.x;
+        const uint64_t kk = (uint64_t)threadIdx.x * per;
+        if (kk >= tot) continue;
+        uint64_t lo = kk > lb ? kk - lb : 0, hi = kk < la ? kk : la;
+        while (lo < hi) {
+          const uint64_t mid = (lo + hi) >> 1;
+          if (rec_less(A[mid], B[kk - 1 - mid], jobs, single, P.src)) lo = mid + 1;
+          else hi = mid;
         }
-        __syncthreads();
+        uint64_t i = lo, j = kk - lo;
+        const uint64_t e = kk + per < tot ? kk + per : tot;
+        for (uint64_t o = kk; o < e; ++o) {
+          const bool takeA = j >= lb || (i < la && !rec_less(B[j], A[i], jobs, single, P.src));
+          out[a0 + o] = takeA ? A[i++] : B[j++];
+        }
       }
+      __syncthreads();
+      SortRec* t = in;
+      in = out;
+      out = t;
     }
-    for (int i = threadIdx.x; i < L; i += blockDim.x) r[i] = sh[i];
+    if (in != home)
+      for (uint64_t i = threadIdx.x; i < L; i += blockDim.x) home[i] = in[i];
     __syncthreads();
   }
 }
@@ -1042,22 +1111,18 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
   const unsigned g256 = (unsigned)((R + 255) / 256);
   if (R < RADIX_MIN_RECORDS) {
     // small record sets: comparison sort of (key1, s0, index) keys
-    const int kbs = SB * (int)sizeof(KeyRec), kmg = MTILE * (int)sizeof(KeyRec);
-    if ((e = cudaFuncSetAttribute(blocksort_kernel<KeyRec, KeyCmp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  kbs)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(merge_kernel<KeyRec, KeyCmp>, cudaFuncAttributeMaxDynamicSharedMemorySize, kmg)) !=
-            cudaSuccess)
-      return e;
+    constexpr int kbs = KSB * (int)sizeof(KeyRec), kmg = KMT * KMI * (int)sizeof(KeyRec);
+    static_assert(kbs <= 40 * 1024 && kmg <= 40 * 1024, "sort tiles must fit the default shared-memory limit");
     wc_kkeys_kernel<<<g256, 256, 0, s>>>(P);
-    blocksort_kernel<KeyRec, KeyCmp><<<(unsigned)((R + SB - 1) / SB), SB_THREADS, kbs, s>>>(P.kr[0], P.glob,
-                                                                                          KeyCmp{}, 0ull);
+    blocksort_kernel<KeyRec, KeyCmp, KSB, KSB_THREADS><<<(unsigned)((R + KSB - 1) / KSB), KSB_THREADS, kbs, s>>>(
+        P.kr[0], P.glob, KeyCmp{});
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *nk += 2;
     KeyRec* ks = P.kr[0];
     KeyRec* kd = P.kr[1];
-    for (uint64_t L = SB; L < R; L *= 2) {
-      merge_kernel<KeyRec, KeyCmp><<<(unsigned)((R + MTILE - 1) / MTILE), MT, kmg, s>>>(ks, kd, L, P.glob,
-                                                                                       KeyCmp{}, 0ull);
+    for (uint64_t L = KSB; L < R; L *= 2) {
+      merge_kernel<KeyRec, KeyCmp, KMT, KMI><<<(unsigned)((R + KMT * KMI - 1) / (KMT * KMI)), KMT, kmg, s>>>(
+          ks, kd, L, P.glob, KeyCmp{});
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       ++*nk;
       KeyRec* t = ks;
@@ -1084,46 +1149,20 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // ties on (key1, s0): the full order
   wc_rfix_kernel<<<g256, 256, 0, s>>>(P, jobs, single, max_runs(R));
-  {
-    const int fx_smem = SB * (int)sizeof(SortRec);
-    if ((e = cudaFuncSetAttribute(wc_rfix_long_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem)) !=
-        cudaSuccess)
-      return e;
-    wc_rfix_long_kernel<<<64, SB_THREADS, fx_smem, s>>>(P, jobs, single, max_runs(R));
-  }
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  *nk += 3;
-  // fallback (only if a tie run was too long): comparison sort of whole records
-  const FullCmp fc{jobs, single, P.src};
-  const int bs_smem = SB * (int)sizeof(SortRec);
-  const int mg_smem = MTILE * (int)sizeof(SortRec);
-  if ((e = cudaFuncSetAttribute(blocksort_kernel<SortRec, FullCmp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                bs_smem)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(merge_kernel<SortRec, FullCmp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                mg_smem)) != cudaSuccess)
+  const int fx_smem = SB * (int)sizeof(SortRec);
+  if ((e = cudaFuncSetAttribute(wc_rfix_long_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem)) !=
+          cudaSuccess ||
+      (e = cudaFuncSetAttribute(wc_rfix_huge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem)) !=
+          cudaSuccess)
     return e;
-  blocksort_kernel<SortRec, FullCmp><<<(unsigned)((R + SB - 1) / SB), SB_THREADS, bs_smem, s>>>(P.r0, P.glob, fc,
-                                                                                                1ull);
+  wc_rfix_long_kernel<<<64, SB_THREADS, fx_smem, s>>>(P, jobs, single, max_runs(R));
+  wc_rfix_huge_kernel<<<16, SB_THREADS, fx_smem, s>>>(P, jobs, single, max_runs(R));
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  ++*nk;
-  SortRec* src = P.r0;
-  SortRec* dst = P.r1;
-  for (uint64_t L = SB; L < R; L *= 2) {
-    merge_kernel<SortRec, FullCmp><<<(unsigned)((R + MTILE - 1) / MTILE), MT, mg_smem, s>>>(src, dst, L, P.glob, fc,
-                                                                                           1ull);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    ++*nk;
-    SortRec* t = src;
-    src = dst;
-    dst = t;
-  }
-  wc_lensum_kernel<<<(unsigned)nb, CB, 0, s>>>(src, P);  // src: the fallback's result
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  *nk += 4;
+  wc_lensum_kernel<<<(unsigned)nb, CB, 0, s>>>(P);
   wc_bscan_kernel<<<1, CB, 0, s>>>(P, nb);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  wc_bounds_kernel<<<(unsigned)nb, CB, 0, s>>>(src, jobs, single, P);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  wc_gather_kernel<<<g256, 256, 0, s>>>(src, jobs, single, P);
+  wc_bounds_kernel<<<(unsigned)nb, CB, 0, s>>>(jobs, single, P);
+  wc_gather_kernel<<<g256, 256, 0, s>>>(jobs, single, P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   *nk += 4;
   return cudaSuccess;

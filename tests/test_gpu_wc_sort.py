@@ -2,10 +2,11 @@
 words (job/count and the first 8 key bytes).
 
 Distinct words that share their first 8 bytes and their count form one tie
-run after the radix passes.  Runs of up to 32 are ordered by one thread,
-runs of up to 2048 by one CTA's bitonic sort, and a longer run switches the
-batch to the comparison sort; each path must give the oracle's bytes, also
-with long keys (> 15 bytes) whose first 16 bytes agree, and inside a batch.
+run after the key sort.  Runs of up to 32 are ordered by one thread, runs of
+up to 2048 by one CTA's bitonic sort, and longer runs by one CTA's merge sort
+each; every path must give the oracle's bytes, also with long keys (> 15
+bytes) whose first 16 bytes agree, with several long runs in one job, and
+inside a batch.
 The radix sort runs for record capacities of 2^20 and up (a pinned table of
 2^20 slots here); smaller ones use the comparison sort alone (slots=0)."""
 import numpy as np
@@ -35,6 +36,20 @@ def test_tie_runs_short_prefix(mr, nwords, slots):
 @pytest.mark.parametrize("nwords", [7, 300, 3000])
 def test_tie_runs_long_keys(mr, nwords, slots):
     raw = _text(nwords, b"prefix_shared_by_long_keys_", 2, nwords)
+    assert mr.wordcount(raw, wc_slots=slots) == oracle.wordcount(raw)
+
+
+@pytest.mark.parametrize("slots", [0, 1 << 20])
+def test_several_huge_tie_runs(mr, slots):
+    """Runs of 2049..20000 records (one to four merge passes), three of them
+    in one job (counts 1, 2 and 3 keep them apart), plus short runs."""
+    rng = np.random.default_rng(5)
+    toks = []
+    for reps, n, pre in ((1, 20000, b"hugehuge"), (2, 4097, b"bigbigbi"), (3, 2049, b"midmidmi")):
+        toks += [pre + b"%06d" % i for i in range(n) for _ in range(reps)]
+    toks += [b"x", b"y", b"x"]
+    rng.shuffle(toks)
+    raw = b" ".join(toks) + b"\n"
     assert mr.wordcount(raw, wc_slots=slots) == oracle.wordcount(raw)
 
 
