@@ -256,6 +256,9 @@ struct Post {
   uint32_t* plan;             // [NPASS] bit 0 active, bit 1 source buffer; [NPASS] final buffer
   uint2* runs;                // tie runs longer than FIX_THREAD: {first, length}
   struct KeyRec* kr[2];       // compact keys for the comparison sort of small record sets
+  uint32_t* ss;               // sample sort: [0] buckets; counts, offsets (+ end), cursors (ss_* below)
+  uint32_t* ss_rank;          // sample sort: [S] ranks of the sample
+  uint16_t* bkt;              // sample sort: [R] bucket of each compacted record
 };
 
 __device__ __forceinline__ uint64_t bswap64(uint64_t v) {
@@ -907,38 +910,93 @@ __global__ void __launch_bounds__(256) wc_rfix_kernel(Post P, const JobDev* jobs
   }
 }
 
-__device__ __forceinline__ bool rec_less_pad(const SortRec& a, const SortRec& b, const JobDev* jobs,
-                                             const JobDev& single, const unsigned long long* src) {
-  const bool a_pad = a.idx == 0xffffffffu, b_pad = b.idx == 0xffffffffu;
-  if (a_pad || b_pad) return b_pad && !a_pad;
-  return rec_less(a, b, jobs, single, src);
-}
+// Full record order (a pad, idx == ~0, sorts last).
+struct RecCmp {
+  const JobDev* jobs;
+  JobDev single;
+  const unsigned long long* src;
+  __device__ bool less(const SortRec& a, const SortRec& b) const {
+    const bool a_pad = a.idx == 0xffffffffu, b_pad = b.idx == 0xffffffffu;
+    if (a_pad || b_pad) return b_pad && !a_pad;
+    return rec_less(a, b, jobs, single, src);
+  }
+  __device__ static SortRec pad() { return SortRec{~0ull, ~0ull, ~0ull, 0xffffffffu, 0xffffffffu}; }
+};
 
-// Full-order bitonic sort of r[0..L) (L <= SB) by the CTA in shared memory.
-__device__ void cta_sort_run(SortRec* r, int L, SortRec* sh, const JobDev* jobs, const JobDev& single,
-                             const unsigned long long* src) {
-  int n2 = 1;
-  while (n2 < L) n2 <<= 1;
-  for (int i = threadIdx.x; i < n2; i += blockDim.x)
-    sh[i] = i < L ? r[i] : SortRec{~0ull, ~0ull, ~0ull, 0xffffffffu, 0xffffffffu};
-  __syncthreads();
+// CTA-wide bitonic sort of sh[0..n2) (n2 a power of two).
+template <class R, class C>
+__device__ void cta_bitonic(R* sh, int n2, const C& cmp) {
   for (int kk = 2; kk <= n2; kk <<= 1) {
     for (int jj = kk >> 1; jj > 0; jj >>= 1) {
       for (int t = threadIdx.x; t < n2 / 2; t += blockDim.x) {
         const int lo = 2 * jj * (t / jj) + (t % jj);
         const int hi = lo + jj;
         const bool up = (lo & kk) == 0;
-        const SortRec a = sh[lo], bb = sh[hi];
-        if (rec_less_pad(bb, a, jobs, single, src) == up) {
-          sh[lo] = bb;
+        const R a = sh[lo], b = sh[hi];
+        if (cmp.less(b, a) == up) {
+          sh[lo] = b;
           sh[hi] = a;
         }
       }
       __syncthreads();
     }
   }
-  for (int i = threadIdx.x; i < L; i += blockDim.x) r[i] = sh[i];
+}
+
+// r[0..L) into sh (padded to a power of two) and sorted there; L <= capacity.
+template <class R, class C>
+__device__ void cta_sort_smem(const R* r, int L, R* sh, const C& cmp) {
+  int n2 = 1;
+  while (n2 < L) n2 <<= 1;
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) sh[i] = i < L ? r[i] : C::pad();
   __syncthreads();
+  cta_bitonic(sh, n2, cmp);
+}
+
+// Sort r[0..L) by one CTA: tiles of up to cap records (a power of two)
+// sorted in shared memory, then merge passes of doubling width between r and
+// tmp; in a pass each thread finds where its share of a pair's outputs starts
+// in the two inputs (binary search on the merge path) and merges
+// sequentially.  Returns the buffer that holds the result (r or tmp).
+template <class R, class C>
+__device__ R* cta_sort(R* r, R* tmp, uint64_t L, R* sh, int cap, const C& cmp) {
+  for (uint64_t t0 = 0; t0 < L; t0 += cap) {
+    const int n = (int)(L - t0 < (uint64_t)cap ? L - t0 : (uint64_t)cap);
+    cta_sort_smem(r + t0, n, sh, cmp);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) r[t0 + i] = sh[i];
+    __syncthreads();
+  }
+  R* in = r;
+  R* out = tmp;
+  for (uint64_t W = cap; W < L; W *= 2) {
+    for (uint64_t a0 = 0; a0 < L; a0 += 2 * W) {
+      const uint64_t la = L - a0 < W ? L - a0 : W;
+      const uint64_t lb = L - a0 > W ? (L - a0 - W < W ? L - a0 - W : W) : 0;
+      const R* A = in + a0;
+      const R* B = A + la;
+      const uint64_t tot = la + lb;
+      const uint64_t per = (tot + blockDim.x - 1) / blockDim.x;
+      const uint64_t kk = (uint64_t)threadIdx.x * per;
+      if (kk >= tot) continue;
+      uint64_t lo = kk > lb ? kk - lb : 0, hi = kk < la ? kk : la;
+      while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (cmp.less(A[mid], B[kk - 1 - mid])) lo = mid + 1;
+        else hi = mid;
+      }
+      uint64_t i = lo, j = kk - lo;
+      const uint64_t e = kk + per < tot ? kk + per : tot;
+      for (uint64_t o = kk; o < e; ++o) {
+        const bool takeA = j >= lb || (i < la && !cmp.less(B[j], A[i]));
+        out[a0 + o] = takeA ? A[i++] : B[j++];
+      }
+    }
+    __syncthreads();
+    R* t = in;
+    in = out;
+    out = t;
+  }
+  return in;
 }
 
 // One CTA per listed tie run of up to SB records.
@@ -946,64 +1004,240 @@ __global__ void __launch_bounds__(SB_THREADS) wc_rfix_long_kernel(Post P, const 
                                                                   uint64_t max_runs) {
   extern __shared__ __align__(16) unsigned char rf_raw[];
   SortRec* sh = reinterpret_cast<SortRec*>(rf_raw);
+  const RecCmp cmp{jobs, single, P.src};
   uint64_t nr = P.glob[2];
   if (nr > max_runs) nr = max_runs;
   for (uint64_t k = blockIdx.x; k < nr; k += gridDim.x) {
     const uint2 run = P.runs[k];
-    cta_sort_run(P.r1 + run.x, (int)run.y, sh, jobs, single, P.src);
+    SortRec* r = P.r1 + run.x;
+    cta_sort_smem(r, (int)run.y, sh, cmp);
+    for (int i = threadIdx.x; i < (int)run.y; i += blockDim.x) r[i] = sh[i];
+    __syncthreads();
   }
 }
 
-// One CTA per listed tie run longer than SB: bitonic sort of each SB-record
-// tile, then merge passes of doubling width between the run's place in P.r1
-// and the same place in P.r0 (free once the records are in key order).  In a
-// pass each thread finds where its share of a pair's outputs starts in the
-// two inputs (binary search on the merge path), then merges sequentially.
+// One CTA per listed tie run longer than SB, merge-sorted with the same
+// place in P.r0 (free once the records are in key order) as scratch.
 __global__ void __launch_bounds__(SB_THREADS) wc_rfix_huge_kernel(Post P, const JobDev* jobs, JobDev single,
                                                                   uint64_t max_runs) {
   extern __shared__ __align__(16) unsigned char rh_raw[];
   SortRec* sh = reinterpret_cast<SortRec*>(rh_raw);
+  const RecCmp cmp{jobs, single, P.src};
   uint64_t nr = P.glob[3];
   if (nr > max_runs) nr = max_runs;
   for (uint64_t k = blockIdx.x; k < nr; k += gridDim.x) {
     const uint2 run = P.runs[max_runs - 1 - k];
-    const uint64_t L = run.y;
     SortRec* const home = P.r1 + run.x;
-    for (uint64_t t0 = 0; t0 < L; t0 += SB)
-      cta_sort_run(home + t0, (int)(L - t0 < (uint64_t)SB ? L - t0 : SB), sh, jobs, single, P.src);
-    SortRec* in = home;
-    SortRec* out = P.r0 + run.x;
-    for (uint64_t W = SB; W < L; W *= 2) {
-      for (uint64_t a0 = 0; a0 < L; a0 += 2 * W) {
-        const uint64_t la = L - a0 < W ? L - a0 : W;
-        const uint64_t lb = L - a0 > W ? (L - a0 - W < W ? L - a0 - W : W) : 0;
-        const SortRec* A = in + a0;
-        const SortRec* B = A + la;
-        const uint64_t tot = la + lb;
-        const uint64_t per = (tot + blockDim.x - 1) / blockDim.x;
-        const uint64_t kk = (uint64_t)threadIdx.x * per;
-        if (kk >= tot) continue;
-        uint64_t lo = kk > lb ? kk - lb : 0, hi = kk < la ? kk : la;
-        while (lo < hi) {
-          const uint64_t mid = (lo + hi) >> 1;
-          if (rec_less(A[mid], B[kk - 1 - mid], jobs, single, P.src)) lo = mid + 1;
-          else hi = mid;
-        }
-        uint64_t i = lo, j = kk - lo;
-        const uint64_t e = kk + per < tot ? kk + per : tot;
-        for (uint64_t o = kk; o < e; ++o) {
-          const bool takeA = j >= lb || (i < la && !rec_less(B[j], A[i], jobs, single, P.src));
-          out[a0 + o] = takeA ? A[i++] : B[j++];
-        }
-      }
-      __syncthreads();
-      SortRec* t = in;
-      in = out;
-      out = t;
-    }
-    if (in != home)
-      for (uint64_t i = threadIdx.x; i < L; i += blockDim.x) home[i] = in[i];
+    const SortRec* res = cta_sort(home, P.r0 + run.x, run.y, sh, SB, cmp);
+    if (res != home)
+      for (uint64_t i = threadIdx.x; i < run.y; i += blockDim.x) home[i] = res[i];
     __syncthreads();
+  }
+}
+
+// Sample sort of compact keys, for record capacities up to SS_MAX_RECORDS:
+// four launches instead of a block sort and one launch per merge pass.
+// Splitters drawn from evenly spaced records of the compacted array (hash
+// order, so effectively a random sample) cut the keys into buckets of about
+// SS_B records; one CTA per bucket then places each key by its rank, the
+// number of smaller keys in the bucket (keys are distinct: the index breaks
+// ties), counted against the bucket held in shared memory; every thread reads
+// the same key at a time, so the reads are broadcasts and the pass needs no
+// barrier.  The sample is ranked the same way.  A bucket over SS_RANK_MAX
+// records (rare with SS_OVER samples per bucket) is sorted by its CTA with
+// bitonic tiles and merge passes.
+constexpr uint64_t SS_MAX_RECORDS = 1ull << 17;
+constexpr int SS_B = 256;
+constexpr int SS_MAXB = (int)(SS_MAX_RECORDS / SS_B);
+constexpr int SS_OVER = 8;
+constexpr int SS_SMAX = SS_MAXB * SS_OVER;
+constexpr int SS_RANK_MAX = 1024;
+constexpr int SS_CAP = 2048;  // bitonic tile of the fallback
+constexpr int SS_T = 256;
+constexpr int SS_WORDS = 8 + 3 * SS_MAXB + 1;
+__device__ __forceinline__ uint32_t* ss_cnt(const Post& P) { return P.ss + 8; }
+__device__ __forceinline__ uint32_t* ss_off(const Post& P) { return P.ss + 8 + SS_MAXB; }  // nb + 1 entries
+__device__ __forceinline__ uint32_t* ss_cur(const Post& P) { return P.ss + 9 + 2 * SS_MAXB; }
+
+__device__ __forceinline__ KeyRec key_of(const SortRec& r, uint64_t i) { return KeyRec{r.key1, r.s0, (uint32_t)i, 0u}; }
+
+// Keys in shared memory as (key1, s0) pairs plus indices.  rank() counts the
+// keys below a given one; one comparison is the borrow of the 160-bit
+// difference b - a (five chained 32-bit subtractions, no branches).
+struct KeySoA {
+  ulonglong2* k;
+  uint32_t* idx;
+  __device__ KeySoA(unsigned char* raw, int cap)
+      : k(reinterpret_cast<ulonglong2*>(raw)), idx(reinterpret_cast<uint32_t*>(reinterpret_cast<ulonglong2*>(raw) + cap)) {}
+  __device__ void put(int i, const KeyRec& r) {
+    k[i] = make_ulonglong2(r.k1, r.k0);
+    idx[i] = r.idx;
+  }
+  __device__ uint32_t rank(int j0, int j1, unsigned long long a1, unsigned long long a0, uint32_t ai) const {
+    const uint32_t a1h = (uint32_t)(a1 >> 32), a1l = (uint32_t)a1, a0h = (uint32_t)(a0 >> 32), a0l = (uint32_t)a0;
+    uint32_t r = 0;
+#pragma unroll 4
+    for (int j = j0; j < j1; ++j) {
+      const ulonglong2 b = k[j];
+      const uint32_t bi = idx[j];
+      uint32_t borrow;
+      asm("{\n\t.reg .u32 t;\n\t"
+          "sub.cc.u32 t, %1, %6;\n\t"
+          "subc.cc.u32 t, %2, %7;\n\t"
+          "subc.cc.u32 t, %3, %8;\n\t"
+          "subc.cc.u32 t, %4, %9;\n\t"
+          "subc.cc.u32 t, %5, %10;\n\t"
+          "subc.u32 %0, 0, 0;\n\t}"
+          : "=r"(borrow)
+          : "r"(bi), "r"((uint32_t)b.y), "r"((uint32_t)(b.y >> 32)), "r"((uint32_t)b.x), "r"((uint32_t)(b.x >> 32)),
+            "r"(ai), "r"(a0l), "r"(a0h), "r"(a1l), "r"(a1h));
+      r -= borrow;  // borrow is 0 or 0xffffffff
+    }
+    return r;
+  }
+};
+constexpr int soa_bytes(int cap) { return cap * 20; }
+constexpr int SS_PARTS = 4;  // the sample's ranks are counted in this many parts
+
+__device__ __forceinline__ void ss_geometry(uint64_t m, uint64_t& nb, uint64_t& S) {
+  nb = (m + SS_B - 1) / SS_B;
+  nb = nb < 1 ? 1 : (nb > (uint64_t)SS_MAXB ? (uint64_t)SS_MAXB : nb);
+  S = m < nb * SS_OVER ? m : nb * SS_OVER;
+}
+
+// Ranks of the sample (evenly spaced records), counted in SS_PARTS parts:
+// CTA (c, part) ranks samples 256c.. against the part-th slice of the sample
+// and adds to P.ss_rank.  CTA 0 also records the number of buckets.  The
+// bucket counters and rank counters start at zero (cleared with P.glob).
+__global__ void __launch_bounds__(256) wc_ss_sample_kernel(Post P) {
+  extern __shared__ __align__(16) unsigned char sp_raw[];
+  const uint64_t m = P.glob[0];
+  uint64_t nb, S;
+  ss_geometry(m, nb, S);
+  const uint32_t c = blockIdx.x / SS_PARTS, part = blockIdx.x % SS_PARTS;
+  if (blockIdx.x == 0 && threadIdx.x == 0) P.ss[0] = (uint32_t)nb;
+  if ((uint64_t)c * 256 >= S) return;
+  const uint64_t q0 = (S * part) / SS_PARTS, q1 = (S * (part + 1)) / SS_PARTS;
+  KeySoA K(sp_raw, SS_SMAX);
+  for (uint64_t j = threadIdx.x; j < S; j += 256) {
+    const uint64_t q = ((2 * j + 1) * m) / (2 * S);
+    K.put((int)j, key_of(P.r0[q], q));
+  }
+  __syncthreads();
+  const uint64_t j = (uint64_t)c * 256 + threadIdx.x;
+  if (j < S) {
+    const uint32_t r = K.rank((int)q0, (int)q1, K.k[j].x, K.k[j].y, K.idx[j]);
+    if (r) atomicAdd(&P.ss_rank[j], r);
+  }
+}
+
+// Bucket of each record (number of splitters below its key) and bucket sizes.
+__global__ void __launch_bounds__(256) wc_ss_count_kernel(Post P) {
+  __shared__ KeyRec spl[SS_MAXB];
+  __shared__ uint32_t cnt[SS_MAXB];
+  const uint64_t m = P.glob[0];
+  if ((uint64_t)blockIdx.x * 256 >= m) return;
+  uint64_t nb, S;
+  ss_geometry(m, nb, S);
+  // splitter b is the sample of rank ((b + 1) * S) / nb (S >= nb: distinct ranks)
+  for (uint64_t j = threadIdx.x; j < S; j += 256) {
+    const uint64_t r = P.ss_rank[j];
+    const uint64_t u = (r * nb + S - 1) / S;  // the only candidate b + 1
+    if (u >= 1 && u < nb && (u * S) / nb == r) {
+      const uint64_t q = ((2 * j + 1) * m) / (2 * S);
+      spl[u - 1] = key_of(P.r0[q], q);
+    }
+  }
+  for (uint64_t t = threadIdx.x; t < nb; t += 256) cnt[t] = 0u;
+  __syncthreads();
+  const uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
+  if (i < m) {
+    const KeyRec k = key_of(P.r0[i], i);
+    const KeyCmp cmp;
+    uint32_t lo = 0, hi = (uint32_t)nb - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (cmp.less(spl[mid], k)) lo = mid + 1;
+      else hi = mid;
+    }
+    P.bkt[i] = (uint16_t)lo;
+    atomicAdd(&cnt[lo], 1u);
+  }
+  __syncthreads();
+  for (uint64_t t = threadIdx.x; t < nb; t += 256)
+    if (cnt[t]) atomicAdd(&ss_cnt(P)[t], cnt[t]);
+}
+
+// Bucket offsets (each CTA scans the counts; CTA 0 stores them), then each
+// CTA reserves one range per bucket it holds and places its keys there.
+__global__ void __launch_bounds__(256) wc_ss_scatter_kernel(Post P) {
+  __shared__ uint32_t off[SS_MAXB + 1];
+  __shared__ uint32_t cnt[SS_MAXB];
+  __shared__ uint32_t wsum[8];
+  const uint64_t m = P.glob[0];
+  const uint32_t nb = P.ss[0];
+  if (blockIdx.x > 0 && (uint64_t)blockIdx.x * 256 >= m) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // exclusive scan of the counts, two buckets per thread (nb <= 512)
+  const uint32_t b0 = 2 * threadIdx.x;
+  const uint32_t c0 = b0 < nb ? ss_cnt(P)[b0] : 0u, c1 = b0 + 1 < nb ? ss_cnt(P)[b0 + 1] : 0u;
+  uint32_t incl = c0 + c1;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  uint32_t wbase = 0;
+  for (int w = 0; w < warp; ++w) wbase += wsum[w];
+  const uint32_t ex = wbase + incl - (c0 + c1);
+  if (b0 < nb) off[b0] = ex;
+  if (b0 + 1 < nb) off[b0 + 1] = ex + c0;
+  if (threadIdx.x == 0) off[nb] = (uint32_t)m;
+  for (uint32_t t = threadIdx.x; t < nb; t += 256) cnt[t] = 0u;
+  __syncthreads();
+  if (blockIdx.x == 0)
+    for (uint32_t t = threadIdx.x; t <= nb; t += 256) ss_off(P)[t] = off[t];
+  if ((uint64_t)blockIdx.x * 256 >= m) return;
+  const uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
+  uint32_t b = 0, r = 0;
+  if (i < m) {
+    b = P.bkt[i];
+    r = atomicAdd(&cnt[b], 1u);
+  }
+  __syncthreads();
+  for (uint32_t t = threadIdx.x; t < nb; t += 256)
+    if (cnt[t]) cnt[t] = off[t] + atomicAdd(&ss_cur(P)[t], cnt[t]);
+  __syncthreads();
+  if (i < m) P.kr[0][cnt[b] + r] = key_of(P.r0[i], i);
+}
+
+// Up to SS_RANK_MAX / SS_T CTAs per bucket: CTA (b, ch) ranks keys
+// SS_T*ch.. of bucket b against the whole bucket, then gathers their records
+// straight to those places in P.r1.  A bucket over SS_RANK_MAX keys is sorted
+// by its first CTA (bitonic tiles, merge passes).
+constexpr int SS_CH = SS_RANK_MAX / SS_T;
+__global__ void __launch_bounds__(SS_T) wc_ss_bsort_kernel(Post P) {
+  extern __shared__ __align__(16) unsigned char sb_raw[];
+  const uint32_t nb = P.ss[0];
+  const uint32_t b = blockIdx.x / SS_CH, ch = blockIdx.x % SS_CH;
+  if (b >= nb) return;
+  const uint32_t o = ss_off(P)[b], L = ss_off(P)[b + 1] - o;
+  const KeyRec* in = P.kr[0] + o;
+  if (L <= (uint32_t)SS_RANK_MAX) {
+    if (ch * SS_T >= L) return;
+    KeySoA K(sb_raw, SS_RANK_MAX);
+    for (uint32_t j = threadIdx.x; j < L; j += SS_T) K.put((int)j, in[j]);
+    __syncthreads();
+    const uint32_t j = ch * SS_T + threadIdx.x;
+    if (j < L) {
+      const uint32_t ai = K.idx[j];
+      P.r1[o + K.rank(0, (int)L, K.k[j].x, K.k[j].y, ai)] = P.r0[ai];
+    }
+  } else if (ch == 0) {
+    KeyRec* sh = reinterpret_cast<KeyRec*>(sb_raw);
+    const KeyRec* res = cta_sort(P.kr[0] + o, P.kr[1] + o, L, sh, SS_CAP, KeyCmp{});
+    for (uint32_t j = threadIdx.x; j < L; j += SS_T) P.r1[o + j] = P.r0[res[j].idx];
   }
 }
 
@@ -1013,18 +1247,24 @@ constexpr uint64_t ca256(uint64_t x) { return (x + 255) & ~255ull; }
 constexpr uint64_t rtiles(uint64_t R) { return (R + RTILE - 1) / RTILE; }
 constexpr uint64_t rchunks(uint64_t R) { return (rtiles(R) + RCHUNK - 1) / RCHUNK; }
 constexpr uint64_t max_runs(uint64_t R) { return R / (FIX_THREAD + 1) + 1; }
+// glob, and for sample-sorted capacities the sample-sort words, cleared by one memset
+constexpr uint64_t head_bytes(uint64_t R) { return 256 + (R <= SS_MAX_RECORDS ? ca256((SS_WORDS + SS_SMAX) * 4) : 0); }
 constexpr uint64_t sortbuf_bytes(uint64_t R) {
-  return 256 + 2 * ca256(R * sizeof(SortRec)) + 2 * ca256(R * 8) + ca256(((R + CB - 1) / CB) * 8) +
+  return head_bytes(R) + 2 * ca256(R * sizeof(SortRec)) + 2 * ca256(R * 8) + ca256(((R + CB - 1) / CB) * 8) +
          ca256(max_runs(R) * 8) +
          (R >= RADIX_MIN_RECORDS ? 4 * ca256(R * 8) + 2 * ca256(R * 4) + ca256(rtiles(R) * 256 * 4) +
                                        ca256(rchunks(R) * 256 * 4) + 256
-                                 : 2 * ca256(R * sizeof(KeyRec)));
+                                 : 2 * ca256(R * sizeof(KeyRec)) + ca256(R * 2));
 }
 
 Post carve_post(uint8_t* p, uint64_t R) {
-  Post P;
+  Post P{};
   P.glob = reinterpret_cast<unsigned long long*>(p);
-  p += 256;
+  if (R <= SS_MAX_RECORDS) {
+    P.ss = reinterpret_cast<uint32_t*>(p + 256);
+    P.ss_rank = P.ss + SS_WORDS;
+  }
+  p += head_bytes(R);
   P.r0 = reinterpret_cast<SortRec*>(p);
   p += a256(R * sizeof(SortRec));
   P.r1 = reinterpret_cast<SortRec*>(p);
@@ -1042,6 +1282,7 @@ Post carve_post(uint8_t* p, uint64_t R) {
       P.kr[q] = reinterpret_cast<KeyRec*>(p);
       p += a256(R * sizeof(KeyRec));
     }
+    P.bkt = reinterpret_cast<uint16_t*>(p);
     return P;
   }
   for (int q = 0; q < 2; ++q) {
@@ -1103,13 +1344,32 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
                                         uint64_t* nk) {
   cudaError_t e;
   Post P = carve_post(sortbuf, R);
-  if ((e = cudaMemsetAsync(P.glob, 0, 64, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(P.glob, 0, head_bytes(R), s)) != cudaSuccess) return e;
   wc_compact_kernel<<<(unsigned)nblocks, CB, 0, s>>>(jobs, single, njobs, P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   ++*nk;
   const uint64_t nb = (R + CB - 1) / CB;
   const unsigned g256 = (unsigned)((R + 255) / 256);
-  if (R < RADIX_MIN_RECORDS) {
+  if (R <= SS_MAX_RECORDS) {
+    // sample sort of (key1, s0, index) keys; the bucket pass gathers the records
+    constexpr int sp_smem = soa_bytes(SS_SMAX);
+    constexpr int sb_smem = SS_CAP * (int)sizeof(KeyRec) > soa_bytes(SS_RANK_MAX) ? SS_CAP * (int)sizeof(KeyRec)
+                                                                                   : soa_bytes(SS_RANK_MAX);
+    if ((e = cudaFuncSetAttribute(wc_ss_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sp_smem)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(wc_ss_bsort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sb_smem)) !=
+            cudaSuccess)
+      return e;
+    const uint64_t nbmax = (R + SS_B - 1) / SS_B < (uint64_t)SS_MAXB ? (R + SS_B - 1) / SS_B : (uint64_t)SS_MAXB;
+    const uint64_t smax = R < nbmax * SS_OVER ? R : nbmax * SS_OVER;
+    const uint64_t sblocks = (smax + 255) / 256 < 1 ? 1 : (smax + 255) / 256;
+    wc_ss_sample_kernel<<<(unsigned)(sblocks * SS_PARTS), 256, sp_smem, s>>>(P);
+    wc_ss_count_kernel<<<g256, 256, 0, s>>>(P);
+    wc_ss_scatter_kernel<<<g256, 256, 0, s>>>(P);
+    wc_ss_bsort_kernel<<<(unsigned)((nbmax < 1 ? 1 : nbmax) * SS_CH), SS_T, sb_smem, s>>>(P);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    *nk += 3;
+  } else if (R < RADIX_MIN_RECORDS) {
     // small record sets: comparison sort of (key1, s0, index) keys
     constexpr int kbs = KSB * (int)sizeof(KeyRec), kmg = KMT * KMI * (int)sizeof(KeyRec);
     static_assert(kbs <= 40 * 1024 && kmg <= 40 * 1024, "sort tiles must fit the default shared-memory limit");
