@@ -1047,14 +1047,17 @@ __global__ void __launch_bounds__(SB_THREADS) wc_rfix_huge_kernel(Post P, const 
 // records (rare with SS_OVER samples per bucket) is sorted by its CTA with
 // bitonic tiles and merge passes.
 constexpr uint64_t SS_MAX_RECORDS = 1ull << 17;
-constexpr int SS_B = 256;
+constexpr int SS_B = 128;
 constexpr int SS_MAXB = (int)(SS_MAX_RECORDS / SS_B);
-constexpr int SS_OVER = 8;
+constexpr int SS_OVER = 4;
 constexpr int SS_SMAX = SS_MAXB * SS_OVER;
 constexpr int SS_RANK_MAX = 1024;
 constexpr int SS_CAP = 2048;  // bitonic tile of the fallback
 constexpr int SS_T = 256;
 constexpr int SS_WORDS = 8 + 3 * SS_MAXB + 1;
+constexpr int SS_BPT = (SS_MAXB + 255) / 256;  // buckets per thread in the offset scan (256 threads)
+static_assert(SS_MAXB <= 65535 && SS_BPT <= 8, "bucket ids are 16-bit; the offset scan holds SS_BPT counts a thread");
+static_assert(SS_SMAX * 20 <= 227 * 1024, "the ranked sample must fit one CTA's shared memory");
 __device__ __forceinline__ uint32_t* ss_cnt(const Post& P) { return P.ss + 8; }
 __device__ __forceinline__ uint32_t* ss_off(const Post& P) { return P.ss + 8 + SS_MAXB; }  // nb + 1 entries
 __device__ __forceinline__ uint32_t* ss_cur(const Post& P) { return P.ss + 9 + 2 * SS_MAXB; }
@@ -1178,21 +1181,28 @@ __global__ void __launch_bounds__(256) wc_ss_scatter_kernel(Post P) {
   const uint32_t nb = P.ss[0];
   if (blockIdx.x > 0 && (uint64_t)blockIdx.x * 256 >= m) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // exclusive scan of the counts, two buckets per thread (nb <= 512)
-  const uint32_t b0 = 2 * threadIdx.x;
-  const uint32_t c0 = b0 < nb ? ss_cnt(P)[b0] : 0u, c1 = b0 + 1 < nb ? ss_cnt(P)[b0 + 1] : 0u;
-  uint32_t incl = c0 + c1;
+  // exclusive scan of the counts, SS_BPT consecutive buckets per thread
+  const uint32_t b0 = SS_BPT * threadIdx.x;
+  uint32_t c[SS_BPT], tot = 0;
+#pragma unroll
+  for (int q = 0; q < SS_BPT; ++q) {
+    c[q] = b0 + q < nb ? ss_cnt(P)[b0 + q] : 0u;
+    tot += c[q];
+  }
+  uint32_t incl = tot;
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += v;
   }
   if (lane == 31) wsum[warp] = incl;
   __syncthreads();
-  uint32_t wbase = 0;
-  for (int w = 0; w < warp; ++w) wbase += wsum[w];
-  const uint32_t ex = wbase + incl - (c0 + c1);
-  if (b0 < nb) off[b0] = ex;
-  if (b0 + 1 < nb) off[b0 + 1] = ex + c0;
+  uint32_t ex = incl - tot;
+  for (int w = 0; w < warp; ++w) ex += wsum[w];
+#pragma unroll
+  for (int q = 0; q < SS_BPT; ++q) {
+    if (b0 + q < nb) off[b0 + q] = ex;
+    ex += c[q];
+  }
   if (threadIdx.x == 0) off[nb] = (uint32_t)m;
   for (uint32_t t = threadIdx.x; t < nb; t += 256) cnt[t] = 0u;
   __syncthreads();
