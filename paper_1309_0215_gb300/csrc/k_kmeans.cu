@@ -27,6 +27,7 @@
 //    per run instead of one per coordinate.
 #include <cmath>
 
+#include "dev_pipe.cuh"
 #include "mr_internal.h"
 
 namespace mrgb {
@@ -696,10 +697,20 @@ __global__ void __launch_bounds__(256) km_sum_kernel(const float* __restrict__ x
 // Update step with local arrays (Sec. III-E: the array container, privatised
 // per thread block).  A CTA's [k][d] fixed-point sums and [k] counts live in
 // shared memory; one CTA per SM streams a contiguous range of points in input
-// order (coalesced rows: no sort and no gather) and adds each coordinate with a
-// shared-memory atomic.  It then stores its sums as one partial (plain stores)
-// and adds its counts to the global counts; km_reduce_finalize_kernel adds the
-// partials.  Integer sums make the result independent of the order.
+// order (coalesced rows: no sort and no gather) and adds each coordinate with
+// shared-memory atomics.  A 64-bit sum is kept as two 32-bit words, each
+// added by a native 32-bit atomic: the low word's add returns the old value,
+// and a carry out of it (new < old) goes into the high word's add, so
+// hi * 2^32 + lo is the exact sum modulo 2^64 (which holds it: the scale
+// keeps |sum| below 2^62).  The CTA then stores its sums as one partial
+// (plain stores) and adds its counts to the global counts;
+// km_reduce_finalize_kernel adds the partials.  Integer sums make the result
+// independent of the order.
+__device__ __forceinline__ void add64_split(uint32_t* lo, uint32_t* hi, long long q) {
+  const uint32_t ql = (uint32_t)q;
+  const uint32_t old = atomicAdd(lo, ql);
+  atomicAdd(hi, (uint32_t)((unsigned long long)q >> 32) + (old + ql < old ? 1u : 0u));
+}
 constexpr int LS_THREADS = 1024;
 constexpr int LS_ROWS = 4;  // rows in flight per warp
 constexpr uint32_t LS_MAX_CTAS = 160;  // partials held in scratch
@@ -712,9 +723,10 @@ __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_kernel(const float
                                                                      unsigned long long* counts) {
   extern __shared__ __align__(16) unsigned char ls_sm[];
   const uint64_t kd = (uint64_t)k * d;
-  unsigned long long* S = reinterpret_cast<unsigned long long*>(ls_sm);
-  unsigned int* C = reinterpret_cast<unsigned int*>(S + kd);
-  for (uint64_t i = threadIdx.x; i < kd; i += LS_THREADS) S[i] = 0;
+  uint32_t* SL = reinterpret_cast<uint32_t*>(ls_sm);  // low words [k][d]
+  uint32_t* SH = SL + kd;                             // high words [k][d]
+  unsigned int* C = SH + kd;
+  for (uint64_t i = threadIdx.x; i < 2 * kd; i += LS_THREADS) SL[i] = 0;
   for (uint32_t i = threadIdx.x; i < k; i += LS_THREADS) C[i] = 0;
   __syncthreads();
   const float scale = ldexpf(1.f, *shift);
@@ -744,16 +756,126 @@ __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_kernel(const float
 #pragma unroll
         for (int u = 0; u < LS_ROWS; ++u) {
           if (rr + u >= nr) break;  // warp-uniform
-          const uint64_t b = (uint64_t)c[u] * d;
-          if (dj0 < d) atomicAdd(&S[b + dj0], (unsigned long long)rint_i64(v[u][0] * scale));
-          if (dj1 < d) atomicAdd(&S[b + dj1], (unsigned long long)rint_i64(v[u][1] * scale));
+          const uint32_t b = c[u] * d;
+          if (dj0 < d) add64_split(SL + b + dj0, SH + b + dj0, rint_i64(v[u][0] * scale));
+          if (dj1 < d) add64_split(SL + b + dj1, SH + b + dj1, rint_i64(v[u][1] * scale));
         }
       }
     }
   }
   __syncthreads();
   long long* P = part + (uint64_t)blockIdx.x * kd;
-  for (uint64_t i = threadIdx.x; i < kd; i += LS_THREADS) P[i] = (long long)S[i];
+  for (uint64_t i = threadIdx.x; i < kd; i += LS_THREADS)
+    P[i] = (long long)(((unsigned long long)SH[i] << 32) | SL[i]);
+  for (uint32_t i = threadIdx.x; i < k; i += LS_THREADS)
+    if (C[i]) atomicAdd(counts + i, (unsigned long long)C[i]);
+}
+
+// Pipelined form of the local-array update, for rows of a multiple of 4
+// floats starting 16-byte aligned: thread 0 streams chunks of `rows`
+// consecutive points and their cluster ids into an LP_ST-deep shared-memory
+// ring with bulk copies (completion counted on one mbarrier per stage), so
+// loads stay in flight while the warps add earlier chunks; warp w takes rows
+// w, w + 32, ... of a chunk and then releases the stage on a second mbarrier,
+// which thread 0 waits on before refilling the stage.  Every wait is bounded;
+// on timeout the CTA stops once its copies have landed and counts itself in
+// *timeouts.
+constexpr int LP_ST = 3;
+constexpr uint32_t LP_CHUNK_MAX = 24 * 1024;  // bytes of points per stage, at most
+__host__ __device__ constexpr uint64_t lp_fixed_bytes(uint64_t kd, uint64_t k) {
+  return (((2 * kd + k) * 4 + 127) & ~127ull) + 2 * LP_ST * 8 + 16;
+}
+template <bool D64>
+__global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_pipe_kernel(
+    const float* __restrict__ x, uint32_t n, uint32_t d, uint32_t k, const int32_t* __restrict__ assign,
+    const int* shift, long long* __restrict__ part, unsigned long long* counts, uint32_t rows,
+    unsigned long long* timeouts) {
+  using namespace pipe;
+  extern __shared__ __align__(128) unsigned char lp_sm[];
+  const uint64_t kd = (uint64_t)k * d;
+  uint32_t* SL = reinterpret_cast<uint32_t*>(lp_sm);
+  uint32_t* SH = SL + kd;
+  unsigned int* C = SH + kd;
+  float* xs = reinterpret_cast<float*>(lp_sm + (((2 * kd + k) * 4 + 127) & ~127ull));
+  const uint64_t xst = (uint64_t)rows * d;  // floats per stage
+  int32_t* as = reinterpret_cast<int32_t*>(xs + LP_ST * xst);
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(as + LP_ST * rows);
+  unsigned long long* empty = full + LP_ST;
+  volatile int* err = reinterpret_cast<volatile int*>(empty + LP_ST);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // a CTA's range is a whole number of chunks, so every chunk starts 16-byte aligned
+  const uint64_t per = ((((uint64_t)n + gridDim.x - 1) / gridDim.x + rows - 1) / rows) * rows;
+  const uint64_t p0 = (uint64_t)blockIdx.x * per;
+  const uint64_t p1 = p0 + per < (uint64_t)n ? p0 + per : (uint64_t)n;
+  const uint32_t nchunks = p0 < p1 ? (uint32_t)((p1 - p0 + rows - 1) / rows) : 0u;
+  for (uint64_t i = threadIdx.x; i < 2 * kd; i += LS_THREADS) SL[i] = 0;
+  for (uint32_t i = threadIdx.x; i < k; i += LS_THREADS) C[i] = 0;
+  if (threadIdx.x == 0) {
+    *err = 0;
+    for (int q = 0; q < LP_ST; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], LS_THREADS / 32);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t issued = 0;  // thread 0: chunks whose copies were started
+  auto issue = [&](uint32_t c) {
+    const uint32_t q = c % LP_ST;
+    const uint64_t r0 = p0 + (uint64_t)c * rows;
+    const uint32_t nr = (uint32_t)(p1 - r0 < rows ? p1 - r0 : rows);
+    const uint32_t xb = nr * d * 4, ab = ((nr + 3) & ~3u) * 4;  // ids rounded up to 16 bytes (buffer padding)
+    mbar_expect_tx(&full[q], xb + ab);
+    bulk_g2s(xs + q * xst, x + r0 * d, xb, &full[q]);
+    bulk_g2s(as + q * rows, assign + r0, ab, &full[q]);
+    issued = c + 1;
+  };
+  if (threadIdx.x == 0)
+    for (uint32_t c = 0; c < nchunks && c < (uint32_t)LP_ST; ++c) issue(c);
+  const float scale = ldexpf(1.f, *shift);
+  uint32_t c = 0;
+  for (; c < nchunks; ++c) {
+    const uint32_t q = c % LP_ST, par = (c / LP_ST) & 1u;
+    if (!mbar_wait(&full[q], par, err)) break;
+    const uint64_t r0 = p0 + (uint64_t)c * rows;
+    const uint32_t nr = (uint32_t)(p1 - r0 < rows ? p1 - r0 : rows);
+    const float* X = xs + q * xst;
+    const int32_t* A = as + q * rows;
+    for (uint32_t j = warp; j < nr; j += LS_THREADS / 32) {
+      const int a = A[j];
+      const uint32_t cl = (a < 0 || (uint32_t)a >= k) ? 0u : (uint32_t)a;
+      if (lane == 0) atomicAdd(&C[cl], 1u);
+      if (D64) {  // lane holds dimensions lane and lane + 32
+        const float* row = X + j * 64u;
+        const uint32_t b = cl * 64u + lane;
+        const long long q0 = rint_i64(row[lane] * scale), q1 = rint_i64(row[lane + 32] * scale);
+        add64_split(SL + b, SH + b, q0);
+        add64_split(SL + b + 32, SH + b + 32, q1);
+      } else {
+        const float* row = X + (uint64_t)j * d;
+        const uint32_t b = cl * d;
+        for (uint32_t dj = lane; dj < d; dj += 32) add64_split(SL + b + dj, SH + b + dj, rint_i64(row[dj] * scale));
+      }
+    }
+    fence_proxy_async();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[q]);
+    if (threadIdx.x == 0 && c + LP_ST < nchunks) {
+      if (!mbar_wait(&empty[q], par, err)) break;
+      issue(c + LP_ST);
+    }
+  }
+  if (threadIdx.x == 0 && *err) {
+    // let the copies still in flight land before the CTA leaves
+    for (uint32_t w = c; w < issued; ++w)
+      for (long long i = 0; i < SPIN_LIMIT && !mbar_try(&full[w % LP_ST], (w / LP_ST) & 1u); ++i) {
+      }
+    atomicAdd(timeouts, 1ull);
+  }
+  __syncthreads();
+  long long* P = part + (uint64_t)blockIdx.x * kd;
+  for (uint64_t i = threadIdx.x; i < kd; i += LS_THREADS)
+    P[i] = (long long)(((unsigned long long)SH[i] << 32) | SL[i]);
   for (uint32_t i = threadIdx.x; i < k; i += LS_THREADS)
     if (C[i]) atomicAdd(counts + i, (unsigned long long)C[i]);
 }
@@ -823,7 +945,7 @@ inline uint64_t a256(uint64_t x) { return (x + 255) & ~255ull; }
 size_t km_scratch_bytes(uint32_t n, uint32_t d, uint32_t k, int precision) {
   uint64_t b = 0;
   b += a256((uint64_t)k * d * 4);      // cent
-  b += a256((uint64_t)n * 4);          // assign
+  b += a256((uint64_t)n * 4 + 16);     // assign (+16: the update copies ids in 16-byte units)
   b += a256((uint64_t)k * d * 8);      // sums
   b += a256((uint64_t)k * 8);          // counts
   b += a256(4 * 8);                    // stats
@@ -846,7 +968,7 @@ cudaError_t km_carve(KmBuffers& b, uint8_t* p, size_t bytes) {
   uint8_t* q = p;
   auto take = [&](uint64_t sz) { uint8_t* r = q; q += a256(sz); return r; };
   b.cent = reinterpret_cast<float*>(take(k * d * 4));
-  b.assign = reinterpret_cast<int32_t*>(take(n * 4));
+  b.assign = reinterpret_cast<int32_t*>(take(n * 4 + 16));
   b.sums = reinterpret_cast<long long*>(take(k * d * 8));
   b.counts = reinterpret_cast<unsigned long long*>(take(k * 8));
   b.stats = reinterpret_cast<unsigned long long*>(take(32));
@@ -903,6 +1025,25 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
   if (local && (e = cudaFuncSetAttribute(km_local_sum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          ls_bytes)) != cudaSuccess)
     return e;
+  // pipelined update: rows of a multiple of 4 floats, 16-byte aligned points, and a ring of >= 4 rows a stage
+  uint32_t lp_rows = 0;
+  int lp_bytes = 0;
+  if (local && d % 4 == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+    const uint64_t fixed = lp_fixed_bytes((uint64_t)k * d, k);
+    const uint64_t avail = (uint64_t)di.smem_optin > fixed ? (uint64_t)di.smem_optin - fixed : 0;
+    uint64_t r = avail / LP_ST / ((uint64_t)d * 4 + 4);
+    if (r > LP_CHUNK_MAX / ((uint64_t)d * 4)) r = LP_CHUNK_MAX / ((uint64_t)d * 4);
+    r &= ~3ull;
+    if (r >= 4) {
+      lp_rows = (uint32_t)r;
+      lp_bytes = (int)(fixed + LP_ST * r * ((uint64_t)d * 4 + 4));
+      if ((e = cudaFuncSetAttribute(km_local_sum_pipe_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    lp_bytes)) != cudaSuccess ||
+          (e = cudaFuncSetAttribute(km_local_sum_pipe_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    lp_bytes)) != cudaSuccess)
+        return e;
+    }
+  }
   uint32_t ls_grid = (uint32_t)di.sms < LS_MAX_CTAS ? (uint32_t)di.sms : LS_MAX_CTAS;
   if ((uint64_t)ls_grid * 1024 > n) ls_grid = (uint32_t)((n + 1023) / 1024);
   if (ls_grid < 1) ls_grid = 1;
@@ -934,7 +1075,12 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
     else
       km_recheck_fp64_kernel<<<di.sms * 4, 256, 0, s>>>(x, d, b.cent, k, b.flagged, b.nflag, b.assign, b.stats + 1);
     if (local) {  // update with local arrays
-      km_local_sum_kernel<<<ls_grid, LS_THREADS, ls_bytes, s>>>(x, n, d, k, b.assign, shift, b.part, b.counts);
+      if (lp_rows)
+        (d == 64 ? km_local_sum_pipe_kernel<true> : km_local_sum_pipe_kernel<false>)<<<ls_grid, LS_THREADS, lp_bytes,
+                                                                                        s>>>(
+            x, n, d, k, b.assign, shift, b.part, b.counts, lp_rows, b.stats + 3);
+      else
+        km_local_sum_kernel<<<ls_grid, LS_THREADS, ls_bytes, s>>>(x, n, d, k, b.assign, shift, b.part, b.counts);
       km_reduce_finalize_kernel<<<(unsigned)(((uint64_t)k * d + 31) / 32), RF_THREADS, 0, s>>>(
           b.part, ls_grid, b.cent, k, d, b.counts, shift, cmax_bits);
       *nk += 4;

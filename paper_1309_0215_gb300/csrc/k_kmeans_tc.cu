@@ -45,6 +45,7 @@
 // FP64), so assignments equal the FP64 argmin.
 #include <cuda_bf16.h>
 
+#include "dev_pipe.cuh"
 #include "mr_internal.h"
 
 namespace mrgb {
@@ -64,8 +65,6 @@ constexpr int STAGES = 2;         // operand stages
 constexpr int XST = 2;            // FP32 staging buffers filled by the bulk copy engine
 constexpr int ACCS = 2;           // TMEM accumulators
 constexpr uint32_t TMEM_COLS = 512;  // two 256-column FP32 accumulators
-constexpr long long SPIN_LIMIT = 1ll << 20;
-constexpr uint32_t SUSPEND_NS = 1000;  // a waiting thread sleeps up to this long per poll
 constexpr int NSET = 8;           // independent running top-2s per epilogue thread
 constexpr int CHUNK = 32;         // TMEM columns per tcgen05.ld in the epilogue
 
@@ -89,50 +88,8 @@ struct __align__(1024) TcSmem {
 
 static_assert(sizeof(TcSmem) + 1024 <= 232448, "shared memory of one CTA");
 
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+using namespace pipe;
 
-__device__ __forceinline__ void mbar_init(unsigned long long* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
-}
-// Poll for the completion of the phase with the given parity; the thread is
-// suspended until the phase completes or SUSPEND_NS elapse, so waiting warps
-// do not take issue slots from the working ones.
-__device__ __forceinline__ bool mbar_try(unsigned long long* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(su32(b)), "r"(parity), "r"(SUSPEND_NS)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait (at most SPIN_LIMIT polls of at most SUSPEND_NS each, about a
-// second) for the completion of the phase with the given parity.
-__device__ bool mbar_wait(unsigned long long* b, uint32_t parity, volatile int* err) {
-  for (long long i = 0; i < SPIN_LIMIT; ++i) {
-    if (mbar_try(b, parity)) return true;
-    if ((i & 15) == 15 && *err) return false;
-  }
-  *err = 1;
-  return false;
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-// One contiguous global -> shared copy by the bulk copy engine; completion is
-// signalled as transaction bytes on the mbarrier.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* b) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(dst)),
-      "l"(src), "r"(bytes), "r"(su32(b))
-      : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -273,7 +230,7 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
       mbar_init(&S.tempty[q], CVT_WARPS);
     }
     mbar_init(&S.drained, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_mbar_init();
   }
   if (warp == MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&S.tmem_base)),

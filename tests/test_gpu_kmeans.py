@@ -50,6 +50,21 @@ def test_kmeans_fp32_vs_oracle(mr, n, d, k, iters):
     assert int(stats[2]) == iters
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_kmeans_points_not_16_byte_aligned(mr, precision):
+    """Points 4 bytes into a buffer: the update cannot stream them with bulk
+    copies and takes the plain local-array kernel."""
+    import torch
+    x, _, _ = synth.kmeans_points(5000, 64, 32, seed=51)
+    init = synth.kmeans_init(x, 32, seed=52)
+    buf = torch.zeros(x.size + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = torch.from_numpy(x.ravel()).cuda()
+    c_ref, a_ref = oracle.kmeans(x, init, 3)
+    c, a, stats = mr.kmeans(buf[1:].view(5000, 64), _dev(init), 3, precision)
+    assert np.array_equal(a, a_ref)
+    assert _rel_err(c, c_ref) <= TOL
+
+
 def test_kmeans_host_inputs(mr):
     x, _, _ = synth.kmeans_points(4096, 32, 64, seed=5)
     init = synth.kmeans_init(x, 64, seed=6)
