@@ -128,9 +128,29 @@ struct mr_ctx {
   Slot slots[SERVE_SLOTS];
   std::vector<Job*> serve_pending;  // admitted, waiting for a free slot
   cudaEvent_t serve_ready = nullptr;
+  // plain runs: jobs after the first run concurrently on these streams,
+  // forked from and joined back into the context stream
+  static constexpr int PLAIN_AUX = 3;
+  cudaStream_t plain_aux[PLAIN_AUX] = {};
+  cudaEvent_t plain_fork = nullptr;
+  cudaEvent_t plain_join[PLAIN_AUX] = {};
+  // CUDA events and kernel timers of released (finished) jobs, reused by
+  // later jobs so that adding a job creates none in the steady state
+  std::vector<cudaEvent_t> ev_done, ev_timing;
+  std::vector<KTimer*> kt_pool;
 };
 
 namespace {
+
+cudaError_t pooled_event(mr_ctx* c, bool timing, cudaEvent_t* e) {
+  std::vector<cudaEvent_t>& pool = timing ? c->ev_timing : c->ev_done;
+  if (!pool.empty()) {
+    *e = pool.back();
+    pool.pop_back();
+    return cudaSuccess;
+  }
+  return timing ? cudaEventCreate(e) : cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+}
 
 struct DeviceGuard {
   int prev = -1;
@@ -377,11 +397,13 @@ mr_status alloc_job_memory(mr_ctx* c, Job* j) {
   return MR_EINVAL;
 }
 
+// A job is freed only once it has finished (mr_release waits for it), so its
+// events can go back to the context's pools.
 void free_job(mr_ctx* c, Job* j) {
-  if (j->done) cudaEventDestroy(j->done);
-  if (j->t0) cudaEventDestroy(j->t0);
-  if (j->t1) cudaEventDestroy(j->t1);
-  kt_destroy(j->kt);
+  if (j->done) c->ev_done.push_back(j->done);
+  if (j->t0) c->ev_timing.push_back(j->t0);
+  if (j->t1) c->ev_timing.push_back(j->t1);
+  if (j->kt) c->kt_pool.push_back(j->kt);
   dev_free(c, j->slab, j->slab_bytes);
   dev_free(c, j->in_owned, j->in_owned_bytes);
   delete j;
@@ -462,6 +484,41 @@ mr_status enqueue_plain_on(mr_ctx* c, Job* j, cudaStream_t st) {
 }
 
 mr_status enqueue_plain(mr_ctx* c, Job* j) { return enqueue_plain_on(c, j, c->stream); }
+
+// The jobs of one plain run are independent (each has its own input,
+// containers and result), so they run concurrently: the first on the
+// context stream, the others round robin on PLAIN_AUX internal streams that
+// wait for the work already on the context stream; the context stream then
+// waits for them, so later work on it (and the next run) sees every job done.
+// Two bandwidth-bound jobs overlap their ramp-up and tail this way.
+mr_status enqueue_plain_all(mr_ctx* c, const std::vector<Job*>& jobs) {
+  if (jobs.size() <= 1) {
+    for (Job* j : jobs) {
+      mr_status st = enqueue_plain(c, j);
+      if (st) return st;
+    }
+    return MR_OK;
+  }
+  if (!c->plain_fork) {
+    MR_CUDA_TRY(cudaEventCreateWithFlags(&c->plain_fork, cudaEventDisableTiming));
+    for (int a = 0; a < mr_ctx::PLAIN_AUX; ++a) {
+      MR_CUDA_TRY(cudaStreamCreateWithFlags(&c->plain_aux[a], cudaStreamNonBlocking));
+      MR_CUDA_TRY(cudaEventCreateWithFlags(&c->plain_join[a], cudaEventDisableTiming));
+    }
+  }
+  MR_CUDA_TRY(cudaEventRecord(c->plain_fork, c->stream));
+  const int used = (int)(jobs.size() - 1 < (size_t)mr_ctx::PLAIN_AUX ? jobs.size() - 1 : mr_ctx::PLAIN_AUX);
+  for (int a = 0; a < used; ++a) MR_CUDA_TRY(cudaStreamWaitEvent(c->plain_aux[a], c->plain_fork, 0));
+  for (size_t i = 0; i < jobs.size(); ++i) {
+    mr_status st = enqueue_plain_on(c, jobs[i], i == 0 ? c->stream : c->plain_aux[(i - 1) % mr_ctx::PLAIN_AUX]);
+    if (st) return st;
+  }
+  for (int a = 0; a < used; ++a) {
+    MR_CUDA_TRY(cudaEventRecord(c->plain_join[a], c->plain_aux[a]));
+    MR_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->plain_join[a], 0));
+  }
+  return MR_OK;
+}
 
 mr_status ensure_scratch(mr_ctx* c, void** p, uint64_t* have, uint64_t need) {
   need = align256(need ? need : 256);
@@ -824,11 +881,16 @@ mr_status add_job_impl(mr_ctx* c, const mr_job_desc* desc, uint64_t* job_id) {
   if (!j) return MR_ENOMEM;
   j->desc = *desc;
   j->container = plan_container(c, desc);
-  cudaError_t e = cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming);
+  cudaError_t e = pooled_event(c, false, &j->done);
   if (e == cudaSuccess && (c->flags & MR_FLAG_TIMING)) {
-    e = cudaEventCreate(&j->t0);
-    if (e == cudaSuccess) e = cudaEventCreate(&j->t1);
-    if (e == cudaSuccess && !(j->kt = new (std::nothrow) KTimer())) e = cudaErrorMemoryAllocation;
+    e = pooled_event(c, true, &j->t0);
+    if (e == cudaSuccess) e = pooled_event(c, true, &j->t1);
+    if (e == cudaSuccess && !c->kt_pool.empty()) {
+      j->kt = c->kt_pool.back();
+      c->kt_pool.pop_back();
+    } else if (e == cudaSuccess && !(j->kt = new (std::nothrow) KTimer())) {
+      e = cudaErrorMemoryAllocation;
+    }
   }
   if (e != cudaSuccess) {
     set_last_error("cudaEventCreate", e);
@@ -962,6 +1024,17 @@ void mr_destroy(mr_ctx* c) {
     }
   }
   if (c->serve_ready) cudaEventDestroy(c->serve_ready);
+  for (int a = 0; a < mr_ctx::PLAIN_AUX; ++a) {
+    if (c->plain_aux[a]) {
+      cudaStreamSynchronize(c->plain_aux[a]);
+      cudaStreamDestroy(c->plain_aux[a]);
+    }
+    if (c->plain_join[a]) cudaEventDestroy(c->plain_join[a]);
+  }
+  if (c->plain_fork) cudaEventDestroy(c->plain_fork);
+  for (cudaEvent_t e : c->ev_done) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev_timing) cudaEventDestroy(e);
+  for (KTimer* t : c->kt_pool) kt_destroy(t);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -984,11 +1057,7 @@ mr_status mr_run(mr_ctx* c, mr_mode mode) {
   }
   c->pending.clear();
   if (mode == MR_RUN_BATCHED) return enqueue_batched(c, jobs);
-  for (Job* j : jobs) {
-    mr_status st = enqueue_plain(c, j);
-    if (st) return st;
-  }
-  return MR_OK;
+  return enqueue_plain_all(c, jobs);
 }
 
 mr_status mr_fetch(mr_ctx* c, uint64_t job_id, void* buf, uint64_t buf_bytes, uint64_t* needed) {
