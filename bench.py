@@ -239,9 +239,10 @@ def run_ours(args):
         total_bytes = d_px.numel() + d_xy.numel()
 
         def step():
+            # two independent jobs: concurrent launch sequences
             a = ctx.add_job(mr.HIST_RGB8, d_px)
             b = ctx.add_job(mr.LINREG_I8, d_xy)
-            ctx.run()
+            ctx.run(mr.RUN_CONCURRENT)
             return [a, b]
         dominant = ("hist_smem_kernel", ["paper_1309_0215_gb300/csrc/k_array.cu",
                                          "paper_1309_0215_gb300/csrc/dev_array.cuh"], d_px.numel())
@@ -373,7 +374,7 @@ def run_ours(args):
 
         def e2e_step():
             ids = [(k, adders[k](t)) for k, t in pinned.items()]
-            ctx.run()
+            ctx.run(mr.RUN_CONCURRENT)
             for k, j in ids:
                 out_bytes[k] = len(ctx.fetch(j))
                 ctx.release(j)
@@ -594,6 +595,20 @@ def run_batched(args):
     plain_ms = ev0.elapsed_time(ev1)
     for i in small[:8]:
         assert ctx.fetch(ids2[i]) == ctx.fetch(ids[i])
+    for j in ids2:
+        ctx.release(j)
+    # concurrent plain path: the same launch sequences on four streams
+    ids3 = [ctx.add_job(kinds[k], slice_of(k, n, o)[1]) for k, n, o in specs]
+    ctx.sync()
+    ev0.record(stream)
+    w0 = time.perf_counter()
+    ctx.run(mr.RUN_CONCURRENT)
+    ev1.record(stream)
+    ev1.synchronize()
+    conc_wall = time.perf_counter() - w0
+    conc_ms = ev0.elapsed_time(ev1)
+    for i in small[:8]:
+        assert ctx.fetch(ids3[i]) == ctx.fetch(ids[i])
     tune = ctx.tuning()
     ctx.close()
     hbm_peak, _, _, peak_src = _peaks()
@@ -610,6 +625,9 @@ def run_batched(args):
         "plain": {"ms_device": round(plain_ms, 3), "ms_wall": round(1e3 * plain_wall, 3),
                   "jobs_per_s": round(njobs / (max(plain_ms, 1e3 * plain_wall) / 1e3), 1)},
         "speedup_vs_plain": round(max(plain_ms, 1e3 * plain_wall) / ms, 2),
+        "concurrent_plain": {"ms_device": round(conc_ms, 3), "ms_wall": round(1e3 * conc_wall, 3),
+                             "jobs_per_s": round(njobs / (max(conc_ms, 1e3 * conc_wall) / 1e3), 1)},
+        "speedup_vs_concurrent_plain": round(max(conc_ms, 1e3 * conc_wall) / ms, 2),
         "first_run_s_incl_autotune": round(t_first, 3), "tuning": tune, "gpu_launches": int(launches),
     }), flush=True)
 

@@ -97,11 +97,12 @@ typedef enum {
 } mr_container;
 
 typedef enum {
-  MR_RUN_PLAIN = 0,       /* one launch sequence per job; the jobs of one run
-                           * are independent and run concurrently on internal
-                           * streams forked from and joined back into the
-                           * context stream */
-  MR_RUN_BATCHED = 1      /* all pending array/hash jobs in one persistent launch */
+  MR_RUN_PLAIN = 0,       /* one launch sequence per job, in submission order */
+  MR_RUN_BATCHED = 1,     /* all pending array/hash jobs in one persistent launch */
+  MR_RUN_CONCURRENT = 2   /* one launch sequence per job; the jobs of the run
+                           * (independent by construction) run concurrently on
+                           * internal streams forked from and joined back into
+                           * the context stream */
 } mr_mode;
 
 typedef enum {

@@ -128,7 +128,7 @@ struct mr_ctx {
   Slot slots[SERVE_SLOTS];
   std::vector<Job*> serve_pending;  // admitted, waiting for a free slot
   cudaEvent_t serve_ready = nullptr;
-  // plain runs: jobs after the first run concurrently on these streams,
+  // concurrent runs: jobs after the first run on these streams,
   // forked from and joined back into the context stream
   static constexpr int PLAIN_AUX = 3;
   cudaStream_t plain_aux[PLAIN_AUX] = {};
@@ -485,13 +485,13 @@ mr_status enqueue_plain_on(mr_ctx* c, Job* j, cudaStream_t st) {
 
 mr_status enqueue_plain(mr_ctx* c, Job* j) { return enqueue_plain_on(c, j, c->stream); }
 
-// The jobs of one plain run are independent (each has its own input,
-// containers and result), so they run concurrently: the first on the
+// MR_RUN_CONCURRENT: the jobs of a run are independent (each has its own
+// input, containers and result), so they run concurrently: the first on the
 // context stream, the others round robin on PLAIN_AUX internal streams that
 // wait for the work already on the context stream; the context stream then
 // waits for them, so later work on it (and the next run) sees every job done.
 // Two bandwidth-bound jobs overlap their ramp-up and tail this way.
-mr_status enqueue_plain_all(mr_ctx* c, const std::vector<Job*>& jobs) {
+mr_status enqueue_concurrent(mr_ctx* c, const std::vector<Job*>& jobs) {
   if (jobs.size() <= 1) {
     for (Job* j : jobs) {
       mr_status st = enqueue_plain(c, j);
@@ -1048,7 +1048,7 @@ mr_status mr_add_job(mr_ctx* c, const mr_job_desc* desc, uint64_t* job_id) {
 }
 
 mr_status mr_run(mr_ctx* c, mr_mode mode) {
-  if (!c || (mode != MR_RUN_PLAIN && mode != MR_RUN_BATCHED)) return MR_EINVAL;
+  if (!c || (mode != MR_RUN_PLAIN && mode != MR_RUN_BATCHED && mode != MR_RUN_CONCURRENT)) return MR_EINVAL;
   DeviceGuard g(c->device);
   std::vector<Job*> jobs;
   for (uint64_t id : c->pending) {
@@ -1057,7 +1057,12 @@ mr_status mr_run(mr_ctx* c, mr_mode mode) {
   }
   c->pending.clear();
   if (mode == MR_RUN_BATCHED) return enqueue_batched(c, jobs);
-  return enqueue_plain_all(c, jobs);
+  if (mode == MR_RUN_CONCURRENT) return enqueue_concurrent(c, jobs);
+  for (Job* j : jobs) {
+    mr_status st = enqueue_plain(c, j);
+    if (st) return st;
+  }
+  return MR_OK;
 }
 
 mr_status mr_fetch(mr_ctx* c, uint64_t job_id, void* buf, uint64_t buf_bytes, uint64_t* needed) {

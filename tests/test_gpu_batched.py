@@ -67,6 +67,38 @@ def test_batched_mixed_jobs_equal_oracle_and_plain(mr, autotune):
     c.close()
 
 
+def test_concurrent_run_equals_oracle(mr):
+    """MR_RUN_CONCURRENT: the jobs of a run (array, word-count, key-histogram,
+    Bloom and k-means kinds) on forked streams; each result equals the
+    oracle's, and work enqueued after the run on the context stream sees all
+    of them (a second concurrent run over the same inputs gives equal bytes)."""
+    import torch
+    jobs = _mixed_jobs(23, 30, 2 << 20)
+    kinds = {0: mr.WORDCOUNT, 1: mr.HIST_RGB8, 2: mr.LINREG_I8}
+    dev = [torch.from_numpy(np.ascontiguousarray(d)).cuda() for _, d in jobs]
+    keys = synth.keys_u32(1_000_003, 70_000, seed=24)
+    seq = synth.dna(300_000, seed=25)
+    x, _, _ = synth.kmeans_points(4000, 16, 8, seed=26)
+    init = synth.kmeans_init(x, 8, seed=27)
+    c = mr.Context()
+    for rep in range(2):
+        ids = [c.add_job(kinds[k], t) for (k, _), t in zip(jobs, dev)]
+        jk = c.add_job(mr.HIST_U32, keys, hist_bins=65_000)
+        jb = c.add_job(mr.BLOOM_DNA, seq, bloom_kmer=21, bloom_bits=1_000_003, bloom_hashes=4)
+        jm = c.add_job(mr.KMEANS_F32, x, km_dims=16, km_k=8, km_iters=2, km_init=init)
+        c.run(mr.RUN_CONCURRENT)
+        for (k, d), j in zip(jobs, ids):
+            assert c.fetch(j) == _expect(k, d)
+        assert np.array_equal(np.frombuffer(c.fetch(jk), dtype=np.uint64), oracle.hist_u32(keys, 65_000))
+        assert np.array_equal(np.frombuffer(c.fetch(jb), dtype=np.uint8), oracle.bloom_dna(seq, 21, 1_000_003, 4))
+        cent, assign, _ = mr.split_kmeans_result(c.fetch(jm), 4000, 16, 8)
+        _, a_ref = oracle.kmeans(x, init, 2)
+        assert np.array_equal(assign, a_ref)
+        for j in ids + [jk, jb, jm]:
+            c.release(j)
+    c.close()
+
+
 def test_batched_edge_jobs(mr):
     """Empty inputs, one-byte jobs, unaligned device pointers, a hot key and
     jobs whose automatic table overflows inside the batch (re-run at fetch)."""
