@@ -271,6 +271,27 @@ __device__ inline void local_flush(WarpLocal& L, int& occ, const JobDev& J) {
   occ = 0;
 }
 
+__device__ __forceinline__ uint4 shfl_down_u4(const uint4& v, int d) {
+  return make_uint4(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d),
+                    __shfl_down_sync(0xffffffffu, v.z, d), __shfl_down_sync(0xffffffffu, v.w, d));
+}
+__device__ __forceinline__ uint4 shfl_u4(const uint4& v, int src) {
+  return make_uint4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                    __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
+}
+// Bytes [sh, sh + 16) of the 32-byte little-endian window a | b (sh < 16).
+__device__ __forceinline__ uint4 shift_window(const uint4& a, const uint4& b, uint32_t sh) {
+  const uint32_t q = sh >> 2, r = (sh & 3) * 8;
+  // t_i = word i + q of the window, picked without indexing registers
+  const uint32_t t0 = q == 0 ? a.x : q == 1 ? a.y : q == 2 ? a.z : a.w;
+  const uint32_t t1 = q == 0 ? a.y : q == 1 ? a.z : q == 2 ? a.w : b.x;
+  const uint32_t t2 = q == 0 ? a.z : q == 1 ? a.w : q == 2 ? b.x : b.y;
+  const uint32_t t3 = q == 0 ? a.w : q == 1 ? b.x : q == 2 ? b.y : b.z;
+  const uint32_t t4 = q == 0 ? b.x : q == 1 ? b.y : q == 2 ? b.z : b.w;
+  return make_uint4(__funnelshift_r(t0, t1, r), __funnelshift_r(t1, t2, r), __funnelshift_r(t2, t3, r),
+                    __funnelshift_r(t3, t4, r));
+}
+
 // One warp maps and combines the tokens whose first byte lies in segment seg.
 // miss(lane_has_miss, token) is called by all 32 lanes after each round of
 // up to 32 tokens and disposes of the tokens the cache did not take.
@@ -282,13 +303,28 @@ __device__ inline void warp_segment_t(const JobDev& J, uint64_t seg, WarpLocal& 
   const uint64_t n = J.n;
   const uint64_t rem = n - base;
   // stage the segment and its halo; bytes past the input end read as spaces
-  const bool vec = ((reinterpret_cast<uintptr_t>(in) & 15) == 0) && rem >= (uint64_t)BUF;
+  const uintptr_t sa = reinterpret_cast<uintptr_t>(in + base);
   uint4 mine;
-  if (vec) {
-    const uint4* src = reinterpret_cast<const uint4*>(in + base);
+  if (rem >= (uint64_t)BUF && (sa & 15) == 0) {
+    const uint4* src = reinterpret_cast<const uint4*>(sa);
     mine = __ldg(src + lane);
     reinterpret_cast<uint4*>(L.buf)[lane] = mine;
     if (lane < HALO / 16) reinterpret_cast<uint4*>(L.buf)[32 + lane] = __ldg(src + 32 + lane);
+  } else if (rem >= (uint64_t)BUF) {
+    // unaligned input: the 37 aligned words covering the 576 staged bytes
+    // (each holds at least one input byte, so no load leaves the input's
+    // 16-byte blocks), shifted into place; lane l needs words l and l + 1,
+    // lanes 0..3 also words 32 + l and 33 + l for the halo
+    const uint32_t sh = (uint32_t)(sa & 15);
+    const uint4* src = reinterpret_cast<const uint4*>(sa - sh);
+    const uint4 a = __ldg(src + lane);
+    const uint4 e = lane <= HALO / 16 ? __ldg(src + 32 + lane) : make_uint4(0u, 0u, 0u, 0u);
+    uint4 b = shfl_down_u4(a, 1), en = shfl_down_u4(e, 1);
+    const uint4 w32 = shfl_u4(e, 0);
+    if (lane == 31) b = w32;
+    mine = shift_window(a, b, sh);
+    reinterpret_cast<uint4*>(L.buf)[lane] = mine;
+    if (lane < HALO / 16) reinterpret_cast<uint4*>(L.buf)[32 + lane] = shift_window(e, en, sh);
   } else {
     for (uint32_t r = lane; r < (uint32_t)BUF; r += 32) L.buf[r] = r < rem ? in[base + r] : (uint8_t)' ';
     __syncwarp();

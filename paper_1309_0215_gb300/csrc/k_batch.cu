@@ -69,39 +69,50 @@ __device__ __forceinline__ void block_reduce_add5(long long (&acc)[5], long long
   __syncthreads();
 }
 
-// histogram tile [t0, t1) of a job (t0 a multiple of 1536), local arrays
-__device__ void hist_tile_smem(const BatchJob& J, uint64_t t0, uint64_t t1, uint32_t sbase) {
+// Bytes before the first 16-byte aligned address of a job's input (at most n).
+__device__ __forceinline__ uint64_t arr_head(const uint8_t* in, uint64_t n) {
+  const uint64_t h = (16 - ((uintptr_t)in & 15)) & 15;
+  return h < n ? h : n;
+}
+
+// histogram tile with local arrays.  Array tiles are counted from the job's
+// first aligned address B = in + h: [t0, t1) is relative to B (t0 a multiple
+// of 1536), and tile 0 also takes the h head bytes, so every tile streams
+// aligned 128-bit loads whatever the input's alignment.  Byte k of B has
+// channel (h + k) % 3, hence the rotation (h + lane) % 3.
+__device__ void hist_tile_smem(const BatchJob& J, uint64_t h, uint64_t t0, uint64_t t1, bool first, uint32_t sbase) {
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lb = sbase + (lane % BH_COLS) * 4;
   const uint8_t* in = J.in;
-  uint64_t scalar0 = t0;
-  if (((uintptr_t)in & 15) == 0) {
-    const uint32_t rot0 = lane % 3;  // tiles and chunks start at multiples of 3
-    uint32_t cb[3];
+  const uint8_t* B = in + h;
+  const uint32_t rot0 = (uint32_t)((h + lane) % 3);
+  uint32_t cb[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) cb[q] = lb + ((rot0 + q) % 3) * (256u * BH_COLS * 4);
-    const uint64_t c0 = t0 / arr::CHUNK, c1 = c0 + (t1 - t0) / arr::CHUNK;
-    const uint4* vin = reinterpret_cast<const uint4*>(in);
-    uint64_t c = c0 + warp;
-    for (; c + BWARPS < c1; c += BWARPS) {
-      const uint4* p = vin + c * arr::CHUNK_VEC + lane;
-      uint4 a0 = arr::ldg_stream(p), a1 = arr::ldg_stream(p + 32), a2 = arr::ldg_stream(p + 64);
-      arr::hist_vec<0, BH_COLS>(a0, cb);
-      arr::hist_vec<1, BH_COLS>(a1, cb);
-      arr::hist_vec<2, BH_COLS>(a2, cb);
-    }
-    if (c < c1) {
-      const uint4* p = vin + c * arr::CHUNK_VEC + lane;
-      uint4 a0 = arr::ldg_stream(p), a1 = arr::ldg_stream(p + 32), a2 = arr::ldg_stream(p + 64);
-      arr::hist_vec<0, BH_COLS>(a0, cb);
-      arr::hist_vec<1, BH_COLS>(a1, cb);
-      arr::hist_vec<2, BH_COLS>(a2, cb);
-    }
-    scalar0 = c1 * arr::CHUNK;
+  for (int q = 0; q < 3; ++q) cb[q] = lb + ((rot0 + q) % 3) * (256u * BH_COLS * 4);
+  const uint64_t c0 = t0 / arr::CHUNK, c1 = t1 > t0 ? c0 + (t1 - t0) / arr::CHUNK : c0;
+  const uint4* vin = reinterpret_cast<const uint4*>(B);
+  uint64_t c = c0 + warp;
+  for (; c + BWARPS < c1; c += BWARPS) {
+    const uint4* p = vin + c * arr::CHUNK_VEC + lane;
+    uint4 a0 = arr::ldg_stream(p), a1 = arr::ldg_stream(p + 32), a2 = arr::ldg_stream(p + 64);
+    arr::hist_vec<0, BH_COLS>(a0, cb);
+    arr::hist_vec<1, BH_COLS>(a1, cb);
+    arr::hist_vec<2, BH_COLS>(a2, cb);
   }
-  for (uint64_t i = scalar0 + threadIdx.x; i < t1; i += BT)
-    arr::red_shared_add(lb + (uint32_t)(i % 3) * (256u * BH_COLS * 4) + (uint32_t)in[i] * (BH_COLS * 4),
-                        1u);
+  if (c < c1) {
+    const uint4* p = vin + c * arr::CHUNK_VEC + lane;
+    uint4 a0 = arr::ldg_stream(p), a1 = arr::ldg_stream(p + 32), a2 = arr::ldg_stream(p + 64);
+    arr::hist_vec<0, BH_COLS>(a0, cb);
+    arr::hist_vec<1, BH_COLS>(a1, cb);
+    arr::hist_vec<2, BH_COLS>(a2, cb);
+  }
+  // ragged tail of the tile (job offsets h + [c1 * CHUNK, t1)) and, in tile 0, the head [0, h)
+  const uint64_t tail0 = h + c1 * arr::CHUNK, tail1 = t1 > t0 ? h + t1 : tail0;
+  const uint64_t nhead = first ? h : 0;
+  for (uint64_t t = threadIdx.x; t < nhead + (tail1 - tail0); t += BT) {
+    const uint64_t i = t < nhead ? t : tail0 + (t - nhead);
+    arr::red_shared_add(lb + (uint32_t)(i % 3) * (256u * BH_COLS * 4) + (uint32_t)in[i] * (BH_COLS * 4), 1u);
+  }
 }
 
 // histogram tile without local arrays: 64-bit atomics on the global bins
@@ -110,12 +121,15 @@ __device__ void hist_tile_global(const BatchJob& J, uint64_t t0, uint64_t t1) {
   for (uint64_t i = t0 + threadIdx.x; i < t1; i += BT) atomicAdd(bins + (i % 3) * 256 + J.in[i], 1ull);
 }
 
-__device__ void linreg_tile(const BatchJob& J, uint64_t t0, uint64_t t1, long long (&acc)[5]) {
+// Regression tile.  With an even head h the tile is [t0, t1) relative to
+// B = in + h (aligned 128-bit loads of whole pairs; tile 0 also takes the
+// head); an odd-aligned input (h odd) keeps job offsets and reads bytes.
+__device__ void linreg_tile(const BatchJob& J, uint64_t h, uint64_t t0, uint64_t t1, bool first, long long (&acc)[5]) {
   const int8_t* in = reinterpret_cast<const int8_t*>(J.in);
-  uint64_t scalar0 = t0;
-  if (((uintptr_t)in & 15) == 0) {
-    const uint64_t v0 = t0 / 16, v1 = t1 / 16;  // t0 is a multiple of 16
-    const uint4* vin = reinterpret_cast<const uint4*>(in);
+  uint64_t s0 = t0, s1 = t1;  // byte range still to do (job offsets)
+  if ((h & 1) == 0) {
+    const uint64_t v0 = t0 / 16, v1 = t1 > t0 ? t0 / 16 + (t1 - t0) / 16 : v0;  // t0 is a multiple of 16
+    const uint4* vin = reinterpret_cast<const uint4*>(in + h);
     int p[5] = {0, 0, 0, 0, 0};  // at most a tile per flush: far below the int32 limit
     uint64_t v = v0 + threadIdx.x;
     for (; v + BT < v1; v += 2 * BT) {
@@ -130,9 +144,16 @@ __device__ void linreg_tile(const BatchJob& J, uint64_t t0, uint64_t t1, long lo
     }
 #pragma unroll
     for (int i = 0; i < 5; ++i) acc[i] += p[i];
-    scalar0 = v1 * 16;
+    s0 = h + v1 * 16;
+    s1 = t1 > t0 ? h + t1 : s0;
+    if (first) {  // the head pairs [0, h)
+      for (uint64_t i = threadIdx.x; 2 * i < h; i += BT) {
+        const long long x = in[2 * i], y = in[2 * i + 1];
+        acc[0] += x; acc[1] += y; acc[2] += x * x; acc[3] += y * y; acc[4] += x * y;
+      }
+    }
   }
-  for (uint64_t i = scalar0 / 2 + threadIdx.x; 2 * i + 1 < t1 + 1 && 2 * i < t1; i += BT) {
+  for (uint64_t i = s0 / 2 + threadIdx.x; 2 * i + 1 < s1; i += BT) {
     const long long x = in[2 * i], y = in[2 * i + 1];
     acc[0] += x; acc[1] += y; acc[2] += x * x; acc[3] += y * y; acc[4] += x * y;
   }
@@ -212,15 +233,22 @@ batch_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs, uint64_t total_t
       for (uint64_t sg = s0 + (threadIdx.x >> 5); sg < s1; sg += BWARPS) wc::warp_segment(s_jd, sg, L, occ);
     } else {
       const uint64_t t0 = local * arr_tile;
-      const uint64_t t1 = (t0 + arr_tile) < J.n ? t0 + arr_tile : J.n;
-      if (J.kind == MR_HIST_RGB8) {
-        if (cont == MR_C_GLOBAL_ARRAY) hist_tile_global(J, t0, t1);
-        else hist_tile_smem(J, t0, t1, sbase);
+      if (J.kind == MR_HIST_RGB8 && cont == MR_C_GLOBAL_ARRAY) {
+        hist_tile_global(J, t0, (t0 + arr_tile) < J.n ? t0 + arr_tile : J.n);
       } else {
-        // sums reduced per tile: no registers stay reserved across tiles
-        long long acc[5] = {0, 0, 0, 0, 0};
-        linreg_tile(J, t0, t1, acc);
-        block_reduce_add5(acc, static_cast<long long*>(J.out), part);
+        // tiles counted from the first aligned address (odd-aligned regression inputs: from the start)
+        uint64_t h = arr_head(J.in, J.n);
+        if (J.kind == MR_LINREG_I8 && (h & 1)) h = 0;
+        const uint64_t bn = J.n - h;
+        const uint64_t t1 = (t0 + arr_tile) < bn ? t0 + arr_tile : bn;
+        if (J.kind == MR_HIST_RGB8) {
+          hist_tile_smem(J, h, t0, t1, local == 0, sbase);
+        } else {
+          // sums reduced per tile: no registers stay reserved across tiles
+          long long acc[5] = {0, 0, 0, 0, 0};
+          linreg_tile(J, (((uintptr_t)J.in & 1) == 0) ? h : 1, t0, t1, local == 0, acc);
+          block_reduce_add5(acc, static_cast<long long*>(J.out), part);
+        }
       }
     }
   }

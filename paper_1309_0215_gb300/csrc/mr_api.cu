@@ -636,11 +636,15 @@ mr_status autotune_batch(mr_ctx* c, const std::vector<Job*>& jobs) {
   float best_ms = 0.f;
   mr_status st = time_candidate(c, jobs, best, &best_ms);
   if (st) return st;
-  const uint64_t arr_c[] = {1536ull * 32, 1536ull * 128, 1536ull * 512};
-  const uint64_t wc_c[] = {512ull * 32, 512ull * 128, 512ull * 512};
+  // Larger word-count tiles mean fewer job switches per CTA (each switch
+  // flushes and clears the warps' hot-key caches); smaller ones balance
+  // better at the end of a batch.
+  const uint64_t arr_c[] = {1536ull * 32, 1536ull * 128, 1536ull * 512, 1536ull * 2048};
+  const uint64_t wc_c[] = {512ull * 32, 512ull * 128, 512ull * 512, 512ull * 2048, 512ull * 8192};
   const uint64_t hg_c[] = {0, 1ull << 14, 1ull << 17};
+  const int ncand[3] = {4, 5, 3};
   for (int dim = 0; dim < 3; ++dim) {
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < ncand[dim]; ++k) {
       mr_tuning t = best;
       if (dim == 0) t.arr_tile = arr_c[k];
       else if (dim == 1) t.wc_tile = wc_c[k];

@@ -67,6 +67,36 @@ def test_batched_mixed_jobs_equal_oracle_and_plain(mr, autotune):
     c.close()
 
 
+@pytest.mark.parametrize("mode", ["batched", "plain"])
+def test_jobs_on_unaligned_slices(mr, mode):
+    """Jobs that are views at arbitrary byte offsets of one device buffer (as
+    a caller slicing a resident pool passes them): the kernels stream them
+    from their first 16-byte aligned address, with the head and the tail
+    done bytewise.  Sizes span one tile to many; regression offsets are odd
+    and even (an odd-aligned input keeps bytewise pair loads)."""
+    import torch
+    rng = np.random.default_rng(31)
+    text, _, _ = synth.wc_text(12 << 20, nwords=20000, seed=32)
+    px = synth.hist_rgb8(4 << 20, seed=33)
+    xy = synth.linreg_i8(3 << 20, seed=34)
+    pools = [torch.from_numpy(a).cuda() for a in (text, px, xy)]
+    hosts = [text, px, xy]
+    kinds = {0: mr.WORDCOUNT, 1: mr.HIST_RGB8, 2: mr.LINREG_I8}
+    jobs = []
+    for i in range(48):
+        k = i % 3
+        size = int(rng.integers(1000, 3 << 20)) if i % 4 else int(rng.integers(1, 700))
+        size -= size % (1, 3, 2)[k]
+        off = int(rng.integers(0, hosts[k].size - size))
+        jobs.append((k, off, size))
+    c = mr.Context(autotune=False)
+    ids = [c.add_job(kinds[k], pools[k][off: off + n]) for k, off, n in jobs]
+    c.run(mr.RUN_BATCHED if mode == "batched" else mr.RUN_PLAIN)
+    for (k, off, n), j in zip(jobs, ids):
+        assert c.fetch(j) == _expect(k, hosts[k][off: off + n]), (k, off, n)
+    c.close()
+
+
 def test_concurrent_run_equals_oracle(mr):
     """MR_RUN_CONCURRENT: the jobs of a run (array, word-count, key-histogram,
     Bloom and k-means kinds) on forked streams; each result equals the
