@@ -105,7 +105,7 @@ struct mr_ctx {
   cudaGraphExec_t batch_exec = nullptr;
   std::vector<uint64_t> batch_ids;
   uint64_t batch_launches = 0;  // kernels per replay of the graph
-  mr_tuning tune{3ull * 1536 * 128, 512ull * 128, 0, 0.f, 0};
+  mr_tuning tune{1536ull * 512, 512ull * 512, 0, 0.f, 0};  // the autotuner's usual choice on GB300
   // serving: continuous batching over a few internal streams ("slots")
   struct Slot {
     cudaStream_t s = nullptr;

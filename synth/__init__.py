@@ -5,7 +5,7 @@ available, so every job runs on inputs produced here.  This module only
 produces inputs: it holds none of the map/reduce arithmetic, and it is the one
 piece of code that both the oracle and the CUDA path consume.
 
-Recipes (the readings of the workload descriptions are listed in the design doc):
+Recipes:
 
 * word count: 50,000 distinct lowercase words of length 3..12 (letters uniform
   on a..z, duplicates rejected), drawn Zipf(s=1) by rank; single spaces, a
