@@ -256,8 +256,9 @@ struct Post {
   uint32_t* plan;             // [NPASS] bit 0 active, bit 1 source buffer; [NPASS] final buffer
   uint2* runs;                // tie runs longer than FIX_THREAD: {first, length}
   struct KeyRec* kr[2];       // compact keys for the comparison sort of small record sets
-  uint32_t* ss;               // sample sort: [0] buckets; counts, offsets (+ end), cursors (ss_* below)
+  uint32_t* ss;               // sample sort: [0] buckets, [8..) group tickets; counts, offsets (+ end), cursors
   uint32_t* ss_rank;          // sample sort: [S] ranks of the sample
+  struct KeyRec* spl;         // sample sort: the nb - 1 splitters
   uint16_t* bkt;              // sample sort: [R] bucket of each compacted record
 };
 
@@ -513,32 +514,38 @@ __global__ void __launch_bounds__(T) merge_kernel(const R* __restrict__ src, R* 
   }
 }
 
+// Per-block sums of the key lengths; the block that finishes last (a ticket
+// in P.glob[8]) then turns them into an exclusive scan in place.
 __global__ void __launch_bounds__(CB) wc_lensum_kernel(Post P) {
   __shared__ unsigned long long ws[32];
-  const SortRec* recs = P.r1;
-  const uint64_t m = *P.glob;
-  const uint64_t i = (uint64_t)blockIdx.x * CB + threadIdx.x;
-  unsigned long long v = i < m ? recs[i].len : 0;
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long s = 0;
-    for (int w = 0; w < 32; ++w) s += ws[w];
-    P.bsum[blockIdx.x] = s;
-  }
-}
-
-// exclusive scan of the block sums (one CTA)
-__global__ void __launch_bounds__(CB) wc_bscan_kernel(Post P, uint64_t nb) {
   __shared__ unsigned long long carry;
   __shared__ unsigned long long wsum[32];
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
+  __shared__ bool last;
+  const SortRec* recs = P.r1;
+  const uint64_t m = *P.glob;
+  const uint64_t nb = gridDim.x;
+  {
+    const uint64_t i = (uint64_t)blockIdx.x * CB + threadIdx.x;
+    unsigned long long v = i < m ? recs[i].len : 0;
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long s = 0;
+      for (int w = 0; w < 32; ++w) s += ws[w];
+      P.bsum[blockIdx.x] = s;
+      __threadfence();
+      last = atomicAdd(P.glob + 8, 1ull) == nb - 1;
+      carry = 0;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint64_t b = 0; b < nb; b += CB) {
     const uint64_t i = b + threadIdx.x;
-    const unsigned long long v = i < nb ? P.bsum[i] : 0;
+    const unsigned long long v = i < nb ? __ldcg(P.bsum + i) : 0;
     unsigned long long incl = v;
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
@@ -858,9 +865,8 @@ __device__ __forceinline__ bool rtie(const SortRec& a, const SortRec& b) { retur
 
 // Records that tie on (key1, s0) are ordered by the full comparison: a run
 // of up to FIX_THREAD by its first thread; longer ones are listed for
-// wc_rfix_long_kernel (up to SB records: P.runs from the front, count in
-// P.glob[2]) or wc_rfix_huge_kernel (P.runs from the back, count in
-// P.glob[3]).  Every listed run is longer than FIX_THREAD, so both lists
+// wc_rfix_cta_kernel: up to SB records in P.runs from the front (count in
+// P.glob[2]), longer ones from the back (count in P.glob[3]).  Every listed run is longer than FIX_THREAD, so both lists
 // together hold fewer than max_runs entries.
 __global__ void __launch_bounds__(256) wc_rfix_kernel(Post P, const JobDev* jobs, JobDev single, uint64_t max_runs) {
   const uint64_t m = *P.glob;
@@ -999,38 +1005,29 @@ __device__ R* cta_sort(R* r, R* tmp, uint64_t L, R* sh, int cap, const C& cmp) {
   return in;
 }
 
-// One CTA per listed tie run of up to SB records.
-__global__ void __launch_bounds__(SB_THREADS) wc_rfix_long_kernel(Post P, const JobDev* jobs, JobDev single,
-                                                                  uint64_t max_runs) {
+// One CTA per listed tie run: runs of up to SB records (P.runs from the
+// front) by a bitonic sort in shared memory, longer ones (P.runs from the
+// back) by a merge sort with the same place in P.r0 (free once the records
+// are in key order) as scratch.
+__global__ void __launch_bounds__(SB_THREADS) wc_rfix_cta_kernel(Post P, const JobDev* jobs, JobDev single,
+                                                                 uint64_t max_runs) {
   extern __shared__ __align__(16) unsigned char rf_raw[];
   SortRec* sh = reinterpret_cast<SortRec*>(rf_raw);
   const RecCmp cmp{jobs, single, P.src};
-  uint64_t nr = P.glob[2];
-  if (nr > max_runs) nr = max_runs;
-  for (uint64_t k = blockIdx.x; k < nr; k += gridDim.x) {
-    const uint2 run = P.runs[k];
-    SortRec* r = P.r1 + run.x;
-    cta_sort_smem(r, (int)run.y, sh, cmp);
-    for (int i = threadIdx.x; i < (int)run.y; i += blockDim.x) r[i] = sh[i];
-    __syncthreads();
-  }
-}
-
-// One CTA per listed tie run longer than SB, merge-sorted with the same
-// place in P.r0 (free once the records are in key order) as scratch.
-__global__ void __launch_bounds__(SB_THREADS) wc_rfix_huge_kernel(Post P, const JobDev* jobs, JobDev single,
-                                                                  uint64_t max_runs) {
-  extern __shared__ __align__(16) unsigned char rh_raw[];
-  SortRec* sh = reinterpret_cast<SortRec*>(rh_raw);
-  const RecCmp cmp{jobs, single, P.src};
-  uint64_t nr = P.glob[3];
-  if (nr > max_runs) nr = max_runs;
-  for (uint64_t k = blockIdx.x; k < nr; k += gridDim.x) {
-    const uint2 run = P.runs[max_runs - 1 - k];
+  uint64_t nl = P.glob[2], nh = P.glob[3];
+  if (nl > max_runs) nl = max_runs;
+  if (nh > max_runs - nl) nh = max_runs - nl;
+  for (uint64_t k = blockIdx.x; k < nl + nh; k += gridDim.x) {
+    const uint2 run = k < nl ? P.runs[k] : P.runs[max_runs - 1 - (k - nl)];
     SortRec* const home = P.r1 + run.x;
-    const SortRec* res = cta_sort(home, P.r0 + run.x, run.y, sh, SB, cmp);
-    if (res != home)
-      for (uint64_t i = threadIdx.x; i < run.y; i += blockDim.x) home[i] = res[i];
+    if (k < nl) {
+      cta_sort_smem(home, (int)run.y, sh, cmp);
+      for (int i = threadIdx.x; i < (int)run.y; i += blockDim.x) home[i] = sh[i];
+    } else {
+      const SortRec* res = cta_sort(home, P.r0 + run.x, run.y, sh, SB, cmp);
+      if (res != home)
+        for (uint64_t i = threadIdx.x; i < run.y; i += blockDim.x) home[i] = res[i];
+    }
     __syncthreads();
   }
 }
@@ -1054,13 +1051,15 @@ constexpr int SS_SMAX = SS_MAXB * SS_OVER;
 constexpr int SS_RANK_MAX = 1024;
 constexpr int SS_CAP = 2048;  // bitonic tile of the fallback
 constexpr int SS_T = 256;
-constexpr int SS_WORDS = 8 + 3 * SS_MAXB + 1;
+constexpr int SS_HDR = 32;  // [0] buckets, [8, 8 + SS_SMAX / 256) sample-group tickets
+constexpr int SS_WORDS = SS_HDR + 3 * SS_MAXB + 1;
 constexpr int SS_BPT = (SS_MAXB + 255) / 256;  // buckets per thread in the offset scan (256 threads)
 static_assert(SS_MAXB <= 65535 && SS_BPT <= 8, "bucket ids are 16-bit; the offset scan holds SS_BPT counts a thread");
 static_assert(SS_SMAX * 20 <= 227 * 1024, "the ranked sample must fit one CTA's shared memory");
-__device__ __forceinline__ uint32_t* ss_cnt(const Post& P) { return P.ss + 8; }
-__device__ __forceinline__ uint32_t* ss_off(const Post& P) { return P.ss + 8 + SS_MAXB; }  // nb + 1 entries
-__device__ __forceinline__ uint32_t* ss_cur(const Post& P) { return P.ss + 9 + 2 * SS_MAXB; }
+static_assert(8 + SS_SMAX / 256 <= SS_HDR, "one ticket per group of 256 samples");
+__device__ __forceinline__ uint32_t* ss_cnt(const Post& P) { return P.ss + SS_HDR; }
+__device__ __forceinline__ uint32_t* ss_off(const Post& P) { return P.ss + SS_HDR + SS_MAXB; }  // nb + 1 entries
+__device__ __forceinline__ uint32_t* ss_cur(const Post& P) { return P.ss + SS_HDR + 1 + 2 * SS_MAXB; }
 
 __device__ __forceinline__ KeyRec key_of(const SortRec& r, uint64_t i) { return KeyRec{r.key1, r.s0, (uint32_t)i, 0u}; }
 
@@ -1110,8 +1109,11 @@ __device__ __forceinline__ void ss_geometry(uint64_t m, uint64_t& nb, uint64_t& 
 
 // Ranks of the sample (evenly spaced records), counted in SS_PARTS parts:
 // CTA (c, part) ranks samples 256c.. against the part-th slice of the sample
-// and adds to P.ss_rank.  CTA 0 also records the number of buckets.  The
-// bucket counters and rank counters start at zero (cleared with P.glob).
+// and adds to P.ss_rank; the last of a group's SS_PARTS CTAs (a ticket) then
+// holds the group's final ranks and writes the splitters among them:
+// splitter b is the sample of rank ((b + 1) * S) / nb (distinct ranks, as
+// S >= nb).  CTA 0 also records the number of buckets.  Tickets, bucket
+// counters and rank counters start at zero (cleared with P.glob).
 __global__ void __launch_bounds__(256) wc_ss_sample_kernel(Post P) {
   extern __shared__ __align__(16) unsigned char sp_raw[];
   const uint64_t m = P.glob[0];
@@ -1132,6 +1134,18 @@ __global__ void __launch_bounds__(256) wc_ss_sample_kernel(Post P) {
     const uint32_t r = K.rank((int)q0, (int)q1, K.k[j].x, K.k[j].y, K.idx[j]);
     if (r) atomicAdd(&P.ss_rank[j], r);
   }
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&P.ss[8 + c], 1u) == SS_PARTS - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (j < S) {
+    const uint64_t r = __ldcg(P.ss_rank + j);
+    const uint64_t u = (r * nb + S - 1) / S;  // the only candidate b + 1
+    if (u >= 1 && u < nb && (u * S) / nb == r) P.spl[u - 1] = KeyRec{K.k[j].x, K.k[j].y, K.idx[j], 0u};
+  }
 }
 
 // Bucket of each record (number of splitters below its key) and bucket sizes.
@@ -1142,15 +1156,7 @@ __global__ void __launch_bounds__(256) wc_ss_count_kernel(Post P) {
   if ((uint64_t)blockIdx.x * 256 >= m) return;
   uint64_t nb, S;
   ss_geometry(m, nb, S);
-  // splitter b is the sample of rank ((b + 1) * S) / nb (S >= nb: distinct ranks)
-  for (uint64_t j = threadIdx.x; j < S; j += 256) {
-    const uint64_t r = P.ss_rank[j];
-    const uint64_t u = (r * nb + S - 1) / S;  // the only candidate b + 1
-    if (u >= 1 && u < nb && (u * S) / nb == r) {
-      const uint64_t q = ((2 * j + 1) * m) / (2 * S);
-      spl[u - 1] = key_of(P.r0[q], q);
-    }
-  }
+  for (uint64_t t = threadIdx.x; t + 1 < nb; t += 256) spl[t] = P.spl[t];
   for (uint64_t t = threadIdx.x; t < nb; t += 256) cnt[t] = 0u;
   __syncthreads();
   const uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
@@ -1264,7 +1270,7 @@ constexpr uint64_t sortbuf_bytes(uint64_t R) {
          ca256(max_runs(R) * 8) +
          (R >= RADIX_MIN_RECORDS ? 4 * ca256(R * 8) + 2 * ca256(R * 4) + ca256(rtiles(R) * 256 * 4) +
                                        ca256(rchunks(R) * 256 * 4) + 256
-                                 : 2 * ca256(R * sizeof(KeyRec)) + ca256(R * 2));
+                                 : 2 * ca256(R * sizeof(KeyRec)) + ca256(R * 2) + ca256(SS_MAXB * sizeof(KeyRec)));
 }
 
 Post carve_post(uint8_t* p, uint64_t R) {
@@ -1293,6 +1299,8 @@ Post carve_post(uint8_t* p, uint64_t R) {
       p += a256(R * sizeof(KeyRec));
     }
     P.bkt = reinterpret_cast<uint16_t*>(p);
+    p += a256(R * 2);
+    P.spl = reinterpret_cast<KeyRec*>(p);
     return P;
   }
   for (int q = 0; q < 2; ++q) {
@@ -1420,21 +1428,17 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
   // ties on (key1, s0): the full order
   wc_rfix_kernel<<<g256, 256, 0, s>>>(P, jobs, single, max_runs(R));
   const int fx_smem = SB * (int)sizeof(SortRec);
-  if ((e = cudaFuncSetAttribute(wc_rfix_long_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem)) !=
-          cudaSuccess ||
-      (e = cudaFuncSetAttribute(wc_rfix_huge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem)) !=
-          cudaSuccess)
+  if ((e = cudaFuncSetAttribute(wc_rfix_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem)) !=
+      cudaSuccess)
     return e;
-  wc_rfix_long_kernel<<<64, SB_THREADS, fx_smem, s>>>(P, jobs, single, max_runs(R));
-  wc_rfix_huge_kernel<<<16, SB_THREADS, fx_smem, s>>>(P, jobs, single, max_runs(R));
+  wc_rfix_cta_kernel<<<64, SB_THREADS, fx_smem, s>>>(P, jobs, single, max_runs(R));
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  *nk += 4;
+  *nk += 3;
   wc_lensum_kernel<<<(unsigned)nb, CB, 0, s>>>(P);
-  wc_bscan_kernel<<<1, CB, 0, s>>>(P, nb);
   wc_bounds_kernel<<<(unsigned)nb, CB, 0, s>>>(jobs, single, P);
   wc_gather_kernel<<<g256, 256, 0, s>>>(jobs, single, P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  *nk += 4;
+  *nk += 3;
   return cudaSuccess;
 }
 
