@@ -1049,6 +1049,9 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
   if (ls_grid < 1) ls_grid = 1;
   const int rc_bytes = (int)((uint64_t)k * (d + 1) * 4);
   const bool rc_smem = k <= 32 * KLANE && rc_bytes <= di.smem_optin;
+  // as many re-check CTAs per SM as the centroid copies allow (at most 3: 48 warps)
+  int rc_per_sm = rc_smem ? (di.smem_optin + 1024) / (rc_bytes + 1024) : 1;
+  rc_per_sm = rc_per_sm < 1 ? 1 : (rc_per_sm > 3 ? 3 : rc_per_sm);
   if (rc_smem &&
       (e = cudaFuncSetAttribute(km_recheck_fp64_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, rc_bytes)) !=
           cudaSuccess)
@@ -1067,10 +1070,11 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
       if ((e = cudaGetLastError()) != cudaSuccess || (e = kt_end(b.kt, s)) != cudaSuccess) return e;
       ++*nk;
     }
-    km_pair_kernel<<<di.sms * 4, 256, 0, s>>>(x, d, b.cent, b.pairs, b.nflag + 4, b.assign, b.stats + 1);
+    // one warp per pair, latency-bound: a full SM of warps (32 registers a thread)
+    km_pair_kernel<<<di.sms * 8, 256, 0, s>>>(x, d, b.cent, b.pairs, b.nflag + 4, b.assign, b.stats + 1);
     ++*nk;
     if (rc_smem)
-      km_recheck_fp64_smem_kernel<<<di.sms, 512, rc_bytes, s>>>(x, d, b.cent, k, b.flagged, b.nflag, b.assign,
+      km_recheck_fp64_smem_kernel<<<di.sms * rc_per_sm, 512, rc_bytes, s>>>(x, d, b.cent, k, b.flagged, b.nflag, b.assign,
                                                                 b.stats + 1);
     else
       km_recheck_fp64_kernel<<<di.sms * 4, 256, 0, s>>>(x, d, b.cent, k, b.flagged, b.nflag, b.assign, b.stats + 1);
