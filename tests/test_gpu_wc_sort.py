@@ -7,8 +7,9 @@ up to 2048 by one CTA's bitonic sort, and longer runs by one CTA's merge sort
 each; every path must give the oracle's bytes, also with long keys (> 15
 bytes) whose first 16 bytes agree, with several long runs in one job, and
 inside a batch.
-The radix sort runs for record capacities of 2^20 and up (a pinned table of
-2^20 slots here); smaller ones use the comparison sort alone (slots=0)."""
+Record capacities up to 2^17 (automatic tables, slots=0) take the sample
+sort of compact keys, up to 2^20 the block sort + merge passes (slots=2^18),
+from 2^20 on the radix sort (slots=2^20)."""
 import numpy as np
 import pytest
 
@@ -25,21 +26,21 @@ def _text(nwords: int, prefix: bytes, reps: int, seed: int) -> bytes:
     return b" ".join(toks) + b"\n"
 
 
-@pytest.mark.parametrize("slots", [0, 1 << 20])
+@pytest.mark.parametrize("slots", [0, 1 << 18, 1 << 20])
 @pytest.mark.parametrize("nwords", [2, 5, 32, 33, 700, 2048, 2049, 5000])
 def test_tie_runs_short_prefix(mr, nwords, slots):
     raw = _text(nwords, b"abcdefgh", 3, nwords) + b" zz yy zz"
     assert mr.wordcount(raw, wc_slots=slots) == oracle.wordcount(raw)
 
 
-@pytest.mark.parametrize("slots", [0, 1 << 20])
+@pytest.mark.parametrize("slots", [0, 1 << 18, 1 << 20])
 @pytest.mark.parametrize("nwords", [7, 300, 3000])
 def test_tie_runs_long_keys(mr, nwords, slots):
     raw = _text(nwords, b"prefix_shared_by_long_keys_", 2, nwords)
     assert mr.wordcount(raw, wc_slots=slots) == oracle.wordcount(raw)
 
 
-@pytest.mark.parametrize("slots", [0, 1 << 20])
+@pytest.mark.parametrize("slots", [0, 1 << 18, 1 << 20])
 def test_several_huge_tie_runs(mr, slots):
     """Runs of 2049..20000 records (one to four merge passes), three of them
     in one job (counts 1, 2 and 3 keep them apart), plus short runs."""
