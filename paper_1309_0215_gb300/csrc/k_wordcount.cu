@@ -514,34 +514,12 @@ __global__ void __launch_bounds__(T) merge_kernel(const R* __restrict__ src, R* 
   }
 }
 
-// Per-block sums of the key lengths; the block that finishes last (a ticket
-// in P.glob[8]) then turns them into an exclusive scan in place.
-__global__ void __launch_bounds__(CB) wc_lensum_kernel(Post P) {
-  __shared__ unsigned long long ws[32];
+// Exclusive scan of the block sums P.bsum[0..nb) in place, by one CTA.
+__device__ void bsum_scan(Post& P, uint64_t nb) {
   __shared__ unsigned long long carry;
   __shared__ unsigned long long wsum[32];
-  __shared__ bool last;
-  const SortRec* recs = P.r1;
-  const uint64_t m = *P.glob;
-  const uint64_t nb = gridDim.x;
-  {
-    const uint64_t i = (uint64_t)blockIdx.x * CB + threadIdx.x;
-    unsigned long long v = i < m ? recs[i].len : 0;
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned long long s = 0;
-      for (int w = 0; w < 32; ++w) s += ws[w];
-      P.bsum[blockIdx.x] = s;
-      __threadfence();
-      last = atomicAdd(P.glob + 8, 1ull) == nb - 1;
-      carry = 0;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-  }
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint64_t b = 0; b < nb; b += CB) {
     const uint64_t i = b + threadIdx.x;
@@ -570,6 +548,39 @@ __global__ void __launch_bounds__(CB) wc_lensum_kernel(Post P) {
     __syncthreads();
   }
 }
+
+
+// Per-block sums of the key lengths.  With fuse (few blocks) the block that
+// finishes last (a ticket in P.glob[8]) then scans them in place; with many
+// blocks the tickets would serialise on one address, so wc_bscan_kernel does
+// the scan instead.
+__global__ void __launch_bounds__(CB) wc_lensum_kernel(Post P, bool fuse) {
+  __shared__ unsigned long long ws[32];
+  __shared__ bool last;
+  const SortRec* recs = P.r1;
+  const uint64_t m = *P.glob;
+  const uint64_t i = (uint64_t)blockIdx.x * CB + threadIdx.x;
+  unsigned long long v = i < m ? recs[i].len : 0;
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long s = 0;
+    for (int w = 0; w < 32; ++w) s += ws[w];
+    P.bsum[blockIdx.x] = s;
+    if (fuse) {
+      __threadfence();
+      last = atomicAdd(P.glob + 8, 1ull) == gridDim.x - 1;
+    }
+  }
+  __syncthreads();
+  if (!fuse || !last) return;
+  __threadfence();
+  bsum_scan(P, gridDim.x);
+}
+
+__global__ void __launch_bounds__(CB) wc_bscan_kernel(Post P, uint64_t nb) { bsum_scan(P, nb); }
+constexpr uint64_t LENSUM_FUSE_BLOCKS = 4096;
 
 // Exclusive length scan per record; each job's first / end record and the
 // scan at both are stored in the job's state as 64-bit fields 1..4.
@@ -1434,7 +1445,11 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
   wc_rfix_cta_kernel<<<64, SB_THREADS, fx_smem, s>>>(P, jobs, single, max_runs(R));
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   *nk += 3;
-  wc_lensum_kernel<<<(unsigned)nb, CB, 0, s>>>(P);
+  wc_lensum_kernel<<<(unsigned)nb, CB, 0, s>>>(P, nb <= LENSUM_FUSE_BLOCKS);
+  if (nb > LENSUM_FUSE_BLOCKS) {
+    wc_bscan_kernel<<<1, CB, 0, s>>>(P, nb);
+    ++*nk;
+  }
   wc_bounds_kernel<<<(unsigned)nb, CB, 0, s>>>(jobs, single, P);
   wc_gather_kernel<<<g256, 256, 0, s>>>(jobs, single, P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
