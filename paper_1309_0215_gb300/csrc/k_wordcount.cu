@@ -736,7 +736,8 @@ __global__ void __launch_bounds__(RT) wc_rhist_kernel(Post P, int p) {
   P.hist[(uint64_t)blockIdx.x * 256 + threadIdx.x] = h[threadIdx.x];
 }
 
-// Per digit: sum of each chunk of RCHUNK tiles.
+// Per digit and chunk of RCHUNK tiles: the tiles' counts become exclusive
+// prefixes within the chunk (in place), the chunk's sum goes to P.csum.
 __global__ void __launch_bounds__(RT) wc_rscan1_kernel(Post P, int p) {
   if (!(P.plan[p] & 1u)) return;
   const uint64_t m = *P.glob;
@@ -744,8 +745,15 @@ __global__ void __launch_bounds__(RT) wc_rscan1_kernel(Post P, int p) {
   const uint64_t b0 = (uint64_t)blockIdx.x * RCHUNK;
   if (b0 >= ntiles) return;
   const uint64_t b1 = (b0 + RCHUNK) < ntiles ? b0 + RCHUNK : ntiles;
+  uint32_t cnt[RCHUNK];
+#pragma unroll
+  for (int q = 0; q < RCHUNK; ++q) cnt[q] = b0 + q < b1 ? P.hist[(b0 + q) * 256 + threadIdx.x] : 0u;
   uint32_t sum = 0;
-  for (uint64_t b = b0; b < b1; ++b) sum += P.hist[b * 256 + threadIdx.x];
+#pragma unroll
+  for (int q = 0; q < RCHUNK; ++q) {
+    if (b0 + q < b1) P.hist[(b0 + q) * 256 + threadIdx.x] = sum;
+    sum += cnt[q];
+  }
   P.csum[(uint64_t)blockIdx.x * 256 + threadIdx.x] = sum;
 }
 
@@ -783,7 +791,7 @@ __global__ void __launch_bounds__(RT) wc_rscan2_kernel(Post P, int p) {
 // warp, lane).  Per round: lanes with the same digit are found with 8
 // ballots (one per digit bit); each warp's digit counts are prefix-summed
 // over the warps in order, on top of the counts of earlier rounds and of
-// earlier tiles (chunk offset + tiles of the chunk before this one).
+// earlier tiles (chunk offset + the tile's prefix within its chunk).
 __global__ void __launch_bounds__(RT) wc_rscatter_kernel(Post P, int p) {
   __shared__ uint32_t run[256];
   __shared__ uint32_t wh[RT / 32][256];
@@ -795,12 +803,8 @@ __global__ void __launch_bounds__(RT) wc_rscatter_kernel(Post P, int p) {
   if (t0 >= m) return;
   const uint32_t src = (plan >> 1) & 1u, dst = src ^ 1u;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  {
-    const uint64_t c = b / RCHUNK;
-    uint32_t off = P.csum[c * 256 + threadIdx.x];
-    for (uint64_t q = c * RCHUNK; q < b; ++q) off += P.hist[q * 256 + threadIdx.x];
-    run[threadIdx.x] = off;
-  }
+  // chunk offset + this tile's prefix within the chunk
+  run[threadIdx.x] = P.csum[(b / RCHUNK) * 256 + threadIdx.x] + P.hist[b * 256 + threadIdx.x];
   const unsigned below = (1u << lane) - 1u;
   for (int k = 0; k < RIPT; ++k) {
     const uint64_t i = t0 + (uint64_t)k * RT + threadIdx.x;
