@@ -24,20 +24,22 @@
 //  * Global container: open addressing with a 128-bit CAS per new key and an
 //    atomicAdd per combine (see dev_wordcount.cuh).
 //  * Merge + sort: occupied slots of every job are compacted into one record
-//    array and sorted once by (job, count desc, key asc), so a batch of jobs
-//    is ordered by a single launch sequence.  The sort is a stable LSD radix
-//    sort (8-bit digits) on (job/count word, first 8 key bytes); digit
-//    positions that are equal in every key are skipped, decided on the
-//    device so the sequence can be captured in a CUDA graph.  Records that
-//    tie on both words (keys sharing their first 8 bytes and their count)
-//    are then ordered by the full comparison (one thread per short run, one
-//    CTA per run of up to 2048).  A longer tie run switches the whole batch
-//    to the comparison sort kept as a fallback: a shared-memory bitonic sort
-//    of 2048-record blocks, then merge passes whose split points come from a
-//    warp-cooperative 33-way search.  Per-job boundaries and a scan of key
-//    lengths then place each job's records and key bytes in its result:
-//    {u64 n, u64 key bytes; n x {u64 count, u64 key_off, u64 key_len}; key
-//    bytes}.
+//    array and sorted by (job, count desc, key asc), so a batch of jobs is
+//    ordered by a single launch sequence.  The sort path follows the record
+//    capacity: up to 2^17 records a sample sort of compact (job/count word,
+//    first 8 key bytes, index) keys, whose buckets are placed by rank in
+//    shared memory; a batch of jobs whose tables each hold at most 2^17 slots
+//    the same sample sort per job, all jobs side by side (segmented: one
+//    sample, splitter set and bucket range per job); up to 2^20 a bitonic
+//    block sort and merge passes; beyond, a stable LSD radix sort (8-bit
+//    digits) whose digit positions equal in every key are skipped, decided on
+//    the device so the sequence can be captured in a CUDA graph.  Records
+//    that tie on both words (keys sharing their first 8 bytes and their
+//    count) are then ordered by the full comparison (one thread per short
+//    run, one CTA per longer run: bitonic sort up to 2048, merge sort
+//    beyond).  Per-job boundaries and a scan of key lengths then place each
+//    job's records and key bytes in its result: {u64 n, u64 key bytes;
+//    n x {u64 count, u64 key_off, u64 key_len}; key bytes}.
 #include "mr_internal.h"
 #include "dev_wordcount.cuh"
 
@@ -260,6 +262,15 @@ struct Post {
   uint32_t* ss_rank;          // sample sort: [S] ranks of the sample
   struct KeyRec* spl;         // sample sort: the nb - 1 splitters
   uint16_t* bkt;              // sample sort: [R] bucket of each compacted record
+  // segmented sample sort (several jobs sorted side by side, one bucket set
+  // per job); jcur == nullptr outside it
+  struct SegJob* seg;         // [jobs] where each job's records and buckets start
+  uint32_t* jcur;             // [jobs] records compacted per job (cleared with bcnt)
+  uint32_t* bcnt;             // [buckets] records per bucket
+  uint32_t* boff;             // [buckets + 1] first record of each bucket (dense)
+  uint2* bpos;                // [records] bucket and place in the bucket of each record (dense)
+  uint32_t* kidx;             // [records] record indices in bucket order (dense)
+  struct KeyRec* kra;         // [records] keys of a bucket too large to rank (dense)
 };
 
 __device__ __forceinline__ uint64_t bswap64(uint64_t v) {
@@ -324,7 +335,9 @@ __device__ __forceinline__ int block_excl_scan(int v, int* tmp, int& total) {
 
 // Occupied slots of every job -> records.  Block b belongs to the job whose
 // block range contains b.  The first block of a job also zeroes the job's
-// result header (a job with no records keeps {0, 0}).
+// result header (a job with no records keeps {0, 0}).  Records are packed
+// from index 0 for the whole batch, or, for the segmented sort, from the
+// start of each job's own slot range (P.jcur counts them per job).
 __global__ void __launch_bounds__(CB) wc_compact_kernel(const JobDev* jobs, JobDev single, uint32_t njobs, Post P) {
   __shared__ int tmp[33];
   __shared__ unsigned long long blk_base;
@@ -340,7 +353,12 @@ __global__ void __launch_bounds__(CB) wc_compact_kernel(const JobDev* jobs, JobD
   const bool occ = w1 != 0;
   int total;
   const int r = block_excl_scan(occ ? 1 : 0, tmp, total);
-  if (threadIdx.x == 0) blk_base = total ? atomicAdd(P.glob, (unsigned long long)total) : 0ull;
+  if (threadIdx.x == 0) {
+    if (P.jcur)  // segmented sort: the job's records fill the start of its own slot range
+      blk_base = total ? J.blk0 * CB + atomicAdd(P.jcur + j, (uint32_t)total) : 0ull;
+    else
+      blk_base = total ? atomicAdd(P.glob, (unsigned long long)total) : 0ull;
+  }
   __syncthreads();
   if (!occ) return;
   const uint64_t i = blk_base + (uint64_t)r;
@@ -1272,6 +1290,286 @@ __global__ void __launch_bounds__(SS_T) wc_ss_bsort_kernel(Post P) {
   }
 }
 
+// ------------------------------------------- segmented sample sort (batches)
+// A batch of word-count jobs whose tables hold at most SS_MAX_RECORDS slots
+// each is sorted job by job, all jobs side by side: every job gets its own
+// sample, splitters and buckets (the geometry of the one-job sample sort), a
+// bucket never mixes jobs, and the work per record stays that of a sort of at
+// most 2^17 records however many records the batch holds (a radix sort of
+// the whole batch runs a dozen digit passes over all of them).  Compaction
+// puts job j's records at the start of the job's own slot range; the plan
+// then gives each job a dense range (jobs in order) and a range of buckets.
+struct SegJob {
+  uint32_t cbase;  // first record of the job in slot order (compacted records)
+  uint32_t d;      // first record of the job in the dense sorted order
+  uint32_t m;      // records of the job
+  uint32_t nb;     // buckets of the job
+  uint32_t bbase;  // first bucket of the job
+  uint32_t pad[3];
+};
+static_assert(sizeof(SegJob) == 32, "SegJob layout");
+constexpr int SEG_T = 256;
+constexpr int SEG_I = 8;
+constexpr int SEG_TILE = SEG_T * SEG_I;       // dense records per tile of the count and scatter passes
+constexpr int SEG_SAMPLE_T = 512;             // threads of the sample sort
+constexpr int SEG_BI = SS_RANK_MAX / SEG_T;   // records of a ranked bucket per thread
+constexpr int SEG_FB_CAP = 1024;              // bitonic tile of the large-bucket fallback
+constexpr int SEG_BSORT_SMEM = SEG_FB_CAP * (int)sizeof(KeyRec) > soa_bytes(SS_RANK_MAX)
+                                   ? SEG_FB_CAP * (int)sizeof(KeyRec)
+                                   : soa_bytes(SS_RANK_MAX);
+static_assert(SS_MAXB <= SS_BPT * 256, "one CTA of 256 threads scans a job's bucket counts");
+
+// Per-job record counts (P.jcur, from the compaction) -> dense and bucket
+// ranges; one CTA scans the jobs in chunks of CB.  P.glob[0] = records,
+// P.glob[12] = buckets.  Both sums stay below 2^32 (the record indices are
+// 32-bit), so they are scanned as the two halves of one 64-bit word.
+__global__ void __launch_bounds__(CB) wc_seg_plan_kernel(const JobDev* jobs, uint32_t njobs, Post P) {
+  __shared__ unsigned long long ws[33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long carry = 0;
+  for (uint32_t j0 = 0; j0 < njobs; j0 += CB) {
+    const uint32_t j = j0 + threadIdx.x;
+    uint64_t m = 0, nb = 0, S = 0;
+    if (j < njobs) {
+      m = P.jcur[j];
+      ss_geometry(m, nb, S);
+    }
+    const unsigned long long v = (nb << 32) | m;
+    unsigned long long incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) ws[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned long long w = ws[lane];
+      unsigned long long wi = w;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += t;
+      }
+      ws[lane] = wi - w;
+      if (lane == 31) ws[32] = wi;
+    }
+    __syncthreads();
+    const unsigned long long ex = carry + ws[warp] + incl - v;
+    if (j < njobs)
+      P.seg[j] = SegJob{(uint32_t)(jobs[j].blk0 * CB), (uint32_t)ex, (uint32_t)m, (uint32_t)nb, (uint32_t)(ex >> 32),
+                        {0u, 0u, 0u}};
+    carry += ws[32];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    P.glob[0] = carry & 0xffffffffull;
+    P.glob[12] = carry >> 32;
+  }
+}
+
+// Splitters of each job: its sample (S evenly spaced records of the job in
+// slot order, as in the one-job sort) sorted by one CTA with a bitonic
+// network in shared memory; splitter u - 1 is the sample of rank (u * S) / nb.
+__global__ void __launch_bounds__(SEG_SAMPLE_T) wc_seg_sample_kernel(Post P, uint32_t njobs) {
+  extern __shared__ __align__(16) unsigned char sg_raw[];
+  KeyRec* sh = reinterpret_cast<KeyRec*>(sg_raw);
+  for (uint32_t j = blockIdx.x; j < njobs; j += gridDim.x) {
+    const SegJob g = P.seg[j];
+    uint64_t nb, S;
+    ss_geometry(g.m, nb, S);
+    if (nb < 2) continue;
+    int n2 = 1;
+    while (n2 < (int)S) n2 <<= 1;
+    for (int t = threadIdx.x; t < n2; t += SEG_SAMPLE_T) {
+      if (t < (int)S) {
+        const uint64_t q = g.cbase + ((2 * (uint64_t)t + 1) * g.m) / (2 * S);
+        const ulonglong2 kk = *reinterpret_cast<const ulonglong2*>(P.r0 + q);
+        sh[t] = KeyRec{kk.x, kk.y, (uint32_t)q, 0u};
+      } else {
+        sh[t] = KeyCmp::pad();
+      }
+    }
+    __syncthreads();
+    cta_bitonic(sh, n2, KeyCmp{});
+    for (uint64_t u = 1 + threadIdx.x; u < nb; u += SEG_SAMPLE_T) P.spl[g.bbase + u - 1] = sh[(u * S) / nb];
+    __syncthreads();
+  }
+}
+
+// The job that holds dense record k < records: the last job that starts at
+// or before k (a job without records starts where the next one does, so the
+// last one starting there has records).
+__device__ __forceinline__ uint32_t seg_job_of(const SegJob* seg, uint32_t njobs, uint64_t k) {
+  uint32_t lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (seg[mid].d <= k) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Bucket of each record (its job's splitters in shared memory) and its place
+// in the bucket: a CTA counts its records per bucket in shared memory, then
+// reserves each bucket's share with one global atomic whose old value is
+// where the share starts.  A tile of SEG_TILE dense records usually lies in
+// one job; one that spans several takes them one job at a time.
+__global__ void __launch_bounds__(SEG_T) wc_seg_count_kernel(Post P, uint32_t njobs) {
+  __shared__ KeyRec spl[SS_MAXB];
+  __shared__ uint32_t cnt[SS_MAXB];
+  __shared__ uint32_t jfirst;
+  const uint64_t M = P.glob[0];
+  const KeyCmp cmp;
+  for (uint64_t k0 = (uint64_t)blockIdx.x * SEG_TILE; k0 < M; k0 += (uint64_t)gridDim.x * SEG_TILE) {
+    const uint64_t k1 = k0 + SEG_TILE < M ? k0 + SEG_TILE : M;
+    if (threadIdx.x == 0) jfirst = seg_job_of(P.seg, njobs, k0);
+    __syncthreads();
+    uint32_t bk[SEG_I], lr[SEG_I];
+    for (uint32_t j = jfirst; j < njobs; ++j) {
+      const SegJob g = P.seg[j];
+      if (g.d >= k1) break;
+      if (g.m == 0) continue;
+      for (uint32_t t = threadIdx.x; t + 1 < g.nb; t += SEG_T) spl[t] = P.spl[g.bbase + t];
+      for (uint32_t t = threadIdx.x; t < g.nb; t += SEG_T) cnt[t] = 0u;
+      __syncthreads();
+      const uint64_t a = k0 > g.d ? k0 : g.d;
+      const uint64_t b = k1 < (uint64_t)g.d + g.m ? k1 : (uint64_t)g.d + g.m;
+#pragma unroll
+      for (int q = 0; q < SEG_I; ++q) {
+        const uint64_t k = k0 + q * SEG_T + threadIdx.x;
+        if (k >= a && k < b) {
+          const uint64_t i = g.cbase + (k - g.d);
+          const ulonglong2 kk = *reinterpret_cast<const ulonglong2*>(P.r0 + i);
+          const KeyRec key{kk.x, kk.y, (uint32_t)i, 0u};
+          uint32_t lo = 0, hi = g.nb - 1;
+          while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (cmp.less(spl[mid], key)) lo = mid + 1;
+            else hi = mid;
+          }
+          bk[q] = lo;
+          lr[q] = atomicAdd(&cnt[lo], 1u);
+        }
+      }
+      __syncthreads();
+      for (uint32_t t = threadIdx.x; t < g.nb; t += SEG_T)
+        if (cnt[t]) cnt[t] = atomicAdd(P.bcnt + g.bbase + t, cnt[t]);
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < SEG_I; ++q) {
+        const uint64_t k = k0 + q * SEG_T + threadIdx.x;
+        if (k >= a && k < b) P.bpos[k] = make_uint2(g.bbase + bk[q], cnt[bk[q]] + lr[q]);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Bucket offsets, one CTA per job: the job's dense start plus the exclusive
+// scan of its bucket counts; boff[bbase + nb] is the job's end (the next
+// job's start, written by both with the same value).
+__global__ void __launch_bounds__(256) wc_seg_offsets_kernel(Post P, uint32_t njobs) {
+  __shared__ uint32_t wsum[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t j = blockIdx.x; j < njobs; j += gridDim.x) {
+    const SegJob g = P.seg[j];
+    const uint32_t b0 = SS_BPT * threadIdx.x;
+    uint32_t c[SS_BPT], tot = 0;
+#pragma unroll
+    for (int q = 0; q < SS_BPT; ++q) {
+      c[q] = b0 + q < g.nb ? P.bcnt[g.bbase + b0 + q] : 0u;
+      tot += c[q];
+    }
+    uint32_t incl = tot;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    uint32_t ex = g.d + incl - tot;
+    for (int w = 0; w < warp; ++w) ex += wsum[w];
+#pragma unroll
+    for (int q = 0; q < SS_BPT; ++q) {
+      if (b0 + q < g.nb) P.boff[g.bbase + b0 + q] = ex;
+      ex += c[q];
+    }
+    if (threadIdx.x == 0) P.boff[g.bbase + g.nb] = g.d + g.m;
+    __syncthreads();
+  }
+}
+
+// Record indices (slot order) to their places in bucket order.
+__global__ void __launch_bounds__(SEG_T) wc_seg_scatter_kernel(Post P, uint32_t njobs) {
+  __shared__ uint32_t jfirst;
+  const uint64_t M = P.glob[0];
+  for (uint64_t k0 = (uint64_t)blockIdx.x * SEG_TILE; k0 < M; k0 += (uint64_t)gridDim.x * SEG_TILE) {
+    if (threadIdx.x == 0) jfirst = seg_job_of(P.seg, njobs, k0);
+    __syncthreads();
+    uint32_t j = jfirst;
+    SegJob g = P.seg[j];
+#pragma unroll
+    for (int q = 0; q < SEG_I; ++q) {
+      const uint64_t k = k0 + q * SEG_T + threadIdx.x;
+      if (k < M) {
+        while (k >= (uint64_t)g.d + g.m) g = P.seg[++j];
+        const uint2 bp = P.bpos[k];
+        P.kidx[P.boff[bp.x] + bp.y] = g.cbase + (uint32_t)(k - g.d);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Buckets in key order, one bucket at a time per CTA: the bucket's keys go
+// to shared memory and each record is written to the place its rank in the
+// bucket gives (keys are distinct: the index breaks ties).  A bucket over
+// SS_RANK_MAX records (rare with SS_OVER samples per bucket) is sorted by the
+// CTA's bitonic tiles and merge passes on compact keys in P.kra, with the
+// bucket's place in P.r1 as scratch, then gathered.
+__global__ void __launch_bounds__(SEG_T, 4) wc_seg_bsort_kernel(Post P) {
+  extern __shared__ __align__(16) unsigned char sb_raw[];
+  const uint64_t nbk = P.glob[12];
+  for (uint64_t b = blockIdx.x; b < nbk; b += gridDim.x) {
+    const uint32_t o = P.boff[b], L = P.boff[b + 1] - o;
+    if (L <= (uint32_t)SS_RANK_MAX) {
+      KeySoA K(sb_raw, SS_RANK_MAX);
+      uint32_t ix[SEG_BI];
+#pragma unroll
+      for (int q = 0; q < SEG_BI; ++q) {
+        const uint32_t t = threadIdx.x + q * SEG_T;
+        if (t < L) {
+          ix[q] = P.kidx[o + t];
+          const ulonglong2 kk = *reinterpret_cast<const ulonglong2*>(P.r0 + ix[q]);
+          K.put((int)t, KeyRec{kk.x, kk.y, ix[q], 0u});
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < SEG_BI; ++q) {
+        const uint32_t t = threadIdx.x + q * SEG_T;
+        if (t < L) P.r1[o + K.rank(0, (int)L, K.k[t].x, K.k[t].y, ix[q])] = P.r0[ix[q]];
+      }
+      __syncthreads();
+    } else {
+      KeyRec* a = P.kra + o;
+      for (uint32_t t = threadIdx.x; t < L; t += SEG_T) {
+        const uint32_t i = P.kidx[o + t];
+        const ulonglong2 kk = *reinterpret_cast<const ulonglong2*>(P.r0 + i);
+        a[t] = KeyRec{kk.x, kk.y, i, 0u};
+      }
+      __syncthreads();
+      KeyRec* sh = reinterpret_cast<KeyRec*>(sb_raw);
+      const KeyRec* res = cta_sort(a, reinterpret_cast<KeyRec*>(P.r1 + o), L, sh, SEG_FB_CAP, KeyCmp{});
+      if (res != a) {  // the result sits in the bucket's output place: move it out first
+        for (uint32_t t = threadIdx.x; t < L; t += SEG_T) a[t] = res[t];
+        __syncthreads();
+      }
+      for (uint32_t t = threadIdx.x; t < L; t += SEG_T) P.r1[o + t] = P.r0[a[t].idx];
+      __syncthreads();
+    }
+  }
+}
+
 inline uint64_t a256(uint64_t x) { return (x + 255) & ~255ull; }
 
 constexpr uint64_t ca256(uint64_t x) { return (x + 255) & ~255ull; }
@@ -1286,6 +1584,74 @@ constexpr uint64_t sortbuf_bytes(uint64_t R) {
          (R >= RADIX_MIN_RECORDS ? 4 * ca256(R * 8) + 2 * ca256(R * 4) + ca256(rtiles(R) * 256 * 4) +
                                        ca256(rchunks(R) * 256 * 4) + 256
                                  : 2 * ca256(R * sizeof(KeyRec)) + ca256(R * 2) + ca256(SS_MAXB * sizeof(KeyRec)));
+}
+
+// Bytes of the parts every sort path shares (head, record arrays, scans,
+// run list); the path's own arrays follow.
+constexpr uint64_t post_common_bytes(uint64_t R) {
+  return head_bytes(R) + 2 * ca256(R * sizeof(SortRec)) + 2 * ca256(R * 8) + ca256(((R + CB - 1) / CB) * 8) +
+         ca256(max_runs(R) * 8);
+}
+
+// Segmented sample sort of a batch (see SegJob): the decision, made on the
+// host from the jobs' table sizes, and the bucket and sample bounds.
+struct SegGeom {
+  bool on = false;
+  uint64_t nbmax = 0;  // buckets, at most
+  uint64_t smax = 0;   // largest sample of one job
+  uint64_t bytes = 0;  // scratch past post_common_bytes
+};
+
+void host_ss_geometry(uint64_t m, uint64_t& nb, uint64_t& S) {
+  nb = (m + SS_B - 1) / SS_B;
+  nb = nb < 1 ? 1 : (nb > (uint64_t)SS_MAXB ? (uint64_t)SS_MAXB : nb);
+  S = m < nb * SS_OVER ? m : nb * SS_OVER;
+}
+
+uint64_t seg_bytes(uint64_t R, uint64_t njobs, uint64_t nbmax) {
+  return ca256(njobs * sizeof(SegJob)) + ca256((njobs + nbmax) * 4) + ca256((nbmax + 1) * 4) +
+         ca256(nbmax * sizeof(KeyRec)) + ca256(R * 8) + ca256(R * 4) + ca256(R * sizeof(KeyRec));
+}
+
+// Several jobs, more records than the one-job sample sort takes, and every
+// table a whole number of compaction blocks of at most SS_MAX_RECORDS slots
+// laid end to end (job j's slots start at blk0 * CB), so that each job's
+// records have a range of their own and a job's sort is the one-job sort's.
+SegGeom seg_geometry(const JobDev* hjobs, uint32_t njobs, uint64_t R) {
+  SegGeom G;
+  if (njobs < 2 || R <= SS_MAX_RECORDS || R >= (1ull << 32)) return G;
+  uint64_t base = 0;
+  for (uint32_t j = 0; j < njobs; ++j) {
+    const uint64_t cap = hjobs[j].cap;
+    if (cap < (uint64_t)CB || cap > SS_MAX_RECORDS || cap % CB || hjobs[j].blk0 * CB != base) return G;
+    base += cap;
+    uint64_t nb, S;
+    host_ss_geometry(cap, nb, S);
+    G.nbmax += nb;
+    if (S > G.smax) G.smax = S;
+  }
+  if (base != R) return G;
+  G.bytes = seg_bytes(R, njobs, G.nbmax);
+  G.on = post_common_bytes(R) + G.bytes <= sortbuf_bytes(R);
+  return G;
+}
+
+void carve_seg(Post& P, uint8_t* base, uint64_t R, uint32_t njobs, const SegGeom& G) {
+  uint8_t* p = base + post_common_bytes(R);
+  P.seg = reinterpret_cast<SegJob*>(p);
+  p += a256(njobs * sizeof(SegJob));
+  P.jcur = reinterpret_cast<uint32_t*>(p);
+  P.bcnt = P.jcur + njobs;
+  p += a256((njobs + G.nbmax) * 4);
+  P.boff = reinterpret_cast<uint32_t*>(p);
+  p += a256((G.nbmax + 1) * 4);
+  P.spl = reinterpret_cast<KeyRec*>(p);
+  p += a256(G.nbmax * sizeof(KeyRec));
+  P.bpos = reinterpret_cast<uint2*>(p);
+  p += a256(R * 8);
+  P.kidx = reinterpret_cast<uint32_t*>(p);
+  p += a256(R * 4);
+  P.kra = reinterpret_cast<KeyRec*>(p);
 }
 
 Post carve_post(uint8_t* p, uint64_t R) {
@@ -1372,18 +1738,42 @@ wc::JobDev wc_job_dev(const uint8_t* in, uint64_t n, const WcBuffers& b, uint64_
 
 uint64_t wc_compact_blocks(uint64_t cap) { return (cap + CB - 1) / CB; }
 
-cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev& single, uint32_t njobs,
-                                        uint64_t nblocks, uint64_t R, uint8_t* sortbuf, cudaStream_t s,
+cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev* hjobs, uint32_t njobs,
+                                        uint64_t nblocks, uint64_t R, uint8_t* sortbuf, int sms, cudaStream_t s,
                                         uint64_t* nk) {
   cudaError_t e;
+  const JobDev& single = hjobs[0];
   Post P = carve_post(sortbuf, R);
+  const SegGeom G = jobs ? seg_geometry(hjobs, njobs, R) : SegGeom{};
+  if (G.on) carve_seg(P, sortbuf, R, njobs, G);
   if ((e = cudaMemsetAsync(P.glob, 0, head_bytes(R), s)) != cudaSuccess) return e;
+  if (G.on && (e = cudaMemsetAsync(P.jcur, 0, (njobs + G.nbmax) * 4, s)) != cudaSuccess) return e;
   wc_compact_kernel<<<(unsigned)nblocks, CB, 0, s>>>(jobs, single, njobs, P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   ++*nk;
   const uint64_t nb = (R + CB - 1) / CB;
   const unsigned g256 = (unsigned)((R + 255) / 256);
-  if (R <= SS_MAX_RECORDS) {
+  if (G.on) {
+    // segmented sample sort: per-job splitters and buckets, all jobs side by side
+    int n2 = 1;
+    while ((uint64_t)n2 < G.smax) n2 <<= 1;
+    const int sg_smem = n2 * (int)sizeof(KeyRec);
+    if ((e = cudaFuncSetAttribute(wc_seg_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sg_smem)) !=
+        cudaSuccess)
+      return e;
+    const uint64_t tiles = (R + SEG_TILE - 1) / SEG_TILE;
+    const uint64_t gmax = 8ull * (uint64_t)(sms > 0 ? sms : 1);
+    const unsigned gt = (unsigned)(tiles < gmax ? tiles : gmax);
+    const unsigned gb = (unsigned)(G.nbmax < gmax ? G.nbmax : gmax);
+    wc_seg_plan_kernel<<<1, CB, 0, s>>>(jobs, njobs, P);
+    wc_seg_sample_kernel<<<njobs, SEG_SAMPLE_T, sg_smem, s>>>(P, njobs);
+    wc_seg_count_kernel<<<gt, SEG_T, 0, s>>>(P, njobs);
+    wc_seg_offsets_kernel<<<njobs, 256, 0, s>>>(P, njobs);
+    wc_seg_scatter_kernel<<<gt, SEG_T, 0, s>>>(P, njobs);
+    wc_seg_bsort_kernel<<<gb, SEG_T, SEG_BSORT_SMEM, s>>>(P);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    *nk += 6;
+  } else if (R <= SS_MAX_RECORDS) {
     // sample sort of (key1, s0, index) keys; the bucket pass gathers the records
     constexpr int sp_smem = soa_bytes(SS_SMAX);
     constexpr int sb_smem = SS_CAP * (int)sizeof(KeyRec) > soa_bytes(SS_RANK_MAX) ? SS_CAP * (int)sizeof(KeyRec)
@@ -1493,7 +1883,7 @@ cudaError_t launch_wordcount(const uint8_t* in, uint64_t n, const WcBuffers& b, 
     if ((e = cudaGetLastError()) != cudaSuccess || (e = kt_end(kt, s)) != cudaSuccess) return e;
     ++*nk;
   }
-  return launch_wordcount_post_multi(nullptr, J, 1, wc_compact_blocks(b.cap), b.cap, b.sortbuf, s, nk);
+  return launch_wordcount_post_multi(nullptr, &J, 1, wc_compact_blocks(b.cap), b.cap, b.sortbuf, di.sms, s, nk);
 }
 
 }  // namespace mrgb

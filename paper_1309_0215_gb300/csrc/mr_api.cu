@@ -588,8 +588,9 @@ mr_status build_batch_graph(mr_ctx* c, const std::vector<Job*>& jobs, const mr_t
                                static_cast<unsigned long long*>(c->batch_cursor), tp.arr_tile, tp.wc_tile, c->di,
                                c->stream, &nk);
   if (e == cudaSuccess && !wj.empty())
-    e = launch_wordcount_post_multi(static_cast<const wc::JobDev*>(c->batch_wc), wj[0], (uint32_t)wj.size(),
-                                    wc_blocks, wc_records, static_cast<uint8_t*>(c->batch_sort), c->stream, &nk);
+    e = launch_wordcount_post_multi(static_cast<const wc::JobDev*>(c->batch_wc), wj.data(), (uint32_t)wj.size(),
+                                    wc_blocks, wc_records, static_cast<uint8_t*>(c->batch_sort), c->di.sms,
+                                    c->stream, &nk);
   cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
   if (e != cudaSuccess || e2 != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -770,9 +771,10 @@ mr_status serve_pump(mr_ctx* c) {
                              static_cast<unsigned long long*>(slot->cursor), c->tune.arr_tile, c->tune.wc_tile, c->di,
                              slot->s, &c->launches));
     if (!P.wj.empty())
-      MR_CUDA_TRY(launch_wordcount_post_multi(static_cast<const wc::JobDev*>(slot->wcd), P.wj[0],
+      MR_CUDA_TRY(launch_wordcount_post_multi(static_cast<const wc::JobDev*>(slot->wcd), P.wj.data(),
                                               (uint32_t)P.wj.size(), P.wc_blocks, P.wc_records,
-                                              static_cast<uint8_t*>(slot->sort), slot->s, &c->launches));
+                                              static_cast<uint8_t*>(slot->sort), c->di.sms, slot->s,
+                                              &c->launches));
     for (Job* j : arr) {
       if (j->t1) MR_CUDA_TRY(cudaEventRecord(j->t1, slot->s));
       MR_CUDA_TRY(cudaEventRecord(j->done, slot->s));

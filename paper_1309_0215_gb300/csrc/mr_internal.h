@@ -86,10 +86,11 @@ int wc_map_smem_bytes();
 uint64_t wc_compact_blocks(uint64_t cap);
 wc::JobDev wc_job_dev(const uint8_t* in, uint64_t n, const WcBuffers& b, uint64_t blk0);
 // Compaction, sort (by job, count desc, key asc), bounds and gather for
-// njobs jobs (jobs: device array, or nullptr with `single` for one job).
-cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev& single, uint32_t njobs,
-                                        uint64_t nblocks, uint64_t records, uint8_t* sortbuf, cudaStream_t s,
-                                        uint64_t* nk);
+// njobs jobs (jobs: device array, or nullptr for one job; hjobs: the same
+// descriptors in host memory, njobs of them).  sms sizes persistent grids.
+cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev* hjobs, uint32_t njobs,
+                                        uint64_t nblocks, uint64_t records, uint8_t* sortbuf, int sms,
+                                        cudaStream_t s, uint64_t* nk);
 // Zero the table and state, run map+combine, compaction, sort and gather.
 // *nk is incremented by the number of kernels launched.
 // pipelined: the map pass runs as mapper warps handing cache misses to

@@ -9,7 +9,9 @@ bytes) whose first 16 bytes agree, with several long runs in one job, and
 inside a batch.
 Record capacities up to 2^17 (automatic tables, slots=0) take the sample
 sort of compact keys, up to 2^20 the block sort + merge passes (slots=2^18),
-from 2^20 on the radix sort (slots=2^20)."""
+from 2^20 on the radix sort (slots=2^20).  A batch whose tables each hold at
+most 2^17 slots, and more than 2^17 together, is sorted job by job (the
+segmented sample sort: one sample, splitter set and bucket range per job)."""
 import numpy as np
 import pytest
 
@@ -60,7 +62,7 @@ def test_radix_path_on_wordcount_text(mr):
     assert mr.wordcount(text, wc_slots=1 << 20) == oracle.wordcount(text)
 
 
-@pytest.mark.parametrize("slots", [0, 1 << 18])
+@pytest.mark.parametrize("slots", [0, 1 << 16, 1 << 18])
 def test_tie_runs_in_a_batch(mr, slots):
     import torch
     raws = [_text(40, b"qqqqqqqq", 2, 1), _text(2500, b"rrrrrrrr", 1, 2), b"a b a", _text(900, b"ssssssss_", 4, 3)]
@@ -68,6 +70,45 @@ def test_tie_runs_in_a_batch(mr, slots):
     ids = [c.add_job(mr.WORDCOUNT, torch.frombuffer(bytearray(r), dtype=torch.uint8).cuda(), wc_slots=slots)
            for r in raws]
     c.run(mr.RUN_BATCHED)
+    for j, r in zip(ids, raws):
+        assert c.fetch(j) == oracle.wordcount(r)
+    c.close()
+
+
+def test_segmented_sort_many_jobs(mr):
+    """The segmented sample sort over 260 jobs: jobs without records (empty,
+    whitespace only) between others, one-word jobs, tie runs and long keys
+    inside jobs, and slices of Zipf text up to 4 MiB (up to ~500 buckets in
+    a job; tiles of the count and scatter passes that span several jobs)."""
+    import torch
+    import synth
+    text, _, _ = synth.wc_text(8 << 20, nwords=50000, seed=41)
+    rng = np.random.default_rng(42)
+    raws = []
+    for i in range(260):
+        r = i % 13
+        if r == 0:
+            raws.append(b"")
+        elif r == 1:
+            raws.append(b"solo")
+        elif r == 2:
+            raws.append(b"  \n\t ")
+        elif r == 3:
+            raws.append(_text(300 + i, b"tietieti", 2, i))
+        elif r == 4:
+            raws.append(_text(50, b"prefix_shared_by_long_keys_", 3, i))
+        else:
+            n = int(np.exp(rng.uniform(np.log(100), np.log(4 << 20))))
+            off = int(rng.integers(0, text.size - n))
+            raws.append(text[off: off + n].tobytes())
+    c = mr.Context(autotune=False)
+    bufs = [torch.frombuffer(bytearray(r), dtype=torch.uint8).cuda() if r
+            else torch.zeros(0, dtype=torch.uint8, device="cuda") for r in raws]
+    ids = [c.add_job(mr.WORDCOUNT, b) for b in bufs]
+    c.run(mr.RUN_BATCHED)
+    for j, r in zip(ids, raws):
+        assert c.fetch(j) == oracle.wordcount(r)
+    c.rerun()
     for j, r in zip(ids, raws):
         assert c.fetch(j) == oracle.wordcount(r)
     c.close()
