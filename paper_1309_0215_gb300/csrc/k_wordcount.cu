@@ -577,6 +577,7 @@ __global__ void __launch_bounds__(CB) wc_lensum_kernel(Post P, bool fuse) {
   __shared__ bool last;
   const SortRec* recs = P.r1;
   const uint64_t m = *P.glob;
+  if (!fuse && (uint64_t)blockIdx.x * CB >= m) return;
   const uint64_t i = (uint64_t)blockIdx.x * CB + threadIdx.x;
   unsigned long long v = i < m ? recs[i].len : 0;
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -597,7 +598,11 @@ __global__ void __launch_bounds__(CB) wc_lensum_kernel(Post P, bool fuse) {
   bsum_scan(P, gridDim.x);
 }
 
-__global__ void __launch_bounds__(CB) wc_bscan_kernel(Post P, uint64_t nb) { bsum_scan(P, nb); }
+// Blocks past the last record hold no lengths: only the live ones are scanned.
+__global__ void __launch_bounds__(CB) wc_bscan_kernel(Post P, uint64_t nb) {
+  const uint64_t live = (P.glob[0] + CB - 1) / CB;
+  bsum_scan(P, live < nb ? live : nb);
+}
 constexpr uint64_t LENSUM_FUSE_BLOCKS = 4096;
 
 // Exclusive length scan per record; each job's first / end record and the
@@ -1312,11 +1317,7 @@ constexpr int SEG_T = 256;
 constexpr int SEG_I = 8;
 constexpr int SEG_TILE = SEG_T * SEG_I;       // dense records per tile of the count and scatter passes
 constexpr int SEG_SAMPLE_T = 512;             // threads of the sample sort
-constexpr int SEG_BI = SS_RANK_MAX / SEG_T;   // records of a ranked bucket per thread
 constexpr int SEG_FB_CAP = 1024;              // bitonic tile of the large-bucket fallback
-constexpr int SEG_BSORT_SMEM = SEG_FB_CAP * (int)sizeof(KeyRec) > soa_bytes(SS_RANK_MAX)
-                                   ? SEG_FB_CAP * (int)sizeof(KeyRec)
-                                   : soa_bytes(SS_RANK_MAX);
 static_assert(SS_MAXB <= SS_BPT * 256, "one CTA of 256 threads scans a job's bucket counts");
 
 // Per-job record counts (P.jcur, from the compaction) -> dense and bucket
@@ -1522,37 +1523,99 @@ __global__ void __launch_bounds__(SEG_T) wc_seg_scatter_kernel(Post P, uint32_t 
 
 // Buckets in key order, one bucket at a time per CTA: the bucket's keys go
 // to shared memory and each record is written to the place its rank in the
-// bucket gives (keys are distinct: the index breaks ties).  A bucket over
+// bucket gives (keys are distinct: the index breaks ties).  All keys of a
+// bucket belong to one job, so the high word of key1 (job, and the count's
+// bits from 2^32 up) is the same in all of them when every count is below
+// 2^32: the rank then compares 128-bit keys {key1 low word, s0, index} with
+// one shared-memory load each; otherwise 160-bit keys.  A bucket over
 // SS_RANK_MAX records (rare with SS_OVER samples per bucket) is sorted by the
 // CTA's bitonic tiles and merge passes on compact keys in P.kra, with the
 // bucket's place in P.r1 as scratch, then gathered.
-__global__ void __launch_bounds__(SEG_T, 4) wc_seg_bsort_kernel(Post P) {
+__device__ __forceinline__ uint32_t rank128(const uint4* k, int n, uint4 a) {
+  uint32_t r = 0;
+#pragma unroll 4
+  for (int j = 0; j < n; ++j) {
+    const uint4 b = k[j];
+    uint32_t borrow;
+    asm("{\n\t.reg .u32 t;\n\t"
+        "sub.cc.u32 t, %1, %5;\n\t"
+        "subc.cc.u32 t, %2, %6;\n\t"
+        "subc.cc.u32 t, %3, %7;\n\t"
+        "subc.cc.u32 t, %4, %8;\n\t"
+        "subc.u32 %0, 0, 0;\n\t}"
+        : "=r"(borrow)
+        : "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w), "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w));
+    r -= borrow;  // borrow is 0 or 0xffffffff: b < a
+  }
+  return r;
+}
+__device__ __forceinline__ uint32_t rank160(const uint4* k, const uint32_t* hi, int n, uint4 a, uint32_t ah) {
+  uint32_t r = 0;
+#pragma unroll 4
+  for (int j = 0; j < n; ++j) {
+    const uint4 b = k[j];
+    const uint32_t bh = hi[j];
+    uint32_t borrow;
+    asm("{\n\t.reg .u32 t;\n\t"
+        "sub.cc.u32 t, %1, %6;\n\t"
+        "subc.cc.u32 t, %2, %7;\n\t"
+        "subc.cc.u32 t, %3, %8;\n\t"
+        "subc.cc.u32 t, %4, %9;\n\t"
+        "subc.cc.u32 t, %5, %10;\n\t"
+        "subc.u32 %0, 0, 0;\n\t}"
+        : "=r"(borrow)
+        : "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w), "r"(bh), "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(ah));
+    r -= borrow;
+  }
+  return r;
+}
+constexpr int SEG_BT = 128;                      // threads of the bucket pass
+constexpr int SEG_BKEYS = SS_RANK_MAX / SEG_BT;  // keys of a ranked bucket per thread
+constexpr int SEG_BSORT_SMEM = SEG_FB_CAP * (int)sizeof(KeyRec) > SS_RANK_MAX * 20 ? SEG_FB_CAP * (int)sizeof(KeyRec)
+                                                                                  : SS_RANK_MAX * 20;
+__global__ void __launch_bounds__(SEG_BT, 7) wc_seg_bsort_kernel(Post P) {
   extern __shared__ __align__(16) unsigned char sb_raw[];
+  uint4* k4 = reinterpret_cast<uint4*>(sb_raw);                           // {idx, s0 lo, s0 hi, key1 lo}
+  uint32_t* kh = reinterpret_cast<uint32_t*>(sb_raw + SS_RANK_MAX * 16);  // key1 hi
   const uint64_t nbk = P.glob[12];
   for (uint64_t b = blockIdx.x; b < nbk; b += gridDim.x) {
     const uint32_t o = P.boff[b], L = P.boff[b + 1] - o;
     if (L <= (uint32_t)SS_RANK_MAX) {
-      KeySoA K(sb_raw, SS_RANK_MAX);
-      uint32_t ix[SEG_BI];
+      int low = 1;
 #pragma unroll
-      for (int q = 0; q < SEG_BI; ++q) {
-        const uint32_t t = threadIdx.x + q * SEG_T;
+      for (int q = 0; q < SEG_BKEYS; ++q) {
+        const uint32_t t = threadIdx.x + q * SEG_BT;
         if (t < L) {
-          ix[q] = P.kidx[o + t];
-          const ulonglong2 kk = *reinterpret_cast<const ulonglong2*>(P.r0 + ix[q]);
-          K.put((int)t, KeyRec{kk.x, kk.y, ix[q], 0u});
+          const uint32_t i = P.kidx[o + t];
+          const ulonglong2 kk = *reinterpret_cast<const ulonglong2*>(P.r0 + i);
+          k4[t] = make_uint4(i, (uint32_t)kk.y, (uint32_t)(kk.y >> 32), (uint32_t)kk.x);
+          kh[t] = (uint32_t)(kk.x >> 32);
+          low &= (int)((kk.x >> 32) & 0xFFu) == 0xFF;  // count below 2^32
         }
       }
-      __syncthreads();
+      if (__syncthreads_and(low)) {
 #pragma unroll
-      for (int q = 0; q < SEG_BI; ++q) {
-        const uint32_t t = threadIdx.x + q * SEG_T;
-        if (t < L) P.r1[o + K.rank(0, (int)L, K.k[t].x, K.k[t].y, ix[q])] = P.r0[ix[q]];
+        for (int q = 0; q < SEG_BKEYS; ++q) {
+          const uint32_t t = threadIdx.x + q * SEG_BT;
+          if (t < L) {
+            const uint4 a = k4[t];
+            P.r1[o + rank128(k4, (int)L, a)] = P.r0[a.x];
+          }
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < SEG_BKEYS; ++q) {
+          const uint32_t t = threadIdx.x + q * SEG_BT;
+          if (t < L) {
+            const uint4 a = k4[t];
+            P.r1[o + rank160(k4, kh, (int)L, a, kh[t])] = P.r0[a.x];
+          }
+        }
       }
       __syncthreads();
     } else {
       KeyRec* a = P.kra + o;
-      for (uint32_t t = threadIdx.x; t < L; t += SEG_T) {
+      for (uint32_t t = threadIdx.x; t < L; t += SEG_BT) {
         const uint32_t i = P.kidx[o + t];
         const ulonglong2 kk = *reinterpret_cast<const ulonglong2*>(P.r0 + i);
         a[t] = KeyRec{kk.x, kk.y, i, 0u};
@@ -1561,10 +1624,10 @@ __global__ void __launch_bounds__(SEG_T, 4) wc_seg_bsort_kernel(Post P) {
       KeyRec* sh = reinterpret_cast<KeyRec*>(sb_raw);
       const KeyRec* res = cta_sort(a, reinterpret_cast<KeyRec*>(P.r1 + o), L, sh, SEG_FB_CAP, KeyCmp{});
       if (res != a) {  // the result sits in the bucket's output place: move it out first
-        for (uint32_t t = threadIdx.x; t < L; t += SEG_T) a[t] = res[t];
+        for (uint32_t t = threadIdx.x; t < L; t += SEG_BT) a[t] = res[t];
         __syncthreads();
       }
-      for (uint32_t t = threadIdx.x; t < L; t += SEG_T) P.r1[o + t] = P.r0[a[t].idx];
+      for (uint32_t t = threadIdx.x; t < L; t += SEG_BT) P.r1[o + t] = P.r0[a[t].idx];
       __syncthreads();
     }
   }
@@ -1762,15 +1825,15 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
         cudaSuccess)
       return e;
     const uint64_t tiles = (R + SEG_TILE - 1) / SEG_TILE;
-    const uint64_t gmax = 8ull * (uint64_t)(sms > 0 ? sms : 1);
+    const uint64_t gmax = 8ull * (uint64_t)(sms > 0 ? sms : 1), gbmax = 14ull * (uint64_t)(sms > 0 ? sms : 1);
     const unsigned gt = (unsigned)(tiles < gmax ? tiles : gmax);
-    const unsigned gb = (unsigned)(G.nbmax < gmax ? G.nbmax : gmax);
+    const unsigned gb = (unsigned)(G.nbmax < gbmax ? G.nbmax : gbmax);
     wc_seg_plan_kernel<<<1, CB, 0, s>>>(jobs, njobs, P);
     wc_seg_sample_kernel<<<njobs, SEG_SAMPLE_T, sg_smem, s>>>(P, njobs);
     wc_seg_count_kernel<<<gt, SEG_T, 0, s>>>(P, njobs);
     wc_seg_offsets_kernel<<<njobs, 256, 0, s>>>(P, njobs);
     wc_seg_scatter_kernel<<<gt, SEG_T, 0, s>>>(P, njobs);
-    wc_seg_bsort_kernel<<<gb, SEG_T, SEG_BSORT_SMEM, s>>>(P);
+    wc_seg_bsort_kernel<<<gb, SEG_BT, SEG_BSORT_SMEM, s>>>(P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *nk += 6;
   } else if (R <= SS_MAX_RECORDS) {
