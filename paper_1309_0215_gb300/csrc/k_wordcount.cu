@@ -271,6 +271,7 @@ struct Post {
   uint2* bpos;                // [records] bucket and place in the bucket of each record (dense)
   uint32_t* kidx;             // [records] record indices in bucket order (dense)
   struct KeyRec* kra;         // [records] keys of a bucket too large to rank (dense)
+  uint32_t* big;              // [buckets] buckets over one warp's share (count in glob[13])
 };
 
 __device__ __forceinline__ uint64_t bswap64(uint64_t v) {
@@ -1071,24 +1072,23 @@ __global__ void __launch_bounds__(SB_THREADS) wc_rfix_cta_kernel(Post P, const J
 }
 
 // Sample sort of compact keys, for record capacities up to SS_MAX_RECORDS:
-// four launches instead of a block sort and one launch per merge pass.
+// five launches instead of a block sort and one launch per merge pass.
 // Splitters drawn from evenly spaced records of the compacted array (hash
 // order, so effectively a random sample) cut the keys into buckets of about
 // SS_B records; one CTA per bucket then places each key by its rank, the
 // number of smaller keys in the bucket (keys are distinct: the index breaks
-// ties), counted against the bucket held in shared memory; every thread reads
-// the same key at a time, so the reads are broadcasts and the pass needs no
-// barrier.  The sample is ranked the same way.  A bucket over SS_RANK_MAX
-// records (rare with SS_OVER samples per bucket) is sorted by its CTA with
-// bitonic tiles and merge passes.
+// ties), counted against the bucket held in shared memory; every thread
+// reads the same key at a time, so the reads are broadcasts.  The sample is
+// ranked the same way, in parts.  A bucket over SS_RANK_MAX records (rare
+// with SS_OVER samples per bucket) is sorted by its CTA with bitonic tiles
+// and merge passes (the bucket code is shared with the segmented sort,
+// further down).
 constexpr uint64_t SS_MAX_RECORDS = 1ull << 17;
 constexpr int SS_B = 128;
 constexpr int SS_MAXB = (int)(SS_MAX_RECORDS / SS_B);
 constexpr int SS_OVER = 4;
 constexpr int SS_SMAX = SS_MAXB * SS_OVER;
 constexpr int SS_RANK_MAX = 1024;
-constexpr int SS_CAP = 2048;  // bitonic tile of the fallback
-constexpr int SS_T = 256;
 constexpr int SS_HDR = 32;  // [0] buckets, [8, 8 + SS_SMAX / 256) sample-group tickets
 constexpr int SS_WORDS = SS_HDR + 3 * SS_MAXB + 1;
 constexpr int SS_BPT = (SS_MAXB + 255) / 256;  // buckets per thread in the offset scan (256 threads)
@@ -1136,8 +1136,8 @@ struct KeySoA {
     return r;
   }
 };
-constexpr int soa_bytes(int cap) { return cap * 20; }
-constexpr int SS_PARTS = 4;  // the sample's ranks are counted in this many parts
+constexpr int SS_PARTS = 16;  // the sample's ranks are counted in this many parts
+static_assert(SS_SMAX / SS_PARTS <= 256, "a part's slice of the sample fits one slot per thread");
 
 __device__ __forceinline__ void ss_geometry(uint64_t m, uint64_t& nb, uint64_t& S) {
   nb = (m + SS_B - 1) / SS_B;
@@ -1146,14 +1146,15 @@ __device__ __forceinline__ void ss_geometry(uint64_t m, uint64_t& nb, uint64_t& 
 }
 
 // Ranks of the sample (evenly spaced records), counted in SS_PARTS parts:
-// CTA (c, part) ranks samples 256c.. against the part-th slice of the sample
-// and adds to P.ss_rank; the last of a group's SS_PARTS CTAs (a ticket) then
-// holds the group's final ranks and writes the splitters among them:
-// splitter b is the sample of rank ((b + 1) * S) / nb (distinct ranks, as
-// S >= nb).  CTA 0 also records the number of buckets.  Tickets, bucket
-// counters and rank counters start at zero (cleared with P.glob).
-__global__ void __launch_bounds__(256) wc_ss_sample_kernel(Post P) {
-  extern __shared__ __align__(16) unsigned char sp_raw[];
+// CTA (c, part) ranks samples 256c.. (one per thread, held in registers)
+// against the part-th slice of the sample (in shared memory) and adds to
+// P.ss_rank; the last of a group's SS_PARTS CTAs (a ticket) then holds the
+// group's final ranks and writes the splitters among them: splitter b is the
+// sample of rank ((b + 1) * S) / nb (distinct ranks, as S >= nb).  CTA 0
+// also records the number of buckets.  Tickets, bucket counters and rank
+// counters start at zero (cleared with P.glob).
+__global__ void __launch_bounds__(256, 4) wc_ss_sample_kernel(Post P) {
+  __shared__ __align__(16) unsigned char sp_raw[256 * 20];  // KeySoA of 256 keys
   const uint64_t m = P.glob[0];
   uint64_t nb, S;
   ss_geometry(m, nb, S);
@@ -1161,15 +1162,20 @@ __global__ void __launch_bounds__(256) wc_ss_sample_kernel(Post P) {
   if (blockIdx.x == 0 && threadIdx.x == 0) P.ss[0] = (uint32_t)nb;
   if ((uint64_t)c * 256 >= S) return;
   const uint64_t q0 = (S * part) / SS_PARTS, q1 = (S * (part + 1)) / SS_PARTS;
-  KeySoA K(sp_raw, SS_SMAX);
-  for (uint64_t j = threadIdx.x; j < S; j += 256) {
+  KeySoA K(sp_raw, 256);
+  for (uint64_t j = q0 + threadIdx.x; j < q1; j += 256) {
     const uint64_t q = ((2 * j + 1) * m) / (2 * S);
-    K.put((int)j, key_of(P.r0[q], q));
+    K.put((int)(j - q0), key_of(P.r0[q], q));
+  }
+  const uint64_t j = (uint64_t)c * 256 + threadIdx.x;
+  KeyRec own{0ull, 0ull, 0u, 0u};
+  if (j < S) {
+    const uint64_t q = ((2 * j + 1) * m) / (2 * S);
+    own = key_of(P.r0[q], q);
   }
   __syncthreads();
-  const uint64_t j = (uint64_t)c * 256 + threadIdx.x;
   if (j < S) {
-    const uint32_t r = K.rank((int)q0, (int)q1, K.k[j].x, K.k[j].y, K.idx[j]);
+    const uint32_t r = K.rank(0, (int)(q1 - q0), own.k1, own.k0, own.idx);
     if (r) atomicAdd(&P.ss_rank[j], r);
   }
   __shared__ bool last;
@@ -1182,7 +1188,7 @@ __global__ void __launch_bounds__(256) wc_ss_sample_kernel(Post P) {
   if (j < S) {
     const uint64_t r = __ldcg(P.ss_rank + j);
     const uint64_t u = (r * nb + S - 1) / S;  // the only candidate b + 1
-    if (u >= 1 && u < nb && (u * S) / nb == r) P.spl[u - 1] = KeyRec{K.k[j].x, K.k[j].y, K.idx[j], 0u};
+    if (u >= 1 && u < nb && (u * S) / nb == r) P.spl[u - 1] = own;
   }
 }
 
@@ -1266,44 +1272,18 @@ __global__ void __launch_bounds__(256) wc_ss_scatter_kernel(Post P) {
   if (i < m) P.kr[0][cnt[b] + r] = key_of(P.r0[i], i);
 }
 
-// Up to SS_RANK_MAX / SS_T CTAs per bucket: CTA (b, ch) ranks keys
-// SS_T*ch.. of bucket b against the whole bucket, then gathers their records
-// straight to those places in P.r1.  A bucket over SS_RANK_MAX keys is sorted
-// by its first CTA (bitonic tiles, merge passes).
-constexpr int SS_CH = SS_RANK_MAX / SS_T;
-__global__ void __launch_bounds__(SS_T) wc_ss_bsort_kernel(Post P) {
-  extern __shared__ __align__(16) unsigned char sb_raw[];
-  const uint32_t nb = P.ss[0];
-  const uint32_t b = blockIdx.x / SS_CH, ch = blockIdx.x % SS_CH;
-  if (b >= nb) return;
-  const uint32_t o = ss_off(P)[b], L = ss_off(P)[b + 1] - o;
-  const KeyRec* in = P.kr[0] + o;
-  if (L <= (uint32_t)SS_RANK_MAX) {
-    if (ch * SS_T >= L) return;
-    KeySoA K(sb_raw, SS_RANK_MAX);
-    for (uint32_t j = threadIdx.x; j < L; j += SS_T) K.put((int)j, in[j]);
-    __syncthreads();
-    const uint32_t j = ch * SS_T + threadIdx.x;
-    if (j < L) {
-      const uint32_t ai = K.idx[j];
-      P.r1[o + K.rank(0, (int)L, K.k[j].x, K.k[j].y, ai)] = P.r0[ai];
-    }
-  } else if (ch == 0) {
-    KeyRec* sh = reinterpret_cast<KeyRec*>(sb_raw);
-    const KeyRec* res = cta_sort(P.kr[0] + o, P.kr[1] + o, L, sh, SS_CAP, KeyCmp{});
-    for (uint32_t j = threadIdx.x; j < L; j += SS_T) P.r1[o + j] = P.r0[res[j].idx];
-  }
-}
-
 // ------------------------------------------- segmented sample sort (batches)
 // A batch of word-count jobs whose tables hold at most SS_MAX_RECORDS slots
 // each is sorted job by job, all jobs side by side: every job gets its own
-// sample, splitters and buckets (the geometry of the one-job sample sort), a
-// bucket never mixes jobs, and the work per record stays that of a sort of at
-// most 2^17 records however many records the batch holds (a radix sort of
-// the whole batch runs a dozen digit passes over all of them).  Compaction
-// puts job j's records at the start of the job's own slot range; the plan
-// then gives each job a dense range (jobs in order) and a range of buckets.
+// sample, splitters and buckets of about SEG_B records, a bucket never mixes
+// jobs, and the work per record stays that of a sort of at most 2^17
+// records however many records the batch holds (a radix sort of the whole
+// batch runs a dozen digit passes over all of them).  Compaction puts job
+// j's records at the start of the job's own slot range; the plan then gives
+// each job a dense range (jobs in order) and a range of buckets.  Buckets are
+// placed by rank, one warp per bucket, from the bucket's keys in the warp's
+// shared memory; the few over SEG_WCAP records are listed and placed by a
+// CTA each.
 struct SegJob {
   uint32_t cbase;  // first record of the job in slot order (compacted records)
   uint32_t d;      // first record of the job in the dense sorted order
@@ -1313,12 +1293,31 @@ struct SegJob {
   uint32_t pad[3];
 };
 static_assert(sizeof(SegJob) == 32, "SegJob layout");
+constexpr int SEG_B = 64;                                // records per bucket, on average
+constexpr int SEG_OVER = 2;                              // samples per bucket
+constexpr int SEG_MAXB = (int)(SS_MAX_RECORDS / SEG_B);  // buckets of one job, at most
+constexpr int SEG_SMAX = SEG_MAXB * SEG_OVER;            // sample of one job, at most
 constexpr int SEG_T = 256;
 constexpr int SEG_I = 8;
-constexpr int SEG_TILE = SEG_T * SEG_I;       // dense records per tile of the count and scatter passes
-constexpr int SEG_SAMPLE_T = 512;             // threads of the sample sort
-constexpr int SEG_FB_CAP = 1024;              // bitonic tile of the large-bucket fallback
-static_assert(SS_MAXB <= SS_BPT * 256, "one CTA of 256 threads scans a job's bucket counts");
+constexpr int SEG_TILE = SEG_T * SEG_I;   // dense records per tile of the count and scatter passes
+constexpr int SEG_SAMPLE_T = 512;         // threads of the sample sort
+constexpr int SEG_BPT = SEG_MAXB / 256;   // bucket counts per thread in the offset scan
+constexpr int SEG_COUNT_SMEM = SEG_MAXB * (16 + 4 + 4);  // splitters (keys, indices), bucket counts
+constexpr int SEG_WCAP = 256;             // largest bucket one warp places
+constexpr int SEG_WARPS = 8;              // warps per CTA of the warp pass
+constexpr int SEG_WSORT_SMEM = SEG_WARPS * SEG_WCAP * 20;
+constexpr int SEG_BT = 128;               // threads of the large-bucket pass
+constexpr int SEG_FB_CAP = 1024;          // bitonic tile of its merge sort
+constexpr int SEG_BSORT_SMEM = SEG_FB_CAP * (int)sizeof(KeyRec) > SS_RANK_MAX * 20 ? SEG_FB_CAP * (int)sizeof(KeyRec)
+                                                                                  : SS_RANK_MAX * 20;
+static_assert(SEG_MAXB % 256 == 0 && SEG_SMAX * (int)sizeof(KeyRec) <= 227 * 1024, "segmented sort geometry");
+
+// Buckets and sample size of a job of m records (m <= SS_MAX_RECORDS).
+__host__ __device__ __forceinline__ void seg_geom(uint64_t m, uint64_t& nb, uint64_t& S) {
+  nb = (m + SEG_B - 1) / SEG_B;
+  nb = nb < 1 ? 1 : (nb > (uint64_t)SEG_MAXB ? (uint64_t)SEG_MAXB : nb);
+  S = m < nb * SEG_OVER ? m : nb * SEG_OVER;
+}
 
 // Per-job record counts (P.jcur, from the compaction) -> dense and bucket
 // ranges; one CTA scans the jobs in chunks of CB.  P.glob[0] = records,
@@ -1333,7 +1332,7 @@ __global__ void __launch_bounds__(CB) wc_seg_plan_kernel(const JobDev* jobs, uin
     uint64_t m = 0, nb = 0, S = 0;
     if (j < njobs) {
       m = P.jcur[j];
-      ss_geometry(m, nb, S);
+      seg_geom(m, nb, S);
     }
     const unsigned long long v = (nb << 32) | m;
     unsigned long long incl = v;
@@ -1368,15 +1367,15 @@ __global__ void __launch_bounds__(CB) wc_seg_plan_kernel(const JobDev* jobs, uin
 }
 
 // Splitters of each job: its sample (S evenly spaced records of the job in
-// slot order, as in the one-job sort) sorted by one CTA with a bitonic
-// network in shared memory; splitter u - 1 is the sample of rank (u * S) / nb.
+// slot order, i.e. hash order) sorted by one CTA with a bitonic network in
+// shared memory; splitter u - 1 is the sample of rank (u * S) / nb.
 __global__ void __launch_bounds__(SEG_SAMPLE_T) wc_seg_sample_kernel(Post P, uint32_t njobs) {
   extern __shared__ __align__(16) unsigned char sg_raw[];
   KeyRec* sh = reinterpret_cast<KeyRec*>(sg_raw);
   for (uint32_t j = blockIdx.x; j < njobs; j += gridDim.x) {
     const SegJob g = P.seg[j];
     uint64_t nb, S;
-    ss_geometry(g.m, nb, S);
+    seg_geom(g.m, nb, S);
     if (nb < 2) continue;
     int n2 = 1;
     while (n2 < (int)S) n2 <<= 1;
@@ -1415,11 +1414,12 @@ __device__ __forceinline__ uint32_t seg_job_of(const SegJob* seg, uint32_t njobs
 // where the share starts.  A tile of SEG_TILE dense records usually lies in
 // one job; one that spans several takes them one job at a time.
 __global__ void __launch_bounds__(SEG_T) wc_seg_count_kernel(Post P, uint32_t njobs) {
-  __shared__ KeyRec spl[SS_MAXB];
-  __shared__ uint32_t cnt[SS_MAXB];
+  extern __shared__ __align__(16) unsigned char sc_raw[];
+  ulonglong2* sk = reinterpret_cast<ulonglong2*>(sc_raw);                  // splitter (key1, s0)
+  uint32_t* si = reinterpret_cast<uint32_t*>(sc_raw + SEG_MAXB * 16);    // splitter index
+  uint32_t* cnt = si + SEG_MAXB;
   __shared__ uint32_t jfirst;
   const uint64_t M = P.glob[0];
-  const KeyCmp cmp;
   for (uint64_t k0 = (uint64_t)blockIdx.x * SEG_TILE; k0 < M; k0 += (uint64_t)gridDim.x * SEG_TILE) {
     const uint64_t k1 = k0 + SEG_TILE < M ? k0 + SEG_TILE : M;
     if (threadIdx.x == 0) jfirst = seg_job_of(P.seg, njobs, k0);
@@ -1429,7 +1429,11 @@ __global__ void __launch_bounds__(SEG_T) wc_seg_count_kernel(Post P, uint32_t nj
       const SegJob g = P.seg[j];
       if (g.d >= k1) break;
       if (g.m == 0) continue;
-      for (uint32_t t = threadIdx.x; t + 1 < g.nb; t += SEG_T) spl[t] = P.spl[g.bbase + t];
+      for (uint32_t t = threadIdx.x; t + 1 < g.nb; t += SEG_T) {
+        const KeyRec r = P.spl[g.bbase + t];
+        sk[t] = make_ulonglong2(r.k1, r.k0);
+        si[t] = r.idx;
+      }
       for (uint32_t t = threadIdx.x; t < g.nb; t += SEG_T) cnt[t] = 0u;
       __syncthreads();
       const uint64_t a = k0 > g.d ? k0 : g.d;
@@ -1438,13 +1442,14 @@ __global__ void __launch_bounds__(SEG_T) wc_seg_count_kernel(Post P, uint32_t nj
       for (int q = 0; q < SEG_I; ++q) {
         const uint64_t k = k0 + q * SEG_T + threadIdx.x;
         if (k >= a && k < b) {
-          const uint64_t i = g.cbase + (k - g.d);
+          const uint32_t i = g.cbase + (uint32_t)(k - g.d);
           const ulonglong2 kk = *reinterpret_cast<const ulonglong2*>(P.r0 + i);
-          const KeyRec key{kk.x, kk.y, (uint32_t)i, 0u};
           uint32_t lo = 0, hi = g.nb - 1;
-          while (lo < hi) {
+          while (lo < hi) {  // first splitter not below the key
             const uint32_t mid = (lo + hi) >> 1;
-            if (cmp.less(spl[mid], key)) lo = mid + 1;
+            const ulonglong2 s = sk[mid];
+            const bool below = s.x < kk.x || (s.x == kk.x && (s.y < kk.y || (s.y == kk.y && si[mid] < i)));
+            if (below) lo = mid + 1;
             else hi = mid;
           }
           bk[q] = lo;
@@ -1473,10 +1478,10 @@ __global__ void __launch_bounds__(256) wc_seg_offsets_kernel(Post P, uint32_t nj
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint32_t j = blockIdx.x; j < njobs; j += gridDim.x) {
     const SegJob g = P.seg[j];
-    const uint32_t b0 = SS_BPT * threadIdx.x;
-    uint32_t c[SS_BPT], tot = 0;
+    const uint32_t b0 = SEG_BPT * threadIdx.x;
+    uint32_t c[SEG_BPT], tot = 0;
 #pragma unroll
-    for (int q = 0; q < SS_BPT; ++q) {
+    for (int q = 0; q < SEG_BPT; ++q) {
       c[q] = b0 + q < g.nb ? P.bcnt[g.bbase + b0 + q] : 0u;
       tot += c[q];
     }
@@ -1490,7 +1495,7 @@ __global__ void __launch_bounds__(256) wc_seg_offsets_kernel(Post P, uint32_t nj
     uint32_t ex = g.d + incl - tot;
     for (int w = 0; w < warp; ++w) ex += wsum[w];
 #pragma unroll
-    for (int q = 0; q < SS_BPT; ++q) {
+    for (int q = 0; q < SEG_BPT; ++q) {
       if (b0 + q < g.nb) P.boff[g.bbase + b0 + q] = ex;
       ex += c[q];
     }
@@ -1521,16 +1526,11 @@ __global__ void __launch_bounds__(SEG_T) wc_seg_scatter_kernel(Post P, uint32_t 
   }
 }
 
-// Buckets in key order, one bucket at a time per CTA: the bucket's keys go
-// to shared memory and each record is written to the place its rank in the
-// bucket gives (keys are distinct: the index breaks ties).  All keys of a
-// bucket belong to one job, so the high word of key1 (job, and the count's
-// bits from 2^32 up) is the same in all of them when every count is below
-// 2^32: the rank then compares 128-bit keys {key1 low word, s0, index} with
-// one shared-memory load each; otherwise 160-bit keys.  A bucket over
-// SS_RANK_MAX records (rare with SS_OVER samples per bucket) is sorted by the
-// CTA's bitonic tiles and merge passes on compact keys in P.kra, with the
-// bucket's place in P.r1 as scratch, then gathered.
+// Rank of key a among k[0..n): the number of keys below it.  rank128
+// compares {index, s0, key1 low word} (one shared-memory load each, one
+// comparison = the borrow of a 4-word subtraction), for keys whose key1 high
+// word (the job, and the count's bits from 2^32 up) is the same; rank160
+// adds key1's high word.
 __device__ __forceinline__ uint32_t rank128(const uint4* k, int n, uint4 a) {
   uint32_t r = 0;
 #pragma unroll 4
@@ -1569,68 +1569,157 @@ __device__ __forceinline__ uint32_t rank160(const uint4* k, const uint32_t* hi, 
   }
   return r;
 }
-constexpr int SEG_BT = 128;                      // threads of the bucket pass
-constexpr int SEG_BKEYS = SS_RANK_MAX / SEG_BT;  // keys of a ranked bucket per thread
-constexpr int SEG_BSORT_SMEM = SEG_FB_CAP * (int)sizeof(KeyRec) > SS_RANK_MAX * 20 ? SEG_FB_CAP * (int)sizeof(KeyRec)
-                                                                                  : SS_RANK_MAX * 20;
-__global__ void __launch_bounds__(SEG_BT, 7) wc_seg_bsort_kernel(Post P) {
-  extern __shared__ __align__(16) unsigned char sb_raw[];
-  uint4* k4 = reinterpret_cast<uint4*>(sb_raw);                           // {idx, s0 lo, s0 hi, key1 lo}
-  uint32_t* kh = reinterpret_cast<uint32_t*>(sb_raw + SS_RANK_MAX * 16);  // key1 hi
-  const uint64_t nbk = P.glob[12];
-  for (uint64_t b = blockIdx.x; b < nbk; b += gridDim.x) {
-    const uint32_t o = P.boff[b], L = P.boff[b + 1] - o;
-    if (L <= (uint32_t)SS_RANK_MAX) {
-      int low = 1;
-#pragma unroll
-      for (int q = 0; q < SEG_BKEYS; ++q) {
-        const uint32_t t = threadIdx.x + q * SEG_BT;
-        if (t < L) {
-          const uint32_t i = P.kidx[o + t];
-          const ulonglong2 kk = *reinterpret_cast<const ulonglong2*>(P.r0 + i);
-          k4[t] = make_uint4(i, (uint32_t)kk.y, (uint32_t)(kk.y >> 32), (uint32_t)kk.x);
-          kh[t] = (uint32_t)(kk.x >> 32);
-          low &= (int)((kk.x >> 32) & 0xFFu) == 0xFF;  // count below 2^32
-        }
-      }
-      if (__syncthreads_and(low)) {
-#pragma unroll
-        for (int q = 0; q < SEG_BKEYS; ++q) {
-          const uint32_t t = threadIdx.x + q * SEG_BT;
-          if (t < L) {
-            const uint4 a = k4[t];
-            P.r1[o + rank128(k4, (int)L, a)] = P.r0[a.x];
-          }
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < SEG_BKEYS; ++q) {
-          const uint32_t t = threadIdx.x + q * SEG_BT;
-          if (t < L) {
-            const uint4 a = k4[t];
-            P.r1[o + rank160(k4, kh, (int)L, a, kh[t])] = P.r0[a.x];
-          }
-        }
-      }
-      __syncthreads();
-    } else {
-      KeyRec* a = P.kra + o;
-      for (uint32_t t = threadIdx.x; t < L; t += SEG_BT) {
-        const uint32_t i = P.kidx[o + t];
-        const ulonglong2 kk = *reinterpret_cast<const ulonglong2*>(P.r0 + i);
-        a[t] = KeyRec{kk.x, kk.y, i, 0u};
-      }
-      __syncthreads();
-      KeyRec* sh = reinterpret_cast<KeyRec*>(sb_raw);
-      const KeyRec* res = cta_sort(a, reinterpret_cast<KeyRec*>(P.r1 + o), L, sh, SEG_FB_CAP, KeyCmp{});
-      if (res != a) {  // the result sits in the bucket's output place: move it out first
-        for (uint32_t t = threadIdx.x; t < L; t += SEG_BT) a[t] = res[t];
-        __syncthreads();
-      }
-      for (uint32_t t = threadIdx.x; t < L; t += SEG_BT) P.r1[o + t] = P.r0[a[t].idx];
-      __syncthreads();
+
+// Bucket placement, shared by the one-job sample sort (keys of bucket b in
+// P.kr[0][off[b]..off[b + 1]), offsets in ss_off, bucket count in ss[0])
+// and the segmented sort (record indices in P.kidx, keys read from P.r0,
+// offsets in P.boff, bucket count in glob[12]).  A bucket's keys go to
+// shared memory as {index, s0 lo, s0 hi, key1 lo} plus key1 hi; each record
+// is then written to the place its rank in the bucket gives (keys are
+// distinct: the index breaks ties).  When key1's high word is the same in
+// every key of the bucket (one job, every count below 2^32: always so in the
+// segmented sort's buckets) the rank compares 128 bits, else 160.
+template <bool SEG>
+__device__ __forceinline__ void bucket_key(const Post& P, uint32_t o, uint32_t t, uint4* k4, uint32_t* kh) {
+  unsigned long long k1, k0;
+  uint32_t i;
+  if (SEG) {
+    i = P.kidx[o + t];
+    const ulonglong2 kk = *reinterpret_cast<const ulonglong2*>(P.r0 + i);
+    k1 = kk.x;
+    k0 = kk.y;
+  } else {
+    const KeyRec r = P.kr[0][o + t];
+    k1 = r.k1;
+    k0 = r.k0;
+    i = r.idx;
+  }
+  k4[t] = make_uint4(i, (uint32_t)k0, (uint32_t)(k0 >> 32), (uint32_t)k1);
+  kh[t] = (uint32_t)(k1 >> 32);
+}
+template <bool SEG>
+__device__ __forceinline__ uint64_t bucket_count(const Post& P) {
+  return SEG ? P.glob[12] : (uint64_t)P.ss[0];
+}
+template <bool SEG>
+__device__ __forceinline__ const uint32_t* bucket_off(const Post& P) {
+  return SEG ? P.boff : ss_off(P);
+}
+__device__ __forceinline__ void place_by_rank(const Post& P, uint32_t o, uint32_t L, const uint4* k4,
+                                              const uint32_t* kh, bool same_hi, uint32_t t0, uint32_t stride) {
+  if (same_hi) {
+    for (uint32_t t = t0; t < L; t += stride) {
+      const uint4 a = k4[t];
+      P.r1[o + rank128(k4, (int)L, a)] = P.r0[a.x];
+    }
+  } else {
+    for (uint32_t t = t0; t < L; t += stride) {
+      const uint4 a = k4[t];
+      P.r1[o + rank160(k4, kh, (int)L, a, kh[t])] = P.r0[a.x];
     }
   }
+}
+
+// Segmented sort: one warp per bucket of up to WCAP records, from the
+// warp's slice of shared memory (many buckets per SM, each warp its own
+// chain of loads); larger buckets are listed for wc_seg_bucket_cta_kernel.
+template <int WCAP>
+__global__ void __launch_bounds__(SEG_WARPS * 32) wc_seg_bucket_warp_kernel(Post P) {
+  constexpr bool SEG = true;
+  extern __shared__ __align__(16) unsigned char sw_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint4* k4 = reinterpret_cast<uint4*>(sw_raw) + warp * WCAP;
+  uint32_t* kh = reinterpret_cast<uint32_t*>(sw_raw + SEG_WARPS * WCAP * 16) + warp * WCAP;
+  const uint64_t nbk = bucket_count<SEG>(P);
+  const uint32_t* off = bucket_off<SEG>(P);
+  const uint64_t nw = (uint64_t)gridDim.x * SEG_WARPS;
+  for (uint64_t b = (uint64_t)blockIdx.x * SEG_WARPS + warp; b < nbk; b += nw) {
+    const uint32_t o = off[b], L = off[b + 1] - o;
+    if (L > (uint32_t)WCAP) {
+      if (lane == 0) P.big[atomicAdd(P.glob + 13, 1ull)] = (uint32_t)b;
+      continue;
+    }
+#pragma unroll
+    for (int q = 0; q < WCAP / 32; ++q) {
+      const uint32_t t = lane + 32 * q;
+      if (t < L) bucket_key<SEG>(P, o, t, k4, kh);
+    }
+    __syncwarp();
+    bool same = true;
+    for (uint32_t t = lane; t < L; t += 32) same &= kh[t] == kh[0];
+    place_by_rank(P, o, L, k4, kh, __all_sync(0xffffffffu, same), lane, 32);
+    __syncwarp();
+  }
+}
+
+// A bucket by one CTA: up to SS_RANK_MAX records placed by rank as above,
+// larger ones (many times the mean size: rare) sorted by the CTA's bitonic
+// tiles and merge passes on compact keys, then gathered.  The segmented sort
+// builds those keys in P.kra and uses the bucket's place in P.r1 as scratch;
+// the one-job sort has them in P.kr[0] and P.kr[1].
+template <bool SEG, int T>
+__device__ __forceinline__ void bucket_by_cta(const Post& P, uint32_t o, uint32_t L, unsigned char* raw) {
+  uint4* k4 = reinterpret_cast<uint4*>(raw);
+  uint32_t* kh = reinterpret_cast<uint32_t*>(raw + SS_RANK_MAX * 16);
+  if (L <= (uint32_t)SS_RANK_MAX) {
+#pragma unroll
+    for (int q = 0; q < SS_RANK_MAX / T; ++q) {
+      const uint32_t t = threadIdx.x + q * T;
+      if (t < L) bucket_key<SEG>(P, o, t, k4, kh);
+    }
+    __syncthreads();
+    int same = 1;
+    for (uint32_t t = threadIdx.x; t < L; t += T) same &= kh[t] == kh[0];
+    place_by_rank(P, o, L, k4, kh, __syncthreads_and(same), threadIdx.x, T);
+    __syncthreads();
+    return;
+  }
+  KeyRec* a;
+  KeyRec* tmp;
+  if (SEG) {
+    a = P.kra + o;
+    tmp = reinterpret_cast<KeyRec*>(P.r1 + o);
+    for (uint32_t t = threadIdx.x; t < L; t += T) {
+      const uint32_t i = P.kidx[o + t];
+      const ulonglong2 kk = *reinterpret_cast<const ulonglong2*>(P.r0 + i);
+      a[t] = KeyRec{kk.x, kk.y, i, 0u};
+    }
+    __syncthreads();
+  } else {
+    a = P.kr[0] + o;
+    tmp = P.kr[1] + o;
+  }
+  KeyRec* sh = reinterpret_cast<KeyRec*>(raw);
+  const KeyRec* res = cta_sort(a, tmp, L, sh, SEG_FB_CAP, KeyCmp{});
+  if (SEG && res != a) {  // the result sits in the bucket's output place: move it out first
+    for (uint32_t t = threadIdx.x; t < L; t += T) a[t] = res[t];
+    __syncthreads();
+    res = a;
+  }
+  for (uint32_t t = threadIdx.x; t < L; t += T) P.r1[o + t] = P.r0[res[t].idx];
+  __syncthreads();
+}
+
+// Segmented sort: the listed large buckets, one CTA each.
+__global__ void __launch_bounds__(SEG_BT) wc_seg_bucket_cta_kernel(Post P) {
+  extern __shared__ __align__(16) unsigned char sb_raw[];
+  const uint64_t nbig = P.glob[13];
+  for (uint64_t q0 = blockIdx.x; q0 < nbig; q0 += gridDim.x) {
+    const uint32_t b = P.big[q0];
+    bucket_by_cta<true, SEG_BT>(P, P.boff[b], P.boff[b + 1] - P.boff[b], sb_raw);
+  }
+}
+
+// One-job sample sort: one CTA of SS_BUCKET_T threads per bucket (a few
+// hundred buckets of up to a few hundred keys: the largest bucket's ranking
+// sets the pass's length, so all of a CTA's threads share each bucket).
+constexpr int SS_BUCKET_T = 512;
+__global__ void __launch_bounds__(SS_BUCKET_T, 2) wc_ss_bucket_kernel(Post P) {
+  extern __shared__ __align__(16) unsigned char sb_raw[];
+  const uint32_t b = blockIdx.x;
+  if (b >= P.ss[0]) return;
+  const uint32_t o = ss_off(P)[b];
+  bucket_by_cta<false, SS_BUCKET_T>(P, o, ss_off(P)[b + 1] - o, sb_raw);
 }
 
 inline uint64_t a256(uint64_t x) { return (x + 255) & ~255ull; }
@@ -1665,15 +1754,9 @@ struct SegGeom {
   uint64_t bytes = 0;  // scratch past post_common_bytes
 };
 
-void host_ss_geometry(uint64_t m, uint64_t& nb, uint64_t& S) {
-  nb = (m + SS_B - 1) / SS_B;
-  nb = nb < 1 ? 1 : (nb > (uint64_t)SS_MAXB ? (uint64_t)SS_MAXB : nb);
-  S = m < nb * SS_OVER ? m : nb * SS_OVER;
-}
-
 uint64_t seg_bytes(uint64_t R, uint64_t njobs, uint64_t nbmax) {
   return ca256(njobs * sizeof(SegJob)) + ca256((njobs + nbmax) * 4) + ca256((nbmax + 1) * 4) +
-         ca256(nbmax * sizeof(KeyRec)) + ca256(R * 8) + ca256(R * 4) + ca256(R * sizeof(KeyRec));
+         ca256(nbmax * sizeof(KeyRec)) + ca256(nbmax * 4) + ca256(R * 8) + ca256(R * 4) + ca256(R * sizeof(KeyRec));
 }
 
 // Several jobs, more records than the one-job sample sort takes, and every
@@ -1689,7 +1772,7 @@ SegGeom seg_geometry(const JobDev* hjobs, uint32_t njobs, uint64_t R) {
     if (cap < (uint64_t)CB || cap > SS_MAX_RECORDS || cap % CB || hjobs[j].blk0 * CB != base) return G;
     base += cap;
     uint64_t nb, S;
-    host_ss_geometry(cap, nb, S);
+    seg_geom(cap, nb, S);
     G.nbmax += nb;
     if (S > G.smax) G.smax = S;
   }
@@ -1710,6 +1793,8 @@ void carve_seg(Post& P, uint8_t* base, uint64_t R, uint32_t njobs, const SegGeom
   p += a256((G.nbmax + 1) * 4);
   P.spl = reinterpret_cast<KeyRec*>(p);
   p += a256(G.nbmax * sizeof(KeyRec));
+  P.big = reinterpret_cast<uint32_t*>(p);
+  p += a256(G.nbmax * 4);
   P.bpos = reinterpret_cast<uint2*>(p);
   p += a256(R * 8);
   P.kidx = reinterpret_cast<uint32_t*>(p);
@@ -1822,39 +1907,35 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
     while ((uint64_t)n2 < G.smax) n2 <<= 1;
     const int sg_smem = n2 * (int)sizeof(KeyRec);
     if ((e = cudaFuncSetAttribute(wc_seg_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sg_smem)) !=
-        cudaSuccess)
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(wc_seg_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  SEG_COUNT_SMEM)) != cudaSuccess)
       return e;
+    const uint64_t sm = (uint64_t)(sms > 0 ? sms : 1);
     const uint64_t tiles = (R + SEG_TILE - 1) / SEG_TILE;
-    const uint64_t gmax = 8ull * (uint64_t)(sms > 0 ? sms : 1), gbmax = 14ull * (uint64_t)(sms > 0 ? sms : 1);
-    const unsigned gt = (unsigned)(tiles < gmax ? tiles : gmax);
-    const unsigned gb = (unsigned)(G.nbmax < gbmax ? G.nbmax : gbmax);
+    const unsigned gt = (unsigned)(tiles < 8 * sm ? tiles : 8 * sm);
+    const uint64_t wcta = (G.nbmax + SEG_WARPS - 1) / SEG_WARPS;
+    const unsigned gw = (unsigned)(wcta < 4 * sm ? wcta : 4 * sm);  // 4 CTAs per SM (registers)
     wc_seg_plan_kernel<<<1, CB, 0, s>>>(jobs, njobs, P);
     wc_seg_sample_kernel<<<njobs, SEG_SAMPLE_T, sg_smem, s>>>(P, njobs);
-    wc_seg_count_kernel<<<gt, SEG_T, 0, s>>>(P, njobs);
+    wc_seg_count_kernel<<<gt, SEG_T, SEG_COUNT_SMEM, s>>>(P, njobs);
     wc_seg_offsets_kernel<<<njobs, 256, 0, s>>>(P, njobs);
     wc_seg_scatter_kernel<<<gt, SEG_T, 0, s>>>(P, njobs);
-    wc_seg_bsort_kernel<<<gb, SEG_BT, SEG_BSORT_SMEM, s>>>(P);
+    wc_seg_bucket_warp_kernel<SEG_WCAP><<<gw, SEG_WARPS * 32, SEG_WSORT_SMEM, s>>>(P);
+    wc_seg_bucket_cta_kernel<<<(unsigned)sm, SEG_BT, SEG_BSORT_SMEM, s>>>(P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    *nk += 6;
+    *nk += 6;  // the last one is counted with the tie fix-up below
   } else if (R <= SS_MAX_RECORDS) {
     // sample sort of (key1, s0, index) keys; the bucket pass gathers the records
-    constexpr int sp_smem = soa_bytes(SS_SMAX);
-    constexpr int sb_smem = SS_CAP * (int)sizeof(KeyRec) > soa_bytes(SS_RANK_MAX) ? SS_CAP * (int)sizeof(KeyRec)
-                                                                                   : soa_bytes(SS_RANK_MAX);
-    if ((e = cudaFuncSetAttribute(wc_ss_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sp_smem)) !=
-            cudaSuccess ||
-        (e = cudaFuncSetAttribute(wc_ss_bsort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sb_smem)) !=
-            cudaSuccess)
-      return e;
     const uint64_t nbmax = (R + SS_B - 1) / SS_B < (uint64_t)SS_MAXB ? (R + SS_B - 1) / SS_B : (uint64_t)SS_MAXB;
     const uint64_t smax = R < nbmax * SS_OVER ? R : nbmax * SS_OVER;
     const uint64_t sblocks = (smax + 255) / 256 < 1 ? 1 : (smax + 255) / 256;
-    wc_ss_sample_kernel<<<(unsigned)(sblocks * SS_PARTS), 256, sp_smem, s>>>(P);
+    wc_ss_sample_kernel<<<(unsigned)(sblocks * SS_PARTS), 256, 0, s>>>(P);
     wc_ss_count_kernel<<<g256, 256, 0, s>>>(P);
     wc_ss_scatter_kernel<<<g256, 256, 0, s>>>(P);
-    wc_ss_bsort_kernel<<<(unsigned)((nbmax < 1 ? 1 : nbmax) * SS_CH), SS_T, sb_smem, s>>>(P);
+    wc_ss_bucket_kernel<<<(unsigned)(nbmax < 1 ? 1 : nbmax), SS_BUCKET_T, SEG_BSORT_SMEM, s>>>(P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    *nk += 3;
+    *nk += 3;  // the last one is counted with the tie fix-up below
   } else if (R < RADIX_MIN_RECORDS) {
     // small record sets: comparison sort of (key1, s0, index) keys
     constexpr int kbs = KSB * (int)sizeof(KeyRec), kmg = KMT * KMI * (int)sizeof(KeyRec);
@@ -1893,7 +1974,8 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
     wc_rgather_kernel<<<g256, 256, 0, s>>>(P);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  // ties on (key1, s0): the full order
+  // ties on (key1, s0): the full order (the count below also takes the
+  // sort path's last launch)
   wc_rfix_kernel<<<g256, 256, 0, s>>>(P, jobs, single, max_runs(R));
   const int fx_smem = SB * (int)sizeof(SortRec);
   if ((e = cudaFuncSetAttribute(wc_rfix_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem)) !=
