@@ -306,64 +306,10 @@ __device__ __forceinline__ uint32_t find_job_by_block(const JobDev* jobs, uint32
   return lo;
 }
 
-__device__ __forceinline__ int block_excl_scan(int v, int* tmp, int& total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int incl = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) tmp[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    const int w = tmp[lane];
-    int wi = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, wi, o);
-      if (lane >= o) wi += t;
-    }
-    tmp[lane] = wi - w;
-    if (lane == 31) tmp[32] = wi;
-  }
-  __syncthreads();
-  const int r = tmp[warp] + incl - v;
-  total = tmp[32];
-  __syncthreads();
-  return r;
-}
 
-// Occupied slots of every job -> records.  Block b belongs to the job whose
-// block range contains b.  The first block of a job also zeroes the job's
-// result header (a job with no records keeps {0, 0}).  Records are packed
-// from index 0 for the whole batch, or, for the segmented sort, from the
-// start of each job's own slot range (P.jcur counts them per job).
-__global__ void __launch_bounds__(CB) wc_compact_kernel(const JobDev* jobs, JobDev single, uint32_t njobs, Post P) {
-  __shared__ int tmp[33];
-  __shared__ unsigned long long blk_base;
-  const uint32_t j = jobs ? find_job_by_block(jobs, njobs, blockIdx.x) : 0;
-  const JobDev J = job_at(jobs, single, j);
-  const uint64_t slot = ((uint64_t)blockIdx.x - J.blk0) * CB + threadIdx.x;
-  if (blockIdx.x == J.blk0 && threadIdx.x < 2) reinterpret_cast<unsigned long long*>(J.out)[threadIdx.x] = 0;
-  uint64_t w0 = 0, w1 = 0;
-  if (slot < J.cap) {
-    w0 = J.key[2 * slot];
-    w1 = J.key[2 * slot + 1];
-  }
-  const bool occ = w1 != 0;
-  int total;
-  const int r = block_excl_scan(occ ? 1 : 0, tmp, total);
-  if (threadIdx.x == 0) {
-    if (P.jcur)  // segmented sort: the job's records fill the start of its own slot range
-      blk_base = total ? J.blk0 * CB + atomicAdd(P.jcur + j, (uint32_t)total) : 0ull;
-    else
-      blk_base = total ? atomicAdd(P.glob, (unsigned long long)total) : 0ull;
-  }
-  __syncthreads();
-  if (!occ) return;
-  const uint64_t i = blk_base + (uint64_t)r;
-  const uint64_t cnt = J.cnt[slot];
+// One occupied slot (key words w0, w1; count cnt) -> its sort record at index i.
+__device__ __forceinline__ void compact_record(const JobDev& J, uint32_t j, uint64_t cnt, uint64_t w0, uint64_t w1,
+                                               uint64_t i, const Post& P) {
   SortRec rec;
   rec.key1 = ((uint64_t)j << 40) | (CNT_MAX - (cnt < CNT_MAX ? cnt : CNT_MAX));
   rec.idx = (uint32_t)i;
@@ -387,6 +333,82 @@ __global__ void __launch_bounds__(CB) wc_compact_kernel(const JobDev* jobs, JobD
     P.src[i] = off;
   }
   P.r0[i] = rec;
+}
+
+// Occupied slots of every job -> records.  The slots are cut into blocks of
+// CB (job j's blocks start at blk0); a CTA of CT threads takes a contiguous
+// range of blocks, finding its first block's job once and following the job
+// boundaries from there, and loads CPT slots per thread at a time.  The first
+// block of a job also zeroes the job's result header (a job with no records
+// keeps {0, 0}).  Records are packed from index 0 for the whole batch, or,
+// for the segmented sort, from the start of each job's own slot range
+// (P.jcur counts them per job).
+constexpr int CT = 256;
+constexpr int CPT = CB / CT;
+__global__ void __launch_bounds__(CT) wc_compact_kernel(const JobDev* jobs, JobDev single, uint32_t njobs,
+                                                        uint64_t nblocks, Post P) {
+  __shared__ uint32_t wsum[CT / 32];
+  __shared__ unsigned long long blk_base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t per = (nblocks + gridDim.x - 1) / gridDim.x;
+  const uint64_t b0 = (uint64_t)blockIdx.x * per;
+  const uint64_t b1 = b0 + per < nblocks ? b0 + per : nblocks;
+  if (b0 >= b1) return;
+  uint32_t j = jobs ? find_job_by_block(jobs, njobs, b0) : 0;
+  JobDev J = job_at(jobs, single, j);
+  uint64_t next = jobs && j + 1 < njobs ? jobs[j + 1].blk0 : ~0ull;
+  for (uint64_t b = b0; b < b1; ++b) {
+    while (b >= next) {  // uniform across the CTA
+      J = jobs[++j];
+      next = j + 1 < njobs ? jobs[j + 1].blk0 : ~0ull;
+    }
+    if (b == J.blk0 && threadIdx.x < 2) reinterpret_cast<unsigned long long*>(J.out)[threadIdx.x] = 0;
+    const uint64_t s0 = (b - J.blk0) * CB + threadIdx.x;
+    uint64_t w0[CPT], w1[CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      const uint64_t slot = s0 + (uint64_t)q * CT;
+      w0[q] = w1[q] = 0;
+      if (slot < J.cap) {
+        const ulonglong2 k = *reinterpret_cast<const ulonglong2*>(J.key + 2 * slot);
+        w0[q] = k.x;
+        w1[q] = k.y;
+      }
+    }
+    uint32_t c = 0;
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) c += w1[q] != 0;
+    // counts loaded before the scan and the reservation, so their latency
+    // overlaps them (and before any record store, which could alias them)
+    uint64_t cnt[CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) cnt[q] = w1[q] != 0 ? J.cnt[s0 + (uint64_t)q * CT] : 0ull;
+    uint32_t incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    uint32_t ex = incl - c, total = 0;
+#pragma unroll
+    for (int w = 0; w < CT / 32; ++w) {
+      const uint32_t v = wsum[w];
+      if (w < warp) ex += v;
+      total += v;
+    }
+    if (threadIdx.x == 0) {
+      if (P.jcur)  // segmented sort: the job's records fill the start of its own slot range
+        blk_base = total ? J.blk0 * CB + atomicAdd(P.jcur + j, total) : 0ull;
+      else
+        blk_base = total ? atomicAdd(P.glob, (unsigned long long)total) : 0ull;
+    }
+    __syncthreads();
+    uint64_t i = blk_base + ex;
+#pragma unroll
+    for (int q = 0; q < CPT; ++q)
+      if (w1[q] != 0) compact_record(J, j, cnt[q], w0[q], w1[q], i++, P);
+  }
 }
 
 // Tie runs of up to SB records are ordered by one CTA's bitonic sort in
@@ -1896,7 +1918,10 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
   if (G.on) carve_seg(P, sortbuf, R, njobs, G);
   if ((e = cudaMemsetAsync(P.glob, 0, head_bytes(R), s)) != cudaSuccess) return e;
   if (G.on && (e = cudaMemsetAsync(P.jcur, 0, (njobs + G.nbmax) * 4, s)) != cudaSuccess) return e;
-  wc_compact_kernel<<<(unsigned)nblocks, CB, 0, s>>>(jobs, single, njobs, P);
+  {
+    const uint64_t cmax = 4ull * (uint64_t)(sms > 0 ? sms : 1);  // 4 CTAs of CT threads per SM (registers)
+    wc_compact_kernel<<<(unsigned)(nblocks < cmax ? nblocks : cmax), CT, 0, s>>>(jobs, single, njobs, nblocks, P);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   ++*nk;
   const uint64_t nb = (R + CB - 1) / CB;
