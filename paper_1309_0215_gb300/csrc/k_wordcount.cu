@@ -600,23 +600,28 @@ __global__ void __launch_bounds__(CB) wc_lensum_kernel(Post P, bool fuse) {
   __shared__ bool last;
   const SortRec* recs = P.r1;
   const uint64_t m = *P.glob;
-  if (!fuse && (uint64_t)blockIdx.x * CB >= m) return;
-  const uint64_t i = (uint64_t)blockIdx.x * CB + threadIdx.x;
-  unsigned long long v = i < m ? recs[i].len : 0;
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long s = 0;
-    for (int w = 0; w < 32; ++w) s += ws[w];
-    P.bsum[blockIdx.x] = s;
-    if (fuse) {
-      __threadfence();
-      last = atomicAdd(P.glob + 8, 1ull) == gridDim.x - 1;
+  // fused: one block per CB records (all of them, for the ticket count);
+  // otherwise a persistent grid over the live blocks
+  for (uint64_t blk = blockIdx.x; fuse ? blk == blockIdx.x : blk * CB < m; blk += gridDim.x) {
+    const uint64_t i = blk * CB + threadIdx.x;
+    unsigned long long v = i < m ? recs[i].len : 0;
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long s = 0;
+      for (int w = 0; w < 32; ++w) s += ws[w];
+      P.bsum[blk] = s;
     }
+    __syncthreads();
+  }
+  if (!fuse) return;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(P.glob + 8, 1ull) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!fuse || !last) return;
+  if (!last) return;
   __threadfence();
   bsum_scan(P, gridDim.x);
 }
@@ -634,50 +639,50 @@ __global__ void __launch_bounds__(CB) wc_bounds_kernel(const JobDev* jobs, JobDe
   __shared__ unsigned long long wsum[32];
   const SortRec* recs = P.r1;
   const uint64_t m = *P.glob;
-  const uint64_t i = (uint64_t)blockIdx.x * CB + threadIdx.x;
-  if ((uint64_t)blockIdx.x * CB >= m) return;
-  const uint32_t len = i < m ? recs[i].len : 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned long long incl = len;
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) wsum[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    const unsigned long long w = wsum[lane];
-    unsigned long long wi = w;
+  for (uint64_t blk = blockIdx.x; blk * CB < m; blk += gridDim.x) {
+    const uint64_t i = blk * CB + threadIdx.x;
+    const uint32_t len = i < m ? recs[i].len : 0;
+    unsigned long long incl = len;
     for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long t = __shfl_up_sync(0xffffffffu, wi, o);
-      if (lane >= o) wi += t;
+      const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
     }
-    wsum[lane] = wi - w;
-  }
-  __syncthreads();
-  if (i >= m) return;
-  const unsigned long long ex = P.bsum[blockIdx.x] + wsum[warp] + incl - len;
-  P.excl[i] = ex;
-  const uint32_t j = (uint32_t)(recs[i].key1 >> 40);
-  const bool first = i == 0 || (uint32_t)(recs[i - 1].key1 >> 40) != j;
-  const bool last = i + 1 == m || (uint32_t)(recs[i + 1].key1 >> 40) != j;
-  unsigned long long* st = reinterpret_cast<unsigned long long*>(job_at(jobs, single, j).state);
-  if (first) {
-    st[1] = i;
-    st[2] = ex;
-  }
-  if (last) {
-    st[3] = i + 1;
-    st[4] = ex + len;
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned long long w = wsum[lane];
+      unsigned long long wi = w;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += t;
+      }
+      wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    if (i < m) {
+      const unsigned long long ex = P.bsum[blk] + wsum[warp] + incl - len;
+      P.excl[i] = ex;
+      const uint32_t j = (uint32_t)(recs[i].key1 >> 40);
+      const bool first = i == 0 || (uint32_t)(recs[i - 1].key1 >> 40) != j;
+      const bool last = i + 1 == m || (uint32_t)(recs[i + 1].key1 >> 40) != j;
+      unsigned long long* st = reinterpret_cast<unsigned long long*>(job_at(jobs, single, j).state);
+      if (first) {
+        st[1] = i;
+        st[2] = ex;
+      }
+      if (last) {
+        st[3] = i + 1;
+        st[4] = ex + len;
+      }
+    }
+    __syncthreads();
   }
 }
 
 // Records and key bytes into each job's result.
-__global__ void __launch_bounds__(256) wc_gather_kernel(const JobDev* jobs, JobDev single, Post P) {
-  const SortRec* recs = P.r1;
-  const uint64_t m = *P.glob;
-  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
+__device__ __forceinline__ void gather_one(const JobDev* jobs, const JobDev& single, const Post& P,
+                                           const SortRec* recs, uint64_t i) {
   const SortRec r = recs[i];
   const uint32_t j = (uint32_t)(r.key1 >> 40);
   const JobDev J = job_at(jobs, single, j);
@@ -702,6 +707,12 @@ __global__ void __launch_bounds__(256) wc_gather_kernel(const JobDev* jobs, JobD
     const uint8_t* s = J.in + P.src[r.idx];
     for (uint32_t q = 0; q < r.len; ++q) keys[q] = s[q];
   }
+}
+__global__ void __launch_bounds__(256) wc_gather_kernel(const JobDev* jobs, JobDev single, Post P) {
+  const SortRec* recs = P.r1;
+  const uint64_t m = *P.glob;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
+    gather_one(jobs, single, P, recs, i);
 }
 
 
@@ -929,9 +940,8 @@ __device__ __forceinline__ bool rtie(const SortRec& a, const SortRec& b) { retur
 // wc_rfix_cta_kernel: up to SB records in P.runs from the front (count in
 // P.glob[2]), longer ones from the back (count in P.glob[3]).  Every listed run is longer than FIX_THREAD, so both lists
 // together hold fewer than max_runs entries.
-__global__ void __launch_bounds__(256) wc_rfix_kernel(Post P, const JobDev* jobs, JobDev single, uint64_t max_runs) {
-  const uint64_t m = *P.glob;
-  const uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
+__device__ __forceinline__ void rfix_one(const Post& P, const JobDev* jobs, const JobDev& single, uint64_t max_runs,
+                                         uint64_t i, uint64_t m) {
   if (i + 1 >= m) return;
   SortRec* r = P.r1;
   if (!rtie(r[i], r[i + 1])) return;
@@ -975,6 +985,12 @@ __global__ void __launch_bounds__(256) wc_rfix_kernel(Post P, const JobDev* jobs
     const unsigned long long k = atomicAdd(P.glob + 3, 1ull);
     if (k < max_runs) P.runs[max_runs - 1 - k] = make_uint2((uint32_t)i, (uint32_t)L);
   }
+}
+
+__global__ void __launch_bounds__(256) wc_rfix_kernel(Post P, const JobDev* jobs, JobDev single, uint64_t max_runs) {
+  const uint64_t m = *P.glob;
+  for (uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x; i + 1 < m; i += (uint64_t)gridDim.x * 256)
+    rfix_one(P, jobs, single, max_runs, i, m);
 }
 
 // Full record order (a pad, idx == ~0, sorts last).
@@ -2001,7 +2017,12 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // ties on (key1, s0): the full order (the count below also takes the
   // sort path's last launch)
-  wc_rfix_kernel<<<g256, 256, 0, s>>>(P, jobs, single, max_runs(R));
+  // the tail's grids cover the live records only (loops over them)
+  const uint64_t smc = (uint64_t)(sms > 0 ? sms : 1);
+  const unsigned gp256 = (unsigned)(g256 < 8 * smc ? g256 : 8 * smc);  // 8 CTAs per SM (gather: 32 registers)
+  const unsigned gpfix = (unsigned)(g256 < 6 * smc ? g256 : 6 * smc);  // 6 (tie fix-up: 40 registers)
+  const unsigned gpcb = (unsigned)(nb < 2 * smc ? nb : 2 * smc);
+  wc_rfix_kernel<<<gpfix, 256, 0, s>>>(P, jobs, single, max_runs(R));
   const int fx_smem = SB * (int)sizeof(SortRec);
   if ((e = cudaFuncSetAttribute(wc_rfix_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem)) !=
       cudaSuccess)
@@ -2009,13 +2030,13 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
   wc_rfix_cta_kernel<<<64, SB_THREADS, fx_smem, s>>>(P, jobs, single, max_runs(R));
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   *nk += 3;
-  wc_lensum_kernel<<<(unsigned)nb, CB, 0, s>>>(P, nb <= LENSUM_FUSE_BLOCKS);
+  wc_lensum_kernel<<<nb <= LENSUM_FUSE_BLOCKS ? (unsigned)nb : gpcb, CB, 0, s>>>(P, nb <= LENSUM_FUSE_BLOCKS);
   if (nb > LENSUM_FUSE_BLOCKS) {
     wc_bscan_kernel<<<1, CB, 0, s>>>(P, nb);
     ++*nk;
   }
-  wc_bounds_kernel<<<(unsigned)nb, CB, 0, s>>>(jobs, single, P);
-  wc_gather_kernel<<<g256, 256, 0, s>>>(jobs, single, P);
+  wc_bounds_kernel<<<gpcb, CB, 0, s>>>(jobs, single, P);
+  wc_gather_kernel<<<gp256, 256, 0, s>>>(jobs, single, P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   *nk += 3;
   return cudaSuccess;
