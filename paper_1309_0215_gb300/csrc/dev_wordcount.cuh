@@ -330,27 +330,25 @@ __device__ inline void warp_segment_t(const JobDev& J, uint64_t seg, WarpLocal& 
     __syncwarp();
     mine = reinterpret_cast<const uint4*>(L.buf)[lane];
   }
-  // token starts among this lane's 16 bytes
-  uint32_t wsm = byte_bits(ws_bytes(mine.x)) | (byte_bits(ws_bytes(mine.y)) << 4) |
-                 (byte_bits(ws_bytes(mine.z)) << 8) | (byte_bits(ws_bytes(mine.w)) << 12);
-  const uint64_t lb = base + 16 * (uint64_t)lane;
-  if (lb + 16 > n) wsm |= lb >= n ? 0xFFFFu : (0xFFFFu & ~((1u << (uint32_t)(n - lb)) - 1u));
+  // token starts among this lane's 16 bytes (staged bytes past the input
+  // end are spaces, so the input end needs no test of its own)
+  const uint32_t wsm = byte_bits(ws_bytes(mine.x)) | (byte_bits(ws_bytes(mine.y)) << 4) |
+                       (byte_bits(ws_bytes(mine.z)) << 8) | (byte_bits(ws_bytes(mine.w)) << 12);
   {
-    // whitespace bitmap of the staged bytes (segment, then the halo, which
-    // lanes 0..3 classify; staged bytes past the input end are spaces)
-    uint32_t wsh = 0;
-    if (lane < HALO / 16) {
-      const uint4 hv = reinterpret_cast<const uint4*>(L.buf)[32 + lane];
-      wsh = byte_bits(ws_bytes(hv.x)) | (byte_bits(ws_bytes(hv.y)) << 4) | (byte_bits(ws_bytes(hv.z)) << 8) |
-            (byte_bits(ws_bytes(hv.w)) << 12);
-      const uint64_t hb = base + SEG + 16 * (uint64_t)lane;
-      if (hb + 16 > n) wsh |= hb >= n ? 0xFFFFu : (0xFFFFu & ~((1u << (uint32_t)(n - hb)) - 1u));
-    }
+    // whitespace bitmap of the staged bytes: the segment from the lanes'
+    // masks; the halo by lane l testing its bytes l and 32 + l, one ballot
+    // per 32 bytes
+    static_assert(HALO == 64, "the halo is two bitmap words");
+    __syncwarp();  // lanes 0..3 staged the halo
+    const uint32_t h0 = __ballot_sync(0xffffffffu, is_ws(L.buf[SEG + lane]));
+    const uint32_t h1 = __ballot_sync(0xffffffffu, is_ws(L.buf[SEG + 32 + lane]));
     const uint32_t up = __shfl_down_sync(0xffffffffu, wsm, 1);
-    const uint32_t uh = __shfl_down_sync(0xffffffffu, wsh, 1);
     if ((lane & 1) == 0) L.wsb[lane >> 1] = (wsm & 0xFFFFu) | (up << 16);
-    if (lane < HALO / 16 && (lane & 1) == 0) L.wsb[SEG / 32 + (lane >> 1)] = (wsh & 0xFFFFu) | (uh << 16);
-    if (lane == 0) L.wsb[BUF / 32] = 0xFFFFFFFFu;  // past the halo
+    if (lane == 0) {
+      L.wsb[SEG / 32] = h0;
+      L.wsb[SEG / 32 + 1] = h1;
+      L.wsb[BUF / 32] = 0xFFFFFFFFu;  // past the halo
+    }
   }
   uint32_t prev = __shfl_up_sync(0xffffffffu, wsm >> 15, 1) & 1u;
   if (lane == 0) prev = (base == 0) ? 1u : (uint32_t)is_ws(in[base - 1]);
