@@ -1456,14 +1456,18 @@ __global__ void __launch_bounds__(SEG_T) wc_seg_count_kernel(Post P, uint32_t nj
   ulonglong2* sk = reinterpret_cast<ulonglong2*>(sc_raw);                  // splitter (key1, s0)
   uint32_t* si = reinterpret_cast<uint32_t*>(sc_raw + SEG_MAXB * 16);    // splitter index
   uint32_t* cnt = si + SEG_MAXB;
-  __shared__ uint32_t jfirst;
   const uint64_t M = P.glob[0];
-  for (uint64_t k0 = (uint64_t)blockIdx.x * SEG_TILE; k0 < M; k0 += (uint64_t)gridDim.x * SEG_TILE) {
+  // a contiguous range of tiles per CTA: the job of its first record is
+  // found once, later tiles follow the job boundaries
+  const uint64_t ntiles = (M + SEG_TILE - 1) / SEG_TILE, per = (ntiles + gridDim.x - 1) / gridDim.x;
+  const uint64_t tb = (uint64_t)blockIdx.x * per, te = tb + per < ntiles ? tb + per : ntiles;
+  uint32_t jt = tb < te ? seg_job_of(P.seg, njobs, tb * SEG_TILE) : 0u;
+  for (uint64_t tile = tb; tile < te; ++tile) {
+    const uint64_t k0 = tile * SEG_TILE;
     const uint64_t k1 = k0 + SEG_TILE < M ? k0 + SEG_TILE : M;
-    if (threadIdx.x == 0) jfirst = seg_job_of(P.seg, njobs, k0);
-    __syncthreads();
+    while (k0 >= (uint64_t)P.seg[jt].d + P.seg[jt].m) ++jt;  // uniform: a job that ends by k0
     uint32_t bk[SEG_I], lr[SEG_I];
-    for (uint32_t j = jfirst; j < njobs; ++j) {
+    for (uint32_t j = jt; j < njobs; ++j) {
       const SegJob g = P.seg[j];
       if (g.d >= k1) break;
       if (g.m == 0) continue;
@@ -1544,6 +1548,8 @@ __global__ void __launch_bounds__(256) wc_seg_offsets_kernel(Post P, uint32_t nj
 
 // Record indices (slot order) to their places in bucket order.
 __global__ void __launch_bounds__(SEG_T) wc_seg_scatter_kernel(Post P, uint32_t njobs) {
+  // tiles interleaved across CTAs: the CTAs running at a time write into a
+  // few jobs' ranges, where the L2 merges the partial-sector stores
   __shared__ uint32_t jfirst;
   const uint64_t M = P.glob[0];
   for (uint64_t k0 = (uint64_t)blockIdx.x * SEG_TILE; k0 < M; k0 += (uint64_t)gridDim.x * SEG_TILE) {
@@ -1955,11 +1961,12 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
     const uint64_t sm = (uint64_t)(sms > 0 ? sms : 1);
     const uint64_t tiles = (R + SEG_TILE - 1) / SEG_TILE;
     const unsigned gt = (unsigned)(tiles < 8 * sm ? tiles : 8 * sm);
+    const unsigned gc = (unsigned)(tiles < 4 * sm ? tiles : 4 * sm);  // count: 4 CTAs per SM (shared memory)
     const uint64_t wcta = (G.nbmax + SEG_WARPS - 1) / SEG_WARPS;
     const unsigned gw = (unsigned)(wcta < 4 * sm ? wcta : 4 * sm);  // 4 CTAs per SM (registers)
     wc_seg_plan_kernel<<<1, CB, 0, s>>>(jobs, njobs, P);
     wc_seg_sample_kernel<<<njobs, SEG_SAMPLE_T, sg_smem, s>>>(P, njobs);
-    wc_seg_count_kernel<<<gt, SEG_T, SEG_COUNT_SMEM, s>>>(P, njobs);
+    wc_seg_count_kernel<<<gc, SEG_T, SEG_COUNT_SMEM, s>>>(P, njobs);
     wc_seg_offsets_kernel<<<njobs, 256, 0, s>>>(P, njobs);
     wc_seg_scatter_kernel<<<gt, SEG_T, 0, s>>>(P, njobs);
     wc_seg_bucket_warp_kernel<SEG_WCAP><<<gw, SEG_WARPS * 32, SEG_WSORT_SMEM, s>>>(P);
