@@ -588,6 +588,7 @@ __device__ void bsum_scan(Post& P, uint64_t nb) {
     if (threadIdx.x == CB - 1) carry = ex + v;
     __syncthreads();
   }
+  if (threadIdx.x == 0) P.glob[9] = carry;  // all key bytes
 }
 
 
@@ -681,20 +682,14 @@ __global__ void __launch_bounds__(CB) wc_bounds_kernel(const JobDev* jobs, JobDe
 }
 
 // Records and key bytes into each job's result.
-__device__ __forceinline__ void gather_one(const JobDev* jobs, const JobDev& single, const Post& P,
-                                           const SortRec* recs, uint64_t i) {
-  const SortRec r = recs[i];
-  const uint32_t j = (uint32_t)(r.key1 >> 40);
-  const JobDev J = job_at(jobs, single, j);
-  const unsigned long long* st = reinterpret_cast<const unsigned long long*>(J.state);
-  const uint64_t first = st[1], scan0 = st[2], end = st[3], scan1 = st[4];
-  const uint64_t nrec = end - first, li = i - first;
+// Record li of a job's nrec (key bytes at koff of kbytes) into its result.
+__device__ __forceinline__ void emit_record(const JobDev& J, const Post& P, const SortRec& r, uint64_t li,
+                                            uint64_t nrec, uint64_t koff, uint64_t kbytes) {
   unsigned long long* out = reinterpret_cast<unsigned long long*>(J.out);
   if (li == 0) {
     out[0] = nrec;
-    out[1] = scan1 - scan0;
+    out[1] = kbytes;
   }
-  const uint64_t koff = P.excl[i] - scan0;
   unsigned long long* rec = out + 2 + 3 * li;
   rec[0] = CNT_MAX - (r.key1 & CNT_MAX);
   rec[1] = koff;
@@ -708,11 +703,55 @@ __device__ __forceinline__ void gather_one(const JobDev* jobs, const JobDev& sin
     for (uint32_t q = 0; q < r.len; ++q) keys[q] = s[q];
   }
 }
+__device__ __forceinline__ void gather_one(const JobDev* jobs, const JobDev& single, const Post& P,
+                                           const SortRec* recs, uint64_t i) {
+  const SortRec r = recs[i];
+  const uint32_t j = (uint32_t)(r.key1 >> 40);
+  const JobDev J = job_at(jobs, single, j);
+  const unsigned long long* st = reinterpret_cast<const unsigned long long*>(J.state);
+  const uint64_t first = st[1], scan0 = st[2], end = st[3], scan1 = st[4];
+  emit_record(J, P, r, i - first, end - first, P.excl[i] - scan0, scan1 - scan0);
+}
 __global__ void __launch_bounds__(256) wc_gather_kernel(const JobDev* jobs, JobDev single, Post P) {
   const SortRec* recs = P.r1;
   const uint64_t m = *P.glob;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
     gather_one(jobs, single, P, recs, i);
+}
+
+// One job: its records are all records (first 0, end m, key bytes in
+// P.glob[9]), so the bounds pass is not needed: each block scans its key
+// lengths from the block sums and writes its records straight away.
+__global__ void __launch_bounds__(CB) wc_gather1_kernel(JobDev J, Post P) {
+  __shared__ unsigned long long wsum[32];
+  const SortRec* recs = P.r1;
+  const uint64_t m = P.glob[0], kbytes = P.glob[9];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint64_t blk = blockIdx.x; blk * CB < m; blk += gridDim.x) {
+    const uint64_t i = blk * CB + threadIdx.x;
+    SortRec r{};
+    if (i < m) r = recs[i];
+    unsigned long long incl = i < m ? r.len : 0;
+    const unsigned long long len = incl;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned long long w = wsum[lane];
+      unsigned long long wi = w;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += t;
+      }
+      wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    if (i < m) emit_record(J, P, r, i, m, P.bsum[blk] + wsum[warp] + incl - len, kbytes);
+    __syncthreads();
+  }
 }
 
 
@@ -2042,8 +2081,13 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
     wc_bscan_kernel<<<1, CB, 0, s>>>(P, nb);
     ++*nk;
   }
-  wc_bounds_kernel<<<gpcb, CB, 0, s>>>(jobs, single, P);
-  wc_gather_kernel<<<gp256, 256, 0, s>>>(jobs, single, P);
+  if (jobs) {
+    wc_bounds_kernel<<<gpcb, CB, 0, s>>>(jobs, single, P);
+    wc_gather_kernel<<<gp256, 256, 0, s>>>(jobs, single, P);
+  } else {  // one job: bounds known, scan and gather in one pass
+    wc_gather1_kernel<<<gpcb, CB, 0, s>>>(single, P);
+    --*nk;
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   *nk += 3;
   return cudaSuccess;
