@@ -1382,10 +1382,11 @@ constexpr int SEG_BPT = SEG_MAXB / 256;   // bucket counts per thread in the off
 constexpr int SEG_COUNT_SMEM = SEG_MAXB * (16 + 4 + 4);  // splitters (keys, indices), bucket counts
 constexpr int SEG_WCAP = 256;             // largest bucket one warp places
 constexpr int SEG_WARPS = 8;              // warps per CTA of the warp pass
-constexpr int SEG_WSORT_SMEM = SEG_WARPS * SEG_WCAP * 20;
+constexpr int SEG_WARP_SMEM = SEG_WARPS * SEG_WCAP * 20;
 constexpr int SEG_BT = 128;               // threads of the large-bucket pass
 constexpr int SEG_FB_CAP = 1024;          // bitonic tile of its merge sort
-constexpr int SEG_BSORT_SMEM = SEG_FB_CAP * (int)sizeof(KeyRec) > SS_RANK_MAX * 20 ? SEG_FB_CAP * (int)sizeof(KeyRec)
+// shared memory of a CTA that places one bucket (ranked keys, or the merge sort's tile)
+constexpr int BUCKET_CTA_SMEM = SEG_FB_CAP * (int)sizeof(KeyRec) > SS_RANK_MAX * 20 ? SEG_FB_CAP * (int)sizeof(KeyRec)
                                                                                   : SS_RANK_MAX * 20;
 static_assert(SEG_MAXB % 256 == 0 && SEG_SMAX * (int)sizeof(KeyRec) <= 227 * 1024, "segmented sort geometry");
 
@@ -2008,8 +2009,8 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
     wc_seg_count_kernel<<<gc, SEG_T, SEG_COUNT_SMEM, s>>>(P, njobs);
     wc_seg_offsets_kernel<<<njobs, 256, 0, s>>>(P, njobs);
     wc_seg_scatter_kernel<<<gt, SEG_T, 0, s>>>(P, njobs);
-    wc_seg_bucket_warp_kernel<SEG_WCAP><<<gw, SEG_WARPS * 32, SEG_WSORT_SMEM, s>>>(P);
-    wc_seg_bucket_cta_kernel<<<(unsigned)sm, SEG_BT, SEG_BSORT_SMEM, s>>>(P);
+    wc_seg_bucket_warp_kernel<SEG_WCAP><<<gw, SEG_WARPS * 32, SEG_WARP_SMEM, s>>>(P);
+    wc_seg_bucket_cta_kernel<<<(unsigned)sm, SEG_BT, BUCKET_CTA_SMEM, s>>>(P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *nk += 6;  // the last one is counted with the tie fix-up below
   } else if (R <= SS_MAX_RECORDS) {
@@ -2020,7 +2021,7 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
     wc_ss_sample_kernel<<<(unsigned)(sblocks * SS_PARTS), 256, 0, s>>>(P);
     wc_ss_count_kernel<<<g256, 256, 0, s>>>(P);
     wc_ss_scatter_kernel<<<g256, 256, 0, s>>>(P);
-    wc_ss_bucket_kernel<<<(unsigned)(nbmax < 1 ? 1 : nbmax), SS_BUCKET_T, SEG_BSORT_SMEM, s>>>(P);
+    wc_ss_bucket_kernel<<<(unsigned)(nbmax < 1 ? 1 : nbmax), SS_BUCKET_T, BUCKET_CTA_SMEM, s>>>(P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *nk += 3;  // the last one is counted with the tie fix-up below
   } else if (R < RADIX_MIN_RECORDS) {
