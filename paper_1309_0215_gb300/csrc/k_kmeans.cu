@@ -470,6 +470,20 @@ __global__ void km_recheck_fp64_smem_kernel(const float* __restrict__ x, uint32_
       if (lane + 32 * q < k) m32 = fminf(m32, dist[q]);
     for (int o = 16; o; o >>= 1) m32 = fminf(m32, __shfl_xor_sync(0xffffffffu, m32, o));
     const float lim = m32 * widen;
+    // one candidate within the bound: it is the argmin, no FP64 needed
+    uint32_t ncand = 0;
+    int first = -1;
+#pragma unroll
+    for (int q = 0; q < KLANE; ++q) {
+      const uint32_t kk = lane + 32 * q;
+      const bool cq = kk < k && (dist[q] <= lim || m32 != m32);
+      if (cq && first < 0) first = (int)kk;
+      ncand += (uint32_t)__popc(__ballot_sync(0xffffffffu, cq));
+    }
+    if (ncand == 1) {
+      if (first >= 0) assign[p] = first;
+      continue;
+    }
     double best = INFINITY;
     int bk = 0x7fffffff;
 #pragma unroll
