@@ -123,8 +123,11 @@ typedef struct {
   void* cuda_stream;      /* cudaStream_t to enqueue on; NULL = library-owned stream */
   uint64_t hbm_budget;    /* max device bytes held by this context; 0 = unlimited */
   /* Optional device allocator (e.g. a framework's caching allocator).  When
-   * alloc is NULL the library uses cudaMallocAsync on its stream.  alloc
-   * returns NULL on failure; free must accept any pointer alloc returned. */
+   * alloc is NULL the library allocates stream-ordered (cudaMallocFromPoolAsync
+   * on its stream) from a memory pool of its own, which keeps freed memory
+   * for reuse until mr_destroy (so a job's containers cost no new mapping
+   * after the first use).  alloc returns NULL on failure; free must accept
+   * any pointer alloc returned. */
   void* (*alloc)(void* user, size_t bytes);
   void (*free)(void* user, void* ptr);
   void* alloc_user;

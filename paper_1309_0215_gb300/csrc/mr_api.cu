@@ -87,6 +87,10 @@ struct mr_ctx {
   void* (*alloc)(void*, size_t) = nullptr;
   void (*free_fn)(void*, void*) = nullptr;
   void* alloc_user = nullptr;
+  // without a caller allocator: the context's own stream-ordered pool, whose
+  // release threshold keeps freed memory mapped for reuse (the default pool
+  // returns it to the system at every synchronisation)
+  cudaMemPool_t pool = nullptr;
   uint64_t budget = 0;
   uint64_t in_use = 0;
   uint32_t flags = 0;
@@ -173,10 +177,10 @@ mr_status dev_alloc(mr_ctx* c, uint64_t bytes, void** out) {
     p = c->alloc(c->alloc_user, (size_t)bytes);
     if (!p) return MR_ENOMEM;
   } else {
-    cudaError_t e = cudaMallocAsync(&p, (size_t)bytes, c->stream);
+    cudaError_t e = cudaMallocFromPoolAsync(&p, (size_t)bytes, c->pool, c->stream);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      set_last_error("cudaMallocAsync", e);
+      set_last_error("cudaMallocFromPoolAsync", e);
       return e == cudaErrorMemoryAllocation ? MR_ENOMEM : MR_ECUDA;
     }
   }
@@ -825,7 +829,7 @@ Job* find_job(mr_ctx* c, uint64_t id) {
 // it (4x) and re-run until it fits.
 mr_status serve_launch_now(mr_ctx* c, Job* j);
 
-mr_status wait_job(mr_ctx* c, Job* j) {
+mr_status wait_job(mr_ctx* c, Job* j, uint64_t* wc_result_bytes = nullptr) {
   if (j->state == JOB_SERVE_QUEUED) {
     mr_status st = serve_launch_now(c, j);
     if (st) return st;
@@ -842,11 +846,17 @@ mr_status wait_job(mr_ctx* c, Job* j) {
   }
   if (j->desc.kind != MR_WORDCOUNT) return MR_OK;
   for (;;) {
+    // the flag words and the result header, read with one synchronisation
     uint32_t st[4];
+    uint64_t hdr[2];
     MR_CUDA_TRY(cudaMemcpyAsync(st, j->wc.state, 16, cudaMemcpyDeviceToHost, c->stream));
+    MR_CUDA_TRY(cudaMemcpyAsync(hdr, j->wc.out, 16, cudaMemcpyDeviceToHost, c->stream));
     MR_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (st[0] & 2u) return MR_ETIMEOUT;  // a pipelined map pass whose reducer stalled
-    if (!(st[0] & 1u)) return MR_OK;
+    if (!(st[0] & 1u)) {
+      if (wc_result_bytes) *wc_result_bytes = 16 + 24 * hdr[0] + hdr[1];
+      return MR_OK;
+    }
     if (!j->wc_auto) return MR_EOVERFLOW;
     // the job's containers move: a captured batch graph that names them is stale
     for (uint64_t id : c->batch_ids)
@@ -989,8 +999,21 @@ mr_status mr_create(const mr_config* cfg, mr_ctx** out) {
       c->own_stream = e == cudaSuccess;
     }
   }
+  if (e == cudaSuccess && !c->alloc) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = c->device;
+    e = cudaMemPoolCreate(&c->pool, &props);
+    if (e == cudaSuccess) {
+      uint64_t keep = ~0ull;  // never trim at synchronisation; the pool goes with the context
+      e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+  }
   if (e != cudaSuccess) {
     set_last_error("mr_create", e);
+    if (c->pool) cudaMemPoolDestroy(c->pool);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
     return MR_ECUDA;
   }
@@ -1041,6 +1064,9 @@ void mr_destroy(mr_ctx* c) {
   for (cudaEvent_t e : c->ev_done) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_timing) cudaEventDestroy(e);
   for (KTimer* t : c->kt_pool) kt_destroy(t);
+  cudaStreamSynchronize(c->stream);
+  // memory still held (none, normally) is released once it is freed
+  if (c->pool) cudaMemPoolDestroy(c->pool);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -1076,11 +1102,10 @@ mr_status mr_fetch(mr_ctx* c, uint64_t job_id, void* buf, uint64_t buf_bytes, ui
   DeviceGuard g(c->device);
   Job* j = find_job(c, job_id);
   if (!j) return MR_ENOJOB;
-  mr_status st = wait_job(c, j);
-  if (st) return st;
   uint64_t bytes = 0;
-  st = result_size(c, j, &bytes);
+  mr_status st = wait_job(c, j, &bytes);
   if (st) return st;
+  if (j->desc.kind != MR_WORDCOUNT && (st = result_size(c, j, &bytes)) != MR_OK) return st;
   if (needed) *needed = bytes;
   if (!buf) return MR_OK;
   if (buf_bytes < bytes) return MR_EINVAL;
