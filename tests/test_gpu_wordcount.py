@@ -97,3 +97,26 @@ def test_wc_zipf_16MiB_bit_exact(mr):
     assert got == ref
     recs = oracle.parse_wordcount(got)
     assert sum(c for _, c in recs) == len(ranks)
+
+
+def test_contexts_release_their_memory(mr):
+    """A context allocates from a pool of its own that keeps freed memory for
+    reuse; destroying the context hands it back: creating, using and closing
+    contexts in a loop leaves the device's free memory where it was."""
+    import torch
+    text, _, _ = synth.wc_text(4 << 20, seed=77)
+    dev = torch.from_numpy(text).cuda()
+    exp = oracle.wordcount(text)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(12):
+        c = mr.Context()
+        for _ in range(3):
+            j = c.add_job(mr.WORDCOUNT, dev)
+            c.run(mr.RUN_PLAIN)
+            assert c.fetch(j) == exp
+            c.release(j)
+        c.close()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0 - (64 << 20), (free0, free1)
