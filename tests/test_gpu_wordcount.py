@@ -99,10 +99,13 @@ def test_wc_zipf_16MiB_bit_exact(mr):
     assert sum(c for _, c in recs) == len(ranks)
 
 
-def test_contexts_release_their_memory(mr):
-    """A context allocates from a pool of its own that keeps freed memory for
-    reuse; destroying the context hands it back: creating, using and closing
-    contexts in a loop leaves the device's free memory where it was."""
+@pytest.mark.parametrize("torch_alloc", [False, True])
+def test_contexts_release_their_memory(mr, torch_alloc):
+    """Without allocator hooks a context allocates from a pool of its own that
+    keeps freed memory for reuse, and destroying the context hands it back;
+    with torch's caching allocator the blocks go back to torch's cache and
+    are reused.  Either way, creating, using and closing contexts in a loop
+    leaves the device's free memory where it was."""
     import torch
     text, _, _ = synth.wc_text(4 << 20, seed=77)
     dev = torch.from_numpy(text).cuda()
@@ -110,7 +113,7 @@ def test_contexts_release_their_memory(mr):
     torch.cuda.synchronize()
     free0, _ = torch.cuda.mem_get_info()
     for _ in range(12):
-        c = mr.Context()
+        c = mr.Context(use_torch_allocator=torch_alloc)
         for _ in range(3):
             j = c.add_job(mr.WORDCOUNT, dev)
             c.run(mr.RUN_PLAIN)
