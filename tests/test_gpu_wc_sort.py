@@ -112,3 +112,24 @@ def test_segmented_sort_many_jobs(mr):
     for j, r in zip(ids, raws):
         assert c.fetch(j) == oracle.wordcount(r)
     c.close()
+
+
+@pytest.mark.parametrize("live", [0, 1, 2])
+def test_segmented_sort_mostly_empty_jobs(mr, live):
+    """A batch large enough for the segmented sort (48 tables of 4096 slots)
+    whose jobs hold no words at all (whitespace only, empty), except `live`
+    of them: zero records, a single job's records, two jobs far apart."""
+    import torch
+    raws = [b"" if i % 2 else b" \n " * (i + 1) for i in range(48)]
+    if live >= 1:
+        raws[7] = b"alpha beta alpha gamma"
+    if live >= 2:
+        raws[40] = _text(500, b"zzzzzzzz", 3, 40)
+    c = mr.Context()
+    bufs = [torch.frombuffer(bytearray(r), dtype=torch.uint8).cuda() if r
+            else torch.zeros(0, dtype=torch.uint8, device="cuda") for r in raws]
+    ids = [c.add_job(mr.WORDCOUNT, b) for b in bufs]
+    c.run(mr.RUN_BATCHED)
+    for j, r in zip(ids, raws):
+        assert c.fetch(j) == oracle.wordcount(r)
+    c.close()
