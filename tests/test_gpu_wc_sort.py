@@ -133,3 +133,28 @@ def test_segmented_sort_mostly_empty_jobs(mr, live):
     for j, r in zip(ids, raws):
         assert c.fetch(j) == oracle.wordcount(r)
     c.close()
+
+
+@pytest.mark.parametrize("slots", [1024, 2048])
+def test_batch_of_small_pinned_tables(mr, slots):
+    """300 jobs with caller-sized tables of 1024 slots (the smallest table,
+    one compaction block) or 2048, merged by the segmented sort; a table
+    below 1024 slots is refused at mr_add_job."""
+    import torch
+    c0 = mr.Context()
+    with pytest.raises(mr.MRError):
+        c0.add_job(mr.WORDCOUNT, torch.zeros(8, dtype=torch.uint8, device="cuda"), wc_slots=512)
+    c0.close()
+    rng = np.random.default_rng(slots)
+    raws = []
+    for i in range(300):
+        nw = int(rng.integers(0, 300))
+        raws.append(_text(nw, b"w%03d_" % (i % 17), int(rng.integers(1, 4)), i) if nw else b"")
+    c = mr.Context()
+    bufs = [torch.frombuffer(bytearray(r), dtype=torch.uint8).cuda() if r
+            else torch.zeros(0, dtype=torch.uint8, device="cuda") for r in raws]
+    ids = [c.add_job(mr.WORDCOUNT, b, wc_slots=slots) for b in bufs]
+    c.run(mr.RUN_BATCHED)
+    for j, r in zip(ids, raws):
+        assert c.fetch(j) == oracle.wordcount(r)
+    c.close()
