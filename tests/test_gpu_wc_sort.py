@@ -158,3 +158,29 @@ def test_batch_of_small_pinned_tables(mr, slots):
     for j, r in zip(ids, raws):
         assert c.fetch(j) == oracle.wordcount(r)
     c.close()
+
+
+def test_rerun_after_a_table_regrows(mr):
+    """A batch sorted by the segmented sort whose one job overflows its
+    automatic table (2^17 slots, 200,000 distinct words): the fetch regrows
+    that table and re-runs the job; mr_rerun then re-captures the batch with
+    the grown table (now too large for the segmented sort, so the batch takes
+    the comparison sort), and every job still equals the oracle."""
+    import torch
+    import synth
+    text, _, _ = synth.wc_text(6 << 20, nwords=50000, seed=91)
+    raws = [b" ".join(b"%x" % i for i in range(200_000))]
+    rng = np.random.default_rng(92)
+    for _ in range(40):
+        n = int(rng.integers(1 << 10, 1 << 20))
+        off = int(rng.integers(0, text.size - n))
+        raws.append(text[off: off + n].tobytes())
+    c = mr.Context()
+    bufs = [torch.frombuffer(bytearray(r), dtype=torch.uint8).cuda() for r in raws]
+    ids = [c.add_job(mr.WORDCOUNT, b) for b in bufs]
+    c.run(mr.RUN_BATCHED)
+    exp = [oracle.wordcount(r) for r in raws]
+    assert [c.fetch(j) for j in ids] == exp
+    c.rerun()
+    assert [c.fetch(j) for j in ids] == exp
+    c.close()
