@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 def _dev(a, offset_bytes=0):
     """Device copy of a uint8/uint32 array starting offset_bytes into a buffer."""
     import torch
-    raw = np.ascontiguousarray(a).view(np.uint8)
+    raw = np.array(a, copy=True, order="C").view(np.uint8)  # a writable copy for torch
     buf = torch.zeros(raw.size + offset_bytes + 16, dtype=torch.uint8, device="cuda")
     if raw.size:
         buf[offset_bytes: offset_bytes + raw.size] = torch.from_numpy(raw).cuda()
