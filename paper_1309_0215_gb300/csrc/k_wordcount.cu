@@ -441,6 +441,23 @@ struct KeyCmp {
   __device__ static KeyRec pad() { return KeyRec{~0ull, ~0ull, 0xffffffffu, 0u}; }
 };
 
+// Splitter s (key words s.x = key1, s.y = s0, index si) below key k (k.x,
+// k.y, index ki): the borrow of the 160-bit subtraction s - k, no branches.
+__device__ __forceinline__ bool key_below(ulonglong2 s, uint32_t si, ulonglong2 k, uint32_t ki) {
+  uint32_t borrow;
+  asm("{\n\t.reg .u32 t;\n\t"
+      "sub.cc.u32 t, %1, %6;\n\t"
+      "subc.cc.u32 t, %2, %7;\n\t"
+      "subc.cc.u32 t, %3, %8;\n\t"
+      "subc.cc.u32 t, %4, %9;\n\t"
+      "subc.cc.u32 t, %5, %10;\n\t"
+      "subc.u32 %0, 0, 0;\n\t}"
+      : "=r"(borrow)
+      : "r"(si), "r"((uint32_t)s.y), "r"((uint32_t)(s.y >> 32)), "r"((uint32_t)s.x), "r"((uint32_t)(s.x >> 32)),
+        "r"(ki), "r"((uint32_t)k.y), "r"((uint32_t)(k.y >> 32)), "r"((uint32_t)k.x), "r"((uint32_t)(k.x >> 32)));
+  return borrow != 0;
+}
+
 // Block sort: NB items per CTA (NT threads), bitonic network in shared memory.
 template <class R, class C, int NB, int NT>
 __global__ void __launch_bounds__(NT) blocksort_kernel(R* data, const unsigned long long* glob, C cmp) {
@@ -1282,12 +1299,11 @@ __global__ void __launch_bounds__(256) wc_ss_count_kernel(Post P) {
   __syncthreads();
   const uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
   if (i < m) {
-    const KeyRec k = key_of(P.r0[i], i);
-    const KeyCmp cmp;
+    const ulonglong2 kk = *reinterpret_cast<const ulonglong2*>(P.r0 + i);
     uint32_t lo = 0, hi = (uint32_t)nb - 1;
     while (lo < hi) {
       const uint32_t mid = (lo + hi) >> 1;
-      if (cmp.less(spl[mid], k)) lo = mid + 1;
+      if (key_below(make_ulonglong2(spl[mid].k1, spl[mid].k0), spl[mid].idx, kk, (uint32_t)i)) lo = mid + 1;
       else hi = mid;
     }
     P.bkt[i] = (uint16_t)lo;
@@ -1529,9 +1545,7 @@ __global__ void __launch_bounds__(SEG_T) wc_seg_count_kernel(Post P, uint32_t nj
           uint32_t lo = 0, hi = g.nb - 1;
           while (lo < hi) {  // first splitter not below the key
             const uint32_t mid = (lo + hi) >> 1;
-            const ulonglong2 s = sk[mid];
-            const bool below = s.x < kk.x || (s.x == kk.x && (s.y < kk.y || (s.y == kk.y && si[mid] < i)));
-            if (below) lo = mid + 1;
+            if (key_below(sk[mid], si[mid], kk, i)) lo = mid + 1;
             else hi = mid;
           }
           bk[q] = lo;
