@@ -181,7 +181,10 @@ typedef struct {
   uint32_t wc_pipelined;
 } mr_job_desc;
 
-/* Create a context on cfg->device.  *out receives the handle.
+/* Create a context on cfg->device.  *out receives the handle.  A context is
+ * the runtime that carries jobs through the basic workflow of Sec. II-A
+ * (Fig. 1: split, map, partition, reduce, merge) on one GPU; it owns the
+ * stream, the containers of its jobs and their results.
  * Errors: MR_EINVAL (null, bad struct_size, bad device), MR_ECUDA. */
 mr_status mr_create(const mr_config* cfg, mr_ctx** out);
 
@@ -189,20 +192,30 @@ mr_status mr_create(const mr_config* cfg, mr_ctx** out);
 void mr_destroy(mr_ctx* ctx);
 
 /* Validate a job, choose its container, reserve its device memory (and copy a
- * host input to the device) and queue it for the next mr_run.
+ * host input to the device) and queue it for the next mr_run.  A job is the
+ * paper's MapReduce job (Sec. II-A "Programming model": an input array and a
+ * map/reduce function pair, here a built-in mr_kind); the container choice
+ * is the automatic detection of Sec. III-E unless desc->container pins one.
  * *job_id receives an id > 0.  Errors: MR_EINVAL, MR_ENOMEM, MR_EBUDGET,
  * MR_ECUDA. */
 mr_status mr_add_job(mr_ctx* ctx, const mr_job_desc* desc, uint64_t* job_id);
 
-/* Enqueue every pending job on the context stream.  PLAIN launches each job's
- * kernels in order; BATCHED runs all pending word-count / RGB-histogram /
+/* Enqueue every pending job on the context stream: the map phase (split of
+ * the input over CTAs and warps, map with its combiner into local
+ * containers), the reduce into the global container, and the merge and
+ * optional ordering of the result (Sec. II-A workflow, Fig. 1; Sec. III-A
+ * combiners and containers).  PLAIN launches each job's kernels in order; BATCHED runs all pending word-count / RGB-histogram /
  * regression jobs in one persistent kernel, followed by one merge + sort for
  * all word-count jobs, captured as one CUDA graph (k-means, large-key
  * histogram and Bloom-filter jobs always run plain, after the batch).
- * Returns when the work is enqueued (an autotuning run waits). */
+ * Returns when the work is enqueued (an autotuning run waits).  Jobs that
+ * could not be launched (MR_ENOMEM, MR_EBUDGET, MR_ECUDA on the way) stay
+ * pending for the next mr_run. */
 mr_status mr_run(mr_ctx* ctx, mr_mode mode);
 
-/* Copy a finished job's result into host memory buf (buf_bytes long).
+/* Copy a finished job's result into host memory buf (buf_bytes long): the
+ * output of the workflow's last step (Sec. II-A: the merged result pairs,
+ * ordered where the kind orders them; layouts under mr_kind).
  * Blocks until the job is done.  With buf == NULL only *needed is set (the
  * result size in bytes).  A word-count job whose automatic hash table
  * overflowed is re-run with a larger table inside this call.
@@ -223,10 +236,13 @@ mr_status mr_rerun(mr_ctx* ctx);
 /* Current batched-launch parameters of the context. */
 mr_status mr_get_tuning(const mr_ctx* ctx, mr_tuning* out);
 
-/* Free a job's containers and result.  Waits for the job if it is running. */
+/* Free a job's containers and result (the global container of Sec. III-A
+ * and the merged output).  Waits for the job if it is running. */
 mr_status mr_release(mr_ctx* ctx, uint64_t job_id);
 
-/* Serving: admit a request if the context's HBM budget allows (MR_EBUDGET
+/* Serving (not in the paper, whose runtime runs one job at a time; it is the
+ * continuous-batching request loop this library adds around the Sec. II-A
+ * workflow): admit a request if the context's HBM budget allows (MR_EBUDGET
  * otherwise; nothing is queued and the caller retries once results have been
  * released).  Admitted requests are batched continuously: whenever one of the
  * context's internal streams has finished its previous micro-batch, every
@@ -239,7 +255,9 @@ mr_status mr_release(mr_ctx* ctx, uint64_t job_id);
  * launching.  Containers stay resident until mr_release. */
 mr_status mr_submit(mr_ctx* ctx, const mr_job_desc* desc, uint64_t* job_id);
 
-/* MR_OK when the job has finished, MR_ENOTREADY while it runs. */
+/* Serving companion of mr_submit (no counterpart in the paper): MR_OK when
+ * the job has finished, MR_ENOTREADY while it runs; also launches admitted
+ * requests as streams free up. */
 mr_status mr_poll(mr_ctx* ctx, uint64_t job_id);
 
 /* Wait for all work enqueued on the context. */
@@ -247,6 +265,34 @@ mr_status mr_sync(mr_ctx* ctx);
 
 /* Device bytes currently held by the context's jobs. */
 uint64_t mr_bytes_in_use(const mr_ctx* ctx);
+
+/* Diagnostic options of a context (none is part of the paper's method).
+ * They reach code paths that ordinary runs reach only at full size or on a
+ * failure, so that tests can check them on small inputs.  An option applies
+ * to the jobs launched after it is set. */
+typedef enum {
+  /* Polls a bounded device wait makes before it gives up: the mbarrier
+   * waits of the k-means bulk-copy and tensor-core pipelines (default 2^20
+   * polls of at most 1 us each) and the ring waits of the pipelined word
+   * count (default 2^22 polls of ~128 ns).  value = UINT64_MAX restores the
+   * default; 0 gives up at the first wait, so the job's mr_fetch returns
+   * MR_ETIMEOUT.  At most 2^40. */
+  MR_OPT_WAIT_POLLS = 0,
+  /* Upper bound on the CTAs of the k-means persistent kernels (0 = none: one
+   * CTA, or two, per SM), so that a small input runs many tiles per CTA and
+   * reaches the pipelines' steady state. */
+  MR_OPT_KM_GRID_CAP = 1,
+  /* k-means tensor-core pass: tiles each CTA's bulk-copy thread stages before
+   * it stops (0 = no limit).  The waits for the tiles it never stages run
+   * out (after MR_OPT_WAIT_POLLS polls) while earlier tiles are still in the
+   * pipeline, so the kernel's timeout path runs with copies and MMAs in
+   * flight; mr_fetch returns MR_ETIMEOUT. */
+  MR_OPT_KM_STOP_COPIES = 2
+} mr_option;
+
+/* Set a diagnostic option.  Errors: MR_EINVAL (null context, unknown
+ * option, value out of range). */
+mr_status mr_set_option(mr_ctx* ctx, mr_option opt, uint64_t value);
 
 /* Device time in milliseconds between the start and the end of a finished
  * job's kernel sequence on the context stream (the context must have been
@@ -308,8 +354,8 @@ mr_status mr_simdh_hash(const uint8_t* text, uint64_t text_bytes, const uint32_t
  * clears it before use: calls whose work overlaps on the GPU (other threads
  * or streams) race and give wrong results.
  *
- * Errors: MR_EINVAL (null pointer, out_cap too small, input of 2^40 bytes
- * or more), MR_EOVERFLOW (more distinct words than the fixed table holds;
+ * Errors: MR_EINVAL (null pointer, out_cap too small, input_bytes >=
+ * 2^40 - 1), MR_EOVERFLOW (more distinct words than the fixed table holds;
  * the result is then invalid), MR_ECUDA. */
 #define MR_NOALLOC_WC_SLOTS 131072u
 mr_status mr_wordcount_noalloc(const void* d_input, uint64_t input_bytes, void* d_out, uint64_t out_cap,

@@ -29,11 +29,15 @@ KM_FP32, KM_BF16_TC, KM_BF16X1_TC = range(3)
 EXPORTS = ("mr_create", "mr_destroy", "mr_add_job", "mr_run", "mr_fetch", "mr_result_device", "mr_release",
            "mr_submit", "mr_poll", "mr_sync", "mr_bytes_in_use", "mr_job_elapsed_ms", "mr_job_kernel_ms",
            "mr_kernel_launches",
-           "mr_status_str", "mr_last_error", "mr_wordcount_noalloc", "mr_rerun", "mr_get_tuning", "mr_simdh_hash")
+           "mr_status_str", "mr_last_error", "mr_wordcount_noalloc", "mr_rerun", "mr_get_tuning", "mr_simdh_hash",
+           "mr_set_option")
 SIMDH_PADDING, SIMDH_STREAM, SIMDH_WIDE = range(3)
 NOALLOC_WC_SLOTS = 131072
 FLAG_TIMING = 1
 FLAG_AUTOTUNE = 2
+# diagnostic options (mr_set_option)
+OPT_WAIT_POLLS, OPT_KM_GRID_CAP, OPT_KM_STOP_COPIES = range(3)
+OPT_DEFAULT = 2 ** 64 - 1
 
 
 class MRError(RuntimeError):
@@ -110,6 +114,8 @@ def load():
         lib.mr_sync.restype = st
         lib.mr_bytes_in_use.argtypes = [vp]
         lib.mr_bytes_in_use.restype = u64
+        lib.mr_set_option.argtypes = [vp, ctypes.c_int, u64]
+        lib.mr_set_option.restype = st
         lib.mr_job_elapsed_ms.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_float)]
         lib.mr_job_elapsed_ms.restype = st
         lib.mr_job_kernel_ms.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint32)]
@@ -168,7 +174,12 @@ class Context:
     """One library context: a device, a stream and the jobs queued on it."""
 
     def __init__(self, device: Optional[int] = None, stream=None, hbm_budget: int = 0,
-                 use_torch_allocator: bool = True, timing: bool = False, autotune: bool = False):
+                 use_torch_allocator: bool = True, timing: bool = False, autotune: bool = False,
+                 allocator=None):
+        """allocator: optional (alloc, free) pair of Python callables used as
+        the library's device allocator hooks in place of torch's caching
+        allocator: alloc(nbytes) returns a device address or 0 on failure,
+        free(address) releases one."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the map/reduce library runs only on the GPU")
@@ -184,7 +195,21 @@ class Context:
         cfg.hbm_budget = int(hbm_budget)
         cfg.flags = (FLAG_TIMING if timing else 0) | (FLAG_AUTOTUNE if autotune else 0)
         self._cb = None
-        if use_torch_allocator:
+        if allocator is not None:
+            u_alloc, u_free = allocator
+
+            def _alloc(_user, n):
+                try:
+                    return u_alloc(int(n)) or None
+                except Exception:
+                    return None
+
+            def _free(_user, p):
+                u_free(p)
+
+            self._cb = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+            cfg.alloc, cfg.free = self._cb
+        elif use_torch_allocator:
             dev, sptr = self.device, stream.cuda_stream
 
             def _alloc(_user, n):
@@ -305,6 +330,10 @@ class Context:
         ms, n = ctypes.c_float(), ctypes.c_uint32()
         _check(self._lib.mr_job_kernel_ms(self._h, job, ctypes.byref(ms), ctypes.byref(n)), "mr_job_kernel_ms")
         return float(ms.value), int(n.value)
+
+    def set_option(self, opt: int, value: int):
+        """Diagnostic option (OPT_*; include/mr.h mr_option) for jobs launched from now on."""
+        _check(self._lib.mr_set_option(self._h, int(opt), int(value)), "mr_set_option")
 
     @property
     def kernel_launches(self) -> int:

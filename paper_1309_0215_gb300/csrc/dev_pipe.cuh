@@ -30,15 +30,26 @@ __device__ __forceinline__ bool mbar_try(unsigned long long* b, uint32_t parity)
       : "memory");
   return ok != 0;
 }
-// Bounded wait (at most SPIN_LIMIT polls of at most SUSPEND_NS each, about a
-// second) for the completion of the phase with the given parity; gives up
-// early once *err is set, and sets it on timeout.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* b, uint32_t parity, volatile int* err) {
-  for (long long i = 0; i < SPIN_LIMIT; ++i) {
+// Bounded wait (at most `polls` polls of at most SUSPEND_NS each; the
+// default SPIN_LIMIT is about a second) for the completion of the phase with
+// the given parity; gives up early once *err is set, and sets it on timeout.
+// polls = 0 gives up at once.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, uint32_t parity, volatile int* err,
+                                          long long polls = SPIN_LIMIT) {
+  for (long long i = 0; i < polls; ++i) {
     if (mbar_try(b, parity)) return true;
     if ((i & 15) == 15 && *err) return false;
   }
   *err = 1;
+  return false;
+}
+// Teardown wait for work that is certain to complete (a bulk copy already
+// issued, MMAs already committed): polls up to SPIN_LIMIT times whatever
+// *err says, so that a CTA that gave up elsewhere still lets its in-flight
+// copies land and its MMAs finish before it frees TMEM or exits.
+__device__ __forceinline__ bool mbar_drain(unsigned long long* b, uint32_t parity) {
+  for (long long i = 0; i < SPIN_LIMIT; ++i)
+    if (mbar_try(b, parity)) return true;
   return false;
 }
 __device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, uint32_t bytes) {

@@ -803,7 +803,7 @@ template <bool D64>
 __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_pipe_kernel(
     const float* __restrict__ x, uint32_t n, uint32_t d, uint32_t k, const int32_t* __restrict__ assign,
     const int* shift, long long* __restrict__ part, unsigned long long* counts, uint32_t rows,
-    unsigned long long* timeouts) {
+    unsigned long long* timeouts, long long polls) {
   using namespace pipe;
   extern __shared__ __align__(128) unsigned char lp_sm[];
   const uint64_t kd = (uint64_t)k * d;
@@ -850,7 +850,7 @@ __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_pipe_kernel(
   uint32_t c = 0;
   for (; c < nchunks; ++c) {
     const uint32_t q = c % LP_ST, par = (c / LP_ST) & 1u;
-    if (!mbar_wait(&full[q], par, err)) break;
+    if (!mbar_wait(&full[q], par, err, polls)) break;
     const uint64_t r0 = p0 + (uint64_t)c * rows;
     const uint32_t nr = (uint32_t)(p1 - r0 < rows ? p1 - r0 : rows);
     const float* X = xs + q * xst;
@@ -875,15 +875,13 @@ __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_pipe_kernel(
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[q]);
     if (threadIdx.x == 0 && c + LP_ST < nchunks) {
-      if (!mbar_wait(&empty[q], par, err)) break;
+      if (!mbar_wait(&empty[q], par, err, polls)) break;
       issue(c + LP_ST);
     }
   }
   if (threadIdx.x == 0 && *err) {
     // let the copies still in flight land before the CTA leaves
-    for (uint32_t w = c; w < issued; ++w)
-      for (long long i = 0; i < SPIN_LIMIT && !mbar_try(&full[w % LP_ST], (w / LP_ST) & 1u); ++i) {
-      }
+    for (uint32_t w = c; w < issued; ++w) mbar_drain(&full[w % LP_ST], (w / LP_ST) & 1u);
     atomicAdd(timeouts, 1ull);
   }
   __syncthreads();
@@ -1060,7 +1058,9 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
   }
   uint32_t ls_grid = (uint32_t)di.sms < LS_MAX_CTAS ? (uint32_t)di.sms : LS_MAX_CTAS;
   if ((uint64_t)ls_grid * 1024 > n) ls_grid = (uint32_t)((n + 1023) / 1024);
+  if (b.grid_cap && ls_grid > b.grid_cap) ls_grid = b.grid_cap;
   if (ls_grid < 1) ls_grid = 1;
+  const long long polls = b.polls < 0 ? pipe::SPIN_LIMIT : b.polls;
   const int rc_bytes = (int)((uint64_t)k * (d + 1) * 4);
   const bool rc_smem = k <= 32 * KLANE && rc_bytes <= di.smem_optin;
   // as many re-check CTAs per SM as the centroid copies allow (at most 3: 48 warps)
@@ -1071,7 +1071,8 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
           cudaSuccess)
     return e;
   const uint32_t ntiles = (n + TP - 1) / TP;
-  const uint32_t agrid = ntiles < (uint32_t)di.sms * 2 ? ntiles : (uint32_t)di.sms * 2;
+  uint32_t agrid = ntiles < (uint32_t)di.sms * 2 ? ntiles : (uint32_t)di.sms * 2;
+  if (b.grid_cap && agrid > b.grid_cap) agrid = b.grid_cap;
   for (uint32_t it = 0; it < iters; ++it) {
     km_prep_kernel<<<64, 256, 0, s>>>(b.cent, k, d, b.cnorm, cmax_bits, b.sums, b.counts, b.nflag);
     if (b.precision != MR_KM_FP32) {
@@ -1096,7 +1097,7 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
       if (lp_rows)
         (d == 64 ? km_local_sum_pipe_kernel<true> : km_local_sum_pipe_kernel<false>)<<<ls_grid, LS_THREADS, lp_bytes,
                                                                                         s>>>(
-            x, n, d, k, b.assign, shift, b.part, b.counts, lp_rows, b.stats + 3);
+            x, n, d, k, b.assign, shift, b.part, b.counts, lp_rows, b.stats + 3, polls);
       else
         km_local_sum_kernel<<<ls_grid, LS_THREADS, ls_bytes, s>>>(x, n, d, k, b.assign, shift, b.part, b.counts);
       km_reduce_finalize_kernel<<<(unsigned)(((uint64_t)k * d + 31) / 32), RF_THREADS, 0, s>>>(
@@ -1129,7 +1130,8 @@ cudaError_t launch_kmeans_fp32_list(const float* x, uint32_t n, uint32_t d, cons
                                     uint64_t* nk) {
   const int asm_bytes = (DC_MAX * CS_LD + DC_MAX * TP) * 4;
   const uint32_t ntiles = (n + TP - 1) / TP;
-  const uint32_t agrid = ntiles < (uint32_t)di.sms * 2 ? ntiles : (uint32_t)di.sms * 2;
+  uint32_t agrid = ntiles < (uint32_t)di.sms * 2 ? ntiles : (uint32_t)di.sms * 2;
+  if (b.grid_cap && agrid > b.grid_cap) agrid = b.grid_cap;
   (k <= 256 ? km_assign_fp32_kernel<true> : km_assign_fp32_kernel<false>)<<<agrid, KM_THREADS, asm_bytes, s>>>(
       x, n, d, c, k, b.cnorm, b.nflag + 3, list, nlist, b.assign, b.flagged, b.nflag, b.pairs, b.nflag + 4, b.stats);
   ++*nk;

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const float* __restrict__ c, uint32_t k,
                     const float* __restrict__ cnorm, const unsigned int* cmax_bits, int32_t* __restrict__ assign,
                     uint32_t* __restrict__ list, uint32_t* nlist, uint2* __restrict__ pairs, uint32_t* npairs,
-                    unsigned long long* timeouts, float* dbg) {
+                    unsigned long long* timeouts, float* dbg, long long polls, uint32_t stop_copies) {
   extern __shared__ uint8_t tc_raw[];
   TcSmem& S = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -280,7 +280,7 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
       float4 v[8];
       if (vec) {
         // the tile was staged by the bulk copy engine
-        const bool okt = mbar_wait(&S.tfull[q2], (i / XST) & 1, err);
+        const bool okt = mbar_wait(&S.tfull[q2], (i / XST) & 1, err, polls);
         if (!__all_sync(0xffffffffu, okt)) break;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -301,8 +301,8 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
         }
       }
       if (i >= STAGES) {
-        bool ok = mbar_wait(&S.empty_a[s], (u + 1) & 1, err);
-        ok = ok && mbar_wait(&S.nx_free[s], (u + 1) & 1, err);
+        bool ok = mbar_wait(&S.empty_a[s], (u + 1) & 1, err, polls);
+        ok = ok && mbar_wait(&S.nx_free[s], (u + 1) & 1, err, polls);
         if (!__all_sync(0xffffffffu, ok)) break;
       }
 #pragma unroll
@@ -338,18 +338,21 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
       uint32_t issued = 0;
       for (uint32_t i = 0;; ++i) {
         const uint32_t tile = blockIdx.x + i * gridDim.x;
-        if (tile >= ntiles) break;
+        if (tile >= ntiles || (stop_copies && i >= stop_copies)) break;
         const int q2 = (int)(i % XST);
-        if (i >= XST && !mbar_wait(&S.tempty[q2], ((i / XST) + 1) & 1, err)) break;
+        if (i >= XST && !mbar_wait(&S.tempty[q2], ((i / XST) + 1) & 1, err, polls)) break;
         const uint32_t rows = (n - tile * TM) < (uint32_t)TM ? (n - tile * TM) : (uint32_t)TM;
         const uint32_t bytes = rows * KD * 4;
         mbar_expect_tx(&S.tfull[q2], bytes);
         bulk_g2s(S.xs[q2], x + (uint64_t)tile * TM * KD, bytes, &S.tfull[q2]);
         ++issued;
       }
-      // no copy may still be landing in shared memory when the CTA exits
+      // No copy may still be landing in shared memory when the CTA exits.
+      // Copy i was issued only after the converters released copy i - XST
+      // (which they do after its completion), so only the last XST copies
+      // can be in flight; wait for them even when a wait gave up elsewhere.
       for (uint32_t i = issued > (uint32_t)XST ? issued - XST : 0; i < issued; ++i)
-        mbar_wait(&S.tfull[i % XST], (i / XST) & 1, err);
+        mbar_drain(&S.tfull[i % XST], (i / XST) & 1);
     }
     __syncwarp();
   } else if (warp == MMA_WARP) {
@@ -365,8 +368,8 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
         const uint32_t u = i / STAGES;
         const int b = (int)(i & 1);
         const uint32_t v = i >> 1;
-        if (!mbar_wait(&S.full_a[s], u & 1, err)) break;
-        if (i >= ACCS && !mbar_wait(&S.empty_acc[b], (v + 1) & 1, err)) break;
+        if (!mbar_wait(&S.full_a[s], u & 1, err, polls)) break;
+        if (i >= ACCS && !mbar_wait(&S.empty_acc[b], (v + 1) & 1, err, polls)) break;
         tc_fence_after();
         const uint32_t dt = tmem + (uint32_t)b * 256u;
         const uint32_t ah = su32(S.a_hi[s]), al = su32(S.a_lo[s]);
@@ -383,9 +386,12 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
         mma_commit(&S.full_acc[b]);
         ++issued;
       }
-      // no MMA may still be running when TMEM is released
+      // No MMA may still be running when TMEM is released (or when the
+      // operand buffers go away with the CTA): the commit arrives once every
+      // MMA issued above has completed, and that is waited for even when a
+      // wait gave up elsewhere.
       mma_commit(&S.drained);
-      mbar_wait(&S.drained, 0, err);
+      mbar_drain(&S.drained, 0);
       (void)issued;
     }
     __syncwarp();
@@ -414,7 +420,7 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
       const int s = (int)(i % STAGES);
       const int b = (int)(i & 1);
       const uint32_t v = i >> 1;
-      const bool ok = mbar_wait(&S.full_acc[b], v & 1, err);
+      const bool ok = mbar_wait(&S.full_acc[b], v & 1, err, polls);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
       const float nxv = S.nx[s][r];
@@ -444,7 +450,7 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
       for (int a = 0; a < NSET; ++a) lb = min(lb, (t1[a] == w1 || t1[a] == w2) ? t2[a] : t1[a]);
       if (quarter != 0) {
         if (i >= ACCS) {
-          const bool okf = mbar_wait(&S.xfree[b], (v + 1) & 1, err);
+          const bool okf = mbar_wait(&S.xfree[b], (v + 1) & 1, err, polls);
           if (!__all_sync(0xffffffffu, okf)) break;
         }
         S.xw1[b][quarter - 1][r] = (uint32_t)w1;
@@ -456,7 +462,7 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
       }
       int o1[EPI_WARPS / 4 - 1], o2[EPI_WARPS / 4 - 1], ol[EPI_WARPS / 4 - 1];
       {
-        const bool okx = mbar_wait(&S.xfull[b], v & 1, err);
+        const bool okx = mbar_wait(&S.xfull[b], v & 1, err, polls);
         if (!__all_sync(0xffffffffu, okx)) break;
 #pragma unroll
         for (int u = 0; u < EPI_WARPS / 4 - 1; ++u) {
@@ -535,7 +541,7 @@ size_t km_tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
 cudaError_t launch_km_tc_kernel(int terms, const float* x, uint32_t n, uint32_t d, const float* c, uint32_t k,
                                 const float* cnorm, const unsigned int* cmax_bits, int32_t* assign, uint32_t* list,
                                 uint32_t* nlist, uint2* pairs, uint32_t* npairs, unsigned long long* timeouts,
-                                float* dbg, int grid, cudaStream_t s) {
+                                float* dbg, int grid, cudaStream_t s, long long polls, uint32_t stop_copies) {
   const int smem = (int)km_tc_smem_bytes();
   cudaError_t e;
   if (terms == 3) {
@@ -543,13 +549,13 @@ cudaError_t launch_km_tc_kernel(int terms, const float* x, uint32_t n, uint32_t 
         cudaSuccess)
       return e;
     km_tc_assign_kernel<3><<<grid, TC_THREADS, smem, s>>>(x, n, d, c, k, cnorm, cmax_bits, assign, list, nlist,
-                                                           pairs, npairs, timeouts, dbg);
+                                                           pairs, npairs, timeouts, dbg, polls, stop_copies);
   } else {
     if ((e = cudaFuncSetAttribute(km_tc_assign_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
         cudaSuccess)
       return e;
     km_tc_assign_kernel<1><<<grid, TC_THREADS, smem, s>>>(x, n, d, c, k, cnorm, cmax_bits, assign, list, nlist,
-                                                           pairs, npairs, timeouts, dbg);
+                                                           pairs, npairs, timeouts, dbg, polls, stop_copies);
   }
   return cudaGetLastError();
 }
@@ -557,13 +563,15 @@ cudaError_t launch_km_tc_kernel(int terms, const float* x, uint32_t n, uint32_t 
 cudaError_t launch_kmeans_tc_assign(const float* x, uint32_t n, uint32_t d, const float* c, uint32_t k,
                                     KmBuffers& b, const DevInfo& di, cudaStream_t s, uint64_t* nk) {
   const uint32_t ntiles = (n + TM - 1) / TM;
-  const int grid = (int)(ntiles < (uint32_t)di.sms ? ntiles : (uint32_t)di.sms);
+  uint32_t grid = ntiles < (uint32_t)di.sms ? ntiles : (uint32_t)di.sms;
+  if (b.grid_cap && grid > b.grid_cap) grid = b.grid_cap;
   uint32_t* list = reinterpret_cast<uint32_t*>(b.cent_bf16_norm);
   const int terms = b.precision == MR_KM_BF16X1_TC ? 1 : 3;
   cudaError_t e = kt_begin(b.kt, s);
   if (e != cudaSuccess) return e;
   e = launch_km_tc_kernel(terms, x, n, d, c, k, b.cnorm, b.nflag + 3, b.assign, list, b.nflag + 1, b.pairs,
-                          b.nflag + 4, b.stats + 3, nullptr, grid, s);
+                          b.nflag + 4, b.stats + 3, nullptr, (int)grid, s, b.polls < 0 ? SPIN_LIMIT : b.polls,
+                          b.stop_copies);
   if (e != cudaSuccess || (e = kt_end(b.kt, s)) != cudaSuccess) return e;
   ++*nk;
   // near ties of the tensor-core pass: FP32 pass over the list (its own near

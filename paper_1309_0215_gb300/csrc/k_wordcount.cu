@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(MAP_THREADS, 5) wc_map_kernel(JobDev J) {
 constexpr int PIPE_PAIRS = 4;
 constexpr int PIPE_THREADS = 2 * PIPE_PAIRS * 32;
 constexpr int RING = 256;
-constexpr long long PIPE_SPIN_LIMIT = 1ll << 22;  // polls of ~128 ns: about half a second
+constexpr long long PIPE_SPIN_LIMIT = 1ll << 22;  // default polls of ~128 ns: about half a second
 
 struct RingRec {
   unsigned long long w0, w1;
@@ -108,7 +108,8 @@ struct PipeSmem {
 __device__ __forceinline__ unsigned vload(const unsigned int* p) { return *reinterpret_cast<const volatile unsigned int*>(p); }
 __device__ __forceinline__ void vstore(unsigned int* p, unsigned v) { *reinterpret_cast<volatile unsigned int*>(p) = v; }
 
-__global__ void __launch_bounds__(PIPE_THREADS, 4) wc_pipe_kernel(JobDev J) {
+// polls: how many times a ring wait polls before it gives up (0: at once).
+__global__ void __launch_bounds__(PIPE_THREADS, 4) wc_pipe_kernel(JobDev J, long long polls) {
   extern __shared__ __align__(16) unsigned char pipe_smem[];
   PipeSmem& S = *reinterpret_cast<PipeSmem*>(pipe_smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(PIPE_THREADS, 4) wc_pipe_kernel(JobDev J) {
     }
     // wait for the reducer to drain the ring (or to give up)
     bool drained = false, dead = false;
-    for (long long it = 0; it < PIPE_SPIN_LIMIT; ++it) {
+    for (long long it = 0; it < polls; ++it) {
       dead = vload(&R.dead) != 0;
       drained = vload(&R.head) == vload(&R.tail);
       if (dead || drained) break;
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(PIPE_THREADS, 4) wc_pipe_kernel(JobDev J) {
         continue;
       }
       if (dn) break;
-      if (++idle > PIPE_SPIN_LIMIT) {
+      if (++idle > polls) {
         if (lane == 0) {
           __threadfence_block();
           vstore(&R.dead, 1u);
@@ -2109,7 +2110,7 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
 }
 
 cudaError_t launch_wordcount(const uint8_t* in, uint64_t n, const WcBuffers& b, const DevInfo& di, cudaStream_t s,
-                             uint64_t* nk, bool pipelined, KTimer* kt) {
+                             uint64_t* nk, bool pipelined, KTimer* kt, long long pipe_polls) {
   cudaError_t e;
   // table (keys then counts) and state words start at zero
   if ((e = cudaMemsetAsync(b.key, 0, wc_table_bytes(b.cap), s)) != cudaSuccess) return e;
@@ -2124,7 +2125,7 @@ cudaError_t launch_wordcount(const uint8_t* in, uint64_t n, const WcBuffers& b, 
     const uint64_t gmax = 4ull * di.sms;
     if (grid > gmax) grid = gmax;
     if ((e = kt_begin(kt, s)) != cudaSuccess) return e;
-    wc_pipe_kernel<<<(unsigned)grid, PIPE_THREADS, smem, s>>>(J);
+    wc_pipe_kernel<<<(unsigned)grid, PIPE_THREADS, smem, s>>>(J, pipe_polls < 0 ? PIPE_SPIN_LIMIT : pipe_polls);
     if ((e = cudaGetLastError()) != cudaSuccess || (e = kt_end(kt, s)) != cudaSuccess) return e;
     ++*nk;
   } else if (n > 0) {

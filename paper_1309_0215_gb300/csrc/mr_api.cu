@@ -142,6 +142,10 @@ struct mr_ctx {
   // later jobs so that adding a job creates none in the steady state
   std::vector<cudaEvent_t> ev_done, ev_timing;
   std::vector<KTimer*> kt_pool;
+  // diagnostics (mr_set_option), applied to jobs when they are launched
+  long long opt_polls = -1;       // bounded device waits: polls (< 0: default)
+  uint32_t opt_km_grid_cap = 0;   // k-means persistent kernels: CTA cap (0: none)
+  uint32_t opt_km_stop_copies = 0;  // k-means tensor-core kernel: tiles staged per CTA (0: all)
 };
 
 namespace {
@@ -458,7 +462,8 @@ mr_status enqueue_plain_on(mr_ctx* c, Job* j, cudaStream_t st) {
       ++c->launches;
       break;
     case MR_WORDCOUNT:
-      MR_CUDA_TRY(launch_wordcount(j->in, n, j->wc, c->di, st, &c->launches, j->desc.wc_pipelined != 0, j->kt));
+      MR_CUDA_TRY(launch_wordcount(j->in, n, j->wc, c->di, st, &c->launches, j->desc.wc_pipelined != 0, j->kt,
+                                   c->opt_polls));
       break;
     case MR_HIST_U32:
       MR_CUDA_TRY(launch_hist_keys(reinterpret_cast<const uint32_t*>(j->in), n / 4, j->desc.hist_bins,
@@ -476,6 +481,9 @@ mr_status enqueue_plain_on(mr_ctx* c, Job* j, cudaStream_t st) {
       int32_t* oa = reinterpret_cast<int32_t*>(p + (uint64_t)K * D * 4);
       unsigned long long* os = reinterpret_cast<unsigned long long*>(p + km_stats_offset(K, D, N));
       j->km.kt = j->kt;
+      j->km.polls = c->opt_polls;
+      j->km.grid_cap = c->opt_km_grid_cap;
+      j->km.stop_copies = c->opt_km_stop_copies;
       MR_CUDA_TRY(launch_kmeans(reinterpret_cast<const float*>(j->in), j->km_init_dev, j->desc.km_iters, j->km,
                                 c->di, st, oc, oa, os, &c->launches));
       break;
@@ -871,7 +879,7 @@ mr_status wait_job(mr_ctx* c, Job* j, uint64_t* wc_result_bytes = nullptr) {
     mr_status s = alloc_wc(c, j, cap);
     if (s) return s;
     MR_CUDA_TRY(launch_wordcount(j->in, j->desc.input_bytes, j->wc, c->di, c->stream, &c->launches,
-                                 j->desc.wc_pipelined != 0));
+                                 j->desc.wc_pipelined != 0, nullptr, c->opt_polls));
     MR_CUDA_TRY(cudaEventRecord(j->done, c->stream));
     MR_CUDA_TRY(cudaEventSynchronize(j->done));
   }
@@ -1088,13 +1096,21 @@ mr_status mr_run(mr_ctx* c, mr_mode mode) {
     if (j && j->state == JOB_PENDING) jobs.push_back(j);
   }
   c->pending.clear();
-  if (mode == MR_RUN_BATCHED) return enqueue_batched(c, jobs);
-  if (mode == MR_RUN_CONCURRENT) return enqueue_concurrent(c, jobs);
-  for (Job* j : jobs) {
-    mr_status st = enqueue_plain(c, j);
-    if (st) return st;
+  mr_status st = MR_OK;
+  if (mode == MR_RUN_BATCHED) {
+    st = enqueue_batched(c, jobs);
+  } else if (mode == MR_RUN_CONCURRENT) {
+    st = enqueue_concurrent(c, jobs);
+  } else {
+    for (Job* j : jobs)
+      if ((st = enqueue_plain(c, j)) != MR_OK) break;
   }
-  return MR_OK;
+  // jobs that were not launched (an allocation or launch failed on the way)
+  // stay pending, so that a later mr_run can launch them
+  if (st)
+    for (Job* j : jobs)
+      if (j->state == JOB_PENDING) c->pending.push_back(j->id);
+  return st;
 }
 
 mr_status mr_fetch(mr_ctx* c, uint64_t job_id, void* buf, uint64_t buf_bytes, uint64_t* needed) {
@@ -1195,6 +1211,25 @@ mr_status mr_sync(mr_ctx* c) {
 }
 
 uint64_t mr_bytes_in_use(const mr_ctx* c) { return c ? c->in_use : 0; }
+
+mr_status mr_set_option(mr_ctx* c, mr_option opt, uint64_t value) {
+  if (!c) return MR_EINVAL;
+  switch (opt) {
+    case MR_OPT_WAIT_POLLS:
+      if (value != UINT64_MAX && value > (1ull << 40)) return MR_EINVAL;
+      c->opt_polls = value == UINT64_MAX ? -1 : (long long)value;
+      return MR_OK;
+    case MR_OPT_KM_GRID_CAP:
+      if (value > 0xFFFFFFFFull) return MR_EINVAL;
+      c->opt_km_grid_cap = (uint32_t)value;
+      return MR_OK;
+    case MR_OPT_KM_STOP_COPIES:
+      if (value > 0xFFFFFFFFull) return MR_EINVAL;
+      c->opt_km_stop_copies = (uint32_t)value;
+      return MR_OK;
+  }
+  return MR_EINVAL;
+}
 
 uint64_t mr_kernel_launches(const mr_ctx* c) { return c ? c->launches : 0; }
 

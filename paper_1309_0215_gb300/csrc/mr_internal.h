@@ -95,8 +95,9 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
 // *nk is incremented by the number of kernels launched.
 // pipelined: the map pass runs as mapper warps handing cache misses to
 // reducer warps through shared-memory rings (wc_pipe_kernel).
+// pipe_polls: polls of the pipelined pass's bounded ring waits (< 0: default).
 cudaError_t launch_wordcount(const uint8_t* in, uint64_t n, const WcBuffers& b, const DevInfo& di, cudaStream_t s,
-                             uint64_t* nk, bool pipelined = false, KTimer* kt = nullptr);
+                             uint64_t* nk, bool pipelined = false, KTimer* kt = nullptr, long long pipe_polls = -1);
 
 // ---------------------------------------------------------------- k-means
 struct KmBuffers {
@@ -120,6 +121,12 @@ struct KmBuffers {
   KTimer* kt = nullptr;         // times the distance pass of each iteration
   int fx_shift = 32;            // fixed-point scale exponent
   int precision = 0;
+  // diagnostics (mr_set_option): polls of a bounded device wait (< 0: the
+  // default), cap on the CTAs of the persistent kernels (0: none), tiles the
+  // tensor-core kernel's bulk-copy thread stages per CTA (0: all)
+  long long polls = -1;
+  uint32_t grid_cap = 0;
+  uint32_t stop_copies = 0;
 };
 size_t km_scratch_bytes(uint32_t n, uint32_t d, uint32_t k, int precision);
 cudaError_t km_carve(KmBuffers& b, uint8_t* base, size_t bytes);

@@ -31,6 +31,28 @@ def _run(mr, x, init, iters, precision=0, on_device=True):
     return mr.kmeans(x, init, iters, precision)
 
 
+def _assign_all(x, c):
+    """The oracle's FP64 assignment of every point, computed serially on row
+    slices by a pool of host threads (the oracle call releases the GIL)."""
+    import concurrent.futures as cf
+    import os
+    nth = max(1, min(32, os.cpu_count() or 1))
+    step = (x.shape[0] + nth - 1) // nth
+    parts = [x[i: i + step] for i in range(0, x.shape[0], step)]
+    with cf.ThreadPoolExecutor(nth) as ex:
+        return np.concatenate(list(ex.map(lambda p: oracle.kmeans_assign(p, c), parts)))
+
+
+def _run_ctx(mr, ctx, dx, cur, iters, precision):
+    n, d = dx.shape
+    j = ctx.add_job(mr.KMEANS_F32, dx, km_dims=d, km_k=cur.shape[0], km_iters=iters, km_init=_dev(cur),
+                    km_precision=precision)
+    ctx.run()
+    out = mr.split_kmeans_result(ctx.fetch(j), n, d, cur.shape[0])
+    ctx.release(j)
+    return out
+
+
 @pytest.mark.parametrize("n,d,k,iters", [
     (20_000, 64, 256, 3),   # the workload's shape, reduced N
     (5_001, 37, 50, 2),     # ragged dims / tiles
@@ -122,8 +144,11 @@ def test_kmeans_rejects_bad_args(mr):
 
 @pytest.mark.slow
 def test_kmeans_full_size_fp32(mr):
-    """4M x 64 points, K = 256, 10 iterations: determinism across a split run,
-    sampled exact assignment check against FP64 and a full FP64 update check."""
+    """4M x 64 points, K = 256, 10 iterations: determinism across a split run;
+    the tenth iteration's assignment of EVERY point equals the FP64 oracle's
+    on the GPU's ninth centroids, for the FP32 path and both tensor-core
+    paths (whose persistent CTAs run ~216 tiles each here); and the final
+    update equals the oracle's FP64 update within tolerance."""
     import torch
     x, _, _ = synth.kmeans_points(4 << 20, 64, 256)
     init = synth.kmeans_init(x, 256)
@@ -132,11 +157,58 @@ def test_kmeans_full_size_fp32(mr):
     c9, _, _ = mr.kmeans(dx, _dev(init), 9)
     c10b, a10b, _ = mr.kmeans(dx, _dev(c9), 1)
     assert np.array_equal(c10, c10b) and np.array_equal(a10, a10b)
-    rng = np.random.default_rng(0)
-    sample = rng.choice(x.shape[0], 3000, replace=False)
-    assert np.array_equal(a10[sample], oracle.kmeans_assign(x[sample], c9))
+    a_ref = _assign_all(x, c9)
+    assert np.array_equal(a10, a_ref)
+    for precision in (1, 2):
+        _, a_tc, st = mr.kmeans(dx, _dev(c9), 1, precision)
+        assert np.array_equal(a_tc, a_ref), precision
+        assert int(st[3]) == 0
     c_upd, _ = oracle.kmeans_update(x, a10, c9)
     assert _rel_err(c10, c_upd) <= TOL
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_kmeans_many_tiles_per_cta_teacher_forced(mr, precision):
+    """The persistent kernels capped at 4 CTAs: each tensor-core CTA runs ~39
+    tiles of 128 points (its copy ring, operand stages, TMEM accumulators and
+    key hand-off all wrap many times), each FP32 CTA ~78 tiles of 64, and each
+    update CTA ~50 chunks through its 3-stage ring.  Every assignment of every
+    iteration, started from the oracle's centroids, equals the oracle's."""
+    x, _, _ = synth.kmeans_points(20_000, 64, 256, seed=45 + precision)
+    cur = synth.kmeans_init(x, 256, seed=46)
+    dx = _dev(x)
+    ctx = mr.Context()
+    ctx.set_option(mr.OPT_KM_GRID_CAP, 4)
+    for _ in range(3):
+        a_ref = oracle.kmeans_assign(x, cur)
+        c_ref, _ = oracle.kmeans_update(x, a_ref, cur)
+        c, a, st = _run_ctx(mr, ctx, dx, cur, 1, precision)
+        assert np.array_equal(a, a_ref)
+        assert _rel_err(c, c_ref) <= TOL
+        assert int(st[3]) == 0
+        cur = c_ref
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_kmeans_eight_tiles_per_cta_natural_grid(mr, precision):
+    """152 x 8 x 128 points at the default grid (one tensor-core CTA per SM):
+    every CTA runs 8 tiles, past the two-deep rings' first reuse.  All points
+    against the oracle, teacher-forced for two iterations."""
+    import torch
+    n = torch.cuda.get_device_properties(0).multi_processor_count * 8 * 128
+    x, _, _ = synth.kmeans_points(n, 64, 256, seed=47)
+    cur = synth.kmeans_init(x, 256, seed=48)
+    dx = _dev(x)
+    ctx = mr.Context()
+    for _ in range(2):
+        a_ref = _assign_all(x, cur)
+        c_ref, _ = oracle.kmeans_update(x, a_ref, cur)
+        c, a, st = _run_ctx(mr, ctx, dx, cur, 1, precision)
+        assert np.array_equal(a, a_ref)
+        assert _rel_err(c, c_ref) <= TOL
+        cur = c_ref
+    ctx.close()
 
 
 @pytest.mark.parametrize("precision", [1, 2])

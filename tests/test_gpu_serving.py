@@ -3,7 +3,8 @@
 Requests are submitted in waves while earlier ones are still running, so
 they are launched in several overlapping micro-batches; each result must be
 the same as the same request run alone (bit for bit, k-means included: its
-sums are exact integers) and, for the integer kinds, equal the oracle."""
+sums are exact integers) and equal the oracle (k-means: the FP64 argmin
+assignments exactly, centroids within 1e-5 relative)."""
 import numpy as np
 import pytest
 
@@ -84,6 +85,14 @@ def test_serving_mix_equals_alone(mr):
             assert g == oracle.hist_rgb8(data).tobytes()
         elif kind == "lr":
             assert g == oracle.linreg_i8(data).tobytes()
+        else:  # k-means: FP64 argmin assignments, centroids within 1e-5 of the FP64 means
+            x, init, _ = data
+            c_ref, a_ref = oracle.kmeans(x, init, 3)
+            c, a, st = mr.split_kmeans_result(g, x.shape[0], x.shape[1], init.shape[0])
+            assert np.array_equal(a, a_ref)
+            num = np.linalg.norm(c.astype(np.float64) - c_ref.astype(np.float64), axis=1)
+            assert float((num / np.maximum(np.linalg.norm(c_ref.astype(np.float64), axis=1), 1.0)).max()) <= 1e-5
+            assert int(st[3]) == 0
     for j in ids:
         served.release(j)
     assert served.bytes_in_use < (64 << 20)  # only reusable scratch stays

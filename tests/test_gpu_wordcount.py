@@ -99,6 +99,21 @@ def test_wc_zipf_16MiB_bit_exact(mr):
     assert sum(c for _, c in recs) == len(ranks)
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("pipelined", [False, True])
+def test_wc_zipf_320MiB_bit_exact(mr, pipelined):
+    """320 MiB of the same generator's text, past the size at which every warp
+    of the map kernel (5 CTAs x 8 warps per SM, 64 segments of 512 bytes
+    between hot-key cache merges: ~199 MB per launch) merges its cache into
+    the global table in mid-stream and then re-learns the hot keys."""
+    import torch
+    text, ranks, _ = synth.wc_text(320 << 20, seed=synth.SEED_BASE + 11)
+    got = mr.wordcount(torch.from_numpy(text).cuda(), pipelined=pipelined)
+    assert got == oracle.wordcount(text)
+    recs = oracle.parse_wordcount(got)
+    assert sum(c for _, c in recs) == len(ranks)
+
+
 @pytest.mark.parametrize("torch_alloc", [False, True])
 def test_contexts_release_their_memory(mr, torch_alloc):
     """Without allocator hooks a context allocates from a pool of its own that

@@ -4,7 +4,8 @@ pool, or a latency-critical loop that cannot afford cudaMalloc's implicit
 synchronisation).  Its scratch is a fixed device array inside the library.
 
 Called through the C ABI and compared, byte for byte, with the regular
-word-count entry point (mr_add_job / mr_run / mr_fetch) on two calls in a row
+word-count entry point (mr_add_job / mr_run / mr_fetch) and with the CPU
+oracle on two calls in a row
 with different inputs, so a second call cannot pass on the first call's left-
 over table contents.  This file is collected last on purpose.
 """
@@ -13,6 +14,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -41,7 +43,11 @@ def test_noalloc_matches_regular_entry_point_twice(mr):
         st, d_out, nbytes = _call(mr, d_in)
         assert st == mr.MR_OK
         assert nbytes == len(expect)
-        assert d_out[:nbytes].cpu().numpy().tobytes() == expect
+        got = d_out[:nbytes].cpu().numpy().tobytes()
+        assert got == expect
+        # and with the CPU oracle, so that code both entry points share
+        # (the merge and sort after the map pass) is checked independently
+        assert got == oracle.wordcount(text)
 
 
 def test_noalloc_rejects_small_output_and_reports_overflow(mr):
