@@ -528,13 +528,17 @@ __global__ void km_maxabs_kernel(const float* __restrict__ x, uint64_t cnt, unsi
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
-// Fixed-point exponent s: max|x| * 2^s * n < 2^62, capped to [0, 60].
+// Fixed-point exponent s (at most 60): the largest with max|x| 2^s < 2^39 and
+// max|x| 2^s n < 2^62, so every q = rint(x 2^s) fits 40 bits (the update's
+// hi/lo split) and no sum of n of them can overflow int64.  s may be
+// negative for very large inputs; x 2^s then rounds only where it is far
+// below 1/2, and rounds to 0 either way.
 __global__ void km_scale_kernel(const unsigned int* maxabs, uint32_t n, int* shift) {
   const float m = __uint_as_float(*maxabs);
   int s = 60;
   if (m > 0.f) {
-    const double lim = ldexp(1.0, 62);
-    while (s > 0 && (double)m * ldexp(1.0, s) * (double)n >= lim) --s;
+    const double lim = fmin(ldexp(1.0, 39), ldexp(1.0, 62) / (double)n);
+    while (s > -200 && (double)m * ldexp(1.0, s) >= lim) --s;
   }
   *shift = s;
 }
@@ -791,14 +795,44 @@ __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_kernel(const float
 // ring with bulk copies (completion counted on one mbarrier per stage), so
 // loads stay in flight while the warps add earlier chunks; warp w takes rows
 // w, w + 32, ... of a chunk and then releases the stage on a second mbarrier,
-// which thread 0 waits on before refilling the stage.  Every wait is bounded;
-// on timeout the CTA stops once its copies have landed and counts itself in
-// *timeouts.
+// which thread 0 waits on before refilling the stage.
+//
+// Exact sums without 64-bit shared atomics.  The scale keeps |x 2^s| < 2^39
+// (km_scale_kernel), so q = rint(x 2^s) = hi 2^20 + lo with hi, lo integers
+// of magnitude <= 2^19, both formed by FP32 adds that are exact (lq_split);
+// each goes into a 32-bit shared-memory array with a non-returning add.
+// Within a window of at most LP_FLUSH_ROWS points no 32-bit sum can overflow,
+// so after each window the CTA adds hi 2^20 + lo of every (cluster, dim) into
+// its own int64 partial in global memory (plain read-modify-write: no other
+// CTA touches it) and clears the arrays.  Integer sums stay exact and
+// order-independent, equal to the sum of rint(x 2^s) formed any other way.
+//
+// Every wait is bounded.  The loop runs the same chunks and barriers in every
+// thread whatever happens; after a wait gives up, chunks are skipped, thread
+// 0 issues no more copies (it issues chunk c + LP_ST only after it has seen
+// chunk c land), lets the copies it issued land, and the CTA counts itself
+// in *timeouts.
 constexpr int LP_ST = 3;
 constexpr uint32_t LP_CHUNK_MAX = 24 * 1024;  // bytes of points per stage, at most
+constexpr uint32_t LP_FLUSH_ROWS = 4095;     // 4095 * 2^19 < 2^31
 __host__ __device__ constexpr uint64_t lp_fixed_bytes(uint64_t kd, uint64_t k) {
   return (((2 * kd + k) * 4 + 127) & ~127ull) + 2 * LP_ST * 8 + 16;
 }
+// q = rint(v) for |v| < 2^39 as hi 2^20 + lo (|hi|, |lo| <= 2^19).  hf = v
+// rounded to a multiple of 2^20 (adding 1.5 2^43, whose unit in the last
+// place is 2^20, and subtracting it back are exact apart from that rounding);
+// lf = v - hf is exact (|lf| <= 2^19 on v's own grid); hi = hf / 2^20 and
+// lo = rint(lf) are read from the low bits of a sum with 1.5 2^23, whose
+// unit in the last place is 1 (ties to even).  hf is an even integer, so
+// rint(v) = hf + rint(lf).
+__device__ __forceinline__ void lq_split(float v, int& hi, int& lo) {
+  const float hf = __fsub_rn(__fadd_rn(v, 0x1.8p43f), 0x1.8p43f);
+  const float lf = __fsub_rn(v, hf);
+  hi = (int)(__float_as_uint(__fmaf_rn(hf, 0x1p-20f, 0x1.8p23f)) - 0x4B400000u);
+  lo = (int)(__float_as_uint(__fadd_rn(lf, 0x1.8p23f)) - 0x4B400000u);
+}
+__device__ __forceinline__ void red_s32(int* p, int v) { atomicAdd(p, v); }
+
 template <bool D64>
 __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_pipe_kernel(
     const float* __restrict__ x, uint32_t n, uint32_t d, uint32_t k, const int32_t* __restrict__ assign,
@@ -807,9 +841,9 @@ __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_pipe_kernel(
   using namespace pipe;
   extern __shared__ __align__(128) unsigned char lp_sm[];
   const uint64_t kd = (uint64_t)k * d;
-  uint32_t* SL = reinterpret_cast<uint32_t*>(lp_sm);
-  uint32_t* SH = SL + kd;
-  unsigned int* C = SH + kd;
+  int* HI = reinterpret_cast<int*>(lp_sm);
+  int* LO = HI + kd;
+  unsigned int* C = reinterpret_cast<unsigned int*>(LO + kd);
   float* xs = reinterpret_cast<float*>(lp_sm + (((2 * kd + k) * 4 + 127) & ~127ull));
   const uint64_t xst = (uint64_t)rows * d;  // floats per stage
   int32_t* as = reinterpret_cast<int32_t*>(xs + LP_ST * xst);
@@ -822,7 +856,8 @@ __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_pipe_kernel(
   const uint64_t p0 = (uint64_t)blockIdx.x * per;
   const uint64_t p1 = p0 + per < (uint64_t)n ? p0 + per : (uint64_t)n;
   const uint32_t nchunks = p0 < p1 ? (uint32_t)((p1 - p0 + rows - 1) / rows) : 0u;
-  for (uint64_t i = threadIdx.x; i < 2 * kd; i += LS_THREADS) SL[i] = 0;
+  const uint32_t fc = rows < LP_FLUSH_ROWS ? LP_FLUSH_ROWS / rows : 1u;  // chunks per window
+  for (uint64_t i = threadIdx.x; i < 2 * kd; i += LS_THREADS) HI[i] = 0;
   for (uint32_t i = threadIdx.x; i < k; i += LS_THREADS) C[i] = 0;
   if (threadIdx.x == 0) {
     *err = 0;
@@ -833,7 +868,7 @@ __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_pipe_kernel(
     fence_mbar_init();
   }
   __syncthreads();
-  uint32_t issued = 0;  // thread 0: chunks whose copies were started
+  uint32_t issued = 0, seen = 0;  // thread 0: chunks whose copies were started / seen landed
   auto issue = [&](uint32_t c) {
     const uint32_t q = c % LP_ST;
     const uint64_t r0 = p0 + (uint64_t)c * rows;
@@ -847,47 +882,72 @@ __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_pipe_kernel(
   if (threadIdx.x == 0)
     for (uint32_t c = 0; c < nchunks && c < (uint32_t)LP_ST; ++c) issue(c);
   const float scale = ldexpf(1.f, *shift);
-  uint32_t c = 0;
-  for (; c < nchunks; ++c) {
+  long long* P = part + (uint64_t)blockIdx.x * kd;
+  bool written = false;  // the CTA's partial holds a window already (CTA-uniform)
+  auto flush = [&]() {
+    for (uint64_t i = threadIdx.x; i < kd; i += LS_THREADS) {
+      const long long v = (long long)HI[i] * (1ll << 20) + (long long)LO[i];
+      P[i] = written ? P[i] + v : v;
+      HI[i] = 0;
+      LO[i] = 0;
+    }
+    written = true;
+  };
+  for (uint32_t c = 0; c < nchunks; ++c) {
     const uint32_t q = c % LP_ST, par = (c / LP_ST) & 1u;
-    if (!mbar_wait(&full[q], par, err, polls)) break;
-    const uint64_t r0 = p0 + (uint64_t)c * rows;
-    const uint32_t nr = (uint32_t)(p1 - r0 < rows ? p1 - r0 : rows);
-    const float* X = xs + q * xst;
-    const int32_t* A = as + q * rows;
-    for (uint32_t j = warp; j < nr; j += LS_THREADS / 32) {
-      const int a = A[j];
-      const uint32_t cl = (a < 0 || (uint32_t)a >= k) ? 0u : (uint32_t)a;
-      if (lane == 0) atomicAdd(&C[cl], 1u);
-      if (D64) {  // lane holds dimensions lane and lane + 32
-        const float* row = X + j * 64u;
-        const uint32_t b = cl * 64u + lane;
-        const long long q0 = rint_i64(row[lane] * scale), q1 = rint_i64(row[lane + 32] * scale);
-        add64_split(SL + b, SH + b, q0);
-        add64_split(SL + b + 32, SH + b + 32, q1);
-      } else {
-        const float* row = X + (uint64_t)j * d;
-        const uint32_t b = cl * d;
-        for (uint32_t dj = lane; dj < d; dj += 32) add64_split(SL + b + dj, SH + b + dj, rint_i64(row[dj] * scale));
+    const bool ok = !*err && mbar_wait(&full[q], par, err, polls);
+    if (ok) {
+      if (threadIdx.x == 0) seen = c + 1;
+      const uint64_t r0 = p0 + (uint64_t)c * rows;
+      const uint32_t nr = (uint32_t)(p1 - r0 < rows ? p1 - r0 : rows);
+      const float* X = xs + q * xst;
+      const int32_t* A = as + q * rows;
+      for (uint32_t j = warp; j < nr; j += LS_THREADS / 32) {
+        const int a = A[j];
+        const uint32_t cl = (a < 0 || (uint32_t)a >= k) ? 0u : (uint32_t)a;
+        if (lane == 0) atomicAdd(&C[cl], 1u);
+        int h0, l0;
+        if (D64) {  // lane holds dimensions lane and lane + 32
+          const float* row = X + j * 64u;
+          const uint32_t b = cl * 64u + lane;
+          int h1, l1;
+          lq_split(row[lane] * scale, h0, l0);
+          lq_split(row[lane + 32] * scale, h1, l1);
+          red_s32(HI + b, h0);
+          red_s32(LO + b, l0);
+          red_s32(HI + b + 32, h1);
+          red_s32(LO + b + 32, l1);
+        } else {
+          const float* row = X + (uint64_t)j * d;
+          const uint32_t b = cl * d;
+          for (uint32_t dj = lane; dj < d; dj += 32) {
+            lq_split(row[dj] * scale, h0, l0);
+            red_s32(HI + b + dj, h0);
+            red_s32(LO + b + dj, l0);
+          }
+        }
       }
     }
     fence_proxy_async();
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[q]);
-    if (threadIdx.x == 0 && c + LP_ST < nchunks) {
-      if (!mbar_wait(&empty[q], par, err, polls)) break;
-      issue(c + LP_ST);
+    // refill the stage only once this thread has seen chunk c land and every
+    // warp is done with it
+    if (threadIdx.x == 0 && ok && c + LP_ST < nchunks && mbar_wait(&empty[q], par, err, polls)) issue(c + LP_ST);
+    if ((c + 1) % fc == 0 && c + 1 < nchunks) {
+      __syncthreads();
+      flush();
+      __syncthreads();
     }
   }
   if (threadIdx.x == 0 && *err) {
-    // let the copies still in flight land before the CTA leaves
-    for (uint32_t w = c; w < issued; ++w) mbar_drain(&full[w % LP_ST], (w / LP_ST) & 1u);
+    // let the copies still in flight land before the CTA leaves: chunks
+    // [seen, issued), at most one per stage
+    for (uint32_t w = seen; w < issued; ++w) mbar_drain(&full[w % LP_ST], (w / LP_ST) & 1u);
     atomicAdd(timeouts, 1ull);
   }
   __syncthreads();
-  long long* P = part + (uint64_t)blockIdx.x * kd;
-  for (uint64_t i = threadIdx.x; i < kd; i += LS_THREADS)
-    P[i] = (long long)(((unsigned long long)SH[i] << 32) | SL[i]);
+  flush();
   for (uint32_t i = threadIdx.x; i < k; i += LS_THREADS)
     if (C[i]) atomicAdd(counts + i, (unsigned long long)C[i]);
 }
