@@ -287,9 +287,11 @@ def run_ours(args):
             a = ctx.add_job(mr.WORDCOUNT, d_t, wc_pipelined=int(args.pipelined))
             ctx.run()
             return [a]
-        dominant = ("wc_pipe_kernel" if args.pipelined else "wc_map_kernel",
-                    ["paper_1309_0215_gb300/csrc/k_wordcount.cu", "paper_1309_0215_gb300/csrc/dev_wordcount.cuh"],
-                    d_t.numel())
+        # the plain map pass runs the CTA-table kernel from 64 MiB on
+        mapk = "wc_pipe_kernel" if args.pipelined else (
+            "wc_map_cta_kernel" if d_t.numel() >= (64 << 20) else "wc_map_kernel")
+        dominant = (mapk, ["paper_1309_0215_gb300/csrc/k_wordcount.cu",
+                           "paper_1309_0215_gb300/csrc/dev_wordcount.cuh"], d_t.numel())
 
     # Jobs are released RELEASE_LAG steps after they were enqueued, as a
     # serving loop releases its results: the GPU stays that many steps ahead of
@@ -1066,6 +1068,88 @@ def extra_configs(args) -> dict:
 
 
 
+def run_histkeys_sweep(args):
+    """Local arrays vs the global array as the key range grows (the GPU form
+    of the paper's "eliminating local arrays" experiment, Sec. III-E and its
+    evaluation in Sec. IV-B): 256M u32 keys uniform on [0, bins), bins from
+    2^10 to 2^28, so the u32 counters go from a few KB (shared memory) past
+    the 129 MB L2 into HBM.  Each configuration is timed on its counting
+    kernel (CUDA events around every launch); results are checked against
+    the count invariant, and at the smallest sizes against the oracle."""
+    import numpy as np
+    import torch
+    import oracle
+    import synth
+    import paper_1309_0215_gb300 as mr
+    torch.cuda.set_device(0)
+    mr.load()
+    n = max(1 << 20, int(HK_KEYS * args.scale))
+    keys = synth.keys_u32(n, 1 << 28, seed=synth.SEED_BASE + 5)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        dk = torch.from_numpy(keys.view(np.int32)).cuda()
+        dm = torch.empty_like(dk)
+    stream.synchronize()
+    ctx = mr.Context(0, stream=stream, timing=True)
+    smem_max = None
+    rows = []
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    for lb in (10, 12, 14, 15, 16, 18, 20, 22, 24, 25, 26, 28):
+        bins = 1 << lb
+        with torch.cuda.stream(stream):
+            torch.bitwise_and(dk, bins - 1, out=dm)
+        stream.synchronize()
+        for cont, cname in ((mr.C_SMEM_ARRAY, "local arrays (shared memory)"),
+                            (mr.C_CLUSTER_ARRAY, "cluster local arrays (distributed shared memory)"),
+                            (mr.C_GLOBAL_ARRAY, "global array")):
+            try:
+                js = []
+                for i in range(args.warmup + args.steps):
+                    js.append(ctx.add_job(mr.HIST_U32, dm, container=cont, hist_bins=bins))
+                    ctx.run()
+            except mr.MRError as e:
+                if e.status == mr.MR_EINVAL and cont == mr.C_SMEM_ARRAY:
+                    smem_max = smem_max or lb
+                    continue
+                if e.status == mr.MR_EINVAL and cont == mr.C_CLUSTER_ARRAY:
+                    continue
+                raise
+            res = np.frombuffer(ctx.fetch(js[-1]), dtype=np.uint64)
+            assert int(res.sum()) == n and int(res[-1]) == 0, "count invariant"
+            if lb <= 12:
+                assert np.array_equal(res, oracle.hist_u32(keys & (bins - 1), bins)), "oracle"
+            t, c = 0.0, 0
+            for j in js[args.warmup:]:
+                tt, cc = ctx.kernel_ms(j)
+                t += tt
+                c += cc
+            for j in js:
+                ctx.release(j)
+            ms = t / c
+            rows.append({"bins": bins, "counter_bytes": (bins + 1) * 4, "counters_fit_l2": (bins + 1) * 4 <= l2,
+                         "container": cname, "launch_ms": round(ms, 4),
+                         "keys_per_s": round(n / (ms / 1e3), 1), "key_gbs": round(4 * n / (ms / 1e3) / 1e9, 1)})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    ctx.close()
+    # where the global array overtakes the local arrays (the largest bin count
+    # at which local arrays are still at least as fast), from the rows above
+    both = {}
+    for r in rows:
+        both.setdefault(r["bins"], {})[r["container"].split(" ")[0]] = r["launch_ms"]
+    last_local_win = max([b for b, v in both.items() if "local" in v and v["local"] <= v["global"]] or [0])
+    last_cluster_win = max([b for b, v in both.items() if "cluster" in v and v["cluster"] <= v["global"]] or [0])
+    best = max(rows, key=lambda r: r["keys_per_s"])
+    print(json.dumps({
+        "metric": METRIC, "value": best["keys_per_s"], "unit": "keys/s (best configuration)", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["launch_ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32 keys in, u32 counters, u64 out",
+        "data": "synthetic: %d u32 keys uniform on [0, bins)" % n,
+        "config": {"workload": "large-key histogram container sweep, %d keys, bins 2^10..2^28" % n},
+        "l2_bytes": l2, "rows": rows, "local_arrays_fastest_up_to_bins": last_local_win,
+        "cluster_arrays_beat_global_up_to_bins": last_cluster_win,
+        "local_arrays_rejected_from_bins": 1 << smem_max if smem_max else None}), flush=True)
+
+
 def cpu_baseline(workload, inp, max_seconds=30.0):
     """The serial oracle timed on this host's cores (1 thread) on the whole
     step's input, or a leading sample of it if that would exceed max_seconds."""
@@ -1182,7 +1266,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["arrays", "wordcount", "kmeans", "histkeys", "bloom", "batched", "serving",
-                                           "simdh"], default="arrays")
+                                           "simdh", "histkeys-sweep"], default="arrays")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean requests per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     ap.add_argument("--plain-duration", type=float, default=20.0,
@@ -1206,6 +1290,8 @@ def main():
         run_simdh(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "histkeys-sweep":
+        run_histkeys_sweep(args)
     else:
         run_ours(args)
 

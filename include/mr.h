@@ -68,8 +68,10 @@ typedef enum {
    * rounded to FP32; points must be finite (other values give unspecified
    * results).  Output layout (packed): float centroids[K][D], int32
    * assign[n], zero padding to an 8-byte boundary, uint64 stats[4] =
-   * {points re-checked in FP32, points re-checked in FP64, iterations,
-   * device waits that timed out (0 unless mr_fetch returned MR_ETIMEOUT)}. */
+   * {points whose fast-pass result was re-checked (FP32 direct differences),
+   * points of those that needed the FP64 definition, iterations, device
+   * waits that timed out (0 unless mr_fetch returned MR_ETIMEOUT)}, summed
+   * over the iterations. */
   MR_KMEANS_F32 = 3,
   /* Large-key histogram (the paper's Histogram application with 16M unique
    * keys, Sec. IV data sets; array container without local arrays,
@@ -93,7 +95,13 @@ typedef enum {
   MR_C_AUTO = 0,          /* let the library choose (paper Sec. III-E rule) */
   MR_C_SMEM_ARRAY = 1,    /* local arrays in shared memory, flushed to the global array */
   MR_C_GLOBAL_ARRAY = 2,  /* no local arrays: atomics straight on the global array */
-  MR_C_HASH = 3           /* global open-addressing hash table */
+  MR_C_HASH = 3,          /* global open-addressing hash table */
+  MR_C_CLUSTER_ARRAY = 4  /* large-key histogram only, never chosen by
+                             MR_C_AUTO: local arrays spread over the shared
+                             memory of a thread-block cluster of 8 CTAs
+                             (distributed shared memory), one slice of the
+                             bins per CTA; up to 8 x (opt-in shared memory /
+                             4) - 1 bins */
 } mr_container;
 
 typedef enum {

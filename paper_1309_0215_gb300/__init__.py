@@ -21,7 +21,7 @@ from ._build import LIB as _LIB_PATH, build as _build_lib, up_to_date as _up_to_
 # ---------------------------------------------------------------- constants
 MR_OK, MR_EINVAL, MR_ENOMEM, MR_ECUDA, MR_EOVERFLOW, MR_ETIMEOUT, MR_EBUDGET, MR_ENOTREADY, MR_ENOJOB = range(9)
 WORDCOUNT, HIST_RGB8, LINREG_I8, KMEANS_F32, HIST_U32, BLOOM_DNA = range(6)
-C_AUTO, C_SMEM_ARRAY, C_GLOBAL_ARRAY, C_HASH = range(4)
+C_AUTO, C_SMEM_ARRAY, C_GLOBAL_ARRAY, C_HASH, C_CLUSTER_ARRAY = range(5)
 RUN_PLAIN, RUN_BATCHED, RUN_CONCURRENT = range(3)
 KM_FP32, KM_BF16_TC, KM_BF16X1_TC = range(3)
 

@@ -122,8 +122,9 @@ __device__ inline bool long_equal(const uint8_t* __restrict__ in, uint64_t a, ui
 // The token starting at segment-relative byte r (its first 16 bytes are
 // always inside the staged buffer; bytes past the input end were staged as
 // spaces).  Its length comes from the segment's whitespace bitmap.
-__device__ __forceinline__ Tok read_token(const uint8_t* __restrict__ in, uint64_t n, uint64_t base,
-                                          const WarpLocal& W, uint32_t r) {
+template <class B>
+__device__ __forceinline__ Tok read_token(const uint8_t* __restrict__ in, uint64_t n, uint64_t base, const B& W,
+                                          uint32_t r) {
   const uint32_t* wb = reinterpret_cast<const uint32_t*>(W.buf);
   // m bit i: byte r + 1 + i is whitespace
   const uint32_t p = r + 1, wi = p >> 5, bs = p & 31;
@@ -184,26 +185,50 @@ __device__ __forceinline__ uint64_t global_slot(uint32_t h, uint32_t log2cap) {
   return log2cap ? (uint64_t)((h * 0x9E3779B1u) >> (32 - log2cap)) : 0;
 }
 
-// Combine (key, c) into the job's global container.
+// Combine (key, c) into the job's global container.  Linear probing, two
+// slots per step: both slots are loaded before either is examined, so a
+// key that is not in its first slot costs no second round trip to L2, and
+// the lanes of a warp, which probe different keys, finish in fewer steps.
+// A slot loaded before a CAS on the slot before it may be stale, which is
+// harmless: a slot only ever changes from empty to a key.
+__device__ __forceinline__ bool slot_take(const JobDev& J, uint64_t s, uint64_t r0, uint64_t r1, uint64_t w0,
+                                          uint64_t w1, bool is_long, uint64_t c) {
+  unsigned long long* sp = J.key + 2 * s;
+  if (r0 == 0 || r1 == 0) {  // empty, or a read that raced the CAS: ask the CAS
+    cas_slot(sp, w0, w1, r0, r1);
+    if (r0 == 0 && r1 == 0) {
+      atomicAdd(J.cnt + s, (unsigned long long)c);
+      return true;
+    }
+  }
+  if (r1 == w1 && (r0 == w0 || (is_long && long_equal(J.in, r0 - 1, w0 - 1, w1 & LEN_MASK)))) {
+    atomicAdd(J.cnt + s, (unsigned long long)c);
+    return true;
+  }
+  return false;
+}
+
+// WIDTH = 2 loads two slots per step; WIDTH = 1 is plain linear probing,
+// kept for the persistent batch kernel, whose registers are tight.
+template <int WIDTH = 2>
 __device__ inline void global_insert(const JobDev& J, uint64_t w0, uint64_t w1, uint32_t h, uint64_t c) {
   uint64_t slot = global_slot(h, J.log2cap);
   const bool is_long = (w1 >> 56) == 0xFF;
-  for (int p = 0; p < MAX_PROBES; ++p) {
-    unsigned long long* sp = J.key + 2 * slot;
-    uint64_t r0, r1;
-    ld_slot(sp, r0, r1);
-    if (r0 == 0 || r1 == 0) {  // empty, or a read that raced the CAS: ask the CAS
-      cas_slot(sp, w0, w1, r0, r1);
-      if (r0 == 0 && r1 == 0) {
-        atomicAdd(J.cnt + slot, (unsigned long long)c);
-        return;
-      }
+  const uint64_t mask = J.cap - 1;
+  for (int p = 0; p < MAX_PROBES; p += WIDTH) {
+    if (WIDTH == 2) {
+      const uint64_t sb = (slot + 1) & mask;
+      uint64_t a0, a1, b0, b1;
+      ld_slot(J.key + 2 * slot, a0, a1);
+      ld_slot(J.key + 2 * sb, b0, b1);
+      if (slot_take(J, slot, a0, a1, w0, w1, is_long, c)) return;
+      if (slot_take(J, sb, b0, b1, w0, w1, is_long, c)) return;
+    } else {
+      uint64_t a0, a1;
+      ld_slot(J.key + 2 * slot, a0, a1);
+      if (slot_take(J, slot, a0, a1, w0, w1, is_long, c)) return;
     }
-    if (r1 == w1 && (r0 == w0 || (is_long && long_equal(J.in, r0 - 1, w0 - 1, w1 & LEN_MASK)))) {
-      atomicAdd(J.cnt + slot, (unsigned long long)c);
-      return;
-    }
-    slot = (slot + 1) & (J.cap - 1);
+    slot = (slot + WIDTH) & mask;
   }
   atomicOr(J.state, 1u);
 }
@@ -259,11 +284,12 @@ __device__ inline void local_clear(WarpLocal& L) {
 }
 
 // Merge the warp's cache into the global container and empty it.
+template <int WIDTH = 2>
 __device__ inline void local_flush(WarpLocal& L, int& occ, const JobDev& J) {
   __syncwarp();
   for (int s = threadIdx.x & 31; s < LT; s += 32) {
     if (L.w1[s] != 0) {
-      global_insert(J, L.w0[s], L.w1[s], L.h[s], L.cnt[s]);
+      global_insert<WIDTH>(J, L.w0[s], L.w1[s], L.h[s], L.cnt[s]);
       L.w1[s] = 0;
     }
   }
@@ -292,11 +318,12 @@ __device__ __forceinline__ uint4 shift_window(const uint4& a, const uint4& b, ui
                     __funnelshift_r(t3, t4, r));
 }
 
-// One warp maps and combines the tokens whose first byte lies in segment seg.
-// miss(lane_has_miss, token) is called by all 32 lanes after each round of
-// up to 32 tokens and disposes of the tokens the cache did not take.
-template <class Miss>
-__device__ inline void warp_segment_t(const JobDev& J, uint64_t seg, WarpLocal& L, int& occ, Miss&& miss) {
+// Stage segment seg of the job (and its 64-byte halo) in the warp's buffer
+// W (members buf, wsb, starts), build the whitespace bitmap and the list of
+// token starts (segment-relative offsets of the tokens whose first byte lies
+// in the segment) and return how many there are.  All 32 lanes call this.
+template <class B>
+__device__ inline int stage_tokens(const JobDev& J, uint64_t seg, B& L) {
   const int lane = threadIdx.x & 31;
   const uint64_t base = seg * SEG;
   const uint8_t* __restrict__ in = J.in;
@@ -371,25 +398,127 @@ __device__ inline void warp_segment_t(const JobDev& J, uint64_t seg, WarpLocal& 
     }
   }
   __syncwarp();
+  return total;
+}
+
+// One warp maps and combines the tokens whose first byte lies in segment seg.
+// miss(lane_has_miss, token) is called by all 32 lanes after each round of
+// up to 32 tokens and disposes of the tokens the cache did not take.
+template <int WIDTH = 2, class Miss>
+__device__ inline void warp_segment_t(const JobDev& J, uint64_t seg, WarpLocal& L, int& occ, Miss&& miss) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t base = seg * SEG;
+  const int total = stage_tokens(J, seg, L);
   for (int r0 = 0; r0 < total; r0 += 32) {
     const int i = r0 + lane;
     const bool active = i < total;
     Tok t;
-    if (active) t = read_token(in, n, base, L, L.starts[i]);
+    if (active) t = read_token(J.in, J.n, base, L, L.starts[i]);
     else t.w0 = 0, t.w1 = 0, t.h = 0;
     const bool m = combine_local(L, active, t);
     miss(m, t);
     __syncwarp();
   }
   // occ counts segments since the last cache merge
-  if (++occ >= CACHE_EPOCH) local_flush(L, occ, J);
+  if (++occ >= CACHE_EPOCH) local_flush<WIDTH>(L, occ, J);
+}
+
+// ---------------------------------------------------------------------------
+// Local container of the plain map kernel for large inputs: one table per CTA
+// in shared memory, shared by its warps (the paper's bounded local table,
+// Sec. III-D, here per thread block).  Open addressing with two candidate
+// slots per key; a slot is claimed once and never changes key, so once a
+// CTA has seen a couple of thousand distinct keys the table is read-only
+// apart from its counts, and it holds the keys that were frequent early on
+// (for a Zipf-like stream, the hot ones).  A slot is {w0, w1} read with one
+// 128-bit load.  A claim CASes w1 from 0 to CT_BUSY, writes w0, hash and
+// count, fences and then stores w1.  Both words start at zero and keys whose
+// w0 is 0 (tokens of NUL bytes) never enter the table, so a read that meets
+// a claim half done (w1 already stored, w0 not yet seen) does not match and
+// the token goes on as a miss.  A key may end up in two slots (two lanes
+// claiming it at once); both counts reach the global container, which
+// merges them.
+constexpr int CT_SLOTS = 2048;
+constexpr unsigned long long CT_BUSY = 1ull;  // no key has w1 == 1 (its length byte is >= 1)
+struct CtaTable {
+  ulonglong2 key[CT_SLOTS];  // {w0, w1}
+  uint32_t h[CT_SLOTS];
+  uint32_t cnt[CT_SLOTS];
+};
+
+// Per-warp state of the plain map kernel: the staged segment, its
+// whitespace bitmap and token list, and a queue of the tokens the table did
+// not take, which go to the global container 32 at a time (full warps, so
+// the global probing runs once per 32 misses instead of once per round).
+constexpr int MQ = 64;
+struct MapWarp {
+  uint8_t buf[BUF];
+  uint32_t wsb[BUF / 32 + 2];
+  uint16_t starts[SEG / 2];
+  unsigned long long qw0[MQ], qw1[MQ];
+  uint32_t qh[MQ];
+};
+static_assert(sizeof(CtaTable) % 16 == 0 && sizeof(MapWarp) % 16 == 0, "staging buffers must stay 16-byte aligned");
+
+// Count one short token in the CTA table; false if neither of its two
+// slots holds it or could be claimed for it (and for every long token).
+__device__ __forceinline__ bool cta_add(CtaTable& T, const Tok& t) {
+  if ((t.w1 >> 56) == 0xFF || t.w0 == 0) return false;
+  const uint32_t s0 = t.h & (CT_SLOTS - 1);
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const uint32_t s = (s0 + p) & (CT_SLOTS - 1);
+    unsigned long long k0, k1;
+    asm volatile("ld.volatile.shared::cta.v2.u64 {%0, %1}, [%2];"
+                 : "=l"(k0), "=l"(k1)
+                 : "r"((uint32_t)__cvta_generic_to_shared(&T.key[s]))
+                 : "memory");
+    if (k1 == t.w1 && k0 == t.w0) {
+      atomicAdd(&T.cnt[s], 1u);
+      return true;
+    }
+    if (k1 == 0 && atomicCAS(&T.key[s].y, 0ull, CT_BUSY) == 0ull) {
+      T.key[s].x = t.w0;
+      T.h[s] = t.h;
+      T.cnt[s] = 1u;
+      __threadfence_block();
+      *reinterpret_cast<volatile unsigned long long*>(&T.key[s].y) = t.w1;
+      return true;
+    }
+  }
+  return false;
+}
+
+// Queue the round's misses (m: this lane has one); once 32 are queued, the
+// warp inserts the oldest 32 into the global container.  qn / qhd: queued
+// entries and queue head, warp-uniform.
+__device__ __forceinline__ void mq_push(const JobDev& J, MapWarp& W, bool m, const Tok& t, uint32_t& qn,
+                                        uint32_t& qhd) {
+  const int lane = threadIdx.x & 31;
+  const unsigned mm = __ballot_sync(0xffffffffu, m);
+  if (!mm) return;
+  if (m) {
+    const uint32_t pos = (qhd + qn + (uint32_t)__popc(mm & ((1u << lane) - 1u))) & (MQ - 1);
+    W.qw0[pos] = t.w0;
+    W.qw1[pos] = t.w1;
+    W.qh[pos] = t.h;
+  }
+  qn += (uint32_t)__popc(mm);
+  if (qn >= 32) {
+    __syncwarp();
+    const uint32_t q = (qhd + (uint32_t)lane) & (MQ - 1);
+    global_insert(J, W.qw0[q], W.qw1[q], W.qh[q], 1);
+    qhd = (qhd + 32) & (MQ - 1);
+    qn -= 32;
+  }
 }
 
 // The direct form: a token the cache did not take goes straight to the
 // global container.
+template <int WIDTH = 2>
 __device__ inline void warp_segment(const JobDev& J, uint64_t seg, WarpLocal& L, int& occ) {
-  warp_segment_t(J, seg, L, occ, [&](bool m, const Tok& t) {
-    if (m) global_insert(J, t.w0, t.w1, t.h, 1);
+  warp_segment_t<WIDTH>(J, seg, L, occ, [&](bool m, const Tok& t) {
+    if (m) global_insert<WIDTH>(J, t.w0, t.w1, t.h, 1);
   });
 }
 

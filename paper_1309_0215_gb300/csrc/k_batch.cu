@@ -186,7 +186,7 @@ batch_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs, uint64_t total_t
       }
       __syncthreads();
     } else if (kind == MR_WORDCOUNT) {
-      wc::local_flush(L, occ, J.wc);
+      wc::local_flush<1>(L, occ, J.wc);
       __syncthreads();
     }
   };
@@ -230,7 +230,7 @@ batch_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs, uint64_t total_t
       // the job's descriptor from shared memory (copied at the job switch):
       // through a reference to global memory every use in the hot loop would
       // be a global reload, and a register copy would not fit
-      for (uint64_t sg = s0 + (threadIdx.x >> 5); sg < s1; sg += BWARPS) wc::warp_segment(s_jd, sg, L, occ);
+      for (uint64_t sg = s0 + (threadIdx.x >> 5); sg < s1; sg += BWARPS) wc::warp_segment<1>(s_jd, sg, L, occ);
     } else {
       const uint64_t t0 = local * arr_tile;
       if (J.kind == MR_HIST_RGB8 && cont == MR_C_GLOBAL_ARRAY) {

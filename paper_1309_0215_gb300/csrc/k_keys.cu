@@ -157,6 +157,66 @@ hk_smem_kernel(const uint4* __restrict__ base, uint32_t off, uint64_t n, uint32_
   }
 }
 
+// Local arrays spread over a thread-block cluster: the bins are cut into
+// HKC slices of `slice` counters, CTA r of a cluster holding slice r in its
+// shared memory, so a cluster holds HKC times as many bins as one CTA (the
+// paper's local arrays, Sec. III-E, with a cluster of CTAs as the worker).
+// Every CTA streams its share of the keys and adds each one to its slice's
+// owner through distributed shared memory (red.shared::cluster); a cluster
+// barrier before the first add (every slice zeroed) and after the last (every
+// add landed), then each CTA adds its slice's non-zero counters to the global
+// array.  No CTA touches another's shared memory after the second barrier,
+// so CTAs may then exit in any order.
+constexpr int HKC = 8;  // CTAs per cluster (the portable maximum)
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+template <typename C>
+__global__ void __launch_bounds__(HK_SMEM_THREADS)
+hk_cluster_kernel(const uint4* __restrict__ base, uint32_t off, uint64_t n, uint32_t nbins, uint32_t slice,
+                  uint32_t slice_mul, C* __restrict__ cnt) {
+  extern __shared__ uint32_t sh_bins[];
+  const uint32_t rank = cluster_rank();
+  for (uint32_t i = threadIdx.x; i < slice; i += blockDim.x) sh_bins[i] = 0;
+  cluster_sync_all();
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sh_bins);
+  const uint64_t groups = (n + off + 3) / 4;
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += (uint64_t)gridDim.x * blockDim.x) {
+    const uint4 w = ldg_nc(base + g);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int64_t idx = (int64_t)(4 * g + e) - (int64_t)off;
+      if (idx >= 0 && (uint64_t)idx < n) {
+        const uint32_t key = key_at(w, e);
+        const uint32_t k = key < nbins ? key : nbins;
+        // owner = k / slice: the multiply-high estimate is at most one low
+        uint32_t r = __umulhi(k, slice_mul);
+        uint32_t loc = k - r * slice;
+        if (loc >= slice) {
+          ++r;
+          loc -= slice;
+        }
+        uint32_t ra;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(sbase + 4 * loc), "r"(r));
+        asm volatile("red.relaxed.cluster.shared::cluster.add.u32 [%0], 1;" ::"r"(ra) : "memory");
+      }
+    }
+  }
+  cluster_sync_all();
+  const uint64_t b0 = (uint64_t)rank * slice;
+  for (uint32_t i = threadIdx.x; i < slice && b0 + i <= nbins; i += blockDim.x) {
+    const uint32_t v = sh_bins[i];
+    if (v) red_add(cnt + b0 + i, v);
+  }
+}
+
 __global__ void hk_widen_kernel(const uint32_t* __restrict__ c32, uint64_t nb, unsigned long long* __restrict__ out) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += (uint64_t)gridDim.x * blockDim.x)
     out[i] = c32[i];
@@ -253,10 +313,47 @@ bloom_kernel(const uint8_t* __restrict__ seq, uint64_t n, uint32_t L, uint64_t m
 }  // namespace
 
 int hk_smem_max_bins(const DevInfo& di) { return di.smem_optin / 4 - 1; }
+int hk_cluster_max_bins(const DevInfo& di) { return HKC * (di.smem_optin / 4) - 1; }
 
-cudaError_t launch_hist_keys(const uint32_t* keys, uint64_t n, uint32_t nbins, bool smem, void* counters,
+template <typename C>
+static cudaError_t launch_hk_cluster(const uint4* base, uint32_t off, uint64_t n, uint32_t nbins, C* cnt,
+                                     const DevInfo& di, cudaStream_t s) {
+  const uint32_t slice = (uint32_t)(((uint64_t)nbins + 1 + HKC - 1) / HKC);
+  // multiply-high by floor(2^32 / slice) (at most 2^32 - 1) gives
+  // floor(k / slice) or one less, for every k < 2^32
+  const uint64_t sm64 = (1ull << 32) / slice;
+  const uint32_t slice_mul = sm64 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)sm64;
+  const int bytes = (int)(slice * 4);
+  cudaError_t e = cudaFuncSetAttribute(hk_cluster_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  const uint64_t groups = (n + off + 3) / 4;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = HKC;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(HK_SMEM_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = (size_t)bytes;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  // as many clusters as fit the GPU at once (each CTA holds one slice)
+  int clusters = 0;
+  cfg.gridDim = dim3(HKC, 1, 1);
+  if ((e = cudaOccupancyMaxActiveClusters(&clusters, hk_cluster_kernel<C>, &cfg)) != cudaSuccess) return e;
+  if (clusters < 1) return cudaErrorInvalidConfiguration;
+  uint64_t want = (groups + (uint64_t)HK_SMEM_THREADS * 16 * HKC - 1) / ((uint64_t)HK_SMEM_THREADS * 16 * HKC);
+  if (want < 1) want = 1;
+  if (want > (uint64_t)clusters) want = (uint64_t)clusters;
+  cfg.gridDim = dim3((unsigned)(want * HKC), 1, 1);
+  return cudaLaunchKernelEx(&cfg, hk_cluster_kernel<C>, base, off, n, nbins, slice, slice_mul, cnt);
+}
+
+cudaError_t launch_hist_keys(const uint32_t* keys, uint64_t n, uint32_t nbins, int container, void* counters,
                              bool wide, unsigned long long* out, const DevInfo& di, cudaStream_t s, uint64_t* nk,
                              KTimer* kt) {
+  const bool smem = container == MR_C_SMEM_ARRAY;
   const uint64_t nb = (uint64_t)nbins + 1;
   cudaError_t e = cudaMemsetAsync(wide ? (void*)out : counters, 0, nb * (wide ? 8 : 4), s);
   if (e != cudaSuccess) return e;
@@ -284,6 +381,10 @@ cudaError_t launch_hist_keys(const uint32_t* keys, uint64_t n, uint32_t nbins, b
         hk_smem_kernel<uint32_t><<<(int)g, HK_SMEM_THREADS, bytes, s>>>(base, off, n, nbins,
                                                                         static_cast<uint32_t*>(counters));
       }
+    } else if (container == MR_C_CLUSTER_ARRAY) {
+      e = wide ? launch_hk_cluster(base, off, n, nbins, out, di, s)
+               : launch_hk_cluster(base, off, n, nbins, static_cast<uint32_t*>(counters), di, s);
+      if (e != cudaSuccess) return e;
     } else {
       uint64_t g = (groups + HK_THREADS * 8 - 1) / (HK_THREADS * 8);
       g = g < 1 ? 1 : g;

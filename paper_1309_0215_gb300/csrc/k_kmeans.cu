@@ -336,30 +336,48 @@ __device__ __forceinline__ float warp_dist32(const float* __restrict__ xp, const
   return s;
 }
 
+// Exact choice between two centroids for the listed points (pairs whose
+// other centroids are already ruled out), four pairs per warp: lanes 8g ..
+// 8g + 7 take pair g, each lane dimensions s, s + 8, ... of the point and of
+// both centroid rows, so a warp has four points' rows in flight at once.
+// FP32 direct differences first: their relative error is at most g for any
+// summation order (as in the re-check below), so a ratio beyond widen
+// decides the exact order; only closer pairs (and NaNs) take the FP64
+// definition, evaluated by the group's first lane.  stat[0] counts the
+// pairs, stat[1] those that needed FP64.
 __global__ void km_pair_kernel(const float* __restrict__ x, uint32_t d, const float* __restrict__ c,
                                const uint2* __restrict__ pairs, const uint32_t* npairs, int32_t* assign,
                                unsigned long long* stat) {
   const uint32_t np = *npairs;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, grp = lane >> 3, sl = lane & 7;
   const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   if (w0 == 0 && lane == 0 && stat) atomicAdd(stat, (unsigned long long)np);
-  // One warp per pair.  FP32 direct differences first (lanes over the
-  // dimensions, coalesced rows): their relative error is at most g for any
-  // summation order (as in the re-check below), so a ratio beyond widen
-  // decides the exact order; only closer pairs (and NaNs) take the FP64
-  // definition, evaluated by one lane.
   const float g = 1.01f * (float)(d + 8) * 5.9604644775390625e-08f;
   const float widen = (1.f + g) / (1.f - g) * (1.f + 4.f * 5.9604644775390625e-08f);
-  for (uint64_t f = w0; f < np; f += nw) {
-    const uint2 e = pairs[f];
+  uint32_t n64 = 0;
+  for (uint64_t f0 = 4 * w0; f0 < np; f0 += 4 * nw) {
+    const uint64_t f = f0 + (uint64_t)grp;
+    const bool live = f < np;
+    const uint2 e = live ? pairs[f] : make_uint2(0u, 0u);
     const uint32_t k1 = e.y & 0xffffu, k2 = e.y >> 16;
     const float* xp = x + (uint64_t)e.x * d;
     const float* c1 = c + (uint64_t)k1 * d;
     const float* c2 = c + (uint64_t)k2 * d;
-    const float f1 = warp_dist32(xp, c1, d, lane);
-    const float f2 = warp_dist32(xp, c2, d, lane);
-    if (lane == 0) {
+    float f1 = 0.f, f2 = 0.f;
+    if (live)
+      for (uint32_t j = (uint32_t)sl; j < d; j += 8) {
+        const float xv = xp[j];
+        const float t1 = xv - c1[j], t2 = xv - c2[j];
+        f1 = fmaf(t1, t1, f1);
+        f2 = fmaf(t2, t2, f2);
+      }
+#pragma unroll
+    for (int o = 4; o; o >>= 1) {
+      f1 += __shfl_xor_sync(0xffffffffu, f1, o);
+      f2 += __shfl_xor_sync(0xffffffffu, f2, o);
+    }
+    if (live && sl == 0) {
       int32_t w;
       if (f2 > f1 * widen) {
         w = (int32_t)k1;
@@ -369,9 +387,14 @@ __global__ void km_pair_kernel(const float* __restrict__ x, uint32_t d, const fl
         const double s1 = dist64(xp, c1, d);
         const double s2 = dist64(xp, c2, d);
         w = (s2 < s1 || (s2 == s1 && k2 < k1)) ? (int32_t)k2 : (int32_t)k1;
+        ++n64;
       }
       assign[e.x] = w;
     }
+  }
+  if (stat) {
+    n64 = __reduce_add_sync(0xffffffffu, n64);
+    if (lane == 0 && n64) atomicAdd(stat + 1, (unsigned long long)n64);
   }
 }
 
@@ -389,7 +412,11 @@ __global__ void km_recheck_fp64_kernel(const float* __restrict__ x, uint32_t d, 
   const int lane = threadIdx.x & 31;
   const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  if (w0 == 0 && lane == 0 && stat) atomicAdd(stat, (unsigned long long)nf);
+  // every listed point is checked in FP32 and then in FP64 (stat[0], stat[1])
+  if (w0 == 0 && lane == 0 && stat) {
+    atomicAdd(stat, (unsigned long long)nf);
+    atomicAdd(stat + 1, (unsigned long long)nf);
+  }
   const float g = 1.01f * (float)(d + 8) * 5.9604644775390625e-08f;
   const float widen = (1.f + g) / (1.f - g) * (1.f + 4.f * 5.9604644775390625e-08f);
   for (uint64_t f = w0; f < nf; f += nw) {
@@ -433,21 +460,30 @@ __global__ void km_recheck_fp64_kernel(const float* __restrict__ x, uint32_t d, 
 // pass computes their FP32 distances into registers, the warp takes the
 // minimum, and each lane evaluates in FP64 only its own candidates.
 constexpr int KLANE = 8;  // K <= 256
+// Points are handed out in contiguous ranges of at least RC_MIN per CTA, so
+// only as many CTAs stage the centroids as there is work for (the lists are
+// a few thousand points).  stat[0] counts the listed points (all checked in
+// FP32), stat[1] those that needed FP64.
+constexpr uint32_t RC_MIN = 64;
 __global__ void km_recheck_fp64_smem_kernel(const float* __restrict__ x, uint32_t d, const float* __restrict__ c,
                                             uint32_t k, const uint32_t* flagged, const uint32_t* nflag,
                                             int32_t* assign, unsigned long long* stat) {
   extern __shared__ float cs[];  // [k][d + 1]
+  const uint32_t nf = *nflag;
+  const uint32_t per = max(RC_MIN, (nf + gridDim.x - 1) / gridDim.x);
+  const uint64_t f_lo = (uint64_t)blockIdx.x * per;
+  const uint64_t f_hi = f_lo + per < nf ? f_lo + per : nf;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && stat) atomicAdd(stat, (unsigned long long)nf);
+  if (f_lo >= nf) return;  // no work for this CTA: no staging either
   const uint32_t ld = d + 1;
   for (uint32_t t = threadIdx.x; t < k * d; t += blockDim.x) cs[(t / d) * ld + (t % d)] = c[t];
   __syncthreads();
-  const uint32_t nf = *nflag;
   const int lane = threadIdx.x & 31;
-  const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  if (w0 == 0 && lane == 0 && stat) atomicAdd(stat, (unsigned long long)nf);
+  const uint32_t wpb = blockDim.x >> 5;
   const float g = 1.01f * (float)(d + 8) * 5.9604644775390625e-08f;
   const float widen = (1.f + g) / (1.f - g) * (1.f + 4.f * 5.9604644775390625e-08f);
-  for (uint64_t f = w0; f < nf; f += nw) {
+  uint32_t n64 = 0;
+  for (uint64_t f = f_lo + (threadIdx.x >> 5); f < f_hi; f += wpb) {
     const uint32_t p = flagged[f];
     const float* xp = x + (uint64_t)p * d;
     float dist[KLANE];
@@ -484,6 +520,7 @@ __global__ void km_recheck_fp64_smem_kernel(const float* __restrict__ x, uint32_
       if (first >= 0) assign[p] = first;
       continue;
     }
+    ++n64;
     double best = INFINITY;
     int bk = 0x7fffffff;
 #pragma unroll
@@ -505,6 +542,7 @@ __global__ void km_recheck_fp64_smem_kernel(const float* __restrict__ x, uint32_
     }
     if (lane == 0) assign[p] = bk == 0x7fffffff ? 0 : bk;
   }
+  if (stat && lane == 0 && n64) atomicAdd(stat + 1, (unsigned long long)n64);
 }
 
 // max |x| over all coordinates (as float bits; non-negative floats order like ints)
@@ -790,31 +828,35 @@ __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_kernel(const float
 }
 
 // Pipelined form of the local-array update, for rows of a multiple of 4
-// floats starting 16-byte aligned: thread 0 streams chunks of `rows`
-// consecutive points and their cluster ids into an LP_ST-deep shared-memory
-// ring with bulk copies (completion counted on one mbarrier per stage), so
-// loads stay in flight while the warps add earlier chunks; warp w takes rows
-// w, w + 32, ... of a chunk and then releases the stage on a second mbarrier,
-// which thread 0 waits on before refilling the stage.
+// floats starting 16-byte aligned.  Warp 0 is the producer: its lane 0
+// streams chunks of `rows` consecutive points and their cluster ids into an
+// LP_ST-deep shared-memory ring with bulk copies (completion counted on one
+// mbarrier per stage) and refills a stage as soon as every worker warp has
+// released it; warps 1..31 are workers, warp w taking rows w - 1, w - 1 +
+// 31, ... of each chunk.  (With a worker refilling the ring only after its
+// own rows, the ring ran dry and the kernel waited on DRAM latency.)
 //
 // Exact sums without 64-bit shared atomics.  The scale keeps |x 2^s| < 2^39
 // (km_scale_kernel), so q = rint(x 2^s) = hi 2^20 + lo with hi, lo integers
 // of magnitude <= 2^19, both formed by FP32 adds that are exact (lq_split);
 // each goes into a 32-bit shared-memory array with a non-returning add.
 // Within a window of at most LP_FLUSH_ROWS points no 32-bit sum can overflow,
-// so after each window the CTA adds hi 2^20 + lo of every (cluster, dim) into
-// its own int64 partial in global memory (plain read-modify-write: no other
-// CTA touches it) and clears the arrays.  Integer sums stay exact and
-// order-independent, equal to the sum of rint(x 2^s) formed any other way.
+// so after each window the workers add hi 2^20 + lo of every (cluster, dim)
+// into the CTA's own int64 partial in global memory (plain read-modify-
+// write: no other CTA touches it) and clear the arrays.  Integer sums stay
+// exact and order-independent, equal to the sum of rint(x 2^s) formed any
+// other way.
 //
-// Every wait is bounded.  The loop runs the same chunks and barriers in every
-// thread whatever happens; after a wait gives up, chunks are skipped, thread
-// 0 issues no more copies (it issues chunk c + LP_ST only after it has seen
-// chunk c land), lets the copies it issued land, and the CTA counts itself
-// in *timeouts.
-constexpr int LP_ST = 3;
-constexpr uint32_t LP_CHUNK_MAX = 24 * 1024;  // bytes of points per stage, at most
-constexpr uint32_t LP_FLUSH_ROWS = 4095;     // 4095 * 2^19 < 2^31
+// Every wait is bounded.  Workers run the same chunks and barriers whatever
+// happens; after a wait gives up, chunks are skipped and the producer issues
+// no more copies (it issues into a stage only after every worker released
+// the stage's previous chunk with no error raised, i.e. after that chunk
+// landed), lets the last copies it issued land, and the CTA counts itself in
+// *timeouts.
+constexpr int LP_ST = 4;
+constexpr int LP_WORKERS = LS_THREADS / 32 - 1;  // warp 0 produces
+constexpr uint32_t LP_CHUNK_MAX = 24 * 1024;     // bytes of points per stage, at most
+constexpr uint32_t LP_FLUSH_ROWS = 4095;         // 4095 * 2^19 < 2^31
 __host__ __device__ constexpr uint64_t lp_fixed_bytes(uint64_t kd, uint64_t k) {
   return (((2 * kd + k) * 4 + 127) & ~127ull) + 2 * LP_ST * 8 + 16;
 }
@@ -832,6 +874,10 @@ __device__ __forceinline__ void lq_split(float v, int& hi, int& lo) {
   lo = (int)(__float_as_uint(__fadd_rn(lf, 0x1.8p23f)) - 0x4B400000u);
 }
 __device__ __forceinline__ void red_s32(int* p, int v) { atomicAdd(p, v); }
+// barrier 1 among the worker warps only (barrier 0 is __syncthreads)
+__device__ __forceinline__ void workers_sync() {
+  asm volatile("bar.sync 1, %0;" ::"r"(LP_WORKERS * 32) : "memory");
+}
 
 template <bool D64>
 __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_pipe_kernel(
@@ -863,29 +909,15 @@ __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_pipe_kernel(
     *err = 0;
     for (int q = 0; q < LP_ST; ++q) {
       mbar_init(&full[q], 1);
-      mbar_init(&empty[q], LS_THREADS / 32);
+      mbar_init(&empty[q], LP_WORKERS);
     }
     fence_mbar_init();
   }
   __syncthreads();
-  uint32_t issued = 0, seen = 0;  // thread 0: chunks whose copies were started / seen landed
-  auto issue = [&](uint32_t c) {
-    const uint32_t q = c % LP_ST;
-    const uint64_t r0 = p0 + (uint64_t)c * rows;
-    const uint32_t nr = (uint32_t)(p1 - r0 < rows ? p1 - r0 : rows);
-    const uint32_t xb = nr * d * 4, ab = ((nr + 3) & ~3u) * 4;  // ids rounded up to 16 bytes (buffer padding)
-    mbar_expect_tx(&full[q], xb + ab);
-    bulk_g2s(xs + q * xst, x + r0 * d, xb, &full[q]);
-    bulk_g2s(as + q * rows, assign + r0, ab, &full[q]);
-    issued = c + 1;
-  };
-  if (threadIdx.x == 0)
-    for (uint32_t c = 0; c < nchunks && c < (uint32_t)LP_ST; ++c) issue(c);
-  const float scale = ldexpf(1.f, *shift);
   long long* P = part + (uint64_t)blockIdx.x * kd;
-  bool written = false;  // the CTA's partial holds a window already (CTA-uniform)
-  auto flush = [&]() {
-    for (uint64_t i = threadIdx.x; i < kd; i += LS_THREADS) {
+  bool written = false;  // this thread's elements of the CTA's partial hold a window already
+  auto flush = [&](uint32_t t0, uint32_t nt) {
+    for (uint64_t i = t0; i < kd; i += nt) {
       const long long v = (long long)HI[i] * (1ll << 20) + (long long)LO[i];
       P[i] = written ? P[i] + v : v;
       HI[i] = 0;
@@ -893,61 +925,90 @@ __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_pipe_kernel(
     }
     written = true;
   };
-  for (uint32_t c = 0; c < nchunks; ++c) {
-    const uint32_t q = c % LP_ST, par = (c / LP_ST) & 1u;
-    const bool ok = !*err && mbar_wait(&full[q], par, err, polls);
-    if (ok) {
-      if (threadIdx.x == 0) seen = c + 1;
-      const uint64_t r0 = p0 + (uint64_t)c * rows;
-      const uint32_t nr = (uint32_t)(p1 - r0 < rows ? p1 - r0 : rows);
-      const float* X = xs + q * xst;
-      const int32_t* A = as + q * rows;
-      for (uint32_t j = warp; j < nr; j += LS_THREADS / 32) {
-        const int a = A[j];
-        const uint32_t cl = (a < 0 || (uint32_t)a >= k) ? 0u : (uint32_t)a;
-        if (lane == 0) atomicAdd(&C[cl], 1u);
-        int h0, l0;
-        if (D64) {  // lane holds dimensions lane and lane + 32
-          const float* row = X + j * 64u;
-          const uint32_t b = cl * 64u + lane;
-          int h1, l1;
-          lq_split(row[lane] * scale, h0, l0);
-          lq_split(row[lane + 32] * scale, h1, l1);
-          red_s32(HI + b, h0);
-          red_s32(LO + b, l0);
-          red_s32(HI + b + 32, h1);
-          red_s32(LO + b + 32, l1);
+  uint32_t issued = 0;  // thread 0: chunks whose copies were started
+  if (warp == 0) {
+    // ----------------------------------------------------------- producer
+    if (lane == 0) {
+      for (uint32_t c = 0; c < nchunks; ++c) {
+        const uint32_t q = c % LP_ST;
+        // the stage's previous chunk must be released by every worker, with
+        // no error raised (so it landed) before the stage is refilled
+        if (c >= (uint32_t)LP_ST && (!mbar_wait(&empty[q], ((c / LP_ST) + 1) & 1u, err, polls) || *err)) break;
+        const uint64_t r0 = p0 + (uint64_t)c * rows;
+        const uint32_t nr = (uint32_t)(p1 - r0 < rows ? p1 - r0 : rows);
+        const uint32_t xb = nr * d * 4, ab = ((nr + 3) & ~3u) * 4;  // ids rounded up to 16 bytes (buffer padding)
+        mbar_expect_tx(&full[q], xb + ab);
+        bulk_g2s(xs + q * xst, x + r0 * d, xb, &full[q]);
+        bulk_g2s(as + q * rows, assign + r0, ab, &full[q]);
+        issued = c + 1;
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------- workers
+    const float scale = ldexpf(1.f, *shift);
+    const uint32_t wk = (uint32_t)warp - 1;
+    for (uint32_t c = 0; c < nchunks; ++c) {
+      const uint32_t q = c % LP_ST, par = (c / LP_ST) & 1u;
+      const bool ok = !*err && mbar_wait(&full[q], par, err, polls);
+      if (ok) {
+        const uint64_t r0 = p0 + (uint64_t)c * rows;
+        const uint32_t nr = (uint32_t)(p1 - r0 < rows ? p1 - r0 : rows);
+        const float* X = xs + q * xst;
+        const int32_t* A = as + q * rows;
+        if (D64) {
+          // lane holds dimensions lane and lane + 32 of row j
+          for (uint32_t j = wk; j < nr; j += LP_WORKERS) {
+            const int a = A[j];
+            const uint32_t cl = (a < 0 || (uint32_t)a >= k) ? 0u : (uint32_t)a;
+            if (lane == 0) atomicAdd(&C[cl], 1u);
+            const float* row = X + j * 64u;
+            const uint32_t b = cl * 64u + lane;
+            int h0, l0, h1, l1;
+            lq_split(row[lane] * scale, h0, l0);
+            lq_split(row[lane + 32] * scale, h1, l1);
+            red_s32(HI + b, h0);
+            red_s32(LO + b, l0);
+            red_s32(HI + b + 32, h1);
+            red_s32(LO + b + 32, l1);
+          }
         } else {
-          const float* row = X + (uint64_t)j * d;
-          const uint32_t b = cl * d;
-          for (uint32_t dj = lane; dj < d; dj += 32) {
-            lq_split(row[dj] * scale, h0, l0);
-            red_s32(HI + b + dj, h0);
-            red_s32(LO + b + dj, l0);
+          for (uint32_t j = wk; j < nr; j += LP_WORKERS) {
+            const int a = A[j];
+            const uint32_t cl = (a < 0 || (uint32_t)a >= k) ? 0u : (uint32_t)a;
+            if (lane == 0) atomicAdd(&C[cl], 1u);
+            const float* row = X + (uint64_t)j * d;
+            const uint32_t b = cl * d;
+            for (uint32_t dj = lane; dj < d; dj += 32) {
+              int h0, l0;
+              lq_split(row[dj] * scale, h0, l0);
+              red_s32(HI + b + dj, h0);
+              red_s32(LO + b + dj, l0);
+            }
           }
         }
       }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[q]);
+      if ((c + 1) % fc == 0 && c + 1 < nchunks) {
+        workers_sync();
+        flush(threadIdx.x - 32, LP_WORKERS * 32);
+        workers_sync();
+      }
     }
-    fence_proxy_async();
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[q]);
-    // refill the stage only once this thread has seen chunk c land and every
-    // warp is done with it
-    if (threadIdx.x == 0 && ok && c + LP_ST < nchunks && mbar_wait(&empty[q], par, err, polls)) issue(c + LP_ST);
-    if ((c + 1) % fc == 0 && c + 1 < nchunks) {
-      __syncthreads();
-      flush();
-      __syncthreads();
-    }
-  }
-  if (threadIdx.x == 0 && *err) {
-    // let the copies still in flight land before the CTA leaves: chunks
-    // [seen, issued), at most one per stage
-    for (uint32_t w = seen; w < issued; ++w) mbar_drain(&full[w % LP_ST], (w / LP_ST) & 1u);
-    atomicAdd(timeouts, 1ull);
   }
   __syncthreads();
-  flush();
+  if (threadIdx.x == 0 && *err) {
+    // a wait gave up somewhere: only the last LP_ST copies the producer
+    // issued can still be in flight; let them land before the CTA leaves
+    for (uint32_t w = issued > (uint32_t)LP_ST ? issued - LP_ST : 0u; w < issued; ++w)
+      mbar_drain(&full[w % LP_ST], (w / LP_ST) & 1u);
+    atomicAdd(timeouts, 1ull);
+  }
+  // the last window, by the workers with the same element-to-thread mapping
+  // as the windows before (each thread's `written` covers its own elements)
+  if (warp != 0) flush(threadIdx.x - 32, LP_WORKERS * 32);
   for (uint32_t i = threadIdx.x; i < k; i += LS_THREADS)
     if (C[i]) atomicAdd(counts + i, (unsigned long long)C[i]);
 }
@@ -1146,13 +1207,18 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
       ++*nk;
     }
     // one warp per pair, latency-bound: a full SM of warps (32 registers a thread)
-    km_pair_kernel<<<di.sms * 8, 256, 0, s>>>(x, d, b.cent, b.pairs, b.nflag + 4, b.assign, b.stats + 1);
+    km_pair_kernel<<<di.sms * 8, 256, 0, s>>>(x, d, b.cent, b.pairs, b.nflag + 4, b.assign, b.stats);
     ++*nk;
+    // the points neither pass could decide: from the tensor-core pass its
+    // list (re-checked straight away with FP32 direct differences, then FP64
+    // where those leave more than one candidate), from the FP32 pass its own
+    const uint32_t* rl = b.precision != MR_KM_FP32 ? reinterpret_cast<const uint32_t*>(b.cent_bf16_norm) : b.flagged;
+    const uint32_t* rn = b.precision != MR_KM_FP32 ? b.nflag + 1 : b.nflag;
     if (rc_smem)
-      km_recheck_fp64_smem_kernel<<<di.sms * rc_per_sm, 512, rc_bytes, s>>>(x, d, b.cent, k, b.flagged, b.nflag, b.assign,
-                                                                b.stats + 1);
+      km_recheck_fp64_smem_kernel<<<di.sms * rc_per_sm, 512, rc_bytes, s>>>(x, d, b.cent, k, rl, rn, b.assign,
+                                                                             b.stats);
     else
-      km_recheck_fp64_kernel<<<di.sms * 4, 256, 0, s>>>(x, d, b.cent, k, b.flagged, b.nflag, b.assign, b.stats + 1);
+      km_recheck_fp64_kernel<<<di.sms * 4, 256, 0, s>>>(x, d, b.cent, k, rl, rn, b.assign, b.stats);
     if (local) {  // update with local arrays
       if (lp_rows)
         (d == 64 ? km_local_sum_pipe_kernel<true> : km_local_sum_pipe_kernel<false>)<<<ls_grid, LS_THREADS, lp_bytes,
@@ -1180,20 +1246,6 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   km_finish_kernel<<<di.sms, 256, 0, s>>>(b.cent, (uint64_t)k * d, out_c, b.assign, n, out_a, b.stats, out_s, iters);
-  ++*nk;
-  return cudaGetLastError();
-}
-
-// FP32 re-check of an index list (used after the BF16 tensor-core pass).
-cudaError_t launch_kmeans_fp32_list(const float* x, uint32_t n, uint32_t d, const float* c, uint32_t k, KmBuffers& b,
-                                    const uint32_t* list, const uint32_t* nlist, const DevInfo& di, cudaStream_t s,
-                                    uint64_t* nk) {
-  const int asm_bytes = (DC_MAX * CS_LD + DC_MAX * TP) * 4;
-  const uint32_t ntiles = (n + TP - 1) / TP;
-  uint32_t agrid = ntiles < (uint32_t)di.sms * 2 ? ntiles : (uint32_t)di.sms * 2;
-  if (b.grid_cap && agrid > b.grid_cap) agrid = b.grid_cap;
-  (k <= 256 ? km_assign_fp32_kernel<true> : km_assign_fp32_kernel<false>)<<<agrid, KM_THREADS, asm_bytes, s>>>(
-      x, n, d, c, k, b.cnorm, b.nflag + 3, list, nlist, b.assign, b.flagged, b.nflag, b.pairs, b.nflag + 4, b.stats);
   ++*nk;
   return cudaGetLastError();
 }

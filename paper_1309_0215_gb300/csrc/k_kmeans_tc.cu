@@ -530,10 +530,6 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
 
 bool km_tc_supported(uint32_t d, uint32_t k) { return d >= 1 && d <= KD && k >= 1 && k <= NMAX; }
 
-cudaError_t launch_kmeans_fp32_list(const float* x, uint32_t n, uint32_t d, const float* c, uint32_t k, KmBuffers& b,
-                                    const uint32_t* list, const uint32_t* nlist, const DevInfo& di, cudaStream_t s,
-                                    uint64_t* nk);
-
 size_t km_tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
 
 // Raw launch (also used by the diagnostics probe): list/nlist receive the
@@ -574,9 +570,8 @@ cudaError_t launch_kmeans_tc_assign(const float* x, uint32_t n, uint32_t d, cons
                           b.stop_copies);
   if (e != cudaSuccess || (e = kt_end(b.kt, s)) != cudaSuccess) return e;
   ++*nk;
-  // near ties of the tensor-core pass: FP32 pass over the list (its own near
-  // ties go on to the FP64 pass launched by the caller)
-  return launch_kmeans_fp32_list(x, n, d, c, k, b, list, b.nflag + 1, di, s, nk);
+  // the caller re-checks the pairs and the listed near ties
+  return cudaSuccess;
 }
 
 }  // namespace mrgb

@@ -49,8 +49,14 @@ namespace {
 using wc::JobDev;
 using wc::WarpLocal;
 
-constexpr int MAP_WARPS = 8;
+constexpr int MAP_WARPS = 8;                 // per-warp-cache map kernel: 5 CTAs per SM
 constexpr int MAP_THREADS = MAP_WARPS * 32;
+constexpr int CTA_WARPS = 16;               // CTA-table map kernel: 2 CTAs per SM
+constexpr int CTA_THREADS = CTA_WARPS * 32;
+// From this input size on the plain map pass uses the CTA-table kernel: each
+// CTA then sees enough tokens (tens of thousands) that its table pays for
+// its final merge of up to CT_SLOTS keys into the global container.
+constexpr uint64_t CTA_MAP_MIN_BYTES = 64ull << 20;
 constexpr int CB = 1024;            // records per compaction / sort / scan block
 constexpr uint64_t CNT_MAX = (1ull << 40) - 1;
 
@@ -58,6 +64,10 @@ __device__ __forceinline__ JobDev job_at(const JobDev* jobs, const JobDev& singl
   return jobs ? jobs[j] : single;
 }
 
+// Plain map + combine pass for small inputs: each warp combines into its own
+// hot-key cache (wc::WarpLocal) and inserts its misses at once (one slot per
+// probe step: the misses of a round are few and mostly found at their first
+// slot, where the second load costs more than it saves).
 __global__ void __launch_bounds__(MAP_THREADS, 5) wc_map_kernel(JobDev J) {
   extern __shared__ __align__(16) unsigned char wc_smem[];
   WarpLocal& L = reinterpret_cast<WarpLocal*>(wc_smem)[threadIdx.x >> 5];
@@ -66,8 +76,51 @@ __global__ void __launch_bounds__(MAP_THREADS, 5) wc_map_kernel(JobDev J) {
   const uint64_t nseg = (J.n + wc::SEG - 1) / wc::SEG;
   const uint64_t gw = (uint64_t)blockIdx.x * MAP_WARPS + (threadIdx.x >> 5);
   const uint64_t nw = (uint64_t)gridDim.x * MAP_WARPS;
-  for (uint64_t seg = gw; seg < nseg; seg += nw) wc::warp_segment(J, seg, L, occ);
-  wc::local_flush(L, occ, J);
+  for (uint64_t seg = gw; seg < nseg; seg += nw) wc::warp_segment<1>(J, seg, L, occ);
+  wc::local_flush<1>(L, occ, J);
+}
+
+// Plain map + combine pass for large inputs: CTAs of CTA_WARPS warps, two per
+// SM, sharing one local table per CTA (wc::CtaTable); a warp's misses are
+// queued and sent to the global container 32 at a time; at the end every
+// warp empties its queue and the CTA merges its table into the global
+// container.
+__global__ void __launch_bounds__(CTA_THREADS, 2) wc_map_cta_kernel(JobDev J) {
+  extern __shared__ __align__(16) unsigned char wc_smem[];
+  wc::CtaTable& T = *reinterpret_cast<wc::CtaTable*>(wc_smem);
+  wc::MapWarp& W = reinterpret_cast<wc::MapWarp*>(wc_smem + sizeof(wc::CtaTable))[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < wc::CT_SLOTS; i += CTA_THREADS) T.key[i] = make_ulonglong2(0ull, 0ull);
+  __syncthreads();
+  const uint64_t nseg = (J.n + wc::SEG - 1) / wc::SEG;
+  const uint64_t gw = (uint64_t)blockIdx.x * CTA_WARPS + (threadIdx.x >> 5);
+  const uint64_t nw = (uint64_t)gridDim.x * CTA_WARPS;
+  uint32_t qn = 0, qhd = 0;
+  for (uint64_t seg = gw; seg < nseg; seg += nw) {
+    const uint64_t base = seg * wc::SEG;
+    const int total = wc::stage_tokens(J, seg, W);
+    for (int r0 = 0; r0 < total; r0 += 32) {
+      const int i = r0 + lane;
+      bool m = false;
+      wc::Tok t{0, 0, 0};
+      if (i < total) {
+        t = wc::read_token(J.in, J.n, base, W, W.starts[i]);
+        m = !wc::cta_add(T, t);
+      }
+      wc::mq_push(J, W, m, t, qn, qhd);
+      __syncwarp();
+    }
+  }
+  __syncwarp();
+  if ((uint32_t)lane < qn) {
+    const uint32_t q = (qhd + (uint32_t)lane) & (wc::MQ - 1);
+    wc::global_insert(J, W.qw0[q], W.qw1[q], W.qh[q], 1);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < wc::CT_SLOTS; i += CTA_THREADS) {
+    const ulonglong2 k = T.key[i];
+    if (k.y != 0) wc::global_insert(J, k.x, k.y, T.h[i], T.cnt[i]);
+  }
 }
 
 
@@ -1968,6 +2021,7 @@ uint64_t wc_out_bytes(uint64_t cap, uint64_t n) {
 }
 
 int wc_map_smem_bytes() { return MAP_WARPS * (int)sizeof(WarpLocal); }
+static int wc_map_cta_smem_bytes() { return (int)(sizeof(wc::CtaTable) + CTA_WARPS * sizeof(wc::MapWarp)); }
 
 wc::JobDev wc_job_dev(const uint8_t* in, uint64_t n, const WcBuffers& b, uint64_t blk0) {
   JobDev J;
@@ -2126,6 +2180,19 @@ cudaError_t launch_wordcount(const uint8_t* in, uint64_t n, const WcBuffers& b, 
     if (grid > gmax) grid = gmax;
     if ((e = kt_begin(kt, s)) != cudaSuccess) return e;
     wc_pipe_kernel<<<(unsigned)grid, PIPE_THREADS, smem, s>>>(J, pipe_polls < 0 ? PIPE_SPIN_LIMIT : pipe_polls);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = kt_end(kt, s)) != cudaSuccess) return e;
+    ++*nk;
+  } else if (n >= CTA_MAP_MIN_BYTES) {
+    const int smem = wc_map_cta_smem_bytes();
+    if ((e = cudaFuncSetAttribute(wc_map_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+        cudaSuccess)
+      return e;
+    const uint64_t nseg = (n + wc::SEG - 1) / wc::SEG;
+    uint64_t grid = (nseg + CTA_WARPS - 1) / CTA_WARPS;
+    const uint64_t gmax = 2ull * di.sms;
+    if (grid > gmax) grid = gmax;
+    if ((e = kt_begin(kt, s)) != cudaSuccess) return e;
+    wc_map_cta_kernel<<<(unsigned)grid, CTA_THREADS, smem, s>>>(J);
     if ((e = cudaGetLastError()) != cudaSuccess || (e = kt_end(kt, s)) != cudaSuccess) return e;
     ++*nk;
   } else if (n > 0) {

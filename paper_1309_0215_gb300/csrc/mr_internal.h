@@ -55,13 +55,16 @@ cudaError_t kt_end(KTimer* t, cudaStream_t s);
 void kt_destroy(KTimer* t);
 
 // ------------------------------------------- large-key histogram, Bloom
-// Largest bin count whose local arrays (nbins + 1 u32) fit one CTA.
+// Largest bin count whose local arrays (nbins + 1 u32) fit one CTA, and a
+// thread-block cluster of CTAs.
 int hk_smem_max_bins(const DevInfo& di);
-// Histogram of n u32 keys into out[nbins + 1] (zeroed here).  smem: local
-// arrays per CTA; else atomics on the global array.  wide: count straight into
-// the u64 output (needed from 2^32 keys on); else into the u32 counters
-// (nbins + 1 words) and widen at the end.
-cudaError_t launch_hist_keys(const uint32_t* keys, uint64_t n, uint32_t nbins, bool smem, void* counters,
+int hk_cluster_max_bins(const DevInfo& di);
+// Histogram of n u32 keys into out[nbins + 1] (zeroed here).  container:
+// MR_C_SMEM_ARRAY local arrays per CTA, MR_C_CLUSTER_ARRAY local arrays
+// spread over a cluster's shared memory, else atomics on the global array.
+// wide: count straight into the u64 output (needed from 2^32 keys on); else
+// into the u32 counters (nbins + 1 words) and widen at the end.
+cudaError_t launch_hist_keys(const uint32_t* keys, uint64_t n, uint32_t nbins, int container, void* counters,
                              bool wide, unsigned long long* out, const DevInfo& di, cudaStream_t s, uint64_t* nk,
                              KTimer* kt = nullptr);
 // Bloom-filter build over n bases into ceil(m / 32) u32 words (zeroed here).

@@ -1,8 +1,9 @@
 """GPU parity: large-key histogram and Bloom-filter build against the oracle.
 
 Both are integer/bit work, so every result must equal the oracle's bytes.
-Cases cover both containers of the histogram (shared-memory local arrays and
-the global array), key ranges from 1 bin to 16M bins, out-of-range keys,
+Cases cover the three containers of the histogram (shared-memory local
+arrays of one CTA, local arrays spread over a thread-block cluster, the global
+array), key ranges from 1 bin to 16M bins, out-of-range keys,
 skewed keys, ragged lengths and unaligned device pointers; for the Bloom
 filter, window lengths 1..32, filter sizes that are not powers of two, runs
 of non-ACGT bytes and sequences shorter than one window; plus the full-size
@@ -36,6 +37,42 @@ def test_hist_u32_matches_oracle(mr, nbins, container):
     keys = synth.keys_u32(n, nbins + nbins // 8 + 1, seed=nbins)  # about 1 key in 9 out of range
     got = mr.hist_u32(_dev(keys), nbins, container=cmap[container])
     assert np.array_equal(got, oracle.hist_u32(keys, nbins))
+
+
+def _cluster_max_bins():
+    import torch
+    return 8 * (torch.cuda.get_device_properties(0).shared_memory_per_block_optin // 4) - 1
+
+
+@pytest.mark.parametrize("nbins", [1, 7, 8, 40, 70_000, 300_000, "max"])
+def test_hist_u32_cluster_container(mr, nbins):
+    """Local arrays spread over a thread-block cluster's distributed shared
+    memory (a container the caller picks): slice boundaries, the out-of-range
+    bin and the largest bin count the cluster holds, against the oracle and
+    against the automatically chosen container."""
+    if nbins == "max":
+        nbins = _cluster_max_bins()
+    n = 2_000_003
+    keys = synth.keys_u32(n, nbins + nbins // 8 + 1, seed=nbins + 5)
+    got = mr.hist_u32(_dev(keys), nbins, container=mr.C_CLUSTER_ARRAY)
+    assert np.array_equal(got, oracle.hist_u32(keys, nbins))
+    if nbins > 60_000:
+        assert np.array_equal(mr.hist_u32(_dev(keys), nbins), got)  # C_AUTO
+
+
+def test_hist_u32_cluster_container_skewed_unaligned_and_bad_args(mr):
+    sk = synth.keys_u32(3_000_001, 200_000, skewed=True, seed=8)
+    got = mr.hist_u32(_dev(sk, 4), 200_000, container=mr.C_CLUSTER_ARRAY)
+    assert np.array_equal(got, oracle.hist_u32(sk, 200_000))
+    c = mr.Context()
+    keys = synth.keys_u32(1000, 100, seed=2)
+    with pytest.raises(mr.MRError):
+        c.add_job(mr.HIST_U32, keys, hist_bins=_cluster_max_bins() + 1, container=mr.C_CLUSTER_ARRAY)
+    with pytest.raises(mr.MRError):
+        c.add_job(mr.HIST_RGB8, np.zeros(30, dtype=np.uint8), container=mr.C_CLUSTER_ARRAY)
+    with pytest.raises(mr.MRError):
+        c.add_job(mr.WORDCOUNT, b"a b", container=mr.C_CLUSTER_ARRAY)
+    c.close()
 
 
 @pytest.mark.parametrize("offset", [4, 8, 12])
