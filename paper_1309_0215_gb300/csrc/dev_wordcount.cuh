@@ -322,8 +322,11 @@ __device__ __forceinline__ uint4 shift_window(const uint4& a, const uint4& b, ui
 // W (members buf, wsb, starts), build the whitespace bitmap and the list of
 // token starts (segment-relative offsets of the tokens whose first byte lies
 // in the segment) and return how many there are.  All 32 lanes call this.
+// pre: when not null, the caller already loaded this lane's 16 bytes of the
+// segment (pre[0]) and, for lanes 0..3, of the halo (pre[1]) from a
+// 16-byte-aligned segment with at least BUF bytes left (seg_prefetchable).
 template <class B>
-__device__ inline int stage_tokens(const JobDev& J, uint64_t seg, B& L) {
+__device__ inline int stage_tokens(const JobDev& J, uint64_t seg, B& L, const uint4* pre = nullptr) {
   const int lane = threadIdx.x & 31;
   const uint64_t base = seg * SEG;
   const uint8_t* __restrict__ in = J.in;
@@ -332,7 +335,11 @@ __device__ inline int stage_tokens(const JobDev& J, uint64_t seg, B& L) {
   // stage the segment and its halo; bytes past the input end read as spaces
   const uintptr_t sa = reinterpret_cast<uintptr_t>(in + base);
   uint4 mine;
-  if (rem >= (uint64_t)BUF && (sa & 15) == 0) {
+  if (pre) {
+    mine = pre[0];
+    reinterpret_cast<uint4*>(L.buf)[lane] = mine;
+    if (lane < HALO / 16) reinterpret_cast<uint4*>(L.buf)[32 + lane] = pre[1];
+  } else if (rem >= (uint64_t)BUF && (sa & 15) == 0) {
     const uint4* src = reinterpret_cast<const uint4*>(sa);
     mine = __ldg(src + lane);
     reinterpret_cast<uint4*>(L.buf)[lane] = mine;
@@ -399,6 +406,18 @@ __device__ inline int stage_tokens(const JobDev& J, uint64_t seg, B& L) {
   }
   __syncwarp();
   return total;
+}
+
+// Whether segment seg can be staged from registers loaded ahead of time
+// (16-byte aligned, a full buffer of input left), and that load.
+__device__ __forceinline__ bool seg_prefetchable(const JobDev& J, uint64_t seg) {
+  return seg * SEG + BUF <= J.n && (reinterpret_cast<uintptr_t>(J.in + seg * SEG) & 15) == 0;
+}
+__device__ __forceinline__ void seg_prefetch(const JobDev& J, uint64_t seg, uint4 (&pre)[2]) {
+  const int lane = threadIdx.x & 31;
+  const uint4* src = reinterpret_cast<const uint4*>(J.in + seg * SEG);
+  pre[0] = __ldg(src + lane);
+  if (lane < HALO / 16) pre[1] = __ldg(src + 32 + lane);
 }
 
 // One warp maps and combines the tokens whose first byte lies in segment seg.

@@ -187,12 +187,13 @@ __device__ __forceinline__ void top2_keys(const uint32_t (&acc)[CHUNK], uint32_t
 }
 
 // BF16 hi/lo split of two values, packed little-endian (element 0 low half).
+// (one paired round-to-nearest conversion for each of hi and lo)
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
-  const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
-  const __nv_bfloat16 la = __float2bfloat16_rn(a - __bfloat162float(ha));
-  const __nv_bfloat16 lb = __float2bfloat16_rn(b - __bfloat162float(hb));
-  hi = (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
-  lo = (uint32_t)__bfloat16_as_ushort(la) | ((uint32_t)__bfloat16_as_ushort(lb) << 16);
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
 // Byte offset of 16-byte chunk c of row r in a 128-byte-swizzled tile whose

@@ -96,9 +96,17 @@ __global__ void __launch_bounds__(CTA_THREADS, 2) wc_map_cta_kernel(JobDev J) {
   const uint64_t gw = (uint64_t)blockIdx.x * CTA_WARPS + (threadIdx.x >> 5);
   const uint64_t nw = (uint64_t)gridDim.x * CTA_WARPS;
   uint32_t qn = 0, qhd = 0;
+  // the warp's next segment is loaded while it works on the current one
+  uint4 pre[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+  bool have = gw < nseg && wc::seg_prefetchable(J, gw);
+  if (have) wc::seg_prefetch(J, gw, pre);
   for (uint64_t seg = gw; seg < nseg; seg += nw) {
     const uint64_t base = seg * wc::SEG;
-    const int total = wc::stage_tokens(J, seg, W);
+    uint4 cur[2] = {pre[0], pre[1]};
+    const bool cur_ok = have;
+    have = seg + nw < nseg && wc::seg_prefetchable(J, seg + nw);
+    if (have) wc::seg_prefetch(J, seg + nw, pre);
+    const int total = wc::stage_tokens(J, seg, W, cur_ok ? cur : nullptr);
     for (int r0 = 0; r0 < total; r0 += 32) {
       const int i = r0 + lane;
       bool m = false;
