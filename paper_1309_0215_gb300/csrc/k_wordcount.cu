@@ -53,9 +53,10 @@ constexpr int MAP_WARPS = 8;                 // per-warp-cache map kernel: 5 CTA
 constexpr int MAP_THREADS = MAP_WARPS * 32;
 constexpr int CTA_WARPS = 16;               // CTA-table map kernel: 2 CTAs per SM
 constexpr int CTA_THREADS = CTA_WARPS * 32;
-// From this input size on the plain map pass uses the CTA-table kernel: each
-// CTA then sees enough tokens (tens of thousands) that its table pays for
-// its final merge of up to CT_SLOTS keys into the global container.
+// From this input size on the plain map pass uses the CTA-table kernel for a
+// 16-byte-aligned input (whose next segment each warp loads ahead): each CTA
+// then sees enough tokens (tens of thousands) that its table pays for its
+// final merge of up to CT_SLOTS keys into the global container.
 constexpr uint64_t CTA_MAP_MIN_BYTES = 64ull << 20;
 constexpr int CB = 1024;            // records per compaction / sort / scan block
 constexpr uint64_t CNT_MAX = (1ull << 40) - 1;
@@ -2190,7 +2191,7 @@ cudaError_t launch_wordcount(const uint8_t* in, uint64_t n, const WcBuffers& b, 
     wc_pipe_kernel<<<(unsigned)grid, PIPE_THREADS, smem, s>>>(J, pipe_polls < 0 ? PIPE_SPIN_LIMIT : pipe_polls);
     if ((e = cudaGetLastError()) != cudaSuccess || (e = kt_end(kt, s)) != cudaSuccess) return e;
     ++*nk;
-  } else if (n >= CTA_MAP_MIN_BYTES) {
+  } else if (n >= CTA_MAP_MIN_BYTES && (reinterpret_cast<uintptr_t>(in) & 15) == 0) {
     const int smem = wc_map_cta_smem_bytes();
     if ((e = cudaFuncSetAttribute(wc_map_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
         cudaSuccess)

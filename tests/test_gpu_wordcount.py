@@ -60,6 +60,47 @@ def test_wc_tokens_straddle_segments_and_long_keys(mr):
         assert mr.wordcount(_dev(text, off)) == oracle.wordcount(text)
 
 
+@pytest.mark.slow
+def test_wc_large_input_path_edge_content(mr):
+    """Aligned inputs from 64 MiB take the CTA-table map kernel (a shared
+    table per CTA, batched global inserts, segments loaded ahead).  80 MiB of
+    adversarial content: tokens of 1..40 bytes and a few of 600 and 1300
+    (so keys straddle 512- and 1024-byte boundaries and long keys are
+    compared byte by byte), every whitespace byte as a separator, token bytes
+    including 0x00 and bytes >= 0x80 (keys whose first 8 bytes are all zero
+    never enter the CTA tables), a hot key and a long shared-prefix family;
+    aligned (the CTA kernel) and one byte in (the per-warp kernel)."""
+    rng = np.random.default_rng(21)
+    vocab = []
+    for i in range(6000):
+        w = np.array([10, 10, 10, 10, 10, 10, 10, 5, 5, 5, 4.98, .01, .01])
+        L = int(rng.choice([1, 2, 3, 7, 8, 9, 15, 16, 17, 24, 40, 600, 1300], p=w / w.sum()))
+        if i % 7 == 0:  # NUL-led keys, some all NUL
+            b = bytes(L) if i % 14 == 0 else b"\x00" * min(L, 8) + bytes(rng.integers(97, 123, max(0, L - 8)).astype(np.uint8))
+        else:
+            b = bytes(rng.choice(np.frombuffer(b"abcxyz\x01\x7f\x80\xfe\xff", dtype=np.uint8), L))
+        vocab.append(b[:L] if len(b) >= L else b + b"q" * (L - len(b)))
+    vocab += [b"prefix_shared_by_many_keys_" + bytes([97 + (i % 26)]) * (10 + i % 30) for i in range(200)]
+    ws = [b" ", b"\n", b"\t", b"\r", b"\x0b", b"\x0c", b"  ", b" \n\t"]
+    ranks = rng.zipf(1.3, 3_000_000) % len(vocab)
+    seps = rng.integers(0, len(ws), ranks.size)
+    chunks = []
+    total = 0
+    for r, s in zip(ranks, seps):
+        chunks.append(vocab[r])
+        chunks.append(ws[s])
+        total += len(vocab[r]) + len(ws[s])
+        if total >= (80 << 20):
+            break
+    text = b"".join(chunks)
+    while len(text) < (80 << 20):
+        text = text + text[: (80 << 20) - len(text)]
+    text = text[: 80 << 20]
+    exp = oracle.wordcount(text)
+    for off in (0, 1):
+        assert mr.wordcount(_dev(text, off)) == exp, off
+
+
 def test_wc_hot_key_contention(mr):
     text = b"hot " * 500_000 + b"cold hot\n" * 1000
     assert mr.wordcount(_dev(text)) == oracle.wordcount(text)
@@ -99,19 +140,28 @@ def test_wc_zipf_16MiB_bit_exact(mr):
     assert sum(c for _, c in recs) == len(ranks)
 
 
+_BIG = {}
+
+
 @pytest.mark.slow
-@pytest.mark.parametrize("pipelined", [False, True])
-def test_wc_zipf_320MiB_bit_exact(mr, pipelined):
-    """320 MiB of the same generator's text, past the size at which every warp
-    of the map kernel (5 CTAs x 8 warps per SM, 64 segments of 512 bytes
-    between hot-key cache merges: ~199 MB per launch) merges its cache into
-    the global table in mid-stream and then re-learns the hot keys."""
-    import torch
-    text, ranks, _ = synth.wc_text(320 << 20, seed=synth.SEED_BASE + 11)
-    got = mr.wordcount(torch.from_numpy(text).cuda(), pipelined=pipelined)
-    assert got == oracle.wordcount(text)
+@pytest.mark.parametrize("path", ["cta", "warp", "pipelined"])
+def test_wc_zipf_320MiB_bit_exact(mr, path):
+    """320 MiB of the same generator's text through each large-input map
+    path: the CTA-table kernel (16-byte-aligned input); the per-warp-cache
+    kernel (the same text one byte into its buffer), past the size at which
+    every warp (5 CTAs x 8 warps per SM, 64 segments of 512 bytes between
+    hot-key cache merges: ~199 MB per launch) merges its cache into the
+    global table in mid-stream and then re-learns the hot keys; and the
+    pipelined mapper/reducer kernel, whose mappers do the same."""
+    if not _BIG:
+        text, ranks, _ = synth.wc_text(320 << 20, seed=synth.SEED_BASE + 11)
+        _BIG.update(text=text, ntok=len(ranks), exp=oracle.wordcount(text))
+    text = _BIG["text"]
+    d = _dev(text, 1 if path == "warp" else 0)
+    got = mr.wordcount(d, pipelined=path == "pipelined")
+    assert got == _BIG["exp"]
     recs = oracle.parse_wordcount(got)
-    assert sum(c for _, c in recs) == len(ranks)
+    assert sum(c for _, c in recs) == _BIG["ntok"]
 
 
 @pytest.mark.parametrize("torch_alloc", [False, True])
