@@ -23,18 +23,19 @@
 namespace mrgb {
 namespace {
 
-// 8 warps per CTA, five CTAs per SM: 40 warps per SM keep the word-count
-// tiles' latency-bound loops fed (the plain map kernel's shape).  For that
-// the histogram tiles use a narrower local table than the plain kernel:
-// 8 lane columns (lane % 8) per bin, 24 KiB, so lanes 8 apart share a
-// column (a few more shared-memory atomic collisions on equal bins).
-constexpr int BT = 256;
+// 16 warps per CTA, two CTAs per SM: the large-input word-count map
+// kernel's shape.  A word-count tile runs as in that kernel: one local table
+// per CTA shared by its warps (wc::CtaTable), each warp's misses queued and
+// inserted 32 at a time, each warp's next segment loaded ahead.  Histogram
+// tiles use 16 lane columns (lane % 16) per bin, 48 KiB, so lanes 16 apart
+// share a column (a few more shared-memory atomic collisions on equal bins).
+constexpr int BT = 512;
 constexpr int BWARPS = BT / 32;
-constexpr int BCTAS = 5;                 // CTAs per SM
-constexpr int BH_COLS = 8;               // histogram lane columns per bin
+constexpr int BCTAS = 2;                 // CTAs per SM
+constexpr int BH_COLS = 16;              // histogram lane columns per bin
 constexpr int BH_WORDS = arr::HIST_BINS * BH_COLS;
 constexpr int B_SMEM_HIST = BH_WORDS * 4;
-constexpr int B_SMEM_WC = BWARPS * (int)sizeof(wc::WarpLocal);
+constexpr int B_SMEM_WC = (int)(sizeof(wc::CtaTable) + BWARPS * sizeof(wc::MapWarp));
 constexpr int B_SMEM = B_SMEM_HIST > B_SMEM_WC ? B_SMEM_HIST : B_SMEM_WC;
 static_assert(BCTAS * (B_SMEM + 1024) + 4096 <= 232448, "BCTAS batch CTAs must fit one SM's shared memory");
 
@@ -168,11 +169,13 @@ batch_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs, uint64_t total_t
   __shared__ long long part[BWARPS][5];
   __shared__ wc::JobDev s_jd;  // the current word-count job
   uint32_t* hs = reinterpret_cast<uint32_t*>(bsm);
-  wc::WarpLocal& L = reinterpret_cast<wc::WarpLocal*>(bsm)[threadIdx.x >> 5];
+  wc::CtaTable& T = *reinterpret_cast<wc::CtaTable*>(bsm);
+  wc::MapWarp& W = reinterpret_cast<wc::MapWarp*>(bsm + sizeof(wc::CtaTable))[threadIdx.x >> 5];
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(hs);
+  const int lane = threadIdx.x & 31;
   int64_t cur = -1;
   uint32_t kind = 0, cont = 0;
-  int occ = 0;
+  uint32_t qn = 0, qhd = 0;  // this warp's queued misses (word count)
 
   auto flush = [&](const BatchJob& J) {
     if (kind == MR_HIST_RGB8 && cont != MR_C_GLOBAL_ARRAY) {
@@ -186,7 +189,19 @@ batch_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs, uint64_t total_t
       }
       __syncthreads();
     } else if (kind == MR_WORDCOUNT) {
-      wc::local_flush<1>(L, occ, J.wc);
+      // every warp's queued misses, then the CTA's table, into the job's
+      // global container
+      __syncwarp();
+      if ((uint32_t)lane < qn) {
+        const uint32_t q = (qhd + (uint32_t)lane) & (wc::MQ - 1);
+        wc::global_insert(s_jd, W.qw0[q], W.qw1[q], W.qh[q], 1);
+      }
+      qn = qhd = 0;
+      __syncthreads();
+      for (int i = threadIdx.x; i < wc::CT_SLOTS; i += BT) {
+        const ulonglong2 k = T.key[i];
+        if (k.y != 0) wc::global_insert(s_jd, k.x, k.y, T.h[i], T.cnt[i]);
+      }
       __syncthreads();
     }
   };
@@ -198,8 +213,8 @@ batch_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs, uint64_t total_t
       __syncthreads();
     } else if (kind == MR_WORDCOUNT) {
       if (threadIdx.x == 0) s_jd = J.wc;
-      wc::local_clear(L);
-      occ = 0;
+      for (int i = threadIdx.x; i < wc::CT_SLOTS; i += BT) T.key[i] = make_ulonglong2(0ull, 0ull);
+      qn = qhd = 0;
       __syncthreads();
     }
   };
@@ -230,7 +245,29 @@ batch_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs, uint64_t total_t
       // the job's descriptor from shared memory (copied at the job switch):
       // through a reference to global memory every use in the hot loop would
       // be a global reload, and a register copy would not fit
-      for (uint64_t sg = s0 + (threadIdx.x >> 5); sg < s1; sg += BWARPS) wc::warp_segment<1>(s_jd, sg, L, occ);
+      const uint64_t w0 = s0 + (threadIdx.x >> 5);
+      uint4 pre[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+      bool have = w0 < s1 && wc::seg_prefetchable(s_jd, w0);
+      if (have) wc::seg_prefetch(s_jd, w0, pre);
+      for (uint64_t sg = w0; sg < s1; sg += BWARPS) {
+        const uint64_t base = sg * wc::SEG;
+        uint4 cp[2] = {pre[0], pre[1]};
+        const bool cp_ok = have;
+        have = sg + BWARPS < s1 && wc::seg_prefetchable(s_jd, sg + BWARPS);
+        if (have) wc::seg_prefetch(s_jd, sg + BWARPS, pre);
+        const int total = wc::stage_tokens(s_jd, sg, W, cp_ok ? cp : nullptr);
+        for (int r0 = 0; r0 < total; r0 += 32) {
+          const int i = r0 + lane;
+          bool m = false;
+          wc::Tok tk{0, 0, 0};
+          if (i < total) {
+            tk = wc::read_token(s_jd.in, s_jd.n, base, W, W.starts[i]);
+            m = !wc::cta_add(T, tk);
+          }
+          wc::mq_push(s_jd, W, m, tk, qn, qhd);
+          __syncwarp();
+        }
+      }
     } else {
       const uint64_t t0 = local * arr_tile;
       if (J.kind == MR_HIST_RGB8 && cont == MR_C_GLOBAL_ARRAY) {

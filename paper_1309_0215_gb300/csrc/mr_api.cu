@@ -109,7 +109,7 @@ struct mr_ctx {
   cudaGraphExec_t batch_exec = nullptr;
   std::vector<uint64_t> batch_ids;
   uint64_t batch_launches = 0;  // kernels per replay of the graph
-  mr_tuning tune{1536ull * 512, 512ull * 512, 0, 0.f, 0};  // the autotuner's usual choice on GB300
+  mr_tuning tune{1536ull * 2048, 512ull * 2048, 0, 0.f, 0};  // the autotuner's usual choice on GB300
   // serving: continuous batching over a few internal streams ("slots")
   struct Slot {
     cudaStream_t s = nullptr;
