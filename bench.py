@@ -65,14 +65,17 @@ def source_sha(sources) -> str:
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel: str, sources):
-    """Per-launch DRAM bytes (at this workload's size) from the committed ncu
-    summary, if the kernel's sources are unchanged since the capture (else
-    None)."""
+def _traffic(kernel: str, sources, input_bytes: int):
+    """Per-launch DRAM bytes from the committed ncu summary, scaled from the
+    input size it was captured at to this launch's input bytes (the traffic
+    of these kernels grows in proportion to their input), if the kernel's
+    sources are unchanged since the capture (else None)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f)[kernel]
-        return rec["bytes_per_launch"] if rec.get("source_sha") == source_sha(sources) else None
+        if rec.get("source_sha") != source_sha(sources):
+            return None
+        return int(round(rec["bytes_per_launch"] * input_bytes / rec["input_bytes"]))
     except Exception:
         return None
 
@@ -424,7 +427,7 @@ def run_ours(args):
         achieved = kbytes / (kern_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": hbm_peak,
                 "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
-                "traffic": _traffic(kname, ksrc), "algorithmic_bytes_per_launch": int(kbytes),
+                "traffic": _traffic(kname, ksrc, kbytes), "algorithmic_bytes_per_launch": int(kbytes),
                 "launch_ms": round(kern_ms, 5), "launches_timed": int(sum(c for _, (_, c) in job_stats))}
         if args.workload == "arrays":
             step_gbs = total_bytes / (ms_per_step / 1e3) / 1e9
@@ -450,7 +453,7 @@ def run_ours(args):
             ach = flops / (kern_ms / 1e3) / 1e12
             roof = {"bound": bound, "kernel": kname, "achieved": round(ach, 1), "peak": round(peak, 1),
                     "peak_source": peak_src if args.precision else "derived", "unit": unit,
-                    "frac": round(ach / peak, 4), "traffic": _traffic(kname, ksrc),
+                    "frac": round(ach / peak, 4), "traffic": _traffic(kname, ksrc, kbytes),
                     "algorithmic_flops_per_launch": flops, "launch_ms": round(kern_ms, 5),
                     "launches_timed": int(sum(c for _, (_, c) in job_stats)), "note": note}
         line = {

@@ -21,11 +21,14 @@
 //     TMEM lane per point; four warps per lane quadrant, each on a quarter
 //     of the columns), form d~ = fma(-2, acc, ||x||^2) + ||c||^2, pack it
 //     with its column into one sortable 32-bit key and keep the two smallest
-//     keys with unsigned min/max (eight independent top-2s per thread) plus
-//     a lower bound of all other keys; quarters 1..3 hand theirs to quarter
-//     0, which applies the margin tests below.
-// Copies, converters, MMA issue and epilogue overlap through the staging
-// ring, two operand stages and two TMEM accumulators.  Every mbarrier wait is bounded; on timeout the
+//     keys with signed min/max (four independent top-2s per thread) plus
+//     a lower bound of all other keys, and hand them to
+//   * 4 finalizer warps (one per lane quadrant), which merge the four
+//     column quarters of each point and apply the margin tests below, so
+//     that no epilogue warp carries the per-point tail on its own path.
+// Copies, converters, MMA issue, epilogue and finalizers overlap through the
+// staging ring, two operand stages, two TMEM accumulators and two hand-off
+// buffers.  Every mbarrier wait is bounded; on timeout the
 // CTA stops, drains its MMAs, frees TMEM and reports through stats[3].
 //
 // Margin test (rigorous, per point).  With u_b = 2^-8 (BF16 rounding) the
@@ -55,17 +58,20 @@ constexpr int TM = 128;          // points per tile = MMA M = TMEM lanes
 constexpr int KD = 64;           // padded dimension: one 128-byte row of BF16
 constexpr int NMAX = 256;        // centroids: MMA N
 constexpr int EPI_WARPS = 16;     // four per TMEM lane quadrant, each on a quarter of the columns
-constexpr int EPI_COLS = NMAX / (EPI_WARPS / 4);  // 64 columns per epilogue warp
+constexpr int QUARTERS = EPI_WARPS / 4;
+constexpr int EPI_COLS = NMAX / QUARTERS;  // 64 columns per epilogue warp
 constexpr int MMA_WARP = EPI_WARPS;
 constexpr int CVT_WARP0 = MMA_WARP + 1;
-constexpr int CVT_WARPS = 8;
-constexpr int TMA_WARP = CVT_WARP0 + CVT_WARPS;  // 25
-constexpr int TC_THREADS = (EPI_WARPS + 1 + CVT_WARPS + 1) * 32;  // 832
+constexpr int CVT_WARPS = 4;      // each converts 32 rows of a tile
+constexpr int FIN_WARP0 = CVT_WARP0 + CVT_WARPS;
+constexpr int FIN_WARPS = 4;      // one per TMEM lane quadrant: 32 points each
+constexpr int TMA_WARP = FIN_WARP0 + FIN_WARPS;  // 25
+constexpr int TC_THREADS = (EPI_WARPS + 1 + CVT_WARPS + FIN_WARPS + 1) * 32;  // 832
 constexpr int STAGES = 2;         // operand stages
 constexpr int XST = 2;            // FP32 staging buffers filled by the bulk copy engine
 constexpr int ACCS = 2;           // TMEM accumulators
 constexpr uint32_t TMEM_COLS = 512;  // two 256-column FP32 accumulators
-constexpr int NSET = 8;           // independent running top-2s per epilogue thread
+constexpr int NSET = 4;           // independent running top-2s per epilogue thread
 constexpr int CHUNK = 32;         // TMEM columns per tcgen05.ld in the epilogue
 
 struct __align__(1024) TcSmem {
@@ -76,11 +82,13 @@ struct __align__(1024) TcSmem {
   float xs[XST][TM * KD];             // FP32 point tiles (D == 64 path)
   float nx[STAGES][TM];
   float cn[NMAX];
-  // top-2 keys and the lower bound of the other keys of column quarters 1..3, per row
-  uint32_t xw1[ACCS][EPI_WARPS / 4 - 1][TM], xw2[ACCS][EPI_WARPS / 4 - 1][TM], xlb[ACCS][EPI_WARPS / 4 - 1][TM];
+  // per column quarter and row: top-2 keys and the lower bound of the
+  // other keys; and the row's ||x||^2 (epilogue -> finalizers)
+  uint32_t xw1[ACCS][QUARTERS][TM], xw2[ACCS][QUARTERS][TM], xlb[ACCS][QUARTERS][TM];
+  float xnx[ACCS][TM];
   unsigned long long full_a[STAGES], empty_a[STAGES], nx_free[STAGES];
   unsigned long long full_acc[ACCS], empty_acc[ACCS], drained;
-  unsigned long long xfull[ACCS], xfree[ACCS];  // quarters 1..3 hand their keys to quarter 0
+  unsigned long long xfull[ACCS], xfree[ACCS];  // epilogue warps hand their keys to the finalizers
   unsigned long long tfull[XST], tempty[XST];   // FP32 staging ring
   uint32_t tmem_base;
   int err;
@@ -223,8 +231,8 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
     for (int b = 0; b < ACCS; ++b) {
       mbar_init(&S.full_acc[b], 1);
       mbar_init(&S.empty_acc[b], EPI_WARPS);
-      mbar_init(&S.xfull[b], EPI_WARPS - 4);
-      mbar_init(&S.xfree[b], 4);
+      mbar_init(&S.xfull[b], EPI_WARPS);
+      mbar_init(&S.xfree[b], FIN_WARPS);
     }
     for (int q = 0; q < XST; ++q) {
       mbar_init(&S.tfull[q], 1);
@@ -265,10 +273,11 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
 
   if (warp >= CVT_WARP0 && warp < CVT_WARP0 + CVT_WARPS) {
     // ---------------------------------------------------------- converters
-    // Warp cw owns tile rows 16 cw .. 16 cw + 15.  Step q gives lane l row
-    // 16 cw + 2q + l / 16 and dims 4 (l % 16) .. + 3, so one warp load reads
-    // two whole FP32 rows (512 contiguous bytes) and one warp store writes
-    // two whole 128-byte swizzled BF16 rows: no shared-memory bank conflicts.
+    // Warp cw owns tile rows 32 cw .. 32 cw + 31, in two halves of 16.  Step
+    // q of half hf gives lane l row 32 cw + 16 hf + 2q + l / 16 and dims
+    // 4 (l % 16) .. + 3, so one warp load reads two whole FP32 rows (512
+    // contiguous bytes) and one warp store writes two whole 128-byte
+    // swizzled BF16 rows: no shared-memory bank conflicts.
     const int cw = warp - CVT_WARP0;
     const int col = lane & 15, rsub = lane >> 4;
     const bool vec = d == KD && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
@@ -278,50 +287,58 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
       const int s = (int)(i % STAGES);
       const uint32_t u = i / STAGES;
       const int q2 = (int)(i % XST);
-      float4 v[8];
       if (vec) {
         // the tile was staged by the bulk copy engine
         const bool okt = mbar_wait(&S.tfull[q2], (i / XST) & 1, err, polls);
         if (!__all_sync(0xffffffffu, okt)) break;
+      }
+      bool ok = true;
+      for (int hf = 0; hf < 2; ++hf) {
+        const int r0 = 32 * cw + 16 * hf;
+        float4 v[8];
+        if (vec) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int rr = r0 + 2 * q + rsub;
+            v[q] = tile * TM + rr < n ? *reinterpret_cast<const float4*>(&S.xs[q2][rr * KD + 4 * col])
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const uint32_t p = tile * TM + r0 + 2 * q + rsub;
+            const uint32_t d0 = 4 * col;
+            const float* row = x + (uint64_t)p * d;
+            v[q].x = (p < n && d0 < d) ? row[d0] : 0.f;
+            v[q].y = (p < n && d0 + 1 < d) ? row[d0 + 1] : 0.f;
+            v[q].z = (p < n && d0 + 2 < d) ? row[d0 + 2] : 0.f;
+            v[q].w = (p < n && d0 + 3 < d) ? row[d0 + 3] : 0.f;
+          }
+        }
+        if (hf == 0 && i >= STAGES) {
+          ok = mbar_wait(&S.empty_a[s], (u + 1) & 1, err, polls);
+          ok = ok && mbar_wait(&S.nx_free[s], (u + 1) & 1, err, polls);
+          ok = __all_sync(0xffffffffu, ok);
+          if (!ok) break;
+        }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const int rr = 16 * cw + 2 * q + rsub;
-          v[q] = tile * TM + rr < n ? *reinterpret_cast<const float4*>(&S.xs[q2][rr * KD + 4 * col])
-                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+          const int rr = r0 + 2 * q + rsub;
+          float ss = fmaf(v[q].w, v[q].w, fmaf(v[q].z, v[q].z, fmaf(v[q].y, v[q].y, v[q].x * v[q].x)));
+          ss += __shfl_xor_sync(0xffffffffu, ss, 8);
+          ss += __shfl_xor_sync(0xffffffffu, ss, 4);
+          ss += __shfl_xor_sync(0xffffffffu, ss, 2);
+          ss += __shfl_xor_sync(0xffffffffu, ss, 1);
+          if (col == 0) S.nx[s][rr] = ss;
+          uint32_t hi0, lo0, hi1, lo1;
+          split2(v[q].x, v[q].y, hi0, lo0);
+          split2(v[q].z, v[q].w, hi1, lo1);
+          const uint32_t off = swz(rr, col >> 1) + (uint32_t)(col & 1) * 8u;
+          *reinterpret_cast<uint2*>(S.a_hi[s] + off) = make_uint2(hi0, hi1);
+          if (TERMS == 3) *reinterpret_cast<uint2*>(S.a_lo[s] + off) = make_uint2(lo0, lo1);
         }
-      } else {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const uint32_t p = tile * TM + 16 * cw + 2 * q + rsub;
-          const uint32_t d0 = 4 * col;
-          const float* row = x + (uint64_t)p * d;
-          v[q].x = (p < n && d0 < d) ? row[d0] : 0.f;
-          v[q].y = (p < n && d0 + 1 < d) ? row[d0 + 1] : 0.f;
-          v[q].z = (p < n && d0 + 2 < d) ? row[d0 + 2] : 0.f;
-          v[q].w = (p < n && d0 + 3 < d) ? row[d0 + 3] : 0.f;
-        }
       }
-      if (i >= STAGES) {
-        bool ok = mbar_wait(&S.empty_a[s], (u + 1) & 1, err, polls);
-        ok = ok && mbar_wait(&S.nx_free[s], (u + 1) & 1, err, polls);
-        if (!__all_sync(0xffffffffu, ok)) break;
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int rr = 16 * cw + 2 * q + rsub;
-        float ss = fmaf(v[q].w, v[q].w, fmaf(v[q].z, v[q].z, fmaf(v[q].y, v[q].y, v[q].x * v[q].x)));
-        ss += __shfl_xor_sync(0xffffffffu, ss, 8);
-        ss += __shfl_xor_sync(0xffffffffu, ss, 4);
-        ss += __shfl_xor_sync(0xffffffffu, ss, 2);
-        ss += __shfl_xor_sync(0xffffffffu, ss, 1);
-        if (col == 0) S.nx[s][rr] = ss;
-        uint32_t hi0, lo0, hi1, lo1;
-        split2(v[q].x, v[q].y, hi0, lo0);
-        split2(v[q].z, v[q].w, hi1, lo1);
-        const uint32_t off = swz(rr, col >> 1) + (uint32_t)(col & 1) * 8u;
-        *reinterpret_cast<uint2*>(S.a_hi[s] + off) = make_uint2(hi0, hi1);
-        if (TERMS == 3) *reinterpret_cast<uint2*>(S.a_lo[s] + off) = make_uint2(lo0, lo1);
-      }
+      if (!ok) break;
       // The staging buffer is released only here: the bulk copy engine writes
       // through the async proxy, so the shared loads above must be ordered
       // before its next fill by this proxy fence (the stores that consumed
@@ -396,23 +413,87 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
       (void)issued;
     }
     __syncwarp();
+  } else if (warp >= FIN_WARP0 && warp < FIN_WARP0 + FIN_WARPS) {
+    // ------------------------------------------------------------ finalizers
+    // Warp f takes the points of TMEM lane quadrant f (rows 32 f + lane): it
+    // merges the four column quarters' top-2 keys into the row's exact top-2
+    // (g1, g2) and a lower bound g3 of every other key, then applies the
+    // margin tests.
+    const int r = (warp - FIN_WARP0) * 32 + lane;
+    const float eps_sum = TERMS == 3 ? (3.05f * 1.52587890625e-05f + (float)(3 * KD + 8) * 4.76837158203125e-07f)
+                                     : (2.f * 3.90625e-03f + 1.52587890625e-05f + (float)(KD + 8) * 4.76837158203125e-07f);
+    const float eps32 = 1.01f * (float)(d + 8) * 5.9604644775390625e-08f;
+    for (uint32_t i = 0;; ++i) {
+      const uint32_t tile = blockIdx.x + i * gridDim.x;
+      if (tile >= ntiles) break;
+      const int b = (int)(i & 1);
+      const uint32_t v = i >> 1;
+      const bool okx = mbar_wait(&S.xfull[b], v & 1, err, polls);
+      if (!__all_sync(0xffffffffu, okx)) break;
+      int o1[QUARTERS], o2[QUARTERS], ol[QUARTERS];
+#pragma unroll
+      for (int u = 0; u < QUARTERS; ++u) {
+        o1[u] = (int)S.xw1[b][u][r];
+        o2[u] = (int)S.xw2[b][u][r];
+        ol[u] = (int)S.xlb[b][u][r];
+      }
+      const float nxv = S.xnx[b][r];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.xfree[b]);
+      int g1 = o1[0], g2 = o2[0], g3 = ol[0];
+#pragma unroll
+      for (int u = 1; u < QUARTERS; ++u) top2_merge(g1, g2, o1[u], o2[u]);
+      // every key other than g1, g2 is >= g3: the quarters' bounds, and the
+      // quarters' top-2 keys that did not make the row's top-2
+#pragma unroll
+      for (int u = 0; u < QUARTERS; ++u) {
+        g3 = min(g3, ol[u]);
+        g3 = (o1[u] != g1 && o1[u] != g2) ? min(g3, o1[u]) : g3;
+        g3 = (o2[u] != g1 && o2[u] != g2) ? min(g3, o2[u]) : g3;
+      }
+      const uint32_t p = tile * TM + r;
+      bool flag = false, pair = false;
+      if (p < n) {
+        const float d1 = key_dist(g1), d2 = key_dist(g2), d3 = key_dist(g3);
+        const float xn = sqrtf(nxv);
+        const float e = 2.f * eps_sum * xn * cmax + eps32 * (xn + cmax) * (xn + cmax);
+        // keys under-state a distance by less than 2^-15 of it (2^-14 allowed)
+        const float gap = 2.f * e + 6.103515625e-05f * d1;
+        if (g1 < 0) flag = true;  // a negative smallest distance: re-check
+        else if (d2 - d1 > fmaxf(1e-3f * d1, gap)) assign[p] = g1 & 0xFF;
+        else if (d3 - d1 > gap) pair = true;  // only the top two can be the exact minimum
+        else flag = true;
+      }
+      const unsigned pm = __ballot_sync(0xffffffffu, pair);
+      if (pm) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(npairs, (uint32_t)__popc(pm));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (pair)
+          pairs[base + __popc(pm & ((1u << lane) - 1))] =
+              make_uint2(p, ((uint32_t)g1 & 0xFFu) | (((uint32_t)g2 & 0xFFu) << 16));
+      }
+      const unsigned fm = __ballot_sync(0xffffffffu, flag);
+      if (fm) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(nlist, (uint32_t)__popc(fm));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (flag) list[base + __popc(fm & ((1u << lane) - 1))] = p;
+      }
+    }
   } else {
     // ------------------------------------------------------------- epilogue
     // Warp e reads TMEM lane quadrant e % 4 (rows 32 (e % 4) ..) and column
     // quarter e / 4 (EPI_COLS columns), CHUNK columns per tcgen05.ld.  Each
     // distance becomes one sortable 32-bit key (see dist_key), so a running
-    // top-2 costs three unsigned min/max; NSET independent top-2s per thread
+    // top-2 costs three min/max; NSET independent top-2s per thread
     // (columns j mod NSET) keep the dependency chains short.  A warp then
     // reduces its sets to its top-2 (w1, w2) and a lower bound lb of all its
     // other keys (per set: the set's smallest key that is not w1 or w2, or
-    // its second key when both are, which bounds the rest of that set).
-    // Quarters 1..3 hand (w1, w2, lb) to quarter 0, which forms the row's
-    // exact top-2 (g1, g2) and a lower bound g3 of every other key.
+    // its second key when both are, which bounds the rest of that set) and
+    // hands (w1, w2, lb) to the finalizer of its lane quadrant.
     const int q = warp & 3, quarter = warp >> 2;
     const int r = q * 32 + lane;
-    const float eps_sum = TERMS == 3 ? (3.05f * 1.52587890625e-05f + (float)(3 * KD + 8) * 4.76837158203125e-07f)
-                                     : (2.f * 3.90625e-03f + 1.52587890625e-05f + (float)(KD + 8) * 4.76837158203125e-07f);
-    const float eps32 = 1.01f * (float)(d + 8) * 5.9604644775390625e-08f;
     const uint32_t c_lo = (uint32_t)quarter * EPI_COLS;
     const uint32_t c_hi = min(npad, c_lo + (uint32_t)EPI_COLS);
     for (uint32_t i = 0;; ++i) {
@@ -449,73 +530,16 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
       int lb = KEY_NONE;
 #pragma unroll
       for (int a = 0; a < NSET; ++a) lb = min(lb, (t1[a] == w1 || t1[a] == w2) ? t2[a] : t1[a]);
-      if (quarter != 0) {
-        if (i >= ACCS) {
-          const bool okf = mbar_wait(&S.xfree[b], (v + 1) & 1, err, polls);
-          if (!__all_sync(0xffffffffu, okf)) break;
-        }
-        S.xw1[b][quarter - 1][r] = (uint32_t)w1;
-        S.xw2[b][quarter - 1][r] = (uint32_t)w2;
-        S.xlb[b][quarter - 1][r] = (uint32_t)lb;
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&S.xfull[b]);
-        continue;
+      if (i >= ACCS) {
+        const bool okf = mbar_wait(&S.xfree[b], (v + 1) & 1, err, polls);
+        if (!__all_sync(0xffffffffu, okf)) break;
       }
-      int o1[EPI_WARPS / 4 - 1], o2[EPI_WARPS / 4 - 1], ol[EPI_WARPS / 4 - 1];
-      {
-        const bool okx = mbar_wait(&S.xfull[b], v & 1, err, polls);
-        if (!__all_sync(0xffffffffu, okx)) break;
-#pragma unroll
-        for (int u = 0; u < EPI_WARPS / 4 - 1; ++u) {
-          o1[u] = (int)S.xw1[b][u][r];
-          o2[u] = (int)S.xw2[b][u][r];
-          ol[u] = (int)S.xlb[b][u][r];
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&S.xfree[b]);
-      }
-      int g1 = w1, g2 = w2, g3 = lb;
-#pragma unroll
-      for (int u = 0; u < EPI_WARPS / 4 - 1; ++u) top2_merge(g1, g2, o1[u], o2[u]);
-      // every key other than g1, g2 is >= g3: the warps' bounds, and the
-      // warps' top-2 keys that did not make the row's top-2
-      g3 = (w1 != g1 && w1 != g2) ? min(g3, w1) : g3;
-      g3 = (w2 != g1 && w2 != g2) ? min(g3, w2) : g3;
-#pragma unroll
-      for (int u = 0; u < EPI_WARPS / 4 - 1; ++u) {
-        g3 = min(g3, ol[u]);
-        g3 = (o1[u] != g1 && o1[u] != g2) ? min(g3, o1[u]) : g3;
-        g3 = (o2[u] != g1 && o2[u] != g2) ? min(g3, o2[u]) : g3;
-      }
-      const uint32_t p = tile * TM + r;
-      bool flag = false, pair = false;
-      if (p < n) {
-        const float d1 = key_dist(g1), d2 = key_dist(g2), d3 = key_dist(g3);
-        const float xn = sqrtf(nxv);
-        const float e = 2.f * eps_sum * xn * cmax + eps32 * (xn + cmax) * (xn + cmax);
-        // keys under-state a distance by less than 2^-15 of it (2^-14 allowed)
-        const float gap = 2.f * e + 6.103515625e-05f * d1;
-        if (g1 < 0) flag = true;  // a negative smallest distance: re-check
-        else if (d2 - d1 > fmaxf(1e-3f * d1, gap)) assign[p] = g1 & 0xFF;
-        else if (d3 - d1 > gap) pair = true;  // only the top two can be the exact minimum
-        else flag = true;
-      }
-      const unsigned pm = __ballot_sync(0xffffffffu, pair);
-      if (pm) {
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(npairs, (uint32_t)__popc(pm));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (pair)
-          pairs[base + __popc(pm & ((1u << lane) - 1))] =
-              make_uint2(p, ((uint32_t)g1 & 0xFFu) | (((uint32_t)g2 & 0xFFu) << 16));
-      }
-      const unsigned fm = __ballot_sync(0xffffffffu, flag);
-      if (fm) {
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(nlist, (uint32_t)__popc(fm));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (flag) list[base + __popc(fm & ((1u << lane) - 1))] = p;
-      }
+      S.xw1[b][quarter][r] = (uint32_t)w1;
+      S.xw2[b][quarter][r] = (uint32_t)w2;
+      S.xlb[b][quarter][r] = (uint32_t)lb;
+      if (quarter == 0) S.xnx[b][r] = nxv;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.xfull[b]);
     }
   }
   tc_fence_before();
