@@ -1013,6 +1013,140 @@ __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_pipe_kernel(
     if (C[i]) atomicAdd(counts + i, (unsigned long long)C[i]);
 }
 
+// Update step for D = 64 with runs sorted per window (Sec. III-E's array
+// container, privatised per thread block as above, with the shared-memory
+// atomics taken out of the inner loop).  A CTA walks its contiguous range of
+// points in windows of WS_WIN.  For each window it counting-sorts the point
+// indices by cluster in shared memory (a histogram, a scan and a scatter of
+// 16-bit indices), then every warp takes an equal slice of the sorted order
+// and adds its points run by run in registers: lane l reads dimensions 2l
+// and 2l + 1 of each point (one 8-byte load; a warp reads the whole 256-byte
+// row) and keeps q = rint(x 2^s) = hi 2^20 + lo (lq_split) as two 32-bit
+// sums per dimension; when the cluster changes the run is added into the
+// CTA's int64 [k][64] sums with one 64-bit shared-memory add per dimension.
+// A slice holds at most WS_WIN / WS_WARPS points, so no 32-bit run sum can
+// overflow (128 * 2^19 = 2^26).  The CTA stores its sums as its partial and
+// adds its counts to the global counts, like km_local_sum_kernel; the sums are
+// the same integers in any order.  No wait of any kind: only plain loads and
+// block barriers.
+constexpr int WS_THREADS = 1024;
+constexpr int WS_WARPS = WS_THREADS / 32;
+constexpr uint32_t WS_WIN = 4096;  // points per window (16-bit positions)
+constexpr int WS_UNROLL = 8;       // points in flight per warp
+__host__ __device__ constexpr uint64_t ws_smem_bytes(uint64_t k) {
+  return k * 64 * 8 + 3 * k * 4 + 3 * (uint64_t)WS_WIN * 2;
+}
+__device__ __forceinline__ void ws_flush(long long* S, uint32_t c, int lane, int h0, int l0, int h1, int l1) {
+  unsigned long long* p = reinterpret_cast<unsigned long long*>(S + (uint64_t)c * 64 + 2 * lane);
+  atomicAdd(p, (unsigned long long)((long long)h0 * (1ll << 20) + (long long)l0));
+  atomicAdd(p + 1, (unsigned long long)((long long)h1 * (1ll << 20) + (long long)l1));
+}
+__global__ void __launch_bounds__(WS_THREADS, 1) km_window_sum_kernel(const float* __restrict__ x, uint32_t n,
+                                                                      uint32_t k, const int32_t* __restrict__ assign,
+                                                                      const int* shift, long long* __restrict__ part,
+                                                                      unsigned long long* counts) {
+  extern __shared__ __align__(16) unsigned char ws_sm[];
+  long long* S = reinterpret_cast<long long*>(ws_sm);
+  uint32_t* hc = reinterpret_cast<uint32_t*>(S + (uint64_t)k * 64);
+  uint32_t* off = hc + k;
+  uint32_t* C = off + k;
+  uint16_t* wid = reinterpret_cast<uint16_t*>(C + k);
+  uint16_t* perm = wid + WS_WIN;
+  uint16_t* pcl = perm + WS_WIN;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint64_t i = threadIdx.x; i < (uint64_t)k * 64; i += WS_THREADS) S[i] = 0;
+  for (uint32_t i = threadIdx.x; i < k; i += WS_THREADS) C[i] = 0;
+  const uint64_t per = ((uint64_t)n + gridDim.x - 1) / gridDim.x;
+  const uint64_t p0 = (uint64_t)blockIdx.x * per;
+  const uint64_t p1 = p0 + per < (uint64_t)n ? p0 + per : (uint64_t)n;
+  const float scale = ldexpf(1.f, *shift);
+  const uint32_t kl = (k + 31) / 32;  // bins per lane in the scan
+  for (uint64_t w0 = p0; w0 < p1; w0 += WS_WIN) {
+    const uint32_t nr = (uint32_t)(p1 - w0 < WS_WIN ? p1 - w0 : WS_WIN);
+    for (uint32_t t = threadIdx.x; t < k; t += WS_THREADS) hc[t] = 0;
+    __syncthreads();  // hc cleared; the previous window's sorted order is no longer read
+    for (uint32_t r = threadIdx.x; r < nr; r += WS_THREADS) {
+      const uint32_t c = cluster_of(assign, w0 + r, k);
+      wid[r] = (uint16_t)c;
+      atomicAdd(&hc[c], 1u);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      // exclusive scan of the window's cluster sizes (lane l: bins l kl ..)
+      uint32_t tot = 0;
+      for (uint32_t j = 0; j < kl; ++j) {
+        const uint32_t c = (uint32_t)lane * kl + j;
+        if (c < k) tot += hc[c];
+      }
+      uint32_t incl = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      uint32_t run = incl - tot;
+      for (uint32_t j = 0; j < kl; ++j) {
+        const uint32_t c = (uint32_t)lane * kl + j;
+        if (c < k) {
+          const uint32_t h = hc[c];
+          off[c] = run;
+          run += h;
+          C[c] += h;
+        }
+      }
+    }
+    __syncthreads();
+    for (uint32_t r = threadIdx.x; r < nr; r += WS_THREADS) {
+      const uint32_t c = wid[r];
+      const uint32_t pos = atomicAdd(&off[c], 1u);
+      perm[pos] = (uint16_t)r;
+      pcl[pos] = (uint16_t)c;
+    }
+    __syncthreads();
+    // warp slices of the sorted order; runs summed in registers
+    const uint32_t pw = (nr + WS_WARPS - 1) / WS_WARPS;
+    const uint32_t q0 = (uint32_t)warp * pw;
+    const uint32_t q1 = q0 + pw < nr ? q0 + pw : nr;
+    if (q0 < q1) {
+      const float2* X = reinterpret_cast<const float2*>(x + w0 * 64) + lane;
+      uint32_t cur = pcl[q0];
+      int h0 = 0, l0 = 0, h1 = 0, l1 = 0;
+      for (uint32_t q = q0; q < q1; q += WS_UNROLL) {
+        float2 v[WS_UNROLL];
+        uint32_t cl[WS_UNROLL];
+#pragma unroll
+        for (int u = 0; u < WS_UNROLL; ++u) {
+          const uint32_t qq = q + (uint32_t)u;
+          const bool ok = qq < q1;
+          cl[u] = ok ? pcl[qq] : cur;
+          v[u] = ok ? __ldg(X + (uint64_t)perm[qq] * 32) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < WS_UNROLL; ++u) {
+          if (cl[u] != cur) {  // warp-uniform: the run of cluster cur ended
+            ws_flush(S, cur, lane, h0, l0, h1, l1);
+            h0 = l0 = h1 = l1 = 0;
+            cur = cl[u];
+          }
+          int a, b;
+          lq_split(v[u].x * scale, a, b);
+          h0 += a;
+          l0 += b;
+          lq_split(v[u].y * scale, a, b);
+          h1 += a;
+          l1 += b;
+        }
+      }
+      ws_flush(S, cur, lane, h0, l0, h1, l1);
+    }
+  }
+  __syncthreads();
+  long long* P = part + (uint64_t)blockIdx.x * k * 64;
+  for (uint64_t i = threadIdx.x; i < (uint64_t)k * 64; i += WS_THREADS) P[i] = S[i];
+  for (uint32_t i = threadIdx.x; i < k; i += WS_THREADS)
+    if (C[i]) atomicAdd(counts + i, (unsigned long long)C[i]);
+}
+
 // Sum of the g partials of each element (warp w of a CTA adds partials w,
 // w + 8, ... of 32 consecutive elements), then the centroid as in
 // km_finalize_kernel.
@@ -1177,6 +1311,12 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
         return e;
     }
   }
+  // the window-sorted update: D = 64, 8-byte-aligned points, sums and window buffers in shared memory
+  const bool wsum = local && d == 64 && (reinterpret_cast<uintptr_t>(x) & 7) == 0 &&
+                    ws_smem_bytes(k) <= (uint64_t)di.smem_optin;
+  if (wsum && (e = cudaFuncSetAttribute(km_window_sum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)ws_smem_bytes(k))) != cudaSuccess)
+    return e;
   uint32_t ls_grid = (uint32_t)di.sms < LS_MAX_CTAS ? (uint32_t)di.sms : LS_MAX_CTAS;
   if ((uint64_t)ls_grid * 1024 > n) ls_grid = (uint32_t)((n + 1023) / 1024);
   if (b.grid_cap && ls_grid > b.grid_cap) ls_grid = b.grid_cap;
@@ -1220,7 +1360,10 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
     else
       km_recheck_fp64_kernel<<<di.sms * 4, 256, 0, s>>>(x, d, b.cent, k, rl, rn, b.assign, b.stats);
     if (local) {  // update with local arrays
-      if (lp_rows)
+      if (wsum)
+        km_window_sum_kernel<<<ls_grid, WS_THREADS, (int)ws_smem_bytes(k), s>>>(x, n, k, b.assign, shift, b.part,
+                                                                                b.counts);
+      else if (lp_rows)
         (d == 64 ? km_local_sum_pipe_kernel<true> : km_local_sum_pipe_kernel<false>)<<<ls_grid, LS_THREADS, lp_bytes,
                                                                                         s>>>(
             x, n, d, k, b.assign, shift, b.part, b.counts, lp_rows, b.stats + 3, polls);

@@ -56,8 +56,10 @@ def _km_check(mr, ctx, x, init, iters, precision):
 @pytest.mark.parametrize("precision", [0, 1, 2])
 def test_kmeans_wait_gives_up_then_context_recovers(mr, precision):
     """0 polls: the first bounded wait of the pipelined kernels gives up (the
-    tensor-core pass for precision 1 and 2, the bulk-copy update for 0)."""
-    x, _, _ = synth.kmeans_points(12_000, 64, 64, seed=61 + precision)
+    tensor-core pass for precision 1 and 2; for 0 the bulk-copy update, which
+    runs for D other than 64: D = 64 takes the window-sorted update)."""
+    d = 48 if precision == 0 else 64
+    x, _, _ = synth.kmeans_points(12_000, d, 64, seed=61 + precision)
     init = synth.kmeans_init(x, 64, seed=62)
     ctx = mr.Context()
     ctx.set_option(mr.OPT_WAIT_POLLS, 0)
@@ -68,6 +70,18 @@ def test_kmeans_wait_gives_up_then_context_recovers(mr, precision):
     ctx.release(j)
     ctx.set_option(mr.OPT_WAIT_POLLS, mr.OPT_DEFAULT)
     _km_check(mr, ctx, x, init, 2, precision)
+    ctx.close()
+
+
+def test_kmeans_fp32_d64_path_has_no_waits(mr):
+    """The FP32 pass and the window-sorted update (D = 64) wait on nothing, so
+    a wait limit of 0 polls changes nothing there: the job completes and
+    equals the oracle."""
+    x, _, _ = synth.kmeans_points(12_000, 64, 64, seed=64)
+    init = synth.kmeans_init(x, 64, seed=62)
+    ctx = mr.Context()
+    ctx.set_option(mr.OPT_WAIT_POLLS, 0)
+    _km_check(mr, ctx, x, init, 2, 0)
     ctx.close()
 
 

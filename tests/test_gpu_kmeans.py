@@ -59,6 +59,8 @@ def _run_ctx(mr, ctx, dx, cur, iters, precision):
     (3_000, 100, 20, 2),    # D > 64: chunked dimensions
     (4_000, 16, 300, 2),    # K > 256: chunked centroids
     (6_000, 128, 260, 2),   # K*D sums too large for shared memory: the sorted update
+    (9_001, 64, 300, 2),    # window-sorted update with K not a multiple of 32
+    (5_000, 64, 1, 2),      # window-sorted update, one cluster
     (777, 3, 1, 2),         # K = 1: the global mean
     (64, 8, 64, 1),         # every point its own centroid
 ])
@@ -186,6 +188,29 @@ def test_kmeans_many_tiles_per_cta_teacher_forced(mr, precision):
         assert np.array_equal(a, a_ref)
         assert _rel_err(c, c_ref) <= TOL
         assert int(st[3]) == 0
+        cur = c_ref
+    ctx.close()
+
+
+@pytest.mark.parametrize("k", [256, 17])
+def test_kmeans_window_update_many_windows(mr, k):
+    """The D = 64 update sorts each window of 4,096 points by cluster and sums
+    runs in registers.  Two CTAs: each walks two full windows and a ragged
+    third (10,001 points each), so the window loop, the per-window histogram
+    and scatter and the run flushes across windows are all exercised, against
+    the oracle's update from the same assignment."""
+    import torch
+    x, _, _ = synth.kmeans_points(20_002, 64, min(k, 64), seed=71 + k)
+    dx = torch.from_numpy(x).cuda()
+    cur = synth.kmeans_init(x, k, seed=72)
+    ctx = mr.Context()
+    ctx.set_option(mr.OPT_KM_GRID_CAP, 2)
+    for _ in range(2):
+        a_ref = oracle.kmeans_assign(x, cur)
+        c_ref, _ = oracle.kmeans_update(x, a_ref, cur)
+        c, a, st = _run_ctx(mr, ctx, dx, cur, 1, 0)
+        assert np.array_equal(a, a_ref)
+        assert _rel_err(c, c_ref) <= TOL
         cur = c_ref
     ctx.close()
 
