@@ -457,13 +457,18 @@ __device__ inline void warp_segment_t(const JobDev& J, uint64_t seg, WarpLocal& 
 // the token goes on as a miss.  A key may end up in two slots (two lanes
 // claiming it at once); both counts reach the global container, which
 // merges them.
-constexpr int CT_SLOTS = 2048;
 constexpr unsigned long long CT_BUSY = 1ull;  // no key has w1 == 1 (its length byte is >= 1)
-struct CtaTable {
-  ulonglong2 key[CT_SLOTS];  // {w0, w1}
-  uint32_t h[CT_SLOTS];
-  uint32_t cnt[CT_SLOTS];
+template <int NS>
+struct CtaTableT {
+  static constexpr int SLOTS = NS;  // a power of two
+  ulonglong2 key[NS];  // {w0, w1}
+  uint32_t h[NS];
+  uint32_t cnt[NS];
 };
+// the batch kernel's table (two CTAs per SM); the plain map kernel's
+// (one CTA of 32 warps per SM) is twice as large
+using CtaTable = CtaTableT<2048>;
+using CtaTableBig = CtaTableT<4096>;
 
 // Per-warp state of the plain map kernel: the staged segment, its
 // whitespace bitmap and token list, and a queue of the tokens the table did
@@ -481,12 +486,13 @@ static_assert(sizeof(CtaTable) % 16 == 0 && sizeof(MapWarp) % 16 == 0, "staging 
 
 // Count one short token in the CTA table; false if neither of its two
 // slots holds it or could be claimed for it (and for every long token).
-__device__ __forceinline__ bool cta_add(CtaTable& T, const Tok& t) {
+template <class TT>
+__device__ __forceinline__ bool cta_add(TT& T, const Tok& t) {
   if ((t.w1 >> 56) == 0xFF || t.w0 == 0) return false;
-  const uint32_t s0 = t.h & (CT_SLOTS - 1);
+  const uint32_t s0 = t.h & (TT::SLOTS - 1);
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
-    const uint32_t s = (s0 + p) & (CT_SLOTS - 1);
+    const uint32_t s = (s0 + p) & (TT::SLOTS - 1);
     unsigned long long k0, k1;
     asm volatile("ld.volatile.shared::cta.v2.u64 {%0, %1}, [%2];"
                  : "=l"(k0), "=l"(k1)

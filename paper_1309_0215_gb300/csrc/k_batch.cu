@@ -198,7 +198,7 @@ batch_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs, uint64_t total_t
       }
       qn = qhd = 0;
       __syncthreads();
-      for (int i = threadIdx.x; i < wc::CT_SLOTS; i += BT) {
+      for (int i = threadIdx.x; i < wc::CtaTable::SLOTS; i += BT) {
         const ulonglong2 k = T.key[i];
         if (k.y != 0) wc::global_insert(s_jd, k.x, k.y, T.h[i], T.cnt[i]);
       }
@@ -213,7 +213,7 @@ batch_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs, uint64_t total_t
       __syncthreads();
     } else if (kind == MR_WORDCOUNT) {
       if (threadIdx.x == 0) s_jd = J.wc;
-      for (int i = threadIdx.x; i < wc::CT_SLOTS; i += BT) T.key[i] = make_ulonglong2(0ull, 0ull);
+      for (int i = threadIdx.x; i < wc::CtaTable::SLOTS; i += BT) T.key[i] = make_ulonglong2(0ull, 0ull);
       qn = qhd = 0;
       __syncthreads();
     }

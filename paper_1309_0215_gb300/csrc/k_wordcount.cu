@@ -51,12 +51,12 @@ using wc::WarpLocal;
 
 constexpr int MAP_WARPS = 8;                 // per-warp-cache map kernel: 5 CTAs per SM
 constexpr int MAP_THREADS = MAP_WARPS * 32;
-constexpr int CTA_WARPS = 16;               // CTA-table map kernel: 2 CTAs per SM
+constexpr int CTA_WARPS = 32;               // CTA-table map kernel: 1 CTA per SM
 constexpr int CTA_THREADS = CTA_WARPS * 32;
 // From this input size on the plain map pass uses the CTA-table kernel for a
 // 16-byte-aligned input (whose next segment each warp loads ahead): each CTA
 // then sees enough tokens (tens of thousands) that its table pays for its
-// final merge of up to CT_SLOTS keys into the global container.
+// final merge of up to 4,096 keys into the global container.
 constexpr uint64_t CTA_MAP_MIN_BYTES = 64ull << 20;
 constexpr int CB = 1024;            // records per compaction / sort / scan block
 constexpr uint64_t CNT_MAX = (1ull << 40) - 1;
@@ -81,17 +81,17 @@ __global__ void __launch_bounds__(MAP_THREADS, 5) wc_map_kernel(JobDev J) {
   wc::local_flush<1>(L, occ, J);
 }
 
-// Plain map + combine pass for large inputs: CTAs of CTA_WARPS warps, two per
-// SM, sharing one local table per CTA (wc::CtaTable); a warp's misses are
-// queued and sent to the global container 32 at a time; at the end every
-// warp empties its queue and the CTA merges its table into the global
-// container.
-__global__ void __launch_bounds__(CTA_THREADS, 2) wc_map_cta_kernel(JobDev J) {
+// Plain map + combine pass for large inputs: one CTA of CTA_WARPS warps per
+// SM, sharing one local table (wc::CtaTableBig, 4,096 slots); a warp's
+// misses are queued and sent to the global container 32 at a time; at the
+// end every warp empties its queue and the CTA merges its table into the
+// global container.
+__global__ void __launch_bounds__(CTA_THREADS, 1) wc_map_cta_kernel(JobDev J) {
   extern __shared__ __align__(16) unsigned char wc_smem[];
-  wc::CtaTable& T = *reinterpret_cast<wc::CtaTable*>(wc_smem);
-  wc::MapWarp& W = reinterpret_cast<wc::MapWarp*>(wc_smem + sizeof(wc::CtaTable))[threadIdx.x >> 5];
+  wc::CtaTableBig& T = *reinterpret_cast<wc::CtaTableBig*>(wc_smem);
+  wc::MapWarp& W = reinterpret_cast<wc::MapWarp*>(wc_smem + sizeof(wc::CtaTableBig))[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
-  for (int i = threadIdx.x; i < wc::CT_SLOTS; i += CTA_THREADS) T.key[i] = make_ulonglong2(0ull, 0ull);
+  for (int i = threadIdx.x; i < wc::CtaTableBig::SLOTS; i += CTA_THREADS) T.key[i] = make_ulonglong2(0ull, 0ull);
   __syncthreads();
   const uint64_t nseg = (J.n + wc::SEG - 1) / wc::SEG;
   const uint64_t gw = (uint64_t)blockIdx.x * CTA_WARPS + (threadIdx.x >> 5);
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 2) wc_map_cta_kernel(JobDev J) {
     wc::global_insert(J, W.qw0[q], W.qw1[q], W.qh[q], 1);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < wc::CT_SLOTS; i += CTA_THREADS) {
+  for (int i = threadIdx.x; i < wc::CtaTableBig::SLOTS; i += CTA_THREADS) {
     const ulonglong2 k = T.key[i];
     if (k.y != 0) wc::global_insert(J, k.x, k.y, T.h[i], T.cnt[i]);
   }
@@ -2030,7 +2030,7 @@ uint64_t wc_out_bytes(uint64_t cap, uint64_t n) {
 }
 
 int wc_map_smem_bytes() { return MAP_WARPS * (int)sizeof(WarpLocal); }
-static int wc_map_cta_smem_bytes() { return (int)(sizeof(wc::CtaTable) + CTA_WARPS * sizeof(wc::MapWarp)); }
+static int wc_map_cta_smem_bytes() { return (int)(sizeof(wc::CtaTableBig) + CTA_WARPS * sizeof(wc::MapWarp)); }
 
 wc::JobDev wc_job_dev(const uint8_t* in, uint64_t n, const WcBuffers& b, uint64_t blk0) {
   JobDev J;
@@ -2198,7 +2198,7 @@ cudaError_t launch_wordcount(const uint8_t* in, uint64_t n, const WcBuffers& b, 
       return e;
     const uint64_t nseg = (n + wc::SEG - 1) / wc::SEG;
     uint64_t grid = (nseg + CTA_WARPS - 1) / CTA_WARPS;
-    const uint64_t gmax = 2ull * di.sms;
+    const uint64_t gmax = (uint64_t)di.sms;
     if (grid > gmax) grid = gmax;
     if ((e = kt_begin(kt, s)) != cudaSuccess) return e;
     wc_map_cta_kernel<<<(unsigned)grid, CTA_THREADS, smem, s>>>(J);
