@@ -465,9 +465,8 @@ struct CtaTableT {
   uint32_t h[NS];
   uint32_t cnt[NS];
 };
-// the batch kernel's table (two CTAs per SM); the plain map kernel's
-// (one CTA of 32 warps per SM) is twice as large
-using CtaTable = CtaTableT<2048>;
+// the table of the large-input map kernel and the batch kernel (one CTA of
+// 32 warps per SM)
 using CtaTableBig = CtaTableT<4096>;
 
 // Per-warp state of the plain map kernel: the staged segment, its
@@ -482,7 +481,7 @@ struct MapWarp {
   unsigned long long qw0[MQ], qw1[MQ];
   uint32_t qh[MQ];
 };
-static_assert(sizeof(CtaTable) % 16 == 0 && sizeof(MapWarp) % 16 == 0, "staging buffers must stay 16-byte aligned");
+static_assert(sizeof(CtaTableBig) % 16 == 0 && sizeof(MapWarp) % 16 == 0, "staging buffers must stay 16-byte aligned");
 
 // Count one short token in the CTA table; false if neither of its two
 // slots holds it or could be claimed for it (and for every long token).

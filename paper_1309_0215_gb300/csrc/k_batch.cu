@@ -4,12 +4,12 @@
 // Every pending histogram / regression / word-count job is cut into fixed
 // tiles (array jobs: a multiple of 1536 bytes; word count: a multiple of the
 // 512-byte segment), and the tiles of all jobs are laid end to end in one
-// tile space.  Persistent CTAs (two per SM) pull tile indices from a global
+// tile space.  Persistent CTAs (one per SM) pull tile indices from a global
 // atomic cursor, so large and small jobs share the GPU without per-job launch
 // or tail costs.  A CTA keeps the local container of the job it is working on
 // (the paper's combiner, Sec. III-A) across consecutive tiles of that job —
 // lane-column shared-memory arrays for a histogram, registers for the
-// regression sums, per-warp shared-memory hash tables for word count — and
+// regression sums, a CTA-shared hash table for word count — and
 // merges it into the job's global container when it moves to a tile of
 // another job and at the end.  The word-count jobs' merge and sort then run
 // once for all of them (k_wordcount.cu, sort keyed by job).
@@ -23,19 +23,18 @@
 namespace mrgb {
 namespace {
 
-// 16 warps per CTA, two CTAs per SM: the large-input word-count map
-// kernel's shape.  A word-count tile runs as in that kernel: one local table
-// per CTA shared by its warps (wc::CtaTable), each warp's misses queued and
+// 32 warps per CTA, one CTA per SM: the large-input word-count map kernel's
+// shape.  A word-count tile runs as in that kernel: one local table per CTA
+// shared by its warps (wc::CtaTableBig), each warp's misses queued and
 // inserted 32 at a time, each warp's next segment loaded ahead.  Histogram
-// tiles use 16 lane columns (lane % 16) per bin, 48 KiB, so lanes 16 apart
-// share a column (a few more shared-memory atomic collisions on equal bins).
-constexpr int BT = 512;
+// tiles use 32 lane columns per bin (96 KiB), as the plain histogram kernel.
+constexpr int BT = 1024;
 constexpr int BWARPS = BT / 32;
-constexpr int BCTAS = 2;                 // CTAs per SM
-constexpr int BH_COLS = 16;              // histogram lane columns per bin
+constexpr int BCTAS = 1;                 // CTAs per SM
+constexpr int BH_COLS = 32;              // histogram lane columns per bin
 constexpr int BH_WORDS = arr::HIST_BINS * BH_COLS;
 constexpr int B_SMEM_HIST = BH_WORDS * 4;
-constexpr int B_SMEM_WC = (int)(sizeof(wc::CtaTable) + BWARPS * sizeof(wc::MapWarp));
+constexpr int B_SMEM_WC = (int)(sizeof(wc::CtaTableBig) + BWARPS * sizeof(wc::MapWarp));
 constexpr int B_SMEM = B_SMEM_HIST > B_SMEM_WC ? B_SMEM_HIST : B_SMEM_WC;
 static_assert(BCTAS * (B_SMEM + 1024) + 4096 <= 232448, "BCTAS batch CTAs must fit one SM's shared memory");
 
@@ -169,8 +168,8 @@ batch_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs, uint64_t total_t
   __shared__ long long part[BWARPS][5];
   __shared__ wc::JobDev s_jd;  // the current word-count job
   uint32_t* hs = reinterpret_cast<uint32_t*>(bsm);
-  wc::CtaTable& T = *reinterpret_cast<wc::CtaTable*>(bsm);
-  wc::MapWarp& W = reinterpret_cast<wc::MapWarp*>(bsm + sizeof(wc::CtaTable))[threadIdx.x >> 5];
+  wc::CtaTableBig& T = *reinterpret_cast<wc::CtaTableBig*>(bsm);
+  wc::MapWarp& W = reinterpret_cast<wc::MapWarp*>(bsm + sizeof(wc::CtaTableBig))[threadIdx.x >> 5];
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(hs);
   const int lane = threadIdx.x & 31;
   int64_t cur = -1;
@@ -198,7 +197,7 @@ batch_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs, uint64_t total_t
       }
       qn = qhd = 0;
       __syncthreads();
-      for (int i = threadIdx.x; i < wc::CtaTable::SLOTS; i += BT) {
+      for (int i = threadIdx.x; i < wc::CtaTableBig::SLOTS; i += BT) {
         const ulonglong2 k = T.key[i];
         if (k.y != 0) wc::global_insert(s_jd, k.x, k.y, T.h[i], T.cnt[i]);
       }
@@ -213,7 +212,7 @@ batch_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs, uint64_t total_t
       __syncthreads();
     } else if (kind == MR_WORDCOUNT) {
       if (threadIdx.x == 0) s_jd = J.wc;
-      for (int i = threadIdx.x; i < wc::CtaTable::SLOTS; i += BT) T.key[i] = make_ulonglong2(0ull, 0ull);
+      for (int i = threadIdx.x; i < wc::CtaTableBig::SLOTS; i += BT) T.key[i] = make_ulonglong2(0ull, 0ull);
       qn = qhd = 0;
       __syncthreads();
     }
