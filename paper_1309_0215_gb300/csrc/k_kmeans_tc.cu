@@ -23,7 +23,7 @@
 //     with its column into one sortable 32-bit key and keep the two smallest
 //     keys with signed min/max (four independent top-2s per thread) plus
 //     a lower bound of all other keys, and hand them to
-//   * 4 finalizer warps (one per lane quadrant), which merge the four
+//   * 2 finalizer warps (two lane quadrants each), which merge the four
 //     column quarters of each point and apply the margin tests below, so
 //     that no epilogue warp carries the per-point tail on its own path.
 // Copies, converters, MMA issue, epilogue and finalizers overlap through the
@@ -62,11 +62,14 @@ constexpr int QUARTERS = EPI_WARPS / 4;
 constexpr int EPI_COLS = NMAX / QUARTERS;  // 64 columns per epilogue warp
 constexpr int MMA_WARP = EPI_WARPS;
 constexpr int CVT_WARP0 = MMA_WARP + 1;
-constexpr int CVT_WARPS = 4;      // each converts 32 rows of a tile
+constexpr int CVT_WARPS = 8;      // each converts TM / CVT_WARPS rows of a tile
+constexpr int CVT_ROWS = TM / CVT_WARPS;
 constexpr int FIN_WARP0 = CVT_WARP0 + CVT_WARPS;
-constexpr int FIN_WARPS = 4;      // one per TMEM lane quadrant: 32 points each
-constexpr int TMA_WARP = FIN_WARP0 + FIN_WARPS;  // 25
-constexpr int TC_THREADS = (EPI_WARPS + 1 + CVT_WARPS + FIN_WARPS + 1) * 32;  // 832
+constexpr int FIN_WARPS = 2;      // each finalizes 4 / FIN_WARPS TMEM lane quadrants (32 points each)
+constexpr int FIN_QUADS = 4 / FIN_WARPS;
+constexpr int TMA_WARP = FIN_WARP0 + FIN_WARPS;  // 27
+constexpr int TC_THREADS = (EPI_WARPS + 1 + CVT_WARPS + FIN_WARPS + 1) * 32;  // 896
+static_assert(CVT_ROWS % 16 == 0 && 4 % FIN_WARPS == 0, "converter rows and finalizer quadrants");
 constexpr int STAGES = 2;         // operand stages
 constexpr int XST = 2;            // FP32 staging buffers filled by the bulk copy engine
 constexpr int ACCS = 2;           // TMEM accumulators
@@ -273,8 +276,8 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
 
   if (warp >= CVT_WARP0 && warp < CVT_WARP0 + CVT_WARPS) {
     // ---------------------------------------------------------- converters
-    // Warp cw owns tile rows 32 cw .. 32 cw + 31, in two halves of 16.  Step
-    // q of half hf gives lane l row 32 cw + 16 hf + 2q + l / 16 and dims
+    // Warp cw owns tile rows CVT_ROWS cw .., in parts of 16.  Step q of part
+    // hf gives lane l row CVT_ROWS cw + 16 hf + 2q + l / 16 and dims
     // 4 (l % 16) .. + 3, so one warp load reads two whole FP32 rows (512
     // contiguous bytes) and one warp store writes two whole 128-byte
     // swizzled BF16 rows: no shared-memory bank conflicts.
@@ -293,8 +296,8 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
         if (!__all_sync(0xffffffffu, okt)) break;
       }
       bool ok = true;
-      for (int hf = 0; hf < 2; ++hf) {
-        const int r0 = 32 * cw + 16 * hf;
+      for (int hf = 0; hf < CVT_ROWS / 16; ++hf) {
+        const int r0 = CVT_ROWS * cw + 16 * hf;
         float4 v[8];
         if (vec) {
 #pragma unroll
@@ -415,11 +418,11 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
     __syncwarp();
   } else if (warp >= FIN_WARP0 && warp < FIN_WARP0 + FIN_WARPS) {
     // ------------------------------------------------------------ finalizers
-    // Warp f takes the points of TMEM lane quadrant f (rows 32 f + lane): it
-    // merges the four column quarters' top-2 keys into the row's exact top-2
-    // (g1, g2) and a lower bound g3 of every other key, then applies the
-    // margin tests.
-    const int r = (warp - FIN_WARP0) * 32 + lane;
+    // Warp f takes the points of TMEM lane quadrants FIN_QUADS f .. (rows
+    // 32 q + lane of each): it merges the four column quarters' top-2 keys
+    // into the row's exact top-2 (g1, g2) and a lower bound g3 of every other
+    // key, then applies the margin tests.
+    const int fw = warp - FIN_WARP0;
     const float eps_sum = TERMS == 3 ? (3.05f * 1.52587890625e-05f + (float)(3 * KD + 8) * 4.76837158203125e-07f)
                                      : (2.f * 3.90625e-03f + 1.52587890625e-05f + (float)(KD + 8) * 4.76837158203125e-07f);
     const float eps32 = 1.01f * (float)(d + 8) * 5.9604644775390625e-08f;
@@ -430,55 +433,63 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
       const uint32_t v = i >> 1;
       const bool okx = mbar_wait(&S.xfull[b], v & 1, err, polls);
       if (!__all_sync(0xffffffffu, okx)) break;
-      int o1[QUARTERS], o2[QUARTERS], ol[QUARTERS];
+      int o1[FIN_QUADS][QUARTERS], o2[FIN_QUADS][QUARTERS], ol[FIN_QUADS][QUARTERS];
+      float nxv[FIN_QUADS];
 #pragma unroll
-      for (int u = 0; u < QUARTERS; ++u) {
-        o1[u] = (int)S.xw1[b][u][r];
-        o2[u] = (int)S.xw2[b][u][r];
-        ol[u] = (int)S.xlb[b][u][r];
+      for (int h = 0; h < FIN_QUADS; ++h) {
+        const int r = (fw * FIN_QUADS + h) * 32 + lane;
+#pragma unroll
+        for (int u = 0; u < QUARTERS; ++u) {
+          o1[h][u] = (int)S.xw1[b][u][r];
+          o2[h][u] = (int)S.xw2[b][u][r];
+          ol[h][u] = (int)S.xlb[b][u][r];
+        }
+        nxv[h] = S.xnx[b][r];
       }
-      const float nxv = S.xnx[b][r];
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.xfree[b]);
-      int g1 = o1[0], g2 = o2[0], g3 = ol[0];
 #pragma unroll
-      for (int u = 1; u < QUARTERS; ++u) top2_merge(g1, g2, o1[u], o2[u]);
-      // every key other than g1, g2 is >= g3: the quarters' bounds, and the
-      // quarters' top-2 keys that did not make the row's top-2
+      for (int h = 0; h < FIN_QUADS; ++h) {
+        int g1 = o1[h][0], g2 = o2[h][0], g3 = ol[h][0];
 #pragma unroll
-      for (int u = 0; u < QUARTERS; ++u) {
-        g3 = min(g3, ol[u]);
-        g3 = (o1[u] != g1 && o1[u] != g2) ? min(g3, o1[u]) : g3;
-        g3 = (o2[u] != g1 && o2[u] != g2) ? min(g3, o2[u]) : g3;
-      }
-      const uint32_t p = tile * TM + r;
-      bool flag = false, pair = false;
-      if (p < n) {
-        const float d1 = key_dist(g1), d2 = key_dist(g2), d3 = key_dist(g3);
-        const float xn = sqrtf(nxv);
-        const float e = 2.f * eps_sum * xn * cmax + eps32 * (xn + cmax) * (xn + cmax);
-        // keys under-state a distance by less than 2^-15 of it (2^-14 allowed)
-        const float gap = 2.f * e + 6.103515625e-05f * d1;
-        if (g1 < 0) flag = true;  // a negative smallest distance: re-check
-        else if (d2 - d1 > fmaxf(1e-3f * d1, gap)) assign[p] = g1 & 0xFF;
-        else if (d3 - d1 > gap) pair = true;  // only the top two can be the exact minimum
-        else flag = true;
-      }
-      const unsigned pm = __ballot_sync(0xffffffffu, pair);
-      if (pm) {
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(npairs, (uint32_t)__popc(pm));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (pair)
-          pairs[base + __popc(pm & ((1u << lane) - 1))] =
-              make_uint2(p, ((uint32_t)g1 & 0xFFu) | (((uint32_t)g2 & 0xFFu) << 16));
-      }
-      const unsigned fm = __ballot_sync(0xffffffffu, flag);
-      if (fm) {
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(nlist, (uint32_t)__popc(fm));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (flag) list[base + __popc(fm & ((1u << lane) - 1))] = p;
+        for (int u = 1; u < QUARTERS; ++u) top2_merge(g1, g2, o1[h][u], o2[h][u]);
+        // every key other than g1, g2 is >= g3: the quarters' bounds, and the
+        // quarters' top-2 keys that did not make the row's top-2
+#pragma unroll
+        for (int u = 0; u < QUARTERS; ++u) {
+          g3 = min(g3, ol[h][u]);
+          g3 = (o1[h][u] != g1 && o1[h][u] != g2) ? min(g3, o1[h][u]) : g3;
+          g3 = (o2[h][u] != g1 && o2[h][u] != g2) ? min(g3, o2[h][u]) : g3;
+        }
+        const uint32_t p = tile * TM + (uint32_t)((fw * FIN_QUADS + h) * 32 + lane);
+        bool flag = false, pair = false;
+        if (p < n) {
+          const float d1 = key_dist(g1), d2 = key_dist(g2), d3 = key_dist(g3);
+          const float xn = sqrtf(nxv[h]);
+          const float e = 2.f * eps_sum * xn * cmax + eps32 * (xn + cmax) * (xn + cmax);
+          // keys under-state a distance by less than 2^-15 of it (2^-14 allowed)
+          const float gap = 2.f * e + 6.103515625e-05f * d1;
+          if (g1 < 0) flag = true;  // a negative smallest distance: re-check
+          else if (d2 - d1 > fmaxf(1e-3f * d1, gap)) assign[p] = g1 & 0xFF;
+          else if (d3 - d1 > gap) pair = true;  // only the top two can be the exact minimum
+          else flag = true;
+        }
+        const unsigned pm = __ballot_sync(0xffffffffu, pair);
+        if (pm) {
+          uint32_t base = 0;
+          if (lane == 0) base = atomicAdd(npairs, (uint32_t)__popc(pm));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (pair)
+            pairs[base + __popc(pm & ((1u << lane) - 1))] =
+                make_uint2(p, ((uint32_t)g1 & 0xFFu) | (((uint32_t)g2 & 0xFFu) << 16));
+        }
+        const unsigned fm = __ballot_sync(0xffffffffu, flag);
+        if (fm) {
+          uint32_t base = 0;
+          if (lane == 0) base = atomicAdd(nlist, (uint32_t)__popc(fm));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (flag) list[base + __popc(fm & ((1u << lane) - 1))] = p;
+        }
       }
     }
   } else {
