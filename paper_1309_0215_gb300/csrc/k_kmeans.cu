@@ -119,6 +119,7 @@ __global__ void km_prep_kernel(const float* __restrict__ c, uint32_t k, uint32_t
   for (uint64_t i = tid; i < (uint64_t)k; i += nth) counts[i] = 0;
   if (tid < 2) nflag[tid] = 0;
   if (tid == 2) nflag[4] = 0;  // pair list
+  if (tid == 3) nflag[5] = 0;  // FP64 stage list
 }
 
 // FP32 assignment.  A CTA processes tiles of 64 points; warp w owns points
@@ -313,18 +314,6 @@ km_assign_fp32_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const
   }
 }
 
-// Exact FP64 choice between the two candidates of each listed point (the
-// definition's operation order: dimensions in order, separately rounded
-// subtract, multiply and add); the lower index wins an exact tie.
-__device__ __forceinline__ double dist64(const float* __restrict__ xp, const float* __restrict__ cp, uint32_t d) {
-  double s = 0.0;
-  for (uint32_t j = 0; j < d; ++j) {
-    const double t = __dsub_rn((double)xp[j], (double)cp[j]);
-    s = __dadd_rn(s, __dmul_rn(t, t));
-  }
-  return s;
-}
-
 __device__ __forceinline__ float warp_dist32(const float* __restrict__ xp, const float* __restrict__ cp, uint32_t d,
                                              int lane) {
   float s = 0.f;
@@ -342,12 +331,14 @@ __device__ __forceinline__ float warp_dist32(const float* __restrict__ xp, const
 // both centroid rows, so a warp has four points' rows in flight at once.
 // FP32 direct differences first: their relative error is at most g for any
 // summation order (as in the re-check below), so a ratio beyond widen
-// decides the exact order; only closer pairs (and NaNs) take the FP64
-// definition, evaluated by the group's first lane.  stat[0] counts the
-// pairs, stat[1] those that needed FP64.
+// decides the exact order; closer pairs (and NaNs) are appended to the FP64
+// stage's list (deferred, ndef), which km_fp64_stage_kernel then settles
+// with all such points in parallel (the FP64 pipe of this GPU is narrow:
+// done here, a few such points kept a few SMs busy long after the rest had
+// finished).  stat[0] counts the pairs.
 __global__ void km_pair_kernel(const float* __restrict__ x, uint32_t d, const float* __restrict__ c,
                                const uint2* __restrict__ pairs, const uint32_t* npairs, int32_t* assign,
-                               unsigned long long* stat) {
+                               unsigned long long* stat, uint32_t* deferred, uint32_t* ndef) {
   const uint32_t np = *npairs;
   const int lane = threadIdx.x & 31, grp = lane >> 3, sl = lane & 7;
   const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -355,7 +346,6 @@ __global__ void km_pair_kernel(const float* __restrict__ x, uint32_t d, const fl
   if (w0 == 0 && lane == 0 && stat) atomicAdd(stat, (unsigned long long)np);
   const float g = 1.01f * (float)(d + 8) * 5.9604644775390625e-08f;
   const float widen = (1.f + g) / (1.f - g) * (1.f + 4.f * 5.9604644775390625e-08f);
-  uint32_t n64 = 0;
   for (uint64_t f0 = 4 * w0; f0 < np; f0 += 4 * nw) {
     const uint64_t f = f0 + (uint64_t)grp;
     const bool live = f < np;
@@ -378,23 +368,10 @@ __global__ void km_pair_kernel(const float* __restrict__ x, uint32_t d, const fl
       f2 += __shfl_xor_sync(0xffffffffu, f2, o);
     }
     if (live && sl == 0) {
-      int32_t w;
-      if (f2 > f1 * widen) {
-        w = (int32_t)k1;
-      } else if (f1 > f2 * widen) {
-        w = (int32_t)k2;
-      } else {
-        const double s1 = dist64(xp, c1, d);
-        const double s2 = dist64(xp, c2, d);
-        w = (s2 < s1 || (s2 == s1 && k2 < k1)) ? (int32_t)k2 : (int32_t)k1;
-        ++n64;
-      }
-      assign[e.x] = w;
+      if (f2 > f1 * widen) assign[e.x] = (int32_t)k1;
+      else if (f1 > f2 * widen) assign[e.x] = (int32_t)k2;
+      else deferred[atomicAdd(ndef, 1u)] = e.x;
     }
-  }
-  if (stat) {
-    n64 = __reduce_add_sync(0xffffffffu, n64);
-    if (lane == 0 && n64) atomicAdd(stat + 1, (unsigned long long)n64);
   }
 }
 
@@ -457,17 +434,19 @@ __global__ void km_recheck_fp64_kernel(const float* __restrict__ x, uint32_t d, 
 // The same re-check with the centroids staged in shared memory (row stride
 // D + 1 floats: lanes reading different rows at one column hit different
 // banks).  Lane l owns centroids l, l+32, ... (at most KLANE of them): one
-// pass computes their FP32 distances into registers, the warp takes the
-// minimum, and each lane evaluates in FP64 only its own candidates.
+// pass computes their FP32 distances into registers and the warp takes the
+// minimum; a point with more than one candidate within the bound goes to
+// the FP64 stage's list (deferred, ndef).
 constexpr int KLANE = 8;  // K <= 256
 // Points are handed out in contiguous ranges of at least RC_MIN per CTA, so
 // only as many CTAs stage the centroids as there is work for (the lists are
 // a few thousand points).  stat[0] counts the listed points (all checked in
-// FP32), stat[1] those that needed FP64.
+// FP32).
 constexpr uint32_t RC_MIN = 64;
 __global__ void km_recheck_fp64_smem_kernel(const float* __restrict__ x, uint32_t d, const float* __restrict__ c,
                                             uint32_t k, const uint32_t* flagged, const uint32_t* nflag,
-                                            int32_t* assign, unsigned long long* stat) {
+                                            int32_t* assign, unsigned long long* stat, uint32_t* deferred,
+                                            uint32_t* ndef) {
   extern __shared__ float cs[];  // [k][d + 1]
   const uint32_t nf = *nflag;
   const uint32_t per = max(RC_MIN, (nf + gridDim.x - 1) / gridDim.x);
@@ -482,7 +461,6 @@ __global__ void km_recheck_fp64_smem_kernel(const float* __restrict__ x, uint32_
   const uint32_t wpb = blockDim.x >> 5;
   const float g = 1.01f * (float)(d + 8) * 5.9604644775390625e-08f;
   const float widen = (1.f + g) / (1.f - g) * (1.f + 4.f * 5.9604644775390625e-08f);
-  uint32_t n64 = 0;
   for (uint64_t f = f_lo + (threadIdx.x >> 5); f < f_hi; f += wpb) {
     const uint32_t p = flagged[f];
     const float* xp = x + (uint64_t)p * d;
@@ -518,31 +496,109 @@ __global__ void km_recheck_fp64_smem_kernel(const float* __restrict__ x, uint32_
     }
     if (ncand == 1) {
       if (first >= 0) assign[p] = first;
-      continue;
+    } else if (lane == 0) {
+      deferred[atomicAdd(ndef, 1u)] = p;
     }
-    ++n64;
+  }
+}
+
+// The FP64 stage: the exact argmin of each point the pair and re-check passes
+// deferred, one CTA per point (all of them at once: there are tens to a few
+// hundred per iteration).  FP32 direct differences to every centroid (one
+// thread per centroid), the block minimum, the candidates within the
+// relative bound of it; then the definition in FP64 for the candidates only:
+// the products (x_j - c_j)^2, separately rounded, for all dimensions of a
+// chunk of candidates at once, and one thread per candidate adding them with
+// the dimensions in order, so the FP64 pipe (narrow on this GPU) runs 2
+// instructions per (candidate, dimension) spread over the block and one
+// dependent chain of D adds per chunk.  The lowest index wins an exact tie;
+// all-NaN distances give index 0, as the definition.  stat[1] counts the points.
+constexpr int F64_THREADS = 256;
+constexpr uint32_t F64_PROD = 8192;  // doubles of product scratch
+inline size_t fp64_stage_smem(uint32_t d, uint32_t k) {
+  return (size_t)F64_PROD * 8 + (size_t)d * 4 + (size_t)k * 8 + 64;
+}
+__global__ void __launch_bounds__(F64_THREADS) km_fp64_stage_kernel(const float* __restrict__ x, uint32_t d,
+                                                                    const float* __restrict__ c, uint32_t k,
+                                                                    const uint32_t* list, const uint32_t* nlist,
+                                                                    int32_t* assign, unsigned long long* stat) {
+  extern __shared__ __align__(16) unsigned char f64_sm[];
+  double* prod = reinterpret_cast<double*>(f64_sm);   // [cc][d]
+  float* xs = reinterpret_cast<float*>(prod + F64_PROD);  // [d]
+  float* dist = xs + d;                               // [k]
+  uint32_t* cand = reinterpret_cast<uint32_t*>(dist + k);  // [k]
+  __shared__ float red_f[F64_THREADS / 32];
+  __shared__ double red_d[F64_THREADS / 32];
+  __shared__ int red_k[F64_THREADS / 32];
+  __shared__ uint32_t ncand;
+  const uint32_t nf = *nlist;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && stat) atomicAdd(stat + 1, (unsigned long long)nf);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float g = 1.01f * (float)(d + 8) * 5.9604644775390625e-08f;
+  const float widen = (1.f + g) / (1.f - g) * (1.f + 4.f * 5.9604644775390625e-08f);
+  // candidates per product chunk (d <= 1024: at least 8), one summing thread each
+  const uint32_t cc = F64_PROD / d < (uint32_t)F64_THREADS ? F64_PROD / d : (uint32_t)F64_THREADS;
+  for (uint32_t f = blockIdx.x; f < nf; f += gridDim.x) {
+    const uint32_t p = list[f];
+    const float* xp = x + (uint64_t)p * d;
+    __syncthreads();  // the previous point's use of the shared arrays is over
+    for (uint32_t j = threadIdx.x; j < d; j += F64_THREADS) xs[j] = xp[j];
+    if (threadIdx.x == 0) ncand = 0;
+    __syncthreads();
+    float m = INFINITY;
+    for (uint32_t kk = threadIdx.x; kk < k; kk += F64_THREADS) {
+      const float* cp = c + (uint64_t)kk * d;
+      float s32 = 0.f;
+      for (uint32_t j = 0; j < d; ++j) {
+        const float t = xs[j] - __ldg(cp + j);
+        s32 = fmaf(t, t, s32);
+      }
+      dist[kk] = s32;
+      m = fminf(m, s32);
+    }
+    for (int o = 16; o; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) red_f[warp] = m;
+    __syncthreads();
+    float m32 = red_f[0];
+    for (int w = 1; w < F64_THREADS / 32; ++w) m32 = fminf(m32, red_f[w]);
+    const float lim = m32 * widen;
+    for (uint32_t kk = threadIdx.x; kk < k; kk += F64_THREADS)
+      if (dist[kk] <= lim || m32 != m32) cand[atomicAdd(&ncand, 1u)] = kk;
+    __syncthreads();
+    const uint32_t nc = ncand;
     double best = INFINITY;
     int bk = 0x7fffffff;
-#pragma unroll
-    for (int q = 0; q < KLANE; ++q) {
-      const uint32_t kk = lane + 32 * q;
-      if (kk < k && (dist[q] <= lim || m32 != m32)) {
-        double s64 = 0.0;
-        for (uint32_t j = 0; j < d; ++j) {
-          const double t = __dsub_rn((double)__ldg(xp + j), (double)cs[kk * ld + j]);
-          s64 = __dadd_rn(s64, __dmul_rn(t, t));
+    for (uint32_t c0 = 0; c0 < nc; c0 += cc) {
+      const uint32_t cn = nc - c0 < cc ? nc - c0 : cc;
+      for (uint32_t ci = warp; ci < cn; ci += F64_THREADS / 32) {
+        const float* cp = c + (uint64_t)cand[c0 + ci] * d;
+        for (uint32_t j = lane; j < d; j += 32) {
+          const double t = __dsub_rn((double)xs[j], (double)__ldg(cp + j));
+          prod[ci * d + j] = __dmul_rn(t, t);
         }
-        if (s64 < best) best = s64, bk = (int)kk;  // kk increases per lane: the lowest index keeps a tie
       }
+      __syncthreads();
+      if (threadIdx.x < cn) {
+        double s64 = 0.0;
+        for (uint32_t j = 0; j < d; ++j) s64 = __dadd_rn(s64, prod[threadIdx.x * d + j]);
+        const int kk = (int)cand[c0 + threadIdx.x];
+        if (s64 < best || (s64 == best && kk < bk)) best = s64, bk = kk;
+      }
+      __syncthreads();
     }
     for (int o = 16; o; o >>= 1) {
       const double ob = __shfl_xor_sync(0xffffffffu, best, o);
       const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
       if (ob < best || (ob == best && ok < bk)) best = ob, bk = ok;
     }
-    if (lane == 0) assign[p] = bk == 0x7fffffff ? 0 : bk;
+    if (lane == 0) red_d[warp] = best, red_k[warp] = bk;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < F64_THREADS / 32; ++w)
+        if (red_d[w] < best || (red_d[w] == best && red_k[w] < bk)) best = red_d[w], bk = red_k[w];
+      assign[p] = bk == 0x7fffffff ? 0 : bk;
+    }
   }
-  if (stat && lane == 0 && n64) atomicAdd(stat + 1, (unsigned long long)n64);
 }
 
 // max |x| over all coordinates (as float bits; non-negative floats order like ints)
@@ -1219,6 +1275,7 @@ size_t km_scratch_bytes(uint32_t n, uint32_t d, uint32_t k, int precision) {
   b += a256((uint64_t)n * 4);          // flagged
   b += a256(8 * 4);                    // counters: nflag[2], maxabs, cmax, pairs
   b += a256((uint64_t)n * 8);          // pair list
+  b += a256((uint64_t)n * 4);          // FP64 stage list
   b += a256((uint64_t)k * 4 * 2);      // cnorm (||c||^2) + spare
   b += a256(16);                       // shift
   b += a256((uint64_t)k * 4);          // per-cluster write cursor
@@ -1242,6 +1299,7 @@ cudaError_t km_carve(KmBuffers& b, uint8_t* p, size_t bytes) {
   b.flagged = reinterpret_cast<uint32_t*>(take(n * 4));
   b.nflag = reinterpret_cast<uint32_t*>(take(32));
   b.pairs = reinterpret_cast<uint2*>(take(n * 8));
+  b.deferred = reinterpret_cast<uint32_t*>(take(n * 4));
   b.maxabs = reinterpret_cast<unsigned int*>(b.nflag + 2);
   b.cnorm = reinterpret_cast<float*>(take(k * 8));
   b.cent_bf16_norm = nullptr;
@@ -1331,6 +1389,10 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
       (e = cudaFuncSetAttribute(km_recheck_fp64_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, rc_bytes)) !=
           cudaSuccess)
     return e;
+  const int f64_bytes = (int)fp64_stage_smem(d, k);
+  if ((e = cudaFuncSetAttribute(km_fp64_stage_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, f64_bytes)) !=
+      cudaSuccess)
+    return e;
   const uint32_t ntiles = (n + TP - 1) / TP;
   uint32_t agrid = ntiles < (uint32_t)di.sms * 2 ? ntiles : (uint32_t)di.sms * 2;
   if (b.grid_cap && agrid > b.grid_cap) agrid = b.grid_cap;
@@ -1347,18 +1409,25 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
       ++*nk;
     }
     // one warp per pair, latency-bound: a full SM of warps (32 registers a thread)
-    km_pair_kernel<<<di.sms * 8, 256, 0, s>>>(x, d, b.cent, b.pairs, b.nflag + 4, b.assign, b.stats);
+    km_pair_kernel<<<di.sms * 8, 256, 0, s>>>(x, d, b.cent, b.pairs, b.nflag + 4, b.assign, b.stats, b.deferred,
+                                              b.nflag + 5);
     ++*nk;
     // the points neither pass could decide: from the tensor-core pass its
-    // list (re-checked straight away with FP32 direct differences, then FP64
-    // where those leave more than one candidate), from the FP32 pass its own
+    // list (re-checked straight away with FP32 direct differences; the points
+    // where those leave more than one candidate go to the FP64 stage), from
+    // the FP32 pass its own
     const uint32_t* rl = b.precision != MR_KM_FP32 ? reinterpret_cast<const uint32_t*>(b.cent_bf16_norm) : b.flagged;
     const uint32_t* rn = b.precision != MR_KM_FP32 ? b.nflag + 1 : b.nflag;
     if (rc_smem)
       km_recheck_fp64_smem_kernel<<<di.sms * rc_per_sm, 512, rc_bytes, s>>>(x, d, b.cent, k, rl, rn, b.assign,
-                                                                             b.stats);
+                                                                             b.stats, b.deferred, b.nflag + 5);
     else
       km_recheck_fp64_kernel<<<di.sms * 4, 256, 0, s>>>(x, d, b.cent, k, rl, rn, b.assign, b.stats);
+    // the FP64 stage: the points the pair and re-check passes left to the
+    // definition, one CTA each, all at once
+    km_fp64_stage_kernel<<<di.sms * 2, F64_THREADS, f64_bytes, s>>>(x, d, b.cent, k, b.deferred, b.nflag + 5,
+                                                                    b.assign, b.stats);
+    *nk += 2;  // re-check, FP64 stage
     if (local) {  // update with local arrays
       if (wsum)
         km_window_sum_kernel<<<ls_grid, WS_THREADS, (int)ws_smem_bytes(k), s>>>(x, n, k, b.assign, shift, b.part,
@@ -1371,7 +1440,7 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
         km_local_sum_kernel<<<ls_grid, LS_THREADS, ls_bytes, s>>>(x, n, d, k, b.assign, shift, b.part, b.counts);
       km_reduce_finalize_kernel<<<(unsigned)(((uint64_t)k * d + 31) / 32), RF_THREADS, 0, s>>>(
           b.part, ls_grid, b.cent, k, d, b.counts, shift, cmax_bits);
-      *nk += 4;
+      *nk += 3;  // prep, update, reduction
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       continue;
     }
@@ -1385,7 +1454,7 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
     km_sum_kernel<<<(unsigned)((sum_warps * 32 + 255) / 256), 256, 0, s>>>(x, n, d, k, b.kcursor, b.flagged, shift,
                                                                            b.sums);
     km_finalize_kernel<<<64, 256, 0, s>>>(b.cent, k, d, b.sums, b.counts, shift, cmax_bits);
-    *nk += 7;
+    *nk += 6;  // prep, count, offsets, scatter, sums, finalize
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   km_finish_kernel<<<di.sms, 256, 0, s>>>(b.cent, (uint64_t)k * d, out_c, b.assign, n, out_a, b.stats, out_s, iters);

@@ -112,7 +112,9 @@ struct KmBuffers {
   unsigned long long* counts = nullptr;  // [k]
   unsigned long long* stats = nullptr;   // [4]
   uint32_t* flagged = nullptr;  // [n] indices of points to re-check
-  uint32_t* nflag = nullptr;    // [8] counters: [0] FP64 list, [1] FP32 list, [2] max|x| bits, [3] max||c|| bits, [4] pairs
+  uint32_t* nflag = nullptr;    // [8] counters: [0] FP64 list, [1] FP32 list, [2] max|x| bits, [3] max||c|| bits, [4] pairs,
+                                //     [5] points deferred to the FP64 stage
+  uint32_t* deferred = nullptr; // [n] points whose choice needs the FP64 definition
   uint2* pairs = nullptr;       // [n] {point, k1 | k2 << 16}: exact choice between two centroids
   float* xnorm = nullptr;       // [n] ||x||
   float* cnorm = nullptr;       // [k] ||c|| and ||c||^2

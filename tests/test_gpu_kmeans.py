@@ -110,6 +110,22 @@ def test_kmeans_exact_ties_take_lowest_index(mr):
     assert _rel_err(c, c_ref) <= TOL
 
 
+@pytest.mark.parametrize("precision,d", [(0, 64), (1, 64), (0, 8)])
+def test_kmeans_all_centroids_tied(mr, precision, d):
+    """Every centroid the same point: every distance ties, every point goes
+    to the FP64 stage with all 256 centroids as candidates (in chunks of the
+    stage's product scratch: 128 at D = 64, 256 at D = 8), and index 0 wins
+    every tie, as in the definition."""
+    x, _, _ = synth.kmeans_points(3000, d, 16, seed=81 + d)
+    init = np.repeat(x[7:8], 256, axis=0)
+    a_ref = oracle.kmeans_assign(x, init)
+    c_ref, _ = oracle.kmeans_update(x, a_ref, init)
+    c, a, st = _run(mr, x, init, 1, precision)
+    assert np.array_equal(a, a_ref) and not np.any(a)
+    assert int(st[1]) >= 2999  # (a point equal to the centroid may be decided earlier)
+    assert _rel_err(c, c_ref) <= TOL
+
+
 def test_kmeans_empty_cluster_keeps_centroid(mr):
     x, _, _ = synth.kmeans_points(3000, 4, 3, seed=31)
     init = np.concatenate([x[:3], np.full((1, 4), 1e4, dtype=np.float32)])
