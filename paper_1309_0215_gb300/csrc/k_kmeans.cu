@@ -1251,7 +1251,14 @@ __global__ void km_finish_kernel(const float* c, uint64_t kd, float* out_c, cons
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = tid; i < kd; i += nth) out_c[i] = c[i];
-  for (uint64_t i = tid; i < n; i += nth) out_a[i] = assign[i];
+  uint64_t done = 0;
+  if (((reinterpret_cast<uintptr_t>(out_a) | reinterpret_cast<uintptr_t>(assign)) & 15) == 0) {
+    const uint64_t n4 = n / 4;
+    for (uint64_t i = tid; i < n4; i += nth)
+      reinterpret_cast<int4*>(out_a)[i] = reinterpret_cast<const int4*>(assign)[i];
+    done = n4 * 4;
+  }
+  for (uint64_t i = done + tid; i < n; i += nth) out_a[i] = assign[i];
   if (tid == 0) {
     if ((kd + n) & 1) out_a[n] = 0;  // the zero padding before the 8-byte aligned stats
     out_s[0] = stats[0];
@@ -1319,7 +1326,7 @@ cudaError_t km_carve(KmBuffers& b, uint8_t* p, size_t bytes) {
 bool km_tc_supported(uint32_t d, uint32_t k);
 
 cudaError_t launch_kmeans_tc_assign(const float* x, uint32_t n, uint32_t d, const float* c, uint32_t k,
-                                    KmBuffers& b, const DevInfo& di, cudaStream_t s, uint64_t* nk);
+                                    KmBuffers& b, const DevInfo& di, cudaStream_t s, uint64_t* nk, bool maxabs);
 
 cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmBuffers& b, const DevInfo& di,
                           cudaStream_t s, float* out_c, int32_t* out_a, unsigned long long* out_s, uint64_t* nk) {
@@ -1330,9 +1337,14 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
   if ((e = cudaMemcpyAsync(b.cent, init, (size_t)k * d * 4, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(b.stats, 0, 32, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(b.nflag, 0, 32, s)) != cudaSuccess) return e;
-  km_maxabs_kernel<<<di.sms * 4, 256, 0, s>>>(x, (uint64_t)n * d, b.maxabs);
-  km_scale_kernel<<<1, 1, 0, s>>>(b.maxabs, n, shift);
-  *nk += 2;
+  // the fixed-point scale needs max |x|: a pass of its own for the FP32
+  // path; the tensor-core pass finds it while converting the first iteration
+  const bool tc = b.precision != MR_KM_FP32;
+  if (!tc) {
+    km_maxabs_kernel<<<di.sms * 4, 256, 0, s>>>(x, (uint64_t)n * d, b.maxabs);
+    km_scale_kernel<<<1, 1, 0, s>>>(b.maxabs, n, shift);
+    *nk += 2;
+  }
   const int asm_bytes = (DC_MAX * CS_LD + DC_MAX * TP) * 4;
   if ((e = cudaFuncSetAttribute(km_assign_fp32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 asm_bytes)) != cudaSuccess ||
@@ -1399,7 +1411,11 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
   for (uint32_t it = 0; it < iters; ++it) {
     km_prep_kernel<<<64, 256, 0, s>>>(b.cent, k, d, b.cnorm, cmax_bits, b.sums, b.counts, b.nflag);
     if (b.precision != MR_KM_FP32) {
-      if ((e = launch_kmeans_tc_assign(x, n, d, b.cent, k, b, di, s, nk)) != cudaSuccess) return e;
+      if ((e = launch_kmeans_tc_assign(x, n, d, b.cent, k, b, di, s, nk, it == 0)) != cudaSuccess) return e;
+      if (it == 0) {
+        km_scale_kernel<<<1, 1, 0, s>>>(b.maxabs, n, shift);
+        ++*nk;
+      }
     } else {
       if ((e = kt_begin(b.kt, s)) != cudaSuccess) return e;
       (k <= 256 ? km_assign_fp32_kernel<true> : km_assign_fp32_kernel<false>)<<<agrid, KM_THREADS, asm_bytes, s>>>(
@@ -1457,7 +1473,8 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
     *nk += 6;  // prep, count, offsets, scatter, sums, finalize
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  km_finish_kernel<<<di.sms, 256, 0, s>>>(b.cent, (uint64_t)k * d, out_c, b.assign, n, out_a, b.stats, out_s, iters);
+  km_finish_kernel<<<di.sms * 4, 256, 0, s>>>(b.cent, (uint64_t)k * d, out_c, b.assign, n, out_a, b.stats, out_s,
+                                              iters);
   ++*nk;
   return cudaGetLastError();
 }

@@ -216,7 +216,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const float* __restrict__ c, uint32_t k,
                     const float* __restrict__ cnorm, const unsigned int* cmax_bits, int32_t* __restrict__ assign,
                     uint32_t* __restrict__ list, uint32_t* nlist, uint2* __restrict__ pairs, uint32_t* npairs,
-                    unsigned long long* timeouts, float* dbg, long long polls, uint32_t stop_copies) {
+                    unsigned long long* timeouts, float* dbg, long long polls, uint32_t stop_copies,
+                    unsigned int* maxabs) {
   extern __shared__ uint8_t tc_raw[];
   TcSmem& S = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -284,6 +285,7 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
     const int cw = warp - CVT_WARP0;
     const int col = lane & 15, rsub = lane >> 4;
     const bool vec = d == KD && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
+    unsigned int mabs = 0;  // bits of max |x| over the values this thread converts (non-negative floats order as ints)
     for (uint32_t i = 0;; ++i) {
       const uint32_t tile = blockIdx.x + i * gridDim.x;
       if (tile >= ntiles) break;
@@ -327,6 +329,9 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int rr = r0 + 2 * q + rsub;
+          if (maxabs)
+            mabs = max(mabs, max(max(__float_as_uint(fabsf(v[q].x)), __float_as_uint(fabsf(v[q].y))),
+                                 max(__float_as_uint(fabsf(v[q].z)), __float_as_uint(fabsf(v[q].w)))));
           float ss = fmaf(v[q].w, v[q].w, fmaf(v[q].z, v[q].z, fmaf(v[q].y, v[q].y, v[q].x * v[q].x)));
           ss += __shfl_xor_sync(0xffffffffu, ss, 8);
           ss += __shfl_xor_sync(0xffffffffu, ss, 4);
@@ -352,6 +357,10 @@ km_tc_assign_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const f
         mbar_arrive(&S.full_a[s]);
         if (vec) mbar_arrive(&S.tempty[q2]);
       }
+    }
+    if (maxabs) {
+      for (int o = 16; o; o >>= 1) mabs = max(mabs, __shfl_xor_sync(0xffffffffu, mabs, o));
+      if (lane == 0) atomicMax(maxabs, mabs);
     }
   } else if (warp == TMA_WARP) {
     // ------------------------------------------------- bulk-copy producer
@@ -568,12 +577,13 @@ bool km_tc_supported(uint32_t d, uint32_t k) { return d >= 1 && d <= KD && k >= 
 
 size_t km_tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
 
-// Raw launch (also used by the diagnostics probe): list/nlist receive the
-// points that need the FP32 pass.
+// Raw launch: list/nlist receive the points to re-check, pairs/npairs the
+// two-candidate points; maxabs (when not null) receives the bits of max |x|.
 cudaError_t launch_km_tc_kernel(int terms, const float* x, uint32_t n, uint32_t d, const float* c, uint32_t k,
                                 const float* cnorm, const unsigned int* cmax_bits, int32_t* assign, uint32_t* list,
                                 uint32_t* nlist, uint2* pairs, uint32_t* npairs, unsigned long long* timeouts,
-                                float* dbg, int grid, cudaStream_t s, long long polls, uint32_t stop_copies) {
+                                float* dbg, int grid, cudaStream_t s, long long polls, uint32_t stop_copies,
+                                unsigned int* maxabs) {
   const int smem = (int)km_tc_smem_bytes();
   cudaError_t e;
   if (terms == 3) {
@@ -581,19 +591,19 @@ cudaError_t launch_km_tc_kernel(int terms, const float* x, uint32_t n, uint32_t 
         cudaSuccess)
       return e;
     km_tc_assign_kernel<3><<<grid, TC_THREADS, smem, s>>>(x, n, d, c, k, cnorm, cmax_bits, assign, list, nlist,
-                                                           pairs, npairs, timeouts, dbg, polls, stop_copies);
+                                                           pairs, npairs, timeouts, dbg, polls, stop_copies, maxabs);
   } else {
     if ((e = cudaFuncSetAttribute(km_tc_assign_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
         cudaSuccess)
       return e;
     km_tc_assign_kernel<1><<<grid, TC_THREADS, smem, s>>>(x, n, d, c, k, cnorm, cmax_bits, assign, list, nlist,
-                                                           pairs, npairs, timeouts, dbg, polls, stop_copies);
+                                                           pairs, npairs, timeouts, dbg, polls, stop_copies, maxabs);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_kmeans_tc_assign(const float* x, uint32_t n, uint32_t d, const float* c, uint32_t k,
-                                    KmBuffers& b, const DevInfo& di, cudaStream_t s, uint64_t* nk) {
+                                    KmBuffers& b, const DevInfo& di, cudaStream_t s, uint64_t* nk, bool maxabs) {
   const uint32_t ntiles = (n + TM - 1) / TM;
   uint32_t grid = ntiles < (uint32_t)di.sms ? ntiles : (uint32_t)di.sms;
   if (b.grid_cap && grid > b.grid_cap) grid = b.grid_cap;
@@ -603,7 +613,7 @@ cudaError_t launch_kmeans_tc_assign(const float* x, uint32_t n, uint32_t d, cons
   if (e != cudaSuccess) return e;
   e = launch_km_tc_kernel(terms, x, n, d, c, k, b.cnorm, b.nflag + 3, b.assign, list, b.nflag + 1, b.pairs,
                           b.nflag + 4, b.stats + 3, nullptr, (int)grid, s, b.polls < 0 ? SPIN_LIMIT : b.polls,
-                          b.stop_copies);
+                          b.stop_copies, maxabs ? b.maxabs : nullptr);
   if (e != cudaSuccess || (e = kt_end(b.kt, s)) != cudaSuccess) return e;
   ++*nk;
   // the caller re-checks the pairs and the listed near ties
