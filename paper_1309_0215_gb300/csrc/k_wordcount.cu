@@ -677,6 +677,7 @@ __device__ void bsum_scan(Post& P, uint64_t nb) {
 // blocks the tickets would serialise on one address, so wc_bscan_kernel does
 // the scan instead.
 __global__ void __launch_bounds__(CB) wc_lensum_kernel(Post P, bool fuse) {
+  pdl_wait();
   __shared__ unsigned long long ws[32];
   __shared__ bool last;
   const SortRec* recs = P.r1;
@@ -709,6 +710,7 @@ __global__ void __launch_bounds__(CB) wc_lensum_kernel(Post P, bool fuse) {
 
 // Blocks past the last record hold no lengths: only the live ones are scanned.
 __global__ void __launch_bounds__(CB) wc_bscan_kernel(Post P, uint64_t nb) {
+  pdl_wait();
   const uint64_t live = (P.glob[0] + CB - 1) / CB;
   bsum_scan(P, live < nb ? live : nb);
 }
@@ -717,6 +719,7 @@ constexpr uint64_t LENSUM_FUSE_BLOCKS = 4096;
 // Exclusive length scan per record; each job's first / end record and the
 // scan at both are stored in the job's state as 64-bit fields 1..4.
 __global__ void __launch_bounds__(CB) wc_bounds_kernel(const JobDev* jobs, JobDev single, Post P) {
+  pdl_wait();
   __shared__ unsigned long long wsum[32];
   const SortRec* recs = P.r1;
   const uint64_t m = *P.glob;
@@ -793,6 +796,7 @@ __device__ __forceinline__ void gather_one(const JobDev* jobs, const JobDev& sin
   emit_record(J, P, r, i - first, end - first, P.excl[i] - scan0, scan1 - scan0);
 }
 __global__ void __launch_bounds__(256) wc_gather_kernel(const JobDev* jobs, JobDev single, Post P) {
+  pdl_wait();
   const SortRec* recs = P.r1;
   const uint64_t m = *P.glob;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
@@ -803,6 +807,7 @@ __global__ void __launch_bounds__(256) wc_gather_kernel(const JobDev* jobs, JobD
 // P.glob[9]), so the bounds pass is not needed: each block scans its key
 // lengths from the block sums and writes its records straight away.
 __global__ void __launch_bounds__(CB) wc_gather1_kernel(JobDev J, Post P) {
+  pdl_wait();
   __shared__ unsigned long long wsum[32];
   const SortRec* recs = P.r1;
   const uint64_t m = P.glob[0], kbytes = P.glob[9];
@@ -1107,6 +1112,7 @@ __device__ __forceinline__ void rfix_one(const Post& P, const JobDev* jobs, cons
 }
 
 __global__ void __launch_bounds__(256) wc_rfix_kernel(Post P, const JobDev* jobs, JobDev single, uint64_t max_runs) {
+  pdl_wait();
   const uint64_t m = *P.glob;
   for (uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x; i + 1 < m; i += (uint64_t)gridDim.x * 256)
     rfix_one(P, jobs, single, max_runs, i, m);
@@ -1207,6 +1213,7 @@ __device__ R* cta_sort(R* r, R* tmp, uint64_t L, R* sh, int cap, const C& cmp) {
 // are in key order) as scratch.
 __global__ void __launch_bounds__(SB_THREADS) wc_rfix_cta_kernel(Post P, const JobDev* jobs, JobDev single,
                                                                  uint64_t max_runs) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char rf_raw[];
   SortRec* sh = reinterpret_cast<SortRec*>(rf_raw);
   const RecCmp cmp{jobs, single, P.src};
@@ -1311,6 +1318,7 @@ __device__ __forceinline__ void ss_geometry(uint64_t m, uint64_t& nb, uint64_t& 
 // also records the number of buckets.  Tickets, bucket counters and rank
 // counters start at zero (cleared with P.glob).
 __global__ void __launch_bounds__(256, 4) wc_ss_sample_kernel(Post P) {
+  pdl_wait();
   __shared__ __align__(16) unsigned char sp_raw[256 * 20];  // KeySoA of 256 keys
   const uint64_t m = P.glob[0];
   uint64_t nb, S;
@@ -1351,6 +1359,7 @@ __global__ void __launch_bounds__(256, 4) wc_ss_sample_kernel(Post P) {
 
 // Bucket of each record (number of splitters below its key) and bucket sizes.
 __global__ void __launch_bounds__(256) wc_ss_count_kernel(Post P) {
+  pdl_wait();
   __shared__ KeyRec spl[SS_MAXB];
   __shared__ uint32_t cnt[SS_MAXB];
   const uint64_t m = P.glob[0];
@@ -1380,6 +1389,7 @@ __global__ void __launch_bounds__(256) wc_ss_count_kernel(Post P) {
 // Bucket offsets (each CTA scans the counts; CTA 0 stores them), then each
 // CTA reserves one range per bucket it holds and places its keys there.
 __global__ void __launch_bounds__(256) wc_ss_scatter_kernel(Post P) {
+  pdl_wait();
   __shared__ uint32_t off[SS_MAXB + 1];
   __shared__ uint32_t cnt[SS_MAXB];
   __shared__ uint32_t wsum[8];
@@ -1876,6 +1886,7 @@ __global__ void __launch_bounds__(SEG_BT) wc_seg_bucket_cta_kernel(Post P) {
 // sets the pass's length, so all of a CTA's threads share each bucket).
 constexpr int SS_BUCKET_T = 512;
 __global__ void __launch_bounds__(SS_BUCKET_T, 2) wc_ss_bucket_kernel(Post P) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char sb_raw[];
   const uint32_t b = blockIdx.x;
   if (b >= P.ss[0]) return;
@@ -2096,11 +2107,13 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
     const uint64_t nbmax = (R + SS_B - 1) / SS_B < (uint64_t)SS_MAXB ? (R + SS_B - 1) / SS_B : (uint64_t)SS_MAXB;
     const uint64_t smax = R < nbmax * SS_OVER ? R : nbmax * SS_OVER;
     const uint64_t sblocks = (smax + 255) / 256 < 1 ? 1 : (smax + 255) / 256;
-    wc_ss_sample_kernel<<<(unsigned)(sblocks * SS_PARTS), 256, 0, s>>>(P);
-    wc_ss_count_kernel<<<g256, 256, 0, s>>>(P);
-    wc_ss_scatter_kernel<<<g256, 256, 0, s>>>(P);
-    wc_ss_bucket_kernel<<<(unsigned)(nbmax < 1 ? 1 : nbmax), SS_BUCKET_T, BUCKET_CTA_SMEM, s>>>(P);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_pdl(wc_ss_sample_kernel, dim3((unsigned)(sblocks * SS_PARTS)), dim3(256), 0, s, P)) !=
+            cudaSuccess ||
+        (e = launch_pdl(wc_ss_count_kernel, dim3(g256), dim3(256), 0, s, P)) != cudaSuccess ||
+        (e = launch_pdl(wc_ss_scatter_kernel, dim3(g256), dim3(256), 0, s, P)) != cudaSuccess ||
+        (e = launch_pdl(wc_ss_bucket_kernel, dim3((unsigned)(nbmax < 1 ? 1 : nbmax)), dim3(SS_BUCKET_T),
+                        BUCKET_CTA_SMEM, s, P)) != cudaSuccess)
+      return e;
     *nk += 3;  // the last one is counted with the tie fix-up below
   } else if (R < RADIX_MIN_RECORDS) {
     // small record sets: comparison sort of (key1, s0, index) keys
@@ -2147,24 +2160,28 @@ cudaError_t launch_wordcount_post_multi(const wc::JobDev* jobs, const wc::JobDev
   const unsigned gp256 = (unsigned)(g256 < 8 * smc ? g256 : 8 * smc);  // 8 CTAs per SM (gather: 32 registers)
   const unsigned gpfix = (unsigned)(g256 < 6 * smc ? g256 : 6 * smc);  // 6 (tie fix-up: 40 registers)
   const unsigned gpcb = (unsigned)(nb < 2 * smc ? nb : 2 * smc);
-  wc_rfix_kernel<<<gpfix, 256, 0, s>>>(P, jobs, single, max_runs(R));
   const int fx_smem = SB * (int)sizeof(SortRec);
   if ((e = cudaFuncSetAttribute(wc_rfix_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem)) !=
       cudaSuccess)
     return e;
-  wc_rfix_cta_kernel<<<64, SB_THREADS, fx_smem, s>>>(P, jobs, single, max_runs(R));
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_pdl(wc_rfix_kernel, dim3(gpfix), dim3(256), 0, s, P, jobs, single, max_runs(R))) != cudaSuccess ||
+      (e = launch_pdl(wc_rfix_cta_kernel, dim3(64), dim3(SB_THREADS), (size_t)fx_smem, s, P, jobs, single,
+                      max_runs(R))) != cudaSuccess)
+    return e;
   *nk += 3;
-  wc_lensum_kernel<<<nb <= LENSUM_FUSE_BLOCKS ? (unsigned)nb : gpcb, CB, 0, s>>>(P, nb <= LENSUM_FUSE_BLOCKS);
+  if ((e = launch_pdl(wc_lensum_kernel, dim3(nb <= LENSUM_FUSE_BLOCKS ? (unsigned)nb : gpcb), dim3(CB), 0, s, P,
+                      nb <= LENSUM_FUSE_BLOCKS)) != cudaSuccess)
+    return e;
   if (nb > LENSUM_FUSE_BLOCKS) {
-    wc_bscan_kernel<<<1, CB, 0, s>>>(P, nb);
+    if ((e = launch_pdl(wc_bscan_kernel, dim3(1), dim3(CB), 0, s, P, nb)) != cudaSuccess) return e;
     ++*nk;
   }
   if (jobs) {
-    wc_bounds_kernel<<<gpcb, CB, 0, s>>>(jobs, single, P);
-    wc_gather_kernel<<<gp256, 256, 0, s>>>(jobs, single, P);
+    if ((e = launch_pdl(wc_bounds_kernel, dim3(gpcb), dim3(CB), 0, s, jobs, single, P)) != cudaSuccess ||
+        (e = launch_pdl(wc_gather_kernel, dim3(gp256), dim3(256), 0, s, jobs, single, P)) != cudaSuccess)
+      return e;
   } else {  // one job: bounds known, scan and gather in one pass
-    wc_gather1_kernel<<<gpcb, CB, 0, s>>>(single, P);
+    if ((e = launch_pdl(wc_gather1_kernel, dim3(gpcb), dim3(CB), 0, s, single, P)) != cudaSuccess) return e;
     --*nk;
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -1,5 +1,6 @@
 // Internal declarations shared by the CUDA translation units of libmrgb.so.
 #pragma once
+#include <utility>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstddef>
@@ -103,6 +104,31 @@ cudaError_t launch_wordcount(const uint8_t* in, uint64_t n, const WcBuffers& b, 
                              uint64_t* nk, bool pipelined = false, KTimer* kt = nullptr, long long pipe_polls = -1);
 
 // ---------------------------------------------------------------- k-means
+// Programmatic dependent launch: the kernel may be scheduled while the
+// kernel before it on the stream is still finishing (its launch and ramp
+// overlap that kernel's tail); it must call pdl_wait() before touching any
+// memory, which returns once the earlier kernel has completed and its writes
+// are visible.  Used only for kernels that start with pdl_wait() and follow
+// another kernel on the stream.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#endif
+
 struct KmBuffers {
   uint32_t n = 0, d = 0, k = 0;
   float* cent = nullptr;        // [k][d] current centroids (FP32 state)
