@@ -107,6 +107,7 @@ __device__ __forceinline__ void top2lb_merge(uint32_t& a1, uint32_t& a2, uint32_
 // Centroid norms: cn[k] = ||c_k||^2 (FP32, sequential FMA); cmax[0] = max ||c_k||.
 __global__ void km_prep_kernel(const float* __restrict__ c, uint32_t k, uint32_t d, float* __restrict__ cn,
                                unsigned int* cmax_bits, long long* sums, unsigned long long* counts, uint32_t* nflag) {
+  pdl_wait();
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = tid; i < (uint64_t)k; i += nth) {
@@ -385,6 +386,7 @@ __global__ void km_pair_kernel(const float* __restrict__ x, uint32_t d, const fl
 __global__ void km_recheck_fp64_kernel(const float* __restrict__ x, uint32_t d, const float* __restrict__ c, uint32_t k,
                                        const uint32_t* flagged, const uint32_t* nflag, int32_t* assign,
                                        unsigned long long* stat) {
+  pdl_wait();
   const uint32_t nf = *nflag;
   const int lane = threadIdx.x & 31;
   const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -447,6 +449,7 @@ __global__ void km_recheck_fp64_smem_kernel(const float* __restrict__ x, uint32_
                                             uint32_t k, const uint32_t* flagged, const uint32_t* nflag,
                                             int32_t* assign, unsigned long long* stat, uint32_t* deferred,
                                             uint32_t* ndef) {
+  pdl_wait();
   extern __shared__ float cs[];  // [k][d + 1]
   const uint32_t nf = *nflag;
   const uint32_t per = max(RC_MIN, (nf + gridDim.x - 1) / gridDim.x);
@@ -522,6 +525,7 @@ __global__ void __launch_bounds__(F64_THREADS) km_fp64_stage_kernel(const float*
                                                                     const float* __restrict__ c, uint32_t k,
                                                                     const uint32_t* list, const uint32_t* nlist,
                                                                     int32_t* assign, unsigned long long* stat) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char f64_sm[];
   double* prod = reinterpret_cast<double*>(f64_sm);   // [cc][d]
   float* xs = reinterpret_cast<float*>(prod + F64_PROD);  // [d]
@@ -833,6 +837,7 @@ __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_kernel(const float
                                                                      const int32_t* __restrict__ assign,
                                                                      const int* shift, long long* __restrict__ part,
                                                                      unsigned long long* counts) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char ls_sm[];
   const uint64_t kd = (uint64_t)k * d;
   uint32_t* SL = reinterpret_cast<uint32_t*>(ls_sm);  // low words [k][d]
@@ -940,6 +945,7 @@ __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_pipe_kernel(
     const float* __restrict__ x, uint32_t n, uint32_t d, uint32_t k, const int32_t* __restrict__ assign,
     const int* shift, long long* __restrict__ part, unsigned long long* counts, uint32_t rows,
     unsigned long long* timeouts, long long polls) {
+  pdl_wait();
   using namespace pipe;
   extern __shared__ __align__(128) unsigned char lp_sm[];
   const uint64_t kd = (uint64_t)k * d;
@@ -1101,6 +1107,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) km_window_sum_kernel(const floa
                                                                       uint32_t k, const int32_t* __restrict__ assign,
                                                                       const int* shift, long long* __restrict__ part,
                                                                       unsigned long long* counts) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char ws_sm[];
   long long* S = reinterpret_cast<long long*>(ws_sm);
   uint32_t* hc = reinterpret_cast<uint32_t*>(S + (uint64_t)k * 64);
@@ -1211,6 +1218,7 @@ __global__ void __launch_bounds__(RF_THREADS) km_reduce_finalize_kernel(const lo
                                                                         uint32_t g, float* c, uint32_t k, uint32_t d,
                                                                         const unsigned long long* counts,
                                                                         const int* shift, unsigned int* cmax_bits) {
+  pdl_wait();
   __shared__ long long red[RF_THREADS / 32][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint64_t kd = (uint64_t)k * d;
@@ -1248,6 +1256,7 @@ __global__ void km_finalize_kernel(float* c, uint32_t k, uint32_t d, const long 
 __global__ void km_finish_kernel(const float* c, uint64_t kd, float* out_c, const int32_t* assign, uint32_t n,
                                  int32_t* out_a, const unsigned long long* stats, unsigned long long* out_s,
                                  uint32_t iters) {
+  pdl_wait();
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = tid; i < kd; i += nth) out_c[i] = c[i];
@@ -1409,7 +1418,13 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
   uint32_t agrid = ntiles < (uint32_t)di.sms * 2 ? ntiles : (uint32_t)di.sms * 2;
   if (b.grid_cap && agrid > b.grid_cap) agrid = b.grid_cap;
   for (uint32_t it = 0; it < iters; ++it) {
-    km_prep_kernel<<<64, 256, 0, s>>>(b.cent, k, d, b.cnorm, cmax_bits, b.sums, b.counts, b.nflag);
+    // kernels that follow another kernel of this job on the stream start
+    // while it drains (programmatic dependent launch; each waits first)
+    if (it == 0)
+      km_prep_kernel<<<64, 256, 0, s>>>(b.cent, k, d, b.cnorm, cmax_bits, b.sums, b.counts, b.nflag);
+    else if ((e = launch_pdl(km_prep_kernel, dim3(64), dim3(256), 0, s, (const float*)b.cent, k, d, b.cnorm, cmax_bits,
+                             b.sums, b.counts, b.nflag)) != cudaSuccess)
+      return e;
     if (b.precision != MR_KM_FP32) {
       if ((e = launch_kmeans_tc_assign(x, n, d, b.cent, k, b, di, s, nk, it == 0)) != cudaSuccess) return e;
       if (it == 0) {
@@ -1435,27 +1450,35 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
     const uint32_t* rl = b.precision != MR_KM_FP32 ? reinterpret_cast<const uint32_t*>(b.cent_bf16_norm) : b.flagged;
     const uint32_t* rn = b.precision != MR_KM_FP32 ? b.nflag + 1 : b.nflag;
     if (rc_smem)
-      km_recheck_fp64_smem_kernel<<<di.sms * rc_per_sm, 512, rc_bytes, s>>>(x, d, b.cent, k, rl, rn, b.assign,
-                                                                             b.stats, b.deferred, b.nflag + 5);
+      e = launch_pdl(km_recheck_fp64_smem_kernel, dim3(di.sms * rc_per_sm), dim3(512), (size_t)rc_bytes, s, x, d,
+                     (const float*)b.cent, k, rl, rn, b.assign, b.stats, b.deferred, b.nflag + 5);
     else
-      km_recheck_fp64_kernel<<<di.sms * 4, 256, 0, s>>>(x, d, b.cent, k, rl, rn, b.assign, b.stats);
+      e = launch_pdl(km_recheck_fp64_kernel, dim3(di.sms * 4), dim3(256), 0, s, x, d, (const float*)b.cent, k, rl, rn,
+                     b.assign, b.stats);
+    if (e != cudaSuccess) return e;
     // the FP64 stage: the points the pair and re-check passes left to the
     // definition, one CTA each, all at once
-    km_fp64_stage_kernel<<<di.sms * 2, F64_THREADS, f64_bytes, s>>>(x, d, b.cent, k, b.deferred, b.nflag + 5,
-                                                                    b.assign, b.stats);
+    if ((e = launch_pdl(km_fp64_stage_kernel, dim3(di.sms * 2), dim3(F64_THREADS), (size_t)f64_bytes, s, x, d,
+                        (const float*)b.cent, k, (const uint32_t*)b.deferred, (const uint32_t*)(b.nflag + 5), b.assign,
+                        b.stats)) != cudaSuccess)
+      return e;
     *nk += 2;  // re-check, FP64 stage
     if (local) {  // update with local arrays
       if (wsum)
-        km_window_sum_kernel<<<ls_grid, WS_THREADS, (int)ws_smem_bytes(k), s>>>(x, n, k, b.assign, shift, b.part,
-                                                                                b.counts);
+        e = launch_pdl(km_window_sum_kernel, dim3(ls_grid), dim3(WS_THREADS), (size_t)ws_smem_bytes(k), s, x, n, k,
+                       (const int32_t*)b.assign, (const int*)shift, b.part, b.counts);
       else if (lp_rows)
-        (d == 64 ? km_local_sum_pipe_kernel<true> : km_local_sum_pipe_kernel<false>)<<<ls_grid, LS_THREADS, lp_bytes,
-                                                                                        s>>>(
-            x, n, d, k, b.assign, shift, b.part, b.counts, lp_rows, b.stats + 3, polls);
+        e = launch_pdl(d == 64 ? km_local_sum_pipe_kernel<true> : km_local_sum_pipe_kernel<false>, dim3(ls_grid),
+                       dim3(LS_THREADS), (size_t)lp_bytes, s, x, n, d, k, (const int32_t*)b.assign, (const int*)shift,
+                       b.part, b.counts, lp_rows, b.stats + 3, polls);
       else
-        km_local_sum_kernel<<<ls_grid, LS_THREADS, ls_bytes, s>>>(x, n, d, k, b.assign, shift, b.part, b.counts);
-      km_reduce_finalize_kernel<<<(unsigned)(((uint64_t)k * d + 31) / 32), RF_THREADS, 0, s>>>(
-          b.part, ls_grid, b.cent, k, d, b.counts, shift, cmax_bits);
+        e = launch_pdl(km_local_sum_kernel, dim3(ls_grid), dim3(LS_THREADS), (size_t)ls_bytes, s, x, n, d, k,
+                       (const int32_t*)b.assign, (const int*)shift, b.part, b.counts);
+      if (e != cudaSuccess) return e;
+      if ((e = launch_pdl(km_reduce_finalize_kernel, dim3((unsigned)(((uint64_t)k * d + 31) / 32)), dim3(RF_THREADS),
+                          0, s, (const long long*)b.part, ls_grid, b.cent, k, d, (const unsigned long long*)b.counts,
+                          (const int*)shift, cmax_bits)) != cudaSuccess)
+        return e;
       *nk += 3;  // prep, update, reduction
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       continue;
@@ -1473,8 +1496,10 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
     *nk += 6;  // prep, count, offsets, scatter, sums, finalize
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  km_finish_kernel<<<di.sms * 4, 256, 0, s>>>(b.cent, (uint64_t)k * d, out_c, b.assign, n, out_a, b.stats, out_s,
-                                              iters);
+  if ((e = launch_pdl(km_finish_kernel, dim3(di.sms * 4), dim3(256), 0, s, (const float*)b.cent, (uint64_t)k * d,
+                      out_c, (const int32_t*)b.assign, n, out_a, (const unsigned long long*)b.stats, out_s, iters)) !=
+      cudaSuccess)
+    return e;
   ++*nk;
   return cudaGetLastError();
 }
