@@ -292,25 +292,41 @@ batch_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs, uint64_t total_t
 }
 
 // Zero every container the batch accumulates into: histogram bins,
-// regression sums, word-count tables and state words.  One CTA per job.
-__global__ void batch_init_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs) {
-  for (uint32_t j = blockIdx.x; j < njobs; j += gridDim.x) {
-    const BatchJob& J = jobs[j];
-    uint4* p;
-    uint64_t n16;
-    if (J.kind == MR_WORDCOUNT) {
-      p = reinterpret_cast<uint4*>(J.wc.key);
-      n16 = J.wc.cap * 24 / 16;
+// regression sums, word-count tables and state words.  The containers are
+// cut into chunks of BATCH_ZCHUNK bytes numbered across the jobs (zchunk0),
+// so a large word-count table is cleared by many CTAs at once instead of one.
+__device__ __forceinline__ uint32_t find_zjob(const BatchJob* jobs, uint32_t njobs, uint64_t c) {
+  uint32_t lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].zchunk0 <= c) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ uint64_t zero_bytes(const BatchJob& J) {
+  return J.kind == MR_WORDCOUNT ? J.wc.cap * 24 : (J.kind == MR_HIST_RGB8 ? 768 * 8 : 48);
+}
+__global__ void batch_init_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs, uint64_t nchunks) {
+  for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const BatchJob& J = jobs[find_zjob(jobs, njobs, c)];
+    const uint64_t off = (c - J.zchunk0) * BATCH_ZCHUNK;
+    const uint64_t bytes = zero_bytes(J);
+    if (off >= bytes) continue;
+    const uint64_t end = off + BATCH_ZCHUNK < bytes ? off + BATCH_ZCHUNK : bytes;
+    uint4* p = static_cast<uint4*>(J.kind == MR_WORDCOUNT ? static_cast<void*>(J.wc.key) : J.out);
+    for (uint64_t i = off / 16 + threadIdx.x; i < end / 16; i += blockDim.x) p[i] = make_uint4(0, 0, 0, 0);
+    if (J.kind == MR_WORDCOUNT && off == 0)
       for (uint32_t i = threadIdx.x; i < 64 / 4; i += blockDim.x) J.wc.state[i] = 0;
-    } else {
-      p = static_cast<uint4*>(J.out);
-      n16 = J.kind == MR_HIST_RGB8 ? 768 * 8 / 16 : 48 / 16;
-    }
-    for (uint64_t i = threadIdx.x; i < n16; i += blockDim.x) p[i] = make_uint4(0, 0, 0, 0);
   }
 }
 
 }  // namespace
+
+uint64_t batch_zero_chunks(uint32_t kind, uint64_t wc_cap) {
+  const uint64_t bytes = kind == MR_WORDCOUNT ? wc_cap * 24 : (kind == MR_HIST_RGB8 ? 768 * 8 : 48);
+  return (bytes + BATCH_ZCHUNK - 1) / BATCH_ZCHUNK;
+}
 
 uint64_t batch_tiles_for(uint32_t kind, uint64_t n, uint64_t arr_tile, uint64_t wc_tile) {
   const uint64_t t = kind == MR_WORDCOUNT ? wc_tile : arr_tile;
@@ -322,9 +338,10 @@ cudaError_t batch_prepare() {
 }
 
 cudaError_t launch_batch(const BatchJob* jobs_dev, uint32_t njobs, uint64_t total_tiles, unsigned long long* cursor,
-                         uint64_t arr_tile, uint64_t wc_tile, const DevInfo& di, cudaStream_t s, uint64_t* nk) {
+                         uint64_t arr_tile, uint64_t wc_tile, uint64_t total_zchunks, const DevInfo& di,
+                         cudaStream_t s, uint64_t* nk) {
   cudaError_t e;
-  batch_init_kernel<<<di.sms * 4, 256, 0, s>>>(jobs_dev, njobs);
+  batch_init_kernel<<<di.sms * 4, 256, 0, s>>>(jobs_dev, njobs, total_zchunks);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(cursor, 0, 8, s)) != cudaSuccess) return e;
   uint64_t grid = (uint64_t)BCTAS * di.sms;

@@ -553,7 +553,7 @@ mr_status ensure_scratch(mr_ctx* c, void** p, uint64_t* have, uint64_t need) {
 struct BatchPlan {
   std::vector<BatchJob> bj;
   std::vector<wc::JobDev> wj;
-  uint64_t tiles = 0, wc_blocks = 0, wc_records = 0;
+  uint64_t tiles = 0, wc_blocks = 0, wc_records = 0, zchunks = 0;
 };
 
 void plan_batch(const std::vector<Job*>& jobs, const mr_tuning& tp, BatchPlan& P) {
@@ -575,6 +575,8 @@ void plan_batch(const std::vector<Job*>& jobs, const mr_tuning& tp, BatchPlan& P
     b.tile_begin = P.tiles;
     b.ntiles = batch_tiles_for(b.kind, b.n, tp.arr_tile, tp.wc_tile);
     P.tiles += b.ntiles;
+    b.zchunk0 = P.zchunks;
+    P.zchunks += batch_zero_chunks(b.kind, j->desc.kind == MR_WORDCOUNT ? j->wc.cap : 0);
     P.bj.push_back(b);
   }
 }
@@ -603,8 +605,8 @@ mr_status build_batch_graph(mr_ctx* c, const std::vector<Job*>& jobs, const mr_t
   cudaGraph_t g = nullptr;
   MR_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = launch_batch(static_cast<const BatchJob*>(c->batch_desc), (uint32_t)bj.size(), tiles,
-                               static_cast<unsigned long long*>(c->batch_cursor), tp.arr_tile, tp.wc_tile, c->di,
-                               c->stream, &nk);
+                               static_cast<unsigned long long*>(c->batch_cursor), tp.arr_tile, tp.wc_tile,
+                               P.zchunks, c->di, c->stream, &nk);
   if (e == cudaSuccess && !wj.empty())
     e = launch_wordcount_post_multi(static_cast<const wc::JobDev*>(c->batch_wc), wj.data(), (uint32_t)wj.size(),
                                     wc_blocks, wc_records, static_cast<uint8_t*>(c->batch_sort), c->di.sms,
@@ -786,8 +788,8 @@ mr_status serve_pump(mr_ctx* c) {
                                   slot->s));
     MR_CUDA_TRY(batch_prepare());
     MR_CUDA_TRY(launch_batch(static_cast<const BatchJob*>(slot->desc), (uint32_t)P.bj.size(), P.tiles,
-                             static_cast<unsigned long long*>(slot->cursor), c->tune.arr_tile, c->tune.wc_tile, c->di,
-                             slot->s, &c->launches));
+                             static_cast<unsigned long long*>(slot->cursor), c->tune.arr_tile, c->tune.wc_tile,
+                             P.zchunks, c->di, slot->s, &c->launches));
     if (!P.wj.empty())
       MR_CUDA_TRY(launch_wordcount_post_multi(static_cast<const wc::JobDev*>(slot->wcd), P.wj.data(),
                                               (uint32_t)P.wj.size(), P.wc_blocks, P.wc_records,

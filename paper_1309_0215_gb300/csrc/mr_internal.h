@@ -176,11 +176,17 @@ struct BatchJob {
   wc::JobDev wc;       // word count
   uint64_t tile_begin; // first tile index of this job in the batch's tile space
   uint64_t ntiles;
+  uint64_t zchunk0;    // first clearing chunk of this job's container (batch_zero_chunks)
 };
 cudaError_t batch_prepare();
-// Zero the jobs' containers, then run every tile in one persistent launch.
+// Zero the jobs' containers (total_zchunks chunks, see batch_zero_chunks),
+// then run every tile in one persistent launch.
 cudaError_t launch_batch(const BatchJob* jobs_dev, uint32_t njobs, uint64_t total_tiles, unsigned long long* cursor,
-                         uint64_t arr_tile, uint64_t wc_tile, const DevInfo& di, cudaStream_t s, uint64_t* nk);
+                         uint64_t arr_tile, uint64_t wc_tile, uint64_t total_zchunks, const DevInfo& di,
+                         cudaStream_t s, uint64_t* nk);
 uint64_t batch_tiles_for(uint32_t kind, uint64_t n, uint64_t arr_tile, uint64_t wc_tile);
+// Chunks of BATCH_ZCHUNK bytes that clearing the job's container takes.
+constexpr uint64_t BATCH_ZCHUNK = 64 * 1024;
+uint64_t batch_zero_chunks(uint32_t kind, uint64_t wc_cap);
 
 }  // namespace mrgb
