@@ -107,10 +107,13 @@ typedef enum {
 typedef enum {
   MR_RUN_PLAIN = 0,       /* one launch sequence per job, in submission order */
   MR_RUN_BATCHED = 1,     /* all pending array/hash jobs in one persistent launch */
-  MR_RUN_CONCURRENT = 2   /* one launch sequence per job; the jobs of the run
-                           * (independent by construction) run concurrently on
-                           * internal streams forked from and joined back into
-                           * the context stream */
+  MR_RUN_CONCURRENT = 2   /* the jobs of the run (independent by construction)
+                           * run concurrently: 2 to 8 shared-memory RGB
+                           * histograms and int8 regressions as one fused
+                           * launch on the context stream (each job's kernel
+                           * time is that launch's); otherwise one launch
+                           * sequence per job on internal streams forked from
+                           * and joined back into the context stream */
 } mr_mode;
 
 typedef enum {

@@ -28,9 +28,10 @@ namespace {
 using namespace arr;
 constexpr int HIST_THREADS = 1024;
 
-__global__ void __launch_bounds__(HIST_THREADS, 1)
-hist_smem_kernel(const uint8_t* __restrict__ in, uint64_t n, unsigned long long* __restrict__ bins) {
-  extern __shared__ uint32_t hs[];
+// One CTA's share of a histogram job (the grid strides over 1536-byte
+// chunks): local array hs in shared memory, merged into bins at the end.
+__device__ __forceinline__ void hist_smem_body(const uint8_t* __restrict__ in, uint64_t n,
+                                               unsigned long long* __restrict__ bins, uint32_t* hs) {
   for (int i = threadIdx.x; i < HIST_WORDS; i += blockDim.x) hs[i] = 0;
   __syncthreads();
 
@@ -91,6 +92,12 @@ hist_smem_kernel(const uint8_t* __restrict__ in, uint64_t n, unsigned long long*
   }
 }
 
+__global__ void __launch_bounds__(HIST_THREADS, 1)
+hist_smem_kernel(const uint8_t* __restrict__ in, uint64_t n, unsigned long long* __restrict__ bins) {
+  extern __shared__ uint32_t hs[];
+  hist_smem_body(in, n, bins, hs);
+}
+
 // "Eliminated local arrays": every emit is a 64-bit atomic on the global bins.
 __global__ void hist_global_kernel(const uint8_t* __restrict__ in, uint64_t n, unsigned long long* __restrict__ bins) {
   uint64_t o0 = (16 - ((uintptr_t)in & 15)) & 15;
@@ -147,8 +154,8 @@ __device__ __forceinline__ void block_add_sums(long long (&acc)[5], long long* o
   }
 }
 
-__global__ void __launch_bounds__(LR_THREADS)
-linreg_kernel(const int8_t* __restrict__ in, uint64_t n, long long* __restrict__ sums) {
+// One CTA's share of a regression job (the grid strides over 16-byte words).
+__device__ __forceinline__ void linreg_body(const int8_t* __restrict__ in, uint64_t n, long long* __restrict__ sums) {
   long long acc[5] = {0, 0, 0, 0, 0};
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
@@ -198,6 +205,27 @@ linreg_kernel(const int8_t* __restrict__ in, uint64_t n, long long* __restrict__
   block_add_sums(acc, sums);
 }
 
+__global__ void __launch_bounds__(LR_THREADS)
+linreg_kernel(const int8_t* __restrict__ in, uint64_t n, long long* __restrict__ sums) {
+  linreg_body(in, n, sums);
+}
+
+// Several independent array jobs (shared-memory histograms, regressions) as
+// one launch: every CTA takes its share of each job in turn, so the GPU
+// streams the jobs' inputs back to back, with one launch, one ramp and one
+// tail instead of one per job, and no job's CTAs competing with another's
+// for the SMs and HBM while both run.
+__global__ void __launch_bounds__(HIST_THREADS, 1) array_fused_kernel(ArrayJobs J) {
+  extern __shared__ uint32_t hs[];
+  for (uint32_t i = 0; i < J.n; ++i) {
+    __syncthreads();  // the previous job's merge has read the local array
+    if (J.kind[i] == MR_HIST_RGB8)
+      hist_smem_body(J.in[i], J.bytes[i], static_cast<unsigned long long*>(J.out[i]), hs);
+    else
+      linreg_body(reinterpret_cast<const int8_t*>(J.in[i]), J.bytes[i], static_cast<long long*>(J.out[i]));
+  }
+}
+
 }  // namespace
 
 int hist_smem_bytes() { return HIST_WORDS * 4; }
@@ -218,6 +246,19 @@ cudaError_t launch_hist_smem(const uint8_t* in, uint64_t n, uint64_t* bins, int 
 cudaError_t launch_hist_global(const uint8_t* in, uint64_t n, uint64_t* bins, int grid, cudaStream_t s) {
   if (grid < 1) grid = 1;
   hist_global_kernel<<<grid, 512, 0, s>>>(in, n, reinterpret_cast<unsigned long long*>(bins));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_array_fused(const ArrayJobs& jobs, int grid, cudaStream_t s) {
+  static bool attr_done = false;  // per process; the attribute is per function
+  if (!attr_done) {
+    cudaError_t e =
+        cudaFuncSetAttribute(array_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, HIST_WORDS * 4);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  if (grid < 1) grid = 1;
+  array_fused_kernel<<<grid, HIST_THREADS, HIST_WORDS * 4, s>>>(jobs);
   return cudaGetLastError();
 }
 

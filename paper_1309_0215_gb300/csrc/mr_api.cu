@@ -504,12 +504,52 @@ mr_status enqueue_plain_on(mr_ctx* c, Job* j, cudaStream_t st) {
 mr_status enqueue_plain(mr_ctx* c, Job* j) { return enqueue_plain_on(c, j, c->stream); }
 
 // MR_RUN_CONCURRENT: the jobs of a run are independent (each has its own
-// input, containers and result), so they run concurrently: the first on the
-// context stream, the others round robin on PLAIN_AUX internal streams that
-// wait for the work already on the context stream; the context stream then
-// waits for them, so later work on it (and the next run) sees every job done.
-// Two bandwidth-bound jobs overlap their ramp-up and tail this way.
+// input, containers and result), so they run concurrently.  Two to
+// ARRAY_FUSE_MAX shared-memory histograms and regressions run as one fused
+// launch on the context stream (each CTA takes its share of every job in
+// turn).  Otherwise the first job goes on the context stream and the others
+// round robin on PLAIN_AUX internal streams that wait for the work already
+// on the context stream; the context stream then waits for them, so later
+// work on it (and the next run) sees every job done.  Either way two
+// bandwidth-bound jobs overlap their ramp-up and tail.
+// Array jobs that fit one fused launch: shared-memory histograms and regressions.
+bool array_fusable(const Job* j) {
+  return (j->desc.kind == MR_HIST_RGB8 && j->container != MR_C_GLOBAL_ARRAY) || j->desc.kind == MR_LINREG_I8;
+}
+
+mr_status enqueue_array_fused(mr_ctx* c, const std::vector<Job*>& jobs) {
+  cudaStream_t st = c->stream;
+  ArrayJobs A{};
+  A.n = (uint32_t)jobs.size();
+  uint64_t total = 0;
+  for (size_t i = 0; i < jobs.size(); ++i) {
+    Job* j = jobs[i];
+    if (j->t0) MR_CUDA_TRY(cudaEventRecord(j->t0, st));
+    if (j->kt) j->kt->n = 0;
+    MR_CUDA_TRY(cudaMemsetAsync(j->result, 0, j->desc.kind == MR_HIST_RGB8 ? 768 * 8 : 5 * 8, st));
+    A.kind[i] = (uint32_t)j->desc.kind;
+    A.in[i] = j->in;
+    A.bytes[i] = j->desc.input_bytes;
+    A.out[i] = j->result;
+    total += j->desc.input_bytes;
+  }
+  // every job's kernel time is the fused launch's
+  for (Job* j : jobs) MR_CUDA_TRY(kt_begin(j->kt, st));
+  MR_CUDA_TRY(launch_array_fused(A, grid_for(c, total, 1536ull * 32 * 4, 1), st));
+  ++c->launches;
+  for (Job* j : jobs) {
+    MR_CUDA_TRY(kt_end(j->kt, st));
+    if (j->t1) MR_CUDA_TRY(cudaEventRecord(j->t1, st));
+    MR_CUDA_TRY(cudaEventRecord(j->done, st));
+    j->state = JOB_ENQUEUED;
+  }
+  return MR_OK;
+}
+
 mr_status enqueue_concurrent(mr_ctx* c, const std::vector<Job*>& jobs) {
+  bool fuse = jobs.size() >= 2 && jobs.size() <= (size_t)ARRAY_FUSE_MAX;
+  for (const Job* j : jobs) fuse = fuse && array_fusable(j);
+  if (fuse) return enqueue_array_fused(c, jobs);
   if (jobs.size() <= 1) {
     for (Job* j : jobs) {
       mr_status st = enqueue_plain(c, j);

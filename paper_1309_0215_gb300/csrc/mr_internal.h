@@ -37,6 +37,17 @@ cudaError_t launch_hist_smem(const uint8_t* in, uint64_t n, uint64_t* bins, int 
 cudaError_t launch_hist_global(const uint8_t* in, uint64_t n, uint64_t* bins, int grid, cudaStream_t s);
 // int8 regression sums; sums must be zeroed before the launch.
 cudaError_t launch_linreg(const int8_t* in, uint64_t n, int64_t* sums, int grid, cudaStream_t s);
+// Independent array jobs run as one launch (shared-memory histograms and
+// regressions; at most ARRAY_FUSE_MAX).
+constexpr int ARRAY_FUSE_MAX = 8;
+struct ArrayJobs {
+  uint32_t n;
+  uint32_t kind[ARRAY_FUSE_MAX];
+  const uint8_t* in[ARRAY_FUSE_MAX];
+  uint64_t bytes[ARRAY_FUSE_MAX];
+  void* out[ARRAY_FUSE_MAX];
+};
+cudaError_t launch_array_fused(const ArrayJobs& jobs, int grid, cudaStream_t s);
 
 int hist_smem_bytes();         // dynamic shared memory the smem histogram needs
 int hist_block_threads();

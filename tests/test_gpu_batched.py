@@ -156,3 +156,36 @@ def test_batched_edge_jobs(mr):
     c.run(mr.RUN_BATCHED)
     assert [c.fetch(j) for j in ids] == exp
     c.close()
+
+
+@pytest.mark.parametrize("njobs", [2, 5, 8, 9])
+def test_concurrent_array_jobs_fused_equal_oracle(mr, njobs):
+    """Two to eight shared-memory histograms and regressions in one
+    MR_RUN_CONCURRENT run take one fused launch (nine fall back to one launch
+    sequence per job): unaligned slices, ragged lengths, an empty job and a
+    tiny one; every result equals the oracle's, in two runs on one context."""
+    import torch
+    rng = np.random.default_rng(70 + njobs)
+    px = synth.hist_rgb8(2_000_003, seed=71)
+    xy = synth.linreg_i8(1_500_001, seed=72)
+    dp, dx = torch.from_numpy(px).cuda(), torch.from_numpy(xy).cuda()
+    specs = []
+    for i in range(njobs):
+        if i % 2 == 0:
+            n = 3 * int(rng.integers(0, 2_000_000 - 2)) if i else 0
+            off = 3 * int(rng.integers(0, 2))
+            specs.append((mr.HIST_RGB8, px[off: off + n], dp[off: off + n]))
+        else:
+            n = 2 * int(rng.integers(1, 1_500_000 - 5)) if i != 3 else 2
+            off = 2 * int(rng.integers(0, 3)) + 1  # odd byte offsets: unaligned pairs
+            specs.append((mr.LINREG_I8, xy[off: off + n], dx[off: off + n]))
+    c = mr.Context()
+    for rep in range(2):
+        ids = [c.add_job(k, d) for k, _, d in specs]
+        c.run(mr.RUN_CONCURRENT)
+        for (k, h, _), j in zip(specs, ids):
+            got = np.frombuffer(c.fetch(j), dtype=np.uint64 if k == mr.HIST_RGB8 else np.int64)
+            exp = oracle.hist_rgb8(h).astype(np.uint64) if k == mr.HIST_RGB8 else oracle.linreg_i8(h).astype(np.int64)
+            assert np.array_equal(got, exp), (k, len(h))
+            c.release(j)
+    c.close()
