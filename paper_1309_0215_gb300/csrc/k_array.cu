@@ -83,7 +83,9 @@ __device__ __forceinline__ void hist_smem_body(const uint8_t* __restrict__ in, u
     }
   }
   __syncthreads();
-  // merge the local array into the global array
+  // merge the local array into the global array (in the fused launch, once
+  // the kernel that clears the results has finished)
+  pdl_wait();
   for (int bin = threadIdx.x; bin < HIST_BINS; bin += blockDim.x) {
     unsigned long long s = 0;
 #pragma unroll 8
@@ -202,6 +204,7 @@ __device__ __forceinline__ void linreg_body(const int8_t* __restrict__ in, uint6
       acc[0] += x; acc[1] += y; acc[2] += x * x; acc[3] += y * y; acc[4] += x * y;
     }
   }
+  pdl_wait();  // (fused launch: the results are cleared)
   block_add_sums(acc, sums);
 }
 
@@ -214,7 +217,18 @@ linreg_kernel(const int8_t* __restrict__ in, uint64_t n, long long* __restrict__
 // one launch: every CTA takes its share of each job in turn, so the GPU
 // streams the jobs' inputs back to back, with one launch, one ramp and one
 // tail instead of one per job, and no job's CTAs competing with another's
-// for the SMs and HBM while both run.
+// for the SMs and HBM while both run.  The jobs' results are cleared by
+// array_zero_kernel just before; the fused kernel is a programmatic dependent
+// launch that reads and combines its inputs at once and waits for the
+// clearing only before its first global add.
+__global__ void array_zero_kernel(ArrayJobs J) {
+  for (uint32_t i = 0; i < J.n; ++i) {
+    unsigned long long* o = static_cast<unsigned long long*>(J.out[i]);
+    const uint32_t words = J.kind[i] == MR_HIST_RGB8 ? 768u : 5u;
+    for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) o[w] = 0ull;
+  }
+}
+
 __global__ void __launch_bounds__(HIST_THREADS, 1) array_fused_kernel(ArrayJobs J) {
   extern __shared__ uint32_t hs[];
   for (uint32_t i = 0; i < J.n; ++i) {
@@ -258,8 +272,10 @@ cudaError_t launch_array_fused(const ArrayJobs& jobs, int grid, cudaStream_t s) 
     attr_done = true;
   }
   if (grid < 1) grid = 1;
-  array_fused_kernel<<<grid, HIST_THREADS, HIST_WORDS * 4, s>>>(jobs);
-  return cudaGetLastError();
+  array_zero_kernel<<<1, 256, 0, s>>>(jobs);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_pdl(array_fused_kernel, dim3(grid), dim3(HIST_THREADS), (size_t)HIST_WORDS * 4, s, jobs);
 }
 
 cudaError_t launch_linreg(const int8_t* in, uint64_t n, int64_t* sums, int grid, cudaStream_t s) {
