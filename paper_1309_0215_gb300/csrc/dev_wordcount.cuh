@@ -514,8 +514,11 @@ __device__ __forceinline__ bool cta_add(TT& T, const Tok& t) {
 }
 
 // Queue the round's misses (m: this lane has one); once 32 are queued, the
-// warp inserts the oldest 32 into the global container.  qn / qhd: queued
-// entries and queue head, warp-uniform.
+// warp inserts the oldest 32 into the global container (WIDTH table slots
+// loaded per probe step; the batch kernel, whose many small jobs keep the
+// global tables in L2, is faster with one).  qn / qhd: queued entries and
+// queue head, warp-uniform.
+template <int WIDTH = 2>
 __device__ __forceinline__ void mq_push(const JobDev& J, MapWarp& W, bool m, const Tok& t, uint32_t& qn,
                                         uint32_t& qhd) {
   const int lane = threadIdx.x & 31;
@@ -531,7 +534,7 @@ __device__ __forceinline__ void mq_push(const JobDev& J, MapWarp& W, bool m, con
   if (qn >= 32) {
     __syncwarp();
     const uint32_t q = (qhd + (uint32_t)lane) & (MQ - 1);
-    global_insert(J, W.qw0[q], W.qw1[q], W.qh[q], 1);
+    global_insert<WIDTH>(J, W.qw0[q], W.qw1[q], W.qh[q], 1);
     qhd = (qhd + 32) & (MQ - 1);
     qn -= 32;
   }

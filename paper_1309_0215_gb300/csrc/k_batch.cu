@@ -263,7 +263,7 @@ batch_kernel(const BatchJob* __restrict__ jobs, uint32_t njobs, uint64_t total_t
             tk = wc::read_token(s_jd.in, s_jd.n, base, W, W.starts[i]);
             m = !wc::cta_add(T, tk);
           }
-          wc::mq_push(s_jd, W, m, tk, qn, qhd);
+          wc::mq_push<1>(s_jd, W, m, tk, qn, qhd);
           __syncwarp();
         }
       }
