@@ -1095,30 +1095,38 @@ constexpr int WS_THREADS = 1024;
 constexpr int WS_WARPS = WS_THREADS / 32;
 constexpr uint32_t WS_WIN = 4096;  // points per window (16-bit positions)
 constexpr int WS_UNROLL = 8;       // points in flight per warp
-__host__ __device__ constexpr uint64_t ws_smem_bytes(uint64_t k) {
-  return k * 64 * 8 + 3 * k * 4 + 3 * (uint64_t)WS_WIN * 2;
+__host__ __device__ constexpr uint64_t ws_smem_bytes(uint64_t k, uint64_t d) {
+  return k * d * 8 + 3 * k * 4 + 3 * (uint64_t)WS_WIN * 2;
 }
-__device__ __forceinline__ void ws_flush(long long* S, uint32_t c, int lane, int h0, int l0, int h1, int l1) {
-  unsigned long long* p = reinterpret_cast<unsigned long long*>(S + (uint64_t)c * 64 + 2 * lane);
-  atomicAdd(p, (unsigned long long)((long long)h0 * (1ll << 20) + (long long)l0));
-  atomicAdd(p + 1, (unsigned long long)((long long)h1 * (1ll << 20) + (long long)l1));
+// add a run's split sums of dimensions j0 and j1 (when below d) into
+// cluster c's int64 sums
+__device__ __forceinline__ void ws_flush(long long* S, uint32_t c, uint32_t d, uint32_t j0, uint32_t j1, int h0,
+                                         int l0, int h1, int l1) {
+  unsigned long long* p = reinterpret_cast<unsigned long long*>(S + (uint64_t)c * d);
+  if (j0 < d) atomicAdd(p + j0, (unsigned long long)((long long)h0 * (1ll << 20) + (long long)l0));
+  if (j1 < d) atomicAdd(p + j1, (unsigned long long)((long long)h1 * (1ll << 20) + (long long)l1));
 }
+// D64: D = 64 with 8-byte-aligned rows (lane l reads dimensions 2l, 2l + 1
+// with one 8-byte load); otherwise D <= 64, lane l dimensions l and l + 32.
+template <bool D64>
 __global__ void __launch_bounds__(WS_THREADS, 1) km_window_sum_kernel(const float* __restrict__ x, uint32_t n,
-                                                                      uint32_t k, const int32_t* __restrict__ assign,
+                                                                      uint32_t d, uint32_t k,
+                                                                      const int32_t* __restrict__ assign,
                                                                       const int* shift, long long* __restrict__ part,
                                                                       unsigned long long* counts) {
   pdl_wait();
   extern __shared__ __align__(16) unsigned char ws_sm[];
   long long* S = reinterpret_cast<long long*>(ws_sm);
-  uint32_t* hc = reinterpret_cast<uint32_t*>(S + (uint64_t)k * 64);
+  uint32_t* hc = reinterpret_cast<uint32_t*>(S + (uint64_t)k * d);
   uint32_t* off = hc + k;
   uint32_t* C = off + k;
   uint16_t* wid = reinterpret_cast<uint16_t*>(C + k);
   uint16_t* perm = wid + WS_WIN;
   uint16_t* pcl = perm + WS_WIN;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (uint64_t i = threadIdx.x; i < (uint64_t)k * 64; i += WS_THREADS) S[i] = 0;
+  for (uint64_t i = threadIdx.x; i < (uint64_t)k * d; i += WS_THREADS) S[i] = 0;
   for (uint32_t i = threadIdx.x; i < k; i += WS_THREADS) C[i] = 0;
+  const uint32_t j0 = D64 ? 2 * (uint32_t)lane : (uint32_t)lane, j1 = D64 ? j0 + 1 : j0 + 32;
   const uint64_t per = ((uint64_t)n + gridDim.x - 1) / gridDim.x;
   const uint64_t p0 = (uint64_t)blockIdx.x * per;
   const uint64_t p1 = p0 + per < (uint64_t)n ? p0 + per : (uint64_t)n;
@@ -1171,7 +1179,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) km_window_sum_kernel(const floa
     const uint32_t q0 = (uint32_t)warp * pw;
     const uint32_t q1 = q0 + pw < nr ? q0 + pw : nr;
     if (q0 < q1) {
-      const float2* X = reinterpret_cast<const float2*>(x + w0 * 64) + lane;
+      const float* X = x + w0 * d;
       uint32_t cur = pcl[q0];
       int h0 = 0, l0 = 0, h1 = 0, l1 = 0;
       for (uint32_t q = q0; q < q1; q += WS_UNROLL) {
@@ -1182,12 +1190,18 @@ __global__ void __launch_bounds__(WS_THREADS, 1) km_window_sum_kernel(const floa
           const uint32_t qq = q + (uint32_t)u;
           const bool ok = qq < q1;
           cl[u] = ok ? pcl[qq] : cur;
-          v[u] = ok ? __ldg(X + (uint64_t)perm[qq] * 32) : make_float2(0.f, 0.f);
+          const float* row = X + (uint64_t)(ok ? perm[qq] : 0) * d;
+          if (D64) {
+            v[u] = ok ? __ldg(reinterpret_cast<const float2*>(row) + lane) : make_float2(0.f, 0.f);
+          } else {
+            v[u].x = ok && j0 < d ? __ldg(row + j0) : 0.f;
+            v[u].y = ok && j1 < d ? __ldg(row + j1) : 0.f;
+          }
         }
 #pragma unroll
         for (int u = 0; u < WS_UNROLL; ++u) {
           if (cl[u] != cur) {  // warp-uniform: the run of cluster cur ended
-            ws_flush(S, cur, lane, h0, l0, h1, l1);
+            ws_flush(S, cur, d, j0, j1, h0, l0, h1, l1);
             h0 = l0 = h1 = l1 = 0;
             cur = cl[u];
           }
@@ -1200,12 +1214,12 @@ __global__ void __launch_bounds__(WS_THREADS, 1) km_window_sum_kernel(const floa
           l1 += b;
         }
       }
-      ws_flush(S, cur, lane, h0, l0, h1, l1);
+      ws_flush(S, cur, d, j0, j1, h0, l0, h1, l1);
     }
   }
   __syncthreads();
-  long long* P = part + (uint64_t)blockIdx.x * k * 64;
-  for (uint64_t i = threadIdx.x; i < (uint64_t)k * 64; i += WS_THREADS) P[i] = S[i];
+  long long* P = part + (uint64_t)blockIdx.x * k * d;
+  for (uint64_t i = threadIdx.x; i < (uint64_t)k * d; i += WS_THREADS) P[i] = S[i];
   for (uint32_t i = threadIdx.x; i < k; i += WS_THREADS)
     if (C[i]) atomicAdd(counts + i, (unsigned long long)C[i]);
 }
@@ -1390,11 +1404,13 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
         return e;
     }
   }
-  // the window-sorted update: D = 64, 8-byte-aligned points, sums and window buffers in shared memory
-  const bool wsum = local && d == 64 && (reinterpret_cast<uintptr_t>(x) & 7) == 0 &&
-                    ws_smem_bytes(k) <= (uint64_t)di.smem_optin;
-  if (wsum && (e = cudaFuncSetAttribute(km_window_sum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)ws_smem_bytes(k))) != cudaSuccess)
+  // the window-sorted update: D <= 64, sums and window buffers in shared
+  // memory (8-byte loads for D = 64 with 8-byte-aligned points)
+  const bool wsum = local && d <= 64 && ws_smem_bytes(k, d) <= (uint64_t)di.smem_optin;
+  const bool ws64 = d == 64 && (reinterpret_cast<uintptr_t>(x) & 7) == 0;
+  if (wsum && (e = cudaFuncSetAttribute(ws64 ? km_window_sum_kernel<true> : km_window_sum_kernel<false>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem_bytes(k, d))) !=
+                  cudaSuccess)
     return e;
   uint32_t ls_grid = (uint32_t)di.sms < LS_MAX_CTAS ? (uint32_t)di.sms : LS_MAX_CTAS;
   if ((uint64_t)ls_grid * 1024 > n) ls_grid = (uint32_t)((n + 1023) / 1024);
@@ -1465,8 +1481,9 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
     *nk += 2;  // re-check, FP64 stage
     if (local) {  // update with local arrays
       if (wsum)
-        e = launch_pdl(km_window_sum_kernel, dim3(ls_grid), dim3(WS_THREADS), (size_t)ws_smem_bytes(k), s, x, n, k,
-                       (const int32_t*)b.assign, (const int*)shift, b.part, b.counts);
+        e = launch_pdl(ws64 ? km_window_sum_kernel<true> : km_window_sum_kernel<false>, dim3(ls_grid),
+                       dim3(WS_THREADS), (size_t)ws_smem_bytes(k, d), s, x, n, d, k, (const int32_t*)b.assign,
+                       (const int*)shift, b.part, b.counts);
       else if (lp_rows)
         e = launch_pdl(d == 64 ? km_local_sum_pipe_kernel<true> : km_local_sum_pipe_kernel<false>, dim3(ls_grid),
                        dim3(LS_THREADS), (size_t)lp_bytes, s, x, n, d, k, (const int32_t*)b.assign, (const int*)shift,

@@ -57,8 +57,9 @@ def _km_check(mr, ctx, x, init, iters, precision):
 def test_kmeans_wait_gives_up_then_context_recovers(mr, precision):
     """0 polls: the first bounded wait of the pipelined kernels gives up (the
     tensor-core pass for precision 1 and 2; for 0 the bulk-copy update, which
-    runs for D other than 64: D = 64 takes the window-sorted update)."""
-    d = 48 if precision == 0 else 64
+    runs for D > 64 with rows of a multiple of 4 floats: D <= 64 takes the
+    window-sorted update)."""
+    d = 96 if precision == 0 else 64
     x, _, _ = synth.kmeans_points(12_000, d, 64, seed=61 + precision)
     init = synth.kmeans_init(x, 64, seed=62)
     ctx = mr.Context()
@@ -73,11 +74,11 @@ def test_kmeans_wait_gives_up_then_context_recovers(mr, precision):
     ctx.close()
 
 
-def test_kmeans_fp32_d64_path_has_no_waits(mr):
-    """The FP32 pass and the window-sorted update (D = 64) wait on nothing, so
-    a wait limit of 0 polls changes nothing there: the job completes and
+def test_kmeans_fp32_window_path_has_no_waits(mr):
+    """The FP32 pass and the window-sorted update (D <= 64) wait on nothing,
+    so a wait limit of 0 polls changes nothing there: the job completes and
     equals the oracle."""
-    x, _, _ = synth.kmeans_points(12_000, 64, 64, seed=64)
+    x, _, _ = synth.kmeans_points(12_000, 48, 64, seed=64)
     init = synth.kmeans_init(x, 64, seed=62)
     ctx = mr.Context()
     ctx.set_option(mr.OPT_WAIT_POLLS, 0)

@@ -61,6 +61,8 @@ def _run_ctx(mr, ctx, dx, cur, iters, precision):
     (6_000, 128, 260, 2),   # K*D sums too large for shared memory: the sorted update
     (9_001, 64, 300, 2),    # window-sorted update with K not a multiple of 32
     (5_000, 64, 1, 2),      # window-sorted update, one cluster
+    (6_000, 8, 3_000, 2),   # K x D sums fit, but not beside the window buffers: the row-pipelined update
+    (3_001, 67, 20, 2),     # D > 64 and not a multiple of 4: the plain local-array update
     (777, 3, 1, 2),         # K = 1: the global mean
     (64, 8, 64, 1),         # every point its own centroid
 ])
@@ -76,8 +78,8 @@ def test_kmeans_fp32_vs_oracle(mr, n, d, k, iters):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_kmeans_points_not_16_byte_aligned(mr, precision):
-    """Points 4 bytes into a buffer: the update cannot stream them with bulk
-    copies and takes the plain local-array kernel."""
+    """Points 4 bytes into a buffer: no bulk copies and no 8-byte loads; the
+    window-sorted update reads them with 4-byte loads."""
     import torch
     x, _, _ = synth.kmeans_points(5000, 64, 32, seed=51)
     init = synth.kmeans_init(x, 32, seed=52)
@@ -208,15 +210,15 @@ def test_kmeans_many_tiles_per_cta_teacher_forced(mr, precision):
     ctx.close()
 
 
-@pytest.mark.parametrize("k", [256, 17])
-def test_kmeans_window_update_many_windows(mr, k):
-    """The D = 64 update sorts each window of 4,096 points by cluster and sums
-    runs in registers.  Two CTAs: each walks two full windows and a ragged
-    third (10,001 points each), so the window loop, the per-window histogram
-    and scatter and the run flushes across windows are all exercised, against
-    the oracle's update from the same assignment."""
+@pytest.mark.parametrize("d,k", [(64, 256), (64, 17), (48, 256), (37, 17), (33, 100), (8, 64), (1, 5)])
+def test_kmeans_window_update_many_windows(mr, d, k):
+    """The update for D <= 64 sorts each window of 4,096 points by cluster and
+    sums runs in registers (lanes past D idle).  Two CTAs: each walks two full
+    windows and a ragged third (10,001 points each), so the window loop, the
+    per-window histogram and scatter and the run flushes across windows are
+    all exercised, against the oracle's update from the same assignment."""
     import torch
-    x, _, _ = synth.kmeans_points(20_002, 64, min(k, 64), seed=71 + k)
+    x, _, _ = synth.kmeans_points(20_002, d, min(k, 64), seed=71 + k + d)
     dx = torch.from_numpy(x).cuda()
     cur = synth.kmeans_init(x, k, seed=72)
     ctx = mr.Context()
