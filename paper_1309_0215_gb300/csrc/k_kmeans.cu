@@ -434,8 +434,8 @@ __global__ void km_recheck_fp64_kernel(const float* __restrict__ x, uint32_t d, 
 }
 
 // The same re-check with the centroids staged in shared memory (row stride
-// D + 1 floats: lanes reading different rows at one column hit different
-// banks).  Lane l owns centroids l, l+32, ... (at most KLANE of them): one
+// D or D + 1 floats, whichever is odd: lanes reading different rows at one
+// column hit different banks).  Lane l owns centroids l, l+32, ... (at most KLANE of them): one
 // pass computes their FP32 distances into registers and the warp takes the
 // minimum; a point with more than one candidate within the bound goes to
 // the FP64 stage's list (deferred, ndef).
@@ -450,14 +450,14 @@ __global__ void km_recheck_fp64_smem_kernel(const float* __restrict__ x, uint32_
                                             int32_t* assign, unsigned long long* stat, uint32_t* deferred,
                                             uint32_t* ndef) {
   pdl_wait();
-  extern __shared__ float cs[];  // [k][d + 1]
+  extern __shared__ float cs[];  // [k][d | 1]
   const uint32_t nf = *nflag;
   const uint32_t per = max(RC_MIN, (nf + gridDim.x - 1) / gridDim.x);
   const uint64_t f_lo = (uint64_t)blockIdx.x * per;
   const uint64_t f_hi = f_lo + per < nf ? f_lo + per : nf;
   if (blockIdx.x == 0 && threadIdx.x == 0 && stat) atomicAdd(stat, (unsigned long long)nf);
   if (f_lo >= nf) return;  // no work for this CTA: no staging either
-  const uint32_t ld = d + 1;
+  const uint32_t ld = d | 1;
   for (uint32_t t = threadIdx.x; t < k * d; t += blockDim.x) cs[(t / d) * ld + (t % d)] = c[t];
   __syncthreads();
   const int lane = threadIdx.x & 31;
