@@ -38,6 +38,7 @@ constexpr int TP = 64;            // points per tile (8 per warp)
 constexpr int KC_MAX = 256;       // centroids per chunk (8 per lane)
 constexpr int DC_MAX = 64;        // dims per chunk
 constexpr int CS_LD = KC_MAX + 1;  // staged centroid row stride: the transposing stores hit distinct banks
+constexpr int XS_LD = TP + 4;      // staged point row stride (16-byte rows; see the point loads)
 
 // Running top three distances (the two smallest with their indices);
 // between equal distances the lower index ranks first.
@@ -141,11 +142,12 @@ km_assign_fp32_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const
   const int dc = d < DC_MAX ? (int)d : DC_MAX;
   const int kc = k < KC_MAX ? (int)k : KC_MAX;
   float* cs = km_sm;              // [dc][CS_LD]
-  float* xs = km_sm + DC_MAX * CS_LD;  // [dc][TP]
+  float* xs = km_sm + DC_MAX * CS_LD;  // [dc][XS_LD]
   __shared__ float nx_s[TP];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t npts = idx ? *nidx : n;
   const bool resident = k <= KC_MAX && d <= DC_MAX;
+  const bool vec4 = (d & 3) == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0;
   const float cmax = __uint_as_float(*cmax_bits);
   const float eps = 1.01f * (float)(d + 8) * 5.9604645e-8f;  // 2^-24
   if (idx && blockIdx.x == 0 && threadIdx.x == 0 && stat) atomicAdd(stat, (unsigned long long)npts);
@@ -184,23 +186,39 @@ km_assign_fp32_kernel(const float* __restrict__ x, uint32_t n, uint32_t d, const
       for (uint32_t d0 = 0; d0 < d; d0 += DC_MAX) {
         __syncthreads();
         if (!resident) load_c(k0, d0);
-        for (int t = threadIdx.x; t < TP * dc; t += KM_THREADS) {
-          const int pp = t / dc, dd = t % dc;
-          const uint32_t pi = p0 + pp, dg = d0 + dd;
-          float v = 0.f;
-          if (pi < npts && dg < d) {
+        const int dlim = (int)((d - d0) < (uint32_t)dc ? (d - d0) : (uint32_t)dc);
+        // A warp item is 16 points x 8 dims: lane l loads point 16 (wi % 4) +
+        // l % 16, dims 8 (wi / 4) + 4 (l / 16) .. + 3 (one 16-byte load when
+        // rows allow), and stores them transposed; with the row stride TP + 4
+        // the 32 lanes of each store hit 32 banks.
+        for (int wi = warp; wi < (TP / 16) * ((dc + 7) / 8); wi += KM_THREADS / 32) {
+          const int pp = 16 * (wi % (TP / 16)) + (lane & 15);
+          const int dd = 8 * (wi / (TP / 16)) + 4 * (lane >> 4);
+          const uint32_t pi = p0 + pp;
+          float v[4] = {0.f, 0.f, 0.f, 0.f};
+          if (pi < npts) {
             const uint32_t p = idx ? idx[pi] : pi;
-            v = x[(uint64_t)p * d + dg];
+            const float* row = x + (uint64_t)p * d + d0 + dd;
+            if (vec4 && dd + 4 <= dlim) {
+              const float4 q = __ldg(reinterpret_cast<const float4*>(row));
+              v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+            } else {
+#pragma unroll
+              for (int m = 0; m < 4; ++m)
+                if (dd + m < dlim) v[m] = __ldg(row + m);
+            }
           }
-          xs[dd * TP + pp] = v;
+#pragma unroll
+          for (int m = 0; m < 4; ++m)
+            if (dd + m < dc) xs[(dd + m) * XS_LD + pp] = v[m];
         }
         __syncthreads();
-        const int dlim = (int)((d - d0) < (uint32_t)dc ? (d - d0) : (uint32_t)dc);
         if (k0 == 0 && threadIdx.x < TP)
-          for (int dd = 0; dd < dlim; ++dd) nxacc = fmaf(xs[dd * TP + threadIdx.x], xs[dd * TP + threadIdx.x], nxacc);
+          for (int dd = 0; dd < dlim; ++dd)
+            nxacc = fmaf(xs[dd * XS_LD + threadIdx.x], xs[dd * XS_LD + threadIdx.x], nxacc);
         for (int dd = 0; dd < dlim; ++dd) {
-          const float4 xa = *reinterpret_cast<const float4*>(&xs[dd * TP + warp * 8]);
-          const float4 xb = *reinterpret_cast<const float4*>(&xs[dd * TP + warp * 8 + 4]);
+          const float4 xa = *reinterpret_cast<const float4*>(&xs[dd * XS_LD + warp * 8]);
+          const float4 xb = *reinterpret_cast<const float4*>(&xs[dd * XS_LD + warp * 8 + 4]);
           const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
           float cv[8];
 #pragma unroll
@@ -1368,7 +1386,7 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
     km_scale_kernel<<<1, 1, 0, s>>>(b.maxabs, n, shift);
     *nk += 2;
   }
-  const int asm_bytes = (DC_MAX * CS_LD + DC_MAX * TP) * 4;
+  const int asm_bytes = (DC_MAX * CS_LD + DC_MAX * XS_LD) * 4;
   if ((e = cudaFuncSetAttribute(km_assign_fp32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 asm_bytes)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(km_assign_fp32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
