@@ -122,14 +122,14 @@ struct mr_ctx {
     void* sort = nullptr;
     uint64_t sort_bytes = 0;
     void* cursor = nullptr;
-    // plain-only requests (k-means, large-key histogram, Bloom) of a
-    // micro-batch run on these streams, round robin, so they overlap
-    static constexpr int AUX = 4;
-    cudaStream_t aux[AUX] = {};
-    cudaEvent_t aux_done[AUX] = {};
   };
   static constexpr int SERVE_SLOTS = 4;
   Slot slots[SERVE_SLOTS];
+  // plain-only requests (k-means, large-key histogram, Bloom) need no slot:
+  // they run on these streams, round robin, beside the micro-batches
+  static constexpr int SERVE_AUX = 8;
+  cudaStream_t serve_aux[SERVE_AUX] = {};
+  uint32_t serve_aux_next = 0;
   std::vector<Job*> serve_pending;  // admitted, waiting for a free slot
   cudaEvent_t serve_ready = nullptr;
   // concurrent runs: jobs after the first run on these streams,
@@ -766,23 +766,52 @@ mr_status enqueue_batched(mr_ctx* c, std::vector<Job*>& jobs) {
   return MR_OK;
 }
 
-// Serving: launch every admitted request that is not running yet as one
-// micro-batch on a slot whose previous micro-batch has finished.  Requests
-// that arrive while the GPU is busy are picked up as soon as a slot frees, so
-// successive micro-batches overlap on the device.  Returns MR_OK also when no
-// slot is free (the requests stay queued).
+// Serving: plain-only requests (k-means, large-key histogram, Bloom) are
+// launched at once on the auxiliary streams, round robin; the other admitted
+// requests that are not running yet go as one micro-batch on a slot whose
+// previous micro-batch has finished.  Requests that arrive while the GPU is
+// busy are picked up as soon as a slot frees, so successive micro-batches
+// overlap on the device.  Slot streams have the higher stream priority, so
+// when SMs free up the block scheduler serves the micro-batches (most
+// requests, each short) before the next blocks of a long k-means.  Returns
+// MR_OK also when no slot is free (the requests stay queued).
 mr_status serve_pump(mr_ctx* c) {
+  if (c->serve_pending.empty()) return MR_OK;
+  if (!c->serve_aux[0]) {
+    int least = 0, greatest = 0;
+    MR_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    for (auto& sl : c->slots) {
+      MR_CUDA_TRY(cudaStreamCreateWithPriority(&sl.s, cudaStreamNonBlocking, greatest));
+      MR_CUDA_TRY(cudaEventCreateWithFlags(&sl.busy, cudaEventDisableTiming));
+    }
+    for (auto& a : c->serve_aux) MR_CUDA_TRY(cudaStreamCreateWithPriority(&a, cudaStreamNonBlocking, least));
+  }
+  // every stream used here must see the submit-time copies and clears on the context stream
+  if (!c->serve_ready) MR_CUDA_TRY(cudaEventCreateWithFlags(&c->serve_ready, cudaEventDisableTiming));
+  MR_CUDA_TRY(cudaEventRecord(c->serve_ready, c->stream));
+  std::vector<Job*> arr;
+  for (size_t i = 0; i < c->serve_pending.size(); ++i) {
+    Job* j = c->serve_pending[i];
+    if (!plain_only(j->desc.kind)) {
+      arr.push_back(j);
+      continue;
+    }
+    cudaStream_t as = c->serve_aux[c->serve_aux_next++ % mr_ctx::SERVE_AUX];
+    cudaError_t e = cudaStreamWaitEvent(as, c->serve_ready, 0);
+    mr_status st = e == cudaSuccess ? enqueue_plain_on(c, j, as) : MR_ECUDA;
+    if (e != cudaSuccess) set_last_error("cudaStreamWaitEvent", e);
+    if (st) {
+      // the requests not launched yet stay queued
+      std::vector<Job*> left(arr);
+      left.insert(left.end(), c->serve_pending.begin() + (ptrdiff_t)i, c->serve_pending.end());
+      c->serve_pending.swap(left);
+      return st;
+    }
+  }
+  c->serve_pending.swap(arr);
   if (c->serve_pending.empty()) return MR_OK;
   mr_ctx::Slot* slot = nullptr;
   for (auto& sl : c->slots) {
-    if (!sl.s) {
-      MR_CUDA_TRY(cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking));
-      MR_CUDA_TRY(cudaEventCreateWithFlags(&sl.busy, cudaEventDisableTiming));
-      for (int a = 0; a < mr_ctx::Slot::AUX; ++a) {
-        MR_CUDA_TRY(cudaStreamCreateWithFlags(&sl.aux[a], cudaStreamNonBlocking));
-        MR_CUDA_TRY(cudaEventCreateWithFlags(&sl.aux_done[a], cudaEventDisableTiming));
-      }
-    }
     if (!sl.used) {
       slot = &sl;
       break;
@@ -800,60 +829,38 @@ mr_status serve_pump(mr_ctx* c) {
   if (!slot) return MR_OK;
   std::vector<Job*> jobs;
   jobs.swap(c->serve_pending);
-  std::vector<Job*> arr;
-  for (Job* j : jobs)
-    if (!plain_only(j->desc.kind)) arr.push_back(j);
-  // the slot stream must see the submit-time copies and clears on the context stream
-  if (!c->serve_ready) MR_CUDA_TRY(cudaEventCreateWithFlags(&c->serve_ready, cudaEventDisableTiming));
-  MR_CUDA_TRY(cudaEventRecord(c->serve_ready, c->stream));
   MR_CUDA_TRY(cudaStreamWaitEvent(slot->s, c->serve_ready, 0));
   for (Job* j : jobs)
     if (j->t0) MR_CUDA_TRY(cudaEventRecord(j->t0, slot->s));
-  if (!arr.empty()) {
-    BatchPlan P;
-    plan_batch(arr, c->tune, P);
-    mr_status st = ensure_scratch(c, &slot->desc, &slot->desc_bytes, P.bj.size() * sizeof(BatchJob));
-    if (!st) st = ensure_scratch(c, &slot->wcd, &slot->wcd_bytes, P.wj.size() * sizeof(wc::JobDev));
-    if (!st && !P.wj.empty()) st = ensure_scratch(c, &slot->sort, &slot->sort_bytes, wc_sortbuf_bytes(P.wc_records));
-    if (!st && !slot->cursor) st = dev_alloc(c, 256, &slot->cursor);
-    if (st) {
-      c->serve_pending.insert(c->serve_pending.begin(), jobs.begin(), jobs.end());
-      return st;
-    }
-    MR_CUDA_TRY(cudaMemcpyAsync(slot->desc, P.bj.data(), P.bj.size() * sizeof(BatchJob), cudaMemcpyHostToDevice,
+  BatchPlan P;
+  plan_batch(jobs, c->tune, P);
+  mr_status st = ensure_scratch(c, &slot->desc, &slot->desc_bytes, P.bj.size() * sizeof(BatchJob));
+  if (!st) st = ensure_scratch(c, &slot->wcd, &slot->wcd_bytes, P.wj.size() * sizeof(wc::JobDev));
+  if (!st && !P.wj.empty()) st = ensure_scratch(c, &slot->sort, &slot->sort_bytes, wc_sortbuf_bytes(P.wc_records));
+  if (!st && !slot->cursor) st = dev_alloc(c, 256, &slot->cursor);
+  if (st) {
+    c->serve_pending.insert(c->serve_pending.begin(), jobs.begin(), jobs.end());
+    return st;
+  }
+  MR_CUDA_TRY(
+      cudaMemcpyAsync(slot->desc, P.bj.data(), P.bj.size() * sizeof(BatchJob), cudaMemcpyHostToDevice, slot->s));
+  if (!P.wj.empty())
+    MR_CUDA_TRY(cudaMemcpyAsync(slot->wcd, P.wj.data(), P.wj.size() * sizeof(wc::JobDev), cudaMemcpyHostToDevice,
                                 slot->s));
-    if (!P.wj.empty())
-      MR_CUDA_TRY(cudaMemcpyAsync(slot->wcd, P.wj.data(), P.wj.size() * sizeof(wc::JobDev), cudaMemcpyHostToDevice,
-                                  slot->s));
-    MR_CUDA_TRY(batch_prepare());
-    MR_CUDA_TRY(launch_batch(static_cast<const BatchJob*>(slot->desc), (uint32_t)P.bj.size(), P.tiles,
-                             static_cast<unsigned long long*>(slot->cursor), c->tune.arr_tile, c->tune.wc_tile,
-                             P.zchunks, c->di, slot->s, &c->launches));
-    if (!P.wj.empty())
-      MR_CUDA_TRY(launch_wordcount_post_multi(static_cast<const wc::JobDev*>(slot->wcd), P.wj.data(),
-                                              (uint32_t)P.wj.size(), P.wc_blocks, P.wc_records,
-                                              static_cast<uint8_t*>(slot->sort), c->di.sms, slot->s,
-                                              &c->launches));
-    for (Job* j : arr) {
-      if (j->t1) MR_CUDA_TRY(cudaEventRecord(j->t1, slot->s));
-      MR_CUDA_TRY(cudaEventRecord(j->done, slot->s));
-      j->state = JOB_ENQUEUED;
-    }
+  MR_CUDA_TRY(batch_prepare());
+  MR_CUDA_TRY(launch_batch(static_cast<const BatchJob*>(slot->desc), (uint32_t)P.bj.size(), P.tiles,
+                           static_cast<unsigned long long*>(slot->cursor), c->tune.arr_tile, c->tune.wc_tile,
+                           P.zchunks, c->di, slot->s, &c->launches));
+  if (!P.wj.empty())
+    MR_CUDA_TRY(launch_wordcount_post_multi(static_cast<const wc::JobDev*>(slot->wcd), P.wj.data(),
+                                            (uint32_t)P.wj.size(), P.wc_blocks, P.wc_records,
+                                            static_cast<uint8_t*>(slot->sort), c->di.sms, slot->s, &c->launches));
+  for (Job* j : jobs) {
+    if (j->t1) MR_CUDA_TRY(cudaEventRecord(j->t1, slot->s));
+    MR_CUDA_TRY(cudaEventRecord(j->done, slot->s));
+    j->state = JOB_ENQUEUED;
   }
-  int na = 0;
-  for (Job* j : jobs)
-    if (plain_only(j->desc.kind)) {
-      cudaStream_t as = slot->aux[na % mr_ctx::Slot::AUX];
-      if (na < mr_ctx::Slot::AUX) MR_CUDA_TRY(cudaStreamWaitEvent(as, c->serve_ready, 0));
-      mr_status st = enqueue_plain_on(c, j, as);
-      if (st) return st;
-      ++na;
-    }
-  // the slot is free again once its batch and its other requests are done
-  for (int a = 0; a < na && a < mr_ctx::Slot::AUX; ++a) {
-    MR_CUDA_TRY(cudaEventRecord(slot->aux_done[a], slot->aux[a]));
-    MR_CUDA_TRY(cudaStreamWaitEvent(slot->s, slot->aux_done[a], 0));
-  }
+  // the slot is free again once its micro-batch is done
   MR_CUDA_TRY(cudaEventRecord(slot->busy, slot->s));
   slot->used = true;
   return MR_OK;
@@ -1082,11 +1089,10 @@ void mr_destroy(mr_ctx* c) {
   cudaStreamSynchronize(c->stream);
   for (auto& kv : c->jobs) free_job(c, kv.second);
   c->jobs.clear();
-  for (auto& sl : c->slots) {
+  for (auto& sl : c->slots)
     if (sl.s) cudaStreamSynchronize(sl.s);
-    for (auto a : sl.aux)
-      if (a) cudaStreamSynchronize(a);
-  }
+  for (auto a : c->serve_aux)
+    if (a) cudaStreamSynchronize(a);
   drop_batch_graph(c);
   for (auto& sl : c->slots) {
     dev_free(c, sl.desc, sl.desc_bytes);
@@ -1102,11 +1108,9 @@ void mr_destroy(mr_ctx* c) {
   for (auto& sl : c->slots) {
     if (sl.busy) cudaEventDestroy(sl.busy);
     if (sl.s) cudaStreamDestroy(sl.s);
-    for (int a = 0; a < mr_ctx::Slot::AUX; ++a) {
-      if (sl.aux_done[a]) cudaEventDestroy(sl.aux_done[a]);
-      if (sl.aux[a]) cudaStreamDestroy(sl.aux[a]);
-    }
   }
+  for (auto a : c->serve_aux)
+    if (a) cudaStreamDestroy(a);
   if (c->serve_ready) cudaEventDestroy(c->serve_ready);
   for (int a = 0; a < mr_ctx::PLAIN_AUX; ++a) {
     if (c->plain_aux[a]) {
@@ -1253,6 +1257,8 @@ mr_status mr_sync(mr_ctx* c) {
   }
   for (auto& sl : c->slots)
     if (sl.s) MR_CUDA_TRY(cudaStreamSynchronize(sl.s));
+  for (auto a : c->serve_aux)
+    if (a) MR_CUDA_TRY(cudaStreamSynchronize(a));
   MR_CUDA_TRY(cudaStreamSynchronize(c->stream));
   return MR_OK;
 }
