@@ -187,14 +187,15 @@ def test_kmeans_full_size_fp32(mr):
     assert _rel_err(c10, c_upd) <= TOL
 
 
-@pytest.mark.parametrize("precision", [0, 1, 2])
-def test_kmeans_many_tiles_per_cta_teacher_forced(mr, precision):
+@pytest.mark.parametrize("precision,d", [(0, 64), (1, 64), (2, 64), (1, 21)])
+def test_kmeans_many_tiles_per_cta_teacher_forced(mr, precision, d):
     """The persistent kernels capped at 4 CTAs: each tensor-core CTA runs ~39
     tiles of 128 points (its copy ring, operand stages, TMEM accumulators and
-    key hand-off all wrap many times), each FP32 CTA ~78 tiles of 64, and each
-    update CTA ~50 chunks through its 3-stage ring.  Every assignment of every
+    key hand-off all wrap many times; D = 21: the converters' own row loads),
+    each FP32 CTA ~78 tiles of 64, and each update
+    CTA its ~5,000 points in two windows.  Every assignment of every
     iteration, started from the oracle's centroids, equals the oracle's."""
-    x, _, _ = synth.kmeans_points(20_000, 64, 256, seed=45 + precision)
+    x, _, _ = synth.kmeans_points(20_000, d, 256, seed=45 + precision)
     cur = synth.kmeans_init(x, 256, seed=46)
     dx = _dev(x)
     ctx = mr.Context()
@@ -260,6 +261,8 @@ def test_kmeans_eight_tiles_per_cta_natural_grid(mr, precision):
     (5_001, 37, 50, 2),     # D < 64 (zero-padded), K not a multiple of 16
     (777, 3, 1, 2),         # K = 1
     (300, 64, 16, 1),       # fewer points than one CTA per SM
+    (641, 1, 4, 2),         # D = 1, a last tile of one point
+    (2_050, 48, 40, 2),     # D a multiple of 16 below 64
 ])
 def test_kmeans_bf16_tensor_core_vs_oracle(mr, precision, n, d, k, iters):
     x, _, _ = synth.kmeans_points(n, d, max(1, min(k, 256)), seed=n + d + k + 7)
