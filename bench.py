@@ -807,7 +807,7 @@ def serving_eval(rate: float, duration: float, plain_duration: float) -> dict:
         ctx = mr.Context(0, stream=stream, hbm_budget=120 << 30)
         waiting = collections.deque()
         inflight = {}
-        lat, nbytes = [], 0
+        lat, kinds, nbytes = [], [], 0
         nxt = 0
         t0 = time.perf_counter()
         while nxt < len(specs) or waiting or inflight:
@@ -822,20 +822,29 @@ def serving_eval(rate: float, duration: float, plain_duration: float) -> dict:
                     if e.status != mr.MR_EBUDGET:
                         raise
                     break
-                inflight[j] = (waiting.popleft()[0], b)
+                sp = waiting.popleft()
+                inflight[j] = (sp[0], b, sp[1])
             for j in list(inflight):
                 if ctx.poll(j):
                     ctx.fetch(j)
-                    arr, b = inflight.pop(j)
+                    arr, b, kind = inflight.pop(j)
                     lat.append(time.perf_counter() - t0 - arr)
+                    kinds.append(kind)
                     nbytes += b
                     ctx.release(j)
         wall = time.perf_counter() - t0
         ctx.close()
-        lat = np.array(lat) * 1e3
+        lat, kinds = np.array(lat) * 1e3, np.array(kinds)
+        by_kind = {}
+        for kind, name in enumerate(("wordcount", "hist_rgb8", "linreg_i8", "kmeans")):
+            v = lat[kinds == kind]
+            if v.size:
+                by_kind[name] = {"requests": int(v.size), "p50_ms": round(float(np.percentile(v, 50)), 3),
+                                 "p99_ms": round(float(np.percentile(v, 99)), 3)}
         return {"requests": len(lat), "wall_s": round(wall, 3), "req_per_s": round(len(lat) / wall, 1),
                 "gbs": round(nbytes / wall / 1e9, 3), "p50_ms": round(float(np.percentile(lat, 50)), 3),
-                "p99_ms": round(float(np.percentile(lat, 99)), 3), "max_ms": round(float(lat.max()), 3)}
+                "p99_ms": round(float(np.percentile(lat, 99)), 3), "max_ms": round(float(lat.max()), 3),
+                "by_kind": by_kind}
 
     served = serve(False, specs)
     plain = serve(True, [sp for sp in specs if sp[0] < plain_duration])
