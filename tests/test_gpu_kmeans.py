@@ -263,6 +263,8 @@ def test_kmeans_eight_tiles_per_cta_natural_grid(mr, precision):
     (300, 64, 16, 1),       # fewer points than one CTA per SM
     (641, 1, 4, 2),         # D = 1, a last tile of one point
     (2_050, 48, 40, 2),     # D a multiple of 16 below 64
+    (6_000, 64, 136, 2),    # 144 columns: the last epilogue quarter idle, the third partly masked
+    (6_000, 20, 200, 2),    # 208 columns
 ])
 def test_kmeans_bf16_tensor_core_vs_oracle(mr, precision, n, d, k, iters):
     x, _, _ = synth.kmeans_points(n, d, max(1, min(k, 256)), seed=n + d + k + 7)
