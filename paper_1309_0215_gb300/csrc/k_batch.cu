@@ -132,6 +132,19 @@ __device__ void linreg_tile(const BatchJob& J, uint64_t h, uint64_t t0, uint64_t
     const uint4* vin = reinterpret_cast<const uint4*>(in + h);
     int p[5] = {0, 0, 0, 0, 0};  // at most a tile per flush: far below the int32 limit
     uint64_t v = v0 + threadIdx.x;
+    // four 16-byte loads in flight per thread, then pairs
+    for (; v + 3 * BT < v1; v += 4 * BT) {
+      uint4 w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) w[u] = arr::ldg_stream(vin + v + u * BT);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        arr::lr_word(w[u].x, p);
+        arr::lr_word(w[u].y, p);
+        arr::lr_word(w[u].z, p);
+        arr::lr_word(w[u].w, p);
+      }
+    }
     for (; v + BT < v1; v += 2 * BT) {
       uint4 a = arr::ldg_stream(vin + v);
       uint4 b = arr::ldg_stream(vin + v + BT);
