@@ -255,15 +255,16 @@ mr_status mr_release(mr_ctx* ctx, uint64_t job_id);
  * continuous-batching request loop this library adds around the Sec. II-A
  * workflow): admit a request if the context's HBM budget allows (MR_EBUDGET
  * otherwise; nothing is queued and the caller retries once results have been
- * released).  Admitted requests are batched continuously: whenever one of the
- * context's internal streams has finished its previous micro-batch, every
- * admitted request that is not running yet is launched on it as one
- * persistent batch (plus one merge + sort for its word-count requests), and
- * its k-means, large-key histogram and Bloom requests are spread over four
- * more streams of that slot so they run concurrently.  Requests that arrive while
- * others run are therefore picked up as soon as a stream frees, and
- * micro-batches overlap on the device.  mr_poll and mr_fetch also drive this
- * launching.  Containers stay resident until mr_release. */
+ * released).  Admitted k-means, large-key histogram and Bloom requests are
+ * launched at once, round robin on eight internal streams.  The others are
+ * batched continuously: whenever one of four further internal streams (at
+ * the higher stream priority) has finished its previous micro-batch, every
+ * admitted word-count, histogram and regression request that is not running
+ * yet is launched on it as one persistent batch (plus one merge + sort for
+ * its word-count requests).  Requests that arrive while others run are
+ * therefore picked up as soon as a stream frees, and micro-batches overlap
+ * on the device.  mr_poll and mr_fetch also drive this launching.
+ * Containers stay resident until mr_release. */
 mr_status mr_submit(mr_ctx* ctx, const mr_job_desc* desc, uint64_t* job_id);
 
 /* Serving companion of mr_submit (no counterpart in the paper): MR_OK when
