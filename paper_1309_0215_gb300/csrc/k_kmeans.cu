@@ -1093,17 +1093,19 @@ __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_pipe_kernel(
     if (C[i]) atomicAdd(counts + i, (unsigned long long)C[i]);
 }
 
-// Update step for D = 64 with runs sorted per window (Sec. III-E's array
+// Update step for D <= 64 with runs sorted per window (Sec. III-E's array
 // container, privatised per thread block as above, with the shared-memory
 // atomics taken out of the inner loop).  A CTA walks its contiguous range of
 // points in windows of WS_WIN.  For each window it counting-sorts the point
 // indices by cluster in shared memory (a histogram, a scan and a scatter of
 // 16-bit indices), then every warp takes an equal slice of the sorted order
-// and adds its points run by run in registers: lane l reads dimensions 2l
-// and 2l + 1 of each point (one 8-byte load; a warp reads the whole 256-byte
-// row) and keeps q = rint(x 2^s) = hi 2^20 + lo (lq_split) as two 32-bit
-// sums per dimension; when the cluster changes the run is added into the
-// CTA's int64 [k][64] sums with one 64-bit shared-memory add per dimension.
+// and adds its points run by run in registers: lane l reads two dimensions
+// of each point (D = 64 with 8-byte-aligned points: 2l and 2l + 1 with one
+// 8-byte load, so a warp reads the whole 256-byte row; otherwise l and
+// l + 32 where below D) and keeps q = rint(x 2^s) = hi 2^20 + lo (lq_split)
+// as two 32-bit sums per dimension; when the cluster changes the run is
+// added into the CTA's int64 [k][D] sums with one 64-bit shared-memory add
+// per dimension.
 // A slice holds at most WS_WIN / WS_WARPS points, so no 32-bit run sum can
 // overflow (128 * 2^19 = 2^26).  The CTA stores its sums as its partial and
 // adds its counts to the global counts, like km_local_sum_kernel; the sums are
