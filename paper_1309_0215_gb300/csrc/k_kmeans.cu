@@ -1096,7 +1096,8 @@ __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_pipe_kernel(
 // Update step for D <= 64 with runs sorted per window (Sec. III-E's array
 // container, privatised per thread block as above, with the shared-memory
 // atomics taken out of the inner loop).  A CTA walks its contiguous range of
-// points in windows of WS_WIN.  For each window it counting-sorts the point
+// points in windows of win points (8,192 where the shared memory allows,
+// else 4,096: fewer windows, fewer sort phases).  For each window it counting-sorts the point
 // indices by cluster in shared memory (a histogram, a scan and a scatter of
 // 16-bit indices), then every warp takes an equal slice of the sorted order
 // and adds its points run by run in registers: lane l reads two dimensions
@@ -1106,17 +1107,17 @@ __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_pipe_kernel(
 // as two 32-bit sums per dimension; when the cluster changes the run is
 // added into the CTA's int64 [k][D] sums with one 64-bit shared-memory add
 // per dimension.
-// A slice holds at most WS_WIN / WS_WARPS points, so no 32-bit run sum can
-// overflow (128 * 2^19 = 2^26).  The CTA stores its sums as its partial and
+// A slice holds at most WS_WIN_MAX / WS_WARPS points, so no 32-bit run sum
+// can overflow (256 * 2^19 = 2^27).  The CTA stores its sums as its partial and
 // adds its counts to the global counts, like km_local_sum_kernel; the sums are
 // the same integers in any order.  No wait of any kind: only plain loads and
 // block barriers.
 constexpr int WS_THREADS = 1024;
 constexpr int WS_WARPS = WS_THREADS / 32;
-constexpr uint32_t WS_WIN = 4096;  // points per window (16-bit positions)
+constexpr uint32_t WS_WIN_MAX = 8192;  // points per window (16-bit positions), or half that
 constexpr int WS_UNROLL = 8;       // points in flight per warp
-__host__ __device__ constexpr uint64_t ws_smem_bytes(uint64_t k, uint64_t d) {
-  return k * d * 8 + 3 * k * 4 + 3 * (uint64_t)WS_WIN * 2;
+__host__ __device__ constexpr uint64_t ws_smem_bytes(uint64_t k, uint64_t d, uint64_t win) {
+  return k * d * 8 + 3 * k * 4 + 3 * win * 2;
 }
 // add a run's split sums of dimensions j0 and j1 (when below d) into
 // cluster c's int64 sums
@@ -1130,7 +1131,7 @@ __device__ __forceinline__ void ws_flush(long long* S, uint32_t c, uint32_t d, u
 // with one 8-byte load); otherwise D <= 64, lane l dimensions l and l + 32.
 template <bool D64>
 __global__ void __launch_bounds__(WS_THREADS, 1) km_window_sum_kernel(const float* __restrict__ x, uint32_t n,
-                                                                      uint32_t d, uint32_t k,
+                                                                      uint32_t d, uint32_t k, uint32_t win,
                                                                       const int32_t* __restrict__ assign,
                                                                       const int* shift, long long* __restrict__ part,
                                                                       unsigned long long* counts) {
@@ -1141,8 +1142,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) km_window_sum_kernel(const floa
   uint32_t* off = hc + k;
   uint32_t* C = off + k;
   uint16_t* wid = reinterpret_cast<uint16_t*>(C + k);
-  uint16_t* perm = wid + WS_WIN;
-  uint16_t* pcl = perm + WS_WIN;
+  uint16_t* perm = wid + win;
+  uint16_t* pcl = perm + win;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint64_t i = threadIdx.x; i < (uint64_t)k * d; i += WS_THREADS) S[i] = 0;
   for (uint32_t i = threadIdx.x; i < k; i += WS_THREADS) C[i] = 0;
@@ -1152,8 +1153,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) km_window_sum_kernel(const floa
   const uint64_t p1 = p0 + per < (uint64_t)n ? p0 + per : (uint64_t)n;
   const float scale = ldexpf(1.f, *shift);
   const uint32_t kl = (k + 31) / 32;  // bins per lane in the scan
-  for (uint64_t w0 = p0; w0 < p1; w0 += WS_WIN) {
-    const uint32_t nr = (uint32_t)(p1 - w0 < WS_WIN ? p1 - w0 : WS_WIN);
+  for (uint64_t w0 = p0; w0 < p1; w0 += win) {
+    const uint32_t nr = (uint32_t)(p1 - w0 < win ? p1 - w0 : win);
     for (uint32_t t = threadIdx.x; t < k; t += WS_THREADS) hc[t] = 0;
     __syncthreads();  // hc cleared; the previous window's sorted order is no longer read
     for (uint32_t r = threadIdx.x; r < nr; r += WS_THREADS) {
@@ -1426,10 +1427,13 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
   }
   // the window-sorted update: D <= 64, sums and window buffers in shared
   // memory (8-byte loads for D = 64 with 8-byte-aligned points)
-  const bool wsum = local && d <= 64 && ws_smem_bytes(k, d) <= (uint64_t)di.smem_optin;
+  const uint32_t ws_win =
+      ws_smem_bytes(k, d, WS_WIN_MAX) <= (uint64_t)di.smem_optin ? WS_WIN_MAX : WS_WIN_MAX / 2;
+  const bool wsum = local && d <= 64 && ws_smem_bytes(k, d, ws_win) <= (uint64_t)di.smem_optin;
   const bool ws64 = d == 64 && (reinterpret_cast<uintptr_t>(x) & 7) == 0;
   if (wsum && (e = cudaFuncSetAttribute(ws64 ? km_window_sum_kernel<true> : km_window_sum_kernel<false>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem_bytes(k, d))) !=
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)ws_smem_bytes(k, d, ws_win))) !=
                   cudaSuccess)
     return e;
   uint32_t ls_grid = (uint32_t)di.sms < LS_MAX_CTAS ? (uint32_t)di.sms : LS_MAX_CTAS;
@@ -1502,8 +1506,8 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
     if (local) {  // update with local arrays
       if (wsum)
         e = launch_pdl(ws64 ? km_window_sum_kernel<true> : km_window_sum_kernel<false>, dim3(ls_grid),
-                       dim3(WS_THREADS), (size_t)ws_smem_bytes(k, d), s, x, n, d, k, (const int32_t*)b.assign,
-                       (const int*)shift, b.part, b.counts);
+                       dim3(WS_THREADS), (size_t)ws_smem_bytes(k, d, ws_win), s, x, n, d, k, ws_win,
+                       (const int32_t*)b.assign, (const int*)shift, b.part, b.counts);
       else if (lp_rows)
         e = launch_pdl(d == 64 ? km_local_sum_pipe_kernel<true> : km_local_sum_pipe_kernel<false>, dim3(ls_grid),
                        dim3(LS_THREADS), (size_t)lp_bytes, s, x, n, d, k, (const int32_t*)b.assign, (const int*)shift,

@@ -211,13 +211,15 @@ def test_kmeans_many_tiles_per_cta_teacher_forced(mr, precision, d):
     ctx.close()
 
 
-@pytest.mark.parametrize("d,k", [(64, 256), (64, 17), (48, 256), (37, 17), (33, 100), (8, 64), (1, 5)])
+@pytest.mark.parametrize("d,k", [(64, 256), (64, 17), (64, 380), (48, 256), (37, 17), (33, 100), (8, 64), (1, 5)])
 def test_kmeans_window_update_many_windows(mr, d, k):
-    """The update for D <= 64 sorts each window of 4,096 points by cluster and
-    sums runs in registers (lanes past D idle).  Two CTAs: each walks two full
-    windows and a ragged third (10,001 points each), so the window loop, the
-    per-window histogram and scatter and the run flushes across windows are
-    all exercised, against the oracle's update from the same assignment."""
+    """The update for D <= 64 sorts each window of 8,192 points (4,096 when
+    the K x D sums leave too little shared memory: K = 380 at D = 64) by
+    cluster and sums runs in registers (lanes past D idle).  Two CTAs of
+    10,001 points each: a full window and a ragged one (4,096: two full and a
+    ragged third), so the window loop, the per-window histogram and scatter
+    and the run flushes across windows are all exercised, against the
+    oracle's update from the same assignment."""
     import torch
     x, _, _ = synth.kmeans_points(20_002, d, min(k, 64), seed=71 + k + d)
     dx = torch.from_numpy(x).cuda()
