@@ -1131,10 +1131,11 @@ __device__ __forceinline__ void ws_flush(long long* S, uint32_t c, uint32_t d, u
 // with one 8-byte load); otherwise D <= 64, lane l dimensions l and l + 32.
 template <bool D64>
 __global__ void __launch_bounds__(WS_THREADS, 1) km_window_sum_kernel(const float* __restrict__ x, uint32_t n,
-                                                                      uint32_t d, uint32_t k, uint32_t win,
+                                                                      uint32_t d_arg, uint32_t k, uint32_t win,
                                                                       const int32_t* __restrict__ assign,
                                                                       const int* shift, long long* __restrict__ part,
                                                                       unsigned long long* counts) {
+  const uint32_t d = D64 ? 64u : d_arg;  // a constant on the 64-wide path
   pdl_wait();
   extern __shared__ __align__(16) unsigned char ws_sm[];
   long long* S = reinterpret_cast<long long*>(ws_sm);
