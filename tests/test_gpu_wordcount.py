@@ -62,7 +62,7 @@ def test_wc_tokens_straddle_segments_and_long_keys(mr):
 
 @pytest.mark.slow
 def test_wc_large_input_path_edge_content(mr):
-    """Aligned inputs from 64 MiB take the CTA-table map kernel (a shared
+    """Aligned inputs from 32 MiB take the CTA-table map kernel (a shared
     table per CTA, batched global inserts, segments loaded ahead).  80 MiB of
     adversarial content: tokens of 1..40 bytes and a few of 600 and 1300
     (so keys straddle 512- and 1024-byte boundaries and long keys are
@@ -138,6 +138,15 @@ def test_wc_zipf_16MiB_bit_exact(mr):
     assert got == ref
     recs = oracle.parse_wordcount(got)
     assert sum(c for _, c in recs) == len(ranks)
+
+
+def test_wc_zipf_40MiB_cta_kernel_bit_exact(mr):
+    """40 MiB of Zipf text (16-byte aligned): just above the size from which
+    the CTA-table map kernel runs."""
+    text, ranks, _ = synth.wc_text(40 << 20, seed=synth.SEED_BASE + 12)
+    got = mr.wordcount(_dev(text))
+    assert got == oracle.wordcount(text)
+    assert sum(c for _, c in oracle.parse_wordcount(got)) == len(ranks)
 
 
 _BIG = {}
