@@ -1100,10 +1100,10 @@ __global__ void __launch_bounds__(LS_THREADS, 1) km_local_sum_pipe_kernel(
 // else 4,096: fewer windows, fewer sort phases).  For each window it counting-sorts the point
 // indices by cluster in shared memory (a histogram, a scan and a scatter of
 // 16-bit indices), then every warp takes an equal slice of the sorted order
-// and adds its points run by run in registers: lane l reads two dimensions
-// of each point (D = 64 with 8-byte-aligned points: 2l and 2l + 1 with one
-// 8-byte load, so a warp reads the whole 256-byte row; otherwise l and
-// l + 32 where below D) and keeps q = rint(x 2^s) = hi 2^20 + lo (lq_split)
+// and adds its points run by run in registers: lane l reads up to two
+// dimensions of each point (D = 64 with 8-byte-aligned points: 2l and
+// 2l + 1 with one 8-byte load, so a warp reads the whole 256-byte row;
+// otherwise l and l + 32 where below D) and keeps q = rint(x 2^s) = hi 2^20 + lo (lq_split)
 // as two 32-bit sums per dimension; when the cluster changes the run is
 // added into the CTA's int64 [k][D] sums with one 64-bit shared-memory add
 // per dimension.
@@ -1119,23 +1119,28 @@ constexpr int WS_UNROLL = 8;       // points in flight per warp
 __host__ __device__ constexpr uint64_t ws_smem_bytes(uint64_t k, uint64_t d, uint64_t win) {
   return k * d * 8 + 3 * k * 4 + 3 * win * 2;
 }
-// add a run's split sums of dimensions j0 and j1 (when below d) into
+// add a run's split sums of dimensions j0 and (TWO) j1, when below d, into
 // cluster c's int64 sums
+template <bool TWO>
 __device__ __forceinline__ void ws_flush(long long* S, uint32_t c, uint32_t d, uint32_t j0, uint32_t j1, int h0,
                                          int l0, int h1, int l1) {
   unsigned long long* p = reinterpret_cast<unsigned long long*>(S + (uint64_t)c * d);
   if (j0 < d) atomicAdd(p + j0, (unsigned long long)((long long)h0 * (1ll << 20) + (long long)l0));
-  if (j1 < d) atomicAdd(p + j1, (unsigned long long)((long long)h1 * (1ll << 20) + (long long)l1));
+  if (TWO && j1 < d) atomicAdd(p + j1, (unsigned long long)((long long)h1 * (1ll << 20) + (long long)l1));
 }
-// D64: D = 64 with 8-byte-aligned rows (lane l reads dimensions 2l, 2l + 1
-// with one 8-byte load); otherwise D <= 64, lane l dimensions l and l + 32.
-template <bool D64>
+// Lanes and dimensions by MODE: WS_D64, D = 64 with 8-byte-aligned rows
+// (lane l reads dimensions 2l, 2l + 1 with one 8-byte load); WS_D32,
+// D <= 32 (lane l dimension l); WS_DANY, D <= 64 (lane l dimensions l and
+// l + 32).
+enum { WS_D64 = 0, WS_D32 = 1, WS_DANY = 2 };
+template <int MODE>
 __global__ void __launch_bounds__(WS_THREADS, 1) km_window_sum_kernel(const float* __restrict__ x, uint32_t n,
                                                                       uint32_t d_arg, uint32_t k, uint32_t win,
                                                                       const int32_t* __restrict__ assign,
                                                                       const int* shift, long long* __restrict__ part,
                                                                       unsigned long long* counts) {
-  const uint32_t d = D64 ? 64u : d_arg;  // a constant on the 64-wide path
+  const uint32_t d = MODE == WS_D64 ? 64u : d_arg;  // a constant on the 64-wide path
+  constexpr bool TWO = MODE != WS_D32;            // two dimensions per lane
   pdl_wait();
   extern __shared__ __align__(16) unsigned char ws_sm[];
   long long* S = reinterpret_cast<long long*>(ws_sm);
@@ -1148,7 +1153,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) km_window_sum_kernel(const floa
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint64_t i = threadIdx.x; i < (uint64_t)k * d; i += WS_THREADS) S[i] = 0;
   for (uint32_t i = threadIdx.x; i < k; i += WS_THREADS) C[i] = 0;
-  const uint32_t j0 = D64 ? 2 * (uint32_t)lane : (uint32_t)lane, j1 = D64 ? j0 + 1 : j0 + 32;
+  const uint32_t j0 = MODE == WS_D64 ? 2 * (uint32_t)lane : (uint32_t)lane;
+  const uint32_t j1 = MODE == WS_D64 ? j0 + 1 : j0 + 32;
   const uint64_t per = ((uint64_t)n + gridDim.x - 1) / gridDim.x;
   const uint64_t p0 = (uint64_t)blockIdx.x * per;
   const uint64_t p1 = p0 + per < (uint64_t)n ? p0 + per : (uint64_t)n;
@@ -1213,17 +1219,17 @@ __global__ void __launch_bounds__(WS_THREADS, 1) km_window_sum_kernel(const floa
           const bool ok = qq < q1;
           cl[u] = ok ? pcl[qq] : cur;
           const float* row = X + (uint64_t)(ok ? perm[qq] : 0) * d;
-          if (D64) {
+          if (MODE == WS_D64) {
             v[u] = ok ? __ldg(reinterpret_cast<const float2*>(row) + lane) : make_float2(0.f, 0.f);
           } else {
             v[u].x = ok && j0 < d ? __ldg(row + j0) : 0.f;
-            v[u].y = ok && j1 < d ? __ldg(row + j1) : 0.f;
+            v[u].y = TWO && ok && j1 < d ? __ldg(row + j1) : 0.f;
           }
         }
 #pragma unroll
         for (int u = 0; u < WS_UNROLL; ++u) {
           if (cl[u] != cur) {  // warp-uniform: the run of cluster cur ended
-            ws_flush(S, cur, d, j0, j1, h0, l0, h1, l1);
+            ws_flush<TWO>(S, cur, d, j0, j1, h0, l0, h1, l1);
             h0 = l0 = h1 = l1 = 0;
             cur = cl[u];
           }
@@ -1231,12 +1237,14 @@ __global__ void __launch_bounds__(WS_THREADS, 1) km_window_sum_kernel(const floa
           lq_split(v[u].x * scale, a, b);
           h0 += a;
           l0 += b;
-          lq_split(v[u].y * scale, a, b);
-          h1 += a;
-          l1 += b;
+          if (TWO) {
+            lq_split(v[u].y * scale, a, b);
+            h1 += a;
+            l1 += b;
+          }
         }
       }
-      ws_flush(S, cur, d, j0, j1, h0, l0, h1, l1);
+      ws_flush<TWO>(S, cur, d, j0, j1, h0, l0, h1, l1);
     }
   }
   __syncthreads();
@@ -1431,11 +1439,11 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
   const uint32_t ws_win =
       ws_smem_bytes(k, d, WS_WIN_MAX) <= (uint64_t)di.smem_optin ? WS_WIN_MAX : WS_WIN_MAX / 2;
   const bool wsum = local && d <= 64 && ws_smem_bytes(k, d, ws_win) <= (uint64_t)di.smem_optin;
-  const bool ws64 = d == 64 && (reinterpret_cast<uintptr_t>(x) & 7) == 0;
-  if (wsum && (e = cudaFuncSetAttribute(ws64 ? km_window_sum_kernel<true> : km_window_sum_kernel<false>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)ws_smem_bytes(k, d, ws_win))) !=
-                  cudaSuccess)
+  auto ws_kernel = d == 64 && (reinterpret_cast<uintptr_t>(x) & 7) == 0 ? km_window_sum_kernel<WS_D64>
+                   : d <= 32                                               ? km_window_sum_kernel<WS_D32>
+                                                                           : km_window_sum_kernel<WS_DANY>;
+  if (wsum && (e = cudaFuncSetAttribute(ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)ws_smem_bytes(k, d, ws_win))) != cudaSuccess)
     return e;
   uint32_t ls_grid = (uint32_t)di.sms < LS_MAX_CTAS ? (uint32_t)di.sms : LS_MAX_CTAS;
   if ((uint64_t)ls_grid * 1024 > n) ls_grid = (uint32_t)((n + 1023) / 1024);
@@ -1506,7 +1514,7 @@ cudaError_t launch_kmeans(const float* x, const float* init, uint32_t iters, KmB
     *nk += 2;  // re-check, FP64 stage
     if (local) {  // update with local arrays
       if (wsum)
-        e = launch_pdl(ws64 ? km_window_sum_kernel<true> : km_window_sum_kernel<false>, dim3(ls_grid),
+        e = launch_pdl(ws_kernel, dim3(ls_grid),
                        dim3(WS_THREADS), (size_t)ws_smem_bytes(k, d, ws_win), s, x, n, d, k, ws_win,
                        (const int32_t*)b.assign, (const int*)shift, b.part, b.counts);
       else if (lp_rows)
