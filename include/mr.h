@@ -256,7 +256,7 @@ mr_status mr_release(mr_ctx* ctx, uint64_t job_id);
  * workflow): admit a request if the context's HBM budget allows (MR_EBUDGET
  * otherwise; nothing is queued and the caller retries once results have been
  * released).  Admitted k-means, large-key histogram and Bloom requests are
- * launched at once, round robin on eight internal streams.  The others are
+ * launched at once, round robin on three internal streams.  The others are
  * batched continuously: whenever one of four further internal streams (at
  * the higher stream priority) has finished its previous micro-batch, every
  * admitted word-count, histogram and regression request that is not running

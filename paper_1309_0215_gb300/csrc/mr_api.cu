@@ -126,8 +126,9 @@ struct mr_ctx {
   static constexpr int SERVE_SLOTS = 4;
   Slot slots[SERVE_SLOTS];
   // plain-only requests (k-means, large-key histogram, Bloom) need no slot:
-  // they run on these streams, round robin, beside the micro-batches
-  static constexpr int SERVE_AUX = 8;
+  // they run on these streams, round robin, beside the micro-batches (three:
+  // more k-means jobs interleaved only stretch each one's latency)
+  static constexpr int SERVE_AUX = 3;
   cudaStream_t serve_aux[SERVE_AUX] = {};
   uint32_t serve_aux_next = 0;
   std::vector<Job*> serve_pending;  // admitted, waiting for a free slot
