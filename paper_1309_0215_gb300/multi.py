@@ -5,8 +5,9 @@ is cut into independent splits, and the intermediate pairs are partitioned
 by key for the reduce): each rank runs the job on its own slice with the
 single-GPU library, then
 
-* array containers (RGB histogram, regression sums) are combined with one
-  all-reduce (sum) of the container;
+* array containers (RGB histogram, regression sums, large-key histogram)
+  are combined with one all-reduce (sum) of the container, and Bloom
+  filters with a bitwise OR of their bit arrays;
 * word count is combined in the paper's partition step: every rank sends
   each of its (key, count) records to the rank that owns the key's hash
   partition (one all-to-all), each rank adds up the counts of its partition
@@ -14,8 +15,11 @@ single-GPU library, then
   result layout of include/mr.h.
 
 Slices are cut where no work unit straddles two of them: on a multiple of 3
-bytes (pixels) or 2 bytes (pairs), and for text just after an ASCII
-whitespace byte, so every token lies in exactly one slice.
+bytes (pixels), 2 bytes (pairs) or 4 bytes (keys), and for text just after
+an ASCII whitespace byte, so every token lies in exactly one slice.  A
+Bloom job's slices own the windows that start in them and overlap the next
+slice by one window less a base, so every window lies whole in exactly one
+slice.
 
 The functions here move and reorder results between ranks; the map and
 combine work itself runs in the library's kernels on each rank.  The merge
@@ -29,7 +33,7 @@ import zlib
 
 import numpy as np
 
-from . import HIST_RGB8, LINREG_I8, WORDCOUNT
+from . import BLOOM_DNA, HIST_RGB8, HIST_U32, LINREG_I8, WORDCOUNT
 
 _WS = frozenset(b" \t\n\v\f\r")
 
@@ -49,17 +53,25 @@ def _whitespace_at_or_after(read, n, pos):
     return n
 
 
-def shard_bounds(kind, n, world, rank, read=None):
+def shard_bounds(kind, n, world, rank, read=None, kmer=None):
     """Byte range [lo, hi) of rank's slice of an n-byte input.
 
-    kind: HIST_RGB8 (slices of whole pixels), LINREG_I8 (whole pairs) or
-    WORDCOUNT (each boundary moved forward to the next whitespace byte, so no
-    token is cut; read(lo, hi) must return input bytes [lo, hi)).  The
+    kind: HIST_RGB8 (slices of whole pixels), LINREG_I8 (whole pairs),
+    HIST_U32 (whole 4-byte keys), WORDCOUNT (each boundary moved forward to
+    the next whitespace byte, so no token is cut; read(lo, hi) must return
+    input bytes [lo, hi)) or BLOOM_DNA (kmer: the window length; the slice
+    holds the windows that start in rank's share of the positions, so it
+    runs kmer - 1 bytes into the next share).  Except for BLOOM_DNA, the
     slices of ranks 0 .. world-1 cover [0, n) without overlap."""
     if world < 1 or not 0 <= rank < world:
         raise ValueError("bad world size or rank")
-    if kind in (HIST_RGB8, LINREG_I8):
-        unit = 3 if kind == HIST_RGB8 else 2
+    if kind == BLOOM_DNA:
+        if not kmer or kmer < 1:
+            raise ValueError("a Bloom job needs its window length")
+        lo, hi = n * rank // world, n * (rank + 1) // world
+        return lo, min(n, hi + kmer - 1)
+    if kind in (HIST_RGB8, LINREG_I8, HIST_U32):
+        unit = {HIST_RGB8: 3, LINREG_I8: 2, HIST_U32: 4}[kind]
         if n % unit:
             raise ValueError("input length is not a multiple of the record size")
         units = n // unit
@@ -85,11 +97,32 @@ def reader(data):
 
 
 def allreduce_sum(t, group=None):
-    """Sum an array container (768 histogram bins or the five regression sums,
-    int64) over all ranks, in place; returns t."""
+    """Sum an array container (768 histogram bins, the five regression sums or
+    a large-key histogram's bins; int64) over all ranks, in place; returns t."""
     import torch.distributed as dist
     dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
     return t
+
+
+def allreduce_or(t, group=None):
+    """Bitwise OR of a Bloom filter's bit array (uint8) over all ranks, in
+    place; returns t.  The ranks' arrays are gathered and ORed where t lives
+    (NCCL has no bitwise reduction)."""
+    import torch
+    import torch.distributed as dist
+    parts = [torch.empty_like(t) for _ in range(dist.get_world_size(group))]
+    dist.all_gather(parts, t, group=group)
+    for p in parts:
+        t.bitwise_or_(p)
+    return t
+
+
+def merge_bloom_local(arrays):
+    """The whole input's Bloom filter from its slices' filters, in one process."""
+    out = np.zeros_like(np.asarray(arrays[0], dtype=np.uint8))
+    for a in arrays:
+        out |= np.asarray(a, dtype=np.uint8)
+    return out
 
 
 # ---------------------------------------------------------------- word count

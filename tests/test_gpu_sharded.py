@@ -40,3 +40,22 @@ def test_sharded_arrays_equal_whole_input(mr):
         s += np.asarray(mr.linreg_i8(dx[lo:hi]), dtype=np.int64)
     assert np.array_equal(h, oracle.hist_rgb8(px).astype(np.uint64))
     assert s.tolist() == oracle.linreg_i8(xy).tolist()
+
+
+def test_sharded_keys_and_bloom_equal_whole_input(mr):
+    """Large-key histogram and Bloom filter over three slices each (the Bloom
+    slices overlapping by a window less a base), merged by sum and OR."""
+    import torch
+    from paper_1309_0215_gb300 import multi
+    keys = synth.keys_u32(3_000_001, 1 << 20, seed=synth.SEED_BASE + 44)
+    seq = synth.dna(2_000_003, seed=synth.SEED_BASE + 45, n_runs=200, max_run=100)
+    dk, ds = torch.from_numpy(keys).cuda(), torch.from_numpy(seq).cuda()
+    h = np.zeros((1 << 20) + 1, dtype=np.uint64)
+    blooms = []
+    for r in range(3):
+        lo, hi = multi.shard_bounds(mr.HIST_U32, dk.numel() * 4, 3, r)
+        h += mr.hist_u32(dk[lo // 4:hi // 4], 1 << 20)
+        lo, hi = multi.shard_bounds(mr.BLOOM_DNA, ds.numel(), 3, r, kmer=32)
+        blooms.append(mr.bloom_dna(ds[lo:hi], 32, 20_000_003, 7))
+    assert np.array_equal(h, oracle.hist_u32(keys, 1 << 20))
+    assert np.array_equal(multi.merge_bloom_local(blooms), oracle.bloom_dna(seq, 32, 20_000_003, 7))

@@ -95,6 +95,63 @@ def test_sharded_jobs_merge_to_the_whole_input_result(ws):
         assert r[2] == h_ref and r[3] == r_ref
 
 
+def _merge_keys_rank(rank, ws, port, q, keys, seq):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import oracle
+    from paper_1309_0215_gb300 import multi, HIST_U32, BLOOM_DNA
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    lo, hi = multi.shard_bounds(HIST_U32, len(keys), ws, rank)
+    h = oracle.hist_u32(np.frombuffer(keys[lo:hi], dtype=np.uint32), 5000)
+    ht = torch.from_numpy(h.view(np.int64).copy())
+    multi.allreduce_sum(ht)
+    lo, hi = multi.shard_bounds(BLOOM_DNA, len(seq), ws, rank, kmer=32)
+    bt = torch.from_numpy(oracle.bloom_dna(seq[lo:hi], 32, 100_003, 7))
+    multi.allreduce_or(bt)
+    q.put((rank, ht.numpy().tobytes(), bt.numpy().tobytes()))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("ws", [2, 3])
+def test_sharded_keys_and_bloom_merge_to_the_whole_input_result(ws):
+    """Large-key histogram slices summed with one all-reduce, Bloom-filter
+    slices (each owning the windows that start in it) ORed, against the
+    oracle on the whole input."""
+    import numpy as np
+    import oracle
+    import synth
+    keys = synth.keys_u32(40_001, 6000, seed=synth.SEED_BASE + 34).tobytes()
+    seq = synth.dna(30_011, seed=synth.SEED_BASE + 35, n_runs=20, max_run=40).tobytes()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_merge_keys_rank, args=(r, ws, port, q, keys, seq)) for r in range(ws)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=300) for _ in range(ws))
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    h_ref = oracle.hist_u32(np.frombuffer(keys, dtype=np.uint32), 5000).tobytes()
+    b_ref = oracle.bloom_dna(seq, 32, 100_003, 7).tobytes()
+    for r in res:
+        assert r[1] == h_ref and r[2] == b_ref
+
+
+def test_bloom_shards_hold_every_window_once():
+    """Each window start belongs to exactly one slice, and that slice holds
+    the whole window (brute force over small inputs and world sizes)."""
+    from paper_1309_0215_gb300 import multi, BLOOM_DNA
+    for n, L in ((1000, 32), (97, 5), (10, 16), (64, 1)):
+        for ws in (1, 2, 3, 7):
+            b = [multi.shard_bounds(BLOOM_DNA, n, ws, r, kmer=L) for r in range(ws)]
+            for p in range(0, n - L + 1):
+                inside = [r for r, (lo, hi) in enumerate(b) if lo <= p and p + L <= hi]
+                assert len(inside) == 1, (n, L, ws, p, inside)
+
+
 def test_shard_bounds_never_cut_a_token():
     import oracle
     from paper_1309_0215_gb300 import multi, WORDCOUNT
